@@ -1,0 +1,66 @@
+"""The oracle's pins must catch plausible mistakes. Each case plants one
+mistake in a copy of pg_oracle.c (on the CPU), builds it, and runs the pin
+suite against it: the suite has to fail."""
+
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "pg_oracle.c")
+PINS = ["tests/test_oracle_newton.py", "tests/test_oracle_table.py", "tests/test_oracle_grad.py"]
+
+MUTATIONS = {
+    "potential sign": ("nadd(&ph, -m / rh);", "nadd(&ph, m / rh);", 0),
+    "list-mode potential sign": ("nadd(&ph, -m / rh);", "nadd(&ph, m / rh);", 1),
+    "softening dropped": ("dz * dz + c->eps2;   /* r^2 + eps^2 */", "dz * dz;"),
+    "difference transposed": ("double dx = c->xj[3 * j] - xi;", "double dx = xi - c->xj[3 * j];", 0),
+    "list-mode difference transposed": ("double dx = c->xj[3 * j] - xi;",
+                                        "double dx = xi - c->xj[3 * j];", 1),
+    "kernel exponent": ("double k3 = m / (rh2 * rh);                           /* m / r_hat^3 */",
+                        "double k3 = m / rh2;"),
+    "self not skipped": ("            if (j == sk) continue;\n            double dx = c->xj[3 * j] - xi;",
+                         "            double dx = c->xj[3 * j] - xi;"),
+    "bin exponent off by one": ("int bE = e - 2;", "int bE = e - 1;"),
+    "knot exponent": ("return ldexp(1.0 + (double)bF / (double)nF, (int)bE + 1);",
+                      "return ldexp(1.0 + (double)bF / (double)nF, (int)bE);"),
+    "s_max fraction": ("(2.0 - ldexp(1.0, -F))", "(2.0 - ldexp(1.0, -F - 1))"),
+    "cutoff entry kept": ("            G0[k] = 0.0f;\n            G1[k] = 0.0f;",
+                          "            G0[k] = v[k];\n            G1[k] = 0.0f;"),
+    "interpolation anchor": ("return (double)G0[k] + (s - orc_knot(E, F, k)) * (double)G1[k];",
+                             "return (double)G0[k] + (s - orc_knot(E, F, k + 1)) * (double)G1[k];"),
+    "S2 denominator": ("70.0 * x4 - 48.0 * x5 + 7.0 * x6) / (35.0 * a * a);",
+                       "70.0 * x4 - 48.0 * x5 + 7.0 * x6) / (35.0 * a * a * a);"),
+    "Gaussian term dropped": ("double w = erfc(u) + (r / (rs * sqrt(M_PI))) * exp(-u * u);",
+                              "double w = erfc(u);"),
+    "periodic image": ("if (box > 0.0) d -= box * nearbyint(d / box);",
+                       "if (box > 0.0) d -= box * floor(d / box);"),
+    "gradient second sum sign": ("nadd(&gx[q], -M->m[o] * (K * wk[q]", "nadd(&gx[q], M->m[o] * (K * wk[q]"),
+    "kernel derivative": ("*Kp = -1.5 * (*K) / rh2;", "*Kp = -0.5 * (*K) / rh2;"),
+    "hat weight": ("acc[kb] += pw * (1.0 - t);", "acc[kb] += pw * t;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_mutation(name, tmp_path):
+    old, new, *which = MUTATIONS[name]
+    src = open(SRC).read()
+    if which:       # the anchor recurs: plant the mistake in one occurrence
+        parts = src.split(old)
+        k = which[0]
+        assert len(parts) > k + 1, f"mutation anchor missing for {name}"
+        src = old.join(parts[:k + 1]) + new + old.join(parts[k + 1:])
+    else:
+        assert src.count(old) == 1, f"mutation anchor not unique for {name}"
+        src = src.replace(old, new)
+    mut = tmp_path / "pg_oracle_mut.c"
+    mut.write_text(src)
+    so = tmp_path / "liborc_mut.so"
+    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-o", str(so), str(mut), "-lm", "-lpthread"],
+                   check=True)
+    env = dict(os.environ, PG_ORACLE_LIB=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
