@@ -1,0 +1,422 @@
+"""Benchmark of the pairwise force loop on GB300.
+
+Workload (default): the 2^20-particle all-pairs Newton set, half a Plummer
+sphere and half a uniform cube of side 4, log-uniform masses, eps = 1e-3,
+FP64 positions with FP32 offsets from FP64 tile centres and compensated
+accumulation. One step = one force evaluation of every particle from every
+particle (i staging and ordering, pair loop, reduction and output), 2^40
+pair evaluations. Metric: interactions per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line. ``--impl reference`` times the FP64 CPU oracle on the
+host cores on a bounded sample of the same workload instead.
+Under torchrun (N > 1) the i-range is split across ranks (strong scaling, no
+data-path collective: every rank generates the same seeded inputs).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gen  # noqa: E402
+
+N_PART = 1 << 20
+EPS = 1e-3
+NEWTON_OPS = 13          # FP32-pipe lane-ops per Newton interaction (f32x2 counts 2)
+FP32_LANES_PER_SM = 128
+PAPER_FLOPS_PER_INT = 38
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pg", choices=["pg", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-rows", action="store_true")
+    ap.add_argument("--n", type=int, default=N_PART,
+                    help="particle count (default: the 2^20 workload; smaller for profiling)")
+    ap.add_argument("--quick", action="store_true",
+                    help="timed steps only: no e2e, extra rows or CPU baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def shard(n, rank, world):
+    """Contiguous i-range [lo, hi) of `rank` among `world` ranks."""
+    lo = (n * rank) // world
+    hi = (n * (rank + 1)) // world
+    return lo, hi
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_baseline(x, m, target_s=12.0):
+    """The FP64 oracle as it stands, timed on this host's cores on a bounded
+    sample of i against all j (interactions/s)."""
+    import oracle
+    oracle.build()
+    nth = oracle.nthreads()
+    # calibrate on a small sample, then size the timed sample
+    idx = gen.sample_indices(len(x), 64, 4242)
+    t0 = time.perf_counter()
+    oracle.newton_subset(x, m, EPS, idx, nthreads_=nth)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    k = int(min(len(x), max(64, 64 * target_s / dt)))
+    idx = gen.sample_indices(len(x), k, 4243)
+    t0 = time.perf_counter()
+    oracle.newton_subset(x, m, EPS, idx, nthreads_=nth)
+    dt = time.perf_counter() - t0
+    pairs = len(idx) * len(x)
+    return {"value": pairs / dt, "unit": "interactions/s", "cores": nth, "kind": "oracle",
+            "sample": f"{len(idx)} i-particles x {len(x)} j-particles of the same set "
+                      f"({pairs:.3e} FP64 pairs, {dt:.1f} s)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if world > 1 and rank != 0:
+        return
+    x, m = gen.plummer_cube_mix(N_PART, gen.CONFIG_SEEDS[2])
+    import oracle
+    oracle.build()
+    nth = oracle.nthreads()
+    # size each step so that warm-up plus timed steps end within a few minutes
+    idx = gen.sample_indices(N_PART, 32, 77)
+    t0 = time.perf_counter()
+    oracle.newton_subset(x, m, EPS, idx, nthreads_=nth)
+    per32 = max(time.perf_counter() - t0, 1e-3)
+    k = int(max(32, min(N_PART, 32 * 8.0 / per32)))
+    idx = gen.sample_indices(N_PART, k, 78)
+    for _ in range(args.warmup):
+        oracle.newton_subset(x, m, EPS, idx[:32], nthreads_=nth)
+    times = []
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.newton_subset(x, m, EPS, idx, nthreads_=nth)
+        times.append(time.perf_counter() - t0)
+    pairs = len(idx) * N_PART
+    value = pairs * len(times) / sum(times)
+    line = {
+        "impl": "reference", "metric": "interactions/s", "value": value, "unit": "interactions/s",
+        "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "newton-allpairs-2^20-plummer+cube", "n": N_PART, "eps": EPS,
+                   "sample_i_per_step": len(idx)},
+        "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": nth, "kind": "oracle",
+                         "sample": f"{len(idx)} i x {N_PART} j per step"},
+        "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def gauss_split(r, rs, eps):
+    """Short-range part of the TreePM Gaussian split, softened: f(r)/r."""
+    u = r / (2 * rs)
+    w = math.erfc(u) + r / (rs * math.sqrt(math.pi)) * math.exp(-u * u)
+    return w / (r * r + eps * eps) ** 1.5
+
+
+def extra_rows(pg, torch, dev):
+    """Throughput of other rows of the path (not the headline): the 4096-body
+    Plummer call (latency-bound) and the tabulated all-pairs kernel."""
+    rows = {}
+    x, m = gen.plummer(4096, gen.CONFIG_SEEDS[1])
+    xd = torch.tensor(x, device=dev)
+    md = torch.tensor(m, device=dev)
+    a = torch.empty_like(xd)
+    p = torch.empty_like(md)
+    st = torch.cuda.current_stream()
+    with pg.Context(dev.index or 0) as c:
+        c.set_stream(st.cuda_stream)
+        c.set_eps(1 / 64)
+        c.set_self(True)
+        c.set_graph(True)
+        c.set_j_dev(xd, md)
+        c.set_i_dev(xd)
+        for _ in range(20):
+            c.run_dev(a, p)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 200
+        e0.record(st)
+        for _ in range(reps):
+            c.run_dev(a, p)
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        rows["newton_plummer_4096"] = {"interactions_per_s": 4096 * 4096 / (ms * 1e-3),
+                                       "us_per_call": ms * 1e3, "graph": True}
+    # tabulated all-pairs: 65536 Plummer, Gaussian-split shape, r_cut = 0.1, E=3, F=5
+    n = 65536
+    x, m = gen.plummer(n, gen.CONFIG_SEEDS[5])
+    r_cut = 0.1
+    xd = torch.tensor(x, device=dev)
+    md = torch.tensor(m, device=dev)
+    a = torch.empty_like(xd)
+    with pg.Context(dev.index or 0) as c:
+        c.set_stream(st.cuda_stream)
+        c.set_mode(pg.PG_TABLE)
+        c.set_table(lambda r: gauss_split(r, r_cut / 4.5, 1 / 64), r_cut, 3, 5)
+        c.set_self(True)
+        c.set_timing(True)
+        c.set_j_dev(xd, md)
+        c.set_i_dev(xd)
+        for _ in range(3):
+            c.run_dev(a)
+        ks = []
+        for _ in range(5):
+            c.run_dev(a)
+            ks.append(c.kernel_time())
+        kms = statistics.median(ks)
+        rows["table_allpairs_65536_E3F5"] = {"interactions_per_s": n * n / (kms * 1e-3),
+                                             "kernel_ms": kms}
+    return rows
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+    import paper_1203_4037_gb300 as pg
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    pg.build()
+
+    npart = args.n
+    if args.quick:
+        args.no_rows = args.no_cpu_baseline = True
+    x, m = gen.plummer_cube_mix(npart, gen.CONFIG_SEEDS[2])
+    lo, hi = shard(npart, rank, world)
+    ni = hi - lo
+    st = torch.cuda.current_stream()
+    xj = torch.tensor(x, device=dev)
+    mj = torch.tensor(m, device=dev)
+    xi = xj[lo:hi].contiguous()
+    acc = torch.empty((ni, 3), dtype=torch.float64, device=dev)
+    pot = torch.empty(ni, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
+
+    ctx = pg.Context(local)
+    ctx.set_stream(st.cuda_stream)
+    ctx.set_eps(EPS)
+    ctx.set_timing(True)
+    ctx.set_j_dev(xj, mj)
+    # the i-particles of this rank are j-particles lo .. hi-1: self pairs drop
+    # out through the self mode only when the ranges coincide (world == 1)
+    ctx.set_self(world == 1)
+    ctx.set_i_dev(xi)
+
+    def step():
+        ctx.set_i_dev(xi)            # i staging every step (positions change in a run)
+        ctx.run_dev(acc, pot)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kern_ms = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(k & 255)         # evict L2 between timed steps (not timed)
+        ev[k][0].record(st)
+        step()
+        ev[k][1].record(st)
+        kern_ms.append(ctx.kernel_time())
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    info = ctx.info()
+    pairs_job = npart * npart                      # all ranks together, one step
+    value = pairs_job * args.steps / (total_ms * 1e-3)
+
+    # end to end through the public host API: pinned-host inputs in, results out
+    e2e = None
+    if rank == 0 and not args.quick:
+        xh_i = np.ascontiguousarray(x[lo:hi])
+        ctx2 = pg.Context(local)
+        ctx2.set_eps(EPS)
+        ctx2.set_self(world == 1)
+        for _ in range(2):
+            ctx2.set_j(x, m)
+            ctx2.set_i(xh_i)
+            ctx2.run()
+            ctx2.get_force(ni)
+        t0 = time.perf_counter()
+        ne = max(2, min(args.steps, 3))
+        for _ in range(ne):
+            ctx2.set_j(x, m)
+            ctx2.set_i(xh_i)
+            ctx2.run()
+            ctx2.get_force(ni)
+        dt = time.perf_counter() - t0
+        ctx2.close()
+        e2e = {"value": pairs_job * ne / dt, "unit": "interactions/s",
+               "h2d_bytes_per_step": npart * 32 + ni * 24, "d2h_bytes_per_step": ni * 32,
+               "steps": ne}
+
+    rows = None
+    if rank == 0 and not args.no_rows:
+        try:
+            rows = extra_rows(pg, torch, dev)
+        except Exception as exc:  # report, do not hide
+            rows = {"error": repr(exc)}
+
+    if rank != 0:
+        ctx.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = measured_peaks()
+    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    peak_int = sms * f_max * FP32_LANES_PER_SM / NEWTON_OPS
+    kms = statistics.median(kern_ms)
+    pairs_rank = ni * npart
+    achieved = pairs_rank / (kms * 1e-3)
+    roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_int / 1e9,
+            "unit": "Ginteractions/s", "frac": achieved / peak_int, "traffic": None,
+            "kernel": "k_allpairs<2,false,false>", "kernel_ms": kms,
+            "peak_basis": f"{sms} SMs x {f_max / 1e6:.0f} MHz x 128 FP32 lanes / 13 ops per "
+                          "interaction (FP32 pipe; MUFU allows 16 per SM-clock)"}
+    if clk.get("sm_mhz"):
+        roof["frac_at_sampled_clock"] = achieved / (sms * clk["sm_mhz"] * 1e6 * FP32_LANES_PER_SM /
+                                                    NEWTON_OPS)
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline(x, m)
+    line = {
+        "metric": "interactions/s", "value": value, "unit": "interactions/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "newton-allpairs-2^20-plummer+cube" if npart == N_PART else
+                   f"newton-allpairs-{npart}-plummer+cube", "n": npart, "eps": EPS,
+                   "positions": "fp64 in, fp32 offsets from fp64 tile centres",
+                   "accumulation": "fp32 per 256-j sub-tile, TwoSum across, fp64 combine",
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"i-range split over {world} GPU(s)"},
+        "gflops_at_38": value * PAPER_FLOPS_PER_INT / 1e9,
+        "roofline": roof,
+        "clocks": clk,
+        "e2e": e2e,
+        # per step: the i pack kernel plus the run's sort, tile, force and combine kernels
+        "gpu_launches": (int(info["launches"]) + 1) * args.steps,
+        "cpu_baseline": cpu,
+        "rows": rows,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

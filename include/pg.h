@@ -1,0 +1,210 @@
+/*
+ * pg.h -- C ABI of the GB300 pairwise-force library.
+ *
+ * The library evaluates the i-particle x j-particle force loop of
+ * Phantom-GRAPE (Tanikawa, Yoshikawa, Nitadori & Okamoto 2012,
+ * arXiv:1203.4037) on one NVIDIA GB300 GPU, in two forms:
+ *
+ *   PG_NEWTON  Eq. (1) with G = 1 and Plummer softening eps:
+ *              a_i = sum_j m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^(3/2),
+ *              phi_i = -sum_j m_j / (|x_j - x_i|^2 + eps^2)^(1/2)
+ *              (the potential's sign is the one of the Newton force loop of
+ *              Section 3.3, which subtracts m/r from the potential);
+ *   PG_TABLE   Eq. (2): a_i = sum_j m_j g(|x_j - x_i|) (x_j - x_i), with
+ *              g = f(r)/r read from the bit-pattern table of Section 3.4
+ *              (E exponent bits, F fraction bits, linear interpolation in
+ *              s = r^2 (s_max - 2) / r_cut^2 + 2) and g = 0 for r >= r_cut.
+ *              No potential is computed in this mode (as in the paper).
+ *
+ * The call sequence follows the GRAPE-5 style API of Section 3.6
+ * (g5_open / g5_set_eps_to_all / g5_set_n / g5_set_xmj /
+ * g5_calculate_force_on_x / g5_close) plus the paper's table setter.
+ *
+ * Conventions for every entry point:
+ *   - positions are row-major double[n][3], masses double[n] (FP64);
+ *   - "host" pointers are ordinary CPU memory the caller owns; the library
+ *     copies what it needs before returning (set_*) or writes into them
+ *     (get_*); "dev" pointers are CUDA device memory on the context's device,
+ *     borrowed only for the duration of the work the call enqueues on the
+ *     context's stream;
+ *   - calls are asynchronous on the context's stream unless stated; the
+ *     library never synchronises the device except in pg_get_force,
+ *     pg_get_table, pg_sync and pg_tune;
+ *   - a context is not thread-safe; use one per host thread;
+ *   - every function returns PG_OK (0) or a negative status; it never aborts
+ *     the process and never traps the GPU. pg_last_error() describes the last
+ *     failure. A device-side wait that runs out of time (PG_ETIMEOUT) is
+ *     reported by the next synchronising call.
+ */
+#ifndef PG_H
+#define PG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pg_ctx pg_ctx;
+
+/* status codes */
+#define PG_OK 0
+#define PG_EINVAL (-1)    /* bad argument (negative size, E+F out of range, r_cut <= 0, ...) */
+#define PG_ESTATE (-2)    /* call out of order (run before j/i/table were set, ...) */
+#define PG_ENOMEM (-3)    /* device or pinned host allocation failed */
+#define PG_ECUDA (-4)     /* a CUDA runtime call failed */
+#define PG_ETIMEOUT (-5)  /* a device-side bounded wait gave up */
+
+/* force modes (pg_set_mode) */
+#define PG_NEWTON 0
+#define PG_TABLE 1
+
+/* Open a context on CUDA device `device` (g5_open, Section 3.6; no rsqrt
+ * bias calibration: the GPU's rsqrt has a documented error bound instead).
+ * *out receives the handle; destroy it with pg_destroy. The context owns an
+ * internal non-blocking stream until pg_set_stream replaces it. */
+int pg_create(pg_ctx **out, int device);
+
+/* Release every resource of the context (g5_close). NULL is ignored. */
+void pg_destroy(pg_ctx *ctx);
+
+/* Enqueue all later work on `cuda_stream` (a cudaStream_t owned by the
+ * caller, e.g. the current PyTorch stream); NULL restores the internal one. */
+int pg_set_stream(pg_ctx *ctx, void *cuda_stream);
+
+/* Plummer softening length used by PG_NEWTON (g5_set_eps_to_all,
+ * Section 3.6): eps >= 0, one value for all particles. With eps = 0 a pair
+ * at zero distance contributes nothing. */
+int pg_set_eps(pg_ctx *ctx, double eps);
+
+/* Select PG_NEWTON (default) or PG_TABLE. */
+int pg_set_mode(pg_ctx *ctx, int mode);
+
+/* Build the force table from a host callback (the paper's non-GRAPE-5
+ * table setter, Section 3.6; construction of Section 3.4.1):
+ *   g(r, user) returns f(r)/r for 0 <= r <= r_cut (finite at r = 0);
+ *   knot k = 2^F bE + bF sits at s_k = 2^(bE+1) (1 + bF/2^F), i.e. at
+ *   r_k = r_cut sqrt((s_k - 2) / (s_max - 2)), s_max = 2^(2^E) (2 - 2^-F);
+ *   v_k = (float) g(r_k) for every knot, the last knot being r_cut itself;
+ *   stored G0_k = v_k and G1_k = (v_{k+1} - v_k) / (s_{k+1} - s_k) (rounded
+ *   once to FP32) for k < 2^(E+F) - 1; the last entry is G0 = G1 = 0, so the
+ *   force is zero at and beyond r_cut.
+ * Requires r_cut > 0, E >= 0, F >= 0, 1 <= E + F <= 13, E <= 7, F <= 20.
+ * The callback runs on the calling thread, 2^(E+F) times, before return. */
+int pg_set_table(pg_ctx *ctx, double (*g)(double r, void *user), void *user, double r_cut,
+                 int E, int F);
+
+/* The same table from knot values v[0 .. n-1] (host, FP32), n = 2^(E+F);
+ * v[n-1] is g at r_cut approached from below. */
+int pg_set_table_values(pg_ctx *ctx, const float *v, long long n, double r_cut, int E, int F);
+
+/* The same from device knot values (FP32, n = 2^(E+F)); the table is
+ * derived on the GPU. Used for trainable tables. */
+int pg_set_table_values_dev(pg_ctx *ctx, const float *v, long long n, double r_cut, int E,
+                            int F);
+
+/* Copy the stored table (G0, G1: FP32 host arrays of n = 2^(E+F)). Syncs. */
+int pg_get_table(pg_ctx *ctx, float *G0, float *G1, long long n);
+
+/* Number of j-particles used by pg_run (g5_set_n). Without it, pg_run uses
+ * the highest address written by pg_set_j / pg_set_j_dev. */
+int pg_set_n(pg_ctx *ctx, long long nj);
+
+/* Store j-particles adr .. adr+nj-1 (g5_set_xmj, Section 3.6): positions
+ * x (host double[nj][3]) and masses m (host double[nj]). Copies. */
+int pg_set_j(pg_ctx *ctx, long long adr, long long nj, const double *x, const double *m);
+
+/* Device twin of pg_set_j: x (device double[nj][3]), m (device double[nj]). */
+int pg_set_j_dev(pg_ctx *ctx, long long adr, long long nj, const double *x, const double *m);
+
+/* The i-particles of the next pg_run: x (host double[ni][3]). Copies. */
+int pg_set_i(pg_ctx *ctx, long long ni, const double *x);
+
+/* Device twin of pg_set_i. */
+int pg_set_i_dev(pg_ctx *ctx, long long ni, const double *x);
+
+/* on != 0: i-particle k is j-particle k (all-pairs use, the same arrays
+ * given to set_j and set_i), and its own pair is left out of the sums, as
+ * in the double-precision reference of Section 4.1. Requires ni <= nj and
+ * bit-identical positions. on = 0 (default): every j counts. */
+int pg_set_self(pg_ctx *ctx, int on);
+
+/* Batched tree-style lists (the usage of Section 5.1: each group of
+ * i-particles shares one interaction list). Group g covers the i-particles
+ * i_off[g] .. i_off[g+1]-1 (indices into the array of pg_set_i) and sums
+ * exactly the j listed in jlist[j_off[g] .. j_off[g+1]-1] (indices into the
+ * j array, 0 <= j < 2^27; repeats allowed; a listed self pair contributes
+ * zero force and, in PG_NEWTON, -m/eps of potential). i_off and j_off are
+ * int64[ngroups+1], non-decreasing, from 0; jlist is int32. Host arrays,
+ * copied. While groups are set pg_run evaluates them instead of all pairs. */
+int pg_set_groups(pg_ctx *ctx, long long ngroups, const long long *i_off, const long long *j_off,
+                  const int *jlist);
+
+/* Drop the groups: pg_run returns to all-pairs mode. */
+int pg_clear_groups(pg_ctx *ctx);
+
+/* Periodic cube of side box > 0 (PG_TABLE only): pg_run bins the
+ * j-particles into a cell grid of side >= r_cut, sorts them by cell, and
+ * sums over the 27 neighbour cells with minimum-image shifts (the PP
+ * neighbour search of PPPM / TreePM codes). Requires r_cut <= box / 3 and the
+ * self mode (the i-particles are the j-particles). box = 0 (default):
+ * open boundaries. */
+int pg_set_periodic(pg_ctx *ctx, double box);
+
+/* Enqueue one force evaluation into the context's own output buffers. */
+int pg_run(pg_ctx *ctx);
+
+/* Copy the last results to the host: a (double[ni][3]) and phi (double[ni],
+ * may be NULL; zeros in PG_TABLE mode). Synchronises; returns PG_ETIMEOUT
+ * if a device wait gave up. ni must equal the count given to pg_set_i. */
+int pg_get_force(pg_ctx *ctx, double *a, double *phi, long long ni);
+
+/* Enqueue one force evaluation writing device outputs: a (device
+ * double[ni][3]), phi (device double[ni] or NULL). */
+int pg_run_dev(pg_ctx *ctx, double *a, double *phi);
+
+/* Gradients of L = sum_i w_i . a_i for the all-pairs self mode
+ * (i-particles = j-particles), recomputing the pair terms: w (device
+ * double[n][3]) in; dx (device double[n][3]), dm (device double[n]) out; in
+ * PG_TABLE mode also dv (device float[2^(E+F)]), the gradient with respect to
+ * the knot values of the table (dv may be NULL). An extension: the paper has
+ * no backward pass. */
+int pg_backward_dev(pg_ctx *ctx, const double *w, double *dx, double *dm, float *dv);
+
+/* Wait for the context's stream and report device-side status. */
+int pg_sync(pg_ctx *ctx);
+
+/* on != 0: pg_run / pg_run_dev capture their launch sequence in a CUDA graph
+ * on first use and replay it while sizes, mode and buffers are unchanged. */
+int pg_set_graph(pg_ctx *ctx, int on);
+
+/* Time the candidate launch shapes of the current workload (i per thread,
+ * CTAs per SM) on the device and keep the fastest. Synchronises. */
+int pg_tune(pg_ctx *ctx);
+
+/* Launch shape override: i per thread = 2*np (np in {1, 2, 4}; 0 = keep),
+ * CTAs per SM (0 = occupancy limit). */
+int pg_set_shape(pg_ctx *ctx, int np, int ctas_per_sm);
+
+/* on != 0: bracket the force kernel of every later run with CUDA events on
+ * the context's stream, so that pg_kernel_time can report its duration. */
+int pg_set_timing(pg_ctx *ctx, int on);
+
+/* Duration in milliseconds of the force kernel of the last run (timing on;
+ * waits for that kernel's end event). */
+int pg_kernel_time(pg_ctx *ctx, double *ms);
+
+/* Counters: out[0] pair evaluations enqueued by the last run, out[1] kernel
+ * launches of the last run, out[2] i per thread, out[3] grid size of the
+ * force kernel, out[4] partial slots per tile. Returns how many were written. */
+int pg_info(pg_ctx *ctx, long long *out, int n);
+
+/* Text of the last error of this context ("" if none); NULL ctx: last
+ * error of pg_create. Valid until the next call on the context. */
+const char *pg_last_error(pg_ctx *ctx);
+
+/* Library version string. */
+const char *pg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PG_H */

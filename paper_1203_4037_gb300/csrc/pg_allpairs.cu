@@ -1,0 +1,381 @@
+// pg_allpairs.cu -- the i-particle x j-particle force loop, all pairs.
+//
+// Method (Tanikawa et al. 2012): for each i, sum over all j
+//   Newton, Eq. (1) with G = 1:  a_i += m_j d / (r^2 + eps^2)^{3/2},
+//                                phi_i -= m_j / (r^2 + eps^2)^{1/2}
+//     (the steps of Section 3.3: difference, r^2 + eps^2, inverse square
+//      root, m/r, m/r^3, accumulate);
+//   tabulated, Eq. (2): a_i += m_j g(r) d with g read from the bit-pattern
+//     table of Section 3.4 (s = min(|d~|^2 + 2, s_max), index from the FP32
+//     bits of s, linear interpolation), positions in the scaled units of
+//     Section 3.4.2 and the result rescaled at the end.
+//
+// GB300 mapping (not the paper's AVX layout):
+//  * work is split stream-K style: the (i-tile, j-sub-tile) units are cut
+//    into equal contiguous ranges, one per CTA, so every SM gets the same
+//    number of pair evaluations whatever the tile counts;
+//  * i-particles sit in registers, 2*NP per thread, packed in pairs for the
+//    FP32x2 instructions; j sub-tiles of kTJ records arrive in shared memory
+//    by bulk copies (double-buffered, completion on an mbarrier);
+//  * precision: the FP64 j record minus the FP64 i-tile centre is rounded to
+//    FP32 once per (j, tile) while staging; the pair loop runs in FP32 with
+//    the MUFU rsqrt; each sub-tile's FP32 partial is folded into a TwoSum
+//    (hi, lo) pair; the per-CTA partials are combined in FP64.
+#include "pg_device.cuh"
+
+namespace pg {
+
+// Bulk-copy raw FP64 j records of unit u into buffer slot.
+__device__ __forceinline__ void issue_jsub(const double4 *jrec, long long nj, int s,
+                                           double4 *dst, uint64_t *bar)
+{
+    long long j0 = (long long)s * kTJ;
+    long long nv = nj - j0;
+    if (nv > kTJ) nv = kTJ;
+    unsigned bytes = (unsigned)(nv * sizeof(double4));
+    mbar_arrive_tx(bar, bytes);
+    bulk_g2s(dst, jrec + j0, bytes, bar);
+}
+
+// which CTA owns unit u under the equal split of W units over `grid` CTAs
+__host__ __device__ __forceinline__ long long stream_k_owner(long long u, long long grid,
+                                                             long long W)
+{
+    return ((u + 1) * grid - 1) / W;
+}
+
+long long stream_k_first(long long u, int grid, long long W)
+{
+    return stream_k_owner(u, grid, W);
+}
+
+template <int NP>
+struct Bi_of {
+    static constexpr int value = kNT * 2 * NP;
+};
+
+int allpairs_bi(int np) { return kNT * 2 * np; }
+
+template <int NP, bool TABLE, bool ZSAFE>
+__global__ void __launch_bounds__(kNT) k_allpairs(AllPairsArgs a)
+{
+    constexpr int Bi = Bi_of<NP>::value;
+    extern __shared__ __align__(128) unsigned char smem[];
+    double4 *raw = reinterpret_cast<double4 *>(smem);                       // [2][kTJ]
+    u64 *cvt = reinterpret_cast<u64 *>(smem + 2 * kTJ * sizeof(double4));   // [kTJ][4]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * kTJ * sizeof(double4) +
+                                                 kTJ * 4 * sizeof(u64));
+    int *flag = reinterpret_cast<int *>(bar + 2);
+    float2 *tab = reinterpret_cast<float2 *>(bar + 4);
+
+    const int tid = threadIdx.x;
+    const long long G = gridDim.x;
+    const long long b = blockIdx.x;
+    const long long u0 = b * a.W / G, u1 = (b + 1) * a.W / G;
+    if (u0 >= u1) return;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    if (TABLE)
+        for (int k = tid; k < a.tab.n; k += kNT) tab[k] = a.tab.AG1[k];
+    __syncthreads();
+
+    // prefetch the first two sub-tiles
+    unsigned pending = 0; // bit k: a copy into buffer k is in flight (thread 0)
+    if (tid == 0) {
+        issue_jsub(a.jrec, a.nj, (int)(u0 % a.njsub), raw, &bar[0]);
+        pending = 1u;
+        if (u0 + 1 < u1) {
+            issue_jsub(a.jrec, a.nj, (int)((u0 + 1) % a.njsub), raw + kTJ, &bar[1]);
+            pending |= 2u;
+        }
+    }
+    unsigned phase = 0;   // bit k: parity of the next completion of buffer k
+
+    // per-thread state
+    u64 xi[NP], yi[NP], zi[NP];
+    u64 ax[NP], ay[NP], az[NP], ph[NP];          // sub-tile partials
+    u64 hx[NP], hy[NP], hz[NP], hp[NP];          // compensated running sums
+    u64 lx[NP], ly[NP], lz[NP], lp[NP];
+    double cx = 0, cy = 0, cz = 0;
+    long long cur = -1;
+
+    const u64 zero2 = 0ull;
+    const float c0 = TABLE ? 2.0f : a.eps2;
+    const u64 c0v = pk2(c0, c0);
+    const double sc = TABLE ? a.tab.scale : 1.0;
+    bool failed = false;
+
+    auto flush = [&](long long t) {
+        long long slot = b - stream_k_owner(t * a.njsub, G, a.W);
+        double4 *dst = a.part + ((size_t)t * a.smax_slots + (size_t)slot) * Bi;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            float h[8], l[8];
+            up2(hx[p], h[0], h[1]); up2(hy[p], h[2], h[3]);
+            up2(hz[p], h[4], h[5]); up2(hp[p], h[6], h[7]);
+            up2(lx[p], l[0], l[1]); up2(ly[p], l[2], l[3]);
+            up2(lz[p], l[4], l[5]); up2(lp[p], l[6], l[7]);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                int li = (2 * p + q) * kNT + tid;
+                if (t * Bi + li < a.ni)
+                    dst[li] = make_double4((double)h[q] + (double)l[q], (double)h[2 + q] + (double)l[2 + q],
+                                           (double)h[4 + q] + (double)l[4 + q],
+                                           (double)h[6 + q] + (double)l[6 + q]);
+            }
+        }
+    };
+
+    for (long long u = u0; u < u1; ++u) {
+        const long long t = u / a.njsub;
+        const int s = (int)(u % a.njsub);
+        const int buf = (int)((u - u0) & 1);
+
+        if (t != cur) {
+            if (cur >= 0) flush(cur);
+            cur = t;
+            double4 c = a.ctr[t];
+            cx = c.x; cy = c.y; cz = c.z;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                float fx[2], fy[2], fz[2];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    long long i = t * Bi + (2 * p + q) * kNT + tid;
+                    if (i < a.ni) {
+                        double4 v = a.xi[i];
+                        fx[q] = (float)((v.x - cx) * sc);
+                        fy[q] = (float)((v.y - cy) * sc);
+                        fz[q] = (float)((v.z - cz) * sc);
+                    } else {
+                        fx[q] = fy[q] = fz[q] = 0.0f;
+                    }
+                }
+                xi[p] = pk2(fx[0], fx[1]);
+                yi[p] = pk2(fy[0], fy[1]);
+                zi[p] = pk2(fz[0], fz[1]);
+                hx[p] = hy[p] = hz[p] = hp[p] = zero2;
+                lx[p] = ly[p] = lz[p] = lp[p] = zero2;
+            }
+        }
+
+        // wait for this sub-tile's raw records (one thread waits, all learn)
+        if (tid == 0) {
+            bool ok = mbar_wait(&bar[buf], (phase >> buf) & 1u, kWaitLimitNs);
+            if (ok) pending &= ~(1u << buf);
+            *flag = ok ? 1 : 0;
+        }
+        __syncthreads();
+        if (*flag == 0) { failed = true; break; }
+        phase ^= 1u << buf;
+
+        // convert: FP64 record minus FP64 tile centre, rounded once to FP32;
+        // each value is stored twice so one 16-byte load yields f32x2 pairs
+        {
+            const long long j0 = (long long)s * kTJ;
+            long long nv = a.nj - j0;
+            if (nv > kTJ) nv = kTJ;
+            const double4 *r = raw + buf * kTJ;
+            for (int e = tid; e < kTJ; e += kNT) {
+                float x, y, z, m;
+                if (e < nv) {
+                    double4 v = r[e];
+                    x = (float)((v.x - cx) * sc);
+                    y = (float)((v.y - cy) * sc);
+                    z = (float)((v.z - cz) * sc);
+                    m = (float)v.w;
+                } else {   // padding: zero mass far away contributes exactly 0
+                    x = y = z = 1.0e4f;
+                    m = 0.0f;
+                }
+                cvt[4 * e + 0] = pk2(x, x);
+                cvt[4 * e + 1] = pk2(y, y);
+                cvt[4 * e + 2] = pk2(z, z);
+                cvt[4 * e + 3] = pk2(m, m);
+            }
+        }
+        __syncthreads();
+        // refill the raw buffer just consumed with unit u + 2
+        if (tid == 0 && u + 2 < u1) {
+            fence_proxy_async();
+            issue_jsub(a.jrec, a.nj, (int)((u + 2) % a.njsub), raw + buf * kTJ, &bar[buf]);
+            pending |= 1u << buf;
+        }
+
+#pragma unroll
+        for (int p = 0; p < NP; ++p) ax[p] = ay[p] = az[p] = ph[p] = zero2;
+
+#pragma unroll 4
+        for (int e = 0; e < kTJ; ++e) {
+            const ulonglong2 xy = reinterpret_cast<const ulonglong2 *>(cvt)[2 * e];
+            const ulonglong2 zm = reinterpret_cast<const ulonglong2 *>(cvt)[2 * e + 1];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const u64 dx = f2sub(xy.x, xi[p]);
+                const u64 dy = f2sub(xy.y, yi[p]);
+                const u64 dz = f2sub(zm.x, zi[p]);
+                u64 r2 = f2fma(dx, dx, c0v);
+                r2 = f2fma(dy, dy, r2);
+                r2 = f2fma(dz, dz, r2);
+                float ra, rb;
+                up2(r2, ra, rb);
+                if (!TABLE) {
+                    float qa = rsq(ra), qb = rsq(rb);
+                    if (ZSAFE) {   // eps = 0: a coincident pair contributes nothing
+                        qa = ra > 0.0f ? qa : 0.0f;
+                        qb = rb > 0.0f ? qb : 0.0f;
+                    }
+                    const u64 q = pk2(qa, qb);
+                    const u64 mq = f2mul(zm.y, q);
+                    const u64 q2 = f2mul(q, q);
+                    const u64 mq3 = f2mul(mq, q2);
+                    ph[p] = f2sub(ph[p], mq);
+                    ax[p] = f2fma(mq3, dx, ax[p]);
+                    ay[p] = f2fma(mq3, dy, ay[p]);
+                    az[p] = f2fma(mq3, dz, az[p]);
+                } else {
+                    ra = fminf(ra, a.tab.s_max);
+                    rb = fminf(rb, a.tab.s_max);
+                    const float2 ta = tab[(__float_as_uint(ra) >> a.tab.shift) - a.tab.base];
+                    const float2 tb = tab[(__float_as_uint(rb) >> a.tab.shift) - a.tab.base];
+                    const u64 g = f2fma(pk2(ra, rb), pk2(ta.y, tb.y), pk2(ta.x, tb.x));
+                    const u64 mg = f2mul(zm.y, g);
+                    ax[p] = f2fma(mg, dx, ax[p]);
+                    ay[p] = f2fma(mg, dy, ay[p]);
+                    az[p] = f2fma(mg, dz, az[p]);
+                }
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            fold2(hx[p], lx[p], ax[p]);
+            fold2(hy[p], ly[p], ay[p]);
+            fold2(hz[p], lz[p], az[p]);
+            if (!TABLE) fold2(hp[p], lp[p], ph[p]);
+        }
+    }
+
+    if (failed) {
+        // let copies still in flight land before the CTA's shared memory goes
+        if (tid == 0) {
+            report(a.status, kStatusTimeout, 1);
+            for (int k = 0; k < 2; ++k)
+                if (pending & (1u << k)) mbar_wait(&bar[k], (phase >> k) & 1u, kWaitLimitNs / 4);
+        }
+        return;
+    }
+    if (cur >= 0) flush(cur);
+}
+
+// ------------------------------------------------------------------ host
+
+size_t allpairs_smem(int np, bool table, int ntab)
+{
+    (void)np;
+    size_t s = 2 * kTJ * sizeof(double4) + kTJ * 4 * sizeof(u64) + 4 * sizeof(uint64_t);
+    if (table) s += (size_t)ntab * sizeof(float2);
+    return s;
+}
+
+// raise the kernel's dynamic shared memory limit once (outside any capture)
+template <int NP, bool TABLE, bool ZSAFE>
+static cudaError_t configure_one()
+{
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_allpairs<NP, TABLE, ZSAFE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)allpairs_smem(NP, TABLE, 1 << 13));
+    done = e == cudaSuccess;
+    return e;
+}
+
+template <int NP, bool TABLE, bool ZSAFE>
+static cudaError_t launch_one(const AllPairsArgs &a, int grid, size_t smem, cudaStream_t st)
+{
+    cudaError_t e = configure_one<NP, TABLE, ZSAFE>();
+    if (e != cudaSuccess) return e;
+    k_allpairs<NP, TABLE, ZSAFE><<<grid, kNT, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NP, bool TABLE, bool ZSAFE>
+static int occupancy_one(size_t smem)
+{
+    auto k = k_allpairs<NP, TABLE, ZSAFE>;
+    if (configure_one<NP, TABLE, ZSAFE>() != cudaSuccess) return 1;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kNT, smem) != cudaSuccess) return 1;
+    return nb > 0 ? nb : 1;
+}
+
+int allpairs_max_blocks_per_sm(int np, bool table, int ntab)
+{
+    size_t smem = allpairs_smem(np, table, ntab);
+    if (table) return np == 1 ? occupancy_one<1, true, false>(smem)
+                     : np == 4 ? occupancy_one<4, true, false>(smem)
+                               : occupancy_one<2, true, false>(smem);
+    return np == 1 ? occupancy_one<1, false, false>(smem)
+         : np == 4 ? occupancy_one<4, false, false>(smem)
+                   : occupancy_one<2, false, false>(smem);
+}
+
+cudaError_t launch_allpairs(const AllPairsArgs &a, int grid, int np, bool table, bool zsafe,
+                            size_t smem, cudaStream_t st)
+{
+    if (grid <= 0) return cudaSuccess;
+#define PG_AP(NP_)                                                                       \
+    if (np == NP_) {                                                                     \
+        if (table) return launch_one<NP_, true, false>(a, grid, smem, st);               \
+        if (zsafe) return launch_one<NP_, false, true>(a, grid, smem, st);               \
+        return launch_one<NP_, false, false>(a, grid, smem, st);                         \
+    }
+    PG_AP(1)
+    PG_AP(2)
+    PG_AP(4)
+#undef PG_AP
+    return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------------ combine
+// One thread per i (tile order): add the CTA partials of its tile in slot
+// order in FP64, take out the self pair's potential term, rescale, scatter.
+__global__ void k_combine(CombineArgs c)
+{
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= c.ni) return;
+    long long t = p / c.Bi;
+    int li = (int)(p % c.Bi);
+    double ax = 0, ay = 0, az = 0, ph = 0;
+    if (c.njsub > 0) {
+        long long bf = stream_k_owner(t * c.njsub, c.grid, c.W);
+        long long bl = stream_k_owner((t + 1) * c.njsub - 1, c.grid, c.W);
+        for (long long s = 0; s <= bl - bf; ++s) {
+            double4 v = c.part[((size_t)t * c.smax_slots + (size_t)s) * c.Bi + li];
+            ax += v.x; ay += v.y; az += v.z; ph += v.w;
+        }
+    }
+    long long k = c.perm ? (long long)c.perm[p] : p;
+    if (c.newton && c.self && c.eps2 > 0.0f && c.njsub > 0) {
+        // the loop added -m_k rsqrt(eps^2) for i's own pair (d = 0 exactly)
+        float mk = (float)c.jrec[k].w;
+        ph += (double)__fmul_rn(mk, rsq(c.eps2));
+    }
+    c.acc[3 * k] = ax * c.accscale;
+    c.acc[3 * k + 1] = ay * c.accscale;
+    c.acc[3 * k + 2] = az * c.accscale;
+    if (c.pot) c.pot[k] = c.newton ? ph : 0.0;
+}
+
+cudaError_t launch_combine(const CombineArgs &c, cudaStream_t st)
+{
+    if (c.ni <= 0) return cudaSuccess;
+    k_combine<<<(unsigned)((c.ni + 255) / 256), 256, 0, st>>>(c);
+    return cudaGetLastError();
+}
+
+}  // namespace pg

@@ -1,0 +1,905 @@
+// pg_api.cu -- the C ABI of include/pg.h: context state, argument checks,
+// host-side table construction (Section 3.4.1), staging copies, and the
+// launch sequences of the force paths, optionally captured in a CUDA graph.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pg.h"
+#include "pg_internal.h"
+
+using namespace pg;
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+struct PinBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;   // last copy out of / into this buffer
+};
+
+}  // namespace
+
+struct pg_ctx {
+    int device = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    int sms = 0;
+
+    double eps = 0.0;
+    int mode = PG_NEWTON;
+    int self = 0;
+    double box = 0.0;
+
+    // table
+    bool have_table = false;
+    int E = 0, F = 0, ntab = 0;
+    double r_cut = 0.0, scale = 1.0, s_max = 0.0;
+    DevBuf G0, G1, AG1;
+
+    // j
+    long long nj_n = -1;          // pg_set_n, -1: unset
+    long long nj_hw = 0;          // high-water mark of set_j
+    DevBuf jrec;                  // double4 records
+    DevBuf stage;                 // raw FP64 staging for host copies
+
+    // i
+    long long ni = -1;
+    DevBuf xi;                    // double4
+    bool i_dirty = true;
+
+    // tiles and ordering
+    DevBuf xt, ctr;
+    SortScratch sort{};
+    DevBuf skeys0, skeys1, svals0, svals1, shist, ssums, sbbox;
+    unsigned *perm = nullptr;     // tile order -> i index (nullptr: identity)
+    int sort_mode = -1;           // -1 auto, 0 never, 1 always
+    int tiled_np = 0;
+
+    // outputs and partials
+    DevBuf acc, pot, part;
+    DevBuf status;                // 2 ints
+
+    // host staging
+    PinBuf pin_j, pin_i, pin_o;
+
+    // groups
+    bool have_groups = false;
+    long long ngroups = 0;
+    DevBuf g_joff, g_jlist, g_items, g_ctr, g_queue;
+    int g_nitems = 0;
+    long long g_pairs = 0;
+
+    // launch shape
+    int np = 2;
+    int ctas_per_sm = 0;
+
+    // graph
+    bool use_graph = false;
+    cudaGraphExec_t gexec = nullptr;
+    std::string gkey;
+
+    // force-kernel timing
+    bool timing = false;
+    cudaEvent_t tk0 = nullptr, tk1 = nullptr;
+    bool timed = false;
+
+    // stats of the last run
+    long long last_pairs = 0, last_launches = 0, last_grid = 0, last_slots = 0;
+
+    std::string err;
+};
+
+static std::string g_create_err;
+
+namespace {
+
+int fail(pg_ctx *c, int code, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(pg_ctx *c, cudaError_t e, const char *where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    (void)cudaGetLastError();
+    return fail(c, PG_ECUDA, m);
+}
+
+#define PG_CUDA(c, call)                                  \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+    } while (0)
+
+int ensure(pg_ctx *c, DevBuf &b, size_t bytes)
+{
+    if (bytes <= b.cap) return PG_OK;
+    if (b.p) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    size_t want = std::max<size_t>(bytes, 256);
+    if (cudaMalloc(&b.p, want) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(c, PG_ENOMEM, "device allocation of " + std::to_string(want) + " bytes failed");
+    }
+    b.cap = want;
+    return PG_OK;
+}
+
+int ensure_pin(pg_ctx *c, PinBuf &b, size_t bytes)
+{
+    if (!b.done) {
+        if (cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming) != cudaSuccess)
+            return cuda_fail(c, cudaGetLastError(), "cudaEventCreate");
+    }
+    // the previous copy through this buffer must have finished
+    if (b.p) PG_CUDA(c, cudaEventSynchronize(b.done));
+    if (bytes <= b.cap) return PG_OK;
+    if (b.p) cudaFreeHost(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    size_t want = std::max<size_t>(bytes, 4096);
+    if (cudaHostAlloc(&b.p, want, cudaHostAllocDefault) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(c, PG_ENOMEM, "pinned allocation of " + std::to_string(want) + " bytes failed");
+    }
+    b.cap = want;
+    return PG_OK;
+}
+
+void free_dev(DevBuf &b)
+{
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+void free_pin(PinBuf &b)
+{
+    if (b.p) cudaFreeHost(b.p);
+    if (b.done) cudaEventDestroy(b.done);
+    b = PinBuf();
+}
+
+void drop_graph(pg_ctx *c)
+{
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->gkey.clear();
+}
+
+long long nj_of(const pg_ctx *c) { return c->nj_n >= 0 ? c->nj_n : c->nj_hw; }
+
+// FP32 bit pattern of knot k (Section 3.4.1: 2.0f plus k ticks of 2^(23-F))
+float knot_s(int k, int F)
+{
+    unsigned u = 0x40000000u + ((unsigned)k << (23 - F));
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+int check_EF(pg_ctx *c, double r_cut, int E, int F)
+{
+    if (!(r_cut > 0.0) || !std::isfinite(r_cut))
+        return fail(c, PG_EINVAL, "r_cut must be positive and finite");
+    if (E < 0 || F < 0 || E > 7 || F > 20 || E + F < 1 || E + F > 13)
+        return fail(c, PG_EINVAL, "need E, F >= 0, E <= 7, F <= 20, 1 <= E+F <= 13");
+    return PG_OK;
+}
+
+// geometry shared by every table setter
+void set_geometry(pg_ctx *c, double r_cut, int E, int F)
+{
+    c->E = E;
+    c->F = F;
+    c->ntab = 1 << (E + F);
+    c->r_cut = r_cut;
+    c->s_max = (double)knot_s(c->ntab - 1, F);   // = 2^(2^E) (2 - 2^-F)
+    c->scale = std::sqrt(c->s_max - 2.0) / r_cut;
+}
+
+// G0/G1 from host knot values; then the device copies and the {A, G1} form
+int upload_table(pg_ctx *c, const std::vector<float> &v)
+{
+    int n = c->ntab;
+    std::vector<float> g0(n), g1(n);
+    for (int k = 0; k < n; ++k) {
+        if (k < n - 1) {
+            double ds = (double)knot_s(k + 1, c->F) - (double)knot_s(k, c->F);
+            g0[k] = v[k];
+            g1[k] = (float)(((double)v[k + 1] - (double)v[k]) / ds);
+        } else {
+            g0[k] = 0.0f;
+            g1[k] = 0.0f;
+        }
+    }
+    int rc;
+    if ((rc = ensure(c, c->G0, n * 4)) || (rc = ensure(c, c->G1, n * 4)) ||
+        (rc = ensure(c, c->AG1, n * 8)))
+        return rc;
+    PG_CUDA(c, cudaMemcpyAsync(c->G0.p, g0.data(), n * 4, cudaMemcpyHostToDevice, c->stream));
+    PG_CUDA(c, cudaMemcpyAsync(c->G1.p, g1.data(), n * 4, cudaMemcpyHostToDevice, c->stream));
+    PG_CUDA(c, launch_table_prep((float *)c->G0.p, (float *)c->G1.p, (float2 *)c->AG1.p, c->E,
+                                 c->F, c->stream));
+    // the host vectors go out of scope: wait for the copies
+    PG_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->have_table = true;
+    drop_graph(c);
+    return PG_OK;
+}
+
+TableDev table_dev(const pg_ctx *c)
+{
+    TableDev t{};
+    t.AG1 = (const float2 *)c->AG1.p;
+    t.n = c->ntab;
+    t.shift = 23 - c->F;
+    t.base = 0x40000000u >> (23 - c->F);
+    t.s_max = (float)c->s_max;
+    t.scale = c->scale;
+    return t;
+}
+
+int read_status(pg_ctx *c)
+{
+    if (!c->status.p) return PG_OK;
+    int st[2] = {0, 0};
+    PG_CUDA(c, cudaMemcpyAsync(st, c->status.p, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+    PG_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (st[0] != 0) {
+        PG_CUDA(c, cudaMemsetAsync(c->status.p, 0, 2 * sizeof(int), c->stream));
+        char buf[128];
+        snprintf(buf, sizeof buf, "device-side wait gave up (code %d, site %d)", st[0], st[1]);
+        return fail(c, st[0] == kStatusTimeout ? PG_ETIMEOUT : PG_ECUDA, buf);
+    }
+    return PG_OK;
+}
+
+}  // namespace
+
+// ====================================================================== API
+
+extern "C" {
+
+const char *pg_version(void) { return "pg 0.1 (sm_103a)"; }
+
+const char *pg_last_error(pg_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
+
+int pg_create(pg_ctx **out, int device)
+{
+    if (!out) return PG_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || device < 0 || device >= ndev) {
+        (void)cudaGetLastError();
+        g_create_err = e != cudaSuccess ? std::string("no CUDA device: ") + cudaGetErrorString(e)
+                                        : "device index out of range";
+        return e != cudaSuccess ? PG_ECUDA : PG_EINVAL;
+    }
+    if ((e = cudaSetDevice(device)) != cudaSuccess) {
+        g_create_err = cudaGetErrorString(e);
+        return PG_ECUDA;
+    }
+    pg_ctx *c = new pg_ctx();
+    c->device = device;
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+    if ((e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        g_create_err = cudaGetErrorString(e);
+        delete c;
+        return PG_ECUDA;
+    }
+    c->stream = c->own_stream;
+    if (ensure(c, c->status, 2 * sizeof(int)) != PG_OK ||
+        cudaMemsetAsync(c->status.p, 0, 2 * sizeof(int), c->stream) != cudaSuccess) {
+        g_create_err = c->err;
+        pg_destroy(c);
+        return PG_ENOMEM;
+    }
+    *out = c;
+    return PG_OK;
+}
+
+void pg_destroy(pg_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    drop_graph(c);
+    DevBuf *bufs[] = {&c->G0, &c->G1, &c->AG1, &c->jrec, &c->stage, &c->xi, &c->xt, &c->ctr,
+                      &c->skeys0, &c->skeys1, &c->svals0, &c->svals1, &c->shist, &c->ssums,
+                      &c->sbbox, &c->acc, &c->pot, &c->part, &c->status, &c->g_joff,
+                      &c->g_jlist, &c->g_items, &c->g_ctr, &c->g_queue};
+    for (DevBuf *b : bufs) free_dev(*b);
+    free_pin(c->pin_j);
+    free_pin(c->pin_i);
+    free_pin(c->pin_o);
+    if (c->tk0) cudaEventDestroy(c->tk0);
+    if (c->tk1) cudaEventDestroy(c->tk1);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    delete c;
+}
+
+int pg_set_stream(pg_ctx *c, void *s)
+{
+    if (!c) return PG_EINVAL;
+    cudaStream_t ns = s ? (cudaStream_t)s : c->own_stream;
+    if (ns != c->stream) {
+        // keep ordering: the new stream waits for work already enqueued
+        cudaEvent_t ev;
+        PG_CUDA(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        PG_CUDA(c, cudaEventRecord(ev, c->stream));
+        PG_CUDA(c, cudaStreamWaitEvent(ns, ev, 0));
+        cudaEventDestroy(ev);
+        c->stream = ns;
+        drop_graph(c);
+    }
+    return PG_OK;
+}
+
+int pg_set_eps(pg_ctx *c, double eps)
+{
+    if (!c) return PG_EINVAL;
+    if (!(eps >= 0.0) || !std::isfinite(eps)) return fail(c, PG_EINVAL, "eps must be >= 0");
+    if (eps != c->eps) drop_graph(c);
+    c->eps = eps;
+    return PG_OK;
+}
+
+int pg_set_mode(pg_ctx *c, int mode)
+{
+    if (!c) return PG_EINVAL;
+    if (mode != PG_NEWTON && mode != PG_TABLE) return fail(c, PG_EINVAL, "unknown mode");
+    if (mode != c->mode) drop_graph(c);
+    c->mode = mode;
+    return PG_OK;
+}
+
+int pg_set_table(pg_ctx *c, double (*g)(double, void *), void *user, double r_cut, int E, int F)
+{
+    if (!c) return PG_EINVAL;
+    if (!g) return fail(c, PG_EINVAL, "g is NULL");
+    int rc = check_EF(c, r_cut, E, F);
+    if (rc) return rc;
+    set_geometry(c, r_cut, E, F);
+    double sc2 = (c->s_max - 2.0) / (r_cut * r_cut);
+    std::vector<float> v(c->ntab);
+    for (int k = 0; k < c->ntab; ++k) {
+        double r = std::sqrt(((double)knot_s(k, F) - 2.0) / sc2);
+        double gv = g(r, user);
+        if (!std::isfinite(gv)) return fail(c, PG_EINVAL, "g(r) is not finite at a knot");
+        v[k] = (float)gv;
+    }
+    return upload_table(c, v);
+}
+
+int pg_set_table_values(pg_ctx *c, const float *v, long long n, double r_cut, int E, int F)
+{
+    if (!c) return PG_EINVAL;
+    if (!v) return fail(c, PG_EINVAL, "v is NULL");
+    int rc = check_EF(c, r_cut, E, F);
+    if (rc) return rc;
+    if (n != (1LL << (E + F))) return fail(c, PG_EINVAL, "n must be 2^(E+F)");
+    set_geometry(c, r_cut, E, F);
+    return upload_table(c, std::vector<float>(v, v + n));
+}
+
+int pg_set_table_values_dev(pg_ctx *c, const float *v, long long n, double r_cut, int E, int F)
+{
+    if (!c) return PG_EINVAL;
+    if (!v) return fail(c, PG_EINVAL, "v is NULL");
+    int rc = check_EF(c, r_cut, E, F);
+    if (rc) return rc;
+    if (n != (1LL << (E + F))) return fail(c, PG_EINVAL, "n must be 2^(E+F)");
+    bool same = c->have_table && c->E == E && c->F == F && c->r_cut == r_cut;
+    set_geometry(c, r_cut, E, F);
+    if ((rc = ensure(c, c->G0, n * 4)) || (rc = ensure(c, c->G1, n * 4)) ||
+        (rc = ensure(c, c->AG1, n * 8)))
+        return rc;
+    PG_CUDA(c, launch_table_from_values(v, (float *)c->G0.p, (float *)c->G1.p, E, F, c->stream));
+    PG_CUDA(c, launch_table_prep((float *)c->G0.p, (float *)c->G1.p, (float2 *)c->AG1.p, E, F,
+                                 c->stream));
+    c->have_table = true;
+    if (!same) drop_graph(c);
+    return PG_OK;
+}
+
+int pg_get_table(pg_ctx *c, float *G0, float *G1, long long n)
+{
+    if (!c) return PG_EINVAL;
+    if (!c->have_table) return fail(c, PG_ESTATE, "no table set");
+    if (n != c->ntab || !G0 || !G1) return fail(c, PG_EINVAL, "n must be 2^(E+F), arrays non-NULL");
+    PG_CUDA(c, cudaMemcpyAsync(G0, c->G0.p, n * 4, cudaMemcpyDeviceToHost, c->stream));
+    PG_CUDA(c, cudaMemcpyAsync(G1, c->G1.p, n * 4, cudaMemcpyDeviceToHost, c->stream));
+    PG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return PG_OK;
+}
+
+int pg_set_n(pg_ctx *c, long long nj)
+{
+    if (!c) return PG_EINVAL;
+    if (nj < 0) return fail(c, PG_EINVAL, "nj must be >= 0");
+    if (nj > c->nj_hw) return fail(c, PG_ESTATE, "set_n beyond the j-particles written");
+    if (nj != c->nj_n) drop_graph(c);
+    c->nj_n = nj;
+    return PG_OK;
+}
+
+static int grow_j(pg_ctx *c, long long end)
+{
+    size_t need = (size_t)end * sizeof(double4);
+    if (need > c->jrec.cap) {
+        // keep the records already written
+        DevBuf nb;
+        size_t want = std::max(need, c->jrec.cap + c->jrec.cap / 2);
+        if (cudaMalloc(&nb.p, want) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(c, PG_ENOMEM, "device allocation for j records failed");
+        }
+        nb.cap = want;
+        if (c->jrec.p && c->nj_hw > 0)
+            PG_CUDA(c, cudaMemcpyAsync(nb.p, c->jrec.p, c->nj_hw * sizeof(double4),
+                                       cudaMemcpyDeviceToDevice, c->stream));
+        PG_CUDA(c, cudaStreamSynchronize(c->stream));
+        free_dev(c->jrec);
+        c->jrec = nb;
+        drop_graph(c);
+    }
+    return PG_OK;
+}
+
+int pg_set_j(pg_ctx *c, long long adr, long long nj, const double *x, const double *m)
+{
+    if (!c) return PG_EINVAL;
+    if (adr < 0 || nj < 0) return fail(c, PG_EINVAL, "adr and nj must be >= 0");
+    if (nj > 0 && (!x || !m)) return fail(c, PG_EINVAL, "x or m is NULL");
+    if (nj == 0) return PG_OK;
+    int rc;
+    if ((rc = grow_j(c, adr + nj))) return rc;
+    size_t bx = (size_t)nj * 24, bm = (size_t)nj * 8;
+    if ((rc = ensure_pin(c, c->pin_j, bx + bm)) || (rc = ensure(c, c->stage, bx + bm))) return rc;
+    std::memcpy(c->pin_j.p, x, bx);
+    std::memcpy((char *)c->pin_j.p + bx, m, bm);
+    PG_CUDA(c, cudaMemcpyAsync(c->stage.p, c->pin_j.p, bx + bm, cudaMemcpyHostToDevice, c->stream));
+    PG_CUDA(c, cudaEventRecord(c->pin_j.done, c->stream));
+    const double *dx = (const double *)c->stage.p;
+    PG_CUDA(c, launch_pack_j(dx, dx + 3 * nj, (double4 *)c->jrec.p + adr, nj, c->stream));
+    c->nj_hw = std::max(c->nj_hw, adr + nj);
+    return PG_OK;
+}
+
+int pg_set_j_dev(pg_ctx *c, long long adr, long long nj, const double *x, const double *m)
+{
+    if (!c) return PG_EINVAL;
+    if (adr < 0 || nj < 0) return fail(c, PG_EINVAL, "adr and nj must be >= 0");
+    if (nj > 0 && (!x || !m)) return fail(c, PG_EINVAL, "x or m is NULL");
+    if (nj == 0) return PG_OK;
+    int rc;
+    if ((rc = grow_j(c, adr + nj))) return rc;
+    PG_CUDA(c, launch_pack_j(x, m, (double4 *)c->jrec.p + adr, nj, c->stream));
+    c->nj_hw = std::max(c->nj_hw, adr + nj);
+    return PG_OK;
+}
+
+static int grow_i(pg_ctx *c, long long ni)
+{
+    if ((size_t)ni * sizeof(double4) > c->xi.cap) drop_graph(c);
+    return ensure(c, c->xi, (size_t)std::max<long long>(ni, 1) * sizeof(double4));
+}
+
+int pg_set_i(pg_ctx *c, long long ni, const double *x)
+{
+    if (!c) return PG_EINVAL;
+    if (ni < 0) return fail(c, PG_EINVAL, "ni must be >= 0");
+    if (ni > 0 && !x) return fail(c, PG_EINVAL, "x is NULL");
+    int rc;
+    if ((rc = grow_i(c, ni))) return rc;
+    if (ni != c->ni) drop_graph(c);
+    c->ni = ni;
+    c->i_dirty = true;
+    if (ni == 0) return PG_OK;
+    size_t bx = (size_t)ni * 24;
+    if ((rc = ensure_pin(c, c->pin_i, bx))) return rc;
+    // the device staging area is only touched in stream order, so j and i
+    // copies can share it
+    if ((rc = ensure(c, c->stage, bx))) return rc;
+    std::memcpy(c->pin_i.p, x, bx);
+    PG_CUDA(c, cudaMemcpyAsync(c->stage.p, c->pin_i.p, bx, cudaMemcpyHostToDevice, c->stream));
+    PG_CUDA(c, cudaEventRecord(c->pin_i.done, c->stream));
+    PG_CUDA(c, launch_pack_i((const double *)c->stage.p, (double4 *)c->xi.p, ni, c->stream));
+    return PG_OK;
+}
+
+int pg_set_i_dev(pg_ctx *c, long long ni, const double *x)
+{
+    if (!c) return PG_EINVAL;
+    if (ni < 0) return fail(c, PG_EINVAL, "ni must be >= 0");
+    if (ni > 0 && !x) return fail(c, PG_EINVAL, "x is NULL");
+    int rc;
+    if ((rc = grow_i(c, ni))) return rc;
+    if (ni != c->ni) drop_graph(c);
+    c->ni = ni;
+    c->i_dirty = true;
+    if (ni > 0) PG_CUDA(c, launch_pack_i(x, (double4 *)c->xi.p, ni, c->stream));
+    return PG_OK;
+}
+
+int pg_set_self(pg_ctx *c, int on)
+{
+    if (!c) return PG_EINVAL;
+    if ((on != 0) != (c->self != 0)) drop_graph(c);
+    c->self = on != 0;
+    return PG_OK;
+}
+
+int pg_set_graph(pg_ctx *c, int on)
+{
+    if (!c) return PG_EINVAL;
+    c->use_graph = on != 0;
+    if (!c->use_graph) drop_graph(c);
+    return PG_OK;
+}
+
+int pg_set_shape(pg_ctx *c, int np, int ctas_per_sm)
+{
+    if (!c) return PG_EINVAL;
+    if (np != 0 && np != 1 && np != 2 && np != 4) return fail(c, PG_EINVAL, "np must be 0, 1, 2 or 4");
+    if (ctas_per_sm < 0) return fail(c, PG_EINVAL, "ctas_per_sm must be >= 0");
+    if (np) c->np = np;
+    c->ctas_per_sm = ctas_per_sm;
+    c->i_dirty = true;
+    drop_graph(c);
+    return PG_OK;
+}
+
+int pg_info(pg_ctx *c, long long *out, int n)
+{
+    if (!c || !out || n < 0) return PG_EINVAL;
+    long long v[5] = {c->last_pairs, c->last_launches, 2LL * c->np, c->last_grid, c->last_slots};
+    int k = std::min(n, 5);
+    for (int i = 0; i < k; ++i) out[i] = v[i];
+    return k;
+}
+
+int pg_set_timing(pg_ctx *c, int on)
+{
+    if (!c) return PG_EINVAL;
+    if (on && !c->tk0) {
+        PG_CUDA(c, cudaEventCreate(&c->tk0));
+        PG_CUDA(c, cudaEventCreate(&c->tk1));
+    }
+    if ((on != 0) != c->timing) drop_graph(c);
+    c->timing = on != 0;
+    c->timed = false;
+    return PG_OK;
+}
+
+int pg_kernel_time(pg_ctx *c, double *ms)
+{
+    if (!c || !ms) return PG_EINVAL;
+    if (!c->timed) return fail(c, PG_ESTATE, "no timed run (pg_set_timing(ctx, 1) first)");
+    PG_CUDA(c, cudaEventSynchronize(c->tk1));
+    float f = 0;
+    PG_CUDA(c, cudaEventElapsedTime(&f, c->tk0, c->tk1));
+    *ms = f;
+    return PG_OK;
+}
+
+int pg_sync(pg_ctx *c)
+{
+    if (!c) return PG_EINVAL;
+    PG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return read_status(c);
+}
+
+}  // extern "C"
+
+// ====================================================================== runs
+
+namespace {
+
+struct Plan {
+    long long ni, nj;
+    int Bi, ntiles, njsub, grid, slots;
+    long long W;
+};
+
+int plan_allpairs(pg_ctx *c, Plan &p)
+{
+    p.ni = c->ni;
+    p.nj = nj_of(c);
+    p.Bi = allpairs_bi(c->np);
+    p.ntiles = (int)((p.ni + p.Bi - 1) / p.Bi);
+    p.njsub = (int)((p.nj + kTJ - 1) / kTJ);
+    p.W = (long long)p.ntiles * p.njsub;
+    int occ = allpairs_max_blocks_per_sm(c->np, c->mode == PG_TABLE, c->ntab);
+    int per = c->ctas_per_sm > 0 ? std::min(c->ctas_per_sm, occ) : occ;
+    long long g = (long long)c->sms * per;
+    p.grid = (int)std::max<long long>(0, std::min<long long>(g, p.W));
+    p.slots = 1;
+    for (long long t = 0; t < p.ntiles && p.grid > 0; ++t) {
+        long long bf = stream_k_first(t * p.njsub, p.grid, p.W);
+        long long bl = stream_k_first((t + 1) * p.njsub - 1, p.grid, p.W);
+        p.slots = std::max<int>(p.slots, (int)(bl - bf + 1));
+    }
+    return PG_OK;
+}
+
+// the i ordering and tile centres (sort only when it pays)
+int enqueue_tiles(pg_ctx *c, const Plan &p)
+{
+    int rc;
+    long long n = p.ni;
+    if ((rc = ensure(c, c->xt, (size_t)std::max<long long>(n, 1) * sizeof(double4))) ||
+        (rc = ensure(c, c->ctr, (size_t)std::max(p.ntiles, 1) * sizeof(double4))))
+        return rc;
+    bool do_sort = c->sort_mode == 1 || (c->sort_mode < 0 && n >= 16384);
+    c->perm = nullptr;
+    if (do_sort && n > 1) {
+        size_t hn = sort_hist_entries(n);
+        size_t nb = (hn + 4095) / 4096 + 1;
+        if ((rc = ensure(c, c->skeys0, n * 4)) || (rc = ensure(c, c->skeys1, n * 4)) ||
+            (rc = ensure(c, c->svals0, n * 4)) || (rc = ensure(c, c->svals1, n * 4)) ||
+            (rc = ensure(c, c->shist, hn * 4)) || (rc = ensure(c, c->ssums, nb * 4)) ||
+            (rc = ensure(c, c->sbbox, 6 * 8)))
+            return rc;
+        c->sort.keys[0] = (unsigned *)c->skeys0.p;
+        c->sort.keys[1] = (unsigned *)c->skeys1.p;
+        c->sort.vals[0] = (unsigned *)c->svals0.p;
+        c->sort.vals[1] = (unsigned *)c->svals1.p;
+        c->sort.hist = (unsigned *)c->shist.p;
+        c->sort.sums = (unsigned *)c->ssums.p;
+        c->sort.bbox = (unsigned long long *)c->sbbox.p;
+        PG_CUDA(c, launch_morton_sort((const double4 *)c->xi.p, n, c->sort, &c->perm, c->stream));
+        c->last_launches += 3 + 5 * 4;
+    }
+    PG_CUDA(c, launch_tile_prep((const double4 *)c->xi.p, c->perm, n, p.Bi, (double4 *)c->xt.p,
+                                (double4 *)c->ctr.p, c->stream));
+    c->last_launches += 1;
+    c->tiled_np = c->np;
+    return PG_OK;
+}
+
+int enqueue_allpairs(pg_ctx *c, const Plan &p, double *acc, double *pot)
+{
+    int rc;
+    bool table = c->mode == PG_TABLE;
+    if (p.ni > 0 && (c->i_dirty || c->use_graph || c->tiled_np != c->np)) {
+        if ((rc = enqueue_tiles(c, p))) return rc;
+        c->i_dirty = false;
+    }
+    if (p.ni == 0) return PG_OK;
+    if ((rc = ensure(c, c->part, (size_t)p.ntiles * p.slots * p.Bi * sizeof(double4)))) return rc;
+    AllPairsArgs a{};
+    a.xi = (const double4 *)c->xt.p;
+    a.ctr = (const double4 *)c->ctr.p;
+    a.jrec = (const double4 *)c->jrec.p;
+    a.ni = p.ni;
+    a.nj = p.nj;
+    a.ntiles = p.ntiles;
+    a.njsub = p.njsub;
+    a.W = p.W;
+    a.smax_slots = p.slots;
+    a.eps2 = (float)(c->eps * c->eps);
+    if (table) a.tab = table_dev(c);
+    a.part = (double4 *)c->part.p;
+    a.status = (int *)c->status.p;
+    bool zsafe = !table && a.eps2 == 0.0f;
+    size_t smem = allpairs_smem(c->np, table, c->ntab);
+    if (p.grid > 0) {
+        if (c->timing) PG_CUDA(c, cudaEventRecord(c->tk0, c->stream));
+        PG_CUDA(c, launch_allpairs(a, p.grid, c->np, table, zsafe, smem, c->stream));
+        if (c->timing) PG_CUDA(c, cudaEventRecord(c->tk1, c->stream));
+        c->timed = c->timing;
+        c->last_launches += 1;
+    }
+    CombineArgs cb{};
+    cb.part = a.part;
+    cb.perm = c->perm;
+    cb.jrec = a.jrec;
+    cb.ni = p.ni;
+    cb.Bi = p.Bi;
+    cb.njsub = p.njsub;
+    cb.smax_slots = p.slots;
+    cb.grid = std::max(p.grid, 1);
+    cb.W = std::max<long long>(p.W, 1);
+    cb.self = c->self;
+    cb.newton = !table;
+    cb.eps2 = a.eps2;
+    cb.accscale = table ? 1.0 / c->scale : 1.0;
+    cb.acc = acc;
+    cb.pot = pot;
+    PG_CUDA(c, launch_combine(cb, c->stream));
+    c->last_launches += 1;
+    c->last_pairs = p.ni * p.nj;
+    c->last_grid = p.grid;
+    c->last_slots = p.slots;
+    return PG_OK;
+}
+
+int check_run_state(pg_ctx *c)
+{
+    if (c->ni < 0) return fail(c, PG_ESTATE, "pg_set_i has not been called");
+    if (c->mode == PG_TABLE && !c->have_table) return fail(c, PG_ESTATE, "table mode without a table");
+    if (c->self && c->ni > nj_of(c))
+        return fail(c, PG_ESTATE, "self mode needs ni <= nj (i-particle k is j-particle k)");
+    if (c->have_groups || c->box > 0.0)
+        return fail(c, PG_ESTATE, "this build has no group or periodic path yet");
+    return PG_OK;
+}
+
+int run_into(pg_ctx *c, double *acc, double *pot)
+{
+    int rc = check_run_state(c);
+    if (rc) return rc;
+    c->last_launches = 0;
+    Plan p;
+    plan_allpairs(c, p);
+    if (!c->use_graph) return enqueue_allpairs(c, p, acc, pot);
+
+    char key[256];
+    snprintf(key, sizeof key, "ap|%lld|%lld|%d|%d|%g|%d|%p|%p|%p|%d|%d|%d", p.ni, p.nj, c->mode,
+             c->np, c->eps, c->self, (void *)acc, (void *)pot, c->jrec.p, c->ctas_per_sm,
+             c->sort_mode, (int)c->timing);
+    if (!c->gexec || c->gkey != key) {
+        drop_graph(c);
+        // this call runs uncaptured, which also makes every allocation the
+        // sequence needs; the capture below records the replay for later calls
+        c->i_dirty = true;
+        if ((rc = enqueue_allpairs(c, p, acc, pot))) return rc;
+        cudaGraph_t graph;
+        PG_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        rc = enqueue_allpairs(c, p, acc, pot);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+        if (rc) {
+            if (e == cudaSuccess) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&c->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+        c->gkey = key;
+        return PG_OK;
+    }
+    PG_CUDA(c, cudaGraphLaunch(c->gexec, c->stream));
+    return PG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pg_run(pg_ctx *c)
+{
+    if (!c) return PG_EINVAL;
+    if (c->ni < 0) return fail(c, PG_ESTATE, "pg_set_i has not been called");
+    int rc;
+    size_t n = (size_t)std::max<long long>(c->ni, 1);
+    if ((rc = ensure(c, c->acc, n * 24)) || (rc = ensure(c, c->pot, n * 8))) return rc;
+    return run_into(c, (double *)c->acc.p, (double *)c->pot.p);
+}
+
+int pg_run_dev(pg_ctx *c, double *a, double *phi)
+{
+    if (!c) return PG_EINVAL;
+    if (!a && c->ni > 0) return fail(c, PG_EINVAL, "a is NULL");
+    return run_into(c, a, phi);
+}
+
+int pg_get_force(pg_ctx *c, double *a, double *phi, long long ni)
+{
+    if (!c) return PG_EINVAL;
+    if (ni != c->ni) return fail(c, PG_EINVAL, "ni differs from the count given to pg_set_i");
+    if (ni > 0 && !a) return fail(c, PG_EINVAL, "a is NULL");
+    if (!c->acc.p) return fail(c, PG_ESTATE, "pg_run has not been called");
+    if (ni == 0) return pg_sync(c);
+    int rc;
+    size_t ba = (size_t)ni * 24, bp = phi ? (size_t)ni * 8 : 0;
+    if ((rc = ensure_pin(c, c->pin_o, ba + bp))) return rc;
+    PG_CUDA(c, cudaMemcpyAsync(c->pin_o.p, c->acc.p, ba, cudaMemcpyDeviceToHost, c->stream));
+    if (phi)
+        PG_CUDA(c, cudaMemcpyAsync((char *)c->pin_o.p + ba, c->pot.p, bp, cudaMemcpyDeviceToHost,
+                                   c->stream));
+    PG_CUDA(c, cudaEventRecord(c->pin_o.done, c->stream));
+    if ((rc = pg_sync(c))) return rc;
+    std::memcpy(a, c->pin_o.p, ba);
+    if (phi) std::memcpy(phi, (char *)c->pin_o.p + ba, bp);
+    return PG_OK;
+}
+
+int pg_set_groups(pg_ctx *c, long long ngroups, const long long *i_off, const long long *j_off,
+                  const int *jlist)
+{
+    (void)ngroups; (void)i_off; (void)j_off; (void)jlist;
+    if (!c) return PG_EINVAL;
+    return fail(c, PG_ESTATE, "this build has no group path yet");
+}
+
+int pg_clear_groups(pg_ctx *c)
+{
+    if (!c) return PG_EINVAL;
+    c->have_groups = false;
+    drop_graph(c);
+    return PG_OK;
+}
+
+int pg_set_periodic(pg_ctx *c, double box)
+{
+    if (!c) return PG_EINVAL;
+    if (!(box >= 0.0)) return fail(c, PG_EINVAL, "box must be >= 0");
+    if (box > 0.0) return fail(c, PG_ESTATE, "this build has no periodic path yet");
+    c->box = 0.0;
+    return PG_OK;
+}
+
+int pg_backward_dev(pg_ctx *c, const double *w, double *dx, double *dm, float *dv)
+{
+    (void)w; (void)dx; (void)dm; (void)dv;
+    if (!c) return PG_EINVAL;
+    return fail(c, PG_ESTATE, "this build has no backward path yet");
+}
+
+int pg_tune(pg_ctx *c)
+{
+    if (!c) return PG_EINVAL;
+    int rc = check_run_state(c);
+    if (rc) return rc;
+    if (c->ni <= 0) return PG_OK;
+    size_t n = (size_t)c->ni;
+    if ((rc = ensure(c, c->acc, n * 24)) || (rc = ensure(c, c->pot, n * 8))) return rc;
+    bool graph = c->use_graph;
+    c->use_graph = false;
+    cudaEvent_t e0, e1;
+    PG_CUDA(c, cudaEventCreate(&e0));
+    PG_CUDA(c, cudaEventCreate(&e1));
+    int best_np = c->np, best_cta = c->ctas_per_sm;
+    float best = 1e30f;
+    const int nps[3] = {1, 2, 4};
+    for (int np : nps) {
+        int occ = allpairs_max_blocks_per_sm(np, c->mode == PG_TABLE, c->ntab);
+        for (int cta = 1; cta <= occ; ++cta) {
+            c->np = np;
+            c->ctas_per_sm = cta;
+            c->i_dirty = true;
+            if ((rc = run_into(c, (double *)c->acc.p, (double *)c->pot.p))) break;
+            PG_CUDA(c, cudaEventRecord(e0, c->stream));
+            for (int r = 0; r < 3 && !rc; ++r) rc = run_into(c, (double *)c->acc.p, (double *)c->pot.p);
+            PG_CUDA(c, cudaEventRecord(e1, c->stream));
+            PG_CUDA(c, cudaEventSynchronize(e1));
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (!rc && ms < best) {
+                best = ms;
+                best_np = np;
+                best_cta = cta;
+            }
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->np = best_np;
+    c->ctas_per_sm = best_cta;
+    c->i_dirty = true;
+    c->use_graph = graph;
+    drop_graph(c);
+    if (rc) return rc;
+    return read_status(c);
+}
+
+}  // extern "C"

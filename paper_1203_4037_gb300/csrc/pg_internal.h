@@ -1,0 +1,184 @@
+// pg_internal.h -- launch arguments and launcher declarations shared by the
+// host side of the pg library (pg_api.cu) and its kernel files. Not part of
+// the public C ABI (that is include/pg.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pg {
+
+// j sub-tile depth of the all-pairs kernel (j records staged per step)
+constexpr int kTJ = 256;
+// threads per CTA of the all-pairs and group kernels
+constexpr int kNT = 128;
+// time limit of any device-side wait, in nanoseconds
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+
+// device status word codes (status[0] = code, status[1] = where)
+constexpr int kStatusTimeout = 1;
+constexpr int kStatusBadIndex = 2;
+
+// Interpolation constants of the bit-pattern table, as the kernels use them.
+struct TableDev {
+    const float2 *AG1;     // per knot {A_k = G0_k - s_k G1_k, G1_k}, 2^(E+F) entries
+    int n;                 // 2^(E+F)
+    int shift;             // 23 - F
+    unsigned base;         // bit pattern of 2.0f >> shift (index of s = 2)
+    float s_max;           // 2^(2^E) (2 - 2^-F)
+    double scale;          // sqrt(s_max - 2) / r_cut: positions -> scaled units
+};
+
+// all-pairs force launch (stream-K split of (i-tile, j-sub-tile) units)
+struct AllPairsArgs {
+    const double4 *xi;     // i positions (x, y, z, -) in tile order
+    const double4 *ctr;    // FP64 centre of each i-tile
+    const double4 *jrec;   // j records (x, y, z, m), FP64
+    long long ni, nj;
+    int ntiles;            // ceil(ni / Bi)
+    int njsub;             // ceil(nj / kTJ)
+    long long W;           // ntiles * njsub work units
+    int smax_slots;        // partial slots per tile
+    float eps2;
+    TableDev tab;
+    double4 *part;         // partial sums [ntiles][smax_slots][Bi]
+    int *status;
+};
+
+// combine partials into the outputs (fixed slot order) and scatter
+struct CombineArgs {
+    const double4 *part;
+    const unsigned *perm;  // tile order -> caller's i index (nullptr: identity)
+    const double4 *jrec;   // for the self term (mass of j = caller's i index)
+    long long ni;
+    int Bi, njsub, smax_slots, grid;
+    long long W;
+    int self;              // leave out i's own pair (i index k == j index k)
+    int newton;            // 1: Newton (has potential), 0: table
+    float eps2;
+    double accscale;       // table: r_cut / sqrt(s_max - 2); Newton: 1
+    double *acc;           // out: (ni, 3)
+    double *pot;           // out: (ni), may be null
+};
+
+// batched groups: one work item = (group, i-range of at most Bi)
+struct GroupItem {
+    int group;
+    int i0;                // first i (index into the i array)
+    int ni;                // i count in this item
+    int pad;
+};
+
+struct GroupArgs {
+    const double4 *xi;     // i positions (x, y, z, -)
+    const double4 *jrec;   // j records (x, y, z, m)
+    const long long *j_off;        // CSR offsets into jlist, ngroups + 1
+    const int *jlist;      // j indices; periodic: low 27 bits index, high 5 bits shift code
+    const GroupItem *items;
+    const double4 *gctr;   // FP64 centre of each group
+    int nitems;
+    int *queue;            // work counter (reset to 0 before each launch)
+    long long nj;          // number of j records (bounds check)
+    float eps2;
+    TableDev tab;
+    double box;            // periodic box (> 0: decode shift codes)
+    const unsigned *perm;  // i index -> output index (nullptr: identity)
+    double accscale;
+    double *acc, *pot;
+    int *status;
+};
+
+// backward (all-pairs, self mode)
+struct BackwardArgs {
+    const double4 *xi;     // positions in tile order (x, y, z, m)
+    const double4 *wv;     // loss weights in tile order (wx, wy, wz, -)
+    const double4 *ctr;    // tile centres
+    const float4 *jw;      // unused slot for future layouts
+    long long n;
+    int ntiles, njsub;
+    long long W;
+    int smax_slots;
+    float eps2;
+    TableDev tab;
+    const double4 *jx;     // j positions+mass (x, y, z, m) in tile order
+    const double4 *jwv;    // j weights (wx, wy, wz, -) in tile order
+    double4 *part;         // partials [ntiles][slots][Bi] {gx, gy, gz, gm}
+    double *dv;            // table gradient accumulators (FP64, 2^(E+F))
+    int *status;
+};
+
+// ---------------------------------------------------------------- launchers
+// all return cudaError_t of the launch
+
+cudaError_t launch_pack_j(const double *x, const double *m, double4 *jrec, long long n,
+                          cudaStream_t st);
+cudaError_t launch_pack_i(const double *x, double4 *xi, long long n, cudaStream_t st);
+
+// spatial ordering of i: Morton keys in the bounding box, LSD radix sort
+struct SortScratch {
+    unsigned *keys[2];
+    unsigned *vals[2];
+    unsigned *hist;        // 256 * nchunks (+ block sums)
+    unsigned *sums;
+    unsigned long long *bbox;  // 6 ordered-int words
+    size_t cap;            // elements
+    size_t hist_cap;
+};
+size_t sort_hist_entries(long long n);
+cudaError_t launch_morton_sort(const double4 *xi, long long n, SortScratch &s, unsigned **perm_out,
+                               cudaStream_t st);
+cudaError_t launch_radix_sort(unsigned *keys, unsigned *vals, long long n, int key_bits,
+                              SortScratch &s, unsigned **keys_out, unsigned **vals_out,
+                              cudaStream_t st);
+
+// gather i into tile order and compute tile centres
+cudaError_t launch_tile_prep(const double4 *xi, const unsigned *perm, long long n, int Bi,
+                             double4 *xi_tiled, double4 *ctr, cudaStream_t st);
+
+cudaError_t launch_allpairs(const AllPairsArgs &a, int grid, int np, bool table, bool zsafe,
+                            size_t smem, cudaStream_t st);
+int allpairs_bi(int np);
+size_t allpairs_smem(int np, bool table, int ntab);
+int allpairs_max_blocks_per_sm(int np, bool table, int ntab);
+cudaError_t launch_combine(const CombineArgs &c, cudaStream_t st);
+long long stream_k_first(long long u, int grid, long long W);
+
+cudaError_t launch_table_prep(const float *G0, const float *G1, float2 *AG1, int E, int F,
+                              cudaStream_t st);
+cudaError_t launch_table_from_values(const float *v, float *G0, float *G1, int E, int F,
+                                     cudaStream_t st);
+
+cudaError_t launch_groups(const GroupArgs &g, int grid, bool table, size_t smem, cudaStream_t st);
+size_t groups_smem(bool table, int ntab);
+int groups_max_blocks_per_sm(bool table, int ntab);
+
+// periodic cell list: bins, sorts and emits per-cell j-lists with shift codes
+struct CellList {
+    int nc;                // cells per axis
+    long long ncell;
+    unsigned *cell_of;     // per particle (input order)
+    unsigned *perm;        // sorted position -> input index
+    unsigned *start;       // ncell + 1
+    long long *j_off;      // ncell + 1
+    int *jlist;
+    long long jlist_cap;
+    double4 *xs;           // particles in cell order (x, y, z, m)
+    double4 *gctr;         // cell centres
+    GroupItem *items;
+    int nitems;
+    unsigned *cost_keys;
+};
+cudaError_t launch_cell_bin(const double4 *jrec, long long n, double box, int nc,
+                            unsigned *cell_of, unsigned *idx, cudaStream_t st);
+
+// backward
+cudaError_t launch_backward(const BackwardArgs &a, int grid, bool table, size_t smem,
+                            cudaStream_t st);
+size_t backward_smem(bool table, int ntab);
+int backward_bi();
+cudaError_t launch_backward_combine(const double4 *part, const unsigned *perm, long long n,
+                                    int Bi, int njsub, int slots, int grid, long long W,
+                                    double *dx, double *dm, cudaStream_t st);
+
+}  // namespace pg

@@ -1,0 +1,116 @@
+"""Parity of the tabulated central force (Eq. 2, Section 3.4) with the FP64
+oracle through the C ABI: the table built by the library equals the
+oracle's bit for bit; all-pairs forces match the oracle's table semantics
+(tight tolerance) and the closed-form shape (table-induced error <= 1e-3);
+the Section 4.2 accuracy run passes on the GPU."""
+
+import numpy as np
+import pytest
+
+import gen
+from pgtest import assert_parity, need_cuda, rel_vec
+
+pytestmark = pytest.mark.gpu
+
+RS = 1 / 256
+
+
+@pytest.fixture(scope="module")
+def pg():
+    return need_cuda()
+
+
+def gs_par(r_cut, eps):
+    return [r_cut / 4.5, eps]
+
+
+@pytest.mark.parametrize("E,F", [(4, 8), (3, 5), (4, 6), (2, 3)])
+def test_table_bits_match_oracle(pg, orc, E, F):
+    r_cut = 4.5 * RS
+    par = [RS, RS / 16]
+    G0o, G1o = orc.table_build(E, F, r_cut, orc.SHAPE_GAUSS_SPLIT, par)
+    n = orc.table_size(E, F)
+    with pg.Context(0) as c:
+        c.set_table(lambda r: orc.shape(orc.SHAPE_GAUSS_SPLIT, par, r), r_cut, E, F)
+        G0, G1 = c.get_table(n)
+        assert np.array_equal(G0.view(np.uint32), G0o.view(np.uint32))
+        assert np.array_equal(G1.view(np.uint32), G1o.view(np.uint32))
+        v = orc.table_values(E, F, r_cut, orc.SHAPE_GAUSS_SPLIT, par)
+        c.set_table_values(v, r_cut, E, F)
+        G0, G1 = c.get_table(n)
+        assert np.array_equal(G0.view(np.uint32), G0o.view(np.uint32))
+        assert np.array_equal(G1.view(np.uint32), G1o.view(np.uint32))
+        torch = pytest.importorskip("torch")
+        c.set_table_values_dev(torch.tensor(v, device="cuda"), r_cut, E, F)
+        G0, G1 = c.get_table(n)
+        assert np.array_equal(G0.view(np.uint32), G0o.view(np.uint32))
+        assert np.array_equal(G1.view(np.uint32), G1o.view(np.uint32))
+
+
+def table_allpairs(pg, x, m, v, r_cut, E, F, shape=None):
+    with pg.Context(0) as c:
+        c.set_mode(pg.PG_TABLE)
+        c.set_table_values(v, r_cut, E, F)
+        c.set_self(True)
+        if shape:
+            c.set_shape(*shape)
+        return c.forces(x, x, m)
+
+
+@pytest.mark.parametrize("E,F,n", [(3, 5, 3000), (4, 8, 4001)])
+@pytest.mark.parametrize("shape", [(1, 0), (2, 0), (4, 0)])
+def test_allpairs_table_semantics(pg, orc, E, F, n, shape):
+    rng = np.random.default_rng(n + E)
+    r_cut = 0.1
+    x = rng.random((n, 3)) * 0.35          # dense: many pairs inside the cutoff
+    m = rng.uniform(0.5, 1.5, n) / n
+    par = gs_par(r_cut, 1 / 64)
+    v = orc.table_values(E, F, r_cut, orc.SHAPE_GAUSS_SPLIT, par)
+    G0, G1 = orc.table_from_values(E, F, v)
+    a, p = table_allpairs(pg, x, m, v, r_cut, E, F, shape)
+    assert np.all(p == 0)
+    ao, amb = orc.table_forces(x, x, m, E, F, r_cut, G0, G1, skip=np.arange(n), window=1e-6)
+    # pairs within rounding distance of the cutoff may fall either side
+    err = np.linalg.norm(a - ao, axis=1)
+    scale = np.linalg.norm(ao, axis=1)
+    rel = np.maximum(err - amb, 0) / scale
+    assert_parity(rel, what="a vs table semantics")
+    # against the closed form: only the table's own error remains
+    ac, ambc = orc.shape_forces(x, x, m, orc.SHAPE_GAUSS_SPLIT, par, r_cut, skip=np.arange(n),
+                                window=1e-6)
+    relc = np.maximum(np.linalg.norm(a - ac, axis=1) - ambc, 0) / np.linalg.norm(ac, axis=1)
+    assert np.max(relc) <= 1e-3
+
+
+def test_section_4_2_run_on_gpu(pg, orc):
+    """S2 PP shape through the GPU table (E = 4, F = 5): each of 4096
+    log-spaced pairs is one i-particle with a unit mass at the origin; PP
+    (GPU) plus PM (closed form) stays within 1e-3 of R(r, eps)."""
+    eps, r_cut, E, F = 3.125e-3, 4.6875e-2, 4, 5
+    d = gen.log_pairs(4096, 77) * r_cut
+    with pg.Context(0) as c:
+        c.set_mode(pg.PG_TABLE)
+        c.set_table(lambda r: orc.shape(orc.SHAPE_S2PP, [eps, r_cut], r), r_cut, E, F)
+        a, _ = c.forces(d, np.zeros((1, 3)), np.ones(1))
+    r = np.linalg.norm(d, axis=1)
+    f_pp = np.einsum("ij,ij->i", a, -d / r[:, None])   # attraction toward the origin
+    worst = 0.0
+    for rr, fp in zip(r, f_pp):
+        exact = orc.s2_profile(rr, eps)
+        worst = max(worst, abs(fp + orc.s2_profile(rr, r_cut) - exact) / exact)
+    assert worst < 1e-3
+
+
+def test_linear_in_r2_shape_exact(pg, orc):
+    E, F, r_cut = 4, 6, 0.25
+    alpha, beta = 3.0, -17.0
+    rng = np.random.default_rng(8)
+    d = rng.uniform(-0.14, 0.14, (5000, 3))
+    d = d[np.linalg.norm(d, axis=1) < 0.999 * r_cut]
+    with pg.Context(0) as c:
+        c.set_mode(pg.PG_TABLE)
+        c.set_table(lambda r: alpha + beta * r * r, r_cut, E, F)
+        a, _ = c.forces(d, np.zeros((1, 3)), np.ones(1))
+    r2 = np.einsum("ij,ij->i", d, d)
+    want = -(alpha + beta * r2)[:, None] * d
+    assert_parity(rel_vec(a, want), median_tol=1e-6, max_tol=1e-5)
