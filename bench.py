@@ -274,6 +274,8 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    # one non-default stream for the library, the timing events and graphs
+    torch.cuda.set_stream(torch.cuda.Stream(device=dev))
     pg.build()
 
     npart = args.n

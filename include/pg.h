@@ -59,15 +59,16 @@ typedef struct pg_ctx pg_ctx;
 
 /* Open a context on CUDA device `device` (g5_open, Section 3.6; no rsqrt
  * bias calibration: the GPU's rsqrt has a documented error bound instead).
- * *out receives the handle; destroy it with pg_destroy. The context owns an
- * internal non-blocking stream until pg_set_stream replaces it. */
+ * *out receives the handle; destroy it with pg_destroy. The context starts
+ * on an internal non-blocking stream of its own (pg_set_stream changes it). */
 int pg_create(pg_ctx **out, int device);
 
 /* Release every resource of the context (g5_close). NULL is ignored. */
 void pg_destroy(pg_ctx *ctx);
 
 /* Enqueue all later work on `cuda_stream` (a cudaStream_t owned by the
- * caller, e.g. the current PyTorch stream); NULL restores the internal one. */
+ * caller, e.g. the current PyTorch stream); NULL is the CUDA legacy default
+ * stream. Work already enqueued is ordered before later work. */
 int pg_set_stream(pg_ctx *ctx, void *cuda_stream);
 
 /* Plummer softening length used by PG_NEWTON (g5_set_eps_to_all,

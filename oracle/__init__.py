@@ -61,7 +61,7 @@ _SIGS = {
     "orc_table_build": (_I, [_I, _I, _D, _I, _P, _P, _P]),
     "orc_table_eval": (_D, [_I, _I, _D, _P, _P, _D]),
     "orc_table_forces": (_I, [_LL, _P, _P, _LL, _P, _P, _I, _I, _D, _P, _P, _D, _D, _P, _P, _I]),
-    "orc_shape_forces": (_I, [_LL, _P, _P, _LL, _P, _P, _I, _P, _D, _D, _D, _P, _P, _I]),
+    "orc_shape_forces": (_I, [_LL, _P, _P, _LL, _P, _P, _I, _P, _D, _D, _D, _P, _P, _P, _I]),
     "orc_grad_newton": (_I, [_LL, _P, _P, _P, _D, _P, _P, _P, _I]),
     "orc_grad_newton_at": (_I, [_LL, _P, _P, _P, _D, _LL, _P, _P, _P, _I]),
     "orc_grad_table": (_I, [_LL, _P, _P, _P, _D, _I, _I, _D, _P, _P, _P, _P, _I]),
@@ -224,16 +224,18 @@ def table_forces(xi, xj, mj, E, F, r_cut, G0, G1, box=0.0, skip=None, window=0.0
 
 
 def shape_forces(xi, xj, mj, shape_id, par, r_cut, box=0.0, skip=None, window=0.0,
-                 nthreads_=None):
-    """O-T1: Eq. (2) with the closed-form shape, pairs with r < r_cut."""
+                 nthreads_=None, with_absum=False):
+    """O-T1: Eq. (2) with the closed-form shape, pairs with r < r_cut.
+    Returns (acc, amb) or, with_absum, (acc, amb, sum_j |pair term|)."""
     xi = _f64(xi, (-1, 3)); xj = _f64(xj, (-1, 3)); mj = _f64(mj); par = _f64(par)
     sk = None if skip is None else np.ascontiguousarray(skip, dtype=np.int64)
     ni = len(xi)
-    acc = np.empty((ni, 3)); amb = np.empty(ni)
+    acc = np.empty((ni, 3)); amb = np.empty(ni); absum = np.empty(ni)
     _chk(lib().orc_shape_forces(ni, _ptr(xi), _ptr(sk), len(xj), _ptr(xj), _ptr(mj),
                                 int(shape_id), _ptr(par), float(r_cut), float(box),
-                                float(window), _ptr(acc), _ptr(amb), nthreads_ or nthreads()))
-    return acc, amb
+                                float(window), _ptr(acc), _ptr(amb), _ptr(absum),
+                                nthreads_ or nthreads()))
+    return (acc, amb, absum) if with_absum else (acc, amb)
 
 
 # ---------------------------------------------------------------- gradients

@@ -373,7 +373,7 @@ typedef struct {
     int E, F; double sc2, smax; const float *G0, *G1;
     /* closed form */
     int shape; const double *par; double r_cut;
-    double window; double *acc; double *amb;
+    double window; double *acc; double *amb; double *absum;
 } tab_ctx;
 
 static void table_body(long long lo, long long hi, void *p)
@@ -435,7 +435,7 @@ static void shape_body(long long lo, long long hi, void *p)
     tab_ctx *c = (tab_ctx *)p;
     double rc2 = c->r_cut * c->r_cut;
     for (long long i = lo; i < hi; ++i) {
-        nsum ax = {0, 0}, ay = {0, 0}, az = {0, 0}, am = {0, 0};
+        nsum ax = {0, 0}, ay = {0, 0}, az = {0, 0}, am = {0, 0}, ab = {0, 0};
         long long sk = c->skip ? c->skip[i] : -1;
         for (long long j = 0; j < c->nj; ++j) {
             if (j == sk) continue;
@@ -452,26 +452,31 @@ static void shape_body(long long lo, long long hi, void *p)
             nadd(&ax, m * g * dx);
             nadd(&ay, m * g * dy);
             nadd(&az, m * g * dz);
+            nadd(&ab, m * fabs(g) * r);
         }
         c->acc[3 * i] = nval(&ax);
         c->acc[3 * i + 1] = nval(&ay);
         c->acc[3 * i + 2] = nval(&az);
         if (c->amb) c->amb[i] = nval(&am);
+        if (c->absum) c->absum[i] = nval(&ab);
     }
 }
 
-/* O-T1: Eq. (2) with the closed-form shape, pairs with r < r_cut only. */
+/* O-T1: Eq. (2) with the closed-form shape, pairs with r < r_cut only.
+ * absum (optional) receives sum_j |m_j g(r_ij) d_ij| per i: a per-pair
+ * relative table error bound (Section 4.2) bounds a per-particle error by
+ * that fraction of this sum. */
 int orc_shape_forces(long long ni, const double *xi, const long long *skip,
                      long long nj, const double *xj, const double *mj,
                      int shape, const double *par, double r_cut, double box,
-                     double window, double *acc, double *amb, int nthreads)
+                     double window, double *acc, double *amb, double *absum, int nthreads)
 {
     if (ni < 0 || nj < 0 || r_cut <= 0) return -1;
     tab_ctx c;
     memset(&c, 0, sizeof c);
     c.xi = xi; c.skip = skip; c.nj = nj; c.xj = xj; c.mj = mj; c.box = box;
     c.shape = shape; c.par = par; c.r_cut = r_cut; c.window = window;
-    c.acc = acc; c.amb = amb;
+    c.acc = acc; c.amb = amb; c.absum = absum;
     parallel_for(ni, nthreads, shape_body, &c);
     return 0;
 }

@@ -71,12 +71,25 @@ struct pg_ctx {
     // host staging
     PinBuf pin_j, pin_i, pin_o;
 
-    // groups
+    // groups (host copies of the CSR offsets rebuild the items when the
+    // launch shape changes)
     bool have_groups = false;
     long long ngroups = 0;
-    DevBuf g_joff, g_jlist, g_items, g_ctr, g_queue;
+    std::vector<long long> h_ioff, h_joff;
+    DevBuf g_ioff, g_joff, g_jlist, g_items, g_ctr, g_queue;
     int g_nitems = 0;
+    int g_items_np = 0;
     long long g_pairs = 0;
+    long long g_maxj = -1;       // largest j index listed
+
+    // periodic cell list
+    CellScratch cells{};
+    DevBuf c_wrapped, c_xs, c_perm, c_start, c_jcount, c_icount, c_joff32, c_joff, c_ioff,
+        c_jlist, c_items_raw, c_items, c_ctr, c_pairs;
+    bool pairs_on_device = false;
+
+    // backward
+    DevBuf bw_wj, bw_wt, bw_dv;
 
     // launch shape
     int np = 2;
@@ -322,8 +335,12 @@ void pg_destroy(pg_ctx *c)
     drop_graph(c);
     DevBuf *bufs[] = {&c->G0, &c->G1, &c->AG1, &c->jrec, &c->stage, &c->xi, &c->xt, &c->ctr,
                       &c->skeys0, &c->skeys1, &c->svals0, &c->svals1, &c->shist, &c->ssums,
-                      &c->sbbox, &c->acc, &c->pot, &c->part, &c->status, &c->g_joff,
-                      &c->g_jlist, &c->g_items, &c->g_ctr, &c->g_queue};
+                      &c->sbbox, &c->acc, &c->pot, &c->part, &c->status, &c->g_ioff,
+                      &c->g_joff, &c->g_jlist, &c->g_items, &c->g_ctr, &c->g_queue,
+                      &c->c_wrapped, &c->c_xs, &c->c_perm, &c->c_start, &c->c_jcount,
+                      &c->c_icount, &c->c_joff32, &c->c_joff, &c->c_ioff, &c->c_jlist,
+                      &c->c_items_raw, &c->c_items, &c->c_ctr, &c->c_pairs, &c->bw_wj,
+                      &c->bw_wt, &c->bw_dv};
     for (DevBuf *b : bufs) free_dev(*b);
     free_pin(c->pin_j);
     free_pin(c->pin_i);
@@ -337,7 +354,7 @@ void pg_destroy(pg_ctx *c)
 int pg_set_stream(pg_ctx *c, void *s)
 {
     if (!c) return PG_EINVAL;
-    cudaStream_t ns = s ? (cudaStream_t)s : c->own_stream;
+    cudaStream_t ns = (cudaStream_t)s;   // NULL: the CUDA legacy default stream
     if (ns != c->stream) {
         // keep ordering: the new stream waits for work already enqueued
         cudaEvent_t ev;
@@ -569,6 +586,13 @@ int pg_set_shape(pg_ctx *c, int np, int ctas_per_sm)
 int pg_info(pg_ctx *c, long long *out, int n)
 {
     if (!c || !out || n < 0) return PG_EINVAL;
+    if (c->pairs_on_device && c->c_pairs.p) {
+        unsigned long long v = 0;
+        PG_CUDA(c, cudaMemcpyAsync(&v, c->c_pairs.p, 8, cudaMemcpyDeviceToHost, c->stream));
+        PG_CUDA(c, cudaStreamSynchronize(c->stream));
+        c->last_pairs = (long long)v;
+        c->pairs_on_device = false;
+    }
     long long v[5] = {c->last_pairs, c->last_launches, 2LL * c->np, c->last_grid, c->last_slots};
     int k = std::min(n, 5);
     for (int i = 0; i < k; ++i) out[i] = v[i];
@@ -735,36 +759,229 @@ int check_run_state(pg_ctx *c)
 {
     if (c->ni < 0) return fail(c, PG_ESTATE, "pg_set_i has not been called");
     if (c->mode == PG_TABLE && !c->have_table) return fail(c, PG_ESTATE, "table mode without a table");
+    if (c->have_groups) {
+        if (c->h_ioff.back() > c->ni)
+            return fail(c, PG_ESTATE, "groups cover more i-particles than pg_set_i gave");
+        if (c->g_maxj >= nj_of(c)) return fail(c, PG_ESTATE, "a j-list index is beyond the j-particles");
+        return PG_OK;
+    }
+    if (c->box > 0.0) {
+        if (c->mode != PG_TABLE) return fail(c, PG_ESTATE, "the periodic cell path needs PG_TABLE");
+        if (!c->self || c->ni != nj_of(c))
+            return fail(c, PG_ESTATE, "the periodic cell path needs the self mode with ni == nj");
+        if (c->r_cut * 3.0 > c->box) return fail(c, PG_ESTATE, "periodic path needs r_cut <= box / 3");
+        return PG_OK;
+    }
     if (c->self && c->ni > nj_of(c))
         return fail(c, PG_ESTATE, "self mode needs ni <= nj (i-particle k is j-particle k)");
-    if (c->have_groups || c->box > 0.0)
-        return fail(c, PG_ESTATE, "this build has no group or periodic path yet");
     return PG_OK;
+}
+
+// host items for the groups: chunks of at most Bi i-particles, longest first
+int upload_group_items(pg_ctx *c)
+{
+    int Bi = groups_bi(c->np);
+    std::vector<GroupItem> items;
+    std::vector<long long> cost;
+    for (long long g = 0; g < c->ngroups; ++g) {
+        long long i0 = c->h_ioff[g], ni = c->h_ioff[g + 1] - i0;
+        long long nj = c->h_joff[g + 1] - c->h_joff[g];
+        for (long long k = 0; k < ni; k += Bi) {
+            GroupItem it;
+            it.group = (int)g;
+            it.i0 = (int)(i0 + k);
+            it.ni = (int)std::min<long long>(Bi, ni - k);
+            it.pad = 0;
+            items.push_back(it);
+            cost.push_back((long long)it.ni * nj);
+        }
+    }
+    std::vector<size_t> order(items.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+    std::vector<GroupItem> sorted(items.size());
+    for (size_t k = 0; k < order.size(); ++k) sorted[k] = items[order[k]];
+    int rc;
+    if ((rc = ensure(c, c->g_items, std::max<size_t>(sorted.size(), 1) * sizeof(GroupItem)))) return rc;
+    if (!sorted.empty())
+        PG_CUDA(c, cudaMemcpy(c->g_items.p, sorted.data(), sorted.size() * sizeof(GroupItem),
+                              cudaMemcpyHostToDevice));
+    c->g_nitems = (int)sorted.size();
+    c->g_items_np = c->np;
+    return PG_OK;
+}
+
+GroupArgs group_args(pg_ctx *c)
+{
+    GroupArgs g{};
+    g.eps2 = (float)(c->eps * c->eps);
+    if (c->mode == PG_TABLE) g.tab = table_dev(c);
+    g.accscale = c->mode == PG_TABLE ? 1.0 / c->scale : 1.0;
+    g.status = (int *)c->status.p;
+    g.queue = (int *)c->g_queue.p;
+    return g;
+}
+
+int launch_group_kernel(pg_ctx *c, const GroupArgs &g)
+{
+    bool table = c->mode == PG_TABLE;
+    int occ = groups_max_blocks_per_sm(c->np, table, c->ntab);
+    int per = c->ctas_per_sm > 0 ? std::min(c->ctas_per_sm, occ) : occ;
+    int grid = c->sms * per;
+    PG_CUDA(c, cudaMemsetAsync(c->g_queue.p, 0, sizeof(int), c->stream));
+    if (c->timing) PG_CUDA(c, cudaEventRecord(c->tk0, c->stream));
+    PG_CUDA(c, launch_groups(g, grid, c->np, table, groups_smem(table, c->ntab), c->stream));
+    if (c->timing) PG_CUDA(c, cudaEventRecord(c->tk1, c->stream));
+    c->timed = c->timing;
+    c->last_grid = grid;
+    c->last_launches += 1;
+    return PG_OK;
+}
+
+int enqueue_groups(pg_ctx *c, double *acc, double *pot)
+{
+    int rc;
+    if (c->g_items_np != c->np && (rc = upload_group_items(c))) return rc;
+    if ((rc = ensure(c, c->g_ctr, (size_t)std::max<long long>(c->ngroups, 1) * sizeof(double4))) ||
+        (rc = ensure(c, c->g_queue, 16)))
+        return rc;
+    if (c->h_ioff.back() < c->ni) {   // i-particles outside every group get zeros
+        PG_CUDA(c, cudaMemsetAsync(acc, 0, (size_t)c->ni * 24, c->stream));
+        if (pot) PG_CUDA(c, cudaMemsetAsync(pot, 0, (size_t)c->ni * 8, c->stream));
+    }
+    PG_CUDA(c, launch_group_ctr((const double4 *)c->xi.p, (const long long *)c->g_ioff.p,
+                                c->ngroups, (double4 *)c->g_ctr.p, c->stream));
+    c->last_launches += 1;
+    GroupArgs g = group_args(c);
+    g.xi = (const double4 *)c->xi.p;
+    g.jrec = (const double4 *)c->jrec.p;
+    g.j_off = (const long long *)c->g_joff.p;
+    g.jlist = (const int *)c->g_jlist.p;
+    g.items = (const GroupItem *)c->g_items.p;
+    g.gctr = (const double4 *)c->g_ctr.p;
+    g.nitems = c->g_nitems;
+    g.nj = nj_of(c);
+    g.box = 0.0;
+    g.perm = nullptr;
+    g.acc = acc;
+    g.pot = pot;
+    if ((rc = launch_group_kernel(c, g))) return rc;
+    c->last_pairs = c->g_pairs;
+    return PG_OK;
+}
+
+int enqueue_cells(pg_ctx *c, double *acc, double *pot)
+{
+    int rc;
+    long long n = c->ni;
+    int nc = (int)std::floor(c->box / c->r_cut);
+    if (nc > 1024) nc = 1024;
+    long long ncell = (long long)nc * nc * nc;
+    int Bi = groups_bi(c->np);
+    long long item_cap = ncell + n / Bi + 1;
+    long long sn = std::max(n, item_cap);
+    CellScratch &s = c->cells;
+    size_t hn = sort_hist_entries(sn);
+    size_t nb = (std::max<size_t>(hn, ncell + 1) + 4095) / 4096 + 1;
+    if ((rc = ensure(c, c->c_wrapped, n * 32)) || (rc = ensure(c, c->c_xs, n * 32)) ||
+        (rc = ensure(c, c->c_perm, n * 4)) || (rc = ensure(c, c->c_start, (ncell + 1) * 4)) ||
+        (rc = ensure(c, c->c_jcount, ncell * 4)) || (rc = ensure(c, c->c_icount, ncell * 4)) ||
+        (rc = ensure(c, c->c_joff32, (ncell + 1) * 4)) || (rc = ensure(c, c->c_joff, (ncell + 1) * 8)) ||
+        (rc = ensure(c, c->c_ioff, (ncell + 1) * 4)) || (rc = ensure(c, c->c_jlist, 27 * n * 4)) ||
+        (rc = ensure(c, c->c_items_raw, item_cap * sizeof(GroupItem))) ||
+        (rc = ensure(c, c->c_items, item_cap * sizeof(GroupItem))) ||
+        (rc = ensure(c, c->c_ctr, ncell * 32)) || (rc = ensure(c, c->c_pairs, 8)) ||
+        (rc = ensure(c, c->skeys0, sn * 4)) || (rc = ensure(c, c->skeys1, sn * 4)) ||
+        (rc = ensure(c, c->svals0, sn * 4)) || (rc = ensure(c, c->svals1, sn * 4)) ||
+        (rc = ensure(c, c->shist, hn * 4)) || (rc = ensure(c, c->ssums, nb * 4)) ||
+        (rc = ensure(c, c->g_queue, 16)))
+        return rc;
+    if (27 * n >= (1LL << 31)) return fail(c, PG_EINVAL, "too many particles for the cell lists");
+    s.wrapped = (double4 *)c->c_wrapped.p;
+    s.xs = (double4 *)c->c_xs.p;
+    s.perm = (unsigned *)c->c_perm.p;
+    s.start = (unsigned *)c->c_start.p;
+    s.jcount = (unsigned *)c->c_jcount.p;
+    s.icount = (unsigned *)c->c_icount.p;
+    s.joff32 = (unsigned *)c->c_joff32.p;
+    s.joff = (long long *)c->c_joff.p;
+    s.ioff = (unsigned *)c->c_ioff.p;
+    s.jlist = (int *)c->c_jlist.p;
+    s.items_raw = (GroupItem *)c->c_items_raw.p;
+    s.items = (GroupItem *)c->c_items.p;
+    s.ctr = (double4 *)c->c_ctr.p;
+    s.item_cap = item_cap;
+    s.pairs = (unsigned long long *)c->c_pairs.p;
+    c->sort.keys[0] = (unsigned *)c->skeys0.p;
+    c->sort.keys[1] = (unsigned *)c->skeys1.p;
+    c->sort.vals[0] = (unsigned *)c->svals0.p;
+    c->sort.vals[1] = (unsigned *)c->svals1.p;
+    c->sort.hist = (unsigned *)c->shist.p;
+    c->sort.sums = (unsigned *)c->ssums.p;
+    PG_CUDA(c, launch_cell_build((const double4 *)c->jrec.p, n, c->box, nc, Bi, s, c->sort,
+                                 c->stream));
+    c->last_launches += 30;
+    GroupArgs g = group_args(c);
+    g.xi = s.xs;
+    g.jrec = s.xs;
+    g.j_off = s.joff;
+    g.jlist = s.jlist;
+    g.items = s.items;
+    g.gctr = s.ctr;
+    g.nitems = -1;
+    g.nitems_dev = s.ioff + ncell;
+    g.nj = n;
+    g.box = c->box;
+    g.perm = s.perm;
+    g.acc = acc;
+    g.pot = pot;
+    if ((rc = launch_group_kernel(c, g))) return rc;
+    c->pairs_on_device = true;
+    return PG_OK;
+}
+
+int enqueue_run(pg_ctx *c, double *acc, double *pot)
+{
+    c->last_launches = 0;
+    if (c->have_groups) return enqueue_groups(c, acc, pot);
+    if (c->box > 0.0) return enqueue_cells(c, acc, pot);
+    Plan p;
+    plan_allpairs(c, p);
+    return enqueue_allpairs(c, p, acc, pot);
 }
 
 int run_into(pg_ctx *c, double *acc, double *pot)
 {
     int rc = check_run_state(c);
     if (rc) return rc;
-    c->last_launches = 0;
-    Plan p;
-    plan_allpairs(c, p);
-    if (!c->use_graph) return enqueue_allpairs(c, p, acc, pot);
+    if (!c->use_graph) return enqueue_run(c, acc, pot);
 
-    char key[256];
-    snprintf(key, sizeof key, "ap|%lld|%lld|%d|%d|%g|%d|%p|%p|%p|%d|%d|%d", p.ni, p.nj, c->mode,
-             c->np, c->eps, c->self, (void *)acc, (void *)pot, c->jrec.p, c->ctas_per_sm,
-             c->sort_mode, (int)c->timing);
+    char key[320];
+    snprintf(key, sizeof key, "%d|%d|%g|%lld|%lld|%d|%d|%g|%d|%p|%p|%p|%p|%d|%d|%d|%lld", (int)c->have_groups,
+             c->mode, c->box, c->ni, nj_of(c), c->np, c->ctas_per_sm, c->eps, c->self,
+             (void *)acc, (void *)pot, c->jrec.p, c->xi.p, c->sort_mode, (int)c->timing,
+             c->g_nitems, c->ngroups);
     if (!c->gexec || c->gkey != key) {
         drop_graph(c);
         // this call runs uncaptured, which also makes every allocation the
         // sequence needs; the capture below records the replay for later calls
         c->i_dirty = true;
-        if ((rc = enqueue_allpairs(c, p, acc, pot))) return rc;
+        if ((rc = enqueue_run(c, acc, pot))) return rc;
+        // a default stream cannot be captured: record on the context's own
+        // stream (capture runs nothing) and launch on the caller's stream
+        cudaStream_t run_stream = c->stream;
+        bool deflt = run_stream == nullptr || run_stream == cudaStreamLegacy ||
+                     run_stream == cudaStreamPerThread;
+        if (deflt) c->stream = c->own_stream;
         cudaGraph_t graph;
-        PG_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        rc = enqueue_allpairs(c, p, acc, pot);
-        cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            c->stream = run_stream;
+            return cuda_fail(c, e, "cudaStreamBeginCapture");
+        }
+        rc = enqueue_run(c, acc, pot);
+        e = cudaStreamEndCapture(c->stream, &graph);
+        c->stream = run_stream;
         if (rc) {
             if (e == cudaSuccess) cudaGraphDestroy(graph);
             return rc;
@@ -825,15 +1042,51 @@ int pg_get_force(pg_ctx *c, double *a, double *phi, long long ni)
 int pg_set_groups(pg_ctx *c, long long ngroups, const long long *i_off, const long long *j_off,
                   const int *jlist)
 {
-    (void)ngroups; (void)i_off; (void)j_off; (void)jlist;
     if (!c) return PG_EINVAL;
-    return fail(c, PG_ESTATE, "this build has no group path yet");
+    if (ngroups < 0 || (ngroups > 0 && (!i_off || !j_off)))
+        return fail(c, PG_EINVAL, "ngroups < 0 or NULL offsets");
+    if (ngroups == 0) return pg_clear_groups(c);
+    if (i_off[0] != 0 || j_off[0] != 0) return fail(c, PG_EINVAL, "offsets must start at 0");
+    long long pairs = 0;
+    for (long long g = 0; g < ngroups; ++g) {
+        if (i_off[g + 1] < i_off[g] || j_off[g + 1] < j_off[g])
+            return fail(c, PG_EINVAL, "offsets must be non-decreasing");
+        pairs += (i_off[g + 1] - i_off[g]) * (j_off[g + 1] - j_off[g]);
+    }
+    long long nlist = j_off[ngroups];
+    if (nlist > 0 && !jlist) return fail(c, PG_EINVAL, "jlist is NULL");
+    if (i_off[ngroups] >= (1LL << 31)) return fail(c, PG_EINVAL, "too many i-particles in groups");
+    long long maxj = -1;
+    for (long long k = 0; k < nlist; ++k) {
+        if (jlist[k] < 0 || jlist[k] >= (1 << 27))
+            return fail(c, PG_EINVAL, "jlist entries must be in [0, 2^27)");
+        maxj = std::max<long long>(maxj, jlist[k]);
+    }
+    int rc;
+    if ((rc = ensure(c, c->g_ioff, (ngroups + 1) * 8)) || (rc = ensure(c, c->g_joff, (ngroups + 1) * 8)) ||
+        (rc = ensure(c, c->g_jlist, std::max<long long>(nlist, 1) * 4)))
+        return rc;
+    PG_CUDA(c, cudaStreamSynchronize(c->stream));
+    PG_CUDA(c, cudaMemcpy(c->g_ioff.p, i_off, (ngroups + 1) * 8, cudaMemcpyHostToDevice));
+    PG_CUDA(c, cudaMemcpy(c->g_joff.p, j_off, (ngroups + 1) * 8, cudaMemcpyHostToDevice));
+    if (nlist > 0) PG_CUDA(c, cudaMemcpy(c->g_jlist.p, jlist, nlist * 4, cudaMemcpyHostToDevice));
+    c->h_ioff.assign(i_off, i_off + ngroups + 1);
+    c->h_joff.assign(j_off, j_off + ngroups + 1);
+    c->ngroups = ngroups;
+    c->g_pairs = pairs;
+    c->g_maxj = maxj;
+    c->have_groups = true;
+    drop_graph(c);
+    return upload_group_items(c);
 }
 
 int pg_clear_groups(pg_ctx *c)
 {
     if (!c) return PG_EINVAL;
     c->have_groups = false;
+    c->ngroups = 0;
+    c->h_ioff.clear();
+    c->h_joff.clear();
     drop_graph(c);
     return PG_OK;
 }
@@ -841,17 +1094,96 @@ int pg_clear_groups(pg_ctx *c)
 int pg_set_periodic(pg_ctx *c, double box)
 {
     if (!c) return PG_EINVAL;
-    if (!(box >= 0.0)) return fail(c, PG_EINVAL, "box must be >= 0");
-    if (box > 0.0) return fail(c, PG_ESTATE, "this build has no periodic path yet");
-    c->box = 0.0;
+    if (!(box >= 0.0) || !std::isfinite(box)) return fail(c, PG_EINVAL, "box must be >= 0 and finite");
+    if (box != c->box) drop_graph(c);
+    c->box = box;
     return PG_OK;
 }
 
 int pg_backward_dev(pg_ctx *c, const double *w, double *dx, double *dm, float *dv)
 {
-    (void)w; (void)dx; (void)dm; (void)dv;
     if (!c) return PG_EINVAL;
-    return fail(c, PG_ESTATE, "this build has no backward path yet");
+    if (!w || !dx || !dm) return fail(c, PG_EINVAL, "w, dx and dm must be device pointers");
+    if (c->mode == PG_TABLE && !c->have_table) return fail(c, PG_ESTATE, "table mode without a table");
+    if (!c->self || c->have_groups || c->box > 0.0 || c->ni < 0 || c->ni != nj_of(c))
+        return fail(c, PG_ESTATE, "the backward pass needs the all-pairs self mode with ni == nj");
+    bool table = c->mode == PG_TABLE;
+    long long n = c->ni;
+    if (n == 0) return PG_OK;
+    int rc;
+    const int Bi = backward_bi();
+    int ntiles = (int)((n + Bi - 1) / Bi);
+    int njsub = (int)((n + kTJ - 1) / kTJ);
+    long long W = (long long)ntiles * njsub;
+    int occ = backward_max_blocks_per_sm(table, c->ntab);
+    int per = c->ctas_per_sm > 0 ? std::min(c->ctas_per_sm, occ) : occ;
+    int grid = (int)std::min<long long>((long long)c->sms * per, W);
+    int slots = 1;
+    for (long long t = 0; t < ntiles; ++t) {
+        long long bf = stream_k_first(t * njsub, grid, W);
+        long long bl = stream_k_first((t + 1) * njsub - 1, grid, W);
+        slots = std::max<int>(slots, (int)(bl - bf + 1));
+    }
+    if ((rc = ensure(c, c->xt, n * sizeof(double4))) || (rc = ensure(c, c->ctr, ntiles * sizeof(double4))) ||
+        (rc = ensure(c, c->bw_wj, n * sizeof(double4))) || (rc = ensure(c, c->bw_wt, n * sizeof(double4))) ||
+        (rc = ensure(c, c->part, (size_t)ntiles * slots * Bi * sizeof(double4))) ||
+        (rc = ensure(c, c->bw_dv, std::max(c->ntab, 1) * sizeof(double))))
+        return rc;
+    c->last_launches = 0;
+    // tile order: the Morton order of the particles when it pays
+    c->perm = nullptr;
+    if (n >= 16384) {
+        size_t hn = sort_hist_entries(n);
+        size_t nb = (hn + 4095) / 4096 + 1;
+        if ((rc = ensure(c, c->skeys0, n * 4)) || (rc = ensure(c, c->skeys1, n * 4)) ||
+            (rc = ensure(c, c->svals0, n * 4)) || (rc = ensure(c, c->svals1, n * 4)) ||
+            (rc = ensure(c, c->shist, hn * 4)) || (rc = ensure(c, c->ssums, nb * 4)) ||
+            (rc = ensure(c, c->sbbox, 6 * 8)))
+            return rc;
+        c->sort.keys[0] = (unsigned *)c->skeys0.p;
+        c->sort.keys[1] = (unsigned *)c->skeys1.p;
+        c->sort.vals[0] = (unsigned *)c->svals0.p;
+        c->sort.vals[1] = (unsigned *)c->svals1.p;
+        c->sort.hist = (unsigned *)c->shist.p;
+        c->sort.sums = (unsigned *)c->ssums.p;
+        c->sort.bbox = (unsigned long long *)c->sbbox.p;
+        PG_CUDA(c, launch_morton_sort((const double4 *)c->jrec.p, n, c->sort, &c->perm, c->stream));
+        c->last_launches += 3 + 5 * 4;
+    }
+    c->i_dirty = true;      // the tile buffers now hold the backward's order
+    PG_CUDA(c, launch_tile_prep((const double4 *)c->jrec.p, c->perm, n, Bi, (double4 *)c->xt.p,
+                                (double4 *)c->ctr.p, c->stream));
+    PG_CUDA(c, launch_pack_w(w, c->perm, n, (double4 *)c->bw_wj.p, (double4 *)c->bw_wt.p, c->stream));
+    if (table && dv) PG_CUDA(c, cudaMemsetAsync(c->bw_dv.p, 0, c->ntab * sizeof(double), c->stream));
+    BackwardArgs a{};
+    a.xi = (const double4 *)c->xt.p;
+    a.wv = (const double4 *)c->bw_wt.p;
+    a.ctr = (const double4 *)c->ctr.p;
+    a.jx = (const double4 *)c->jrec.p;
+    a.jwv = (const double4 *)c->bw_wj.p;
+    a.n = n;
+    a.ntiles = ntiles;
+    a.njsub = njsub;
+    a.W = W;
+    a.smax_slots = slots;
+    a.eps2 = (float)(c->eps * c->eps);
+    if (table) a.tab = table_dev(c);
+    a.part = (double4 *)c->part.p;
+    a.dv = (table && dv) ? (double *)c->bw_dv.p : nullptr;
+    a.status = (int *)c->status.p;
+    if (c->timing) PG_CUDA(c, cudaEventRecord(c->tk0, c->stream));
+    PG_CUDA(c, launch_backward(a, grid, table, backward_smem(table, c->ntab), c->stream));
+    if (c->timing) PG_CUDA(c, cudaEventRecord(c->tk1, c->stream));
+    c->timed = c->timing;
+    double inv = table ? 1.0 / c->scale : 1.0;
+    PG_CUDA(c, launch_backward_combine(a.part, c->perm, n, njsub, slots, grid, W, inv, dx, dm,
+                                       c->stream));
+    if (table && dv) PG_CUDA(c, launch_dv_out((const double *)c->bw_dv.p, c->ntab, inv, dv, c->stream));
+    c->last_launches += 5;
+    c->last_pairs = n * n;
+    c->last_grid = grid;
+    c->last_slots = slots;
+    return PG_OK;
 }
 
 int pg_tune(pg_ctx *c)
@@ -871,7 +1203,9 @@ int pg_tune(pg_ctx *c)
     float best = 1e30f;
     const int nps[3] = {1, 2, 4};
     for (int np : nps) {
-        int occ = allpairs_max_blocks_per_sm(np, c->mode == PG_TABLE, c->ntab);
+        int occ = (c->have_groups || c->box > 0.0)
+                      ? groups_max_blocks_per_sm(np, c->mode == PG_TABLE, c->ntab)
+                      : allpairs_max_blocks_per_sm(np, c->mode == PG_TABLE, c->ntab);
         for (int cta = 1; cta <= occ; ++cta) {
             c->np = np;
             c->ctas_per_sm = cta;

@@ -1,0 +1,345 @@
+// pg_backward.cu -- gradients of L = sum_i w_i . a_i for the all-pairs force
+// (an extension: the paper has no backward pass). Pair terms are recomputed,
+// never stored.
+//
+// With d_kj = x_j - x_k, the pair kernel K(r^2) (Newton: (r^2+eps^2)^(-3/2);
+// table: the interpolant g(s), s = scale^2 r^2 + 2) and J(d) = K I +
+// 2 dK/d(r^2) d d^T (symmetric, even in d):
+//   dL/dx_k = sum_{j != k} J(d_kj) (m_k w_j - m_j w_k)
+//   dL/dm_k = -sum_{j != k} K(r_kj) w_j . d_kj
+//   dL/dv_b = sum_{i, j != i} m_j (w_i . d_ij) dK/dv_b   (table knot values)
+// In the table's scaled units (d~ = scale d) the position term is
+// g u + 2 G1 (d~ . u) d~ with no further factor; the mass and knot terms
+// carry one factor 1/scale, applied at the end.
+//
+// Layout as the forward all-pairs kernel: stream-K units of (i-tile,
+// j-sub-tile), i in registers (KI per thread, scalar FP32), j positions,
+// masses and weights bulk-copied to shared memory and converted to FP32
+// offsets from the FP64 tile centre, TwoSum folding per sub-tile, FP64
+// combine. The knot gradient goes through a per-CTA shared-memory histogram
+// (pairs inside the cutoff only) and one FP64 atomic per knot per CTA.
+#include "pg_device.cuh"
+
+namespace pg {
+
+constexpr int kKI = 4;                      // i per thread
+constexpr int kBiB = kNT * kKI;
+
+int backward_bi() { return kBiB; }
+
+__device__ __forceinline__ void issue_bw(const double4 *jx, const double4 *jw, long long nj, int s,
+                                         double4 *dx, double4 *dw, uint64_t *bar)
+{
+    long long j0 = (long long)s * kTJ;
+    long long nv = nj - j0;
+    if (nv > kTJ) nv = kTJ;
+    unsigned bytes = (unsigned)(nv * sizeof(double4));
+    mbar_arrive_tx(bar, 2 * bytes);
+    bulk_g2s(dx, jx + j0, bytes, bar);
+    bulk_g2s(dw, jw + j0, bytes, bar);
+}
+
+__host__ __device__ __forceinline__ long long sk_owner(long long u, long long grid, long long W)
+{
+    return ((u + 1) * grid - 1) / W;
+}
+
+template <bool TABLE>
+__global__ void __launch_bounds__(kNT) k_backward(BackwardArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    double4 *rawx = reinterpret_cast<double4 *>(smem);                 // [2][kTJ]
+    double4 *raww = rawx + 2 * kTJ;                                     // [2][kTJ]
+    float4 *cv = reinterpret_cast<float4 *>(raww + 2 * kTJ);            // [kTJ][2]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(cv + 2 * kTJ);
+    int *flag = reinterpret_cast<int *>(bar + 2);
+    float2 *tab = reinterpret_cast<float2 *>(bar + 4);
+    float *hist = reinterpret_cast<float *>(tab + (TABLE ? a.tab.n : 0));
+
+    const int tid = threadIdx.x;
+    const long long G = gridDim.x, b = blockIdx.x;
+    const long long u0 = b * a.W / G, u1 = (b + 1) * a.W / G;
+    if (u0 >= u1) return;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    if (TABLE) {
+        for (int k = tid; k < a.tab.n; k += kNT) {
+            tab[k] = a.tab.AG1[k];
+            hist[k] = 0.0f;
+        }
+    }
+    __syncthreads();
+
+    unsigned pending = 0, phase = 0;
+    if (tid == 0) {
+        issue_bw(a.jx, a.jwv, a.n, (int)(u0 % a.njsub), rawx, raww, &bar[0]);
+        pending = 1u;
+        if (u0 + 1 < u1) {
+            issue_bw(a.jx, a.jwv, a.n, (int)((u0 + 1) % a.njsub), rawx + kTJ, raww + kTJ, &bar[1]);
+            pending |= 2u;
+        }
+    }
+
+    const float c0 = TABLE ? 2.0f : a.eps2;
+    const double sc = TABLE ? a.tab.scale : 1.0;
+    float xk[kKI], yk[kKI], zk[kKI], mk[kKI], wkx[kKI], wky[kKI], wkz[kKI];
+    float gx[kKI], gy[kKI], gz[kKI], gm[kKI];
+    float hx[kKI], hy[kKI], hz[kKI], hm[kKI], lx[kKI], ly[kKI], lz[kKI], lm[kKI];
+    double cx = 0, cy = 0, cz = 0;
+    long long cur = -1;
+    bool failed = false;
+
+    auto flush = [&](long long t) {
+        long long slot = b - sk_owner(t * a.njsub, G, a.W);
+        double4 *dst = a.part + ((size_t)t * a.smax_slots + (size_t)slot) * kBiB;
+#pragma unroll
+        for (int q = 0; q < kKI; ++q) {
+            int li = q * kNT + tid;
+            if (t * kBiB + li < a.n)
+                dst[li] = make_double4((double)hx[q] + lx[q], (double)hy[q] + ly[q],
+                                       (double)hz[q] + lz[q], (double)hm[q] + lm[q]);
+        }
+    };
+
+    for (long long u = u0; u < u1; ++u) {
+        const long long t = u / a.njsub;
+        const int s = (int)(u % a.njsub);
+        const int buf = (int)((u - u0) & 1);
+        if (t != cur) {
+            if (cur >= 0) flush(cur);
+            cur = t;
+            double4 c = a.ctr[t];
+            cx = c.x; cy = c.y; cz = c.z;
+#pragma unroll
+            for (int q = 0; q < kKI; ++q) {
+                long long i = t * kBiB + q * kNT + tid;
+                if (i < a.n) {
+                    double4 v = a.xi[i], w = a.wv[i];
+                    xk[q] = (float)((v.x - cx) * sc);
+                    yk[q] = (float)((v.y - cy) * sc);
+                    zk[q] = (float)((v.z - cz) * sc);
+                    mk[q] = (float)v.w;
+                    wkx[q] = (float)w.x; wky[q] = (float)w.y; wkz[q] = (float)w.z;
+                } else {
+                    xk[q] = yk[q] = zk[q] = mk[q] = wkx[q] = wky[q] = wkz[q] = 0.0f;
+                }
+                hx[q] = hy[q] = hz[q] = hm[q] = lx[q] = ly[q] = lz[q] = lm[q] = 0.0f;
+            }
+        }
+        if (tid == 0) {
+            bool ok = mbar_wait(&bar[buf], (phase >> buf) & 1u, kWaitLimitNs);
+            if (ok) pending &= ~(1u << buf);
+            *flag = ok ? 1 : 0;
+        }
+        __syncthreads();
+        if (*flag == 0) { failed = true; break; }
+        phase ^= 1u << buf;
+        {
+            const long long j0 = (long long)s * kTJ;
+            long long nv = a.n - j0;
+            if (nv > kTJ) nv = kTJ;
+            for (int e = tid; e < kTJ; e += kNT) {
+                float4 p, w;
+                if (e < nv) {
+                    double4 v = rawx[buf * kTJ + e], ww = raww[buf * kTJ + e];
+                    p = make_float4((float)((v.x - cx) * sc), (float)((v.y - cy) * sc),
+                                    (float)((v.z - cz) * sc), (float)v.w);
+                    w = make_float4((float)ww.x, (float)ww.y, (float)ww.z, 0.0f);
+                } else {
+                    p = make_float4(1.0e4f, 1.0e4f, 1.0e4f, 0.0f);
+                    w = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                }
+                cv[2 * e] = p;
+                cv[2 * e + 1] = w;
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && u + 2 < u1) {
+            fence_proxy_async();
+            issue_bw(a.jx, a.jwv, a.n, (int)((u + 2) % a.njsub), rawx + buf * kTJ, raww + buf * kTJ,
+                     &bar[buf]);
+            pending |= 1u << buf;
+        }
+#pragma unroll
+        for (int q = 0; q < kKI; ++q) gx[q] = gy[q] = gz[q] = gm[q] = 0.0f;
+#pragma unroll 2
+        for (int e = 0; e < kTJ; ++e) {
+            const float4 p = cv[2 * e], w = cv[2 * e + 1];
+#pragma unroll
+            for (int q = 0; q < kKI; ++q) {
+                const float dx = p.x - xk[q], dy = p.y - yk[q], dz = p.z - zk[q];
+                float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, c0)));
+                // u = m_k w_j - m_j w_k with separate roundings: exactly 0 for j = k
+                const float ux = __fsub_rn(__fmul_rn(mk[q], w.x), __fmul_rn(p.w, wkx[q]));
+                const float uy = __fsub_rn(__fmul_rn(mk[q], w.y), __fmul_rn(p.w, wky[q]));
+                const float uz = __fsub_rn(__fmul_rn(mk[q], w.z), __fmul_rn(p.w, wkz[q]));
+                const float du = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
+                const float wd = fmaf(dx, w.x, fmaf(dy, w.y, dz * w.z));
+                float K, c2;
+                if (!TABLE) {
+                    float q1 = rsq(r2);
+                    q1 = r2 > 0.0f ? q1 : 0.0f;
+                    const float qq = q1 * q1;
+                    K = q1 * qq;
+                    c2 = -3.0f * K * qq * du;
+                } else {
+                    const float sv = fminf(r2, a.tab.s_max);
+                    const unsigned bits = __float_as_uint(sv);
+                    const unsigned idx = (bits >> a.tab.shift) - a.tab.base;
+                    const float2 ag = tab[idx];
+                    K = fmaf(sv, ag.y, ag.x);
+                    c2 = 2.0f * ag.y * du;
+                    if (sv < a.tab.s_max) {
+                        // hat weights of the bin's two knots; the knot spacing
+                        // is 2^(exponent of s_k - F)
+                        const unsigned kb = bits & ~((1u << a.tab.shift) - 1u);
+                        const float sk = __uint_as_float(kb);
+                        const float ds = __uint_as_float((kb & 0x7f800000u) -
+                                                         ((unsigned)(23 - a.tab.shift) << 23));
+                        const float tt = (sv - sk) / ds;
+                        const float pw = p.w * fmaf(dx, wkx[q], fmaf(dy, wky[q], dz * wkz[q]));
+                        atomicAdd(&hist[idx], pw * (1.0f - tt));
+                        atomicAdd(&hist[idx + 1], pw * tt);
+                    }
+                }
+                gx[q] = fmaf(K, ux, fmaf(c2, dx, gx[q]));
+                gy[q] = fmaf(K, uy, fmaf(c2, dy, gy[q]));
+                gz[q] = fmaf(K, uz, fmaf(c2, dz, gz[q]));
+                gm[q] = fmaf(-K, wd, gm[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kKI; ++q) {
+            float sx, ex;
+            two_sum(hx[q], gx[q], sx, ex); hx[q] = sx; lx[q] += ex;
+            two_sum(hy[q], gy[q], sx, ex); hy[q] = sx; ly[q] += ex;
+            two_sum(hz[q], gz[q], sx, ex); hz[q] = sx; lz[q] += ex;
+            two_sum(hm[q], gm[q], sx, ex); hm[q] = sx; lm[q] += ex;
+        }
+    }
+    if (failed) {
+        if (tid == 0) {
+            report(a.status, kStatusTimeout, 3);
+            for (int k = 0; k < 2; ++k)
+                if (pending & (1u << k)) mbar_wait(&bar[k], (phase >> k) & 1u, kWaitLimitNs / 4);
+        }
+        return;
+    }
+    if (cur >= 0) flush(cur);
+    if (TABLE && a.dv) {
+        __syncthreads();
+        for (int k = tid; k < a.tab.n; k += kNT)
+            if (hist[k] != 0.0f) atomicAdd(&a.dv[k], (double)hist[k]);
+    }
+}
+
+size_t backward_smem(bool table, int ntab)
+{
+    size_t s = 4 * kTJ * sizeof(double4) + 2 * kTJ * sizeof(float4) + 4 * sizeof(uint64_t);
+    if (table) s += (size_t)ntab * (sizeof(float2) + sizeof(float));
+    return s;
+}
+
+template <bool TABLE>
+static cudaError_t configure_b()
+{
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_backward<TABLE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)backward_smem(TABLE, 1 << 13));
+    done = e == cudaSuccess;
+    return e;
+}
+
+int backward_max_blocks_per_sm(bool table, int ntab)
+{
+    size_t smem = backward_smem(table, ntab);
+    cudaError_t e = table ? configure_b<true>() : configure_b<false>();
+    if (e != cudaSuccess) return 1;
+    int nb = 0;
+    e = table ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_backward<true>, kNT, smem)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_backward<false>, kNT, smem);
+    return (e == cudaSuccess && nb > 0) ? nb : 1;
+}
+
+cudaError_t launch_backward(const BackwardArgs &a, int grid, bool table, size_t smem,
+                            cudaStream_t st)
+{
+    if (grid <= 0) return cudaSuccess;
+    cudaError_t e = table ? configure_b<true>() : configure_b<false>();
+    if (e != cudaSuccess) return e;
+    if (table) k_backward<true><<<grid, kNT, smem, st>>>(a);
+    else k_backward<false><<<grid, kNT, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// gather loss weights (FP64 [n][3]) into (a) record order and (b) tile order
+__global__ void k_pack_w(const double *__restrict__ w, const unsigned *__restrict__ perm, long long n,
+                         double4 *__restrict__ wj, double4 *__restrict__ wt)
+{
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    wj[p] = make_double4(w[3 * p], w[3 * p + 1], w[3 * p + 2], 0.0);
+    long long k = perm ? (long long)perm[p] : p;
+    wt[p] = make_double4(w[3 * k], w[3 * k + 1], w[3 * k + 2], 0.0);
+}
+
+cudaError_t launch_pack_w(const double *w, const unsigned *perm, long long n, double4 *wj,
+                          double4 *wt, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_pack_w<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(w, perm, n, wj, wt);
+    return cudaGetLastError();
+}
+
+__global__ void k_bw_combine(const double4 *__restrict__ part, const unsigned *__restrict__ perm,
+                             long long n, int njsub, int slots, int grid, long long W, double mscale,
+                             double *__restrict__ dx, double *__restrict__ dm)
+{
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    long long t = p / kBiB;
+    int li = (int)(p % kBiB);
+    double gx = 0, gy = 0, gz = 0, gm = 0;
+    if (njsub > 0) {
+        long long bf = sk_owner(t * njsub, grid, W), bl = sk_owner((t + 1) * njsub - 1, grid, W);
+        for (long long s = 0; s <= bl - bf; ++s) {
+            double4 v = part[((size_t)t * slots + (size_t)s) * kBiB + li];
+            gx += v.x; gy += v.y; gz += v.z; gm += v.w;
+        }
+    }
+    long long k = perm ? (long long)perm[p] : p;
+    dx[3 * k] = gx;
+    dx[3 * k + 1] = gy;
+    dx[3 * k + 2] = gz;
+    dm[k] = gm * mscale;
+}
+
+cudaError_t launch_backward_combine(const double4 *part, const unsigned *perm, long long n, int njsub,
+                                    int slots, int grid, long long W, double mscale, double *dx,
+                                    double *dm, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_bw_combine<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, perm, n, njsub, slots,
+                                                              grid > 0 ? grid : 1, W > 0 ? W : 1,
+                                                              mscale, dx, dm);
+    return cudaGetLastError();
+}
+
+__global__ void k_dv_out(const double *__restrict__ acc, int n, double scale, float *__restrict__ dv)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) dv[k] = (float)(acc[k] * scale);
+}
+
+cudaError_t launch_dv_out(const double *acc, int n, double scale, float *dv, cudaStream_t st)
+{
+    k_dv_out<<<(n + 255) / 256, 256, 0, st>>>(acc, n, scale, dv);
+    return cudaGetLastError();
+}
+
+}  // namespace pg

@@ -77,7 +77,8 @@ struct GroupArgs {
     const int *jlist;      // j indices; periodic: low 27 bits index, high 5 bits shift code
     const GroupItem *items;
     const double4 *gctr;   // FP64 centre of each group
-    int nitems;
+    int nitems;            // item count, or -1: read *nitems_dev
+    const unsigned *nitems_dev;
     int *queue;            // work counter (reset to 0 before each launch)
     long long nj;          // number of j records (bounds check)
     float eps2;
@@ -91,20 +92,19 @@ struct GroupArgs {
 
 // backward (all-pairs, self mode)
 struct BackwardArgs {
-    const double4 *xi;     // positions in tile order (x, y, z, m)
-    const double4 *wv;     // loss weights in tile order (wx, wy, wz, -)
+    const double4 *xi;     // i positions + mass (x, y, z, m) in tile order
+    const double4 *wv;     // i loss weights (wx, wy, wz, -) in tile order
     const double4 *ctr;    // tile centres
-    const float4 *jw;      // unused slot for future layouts
+    const double4 *jx;     // j positions + mass in record order
+    const double4 *jwv;    // j loss weights in record order
     long long n;
     int ntiles, njsub;
     long long W;
     int smax_slots;
     float eps2;
     TableDev tab;
-    const double4 *jx;     // j positions+mass (x, y, z, m) in tile order
-    const double4 *jwv;    // j weights (wx, wy, wz, -) in tile order
     double4 *part;         // partials [ntiles][slots][Bi] {gx, gy, gz, gm}
-    double *dv;            // table gradient accumulators (FP64, 2^(E+F))
+    double *dv;            // knot-gradient accumulators (FP64, 2^(E+F)), may be null
     int *status;
 };
 
@@ -149,36 +149,48 @@ cudaError_t launch_table_prep(const float *G0, const float *G1, float2 *AG1, int
 cudaError_t launch_table_from_values(const float *v, float *G0, float *G1, int E, int F,
                                      cudaStream_t st);
 
-cudaError_t launch_groups(const GroupArgs &g, int grid, bool table, size_t smem, cudaStream_t st);
+cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, size_t smem,
+                          cudaStream_t st);
 size_t groups_smem(bool table, int ntab);
-int groups_max_blocks_per_sm(bool table, int ntab);
+int groups_bi(int np);
+int groups_max_blocks_per_sm(int np, bool table, int ntab);
+cudaError_t launch_group_ctr(const double4 *xi, const long long *i_off, long long ngroups,
+                             double4 *ctr, cudaStream_t st);
 
-// periodic cell list: bins, sorts and emits per-cell j-lists with shift codes
-struct CellList {
-    int nc;                // cells per axis
-    long long ncell;
-    unsigned *cell_of;     // per particle (input order)
-    unsigned *perm;        // sorted position -> input index
-    unsigned *start;       // ncell + 1
-    long long *j_off;      // ncell + 1
-    int *jlist;
-    long long jlist_cap;
-    double4 *xs;           // particles in cell order (x, y, z, m)
-    double4 *gctr;         // cell centres
-    GroupItem *items;
-    int nitems;
-    unsigned *cost_keys;
+// periodic cell list: particles binned and sorted by cell, one group per
+// cell whose j-list is the 27 neighbour cells with image shift codes
+struct CellScratch {
+    double4 *wrapped;      // n: positions wrapped into the box (input order)
+    double4 *xs;           // n: wrapped positions + mass in cell order
+    unsigned *perm;        // n: cell order -> input index (own copy)
+    unsigned *start;       // ncell + 1: first particle of each cell
+    unsigned *jcount;      // ncell
+    unsigned *icount;      // ncell
+    unsigned *joff32;      // ncell + 1
+    long long *joff;       // ncell + 1
+    unsigned *ioff;        // ncell + 1 (ioff[ncell] = number of items)
+    int *jlist;            // 27 n entries
+    GroupItem *items_raw;  // item_cap
+    GroupItem *items;      // item_cap, longest first
+    double4 *ctr;          // ncell cell centres
+    long long item_cap;
+    unsigned long long *pairs;   // evaluated pairs of the build (device)
 };
-cudaError_t launch_cell_bin(const double4 *jrec, long long n, double box, int nc,
-                            unsigned *cell_of, unsigned *idx, cudaStream_t st);
+cudaError_t launch_cell_build(const double4 *jrec, long long n, double box, int nc, int Bi,
+                              CellScratch &s, SortScratch &sort, cudaStream_t st);
+cudaError_t launch_excl_scan(unsigned *a, long long n, unsigned *sums, cudaStream_t st);
 
 // backward
 cudaError_t launch_backward(const BackwardArgs &a, int grid, bool table, size_t smem,
                             cudaStream_t st);
 size_t backward_smem(bool table, int ntab);
 int backward_bi();
+int backward_max_blocks_per_sm(bool table, int ntab);
+cudaError_t launch_pack_w(const double *w, const unsigned *perm, long long n, double4 *wj,
+                          double4 *wt, cudaStream_t st);
 cudaError_t launch_backward_combine(const double4 *part, const unsigned *perm, long long n,
-                                    int Bi, int njsub, int slots, int grid, long long W,
+                                    int njsub, int slots, int grid, long long W, double mscale,
                                     double *dx, double *dm, cudaStream_t st);
+cudaError_t launch_dv_out(const double *acc, int n, double scale, float *dv, cudaStream_t st);
 
 }  // namespace pg

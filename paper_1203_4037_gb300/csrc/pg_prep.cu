@@ -257,6 +257,11 @@ static cudaError_t excl_scan(unsigned *a, long long n, unsigned *sums, cudaStrea
     return cudaGetLastError();
 }
 
+cudaError_t launch_excl_scan(unsigned *a, long long n, unsigned *sums, cudaStream_t st)
+{
+    return excl_scan(a, n, sums, st);
+}
+
 cudaError_t launch_radix_sort(unsigned *keys, unsigned *vals, long long n, int key_bits,
                               SortScratch &s, unsigned **keys_out, unsigned **vals_out,
                               cudaStream_t st)

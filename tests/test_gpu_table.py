@@ -75,11 +75,12 @@ def test_allpairs_table_semantics(pg, orc, E, F, n, shape):
     scale = np.linalg.norm(ao, axis=1)
     rel = np.maximum(err - amb, 0) / scale
     assert_parity(rel, what="a vs table semantics")
-    # against the closed form: only the table's own error remains
-    ac, ambc = orc.shape_forces(x, x, m, orc.SHAPE_GAUSS_SPLIT, par, r_cut, skip=np.arange(n),
-                                window=1e-6)
-    relc = np.maximum(np.linalg.norm(a - ac, axis=1) - ambc, 0) / np.linalg.norm(ac, axis=1)
-    assert np.max(relc) <= 1e-3
+    # against the closed form only the table's own error remains: at most
+    # 1e-3 of each pair term, so per particle at most 1e-3 of sum_j |term|
+    ac, ambc, absum = orc.shape_forces(x, x, m, orc.SHAPE_GAUSS_SPLIT, par, r_cut,
+                                       skip=np.arange(n), window=1e-6, with_absum=True)
+    err = np.maximum(np.linalg.norm(a - ac, axis=1) - ambc, 0)
+    assert np.all(err <= 1e-3 * absum)
 
 
 def test_section_4_2_run_on_gpu(pg, orc):

@@ -215,9 +215,11 @@ def test_closed_form_cutoff_and_periodic_image(orc):
     assert 0.02 > r_cut  # beyond the cutoff: nothing
     assert np.all(a == 0)
     xj = np.array([[0.995, 0.5, 0.5]])
-    a, _ = orc.shape_forces(xi, xj, [1.0], orc.SHAPE_GAUSS_SPLIT, par, r_cut, box=1.0)
+    a, _, absum = orc.shape_forces(xi, xj, [1.0], orc.SHAPE_GAUSS_SPLIT, par, r_cut, box=1.0,
+                                   with_absum=True)
     g = orc.shape(orc.SHAPE_GAUSS_SPLIT, par, 0.015)
     assert a[0, 0] == pytest.approx(-0.015 * g, rel=1e-12)
+    assert absum[0] == pytest.approx(0.015 * g, rel=1e-12)
     # the table path takes the same image
     E, F = 4, 8
     G0, G1 = orc.table_build(E, F, r_cut, orc.SHAPE_GAUSS_SPLIT, par)
