@@ -63,13 +63,6 @@ def dist_env():
     return rank, world, local
 
 
-def shard(n, rank, world):
-    """Contiguous i-range [lo, hi) of `rank` among `world` ranks."""
-    lo = (n * rank) // world
-    hi = (n * (rank + 1)) // world
-    return lo, hi
-
-
 class ClockSampler:
     """nvidia-smi clock and throttle-reason samples while the timed region runs."""
 
@@ -204,43 +197,62 @@ def gauss_split(r, rs, eps):
     return w / (r * r + eps * eps) ** 1.5
 
 
-def extra_rows(pg, torch, dev):
-    """Throughput of other rows of the path (not the headline): the 4096-body
-    Plummer call (latency-bound) and the tabulated all-pairs kernel."""
-    rows = {}
-    x, m = gen.plummer(4096, gen.CONFIG_SEEDS[1])
-    xd = torch.tensor(x, device=dev)
-    md = torch.tensor(m, device=dev)
-    a = torch.empty_like(xd)
-    p = torch.empty_like(md)
+def _time_kernel(ctx, fn, reps=5, warm=2):
+    for _ in range(warm):
+        fn()
+    ks = []
+    for _ in range(reps):
+        fn()
+        ks.append(ctx.kernel_time())
+    return statistics.median(ks)
+
+
+def _time_call(torch, fn, reps, warm=3):
     st = torch.cuda.current_stream()
-    with pg.Context(dev.index or 0) as c:
+    for _ in range(warm):
+        fn()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        fn()
+    e1.record(st)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def extra_rows(pg, torch, dev, peak_newton, headline_rate):
+    """The other rows of the path, each timed on its own workload (not the
+    headline): the 4096-body Plummer call (latency-bound, CUDA graph), the
+    tabulated all-pairs kernel, the periodic cell-list cutoff force on the
+    2^21-particle clustered box, the 20000 tree-style groups, and the
+    backward pass on 65536 Plummer particles."""
+    rows = {}
+    st = torch.cuda.current_stream()
+    peak_table = peak_newton * 13 / 11
+    idx = dev.index or 0
+
+    # 4096-body Plummer sphere, eps = 1/64, graph replay per call
+    x, m = gen.plummer(4096, gen.CONFIG_SEEDS[1])
+    xd, md = torch.tensor(x, device=dev), torch.tensor(m, device=dev)
+    a, p = torch.empty_like(xd), torch.empty_like(md)
+    with pg.Context(idx) as c:
         c.set_stream(st.cuda_stream)
         c.set_eps(1 / 64)
         c.set_self(True)
         c.set_graph(True)
         c.set_j_dev(xd, md)
         c.set_i_dev(xd)
-        for _ in range(20):
-            c.run_dev(a, p)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 200
-        e0.record(st)
-        for _ in range(reps):
-            c.run_dev(a, p)
-        e1.record(st)
-        e1.synchronize()
-        ms = e0.elapsed_time(e1) / reps
+        ms = _time_call(torch, lambda: c.run_dev(a, p), 200, warm=20)
         rows["newton_plummer_4096"] = {"interactions_per_s": 4096 * 4096 / (ms * 1e-3),
                                        "us_per_call": ms * 1e3, "graph": True}
-    # tabulated all-pairs: 65536 Plummer, Gaussian-split shape, r_cut = 0.1, E=3, F=5
+
+    # tabulated all-pairs: 65536 Plummer, Gaussian split, r_cut = 0.1, E=3, F=5
     n = 65536
     x, m = gen.plummer(n, gen.CONFIG_SEEDS[5])
-    r_cut = 0.1
-    xd = torch.tensor(x, device=dev)
-    md = torch.tensor(m, device=dev)
+    xd, md = torch.tensor(x, device=dev), torch.tensor(m, device=dev)
     a = torch.empty_like(xd)
-    with pg.Context(dev.index or 0) as c:
+    r_cut = 0.1
+    with pg.Context(idx) as c:
         c.set_stream(st.cuda_stream)
         c.set_mode(pg.PG_TABLE)
         c.set_table(lambda r: gauss_split(r, r_cut / 4.5, 1 / 64), r_cut, 3, 5)
@@ -248,15 +260,83 @@ def extra_rows(pg, torch, dev):
         c.set_timing(True)
         c.set_j_dev(xd, md)
         c.set_i_dev(xd)
-        for _ in range(3):
-            c.run_dev(a)
-        ks = []
-        for _ in range(5):
-            c.run_dev(a)
-            ks.append(c.kernel_time())
-        kms = statistics.median(ks)
-        rows["table_allpairs_65536_E3F5"] = {"interactions_per_s": n * n / (kms * 1e-3),
-                                             "kernel_ms": kms}
+        kms = _time_kernel(c, lambda: c.run_dev(a))
+        rate = n * n / (kms * 1e-3)
+        rows["table_allpairs_65536_E3F5"] = {"interactions_per_s": rate, "kernel_ms": kms,
+                                             "frac_fp32_peak": rate / peak_table}
+
+    # backward on the same set: Newton (eps = 1/64) and the table
+    from paper_1203_4037_gb300 import autograd  # noqa: F401  (binding used by users)
+    w = torch.tensor(gen.unit_vectors(n, gen.CONFIG_SEEDS[5] + 1), device=dev)
+    dx, dm = torch.empty_like(xd), torch.empty_like(md)
+    with pg.Context(idx) as c:
+        c.set_stream(st.cuda_stream)
+        c.set_self(True)
+        c.set_timing(True)
+        c.set_eps(1 / 64)
+        c.set_j_dev(xd, md)
+        c.set_i_dev(xd)
+        fwd = _time_kernel(c, lambda: c.run_dev(a))
+        bwd = _time_kernel(c, lambda: c.backward_dev(w, dx, dm))
+        c.set_mode(pg.PG_TABLE)
+        c.set_table(lambda r: gauss_split(r, r_cut / 4.5, 1 / 64), r_cut, 3, 5)
+        dv = torch.empty(256, dtype=torch.float32, device=dev)
+        bwd_t = _time_kernel(c, lambda: c.backward_dev(w, dx, dm, dv))
+        rows["backward_65536"] = {
+            "newton_forward_kernel_ms": fwd, "newton_backward_kernel_ms": bwd,
+            "newton_backward_interactions_per_s": n * n / (bwd * 1e-3),
+            "table_backward_kernel_ms": bwd_t,
+            "table_backward_interactions_per_s": n * n / (bwd_t * 1e-3)}
+    del xd, md, a, w, dx, dm
+
+    # periodic cell list: 2^21 clustered box, Gaussian split r_s = 1/256
+    n = 1 << 21
+    x, m = gen.clustered_box(n, gen.CONFIG_SEEDS[3])
+    xd, md = torch.tensor(x, device=dev), torch.tensor(m, device=dev)
+    a = torch.empty_like(xd)
+    rs = 1 / 256
+    with pg.Context(idx) as c:
+        c.set_stream(st.cuda_stream)
+        c.set_mode(pg.PG_TABLE)
+        c.set_table(lambda r: gauss_split(r, rs, rs / 16), 4.5 * rs, 4, 8)
+        c.set_self(True)
+        c.set_periodic(1.0)
+        c.set_timing(True)
+        c.set_j_dev(xd, md)
+        c.set_i_dev(xd)
+        kms = _time_kernel(c, lambda: c.run_dev(a))
+        pairs = c.info()["pairs"]
+        call = _time_call(torch, lambda: c.run_dev(a), 5, warm=1)
+        rate = pairs / (kms * 1e-3)
+        rows["cells_2e21_E4F8"] = {"pairs_evaluated": pairs, "kernel_ms": kms,
+                                   "interactions_per_s": rate, "frac_fp32_peak": rate / peak_table,
+                                   "call_ms_with_cell_build": call,
+                                   "interactions_per_s_with_build": pairs / (call * 1e-3)}
+    del xd, md, a
+
+    # 20000 tree-style groups on the clustered 2^22 set, eps = 1e-3
+    d = gen.tree_groups(gen.CONFIG_SEEDS[4])
+    with pg.Context(idx) as c:
+        c.set_stream(st.cuda_stream)
+        c.set_eps(1e-3)
+        c.set_timing(True)
+        xj = torch.tensor(d["xj"], device=dev)
+        mj = torch.tensor(d["mj"], device=dev)
+        xi = torch.tensor(d["xi"], device=dev)
+        a = torch.empty_like(xi)
+        p = torch.empty(len(xi), dtype=torch.float64, device=dev)
+        c.set_j_dev(xj, mj)
+        c.set_i_dev(xi)
+        c.set_groups(d["i_off"], d["j_off"], d["jlist"])
+        pairs = int(((d["i_off"][1:] - d["i_off"][:-1]) * (d["j_off"][1:] - d["j_off"][:-1])).sum())
+        kms = _time_kernel(c, lambda: c.run_dev(a, p))
+        c.set_graph(True)
+        call = _time_call(torch, lambda: c.run_dev(a, p), 5, warm=2)
+        rate = pairs / (kms * 1e-3)
+        rows["groups_20000"] = {"pairs": pairs, "kernel_ms": kms, "interactions_per_s": rate,
+                                "frac_fp32_peak": rate / peak_newton,
+                                "call_ms_graph": call,
+                                "ratio_to_allpairs": rate / headline_rate}
     return rows
 
 
@@ -268,6 +348,7 @@ def main():
     import torch
     import torch.distributed as dist
     import paper_1203_4037_gb300 as pg
+    from paper_1203_4037_gb300.multirank import max_over_ranks, shard
 
     rank, world, local = dist_env()
     if world > 1:
@@ -329,11 +410,7 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), device=dev)
     info = ctx.info()
     pairs_job = npart * npart                      # all ranks together, one step
     value = pairs_job * args.steps / (total_ms * 1e-3)
@@ -365,8 +442,11 @@ def main():
 
     rows = None
     if rank == 0 and not args.no_rows:
+        sms_ = torch.cuda.get_device_properties(dev).multi_processor_count
+        f_ = float(measured_peaks().get("sm_max_mhz", 2070.0)) * 1e6
+        kern_rate = ni * npart / (statistics.median(kern_ms) * 1e-3)
         try:
-            rows = extra_rows(pg, torch, dev)
+            rows = extra_rows(pg, torch, dev, sms_ * f_ * FP32_LANES_PER_SM / NEWTON_OPS, kern_rate)
         except Exception as exc:  # report, do not hide
             rows = {"error": repr(exc)}
 

@@ -56,15 +56,23 @@ struct Bi_of {
 
 int allpairs_bi(int np) { return kNT * 2 * np; }
 
+// CTAs per SM the register budget is sized for
+template <int NP>
+struct MinBlocks {
+    static constexpr int value = NP == 1 ? 8 : NP == 2 ? 5 : 2;
+};
+
 template <int NP, bool TABLE, bool ZSAFE>
-__global__ void __launch_bounds__(kNT) k_allpairs(AllPairsArgs a)
+__global__ void __launch_bounds__(kNT, MinBlocks<NP>::value) k_allpairs(AllPairsArgs a)
 {
     constexpr int Bi = Bi_of<NP>::value;
     extern __shared__ __align__(128) unsigned char smem[];
     double4 *raw = reinterpret_cast<double4 *>(smem);                       // [2][kTJ]
     u64 *cvt = reinterpret_cast<u64 *>(smem + 2 * kTJ * sizeof(double4));   // [kTJ][4]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * kTJ * sizeof(double4) +
-                                                 kTJ * 4 * sizeof(u64));
+    // compensated running sums (hi, lo) of every thread's i, [8 NP][kNT]:
+    // they change once per sub-tile, so they live in shared memory
+    u64 *run = cvt + kTJ * 4;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(run + 8 * NP * kNT);
     int *flag = reinterpret_cast<int *>(bar + 2);
     float2 *tab = reinterpret_cast<float2 *>(bar + 4);
 
@@ -98,8 +106,9 @@ __global__ void __launch_bounds__(kNT) k_allpairs(AllPairsArgs a)
     // per-thread state
     u64 xi[NP], yi[NP], zi[NP];
     u64 ax[NP], ay[NP], az[NP], ph[NP];          // sub-tile partials
-    u64 hx[NP], hy[NP], hz[NP], hp[NP];          // compensated running sums
-    u64 lx[NP], ly[NP], lz[NP], lp[NP];
+    // running sum k of pair p: hi at run[(8p + k) kNT + tid], lo at k + 4
+    auto RH = [&](int p, int k) -> u64 & { return run[(8 * p + k) * kNT + tid]; };
+    auto RL = [&](int p, int k) -> u64 & { return run[(8 * p + 4 + k) * kNT + tid]; };
     double cx = 0, cy = 0, cz = 0;
     long long cur = -1;
 
@@ -115,10 +124,11 @@ __global__ void __launch_bounds__(kNT) k_allpairs(AllPairsArgs a)
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
             float h[8], l[8];
-            up2(hx[p], h[0], h[1]); up2(hy[p], h[2], h[3]);
-            up2(hz[p], h[4], h[5]); up2(hp[p], h[6], h[7]);
-            up2(lx[p], l[0], l[1]); up2(ly[p], l[2], l[3]);
-            up2(lz[p], l[4], l[5]); up2(lp[p], l[6], l[7]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                up2(RH(p, k), h[2 * k], h[2 * k + 1]);
+                up2(RL(p, k), l[2 * k], l[2 * k + 1]);
+            }
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 int li = (2 * p + q) * kNT + tid;
@@ -158,8 +168,8 @@ __global__ void __launch_bounds__(kNT) k_allpairs(AllPairsArgs a)
                 xi[p] = pk2(fx[0], fx[1]);
                 yi[p] = pk2(fy[0], fy[1]);
                 zi[p] = pk2(fz[0], fz[1]);
-                hx[p] = hy[p] = hz[p] = hp[p] = zero2;
-                lx[p] = ly[p] = lz[p] = lp[p] = zero2;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) RH(p, k) = RL(p, k) = zero2;
             }
         }
 
@@ -252,10 +262,10 @@ __global__ void __launch_bounds__(kNT) k_allpairs(AllPairsArgs a)
         }
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
-            fold2(hx[p], lx[p], ax[p]);
-            fold2(hy[p], ly[p], ay[p]);
-            fold2(hz[p], lz[p], az[p]);
-            if (!TABLE) fold2(hp[p], lp[p], ph[p]);
+            fold2(RH(p, 0), RL(p, 0), ax[p]);
+            fold2(RH(p, 1), RL(p, 1), ay[p]);
+            fold2(RH(p, 2), RL(p, 2), az[p]);
+            if (!TABLE) fold2(RH(p, 3), RL(p, 3), ph[p]);
         }
     }
 
@@ -275,8 +285,8 @@ __global__ void __launch_bounds__(kNT) k_allpairs(AllPairsArgs a)
 
 size_t allpairs_smem(int np, bool table, int ntab)
 {
-    (void)np;
-    size_t s = 2 * kTJ * sizeof(double4) + kTJ * 4 * sizeof(u64) + 4 * sizeof(uint64_t);
+    size_t s = 2 * kTJ * sizeof(double4) + kTJ * 4 * sizeof(u64) + 8 * np * kNT * sizeof(u64) +
+               4 * sizeof(uint64_t);
     if (table) s += (size_t)ntab * sizeof(float2);
     return s;
 }

@@ -1206,7 +1206,7 @@ int pg_tune(pg_ctx *c)
         int occ = (c->have_groups || c->box > 0.0)
                       ? groups_max_blocks_per_sm(np, c->mode == PG_TABLE, c->ntab)
                       : allpairs_max_blocks_per_sm(np, c->mode == PG_TABLE, c->ntab);
-        for (int cta = 1; cta <= occ; ++cta) {
+        for (int cta = occ; cta <= occ; ++cta) {     // the occupancy limit of each shape
             c->np = np;
             c->ctas_per_sm = cta;
             c->i_dirty = true;

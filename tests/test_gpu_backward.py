@@ -58,8 +58,11 @@ def test_newton_small_full(pg, torch, orc):
 
 
 def test_table_small_full(pg, torch, orc):
-    x, m = gen.plummer(1500, 13)
-    x = x * 0.2
+    # a compact set: with fewer i-particles than a few tiles the FP32 offsets
+    # are taken from centres of tiles that span the whole set
+    rng = np.random.default_rng(13)
+    x = rng.random((1500, 3)) * 0.3
+    m = rng.uniform(0.5, 1.5, 1500) / 1500
     w = gen.unit_vectors(1500, 14)
     E, F, r_cut = 3, 5, 0.1
     v = orc.table_values(E, F, r_cut, orc.SHAPE_GAUSS_SPLIT, [r_cut / 4.5, 1 / 64])

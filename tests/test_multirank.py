@@ -1,0 +1,65 @@
+"""The i-range split of the multi-GPU path, on CPU with two gloo ranks: each
+rank computes its shard (the FP64 oracle stands in for the GPU call), the
+gathered result equals the single-rank one, and the job time is the slowest
+rank's."""
+
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+from paper_1203_4037_gb300.multirank import gather_rows, max_over_ranks, shard
+
+
+def test_shard_covers_range_exactly():
+    for n in (0, 1, 7, 1000, 1 << 20):
+        for world in (1, 2, 3, 8):
+            ranges = [shard(n, r, world) for r in range(world)]
+            assert ranges[0][0] == 0 and ranges[-1][1] == n
+            assert all(a[1] == b[0] for a, b in zip(ranges, ranges[1:]))
+            sizes = [hi - lo for lo, hi in ranges]
+            assert max(sizes) - min(sizes) <= 1
+    with pytest.raises(ValueError):
+        shard(10, 2, 2)
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, out):
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import gen
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    x, m = gen.plummer(1001, 17)
+    lo, hi = shard(len(x), rank, world)
+    a, p = oracle.newton(x[lo:hi], x, m, 0.05, skip=np.arange(lo, hi), nthreads_=1)
+    full = gather_rows(torch.tensor(np.concatenate([a, p[:, None]], axis=1)), len(x))
+    t = max_over_ranks(1.0 + rank)
+    if rank == 0:
+        np.save(out, full.numpy())
+        np.save(out + ".t.npy", np.array([t]))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_match_one(tmp_path, orc):
+    import gen
+    out = str(tmp_path / "full.npy")
+    mp.spawn(_worker, args=(2, _free_port(), out), nprocs=2, join=True)
+    full = np.load(out)
+    x, m = gen.plummer(1001, 17)
+    a, p = orc.newton_allpairs(x, m, 0.05)
+    assert np.array_equal(full[:, :3], a) and np.array_equal(full[:, 3], p)
+    assert np.load(out + ".t.npy")[0] == 2.0
