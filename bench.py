@@ -53,6 +53,10 @@ def parse():
                     help="particle count (default: the 2^20 workload; smaller for profiling)")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only: no e2e, extra rows or CPU baseline")
+    ap.add_argument("--workload", default="newton",
+                    choices=["newton", "table", "cells", "groups", "backward"],
+                    help="newton: the headline; the others time one row of the path alone "
+                         "(for profiling) and print its measurements")
     return ap.parse_args()
 
 
@@ -340,10 +344,85 @@ def extra_rows(pg, torch, dev, peak_newton, headline_rate):
     return rows
 
 
+def run_row(args):
+    """Time one non-headline row alone (profiling aid): prints one JSON line."""
+    import torch
+    import paper_1203_4037_gb300 as pg
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    torch.cuda.set_stream(torch.cuda.Stream(device=dev))
+    pg.build()
+    st = torch.cuda.current_stream()
+    out = {"workload": args.workload}
+    if args.workload in ("table", "backward"):
+        n = min(args.n, 65536) if args.n != N_PART else 65536
+        x, m = gen.plummer(n, gen.CONFIG_SEEDS[5])
+        xd, md = torch.tensor(x, device=dev), torch.tensor(m, device=dev)
+        a = torch.empty_like(xd)
+        r_cut = 0.1
+        with pg.Context(0) as c:
+            c.set_stream(st.cuda_stream)
+            c.set_self(True)
+            c.set_timing(True)
+            c.set_j_dev(xd, md)
+            c.set_i_dev(xd)
+            if args.workload == "table":
+                c.set_mode(pg.PG_TABLE)
+                c.set_table(lambda r: gauss_split(r, r_cut / 4.5, 1 / 64), r_cut, 3, 5)
+                kms = _time_kernel(c, lambda: c.run_dev(a), reps=args.steps, warm=args.warmup)
+            else:
+                c.set_eps(1 / 64)
+                w = torch.tensor(gen.unit_vectors(n, gen.CONFIG_SEEDS[5] + 1), device=dev)
+                dx, dm = torch.empty_like(xd), torch.empty_like(md)
+                kms = _time_kernel(c, lambda: c.backward_dev(w, dx, dm), reps=args.steps,
+                                   warm=args.warmup)
+        out.update(n=n, kernel_ms=kms, interactions_per_s=n * n / (kms * 1e-3))
+    elif args.workload == "cells":
+        n = args.n if args.n != N_PART else 1 << 21
+        x, m = gen.clustered_box(n, gen.CONFIG_SEEDS[3])
+        xd, md = torch.tensor(x, device=dev), torch.tensor(m, device=dev)
+        a = torch.empty_like(xd)
+        rs = 1 / 256
+        with pg.Context(0) as c:
+            c.set_stream(st.cuda_stream)
+            c.set_mode(pg.PG_TABLE)
+            c.set_table(lambda r: gauss_split(r, rs, rs / 16), 4.5 * rs, 4, 8)
+            c.set_self(True)
+            c.set_periodic(1.0)
+            c.set_timing(True)
+            c.set_j_dev(xd, md)
+            c.set_i_dev(xd)
+            kms = _time_kernel(c, lambda: c.run_dev(a), reps=args.steps, warm=args.warmup)
+            pairs = c.info()["pairs"]
+        out.update(n=n, pairs=pairs, kernel_ms=kms, interactions_per_s=pairs / (kms * 1e-3))
+    else:
+        ng = 20000 if args.n == N_PART else max(100, args.n // 200)
+        npart = 1 << 22 if args.n == N_PART else args.n
+        d = gen.tree_groups(gen.CONFIG_SEEDS[4], n=npart, ngroups=ng,
+                            n_monopoles=max(1024, npart // 4))
+        with pg.Context(0) as c:
+            c.set_stream(st.cuda_stream)
+            c.set_eps(1e-3)
+            c.set_timing(True)
+            xj, mj = torch.tensor(d["xj"], device=dev), torch.tensor(d["mj"], device=dev)
+            xi = torch.tensor(d["xi"], device=dev)
+            a = torch.empty_like(xi)
+            c.set_j_dev(xj, mj)
+            c.set_i_dev(xi)
+            c.set_groups(d["i_off"], d["j_off"], d["jlist"])
+            kms = _time_kernel(c, lambda: c.run_dev(a), reps=args.steps, warm=args.warmup)
+            pairs = c.info()["pairs"]
+        out.update(groups=ng, pairs=pairs, kernel_ms=kms, interactions_per_s=pairs / (kms * 1e-3))
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload != "newton":
+        run_row(args)
         return
     import torch
     import torch.distributed as dist
