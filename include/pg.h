@@ -198,6 +198,28 @@ int pg_kernel_time(pg_ctx *ctx, double *ms);
  * force kernel, out[4] partial slots per tile. Returns how many were written. */
 int pg_info(pg_ctx *ctx, long long *out, int n);
 
+/* Largest particle count pg_newton_allpairs_noalloc accepts. */
+#define PG_NOALLOC_MAX_N 16384
+
+/* All-pairs Newton forces (as pg_set_self(ctx, 1) + pg_run_dev) for callers
+ * that cannot allocate device memory at call time: a host application whose
+ * memory pool has reserved the whole GPU (cudaMalloc would fail), or a
+ * time-critical loop that must not stall on the device synchronisation that
+ * cudaMalloc and cudaFree can cause. The paper has no counterpart; this is a
+ * convenience of this library. The call uses no context and allocates nothing: its scratch is a
+ * fixed array of about 3.6 MiB that every GPU loading the library holds
+ * until the process exits.
+ *   x: device double[n][3], m: device double[n], a: device double[n][3] out,
+ *   phi: device double[n] out or NULL; eps >= 0; cuda_stream: cudaStream_t
+ *   (NULL: the legacy default stream); the current device is used.
+ * Returns PG_EINVAL when n > PG_NOALLOC_MAX_N (or other bad arguments),
+ * PG_ECUDA when a launch fails; asynchronous otherwise. The first call on a
+ * device looks up the scratch array's device address: make it before any
+ * stream capture. All calls share the one array, so calls that overlap on
+ * the GPU race; order them on one stream. */
+int pg_newton_allpairs_noalloc(const double *x, const double *m, long long n, double eps,
+                               double *a, double *phi, void *cuda_stream);
+
 /* Text of the last error of this context ("" if none); NULL ctx: last
  * error of pg_create. Valid until the next call on the context. */
 const char *pg_last_error(pg_ctx *ctx);

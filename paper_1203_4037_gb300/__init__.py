@@ -66,6 +66,7 @@ SIGNATURES = {
     "pg_set_timing": (_I, [_P, _I]),
     "pg_kernel_time": (_I, [_P, C.POINTER(_D)]),
     "pg_info": (_I, [_P, C.POINTER(_LL), _I]),
+    "pg_newton_allpairs_noalloc": (_I, [_P, _P, _LL, _D, _P, _P, _P]),
     "pg_last_error": (C.c_char_p, [_P]),
     "pg_version": (C.c_char_p, []),
 }
@@ -270,6 +271,22 @@ def pg_info(ctx):
     n = lib().pg_info(ctx, out, 5)
     keys = ["pairs", "launches", "i_per_thread", "grid", "slots"]
     return dict(zip(keys[:n], list(out)[:n]))
+
+
+PG_NOALLOC_MAX_N = 16384
+
+
+def pg_newton_allpairs_noalloc(x, m, n, eps, a, phi=None, stream=None):
+    """All-pairs Newton through the entry point that allocates nothing (for
+    callers that cannot allocate device memory when they need forces).
+    x, m, a, phi: CUDA tensors (or device addresses); n <= PG_NOALLOC_MAX_N."""
+    rc = lib().pg_newton_allpairs_noalloc(_ptr(x), _ptr(m), int(n), float(eps), _ptr(a), _ptr(phi),
+                                          _ptr(stream))
+    if rc != PG_OK:
+        why = (f"n = {n} exceeds PG_NOALLOC_MAX_N = {PG_NOALLOC_MAX_N}" if n > PG_NOALLOC_MAX_N
+               else "bad argument or CUDA launch failure")
+        raise PGError(rc, why)
+    return rc
 
 
 def pg_last_error(ctx):
