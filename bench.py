@@ -53,6 +53,8 @@ def parse():
                     help="particle count (default: the 2^20 workload; smaller for profiling)")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only: no e2e, extra rows or CPU baseline")
+    ap.add_argument("--shape", default=None,
+                    help="np,packed launch shape of the force kernel (default: the library's)")
     ap.add_argument("--workload", default="newton",
                     choices=["newton", "table", "cells", "groups", "backward"],
                     help="newton: the headline; the others time one row of the path alone "
@@ -461,6 +463,9 @@ def main():
     # out through the self mode only when the ranges coincide (world == 1)
     ctx.set_self(world == 1)
     ctx.set_i_dev(xi)
+    if args.shape:
+        np_, packed = (int(v) for v in args.shape.split(","))
+        ctx.set_shape(np_, 0, packed)
 
     def step():
         ctx.set_i_dev(xi)            # i staging every step (positions change in a run)
@@ -544,7 +549,8 @@ def main():
     achieved = pairs_rank / (kms * 1e-3)
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_int / 1e9,
             "unit": "Ginteractions/s", "frac": achieved / peak_int, "traffic": None,
-            "kernel": "k_allpairs<2,false,false>", "kernel_ms": kms,
+            "kernel": f"k_allpairs<np={info['i_per_thread'] // 2}, packed={info['packed']}>",
+            "kernel_ms": kms,
             "peak_basis": f"{sms} SMs x {f_max / 1e6:.0f} MHz x 128 FP32 lanes / 13 ops per "
                           "interaction (FP32 pipe; MUFU allows 16 per SM-clock)"}
     if clk.get("sm_mhz"):

@@ -182,8 +182,9 @@ int pg_set_graph(pg_ctx *ctx, int on);
 int pg_tune(pg_ctx *ctx);
 
 /* Launch shape override: i per thread = 2*np (np in {1, 2, 4}; 0 = keep),
- * CTAs per SM (0 = occupancy limit). */
-int pg_set_shape(pg_ctx *ctx, int np, int ctas_per_sm);
+ * CTAs per SM (0 = occupancy limit), packed = 1: pair arithmetic in packed
+ * FP32x2 instructions, 0: scalar FP32 (same roundings), -1 = keep. */
+int pg_set_shape(pg_ctx *ctx, int np, int ctas_per_sm, int packed);
 
 /* on != 0: bracket the force kernel of every later run with CUDA events on
  * the context's stream, so that pg_kernel_time can report its duration. */
@@ -195,7 +196,8 @@ int pg_kernel_time(pg_ctx *ctx, double *ms);
 
 /* Counters: out[0] pair evaluations enqueued by the last run, out[1] kernel
  * launches of the last run, out[2] i per thread, out[3] grid size of the
- * force kernel, out[4] partial slots per tile. Returns how many were written. */
+ * force kernel, out[4] partial slots per tile, out[5] 1 if the pair arithmetic
+ * is packed FP32x2. Returns how many were written. */
 int pg_info(pg_ctx *ctx, long long *out, int n);
 
 /* Largest particle count pg_newton_allpairs_noalloc accepts. */

@@ -62,7 +62,7 @@ SIGNATURES = {
     "pg_sync": (_I, [_P]),
     "pg_set_graph": (_I, [_P, _I]),
     "pg_tune": (_I, [_P]),
-    "pg_set_shape": (_I, [_P, _I, _I]),
+    "pg_set_shape": (_I, [_P, _I, _I, _I]),
     "pg_set_timing": (_I, [_P, _I]),
     "pg_kernel_time": (_I, [_P, C.POINTER(_D)]),
     "pg_info": (_I, [_P, C.POINTER(_LL), _I]),
@@ -252,8 +252,8 @@ def pg_tune(ctx):
     return _check(ctx, lib().pg_tune(ctx))
 
 
-def pg_set_shape(ctx, np_, ctas_per_sm=0):
-    return _check(ctx, lib().pg_set_shape(ctx, int(np_), int(ctas_per_sm)))
+def pg_set_shape(ctx, np_, ctas_per_sm=0, packed=-1):
+    return _check(ctx, lib().pg_set_shape(ctx, int(np_), int(ctas_per_sm), int(packed)))
 
 
 def pg_set_timing(ctx, on):
@@ -267,9 +267,9 @@ def pg_kernel_time(ctx):
 
 
 def pg_info(ctx):
-    out = (_LL * 5)()
-    n = lib().pg_info(ctx, out, 5)
-    keys = ["pairs", "launches", "i_per_thread", "grid", "slots"]
+    out = (_LL * 6)()
+    n = lib().pg_info(ctx, out, 6)
+    keys = ["pairs", "launches", "i_per_thread", "grid", "slots", "packed"]
     return dict(zip(keys[:n], list(out)[:n]))
 
 
@@ -378,8 +378,8 @@ class Context:
     def set_graph(self, on=True):
         pg_set_graph(self.h, on)
 
-    def set_shape(self, np_, ctas_per_sm=0):
-        pg_set_shape(self.h, np_, ctas_per_sm)
+    def set_shape(self, np_, ctas_per_sm=0, packed=-1):
+        pg_set_shape(self.h, np_, ctas_per_sm, packed)
 
     def set_timing(self, on=True):
         pg_set_timing(self.h, on)

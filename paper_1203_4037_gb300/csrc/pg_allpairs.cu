@@ -56,15 +56,50 @@ struct Bi_of {
 
 int allpairs_bi(int np) { return kNT * 2 * np; }
 
+// Pair arithmetic on two FP32 lanes: packed f32x2 instructions (PK) or two
+// scalar instructions per operation (the same roundings either way).
+template <bool PK>
+struct Lanes;
+
+template <>
+struct Lanes<true> {
+    static __device__ __forceinline__ u64 fma(u64 a, u64 b, u64 c) { return f2fma(a, b, c); }
+    static __device__ __forceinline__ u64 sub(u64 a, u64 b) { return f2sub(a, b); }
+    static __device__ __forceinline__ u64 mul(u64 a, u64 b) { return f2mul(a, b); }
+};
+
+template <>
+struct Lanes<false> {
+    static __device__ __forceinline__ u64 fma(u64 a, u64 b, u64 c)
+    {
+        float a0, a1, b0, b1, c0, c1;
+        up2(a, a0, a1); up2(b, b0, b1); up2(c, c0, c1);
+        return pk2(__fmaf_rn(a0, b0, c0), __fmaf_rn(a1, b1, c1));
+    }
+    static __device__ __forceinline__ u64 sub(u64 a, u64 b)
+    {
+        float a0, a1, b0, b1;
+        up2(a, a0, a1); up2(b, b0, b1);
+        return pk2(__fsub_rn(a0, b0), __fsub_rn(a1, b1));
+    }
+    static __device__ __forceinline__ u64 mul(u64 a, u64 b)
+    {
+        float a0, a1, b0, b1;
+        up2(a, a0, a1); up2(b, b0, b1);
+        return pk2(__fmul_rn(a0, b0), __fmul_rn(a1, b1));
+    }
+};
+
 // CTAs per SM the register budget is sized for
 template <int NP>
 struct MinBlocks {
     static constexpr int value = NP == 1 ? 8 : NP == 2 ? 5 : 2;
 };
 
-template <int NP, bool TABLE, bool ZSAFE>
+template <int NP, bool TABLE, bool ZSAFE, bool PK>
 __global__ void __launch_bounds__(kNT, MinBlocks<NP>::value) k_allpairs(AllPairsArgs a)
 {
+    using V = Lanes<PK>;
     constexpr int Bi = Bi_of<NP>::value;
     extern __shared__ __align__(128) unsigned char smem[];
     double4 *raw = reinterpret_cast<double4 *>(smem);                       // [2][kTJ]
@@ -225,12 +260,12 @@ __global__ void __launch_bounds__(kNT, MinBlocks<NP>::value) k_allpairs(AllPairs
             const ulonglong2 zm = reinterpret_cast<const ulonglong2 *>(cvt)[2 * e + 1];
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
-                const u64 dx = f2sub(xy.x, xi[p]);
-                const u64 dy = f2sub(xy.y, yi[p]);
-                const u64 dz = f2sub(zm.x, zi[p]);
-                u64 r2 = f2fma(dx, dx, c0v);
-                r2 = f2fma(dy, dy, r2);
-                r2 = f2fma(dz, dz, r2);
+                const u64 dx = V::sub(xy.x, xi[p]);
+                const u64 dy = V::sub(xy.y, yi[p]);
+                const u64 dz = V::sub(zm.x, zi[p]);
+                u64 r2 = V::fma(dx, dx, c0v);
+                r2 = V::fma(dy, dy, r2);
+                r2 = V::fma(dz, dz, r2);
                 float ra, rb;
                 up2(r2, ra, rb);
                 if (!TABLE) {
@@ -240,23 +275,23 @@ __global__ void __launch_bounds__(kNT, MinBlocks<NP>::value) k_allpairs(AllPairs
                         qb = rb > 0.0f ? qb : 0.0f;
                     }
                     const u64 q = pk2(qa, qb);
-                    const u64 mq = f2mul(zm.y, q);
-                    const u64 q2 = f2mul(q, q);
-                    const u64 mq3 = f2mul(mq, q2);
-                    ph[p] = f2sub(ph[p], mq);
-                    ax[p] = f2fma(mq3, dx, ax[p]);
-                    ay[p] = f2fma(mq3, dy, ay[p]);
-                    az[p] = f2fma(mq3, dz, az[p]);
+                    const u64 mq = V::mul(zm.y, q);
+                    const u64 q2 = V::mul(q, q);
+                    const u64 mq3 = V::mul(mq, q2);
+                    ph[p] = V::sub(ph[p], mq);
+                    ax[p] = V::fma(mq3, dx, ax[p]);
+                    ay[p] = V::fma(mq3, dy, ay[p]);
+                    az[p] = V::fma(mq3, dz, az[p]);
                 } else {
                     ra = fminf(ra, a.tab.s_max);
                     rb = fminf(rb, a.tab.s_max);
                     const float2 ta = tab[(__float_as_uint(ra) >> a.tab.shift) - a.tab.base];
                     const float2 tb = tab[(__float_as_uint(rb) >> a.tab.shift) - a.tab.base];
-                    const u64 g = f2fma(pk2(ra, rb), pk2(ta.y, tb.y), pk2(ta.x, tb.x));
-                    const u64 mg = f2mul(zm.y, g);
-                    ax[p] = f2fma(mg, dx, ax[p]);
-                    ay[p] = f2fma(mg, dy, ay[p]);
-                    az[p] = f2fma(mg, dz, az[p]);
+                    const u64 g = V::fma(pk2(ra, rb), pk2(ta.y, tb.y), pk2(ta.x, tb.x));
+                    const u64 mg = V::mul(zm.y, g);
+                    ax[p] = V::fma(mg, dx, ax[p]);
+                    ay[p] = V::fma(mg, dy, ay[p]);
+                    az[p] = V::fma(mg, dz, az[p]);
                 }
             }
         }
@@ -292,62 +327,71 @@ size_t allpairs_smem(int np, bool table, int ntab)
 }
 
 // raise the kernel's dynamic shared memory limit once (outside any capture)
-template <int NP, bool TABLE, bool ZSAFE>
+template <int NP, bool TABLE, bool ZSAFE, bool PK>
 static cudaError_t configure_one()
 {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_allpairs<NP, TABLE, ZSAFE>,
+    cudaError_t e = cudaFuncSetAttribute(k_allpairs<NP, TABLE, ZSAFE, PK>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)allpairs_smem(NP, TABLE, 1 << 13));
     done = e == cudaSuccess;
     return e;
 }
 
-template <int NP, bool TABLE, bool ZSAFE>
+template <int NP, bool TABLE, bool ZSAFE, bool PK>
 static cudaError_t launch_one(const AllPairsArgs &a, int grid, size_t smem, cudaStream_t st)
 {
-    cudaError_t e = configure_one<NP, TABLE, ZSAFE>();
+    cudaError_t e = configure_one<NP, TABLE, ZSAFE, PK>();
     if (e != cudaSuccess) return e;
-    k_allpairs<NP, TABLE, ZSAFE><<<grid, kNT, smem, st>>>(a);
+    k_allpairs<NP, TABLE, ZSAFE, PK><<<grid, kNT, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int NP, bool TABLE, bool ZSAFE>
+template <int NP, bool TABLE, bool PK>
 static int occupancy_one(size_t smem)
 {
-    auto k = k_allpairs<NP, TABLE, ZSAFE>;
-    if (configure_one<NP, TABLE, ZSAFE>() != cudaSuccess) return 1;
+    auto k = k_allpairs<NP, TABLE, false, PK>;
+    if (configure_one<NP, TABLE, false, PK>() != cudaSuccess) return 1;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kNT, smem) != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
 }
 
-int allpairs_max_blocks_per_sm(int np, bool table, int ntab)
+template <int NP>
+static int occupancy_np(bool table, bool packed, size_t smem)
+{
+    if (table) return packed ? occupancy_one<NP, true, true>(smem) : occupancy_one<NP, true, false>(smem);
+    return packed ? occupancy_one<NP, false, true>(smem) : occupancy_one<NP, false, false>(smem);
+}
+
+int allpairs_max_blocks_per_sm(int np, bool table, int ntab, bool packed)
 {
     size_t smem = allpairs_smem(np, table, ntab);
-    if (table) return np == 1 ? occupancy_one<1, true, false>(smem)
-                     : np == 4 ? occupancy_one<4, true, false>(smem)
-                               : occupancy_one<2, true, false>(smem);
-    return np == 1 ? occupancy_one<1, false, false>(smem)
-         : np == 4 ? occupancy_one<4, false, false>(smem)
-                   : occupancy_one<2, false, false>(smem);
+    return np == 1 ? occupancy_np<1>(table, packed, smem)
+         : np == 4 ? occupancy_np<4>(table, packed, smem)
+                   : occupancy_np<2>(table, packed, smem);
+}
+
+template <int NP, bool PK>
+static cudaError_t launch_np(const AllPairsArgs &a, int grid, bool table, bool zsafe, size_t smem,
+                             cudaStream_t st)
+{
+    if (table) return launch_one<NP, true, false, PK>(a, grid, smem, st);
+    if (zsafe) return launch_one<NP, false, true, PK>(a, grid, smem, st);
+    return launch_one<NP, false, false, PK>(a, grid, smem, st);
 }
 
 cudaError_t launch_allpairs(const AllPairsArgs &a, int grid, int np, bool table, bool zsafe,
-                            size_t smem, cudaStream_t st)
+                            bool packed, size_t smem, cudaStream_t st)
 {
     if (grid <= 0) return cudaSuccess;
-#define PG_AP(NP_)                                                                       \
-    if (np == NP_) {                                                                     \
-        if (table) return launch_one<NP_, true, false>(a, grid, smem, st);               \
-        if (zsafe) return launch_one<NP_, false, true>(a, grid, smem, st);               \
-        return launch_one<NP_, false, false>(a, grid, smem, st);                         \
-    }
-    PG_AP(1)
-    PG_AP(2)
-    PG_AP(4)
-#undef PG_AP
+    if (np == 1) return packed ? launch_np<1, true>(a, grid, table, zsafe, smem, st)
+                               : launch_np<1, false>(a, grid, table, zsafe, smem, st);
+    if (np == 2) return packed ? launch_np<2, true>(a, grid, table, zsafe, smem, st)
+                               : launch_np<2, false>(a, grid, table, zsafe, smem, st);
+    if (np == 4) return packed ? launch_np<4, true>(a, grid, table, zsafe, smem, st)
+                               : launch_np<4, false>(a, grid, table, zsafe, smem, st);
     return cudaErrorInvalidValue;
 }
 

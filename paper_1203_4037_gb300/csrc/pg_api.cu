@@ -84,7 +84,7 @@ struct pg_ctx {
 
     // periodic cell list
     CellScratch cells{};
-    DevBuf c_wrapped, c_xs, c_perm, c_start, c_jcount, c_icount, c_joff32, c_joff, c_ioff,
+    DevBuf c_wrapped, c_xs, c_xo, c_perm, c_start, c_jcount, c_icount, c_joff32, c_joff, c_ioff,
         c_jlist, c_items_raw, c_items, c_ctr, c_pairs;
     bool pairs_on_device = false;
 
@@ -94,6 +94,7 @@ struct pg_ctx {
     // launch shape
     int np = 2;
     int ctas_per_sm = 0;
+    int packed = 1;             // f32x2 pair arithmetic (0: scalar FP32)
 
     // graph
     bool use_graph = false;
@@ -337,7 +338,7 @@ void pg_destroy(pg_ctx *c)
                       &c->skeys0, &c->skeys1, &c->svals0, &c->svals1, &c->shist, &c->ssums,
                       &c->sbbox, &c->acc, &c->pot, &c->part, &c->status, &c->g_ioff,
                       &c->g_joff, &c->g_jlist, &c->g_items, &c->g_ctr, &c->g_queue,
-                      &c->c_wrapped, &c->c_xs, &c->c_perm, &c->c_start, &c->c_jcount,
+                      &c->c_wrapped, &c->c_xs, &c->c_xo, &c->c_perm, &c->c_start, &c->c_jcount,
                       &c->c_icount, &c->c_joff32, &c->c_joff, &c->c_ioff, &c->c_jlist,
                       &c->c_items_raw, &c->c_items, &c->c_ctr, &c->c_pairs, &c->bw_wj,
                       &c->bw_wt, &c->bw_dv};
@@ -571,13 +572,15 @@ int pg_set_graph(pg_ctx *c, int on)
     return PG_OK;
 }
 
-int pg_set_shape(pg_ctx *c, int np, int ctas_per_sm)
+int pg_set_shape(pg_ctx *c, int np, int ctas_per_sm, int packed)
 {
     if (!c) return PG_EINVAL;
     if (np != 0 && np != 1 && np != 2 && np != 4) return fail(c, PG_EINVAL, "np must be 0, 1, 2 or 4");
     if (ctas_per_sm < 0) return fail(c, PG_EINVAL, "ctas_per_sm must be >= 0");
+    if (packed < -1 || packed > 1) return fail(c, PG_EINVAL, "packed must be -1, 0 or 1");
     if (np) c->np = np;
     c->ctas_per_sm = ctas_per_sm;
+    if (packed >= 0) c->packed = packed;
     c->i_dirty = true;
     drop_graph(c);
     return PG_OK;
@@ -593,8 +596,9 @@ int pg_info(pg_ctx *c, long long *out, int n)
         c->last_pairs = (long long)v;
         c->pairs_on_device = false;
     }
-    long long v[5] = {c->last_pairs, c->last_launches, 2LL * c->np, c->last_grid, c->last_slots};
-    int k = std::min(n, 5);
+    long long v[6] = {c->last_pairs, c->last_launches, 2LL * c->np, c->last_grid, c->last_slots,
+                      (long long)c->packed};
+    int k = std::min(n, 6);
     for (int i = 0; i < k; ++i) out[i] = v[i];
     return k;
 }
@@ -650,7 +654,7 @@ int plan_allpairs(pg_ctx *c, Plan &p)
     p.ntiles = (int)((p.ni + p.Bi - 1) / p.Bi);
     p.njsub = (int)((p.nj + kTJ - 1) / kTJ);
     p.W = (long long)p.ntiles * p.njsub;
-    int occ = allpairs_max_blocks_per_sm(c->np, c->mode == PG_TABLE, c->ntab);
+    int occ = allpairs_max_blocks_per_sm(c->np, c->mode == PG_TABLE, c->ntab, c->packed != 0);
     int per = c->ctas_per_sm > 0 ? std::min(c->ctas_per_sm, occ) : occ;
     long long g = (long long)c->sms * per;
     p.grid = (int)std::max<long long>(0, std::min<long long>(g, p.W));
@@ -726,7 +730,7 @@ int enqueue_allpairs(pg_ctx *c, const Plan &p, double *acc, double *pot)
     size_t smem = allpairs_smem(c->np, table, c->ntab);
     if (p.grid > 0) {
         if (c->timing) PG_CUDA(c, cudaEventRecord(c->tk0, c->stream));
-        PG_CUDA(c, launch_allpairs(a, p.grid, c->np, table, zsafe, smem, c->stream));
+        PG_CUDA(c, launch_allpairs(a, p.grid, c->np, table, zsafe, c->packed != 0, smem, c->stream));
         if (c->timing) PG_CUDA(c, cudaEventRecord(c->tk1, c->stream));
         c->timed = c->timing;
         c->last_launches += 1;
@@ -822,15 +826,16 @@ GroupArgs group_args(pg_ctx *c)
     return g;
 }
 
-int launch_group_kernel(pg_ctx *c, const GroupArgs &g)
+int launch_group_kernel(pg_ctx *c, const GroupArgs &g, bool cell)
 {
     bool table = c->mode == PG_TABLE;
-    int occ = groups_max_blocks_per_sm(c->np, table, c->ntab);
+    int occ = groups_max_blocks_per_sm(c->np, table, c->ntab, cell);
     int per = c->ctas_per_sm > 0 ? std::min(c->ctas_per_sm, occ) : occ;
     int grid = c->sms * per;
     PG_CUDA(c, cudaMemsetAsync(c->g_queue.p, 0, sizeof(int), c->stream));
     if (c->timing) PG_CUDA(c, cudaEventRecord(c->tk0, c->stream));
-    PG_CUDA(c, launch_groups(g, grid, c->np, table, groups_smem(table, c->ntab), c->stream));
+    PG_CUDA(c, launch_groups(g, grid, c->np, table, cell, groups_smem(c->np, table, c->ntab),
+                             c->stream));
     if (c->timing) PG_CUDA(c, cudaEventRecord(c->tk1, c->stream));
     c->timed = c->timing;
     c->last_grid = grid;
@@ -861,11 +866,10 @@ int enqueue_groups(pg_ctx *c, double *acc, double *pot)
     g.gctr = (const double4 *)c->g_ctr.p;
     g.nitems = c->g_nitems;
     g.nj = nj_of(c);
-    g.box = 0.0;
     g.perm = nullptr;
     g.acc = acc;
     g.pot = pot;
-    if ((rc = launch_group_kernel(c, g))) return rc;
+    if ((rc = launch_group_kernel(c, g, false))) return rc;
     c->last_pairs = c->g_pairs;
     return PG_OK;
 }
@@ -884,6 +888,7 @@ int enqueue_cells(pg_ctx *c, double *acc, double *pot)
     size_t hn = sort_hist_entries(sn);
     size_t nb = (std::max<size_t>(hn, ncell + 1) + 4095) / 4096 + 1;
     if ((rc = ensure(c, c->c_wrapped, n * 32)) || (rc = ensure(c, c->c_xs, n * 32)) ||
+        (rc = ensure(c, c->c_xo, n * 16)) ||
         (rc = ensure(c, c->c_perm, n * 4)) || (rc = ensure(c, c->c_start, (ncell + 1) * 4)) ||
         (rc = ensure(c, c->c_jcount, ncell * 4)) || (rc = ensure(c, c->c_icount, ncell * 4)) ||
         (rc = ensure(c, c->c_joff32, (ncell + 1) * 4)) || (rc = ensure(c, c->c_joff, (ncell + 1) * 8)) ||
@@ -899,6 +904,7 @@ int enqueue_cells(pg_ctx *c, double *acc, double *pot)
     if (27 * n >= (1LL << 31)) return fail(c, PG_EINVAL, "too many particles for the cell lists");
     s.wrapped = (double4 *)c->c_wrapped.p;
     s.xs = (double4 *)c->c_xs.p;
+    s.xo = (float4 *)c->c_xo.p;
     s.perm = (unsigned *)c->c_perm.p;
     s.start = (unsigned *)c->c_start.p;
     s.jcount = (unsigned *)c->c_jcount.p;
@@ -918,8 +924,8 @@ int enqueue_cells(pg_ctx *c, double *acc, double *pot)
     c->sort.vals[1] = (unsigned *)c->svals1.p;
     c->sort.hist = (unsigned *)c->shist.p;
     c->sort.sums = (unsigned *)c->ssums.p;
-    PG_CUDA(c, launch_cell_build((const double4 *)c->jrec.p, n, c->box, nc, Bi, s, c->sort,
-                                 c->stream));
+    PG_CUDA(c, launch_cell_build((const double4 *)c->jrec.p, n, c->box, nc, Bi, c->scale, s,
+                                 c->sort, c->stream));
     c->last_launches += 30;
     GroupArgs g = group_args(c);
     g.xi = s.xs;
@@ -931,11 +937,12 @@ int enqueue_cells(pg_ctx *c, double *acc, double *pot)
     g.nitems = -1;
     g.nitems_dev = s.ioff + ncell;
     g.nj = n;
-    g.box = c->box;
+    g.xo = s.xo;
+    g.cell_h = (float)(c->box / nc * c->scale);
     g.perm = s.perm;
     g.acc = acc;
     g.pot = pot;
-    if ((rc = launch_group_kernel(c, g))) return rc;
+    if ((rc = launch_group_kernel(c, g, true))) return rc;
     c->pairs_on_device = true;
     return PG_OK;
 }
@@ -957,8 +964,9 @@ int run_into(pg_ctx *c, double *acc, double *pot)
     if (!c->use_graph) return enqueue_run(c, acc, pot);
 
     char key[320];
-    snprintf(key, sizeof key, "%d|%d|%g|%lld|%lld|%d|%d|%g|%d|%p|%p|%p|%p|%d|%d|%d|%lld", (int)c->have_groups,
-             c->mode, c->box, c->ni, nj_of(c), c->np, c->ctas_per_sm, c->eps, c->self,
+    snprintf(key, sizeof key, "%d|%d|%g|%lld|%lld|%d|%d|%d|%g|%d|%p|%p|%p|%p|%d|%d|%d|%lld",
+             (int)c->have_groups, c->mode, c->box, c->ni, nj_of(c), c->np, c->packed,
+             c->ctas_per_sm, c->eps, c->self,
              (void *)acc, (void *)pot, c->jrec.p, c->xi.p, c->sort_mode, (int)c->timing,
              c->g_nitems, c->ngroups);
     if (!c->gexec || c->gkey != key) {
@@ -1199,15 +1207,18 @@ int pg_tune(pg_ctx *c)
     cudaEvent_t e0, e1;
     PG_CUDA(c, cudaEventCreate(&e0));
     PG_CUDA(c, cudaEventCreate(&e1));
-    int best_np = c->np, best_cta = c->ctas_per_sm;
+    int best_np = c->np, best_cta = c->ctas_per_sm, best_pk = c->packed;
     float best = 1e30f;
     const int nps[3] = {1, 2, 4};
+    bool groups_path = c->have_groups || c->box > 0.0;
+    for (int pk = groups_path ? 1 : 0; pk <= 1 && !rc; ++pk)
     for (int np : nps) {
-        int occ = (c->have_groups || c->box > 0.0)
-                      ? groups_max_blocks_per_sm(np, c->mode == PG_TABLE, c->ntab)
-                      : allpairs_max_blocks_per_sm(np, c->mode == PG_TABLE, c->ntab);
+        int occ = groups_path
+                      ? groups_max_blocks_per_sm(np, c->mode == PG_TABLE, c->ntab, !c->have_groups)
+                      : allpairs_max_blocks_per_sm(np, c->mode == PG_TABLE, c->ntab, pk != 0);
         for (int cta = occ; cta <= occ; ++cta) {     // the occupancy limit of each shape
             c->np = np;
+            c->packed = pk;
             c->ctas_per_sm = cta;
             c->i_dirty = true;
             if ((rc = run_into(c, (double *)c->acc.p, (double *)c->pot.p))) break;
@@ -1221,6 +1232,7 @@ int pg_tune(pg_ctx *c)
                 best = ms;
                 best_np = np;
                 best_cta = cta;
+                best_pk = pk;
             }
         }
         if (rc) break;
@@ -1229,6 +1241,7 @@ int pg_tune(pg_ctx *c)
     cudaEventDestroy(e1);
     c->np = best_np;
     c->ctas_per_sm = best_cta;
+    c->packed = best_pk;
     c->i_dirty = true;
     c->use_graph = graph;
     drop_graph(c);

@@ -17,22 +17,22 @@ namespace pg {
 constexpr int kTJG = 512;          // j entries staged per step
 constexpr int kPerThread = kTJG / kNT;
 
-__device__ __forceinline__ void shift_of(int code, double box, double &sx, double &sy, double &sz)
-{
-    // code = 9 (dx+1) + 3 (dy+1) + (dz+1), dx, dy, dz in {-1, 0, 1}
-    int dx = code / 9 - 1, dy = (code / 3) % 3 - 1, dz = code % 3 - 1;
-    sx = dx * box;
-    sy = dy * box;
-    sz = dz * box;
-}
-
-template <int NP, bool TABLE>
+// Records come in two forms.
+//  CELL = false: FP64 (x, y, z, m) of any particle; the group's FP64 centre is
+//    subtracted in FP64 and the difference rounded once to FP32.
+//  CELL = true: the periodic cell list's FP32 record (o, m), o = the
+//    particle's offset from its cell's corner in scaled units; a j-list entry
+//    carries the direction (dx, dy, dz) in {-1, 0, 1}^3 from the i-cell to the
+//    j-cell, so the j offset in the i-cell's frame is o_j + (dx, dy, dz) h~ --
+//    FP32 only, with the periodic wrap already in the direction.
+template <int NP, bool TABLE, bool CELL>
 __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     u64 *cvt = reinterpret_cast<u64 *>(smem);                            // [kTJG][4]
-    int *sh = reinterpret_cast<int *>(smem + kTJG * 4 * sizeof(u64));   // item slot
-    float2 *tab = reinterpret_cast<float2 *>(smem + kTJG * 4 * sizeof(u64) + 16);
+    u64 *run = cvt + 4 * kTJG;                                           // [8 NP][kNT]
+    int *sh = reinterpret_cast<int *>(run + 8 * NP * kNT);               // item slot
+    float2 *tab = reinterpret_cast<float2 *>(sh + 4);
 
     const int tid = threadIdx.x;
     if (TABLE)
@@ -40,8 +40,10 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
 
     const float c0 = TABLE ? 2.0f : a.eps2;
     const u64 c0v = pk2(c0, c0);
-    const double sc = TABLE ? a.tab.scale : 1.0;
-    const int nitems = a.nitems >= 0 ? a.nitems : *a.nitems_dev;
+    const float scf = TABLE && !CELL ? (float)a.tab.scale : 1.0f;
+    const int nitems = a.nitems >= 0 ? a.nitems : (int)*a.nitems_dev;
+    auto RH = [&](int p, int k) -> u64 & { return run[(8 * p + k) * kNT + tid]; };
+    auto RL = [&](int p, int k) -> u64 & { return run[(8 * p + 4 + k) * kNT + tid]; };
 
     for (;;) {
         __syncthreads();   // previous item fully done with shared memory
@@ -50,8 +52,9 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
         const int item = sh[0];
         if (item >= nitems) break;
         const GroupItem it = a.items[item];
-        const double4 c = a.gctr[it.group];
         const long long jb = a.j_off[it.group], je = a.j_off[it.group + 1];
+        double4 c = make_double4(0, 0, 0, 0);
+        if (!CELL) c = a.gctr[it.group];
 
         // thread layout: nsets sets of 2*NP i-particles, L lanes per set
         const int nsets = (it.ni + 2 * NP - 1) / (2 * NP);
@@ -62,7 +65,6 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
 
         u64 xi[NP], yi[NP], zi[NP];
         u64 ax[NP], ay[NP], az[NP], ph[NP];
-        u64 hx[NP], hy[NP], hz[NP], hp[NP], lx[NP], ly[NP], lz[NP], lp[NP];
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
             float fx[2] = {0, 0}, fy[2] = {0, 0}, fz[2] = {0, 0};
@@ -70,57 +72,67 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
             for (int q = 0; q < 2; ++q) {
                 int k = set * 2 * NP + 2 * p + q;
                 if (active && k < it.ni) {
-                    double4 v = a.xi[it.i0 + k];
-                    fx[q] = (float)((v.x - c.x) * sc);
-                    fy[q] = (float)((v.y - c.y) * sc);
-                    fz[q] = (float)((v.z - c.z) * sc);
+                    if (CELL) {
+                        float4 o = a.xo[it.i0 + k];
+                        fx[q] = o.x; fy[q] = o.y; fz[q] = o.z;
+                    } else {
+                        double4 v = a.xi[it.i0 + k];
+                        fx[q] = (float)(v.x - c.x) * scf;
+                        fy[q] = (float)(v.y - c.y) * scf;
+                        fz[q] = (float)(v.z - c.z) * scf;
+                    }
                 }
             }
             xi[p] = pk2(fx[0], fx[1]);
             yi[p] = pk2(fy[0], fy[1]);
             zi[p] = pk2(fz[0], fz[1]);
-            hx[p] = hy[p] = hz[p] = hp[p] = 0ull;
-            lx[p] = ly[p] = lz[p] = lp[p] = 0ull;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) RH(p, k) = RL(p, k) = 0ull;
         }
 
-        // register prefetch of the first tile's records (and their shift codes)
-        double4 rec[kPerThread];
-        int code[kPerThread];
+        // register prefetch of one tile of records
+        double4 rec[CELL ? 1 : kPerThread];
+        float4 rc32[CELL ? kPerThread : 1];
+        int code[CELL ? kPerThread : 1];
         auto fetch = [&](long long t0) {
 #pragma unroll
             for (int r = 0; r < kPerThread; ++r) {
                 long long e = t0 + r * kNT + tid;
-                code[r] = 13;                  // no image shift
-                if (e < je) {
-                    int raw = a.jlist[e];
-                    long long j = raw & 0x07ffffff;
-                    if (j >= a.nj) {           // bad index: record and contribute nothing
-                        report(a.status, kStatusBadIndex, 2);
-                        rec[r] = make_double4(0, 0, 0, -1.0);
-                        continue;
-                    }
-                    rec[r] = ldg_d4(a.jrec + j);
-                    if (a.box > 0.0) code[r] = (int)(((unsigned)raw) >> 27);
+                bool ok = e < je;
+                int raw = ok ? a.jlist[e] : 0;
+                long long j = raw & 0x07ffffff;
+                if (ok && j >= a.nj) {         // bad index: record it, contribute nothing
+                    report(a.status, kStatusBadIndex, 2);
+                    ok = false;
+                }
+                if (CELL) {
+                    rc32[r] = ok ? __ldg(a.xo + j) : make_float4(0, 0, 0, -1.0f);
+                    code[r] = (int)(((unsigned)raw) >> 27);
                 } else {
-                    rec[r] = make_double4(0, 0, 0, -1.0);   // padding marker
+                    rec[r] = ok ? ldg_d4(a.jrec + j) : make_double4(0, 0, 0, -1.0);
                 }
             }
         };
         fetch(jb);
         for (long long t0 = jb; t0 < je; t0 += kTJG) {
-            // publish the prefetched tile: FP64 record + image shift - centre -> FP32
+            // publish the prefetched tile as FP32 offsets in the i frame
 #pragma unroll
             for (int r = 0; r < kPerThread; ++r) {
                 const int e = r * kNT + tid;
                 float x, y, z, m;
-                if (rec[r].w >= 0.0) {
-                    double sx, sy, sz;
-                    shift_of(code[r], a.box, sx, sy, sz);
-                    x = (float)((rec[r].x + sx - c.x) * sc);
-                    y = (float)((rec[r].y + sy - c.y) * sc);
-                    z = (float)((rec[r].z + sz - c.z) * sc);
+                bool real = CELL ? rc32[r].w >= 0.0f : rec[r].w >= 0.0;
+                if (real && CELL) {
+                    const int cd = code[r];
+                    x = fmaf((float)(cd / 9 - 1), a.cell_h, rc32[r].x);
+                    y = fmaf((float)((cd / 3) % 3 - 1), a.cell_h, rc32[r].y);
+                    z = fmaf((float)(cd % 3 - 1), a.cell_h, rc32[r].z);
+                    m = rc32[r].w;
+                } else if (real) {
+                    x = (float)(rec[r].x - c.x) * scf;
+                    y = (float)(rec[r].y - c.y) * scf;
+                    z = (float)(rec[r].z - c.z) * scf;
                     m = (float)rec[r].w;
-                } else {
+                } else {   // padding: zero mass far away contributes exactly 0
                     x = y = z = 1.0e4f;
                     m = 0.0f;
                 }
@@ -177,10 +189,10 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
                 }
 #pragma unroll
                 for (int p = 0; p < NP; ++p) {
-                    fold2(hx[p], lx[p], ax[p]);
-                    fold2(hy[p], ly[p], ay[p]);
-                    fold2(hz[p], lz[p], az[p]);
-                    if (!TABLE) fold2(hp[p], lp[p], ph[p]);
+                    fold2(RH(p, 0), RL(p, 0), ax[p]);
+                    fold2(RH(p, 1), RL(p, 1), ay[p]);
+                    fold2(RH(p, 2), RL(p, 2), az[p]);
+                    if (!TABLE) fold2(RH(p, 3), RL(p, 3), ph[p]);
                 }
             }
             __syncthreads();   // everyone done with this tile before it is overwritten
@@ -190,10 +202,11 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
             float h[8], l[8];
-            up2(hx[p], h[0], h[1]); up2(hy[p], h[2], h[3]);
-            up2(hz[p], h[4], h[5]); up2(hp[p], h[6], h[7]);
-            up2(lx[p], l[0], l[1]); up2(ly[p], l[2], l[3]);
-            up2(lz[p], l[4], l[5]); up2(lp[p], l[6], l[7]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                up2(RH(p, k), h[2 * k], h[2 * k + 1]);
+                up2(RL(p, k), l[2 * k], l[2 * k + 1]);
+            }
             double v[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) v[k] = (double)h[k] + (double)l[k];
@@ -219,62 +232,78 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
 }
 
 // ------------------------------------------------------------------ host
-size_t groups_smem(bool table, int ntab)
+size_t groups_smem(int np, bool table, int ntab)
 {
-    size_t s = kTJG * 4 * sizeof(u64) + 16;
+    size_t s = kTJG * 4 * sizeof(u64) + 8 * np * kNT * sizeof(u64) + 16;
     if (table) s += (size_t)ntab * sizeof(float2);
     return s;
 }
 
 int groups_bi(int np) { return kNT * 2 * np; }
 
-template <int NP, bool TABLE>
+template <int NP, bool TABLE, bool CELL>
 static cudaError_t configure_g()
 {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_groups<NP, TABLE>,
+    cudaError_t e = cudaFuncSetAttribute(k_groups<NP, TABLE, CELL>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)groups_smem(TABLE, 1 << 13));
+                                         (int)groups_smem(NP, TABLE, 1 << 13));
     done = e == cudaSuccess;
     return e;
 }
 
-template <int NP, bool TABLE>
+template <int NP, bool TABLE, bool CELL>
 static int occ_g(size_t smem)
 {
-    if (configure_g<NP, TABLE>() != cudaSuccess) return 1;
+    if (configure_g<NP, TABLE, CELL>() != cudaSuccess) return 1;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_groups<NP, TABLE>, kNT, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_groups<NP, TABLE, CELL>, kNT, smem) !=
         cudaSuccess)
         return 1;
     return nb > 0 ? nb : 1;
 }
 
-int groups_max_blocks_per_sm(int np, bool table, int ntab)
+int groups_max_blocks_per_sm(int np, bool table, int ntab, bool cell)
 {
-    size_t smem = groups_smem(table, ntab);
-    if (table) return np == 1 ? occ_g<1, true>(smem) : np == 4 ? occ_g<4, true>(smem) : occ_g<2, true>(smem);
-    return np == 1 ? occ_g<1, false>(smem) : np == 4 ? occ_g<4, false>(smem) : occ_g<2, false>(smem);
+    size_t smem = groups_smem(np, table, ntab);
+    if (np == 1) {
+        if (!table) return occ_g<1, false, false>(smem);
+        return cell ? occ_g<1, true, true>(smem) : occ_g<1, true, false>(smem);
+    }
+    if (np == 4) {
+        if (!table) return occ_g<4, false, false>(smem);
+        return cell ? occ_g<4, true, true>(smem) : occ_g<4, true, false>(smem);
+    }
+    if (!table) return occ_g<2, false, false>(smem);
+    return cell ? occ_g<2, true, true>(smem) : occ_g<2, true, false>(smem);
 }
 
-cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, size_t smem,
-                          cudaStream_t st)
+template <int NP, bool TABLE, bool CELL>
+static cudaError_t launch_g(const GroupArgs &g, int grid, size_t smem, cudaStream_t st)
+{
+    cudaError_t e = configure_g<NP, TABLE, CELL>();
+    if (e != cudaSuccess) return e;
+    k_groups<NP, TABLE, CELL><<<grid, kNT, smem, st>>>(g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, bool cell,
+                          size_t smem, cudaStream_t st)
 {
     if (grid <= 0) return cudaSuccess;
-#define PG_G(NP_)                                                        \
-    if (np == NP_) {                                                     \
-        cudaError_t e = table ? configure_g<NP_, true>() : configure_g<NP_, false>(); \
-        if (e != cudaSuccess) return e;                                  \
-        if (table) k_groups<NP_, true><<<grid, kNT, smem, st>>>(g);      \
-        else k_groups<NP_, false><<<grid, kNT, smem, st>>>(g);           \
-        return cudaGetLastError();                                       \
+    if (cell && !table) return cudaErrorInvalidValue;
+    if (np == 1) {
+        if (!table) return launch_g<1, false, false>(g, grid, smem, st);
+        return cell ? launch_g<1, true, true>(g, grid, smem, st) : launch_g<1, true, false>(g, grid, smem, st);
     }
-    PG_G(1)
-    PG_G(2)
-    PG_G(4)
-#undef PG_G
-    return cudaErrorInvalidValue;
+    if (np == 4) {
+        if (!table) return launch_g<4, false, false>(g, grid, smem, st);
+        return cell ? launch_g<4, true, true>(g, grid, smem, st) : launch_g<4, true, false>(g, grid, smem, st);
+    }
+    if (np != 2) return cudaErrorInvalidValue;
+    if (!table) return launch_g<2, false, false>(g, grid, smem, st);
+    return cell ? launch_g<2, true, true>(g, grid, smem, st) : launch_g<2, true, false>(g, grid, smem, st);
 }
 
 // ------------------------------------------------------------------ prep
@@ -348,12 +377,21 @@ __global__ void k_cell_count(const unsigned *__restrict__ key, long long n, unsi
     if (i < n) atomicAdd(&cnt[key[i]], 1u);
 }
 
-// particles in cell order
+// particles in cell order, as FP32 offsets from their cell's corner in the
+// table's scaled units (the FP64 corner is implicit in the cell index)
 __global__ void k_cell_gather(const double4 *__restrict__ wrapped, const unsigned *__restrict__ perm,
-                              long long n, double4 *__restrict__ xs)
+                              const unsigned *__restrict__ key, long long n, int nc, double box,
+                              double scale, double4 *__restrict__ xs, float4 *__restrict__ xo)
 {
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (p < n) xs[p] = wrapped[perm[p]];
+    if (p >= n) return;
+    double4 w = wrapped[perm[p]];
+    xs[p] = w;
+    unsigned c = key[p];
+    int cx = (int)(c / ((unsigned)nc * nc)), cy = (int)((c / nc) % nc), cz = (int)(c % nc);
+    double h = box / nc;
+    xo[p] = make_float4((float)((w.x - cx * h) * scale), (float)((w.y - cy * h) * scale),
+                        (float)((w.z - cz * h) * scale), (float)w.w);
 }
 
 // per cell: number of j entries (27 neighbour cells) and number of items
@@ -401,8 +439,8 @@ __global__ void k_cell_pairs(const unsigned *__restrict__ start, const unsigned 
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(pairs, s);
 }
 
-// one CTA per cell: its j-list, neighbour by neighbour; a neighbour reached
-// across the box boundary carries the shift code of its periodic image
+// one CTA per cell: its j-list, neighbour by neighbour, each entry carrying
+// the direction code of its neighbour cell
 __global__ void k_cell_lists(const unsigned *__restrict__ start, int nc,
                              const unsigned *__restrict__ joff, int *__restrict__ jlist)
 {
@@ -414,14 +452,10 @@ __global__ void k_cell_lists(const unsigned *__restrict__ start, int nc,
     for (int dx = -1; dx <= 1; ++dx)
         for (int dy = -1; dy <= 1; ++dy)
             for (int dz = -1; dz <= 1; ++dz) {
-                int x = cx + dx, y = cy + dy, z = cz + dz;
-                // the image of a wrapped neighbour sits one box length over
-                int sx = x < 0 ? -1 : x >= nc ? 1 : 0;
-                int sy = y < 0 ? -1 : y >= nc ? 1 : 0;
-                int sz = z < 0 ? -1 : z >= nc ? 1 : 0;
-                x = (x + nc) % nc; y = (y + nc) % nc; z = (z + nc) % nc;
+                int x = (cx + dx + nc) % nc, y = (cy + dy + nc) % nc, z = (cz + dz + nc) % nc;
                 long long nb = ((long long)x * nc + y) * nc + z;
-                int code = 9 * (sx + 1) + 3 * (sy + 1) + (sz + 1);
+                // direction from the i-cell to the j-cell (the wrap is implicit in it)
+                int code = 9 * (dx + 1) + 3 * (dy + 1) + (dz + 1);
                 unsigned b = start[nb], cnt = start[nb + 1] - b;
                 for (unsigned k = threadIdx.x; k < cnt; k += blockDim.x)
                     jlist[pos + k] = (int)((b + k) | ((unsigned)code << 27));
@@ -471,7 +505,7 @@ __global__ void k_cell_ctr(int nc, double box, double4 *__restrict__ ctr)
 }
 
 cudaError_t launch_cell_build(const double4 *jrec, long long n, double box, int nc, int Bi,
-                              CellScratch &s, SortScratch &sort, cudaStream_t st)
+                              double scale, CellScratch &s, SortScratch &sort, cudaStream_t st)
 {
     long long ncell = (long long)nc * nc * nc;
     unsigned gb = (unsigned)((n + 255) / 256);
@@ -489,7 +523,7 @@ cudaError_t launch_cell_build(const double4 *jrec, long long n, double box, int 
     cudaMemsetAsync(s.start, 0, (ncell + 1) * sizeof(unsigned), st);
     k_cell_count<<<gb, 256, 0, st>>>(ko, n, s.start);
     if ((e = launch_excl_scan(s.start, ncell + 1, sort.sums, st)) != cudaSuccess) return e;
-    k_cell_gather<<<gb, 256, 0, st>>>(s.wrapped, perm, n, s.xs);
+    k_cell_gather<<<gb, 256, 0, st>>>(s.wrapped, perm, ko, n, nc, box, scale, s.xs, s.xo);
     k_cell_sizes<<<gc, 256, 0, st>>>(s.start, nc, Bi, s.jcount, s.icount);
     cudaMemsetAsync(s.pairs, 0, sizeof(unsigned long long), st);
     k_cell_pairs<<<gc < 1024 ? gc : 1024, 256, 0, st>>>(s.start, s.jcount, ncell, s.pairs);

@@ -83,7 +83,8 @@ struct GroupArgs {
     long long nj;          // number of j records (bounds check)
     float eps2;
     TableDev tab;
-    double box;            // periodic box (> 0: decode shift codes)
+    const float4 *xo;      // cell mode: FP32 offset records (o, m) in scaled units
+    float cell_h;          // cell mode: cell side in scaled units
     const unsigned *perm;  // i index -> output index (nullptr: identity)
     double accscale;
     double *acc, *pot;
@@ -137,10 +138,10 @@ cudaError_t launch_tile_prep(const double4 *xi, const unsigned *perm, long long 
                              double4 *xi_tiled, double4 *ctr, cudaStream_t st);
 
 cudaError_t launch_allpairs(const AllPairsArgs &a, int grid, int np, bool table, bool zsafe,
-                            size_t smem, cudaStream_t st);
+                            bool packed, size_t smem, cudaStream_t st);
 int allpairs_bi(int np);
 size_t allpairs_smem(int np, bool table, int ntab);
-int allpairs_max_blocks_per_sm(int np, bool table, int ntab);
+int allpairs_max_blocks_per_sm(int np, bool table, int ntab, bool packed);
 cudaError_t launch_combine(const CombineArgs &c, cudaStream_t st);
 long long stream_k_first(long long u, int grid, long long W);
 
@@ -149,11 +150,11 @@ cudaError_t launch_table_prep(const float *G0, const float *G1, float2 *AG1, int
 cudaError_t launch_table_from_values(const float *v, float *G0, float *G1, int E, int F,
                                      cudaStream_t st);
 
-cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, size_t smem,
-                          cudaStream_t st);
-size_t groups_smem(bool table, int ntab);
+cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, bool cell,
+                          size_t smem, cudaStream_t st);
+size_t groups_smem(int np, bool table, int ntab);
 int groups_bi(int np);
-int groups_max_blocks_per_sm(int np, bool table, int ntab);
+int groups_max_blocks_per_sm(int np, bool table, int ntab, bool cell);
 cudaError_t launch_group_ctr(const double4 *xi, const long long *i_off, long long ngroups,
                              double4 *ctr, cudaStream_t st);
 
@@ -162,6 +163,7 @@ cudaError_t launch_group_ctr(const double4 *xi, const long long *i_off, long lon
 struct CellScratch {
     double4 *wrapped;      // n: positions wrapped into the box (input order)
     double4 *xs;           // n: wrapped positions + mass in cell order
+    float4 *xo;            // n: FP32 offsets from the cell corner (scaled) + mass, cell order
     unsigned *perm;        // n: cell order -> input index (own copy)
     unsigned *start;       // ncell + 1: first particle of each cell
     unsigned *jcount;      // ncell
@@ -177,7 +179,7 @@ struct CellScratch {
     unsigned long long *pairs;   // evaluated pairs of the build (device)
 };
 cudaError_t launch_cell_build(const double4 *jrec, long long n, double box, int nc, int Bi,
-                              CellScratch &s, SortScratch &sort, cudaStream_t st);
+                              double scale, CellScratch &s, SortScratch &sort, cudaStream_t st);
 cudaError_t launch_excl_scan(unsigned *a, long long n, unsigned *sums, cudaStream_t st);
 
 // backward

@@ -96,7 +96,7 @@ extern "C" int pg_newton_allpairs_noalloc(const double *x, const double *m, long
     const int ntiles = (int)((n + kNoAllocBi - 1) / kNoAllocBi);
     const int njsub = (int)((n + kTJ - 1) / kTJ);
     const long long W = (long long)ntiles * njsub;
-    int occ = allpairs_max_blocks_per_sm(kNoAllocNP, false, 0);
+    int occ = allpairs_max_blocks_per_sm(kNoAllocNP, false, 0, true);
     long long G = std::min<long long>(std::min<long long>(W, 4LL * ntiles), (long long)sms * occ);
     int slots = 1;
     for (long long t = 0; t < ntiles; ++t) {
@@ -122,7 +122,7 @@ extern "C" int pg_newton_allpairs_noalloc(const double *x, const double *m, long
     ap.part = part;
     ap.status = nullptr;
     if (e == cudaSuccess)
-        e = launch_allpairs(ap, (int)G, kNoAllocNP, false, ap.eps2 == 0.0f,
+        e = launch_allpairs(ap, (int)G, kNoAllocNP, false, ap.eps2 == 0.0f, true,
                             allpairs_smem(kNoAllocNP, false, 0), st);
     CombineArgs cb{};
     cb.part = part;

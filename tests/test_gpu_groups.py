@@ -18,9 +18,11 @@ def pg():
     return need_cuda()
 
 
-def run_groups(pg, d, eps, graph=False, reps=1, table=None):
+def run_groups(pg, d, eps, graph=False, reps=1, table=None, np_=0):
     with pg.Context(0) as c:
         c.set_eps(eps)
+        if np_:
+            c.set_shape(np_)
         if table is not None:
             c.set_mode(pg.PG_TABLE)
             c.set_table_values(*table)
@@ -39,9 +41,10 @@ def small():
                            n_monopoles=1 << 12, nj_range=(64, 4000))
 
 
-def test_small_tree_workload(pg, orc, small):
+@pytest.mark.parametrize("np_", [1, 2, 4])
+def test_small_tree_workload(pg, orc, small, np_):
     d = small
-    a, p = run_groups(pg, d, 1e-3)
+    a, p = run_groups(pg, d, 1e-3, np_=np_)
     ao, po = orc.newton_groups(d["i_off"], d["j_off"], d["jlist"], d["xi"], d["xj"], d["mj"], 1e-3)
     assert_parity(rel_vec(a, ao), what="a")
     assert_parity(rel_scalar(p, po), what="phi")

@@ -44,7 +44,8 @@ def test_plummer_4096_full(pg, orc):
 
 
 @pytest.mark.parametrize("n", [1, 2, 255, 1537, 5000])
-@pytest.mark.parametrize("shape", [(1, 0), (2, 0), (4, 0), (2, 1)])
+@pytest.mark.parametrize("shape", [(1, 0, 1), (2, 0, 1), (4, 0, 1), (2, 1, 1),
+                                   (1, 0, 0), (2, 0, 0), (4, 0, 0)])
 def test_ragged_sizes_and_shapes(pg, orc, n, shape):
     x, m = gen.plummer(n, 700 + n)
     m = m * np.exp(np.random.default_rng(n).uniform(-2, 2, n))

@@ -58,7 +58,7 @@ def table_allpairs(pg, x, m, v, r_cut, E, F, shape=None):
 
 
 @pytest.mark.parametrize("E,F,n", [(3, 5, 3000), (4, 8, 4001)])
-@pytest.mark.parametrize("shape", [(1, 0), (2, 0), (4, 0)])
+@pytest.mark.parametrize("shape", [(1, 0, 1), (2, 0, 1), (4, 0, 1), (2, 0, 0)])
 def test_allpairs_table_semantics(pg, orc, E, F, n, shape):
     rng = np.random.default_rng(n + E)
     r_cut = 0.1
