@@ -181,7 +181,8 @@ int pg_set_graph(pg_ctx *ctx, int on);
  * CTAs per SM) on the device and keep the fastest. Synchronises. */
 int pg_tune(pg_ctx *ctx);
 
-/* Launch shape override: i per thread = 2*np (np in {1, 2, 4}; 0 = keep),
+/* Launch shape override: i per thread = 2*np (np in {1, 2, 4}; 0 = chosen
+ * by problem size, the default),
  * CTAs per SM (0 = occupancy limit), packed = 1: pair arithmetic in packed
  * FP32x2 instructions, 0: scalar FP32 (same roundings), -1 = keep. */
 int pg_set_shape(pg_ctx *ctx, int np, int ctas_per_sm, int packed);

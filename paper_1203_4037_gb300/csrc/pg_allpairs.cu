@@ -91,9 +91,12 @@ struct Lanes<false> {
 };
 
 // CTAs per SM the register budget is sized for
+#ifndef PG_NP4_MIN_BLOCKS
+#define PG_NP4_MIN_BLOCKS 3
+#endif
 template <int NP>
 struct MinBlocks {
-    static constexpr int value = NP == 1 ? 8 : NP == 2 ? 5 : 2;
+    static constexpr int value = NP == 1 ? 8 : NP == 2 ? 5 : PG_NP4_MIN_BLOCKS;
 };
 
 template <int NP, bool TABLE, bool ZSAFE, bool PK>

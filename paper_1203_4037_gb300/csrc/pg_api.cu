@@ -91,8 +91,8 @@ struct pg_ctx {
     // backward
     DevBuf bw_wj, bw_wt, bw_dv;
 
-    // launch shape
-    int np = 2;
+    // launch shape (np = 0: chosen by problem size)
+    int np = 0;
     int ctas_per_sm = 0;
     int packed = 1;             // f32x2 pair arithmetic (0: scalar FP32)
 
@@ -107,6 +107,7 @@ struct pg_ctx {
     bool timed = false;
 
     // stats of the last run
+    int last_np = 2;
     long long last_pairs = 0, last_launches = 0, last_grid = 0, last_slots = 0;
 
     std::string err;
@@ -578,7 +579,7 @@ int pg_set_shape(pg_ctx *c, int np, int ctas_per_sm, int packed)
     if (np != 0 && np != 1 && np != 2 && np != 4) return fail(c, PG_EINVAL, "np must be 0, 1, 2 or 4");
     if (ctas_per_sm < 0) return fail(c, PG_EINVAL, "ctas_per_sm must be >= 0");
     if (packed < -1 || packed > 1) return fail(c, PG_EINVAL, "packed must be -1, 0 or 1");
-    if (np) c->np = np;
+    c->np = np;   // 0: chosen by problem size
     c->ctas_per_sm = ctas_per_sm;
     if (packed >= 0) c->packed = packed;
     c->i_dirty = true;
@@ -596,8 +597,8 @@ int pg_info(pg_ctx *c, long long *out, int n)
         c->last_pairs = (long long)v;
         c->pairs_on_device = false;
     }
-    long long v[6] = {c->last_pairs, c->last_launches, 2LL * c->np, c->last_grid, c->last_slots,
-                      (long long)c->packed};
+    long long v[6] = {c->last_pairs, c->last_launches, 2LL * c->last_np, c->last_grid,
+                      c->last_slots, (long long)c->packed};
     int k = std::min(n, 6);
     for (int i = 0; i < k; ++i) out[i] = v[i];
     return k;
@@ -642,19 +643,25 @@ namespace {
 
 struct Plan {
     long long ni, nj;
-    int Bi, ntiles, njsub, grid, slots;
+    int np, Bi, ntiles, njsub, grid, slots;
     long long W;
 };
+
+// i-particles per thread / 2 when not fixed by pg_set_shape: more per thread
+// (more independent work per warp) for large sets, fewer (more tiles to fill
+// the SMs) for small ones
+int auto_np(long long ni) { return ni >= 65536 ? 4 : ni >= 8192 ? 2 : 1; }
 
 int plan_allpairs(pg_ctx *c, Plan &p)
 {
     p.ni = c->ni;
     p.nj = nj_of(c);
-    p.Bi = allpairs_bi(c->np);
+    p.np = c->np ? c->np : auto_np(p.ni);
+    p.Bi = allpairs_bi(p.np);
     p.ntiles = (int)((p.ni + p.Bi - 1) / p.Bi);
     p.njsub = (int)((p.nj + kTJ - 1) / kTJ);
     p.W = (long long)p.ntiles * p.njsub;
-    int occ = allpairs_max_blocks_per_sm(c->np, c->mode == PG_TABLE, c->ntab, c->packed != 0);
+    int occ = allpairs_max_blocks_per_sm(p.np, c->mode == PG_TABLE, c->ntab, c->packed != 0);
     int per = c->ctas_per_sm > 0 ? std::min(c->ctas_per_sm, occ) : occ;
     long long g = (long long)c->sms * per;
     p.grid = (int)std::max<long long>(0, std::min<long long>(g, p.W));
@@ -698,7 +705,7 @@ int enqueue_tiles(pg_ctx *c, const Plan &p)
     PG_CUDA(c, launch_tile_prep((const double4 *)c->xi.p, c->perm, n, p.Bi, (double4 *)c->xt.p,
                                 (double4 *)c->ctr.p, c->stream));
     c->last_launches += 1;
-    c->tiled_np = c->np;
+    c->tiled_np = p.np;
     return PG_OK;
 }
 
@@ -706,7 +713,7 @@ int enqueue_allpairs(pg_ctx *c, const Plan &p, double *acc, double *pot)
 {
     int rc;
     bool table = c->mode == PG_TABLE;
-    if (p.ni > 0 && (c->i_dirty || c->use_graph || c->tiled_np != c->np)) {
+    if (p.ni > 0 && (c->i_dirty || c->use_graph || c->tiled_np != p.np)) {
         if ((rc = enqueue_tiles(c, p))) return rc;
         c->i_dirty = false;
     }
@@ -727,10 +734,11 @@ int enqueue_allpairs(pg_ctx *c, const Plan &p, double *acc, double *pot)
     a.part = (double4 *)c->part.p;
     a.status = (int *)c->status.p;
     bool zsafe = !table && a.eps2 == 0.0f;
-    size_t smem = allpairs_smem(c->np, table, c->ntab);
+    size_t smem = allpairs_smem(p.np, table, c->ntab);
+    c->last_np = p.np;
     if (p.grid > 0) {
         if (c->timing) PG_CUDA(c, cudaEventRecord(c->tk0, c->stream));
-        PG_CUDA(c, launch_allpairs(a, p.grid, c->np, table, zsafe, c->packed != 0, smem, c->stream));
+        PG_CUDA(c, launch_allpairs(a, p.grid, p.np, table, zsafe, c->packed != 0, smem, c->stream));
         if (c->timing) PG_CUDA(c, cudaEventRecord(c->tk1, c->stream));
         c->timed = c->timing;
         c->last_launches += 1;
@@ -782,9 +790,11 @@ int check_run_state(pg_ctx *c)
 }
 
 // host items for the groups: chunks of at most Bi i-particles, longest first
+int groups_np(const pg_ctx *c) { return c->np ? c->np : 2; }
+
 int upload_group_items(pg_ctx *c)
 {
-    int Bi = groups_bi(c->np);
+    int Bi = groups_bi(groups_np(c));
     std::vector<GroupItem> items;
     std::vector<long long> cost;
     for (long long g = 0; g < c->ngroups; ++g) {
@@ -811,7 +821,7 @@ int upload_group_items(pg_ctx *c)
         PG_CUDA(c, cudaMemcpy(c->g_items.p, sorted.data(), sorted.size() * sizeof(GroupItem),
                               cudaMemcpyHostToDevice));
     c->g_nitems = (int)sorted.size();
-    c->g_items_np = c->np;
+    c->g_items_np = groups_np(c);
     return PG_OK;
 }
 
@@ -829,13 +839,14 @@ GroupArgs group_args(pg_ctx *c)
 int launch_group_kernel(pg_ctx *c, const GroupArgs &g, bool cell)
 {
     bool table = c->mode == PG_TABLE;
-    int occ = groups_max_blocks_per_sm(c->np, table, c->ntab, cell);
+    int np = groups_np(c);
+    c->last_np = np;
+    int occ = groups_max_blocks_per_sm(np, table, c->ntab, cell);
     int per = c->ctas_per_sm > 0 ? std::min(c->ctas_per_sm, occ) : occ;
     int grid = c->sms * per;
     PG_CUDA(c, cudaMemsetAsync(c->g_queue.p, 0, sizeof(int), c->stream));
     if (c->timing) PG_CUDA(c, cudaEventRecord(c->tk0, c->stream));
-    PG_CUDA(c, launch_groups(g, grid, c->np, table, cell, groups_smem(c->np, table, c->ntab),
-                             c->stream));
+    PG_CUDA(c, launch_groups(g, grid, np, table, cell, groups_smem(np, table, c->ntab), c->stream));
     if (c->timing) PG_CUDA(c, cudaEventRecord(c->tk1, c->stream));
     c->timed = c->timing;
     c->last_grid = grid;
@@ -846,7 +857,7 @@ int launch_group_kernel(pg_ctx *c, const GroupArgs &g, bool cell)
 int enqueue_groups(pg_ctx *c, double *acc, double *pot)
 {
     int rc;
-    if (c->g_items_np != c->np && (rc = upload_group_items(c))) return rc;
+    if (c->g_items_np != groups_np(c) && (rc = upload_group_items(c))) return rc;
     if ((rc = ensure(c, c->g_ctr, (size_t)std::max<long long>(c->ngroups, 1) * sizeof(double4))) ||
         (rc = ensure(c, c->g_queue, 16)))
         return rc;
@@ -881,7 +892,7 @@ int enqueue_cells(pg_ctx *c, double *acc, double *pot)
     int nc = (int)std::floor(c->box / c->r_cut);
     if (nc > 1024) nc = 1024;
     long long ncell = (long long)nc * nc * nc;
-    int Bi = groups_bi(c->np);
+    int Bi = groups_bi(groups_np(c));
     long long item_cap = ncell + n / Bi + 1;
     long long sn = std::max(n, item_cap);
     CellScratch &s = c->cells;

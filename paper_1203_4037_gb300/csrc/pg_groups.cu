@@ -45,9 +45,16 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
     auto RH = [&](int p, int k) -> u64 & { return run[(8 * p + k) * kNT + tid]; };
     auto RL = [&](int p, int k) -> u64 & { return run[(8 * p + 4 + k) * kNT + tid]; };
 
+    // the next item is claimed while the current one runs (kept in a
+    // register of thread 0), so the queue's atomic latency overlaps work
+    int next = 0;
+    if (tid == 0) next = atomicAdd(a.queue, 1);
     for (;;) {
         __syncthreads();   // previous item fully done with shared memory
-        if (tid == 0) sh[0] = atomicAdd(a.queue, 1);
+        if (tid == 0) {
+            sh[0] = next;
+            if (next < nitems) next = atomicAdd(a.queue, 1);
+        }
         __syncthreads();
         const int item = sh[0];
         if (item >= nitems) break;
@@ -198,7 +205,9 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
             __syncthreads();   // everyone done with this tile before it is overwritten
         }
 
-        // combine the L lanes of each set in FP64, write the set's outputs
+        // combine the L lanes of each set: (hi, lo) pairs merged with FP32
+        // TwoSum across lanes (FP64 would dominate small items on GB300),
+        // one conversion to FP64 on the writing lane
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
             float h[8], l[8];
@@ -207,13 +216,22 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
                 up2(RH(p, k), h[2 * k], h[2 * k + 1]);
                 up2(RL(p, k), l[2 * k], l[2 * k + 1]);
             }
-            double v[8];
+            for (int off = L >> 1; off > 0; off >>= 1) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) v[k] = (double)h[k] + (double)l[k];
-            for (int off = L >> 1; off > 0; off >>= 1)
-#pragma unroll
-                for (int k = 0; k < 8; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
+                for (int k = 0; k < 8; ++k) {
+                    if (TABLE && (k == 6 || k == 7)) continue;   // no potential
+                    const float oh = __shfl_xor_sync(0xffffffffu, h[k], off);
+                    const float ol = __shfl_xor_sync(0xffffffffu, l[k], off);
+                    float sm, er;
+                    two_sum(h[k], oh, sm, er);
+                    h[k] = sm;
+                    l[k] = __fadd_rn(l[k], __fadd_rn(ol, er));
+                }
+            }
             if (active && lane == 0) {
+                double v[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) v[k] = (double)h[k] + (double)l[k];
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
                     int k = set * 2 * NP + 2 * p + q;
