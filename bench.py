@@ -547,8 +547,11 @@ def main():
     kms = statistics.median(kern_ms)
     pairs_rank = ni * npart
     achieved = pairs_rank / (kms * 1e-3)
+    # DRAM bytes per launch of this kernel at this size (ncu, one pass, see
+    # profiles/k_allpairs_newton_2e20_dram.md); null for other sizes or shapes
+    traffic = 100.41e6 if (npart == N_PART and world == 1 and info["i_per_thread"] == 8) else None
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_int / 1e9,
-            "unit": "Ginteractions/s", "frac": achieved / peak_int, "traffic": None,
+            "unit": "Ginteractions/s", "frac": achieved / peak_int, "traffic": traffic,
             "kernel": f"k_allpairs<np={info['i_per_thread'] // 2}, packed={info['packed']}>",
             "kernel_ms": kms,
             "peak_basis": f"{sms} SMs x {f_max / 1e6:.0f} MHz x 128 FP32 lanes / 13 ops per "
@@ -556,6 +559,15 @@ def main():
     if clk.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = achieved / (sms * clk["sm_mhz"] * 1e6 * FP32_LANES_PER_SM /
                                                     NEWTON_OPS)
+    try:
+        # measured ceilings: FP32x2 lane rate and the pair term with register operands
+        ffma2 = pg.pg_microbench(1)[1]
+        mix = pg.pg_microbench(3)[1]
+        roof["measured_fp32x2_lane_ops_per_s"] = ffma2
+        roof["measured_pair_term_ceiling"] = mix / 1e9
+        roof["frac_of_pair_term_ceiling"] = achieved / mix
+    except Exception as exc:  # report, do not hide
+        roof["microbench_error"] = repr(exc)
     cpu = None
     if not args.no_cpu_baseline:
         cpu = cpu_baseline(x, m)

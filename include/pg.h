@@ -201,6 +201,14 @@ int pg_kernel_time(pg_ctx *ctx, double *ms);
  * is packed FP32x2. Returns how many were written. */
 int pg_info(pg_ctx *ctx, long long *out, int n);
 
+/* Measured ceilings on the current device for the roofline (a tool of this
+ * library; the paper quotes only its CPU's peak): kind 0 scalar FP32 FMA,
+ * 1 packed FP32x2 FMA (lane operations), 2 MUFU rsqrt, 3 the Newton pair
+ * term with every operand in registers (interactions). Writes the rate per
+ * SM per clock (at the device's maximum clock) and per second. Synchronises
+ * the legacy default stream. */
+int pg_microbench(int kind, double *per_sm_clock, double *per_second);
+
 /* Largest particle count pg_newton_allpairs_noalloc accepts. */
 #define PG_NOALLOC_MAX_N 16384
 

@@ -66,6 +66,7 @@ SIGNATURES = {
     "pg_set_timing": (_I, [_P, _I]),
     "pg_kernel_time": (_I, [_P, C.POINTER(_D)]),
     "pg_info": (_I, [_P, C.POINTER(_LL), _I]),
+    "pg_microbench": (_I, [_I, C.POINTER(_D), C.POINTER(_D)]),
     "pg_newton_allpairs_noalloc": (_I, [_P, _P, _LL, _D, _P, _P, _P]),
     "pg_last_error": (C.c_char_p, [_P]),
     "pg_version": (C.c_char_p, []),
@@ -271,6 +272,16 @@ def pg_info(ctx):
     n = lib().pg_info(ctx, out, 6)
     keys = ["pairs", "launches", "i_per_thread", "grid", "slots", "packed"]
     return dict(zip(keys[:n], list(out)[:n]))
+
+
+def pg_microbench(kind):
+    """(rate per SM per clock, rate per second) of: 0 FFMA, 1 FFMA2 lane ops,
+    2 MUFU rsqrt, 3 Newton pair-term interactions with register operands."""
+    a, b = C.c_double(), C.c_double()
+    rc = lib().pg_microbench(int(kind), C.byref(a), C.byref(b))
+    if rc != PG_OK:
+        raise PGError(rc, "microbenchmark failed")
+    return a.value, b.value
 
 
 PG_NOALLOC_MAX_N = 16384

@@ -290,7 +290,9 @@ __global__ void __launch_bounds__(kNT, MinBlocks<NP>::value) k_allpairs(AllPairs
                     rb = fminf(rb, a.tab.s_max);
                     const float2 ta = tab[(__float_as_uint(ra) >> a.tab.shift) - a.tab.base];
                     const float2 tb = tab[(__float_as_uint(rb) >> a.tab.shift) - a.tab.base];
-                    const u64 g = V::fma(pk2(ra, rb), pk2(ta.y, tb.y), pk2(ta.x, tb.x));
+                    // each lane's {A, G1} arrives as a pair: two scalar FMAs
+                    // write the packed g without register moves
+                    const u64 g = pk2(__fmaf_rn(ra, ta.y, ta.x), __fmaf_rn(rb, tb.y, tb.x));
                     const u64 mg = V::mul(zm.y, g);
                     ax[p] = V::fma(mg, dx, ax[p]);
                     ay[p] = V::fma(mg, dy, ay[p]);

@@ -790,7 +790,9 @@ int check_run_state(pg_ctx *c)
 }
 
 // host items for the groups: chunks of at most Bi i-particles, longest first
-int groups_np(const pg_ctx *c) { return c->np ? c->np : 2; }
+// largest i-pairs per thread of the groups kernel (items may use half of it):
+// 4 for tree groups of up to hundreds of particles, 2 for the small cells
+int groups_np(const pg_ctx *c) { return c->np ? c->np : (c->have_groups ? 4 : 2); }
 
 int upload_group_items(pg_ctx *c)
 {

@@ -25,25 +25,243 @@ constexpr int kPerThread = kTJG / kNT;
 //    carries the direction (dx, dy, dz) in {-1, 0, 1}^3 from the i-cell to the
 //    j-cell, so the j offset in the i-cell's frame is o_j + (dx, dy, dz) h~ --
 //    FP32 only, with the periodic wrap already in the direction.
+//
+// Thread layout of an item: nsets sets of 2*NP i-particles; each set owns L
+// consecutive lanes of one warp (any L from 1 to 32, sets never straddle a
+// warp), lane l of a set takes the j with index = l (mod L), and the set's
+// lanes are combined by a segmented shuffle reduction at the end. NP (i-pairs
+// per thread) is chosen per item, 2 or 4, for the better thread use.
+
+struct ItemShape {
+    int nsets, L, spw;
+};
+
+__device__ __forceinline__ ItemShape item_shape(int ni, int np)
+{
+    ItemShape s;
+    s.nsets = (ni + 2 * np - 1) / (2 * np);
+    int L = kNT / (s.nsets > 0 ? s.nsets : 1);
+    L = L > 32 ? 32 : L < 1 ? 1 : L;
+    while (L > 1 && (kNT / 32) * (32 / L) < s.nsets) --L;
+    s.L = L;
+    s.spw = 32 / L;
+    return s;
+}
+
 template <int NP, bool TABLE, bool CELL>
+__device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &it, const ItemShape sh,
+                                           u64 *cvt, u64 *run, const float2 *tab, int tid)
+{
+    const long long jb = a.j_off[it.group], je = a.j_off[it.group + 1];
+    double4 c = make_double4(0, 0, 0, 0);
+    if (!CELL) c = a.gctr[it.group];
+    const float c0 = TABLE ? 2.0f : a.eps2;
+    const u64 c0v = pk2(c0, c0);
+    const float scf = TABLE && !CELL ? (float)a.tab.scale : 1.0f;
+    auto RH = [&](int p, int k) -> u64 & { return run[(8 * p + k) * kNT + tid]; };
+    auto RL = [&](int p, int k) -> u64 & { return run[(8 * p + 4 + k) * kNT + tid]; };
+
+    const int L = sh.L;
+    const int wl = tid & 31;
+    const int set = (tid >> 5) * sh.spw + wl / L, lane = wl % L;
+    const bool active = wl < sh.spw * L && set < sh.nsets;
+
+    u64 xi[NP], yi[NP], zi[NP];
+    u64 ax[NP], ay[NP], az[NP], ph[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        float fx[2] = {0, 0}, fy[2] = {0, 0}, fz[2] = {0, 0};
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            int k = set * 2 * NP + 2 * p + q;
+            if (active && k < it.ni) {
+                if (CELL) {
+                    float4 o = a.xo[it.i0 + k];
+                    fx[q] = o.x; fy[q] = o.y; fz[q] = o.z;
+                } else {
+                    double4 v = a.xi[it.i0 + k];
+                    fx[q] = (float)(v.x - c.x) * scf;
+                    fy[q] = (float)(v.y - c.y) * scf;
+                    fz[q] = (float)(v.z - c.z) * scf;
+                }
+            }
+        }
+        xi[p] = pk2(fx[0], fx[1]);
+        yi[p] = pk2(fy[0], fy[1]);
+        zi[p] = pk2(fz[0], fz[1]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) RH(p, k) = RL(p, k) = 0ull;
+    }
+
+    // register prefetch of one tile of records
+    double4 rec[CELL ? 1 : kPerThread];
+    float4 rc32[CELL ? kPerThread : 1];
+    int code[CELL ? kPerThread : 1];
+    auto fetch = [&](long long t0) {
+#pragma unroll
+        for (int r = 0; r < kPerThread; ++r) {
+            long long e = t0 + r * kNT + tid;
+            bool ok = e < je;
+            int raw = ok ? a.jlist[e] : 0;
+            long long j = raw & 0x07ffffff;
+            if (ok && j >= a.nj) {         // bad index: record it, contribute nothing
+                report(a.status, kStatusBadIndex, 2);
+                ok = false;
+            }
+            if (CELL) {
+                rc32[r] = ok ? __ldg(a.xo + j) : make_float4(0, 0, 0, -1.0f);
+                code[r] = (int)(((unsigned)raw) >> 27);
+            } else {
+                rec[r] = ok ? ldg_d4(a.jrec + j) : make_double4(0, 0, 0, -1.0);
+            }
+        }
+    };
+    fetch(jb);
+    for (long long t0 = jb; t0 < je; t0 += kTJG) {
+        // publish the prefetched tile as FP32 offsets in the i frame
+#pragma unroll
+        for (int r = 0; r < kPerThread; ++r) {
+            const int e = r * kNT + tid;
+            float x, y, z, m;
+            bool real = CELL ? rc32[r].w >= 0.0f : rec[r].w >= 0.0;
+            if (real && CELL) {
+                const int cd = code[r];
+                x = fmaf((float)(cd / 9 - 1), a.cell_h, rc32[r].x);
+                y = fmaf((float)((cd / 3) % 3 - 1), a.cell_h, rc32[r].y);
+                z = fmaf((float)(cd % 3 - 1), a.cell_h, rc32[r].z);
+                m = rc32[r].w;
+            } else if (real) {
+                x = (float)(rec[r].x - c.x) * scf;
+                y = (float)(rec[r].y - c.y) * scf;
+                z = (float)(rec[r].z - c.z) * scf;
+                m = (float)rec[r].w;
+            } else {   // padding: zero mass far away contributes exactly 0
+                x = y = z = 1.0e4f;
+                m = 0.0f;
+            }
+            cvt[4 * e + 0] = pk2(x, x);
+            cvt[4 * e + 1] = pk2(y, y);
+            cvt[4 * e + 2] = pk2(z, z);
+            cvt[4 * e + 3] = pk2(m, m);
+        }
+        __syncthreads();
+        if (t0 + kTJG < je) fetch(t0 + kTJG);   // loads in flight during the compute
+        long long nv = je - t0;
+        if (nv > kTJG) nv = kTJG;
+        if (active) {
+#pragma unroll
+            for (int p = 0; p < NP; ++p) ax[p] = ay[p] = az[p] = ph[p] = 0ull;
+            const int nv_lane = (int)nv;
+#pragma unroll 2
+            for (int e = lane; e < nv_lane; e += L) {
+                const ulonglong2 xy = reinterpret_cast<const ulonglong2 *>(cvt)[2 * e];
+                const ulonglong2 zm = reinterpret_cast<const ulonglong2 *>(cvt)[2 * e + 1];
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    const u64 dx = f2sub(xy.x, xi[p]);
+                    const u64 dy = f2sub(xy.y, yi[p]);
+                    const u64 dz = f2sub(zm.x, zi[p]);
+                    u64 r2 = f2fma(dx, dx, c0v);
+                    r2 = f2fma(dy, dy, r2);
+                    r2 = f2fma(dz, dz, r2);
+                    float ra, rb;
+                    up2(r2, ra, rb);
+                    if (!TABLE) {
+                        float qa = rsq(ra), qb = rsq(rb);
+                        qa = ra > 0.0f ? qa : 0.0f;     // eps = 0: coincident pair adds nothing
+                        qb = rb > 0.0f ? qb : 0.0f;
+                        const u64 q = pk2(qa, qb);
+                        const u64 mq = f2mul(zm.y, q);
+                        const u64 mq3 = f2mul(mq, f2mul(q, q));
+                        ph[p] = f2sub(ph[p], mq);
+                        ax[p] = f2fma(mq3, dx, ax[p]);
+                        ay[p] = f2fma(mq3, dy, ay[p]);
+                        az[p] = f2fma(mq3, dz, az[p]);
+                    } else {
+                        ra = fminf(ra, a.tab.s_max);
+                        rb = fminf(rb, a.tab.s_max);
+                        const float2 ta = tab[(__float_as_uint(ra) >> a.tab.shift) - a.tab.base];
+                        const float2 tb = tab[(__float_as_uint(rb) >> a.tab.shift) - a.tab.base];
+                        const u64 g = pk2(__fmaf_rn(ra, ta.y, ta.x), __fmaf_rn(rb, tb.y, tb.x));
+                        const u64 mg = f2mul(zm.y, g);
+                        ax[p] = f2fma(mg, dx, ax[p]);
+                        ay[p] = f2fma(mg, dy, ay[p]);
+                        az[p] = f2fma(mg, dz, az[p]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                fold2(RH(p, 0), RL(p, 0), ax[p]);
+                fold2(RH(p, 1), RL(p, 1), ay[p]);
+                fold2(RH(p, 2), RL(p, 2), az[p]);
+                if (!TABLE) fold2(RH(p, 3), RL(p, 3), ph[p]);
+            }
+        }
+        __syncthreads();   // everyone done with this tile before it is overwritten
+    }
+
+    // combine the L lanes of each set: segmented shuffle reduction of the
+    // (hi, lo) FP32 pairs with TwoSum (FP64 would dominate small items on
+    // GB300), one conversion to FP64 on the set's first lane
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        float h[8], l[8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            up2(RH(p, k), h[2 * k], h[2 * k + 1]);
+            up2(RL(p, k), l[2 * k], l[2 * k + 1]);
+        }
+        for (int off = 1; off < L; off <<= 1) {
+            const bool take = lane + off < L;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (TABLE && (k == 6 || k == 7)) continue;   // no potential
+                const float oh = __shfl_down_sync(0xffffffffu, h[k], off);
+                const float ol = __shfl_down_sync(0xffffffffu, l[k], off);
+                if (take) {
+                    float sm, er;
+                    two_sum(h[k], oh, sm, er);
+                    h[k] = sm;
+                    l[k] = __fadd_rn(l[k], __fadd_rn(ol, er));
+                }
+            }
+        }
+        if (active && lane == 0) {
+            double v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = (double)h[k] + (double)l[k];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                int k = set * 2 * NP + 2 * p + q;
+                if (k < it.ni) {
+                    long long i = it.i0 + k;
+                    long long o = a.perm ? (long long)a.perm[i] : i;
+                    a.acc[3 * o] = v[0 + q] * a.accscale;
+                    a.acc[3 * o + 1] = v[2 + q] * a.accscale;
+                    a.acc[3 * o + 2] = v[4 + q] * a.accscale;
+                    if (a.pot) a.pot[o] = TABLE ? 0.0 : v[6 + q];
+                }
+            }
+        }
+    }
+}
+
+// NPMAX: the largest i-pair count per thread; items whose shape uses the
+// threads better with half of it run with NPMAX / 2
+template <int NPMAX, bool TABLE, bool CELL>
 __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     u64 *cvt = reinterpret_cast<u64 *>(smem);                            // [kTJG][4]
-    u64 *run = cvt + 4 * kTJG;                                           // [8 NP][kNT]
-    int *sh = reinterpret_cast<int *>(run + 8 * NP * kNT);               // item slot
+    u64 *run = cvt + 4 * kTJG;                                           // [8 NPMAX][kNT]
+    int *sh = reinterpret_cast<int *>(run + 8 * NPMAX * kNT);            // item slot
     float2 *tab = reinterpret_cast<float2 *>(sh + 4);
 
     const int tid = threadIdx.x;
     if (TABLE)
         for (int k = tid; k < a.tab.n; k += kNT) tab[k] = a.tab.AG1[k];
-
-    const float c0 = TABLE ? 2.0f : a.eps2;
-    const u64 c0v = pk2(c0, c0);
-    const float scf = TABLE && !CELL ? (float)a.tab.scale : 1.0f;
     const int nitems = a.nitems >= 0 ? a.nitems : (int)*a.nitems_dev;
-    auto RH = [&](int p, int k) -> u64 & { return run[(8 * p + k) * kNT + tid]; };
-    auto RL = [&](int p, int k) -> u64 & { return run[(8 * p + 4 + k) * kNT + tid]; };
 
     // the next item is claimed while the current one runs (kept in a
     // register of thread 0), so the queue's atomic latency overlaps work
@@ -59,193 +277,15 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
         const int item = sh[0];
         if (item >= nitems) break;
         const GroupItem it = a.items[item];
-        const long long jb = a.j_off[it.group], je = a.j_off[it.group + 1];
-        double4 c = make_double4(0, 0, 0, 0);
-        if (!CELL) c = a.gctr[it.group];
-
-        // thread layout: nsets sets of 2*NP i-particles, L lanes per set
-        const int nsets = (it.ni + 2 * NP - 1) / (2 * NP);
-        int L = kNT / (nsets > 0 ? nsets : 1);
-        L = L >= 32 ? 32 : L >= 16 ? 16 : L >= 8 ? 8 : L >= 4 ? 4 : L >= 2 ? 2 : 1;
-        const int set = tid / L, lane = tid % L;
-        const bool active = set < nsets;
-
-        u64 xi[NP], yi[NP], zi[NP];
-        u64 ax[NP], ay[NP], az[NP], ph[NP];
-#pragma unroll
-        for (int p = 0; p < NP; ++p) {
-            float fx[2] = {0, 0}, fy[2] = {0, 0}, fz[2] = {0, 0};
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                int k = set * 2 * NP + 2 * p + q;
-                if (active && k < it.ni) {
-                    if (CELL) {
-                        float4 o = a.xo[it.i0 + k];
-                        fx[q] = o.x; fy[q] = o.y; fz[q] = o.z;
-                    } else {
-                        double4 v = a.xi[it.i0 + k];
-                        fx[q] = (float)(v.x - c.x) * scf;
-                        fy[q] = (float)(v.y - c.y) * scf;
-                        fz[q] = (float)(v.z - c.z) * scf;
-                    }
-                }
-            }
-            xi[p] = pk2(fx[0], fx[1]);
-            yi[p] = pk2(fy[0], fy[1]);
-            zi[p] = pk2(fz[0], fz[1]);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) RH(p, k) = RL(p, k) = 0ull;
-        }
-
-        // register prefetch of one tile of records
-        double4 rec[CELL ? 1 : kPerThread];
-        float4 rc32[CELL ? kPerThread : 1];
-        int code[CELL ? kPerThread : 1];
-        auto fetch = [&](long long t0) {
-#pragma unroll
-            for (int r = 0; r < kPerThread; ++r) {
-                long long e = t0 + r * kNT + tid;
-                bool ok = e < je;
-                int raw = ok ? a.jlist[e] : 0;
-                long long j = raw & 0x07ffffff;
-                if (ok && j >= a.nj) {         // bad index: record it, contribute nothing
-                    report(a.status, kStatusBadIndex, 2);
-                    ok = false;
-                }
-                if (CELL) {
-                    rc32[r] = ok ? __ldg(a.xo + j) : make_float4(0, 0, 0, -1.0f);
-                    code[r] = (int)(((unsigned)raw) >> 27);
-                } else {
-                    rec[r] = ok ? ldg_d4(a.jrec + j) : make_double4(0, 0, 0, -1.0);
-                }
-            }
-        };
-        fetch(jb);
-        for (long long t0 = jb; t0 < je; t0 += kTJG) {
-            // publish the prefetched tile as FP32 offsets in the i frame
-#pragma unroll
-            for (int r = 0; r < kPerThread; ++r) {
-                const int e = r * kNT + tid;
-                float x, y, z, m;
-                bool real = CELL ? rc32[r].w >= 0.0f : rec[r].w >= 0.0;
-                if (real && CELL) {
-                    const int cd = code[r];
-                    x = fmaf((float)(cd / 9 - 1), a.cell_h, rc32[r].x);
-                    y = fmaf((float)((cd / 3) % 3 - 1), a.cell_h, rc32[r].y);
-                    z = fmaf((float)(cd % 3 - 1), a.cell_h, rc32[r].z);
-                    m = rc32[r].w;
-                } else if (real) {
-                    x = (float)(rec[r].x - c.x) * scf;
-                    y = (float)(rec[r].y - c.y) * scf;
-                    z = (float)(rec[r].z - c.z) * scf;
-                    m = (float)rec[r].w;
-                } else {   // padding: zero mass far away contributes exactly 0
-                    x = y = z = 1.0e4f;
-                    m = 0.0f;
-                }
-                cvt[4 * e + 0] = pk2(x, x);
-                cvt[4 * e + 1] = pk2(y, y);
-                cvt[4 * e + 2] = pk2(z, z);
-                cvt[4 * e + 3] = pk2(m, m);
-            }
-            __syncthreads();
-            if (t0 + kTJG < je) fetch(t0 + kTJG);   // loads in flight during the compute
-            long long nv = je - t0;
-            if (nv > kTJG) nv = kTJG;
-            if (active) {
-#pragma unroll
-                for (int p = 0; p < NP; ++p) ax[p] = ay[p] = az[p] = ph[p] = 0ull;
-                const int nv_lane = (int)nv;
-#pragma unroll 2
-                for (int e = lane; e < nv_lane; e += L) {
-                    const ulonglong2 xy = reinterpret_cast<const ulonglong2 *>(cvt)[2 * e];
-                    const ulonglong2 zm = reinterpret_cast<const ulonglong2 *>(cvt)[2 * e + 1];
-#pragma unroll
-                    for (int p = 0; p < NP; ++p) {
-                        const u64 dx = f2sub(xy.x, xi[p]);
-                        const u64 dy = f2sub(xy.y, yi[p]);
-                        const u64 dz = f2sub(zm.x, zi[p]);
-                        u64 r2 = f2fma(dx, dx, c0v);
-                        r2 = f2fma(dy, dy, r2);
-                        r2 = f2fma(dz, dz, r2);
-                        float ra, rb;
-                        up2(r2, ra, rb);
-                        if (!TABLE) {
-                            float qa = rsq(ra), qb = rsq(rb);
-                            qa = ra > 0.0f ? qa : 0.0f;     // eps = 0: coincident pair adds nothing
-                            qb = rb > 0.0f ? qb : 0.0f;
-                            const u64 q = pk2(qa, qb);
-                            const u64 mq = f2mul(zm.y, q);
-                            const u64 mq3 = f2mul(mq, f2mul(q, q));
-                            ph[p] = f2sub(ph[p], mq);
-                            ax[p] = f2fma(mq3, dx, ax[p]);
-                            ay[p] = f2fma(mq3, dy, ay[p]);
-                            az[p] = f2fma(mq3, dz, az[p]);
-                        } else {
-                            ra = fminf(ra, a.tab.s_max);
-                            rb = fminf(rb, a.tab.s_max);
-                            const float2 ta = tab[(__float_as_uint(ra) >> a.tab.shift) - a.tab.base];
-                            const float2 tb = tab[(__float_as_uint(rb) >> a.tab.shift) - a.tab.base];
-                            const u64 g = f2fma(pk2(ra, rb), pk2(ta.y, tb.y), pk2(ta.x, tb.x));
-                            const u64 mg = f2mul(zm.y, g);
-                            ax[p] = f2fma(mg, dx, ax[p]);
-                            ay[p] = f2fma(mg, dy, ay[p]);
-                            az[p] = f2fma(mg, dz, az[p]);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int p = 0; p < NP; ++p) {
-                    fold2(RH(p, 0), RL(p, 0), ax[p]);
-                    fold2(RH(p, 1), RL(p, 1), ay[p]);
-                    fold2(RH(p, 2), RL(p, 2), az[p]);
-                    if (!TABLE) fold2(RH(p, 3), RL(p, 3), ph[p]);
-                }
-            }
-            __syncthreads();   // everyone done with this tile before it is overwritten
-        }
-
-        // combine the L lanes of each set: (hi, lo) pairs merged with FP32
-        // TwoSum across lanes (FP64 would dominate small items on GB300),
-        // one conversion to FP64 on the writing lane
-#pragma unroll
-        for (int p = 0; p < NP; ++p) {
-            float h[8], l[8];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                up2(RH(p, k), h[2 * k], h[2 * k + 1]);
-                up2(RL(p, k), l[2 * k], l[2 * k + 1]);
-            }
-            for (int off = L >> 1; off > 0; off >>= 1) {
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    if (TABLE && (k == 6 || k == 7)) continue;   // no potential
-                    const float oh = __shfl_xor_sync(0xffffffffu, h[k], off);
-                    const float ol = __shfl_xor_sync(0xffffffffu, l[k], off);
-                    float sm, er;
-                    two_sum(h[k], oh, sm, er);
-                    h[k] = sm;
-                    l[k] = __fadd_rn(l[k], __fadd_rn(ol, er));
-                }
-            }
-            if (active && lane == 0) {
-                double v[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) v[k] = (double)h[k] + (double)l[k];
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    int k = set * 2 * NP + 2 * p + q;
-                    if (k < it.ni) {
-                        long long i = it.i0 + k;
-                        long long o = a.perm ? (long long)a.perm[i] : i;
-                        a.acc[3 * o] = v[0 + q] * a.accscale;
-                        a.acc[3 * o + 1] = v[2 + q] * a.accscale;
-                        a.acc[3 * o + 2] = v[4 + q] * a.accscale;
-                        if (a.pot) a.pot[o] = TABLE ? 0.0 : v[6 + q];
-                    }
-                }
+        if (NPMAX > 1 && it.ni <= kNT * NPMAX) {
+            const ItemShape big = item_shape(it.ni, NPMAX);
+            const ItemShape small = item_shape(it.ni, NPMAX / 2);
+            if (small.nsets <= 4 * small.spw && small.nsets * small.L > big.nsets * big.L) {
+                group_item<(NPMAX > 1 ? NPMAX / 2 : 1), TABLE, CELL>(a, it, small, cvt, run, tab, tid);
+                continue;
             }
         }
+        group_item<NPMAX, TABLE, CELL>(a, it, item_shape(it.ni, NPMAX), cvt, run, tab, tid);
     }
 }
 

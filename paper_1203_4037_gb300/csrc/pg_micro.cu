@@ -1,0 +1,136 @@
+// pg_micro.cu -- measured ceilings for the roofline: throughput of scalar
+// FP32 FMA chains, packed FP32x2 FMA chains, MUFU rsqrt chains, and the
+// Newton pair term's exact instruction mix with every operand in registers
+// (no shared or global memory), each timed with CUDA events.
+#include <cuda_runtime.h>
+
+#include "pg.h"
+#include "pg_device.cuh"
+
+namespace pg {
+namespace {
+
+constexpr int kChains = 8;
+constexpr int kMicroThreads = 256;
+constexpr int kSinkSize = 8192;
+
+// destination of the (practically never taken) store that keeps the work alive
+__device__ float g_micro_sink[kSinkSize];
+
+// kind 0: scalar FFMA; 1: packed FFMA2; 2: MUFU rsqrt; 3: the Newton pair mix
+__global__ void __launch_bounds__(kMicroThreads) k_micro(int kind, int iters, float seed)
+{
+    const float s = seed + threadIdx.x * 1e-7f;
+    float acc = 0.0f;
+    if (kind == 0) {
+        float x[kChains];
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) x[c] = s + c;
+        for (int it = 0; it < iters; ++it)
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) x[c] = __fmaf_rn(x[c], 0.999999f, 1e-7f);
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) acc += x[c];
+    } else if (kind == 1) {
+        u64 x[kChains];
+        const u64 a = pk2(0.999999f, 0.999998f), b = pk2(1e-7f, 2e-7f);
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) x[c] = pk2(s + c, s - c);
+        for (int it = 0; it < iters; ++it)
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) x[c] = f2fma(x[c], a, b);
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) {
+            float lo, hi;
+            up2(x[c], lo, hi);
+            acc += lo + hi;
+        }
+    } else if (kind == 2) {
+        float x[kChains];
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) x[c] = 1.5f + s + c;
+        for (int it = 0; it < iters; ++it)
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) x[c] = rsq(x[c]) + 1.0f;
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) acc += x[c];
+    } else {
+        // four i-pairs against a j that moves a little each iteration: the
+        // pair term of the all-pairs kernel (13 FP32x2 + 2 MUFU per pair)
+        u64 xi[4], yi[4], zi[4], ax[4], ay[4], az[4], ph[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            xi[p] = pk2(s + p, s - p);
+            yi[p] = pk2(0.5f * p, -0.25f * p);
+            zi[p] = pk2(0.1f, 0.2f * p);
+            ax[p] = ay[p] = az[p] = ph[p] = 0ull;
+        }
+        u64 xj = pk2(0.3f, 0.3f), yj = pk2(0.7f, 0.7f), zj = pk2(-0.2f, -0.2f), mj = pk2(1e-3f, 1e-3f);
+        const u64 e2 = pk2(1e-4f, 1e-4f), step = pk2(1e-6f, 1e-6f);
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const u64 dx = f2sub(xj, xi[p]), dy = f2sub(yj, yi[p]), dz = f2sub(zj, zi[p]);
+                u64 r2 = f2fma(dx, dx, e2);
+                r2 = f2fma(dy, dy, r2);
+                r2 = f2fma(dz, dz, r2);
+                float ra, rb;
+                up2(r2, ra, rb);
+                const u64 q = pk2(rsq(ra), rsq(rb));
+                const u64 mq = f2mul(mj, q);
+                const u64 mq3 = f2mul(mq, f2mul(q, q));
+                ph[p] = f2sub(ph[p], mq);
+                ax[p] = f2fma(mq3, dx, ax[p]);
+                ay[p] = f2fma(mq3, dy, ay[p]);
+                az[p] = f2fma(mq3, dz, az[p]);
+            }
+            xj = f2add(xj, step);
+        }
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            float a0, a1, b0, b1;
+            up2(f2add(f2add(ax[p], ay[p]), f2add(az[p], ph[p])), a0, a1);
+            up2(xi[p], b0, b1);
+            acc += a0 + a1 + b0 * 0.0f + b1 * 0.0f;
+        }
+    }
+    if (acc == 12345.678f && blockIdx.x < kSinkSize) g_micro_sink[blockIdx.x] = acc;
+}
+
+}  // namespace
+}  // namespace pg
+
+using namespace pg;
+
+extern "C" int pg_microbench(int kind, double *per_sm_clock, double *per_second)
+{
+    if (kind < 0 || kind > 3 || !per_sm_clock || !per_second) return PG_EINVAL;
+    int dev = 0, sms = 0, clk_khz = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { (void)cudaGetLastError(); return PG_ECUDA; }
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
+    const int blocks = sms * 8;
+    const int iters = kind == 2 ? 4096 : 16384;
+    // lane operations per thread per iteration: FFMA 8, FFMA2 16, rsqrt 8,
+    // Newton mix: 8 interactions (4 pairs x 2 lanes)
+    const double per_iter = kind == 0 ? 8.0 : kind == 1 ? 16.0 : kind == 2 ? 8.0 : 8.0;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return PG_ECUDA;
+    }
+    k_micro<<<blocks, kMicroThreads>>>(kind, 64, 0.5f);   // warm-up
+    cudaEventRecord(e0);
+    k_micro<<<blocks, kMicroThreads>>>(kind, iters, 0.5f);
+    cudaEventRecord(e1);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess || ms <= 0) { (void)cudaGetLastError(); return PG_ECUDA; }
+    const double ops = (double)blocks * kMicroThreads * iters * per_iter;
+    *per_second = ops / (ms * 1e-3);
+    *per_sm_clock = *per_second / ((double)sms * clk_khz * 1e3);
+    return PG_OK;
+}
