@@ -76,7 +76,7 @@ struct pg_ctx {
     bool have_groups = false;
     long long ngroups = 0;
     std::vector<long long> h_ioff, h_joff;
-    DevBuf g_ioff, g_joff, g_jlist, g_items, g_ctr, g_queue;
+    DevBuf g_ioff, g_joff, g_jlist, g_items, g_ctr, g_queue, g_jhl, g_ihl;
     int g_nitems = 0;
     int g_items_np = 0;
     long long g_pairs = 0;
@@ -338,7 +338,8 @@ void pg_destroy(pg_ctx *c)
     DevBuf *bufs[] = {&c->G0, &c->G1, &c->AG1, &c->jrec, &c->stage, &c->xi, &c->xt, &c->ctr,
                       &c->skeys0, &c->skeys1, &c->svals0, &c->svals1, &c->shist, &c->ssums,
                       &c->sbbox, &c->acc, &c->pot, &c->part, &c->status, &c->g_ioff,
-                      &c->g_joff, &c->g_jlist, &c->g_items, &c->g_ctr, &c->g_queue,
+                      &c->g_joff, &c->g_jlist, &c->g_items, &c->g_ctr, &c->g_queue, &c->g_jhl,
+                      &c->g_ihl,
                       &c->c_wrapped, &c->c_xs, &c->c_xo, &c->c_perm, &c->c_start, &c->c_jcount,
                       &c->c_icount, &c->c_joff32, &c->c_joff, &c->c_ioff, &c->c_jlist,
                       &c->c_items_raw, &c->c_items, &c->c_ctr, &c->c_pairs, &c->bw_wj,
@@ -848,7 +849,8 @@ int launch_group_kernel(pg_ctx *c, const GroupArgs &g, bool cell)
     int grid = c->sms * per;
     PG_CUDA(c, cudaMemsetAsync(c->g_queue.p, 0, sizeof(int), c->stream));
     if (c->timing) PG_CUDA(c, cudaEventRecord(c->tk0, c->stream));
-    PG_CUDA(c, launch_groups(g, grid, np, table, cell, groups_smem(np, table, c->ntab), c->stream));
+    PG_CUDA(c, launch_groups(g, grid, np, table, cell, !table && g.eps2 == 0.0f,
+                             groups_smem(np, table, c->ntab), c->stream));
     if (c->timing) PG_CUDA(c, cudaEventRecord(c->tk1, c->stream));
     c->timed = c->timing;
     c->last_grid = grid;
@@ -869,7 +871,14 @@ int enqueue_groups(pg_ctx *c, double *acc, double *pot)
     }
     PG_CUDA(c, launch_group_ctr((const double4 *)c->xi.p, (const long long *)c->g_ioff.p,
                                 c->ngroups, (double4 *)c->g_ctr.p, c->stream));
-    c->last_launches += 1;
+    // double-float copies of the j records and i positions for the FP32 differencing
+    long long nj = nj_of(c);
+    if ((rc = ensure(c, c->g_jhl, (size_t)std::max<long long>(nj, 1) * 32)) ||
+        (rc = ensure(c, c->g_ihl, (size_t)std::max<long long>(c->ni, 1) * 32)))
+        return rc;
+    PG_CUDA(c, launch_pack_hilo((const double4 *)c->jrec.p, nj, (float4 *)c->g_jhl.p, c->stream));
+    PG_CUDA(c, launch_pack_hilo((const double4 *)c->xi.p, c->ni, (float4 *)c->g_ihl.p, c->stream));
+    c->last_launches += 3;
     GroupArgs g = group_args(c);
     g.xi = (const double4 *)c->xi.p;
     g.jrec = (const double4 *)c->jrec.p;
@@ -877,6 +886,8 @@ int enqueue_groups(pg_ctx *c, double *acc, double *pot)
     g.jlist = (const int *)c->g_jlist.p;
     g.items = (const GroupItem *)c->g_items.p;
     g.gctr = (const double4 *)c->g_ctr.p;
+    g.jhl = (const float4 *)c->g_jhl.p;
+    g.ihl = (const float4 *)c->g_ihl.p;
     g.nitems = c->g_nitems;
     g.nj = nj_of(c);
     g.perm = nullptr;

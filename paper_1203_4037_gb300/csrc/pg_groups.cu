@@ -18,8 +18,12 @@ constexpr int kTJG = 512;          // j entries staged per step
 constexpr int kPerThread = kTJG / kNT;
 
 // Records come in two forms.
-//  CELL = false: FP64 (x, y, z, m) of any particle; the group's FP64 centre is
-//    subtracted in FP64 and the difference rounded once to FP32.
+//  CELL = false: any particle as a double-float pair, hi = (x, y, z, m) in
+//    FP32 and lo = the FP32 residual of x - hi (built once per run from the
+//    FP64 record). The group's FP64 centre is split the same way and the
+//    offset formed as (hi_j - c_hi) + (lo_j - c_lo) in FP32: the same
+//    rounding as differencing in FP64 and rounding once, without FP64
+//    instructions (GB300 runs FP64 at about two operations per SM-clock).
 //  CELL = true: the periodic cell list's FP32 record (o, m), o = the
 //    particle's offset from its cell's corner in scaled units; a j-list entry
 //    carries the direction (dx, dy, dz) in {-1, 0, 1}^3 from the i-cell to the
@@ -48,13 +52,20 @@ __device__ __forceinline__ ItemShape item_shape(int ni, int np)
     return s;
 }
 
-template <int NP, bool TABLE, bool CELL>
+template <int NP, bool TABLE, bool CELL, bool ZSAFE>
 __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &it, const ItemShape sh,
-                                           u64 *cvt, u64 *run, const float2 *tab, int tid)
+                                           u64 *cvt, u64 *run, const float2 *tab, const float4 *dirt,
+                                           int tid)
 {
     const long long jb = a.j_off[it.group], je = a.j_off[it.group + 1];
     double4 c = make_double4(0, 0, 0, 0);
-    if (!CELL) c = a.gctr[it.group];
+    float chx = 0, chy = 0, chz = 0, clx = 0, cly = 0, clz = 0;   // centre as hi + lo
+    if (!CELL) {
+        c = a.gctr[it.group];
+        chx = (float)c.x; clx = (float)(c.x - (double)chx);
+        chy = (float)c.y; cly = (float)(c.y - (double)chy);
+        chz = (float)c.z; clz = (float)(c.z - (double)chz);
+    }
     const float c0 = TABLE ? 2.0f : a.eps2;
     const u64 c0v = pk2(c0, c0);
     const float scf = TABLE && !CELL ? (float)a.tab.scale : 1.0f;
@@ -79,10 +90,10 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
                     float4 o = a.xo[it.i0 + k];
                     fx[q] = o.x; fy[q] = o.y; fz[q] = o.z;
                 } else {
-                    double4 v = a.xi[it.i0 + k];
-                    fx[q] = (float)(v.x - c.x) * scf;
-                    fy[q] = (float)(v.y - c.y) * scf;
-                    fz[q] = (float)(v.z - c.z) * scf;
+                    const float4 h = a.ihl[2 * (it.i0 + k)], l = a.ihl[2 * (it.i0 + k) + 1];
+                    fx[q] = ((h.x - chx) + (l.x - clx)) * scf;
+                    fy[q] = ((h.y - chy) + (l.y - cly)) * scf;
+                    fz[q] = ((h.z - chz) + (l.z - clz)) * scf;
                 }
             }
         }
@@ -94,8 +105,8 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
     }
 
     // register prefetch of one tile of records
-    double4 rec[CELL ? 1 : kPerThread];
-    float4 rc32[CELL ? kPerThread : 1];
+    float4 rc32[kPerThread];
+    float4 rlo[CELL ? 1 : kPerThread];
     int code[CELL ? kPerThread : 1];
     auto fetch = [&](long long t0) {
 #pragma unroll
@@ -112,7 +123,8 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
                 rc32[r] = ok ? __ldg(a.xo + j) : make_float4(0, 0, 0, -1.0f);
                 code[r] = (int)(((unsigned)raw) >> 27);
             } else {
-                rec[r] = ok ? ldg_d4(a.jrec + j) : make_double4(0, 0, 0, -1.0);
+                rc32[r] = ok ? __ldg(a.jhl + 2 * j) : make_float4(0, 0, 0, -1.0f);
+                rlo[r] = ok ? __ldg(a.jhl + 2 * j + 1) : make_float4(0, 0, 0, 0);
             }
         }
     };
@@ -123,26 +135,28 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
         for (int r = 0; r < kPerThread; ++r) {
             const int e = r * kNT + tid;
             float x, y, z, m;
-            bool real = CELL ? rc32[r].w >= 0.0f : rec[r].w >= 0.0;
+            const bool real = rc32[r].w >= 0.0f;
             if (real && CELL) {
-                const int cd = code[r];
-                x = fmaf((float)(cd / 9 - 1), a.cell_h, rc32[r].x);
-                y = fmaf((float)((cd / 3) % 3 - 1), a.cell_h, rc32[r].y);
-                z = fmaf((float)(cd % 3 - 1), a.cell_h, rc32[r].z);
+                const float4 dv = dirt[code[r]];     // direction x cell side, scaled
+                x = rc32[r].x + dv.x;
+                y = rc32[r].y + dv.y;
+                z = rc32[r].z + dv.z;
                 m = rc32[r].w;
             } else if (real) {
-                x = (float)(rec[r].x - c.x) * scf;
-                y = (float)(rec[r].y - c.y) * scf;
-                z = (float)(rec[r].z - c.z) * scf;
-                m = (float)rec[r].w;
+                x = ((rc32[r].x - chx) + (rlo[r].x - clx)) * scf;
+                y = ((rc32[r].y - chy) + (rlo[r].y - cly)) * scf;
+                z = ((rc32[r].z - chz) + (rlo[r].z - clz)) * scf;
+                m = rc32[r].w;
             } else {   // padding: zero mass far away contributes exactly 0
                 x = y = z = 1.0e4f;
                 m = 0.0f;
             }
-            cvt[4 * e + 0] = pk2(x, x);
-            cvt[4 * e + 1] = pk2(y, y);
-            cvt[4 * e + 2] = pk2(z, z);
-            cvt[4 * e + 3] = pk2(m, m);
+            // separate {x, y} and {z, m} arrays: lanes of a set that read
+            // consecutive j then read consecutive 16-byte words
+            cvt[2 * e + 0] = pk2(x, x);
+            cvt[2 * e + 1] = pk2(y, y);
+            cvt[2 * kTJG + 2 * e + 0] = pk2(z, z);
+            cvt[2 * kTJG + 2 * e + 1] = pk2(m, m);
         }
         __syncthreads();
         if (t0 + kTJG < je) fetch(t0 + kTJG);   // loads in flight during the compute
@@ -154,8 +168,8 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
             const int nv_lane = (int)nv;
 #pragma unroll 2
             for (int e = lane; e < nv_lane; e += L) {
-                const ulonglong2 xy = reinterpret_cast<const ulonglong2 *>(cvt)[2 * e];
-                const ulonglong2 zm = reinterpret_cast<const ulonglong2 *>(cvt)[2 * e + 1];
+                const ulonglong2 xy = reinterpret_cast<const ulonglong2 *>(cvt)[e];
+                const ulonglong2 zm = reinterpret_cast<const ulonglong2 *>(cvt)[kTJG + e];
 #pragma unroll
                 for (int p = 0; p < NP; ++p) {
                     const u64 dx = f2sub(xy.x, xi[p]);
@@ -168,8 +182,10 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
                     up2(r2, ra, rb);
                     if (!TABLE) {
                         float qa = rsq(ra), qb = rsq(rb);
-                        qa = ra > 0.0f ? qa : 0.0f;     // eps = 0: coincident pair adds nothing
-                        qb = rb > 0.0f ? qb : 0.0f;
+                        if (ZSAFE) {   // eps = 0: a coincident pair adds nothing
+                            qa = ra > 0.0f ? qa : 0.0f;
+                            qb = rb > 0.0f ? qb : 0.0f;
+                        }
                         const u64 q = pk2(qa, qb);
                         const u64 mq = f2mul(zm.y, q);
                         const u64 mq3 = f2mul(mq, f2mul(q, q));
@@ -249,18 +265,22 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
 
 // NPMAX: the largest i-pair count per thread; items whose shape uses the
 // threads better with half of it run with NPMAX / 2
-template <int NPMAX, bool TABLE, bool CELL>
+template <int NPMAX, bool TABLE, bool CELL, bool ZSAFE>
 __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     u64 *cvt = reinterpret_cast<u64 *>(smem);                            // [kTJG][4]
     u64 *run = cvt + 4 * kTJG;                                           // [8 NPMAX][kNT]
-    int *sh = reinterpret_cast<int *>(run + 8 * NPMAX * kNT);            // item slot
+    float4 *dirt = reinterpret_cast<float4 *>(run + 8 * NPMAX * kNT);    // [27] cell mode
+    int *sh = reinterpret_cast<int *>(dirt + 28);                        // item slot
     float2 *tab = reinterpret_cast<float2 *>(sh + 4);
 
     const int tid = threadIdx.x;
     if (TABLE)
         for (int k = tid; k < a.tab.n; k += kNT) tab[k] = a.tab.AG1[k];
+    if (CELL && tid < 27)
+        dirt[tid] = make_float4((float)(tid / 9 - 1) * a.cell_h, (float)((tid / 3) % 3 - 1) * a.cell_h,
+                                (float)(tid % 3 - 1) * a.cell_h, 0.0f);
     const int nitems = a.nitems >= 0 ? a.nitems : (int)*a.nitems_dev;
 
     // the next item is claimed while the current one runs (kept in a
@@ -281,87 +301,111 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
             const ItemShape big = item_shape(it.ni, NPMAX);
             const ItemShape small = item_shape(it.ni, NPMAX / 2);
             if (small.nsets <= 4 * small.spw && small.nsets * small.L > big.nsets * big.L) {
-                group_item<(NPMAX > 1 ? NPMAX / 2 : 1), TABLE, CELL>(a, it, small, cvt, run, tab, tid);
+                group_item<(NPMAX > 1 ? NPMAX / 2 : 1), TABLE, CELL, ZSAFE>(a, it, small, cvt, run,
+                                                                             tab, dirt, tid);
                 continue;
             }
         }
-        group_item<NPMAX, TABLE, CELL>(a, it, item_shape(it.ni, NPMAX), cvt, run, tab, tid);
+        group_item<NPMAX, TABLE, CELL, ZSAFE>(a, it, item_shape(it.ni, NPMAX), cvt, run, tab, dirt,
+                                              tid);
     }
 }
 
 // ------------------------------------------------------------------ host
 size_t groups_smem(int np, bool table, int ntab)
 {
-    size_t s = kTJG * 4 * sizeof(u64) + 8 * np * kNT * sizeof(u64) + 16;
+    size_t s = kTJG * 4 * sizeof(u64) + 8 * np * kNT * sizeof(u64) + 28 * 16 + 16;
     if (table) s += (size_t)ntab * sizeof(float2);
     return s;
 }
 
 int groups_bi(int np) { return kNT * 2 * np; }
 
-template <int NP, bool TABLE, bool CELL>
+template <int NP, bool TABLE, bool CELL, bool ZSAFE>
 static cudaError_t configure_g()
 {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_groups<NP, TABLE, CELL>,
+    cudaError_t e = cudaFuncSetAttribute(k_groups<NP, TABLE, CELL, ZSAFE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)groups_smem(NP, TABLE, 1 << 13));
     done = e == cudaSuccess;
     return e;
 }
 
-template <int NP, bool TABLE, bool CELL>
+template <int NP, bool TABLE, bool CELL, bool ZSAFE>
 static int occ_g(size_t smem)
 {
-    if (configure_g<NP, TABLE, CELL>() != cudaSuccess) return 1;
+    if (configure_g<NP, TABLE, CELL, ZSAFE>() != cudaSuccess) return 1;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_groups<NP, TABLE, CELL>, kNT, smem) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_groups<NP, TABLE, CELL, ZSAFE>, kNT,
+                                                      smem) != cudaSuccess)
         return 1;
     return nb > 0 ? nb : 1;
+}
+
+template <int NP>
+static int occ_np(bool table, bool cell, size_t smem)
+{
+    if (!table) return occ_g<NP, false, false, false>(smem);
+    return cell ? occ_g<NP, true, true, false>(smem) : occ_g<NP, true, false, false>(smem);
 }
 
 int groups_max_blocks_per_sm(int np, bool table, int ntab, bool cell)
 {
     size_t smem = groups_smem(np, table, ntab);
-    if (np == 1) {
-        if (!table) return occ_g<1, false, false>(smem);
-        return cell ? occ_g<1, true, true>(smem) : occ_g<1, true, false>(smem);
-    }
-    if (np == 4) {
-        if (!table) return occ_g<4, false, false>(smem);
-        return cell ? occ_g<4, true, true>(smem) : occ_g<4, true, false>(smem);
-    }
-    if (!table) return occ_g<2, false, false>(smem);
-    return cell ? occ_g<2, true, true>(smem) : occ_g<2, true, false>(smem);
+    return np == 1 ? occ_np<1>(table, cell, smem)
+         : np == 4 ? occ_np<4>(table, cell, smem)
+                   : occ_np<2>(table, cell, smem);
 }
 
-template <int NP, bool TABLE, bool CELL>
+template <int NP, bool TABLE, bool CELL, bool ZSAFE>
 static cudaError_t launch_g(const GroupArgs &g, int grid, size_t smem, cudaStream_t st)
 {
-    cudaError_t e = configure_g<NP, TABLE, CELL>();
+    cudaError_t e = configure_g<NP, TABLE, CELL, ZSAFE>();
     if (e != cudaSuccess) return e;
-    k_groups<NP, TABLE, CELL><<<grid, kNT, smem, st>>>(g);
+    k_groups<NP, TABLE, CELL, ZSAFE><<<grid, kNT, smem, st>>>(g);
     return cudaGetLastError();
 }
 
-cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, bool cell,
+template <int NP>
+static cudaError_t launch_gnp(const GroupArgs &g, int grid, bool table, bool cell, bool zsafe,
+                              size_t smem, cudaStream_t st)
+{
+    if (!table) return zsafe ? launch_g<NP, false, false, true>(g, grid, smem, st)
+                             : launch_g<NP, false, false, false>(g, grid, smem, st);
+    return cell ? launch_g<NP, true, true, false>(g, grid, smem, st)
+                : launch_g<NP, true, false, false>(g, grid, smem, st);
+}
+
+cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, bool cell, bool zsafe,
                           size_t smem, cudaStream_t st)
 {
     if (grid <= 0) return cudaSuccess;
     if (cell && !table) return cudaErrorInvalidValue;
-    if (np == 1) {
-        if (!table) return launch_g<1, false, false>(g, grid, smem, st);
-        return cell ? launch_g<1, true, true>(g, grid, smem, st) : launch_g<1, true, false>(g, grid, smem, st);
-    }
-    if (np == 4) {
-        if (!table) return launch_g<4, false, false>(g, grid, smem, st);
-        return cell ? launch_g<4, true, true>(g, grid, smem, st) : launch_g<4, true, false>(g, grid, smem, st);
-    }
-    if (np != 2) return cudaErrorInvalidValue;
-    if (!table) return launch_g<2, false, false>(g, grid, smem, st);
-    return cell ? launch_g<2, true, true>(g, grid, smem, st) : launch_g<2, true, false>(g, grid, smem, st);
+    if (np == 1) return launch_gnp<1>(g, grid, table, cell, zsafe, smem, st);
+    if (np == 2) return launch_gnp<2>(g, grid, table, cell, zsafe, smem, st);
+    if (np == 4) return launch_gnp<4>(g, grid, table, cell, zsafe, smem, st);
+    return cudaErrorInvalidValue;
+}
+
+// double-float records: (hi, m) then (lo, 0) per particle, lo = x - hi
+__global__ void k_pack_hilo(const double4 *__restrict__ in, long long n, float4 *__restrict__ out)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double4 v = in[i];
+    float hx = (float)v.x, hy = (float)v.y, hz = (float)v.z;
+    out[2 * i] = make_float4(hx, hy, hz, (float)v.w);
+    out[2 * i + 1] = make_float4((float)(v.x - (double)hx), (float)(v.y - (double)hy),
+                                 (float)(v.z - (double)hz), 0.0f);
+}
+
+cudaError_t launch_pack_hilo(const double4 *in, long long n, float4 *out, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_pack_hilo<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, n, out);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ prep

@@ -83,6 +83,8 @@ struct GroupArgs {
     long long nj;          // number of j records (bounds check)
     float eps2;
     TableDev tab;
+    const float4 *jhl;     // FP64 mode: j records as (hi, m), (lo, 0) FP32 pairs
+    const float4 *ihl;     // FP64 mode: i positions as (hi, -), (lo, -) FP32 pairs
     const float4 *xo;      // cell mode: FP32 offset records (o, m) in scaled units
     float cell_h;          // cell mode: cell side in scaled units
     const unsigned *perm;  // i index -> output index (nullptr: identity)
@@ -150,8 +152,9 @@ cudaError_t launch_table_prep(const float *G0, const float *G1, float2 *AG1, int
 cudaError_t launch_table_from_values(const float *v, float *G0, float *G1, int E, int F,
                                      cudaStream_t st);
 
-cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, bool cell,
+cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, bool cell, bool zsafe,
                           size_t smem, cudaStream_t st);
+cudaError_t launch_pack_hilo(const double4 *in, long long n, float4 *out, cudaStream_t st);
 size_t groups_smem(int np, bool table, int ntab);
 int groups_bi(int np);
 int groups_max_blocks_per_sm(int np, bool table, int ntab, bool cell);
