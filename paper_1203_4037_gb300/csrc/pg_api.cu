@@ -78,6 +78,7 @@ struct pg_ctx {
     std::vector<long long> h_ioff, h_joff;
     DevBuf g_ioff, g_joff, g_jlist, g_items, g_ctr, g_queue, g_jhl, g_ihl;
     int g_nitems = 0;
+    int g_warp_from = 0;
     int g_items_np = 0;
     long long g_pairs = 0;
     long long g_maxj = -1;       // largest j index listed
@@ -813,9 +814,18 @@ int upload_group_items(pg_ctx *c)
             cost.push_back((long long)it.ni * nj);
         }
     }
+    // CTA-sized items first, longest first, then the warp-sized ones
+    // (at most 32 i-particles), longest first
+    const int kWarpNi = 32;
     std::vector<size_t> order(items.size());
     for (size_t k = 0; k < order.size(); ++k) order[k] = k;
-    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+        bool sa = items[a].ni <= kWarpNi, sb = items[b].ni <= kWarpNi;
+        if (sa != sb) return !sa;
+        return cost[a] > cost[b];
+    });
+    c->g_warp_from = 0;
+    for (const GroupItem &it : items) c->g_warp_from += it.ni > kWarpNi ? 1 : 0;
     std::vector<GroupItem> sorted(items.size());
     for (size_t k = 0; k < order.size(); ++k) sorted[k] = items[order[k]];
     int rc;
@@ -889,6 +899,7 @@ int enqueue_groups(pg_ctx *c, double *acc, double *pot)
     g.jhl = (const float4 *)c->g_jhl.p;
     g.ihl = (const float4 *)c->g_ihl.p;
     g.nitems = c->g_nitems;
+    g.warp_from = c->g_warp_from;
     g.nj = nj_of(c);
     g.perm = nullptr;
     g.acc = acc;
@@ -919,7 +930,7 @@ int enqueue_cells(pg_ctx *c, double *acc, double *pot)
         (rc = ensure(c, c->c_ioff, (ncell + 1) * 4)) || (rc = ensure(c, c->c_jlist, 27 * n * 4)) ||
         (rc = ensure(c, c->c_items_raw, item_cap * sizeof(GroupItem))) ||
         (rc = ensure(c, c->c_items, item_cap * sizeof(GroupItem))) ||
-        (rc = ensure(c, c->c_ctr, ncell * 32)) || (rc = ensure(c, c->c_pairs, 8)) ||
+        (rc = ensure(c, c->c_ctr, ncell * 32)) || (rc = ensure(c, c->c_pairs, 16)) ||
         (rc = ensure(c, c->skeys0, sn * 4)) || (rc = ensure(c, c->skeys1, sn * 4)) ||
         (rc = ensure(c, c->svals0, sn * 4)) || (rc = ensure(c, c->svals1, sn * 4)) ||
         (rc = ensure(c, c->shist, hn * 4)) || (rc = ensure(c, c->ssums, nb * 4)) ||
@@ -942,6 +953,7 @@ int enqueue_cells(pg_ctx *c, double *acc, double *pot)
     s.ctr = (double4 *)c->c_ctr.p;
     s.item_cap = item_cap;
     s.pairs = (unsigned long long *)c->c_pairs.p;
+    s.ncta = (unsigned *)((char *)c->c_pairs.p + 8);
     c->sort.keys[0] = (unsigned *)c->skeys0.p;
     c->sort.keys[1] = (unsigned *)c->skeys1.p;
     c->sort.vals[0] = (unsigned *)c->svals0.p;
@@ -960,6 +972,8 @@ int enqueue_cells(pg_ctx *c, double *acc, double *pot)
     g.gctr = s.ctr;
     g.nitems = -1;
     g.nitems_dev = s.ioff + ncell;
+    g.warp_from = -1;
+    g.warp_from_dev = s.ncta;
     g.nj = n;
     g.xo = s.xo;
     g.cell_h = (float)(c->box / nc * c->scale);

@@ -36,6 +36,34 @@ constexpr int kPerThread = kTJG / kNT;
 // lanes are combined by a segmented shuffle reduction at the end. NP (i-pairs
 // per thread) is chosen per item, 2 or 4, for the better thread use.
 
+// floor(a / b) for 0 <= a < 2^16 and 1 <= b <= 128 as one high multiply by
+// ceil(2^32 / b) (exact in that range), not the generic division sequence
+__constant__ unsigned kRecip[129] = {
+    0u, 0u, 2147483648u, 1431655766u, 1073741824u, 858993460u, 715827883u,
+    613566757u, 536870912u, 477218589u, 429496730u, 390451573u, 357913942u, 330382100u,
+    306783379u, 286331154u, 268435456u, 252645136u, 238609295u, 226050911u, 214748365u,
+    204522253u, 195225787u, 186737709u, 178956971u, 171798692u, 165191050u, 159072863u,
+    153391690u, 148102321u, 143165577u, 138547333u, 134217728u, 130150525u, 126322568u,
+    122713352u, 119304648u, 116080198u, 113025456u, 110127367u, 107374183u, 104755300u,
+    102261127u, 99882961u, 97612894u, 95443718u, 93368855u, 91382283u, 89478486u,
+    87652394u, 85899346u, 84215046u, 82595525u, 81037119u, 79536432u, 78090315u,
+    76695845u, 75350304u, 74051161u, 72796056u, 71582789u, 70409300u, 69273667u,
+    68174085u, 67108864u, 66076420u, 65075263u, 64103990u, 63161284u, 62245903u,
+    61356676u, 60492498u, 59652324u, 58835169u, 58040099u, 57266231u, 56512728u,
+    55778797u, 55063684u, 54366675u, 53687092u, 53024288u, 52377650u, 51746594u,
+    51130564u, 50529028u, 49941481u, 49367441u, 48806447u, 48258060u, 47721859u,
+    47197443u, 46684428u, 46182445u, 45691142u, 45210183u, 44739243u, 44278014u,
+    43826197u, 43383509u, 42949673u, 42524429u, 42107523u, 41698712u, 41297763u,
+    40904451u, 40518560u, 40139882u, 39768216u, 39403370u, 39045158u, 38693400u,
+    38347923u, 38008561u, 37675152u, 37347542u, 37025581u, 36709123u, 36398028u,
+    36092163u, 35791395u, 35495598u, 35204650u, 34918434u, 34636834u, 34359739u,
+    34087043u, 33818641u, 33554432u};
+
+__device__ __forceinline__ int div_small(int a, int b)
+{
+    return b == 1 ? a : (int)__umulhi((unsigned)a, kRecip[b]);
+}
+
 struct ItemShape {
     int nsets, L, spw;
 };
@@ -44,12 +72,22 @@ __device__ __forceinline__ ItemShape item_shape(int ni, int np)
 {
     ItemShape s;
     s.nsets = (ni + 2 * np - 1) / (2 * np);
-    int L = kNT / (s.nsets > 0 ? s.nsets : 1);
+    int L = div_small(kNT, s.nsets > 0 ? s.nsets : 1);
     L = L > 32 ? 32 : L < 1 ? 1 : L;
-    while (L > 1 && (kNT / 32) * (32 / L) < s.nsets) --L;
+    while (L > 1 && (kNT / 32) * div_small(32, L) < s.nsets) --L;
     s.L = L;
-    s.spw = 32 / L;
+    s.spw = div_small(32, L);
     return s;
+}
+
+// one {A, G1} table entry for s in [2, s_max]: byte offset from the FP32
+// bits of s by shift and mask, then a shared load (no integer multiply)
+__device__ __forceinline__ float2 tab_at(unsigned tbase, unsigned bits, int shift3)
+{
+    float2 v;
+    const unsigned addr = tbase + ((bits >> shift3) & ~7u);
+    asm("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+    return v;
 }
 
 template <int NP, bool TABLE, bool CELL, bool ZSAFE>
@@ -69,12 +107,15 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
     const float c0 = TABLE ? 2.0f : a.eps2;
     const u64 c0v = pk2(c0, c0);
     const float scf = TABLE && !CELL ? (float)a.tab.scale : 1.0f;
+    const int sh3 = a.tab.shift - 3;
+    const unsigned tb0 = smem_u32(tab) - (a.tab.base << 3);
     auto RH = [&](int p, int k) -> u64 & { return run[(8 * p + k) * kNT + tid]; };
     auto RL = [&](int p, int k) -> u64 & { return run[(8 * p + 4 + k) * kNT + tid]; };
 
     const int L = sh.L;
     const int wl = tid & 31;
-    const int set = (tid >> 5) * sh.spw + wl / L, lane = wl % L;
+    const int wq = div_small(wl, L);
+    const int set = (tid >> 5) * sh.spw + wq, lane = wl - wq * L;
     const bool active = wl < sh.spw * L && set < sh.nsets;
 
     u64 xi[NP], yi[NP], zi[NP];
@@ -196,8 +237,8 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
                     } else {
                         ra = fminf(ra, a.tab.s_max);
                         rb = fminf(rb, a.tab.s_max);
-                        const float2 ta = tab[(__float_as_uint(ra) >> a.tab.shift) - a.tab.base];
-                        const float2 tb = tab[(__float_as_uint(rb) >> a.tab.shift) - a.tab.base];
+                        const float2 ta = tab_at(tb0, __float_as_uint(ra), sh3);
+                        const float2 tb = tab_at(tb0, __float_as_uint(rb), sh3);
                         const u64 g = pk2(__fmaf_rn(ra, ta.y, ta.x), __fmaf_rn(rb, tb.y, tb.x));
                         const u64 mg = f2mul(zm.y, g);
                         ax[p] = f2fma(mg, dx, ax[p]);
@@ -263,6 +304,168 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
     }
 }
 
+// Warp mode: one warp evaluates one small item (at most kWarpItemNi
+// i-particles per pass, one i-pair per lane) with its own 4 KB slice of the
+// staging buffer and warp-level synchronisation only, so the warps of a CTA
+// work through small items independently instead of meeting at CTA barriers.
+constexpr int kWarpTJ = 128;        // j entries per warp-staged tile
+constexpr int kWarpItemNi = 32;     // items up to this size go to warp mode
+
+template <bool TABLE, bool CELL, bool ZSAFE>
+__device__ __forceinline__ void warp_item(const GroupArgs &a, const GroupItem &it, u64 *wcvt,
+                                          const float2 *tab, const float4 *dirt, int lane32)
+{
+    const long long jb = a.j_off[it.group], je = a.j_off[it.group + 1];
+    float chx = 0, chy = 0, chz = 0, clx = 0, cly = 0, clz = 0;
+    if (!CELL) {
+        const double4 c = a.gctr[it.group];
+        chx = (float)c.x; clx = (float)(c.x - (double)chx);
+        chy = (float)c.y; cly = (float)(c.y - (double)chy);
+        chz = (float)c.z; clz = (float)(c.z - (double)chz);
+    }
+    const float c0 = TABLE ? 2.0f : a.eps2;
+    const u64 c0v = pk2(c0, c0);
+    const float scf = TABLE && !CELL ? (float)a.tab.scale : 1.0f;
+    const int sh3 = a.tab.shift - 3;
+    const unsigned tb0 = smem_u32(tab) - (a.tab.base << 3);
+    ulonglong2 *sxy = reinterpret_cast<ulonglong2 *>(wcvt);            // [kWarpTJ]
+    ulonglong2 *szm = sxy + kWarpTJ;                                   // [kWarpTJ]
+
+    for (int i0 = 0; i0 < it.ni; i0 += 2 * 32) {
+        const int ni = min(2 * 32, it.ni - i0);
+        const int nsets = (ni + 1) / 2;
+        int L = div_small(32, nsets);
+        L = L < 1 ? 1 : L;
+        const int spw = div_small(32, L);
+        const int set = div_small(lane32, L), lane = lane32 - set * L;
+        const bool active = lane32 < spw * L && set < nsets;
+        float fx[2] = {0, 0}, fy[2] = {0, 0}, fz[2] = {0, 0};
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int k = i0 + 2 * set + q;
+            if (active && k < it.ni) {
+                if (CELL) {
+                    const float4 o = a.xo[it.i0 + k];
+                    fx[q] = o.x; fy[q] = o.y; fz[q] = o.z;
+                } else {
+                    const float4 h = a.ihl[2 * (it.i0 + k)], l = a.ihl[2 * (it.i0 + k) + 1];
+                    fx[q] = ((h.x - chx) + (l.x - clx)) * scf;
+                    fy[q] = ((h.y - chy) + (l.y - cly)) * scf;
+                    fz[q] = ((h.z - chz) + (l.z - clz)) * scf;
+                }
+            }
+        }
+        const u64 xi = pk2(fx[0], fx[1]), yi = pk2(fy[0], fy[1]), zi = pk2(fz[0], fz[1]);
+        u64 hx = 0, hy = 0, hz = 0, hp = 0, lx = 0, ly = 0, lz = 0, lp = 0;
+
+        for (long long t0 = jb; t0 < je; t0 += kWarpTJ) {
+            const long long nv = min((long long)kWarpTJ, je - t0);
+#pragma unroll
+            for (int r = 0; r < kWarpTJ / 32; ++r) {
+                const int e = r * 32 + lane32;
+                float x = 1.0e4f, y = 1.0e4f, z = 1.0e4f, m = 0.0f;   // padding adds 0
+                if (e < nv) {
+                    const int raw = a.jlist[t0 + e];
+                    const long long j = raw & 0x07ffffff;
+                    if (j >= a.nj) {
+                        report(a.status, kStatusBadIndex, 4);
+                    } else if (CELL) {
+                        const float4 o = __ldg(a.xo + j);
+                        const float4 dv = dirt[((unsigned)raw) >> 27];
+                        x = o.x + dv.x; y = o.y + dv.y; z = o.z + dv.z; m = o.w;
+                    } else {
+                        const float4 h = __ldg(a.jhl + 2 * j), l = __ldg(a.jhl + 2 * j + 1);
+                        x = ((h.x - chx) + (l.x - clx)) * scf;
+                        y = ((h.y - chy) + (l.y - cly)) * scf;
+                        z = ((h.z - chz) + (l.z - clz)) * scf;
+                        m = h.w;
+                    }
+                }
+                sxy[e] = make_ulonglong2(pk2(x, x), pk2(y, y));
+                szm[e] = make_ulonglong2(pk2(z, z), pk2(m, m));
+            }
+            __syncwarp();
+            if (active) {
+                u64 ax = 0, ay = 0, az = 0, ph = 0;
+                const int nvl = (int)nv;
+#pragma unroll 4
+                for (int e = lane; e < nvl; e += L) {
+                    const ulonglong2 xy = sxy[e], zm = szm[e];
+                    const u64 dx = f2sub(xy.x, xi), dy = f2sub(xy.y, yi), dz = f2sub(zm.x, zi);
+                    u64 r2 = f2fma(dx, dx, c0v);
+                    r2 = f2fma(dy, dy, r2);
+                    r2 = f2fma(dz, dz, r2);
+                    float ra, rb;
+                    up2(r2, ra, rb);
+                    if (!TABLE) {
+                        float qa = rsq(ra), qb = rsq(rb);
+                        if (ZSAFE) {
+                            qa = ra > 0.0f ? qa : 0.0f;
+                            qb = rb > 0.0f ? qb : 0.0f;
+                        }
+                        const u64 q = pk2(qa, qb);
+                        const u64 mq = f2mul(zm.y, q);
+                        const u64 mq3 = f2mul(mq, f2mul(q, q));
+                        ph = f2sub(ph, mq);
+                        ax = f2fma(mq3, dx, ax);
+                        ay = f2fma(mq3, dy, ay);
+                        az = f2fma(mq3, dz, az);
+                    } else {
+                        ra = fminf(ra, a.tab.s_max);
+                        rb = fminf(rb, a.tab.s_max);
+                        const float2 ta = tab_at(tb0, __float_as_uint(ra), sh3);
+                        const float2 tb = tab_at(tb0, __float_as_uint(rb), sh3);
+                        const u64 g = pk2(__fmaf_rn(ra, ta.y, ta.x), __fmaf_rn(rb, tb.y, tb.x));
+                        const u64 mg = f2mul(zm.y, g);
+                        ax = f2fma(mg, dx, ax);
+                        ay = f2fma(mg, dy, ay);
+                        az = f2fma(mg, dz, az);
+                    }
+                }
+                fold2(hx, lx, ax);
+                fold2(hy, ly, ay);
+                fold2(hz, lz, az);
+                if (!TABLE) fold2(hp, lp, ph);
+            }
+            __syncwarp();
+        }
+
+        // segmented reduction of the set's lanes, first lane writes
+        float h[8], l[8];
+        up2(hx, h[0], h[1]); up2(hy, h[2], h[3]); up2(hz, h[4], h[5]); up2(hp, h[6], h[7]);
+        up2(lx, l[0], l[1]); up2(ly, l[2], l[3]); up2(lz, l[4], l[5]); up2(lp, l[6], l[7]);
+        for (int off = 1; off < L; off <<= 1) {
+            const bool take = lane + off < L;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (TABLE && (k == 6 || k == 7)) continue;
+                const float oh = __shfl_down_sync(0xffffffffu, h[k], off);
+                const float ol = __shfl_down_sync(0xffffffffu, l[k], off);
+                if (take) {
+                    float sm, er;
+                    two_sum(h[k], oh, sm, er);
+                    h[k] = sm;
+                    l[k] = __fadd_rn(l[k], __fadd_rn(ol, er));
+                }
+            }
+        }
+        if (active && lane == 0) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int k = i0 + 2 * set + q;
+                if (k < it.ni) {
+                    const long long i = it.i0 + k;
+                    const long long o = a.perm ? (long long)a.perm[i] : i;
+                    a.acc[3 * o] = ((double)h[0 + q] + (double)l[0 + q]) * a.accscale;
+                    a.acc[3 * o + 1] = ((double)h[2 + q] + (double)l[2 + q]) * a.accscale;
+                    a.acc[3 * o + 2] = ((double)h[4 + q] + (double)l[4 + q]) * a.accscale;
+                    if (a.pot) a.pot[o] = TABLE ? 0.0 : (double)h[6 + q] + (double)l[6 + q];
+                }
+            }
+        }
+    }
+}
+
 // NPMAX: the largest i-pair count per thread; items whose shape uses the
 // threads better with half of it run with NPMAX / 2
 template <int NPMAX, bool TABLE, bool CELL, bool ZSAFE>
@@ -283,10 +486,13 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
                                 (float)(tid % 3 - 1) * a.cell_h, 0.0f);
     const int nitems = a.nitems >= 0 ? a.nitems : (int)*a.nitems_dev;
 
+    const int warp_from = a.warp_from >= 0 ? a.warp_from : (int)*a.warp_from_dev;
+
     // the next item is claimed while the current one runs (kept in a
     // register of thread 0), so the queue's atomic latency overlaps work
     int next = 0;
     if (tid == 0) next = atomicAdd(a.queue, 1);
+    int first_small = -1;
     for (;;) {
         __syncthreads();   // previous item fully done with shared memory
         if (tid == 0) {
@@ -295,7 +501,11 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
         }
         __syncthreads();
         const int item = sh[0];
-        if (item >= nitems) break;
+        if (item >= nitems) return;
+        if (item >= warp_from) {   // the small items: continue in warp mode
+            first_small = item;
+            break;
+        }
         const GroupItem it = a.items[item];
         if (NPMAX > 1 && it.ni <= kNT * NPMAX) {
             const ItemShape big = item_shape(it.ni, NPMAX);
@@ -308,6 +518,31 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
         }
         group_item<NPMAX, TABLE, CELL, ZSAFE>(a, it, item_shape(it.ni, NPMAX), cvt, run, tab, dirt,
                                               tid);
+    }
+
+    // warp mode: warp 0 takes the item that ended CTA mode and thread 0's
+    // prefetched claim; every warp then claims its own items
+    __syncthreads();   // no warp still reads the CTA-wide staging buffer
+    const int w = tid >> 5, lane32 = tid & 31;
+    u64 *wcvt = cvt + w * (2 * 2 * kWarpTJ);
+    int cur = w == 0 ? first_small : -1;
+    int held = (w == 0 && lane32 == 0) ? next : -1;
+    for (;;) {
+        if (cur < 0) {
+            int c2 = 0;
+            if (lane32 == 0) {
+                if (held >= 0) {
+                    c2 = held;
+                    held = -1;
+                } else {
+                    c2 = atomicAdd(a.queue, 1);
+                }
+            }
+            cur = __shfl_sync(0xffffffffu, c2, 0);
+        }
+        if (cur >= nitems) break;
+        warp_item<TABLE, CELL, ZSAFE>(a, a.items[cur], wcvt, tab, dirt, lane32);
+        cur = -1;
     }
 }
 
@@ -569,7 +804,7 @@ __global__ void k_cell_lists(const unsigned *__restrict__ start, int nc,
 __global__ void k_cell_items(const unsigned *__restrict__ start, long long ncell, int Bi,
                              const unsigned *__restrict__ ioff, const unsigned *__restrict__ jcount,
                              GroupItem *__restrict__ items, unsigned *__restrict__ keys,
-                             unsigned *__restrict__ vals)
+                             unsigned *__restrict__ vals, unsigned *__restrict__ ncta)
 {
     long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (g >= ncell) return;
@@ -582,10 +817,13 @@ __global__ void k_cell_items(const unsigned *__restrict__ start, long long ncell
         it.ni = (int)min((unsigned)Bi, ni - k * Bi);
         it.pad = 0;
         items[o + k] = it;
-        unsigned long long cost = (unsigned long long)it.ni * jcount[g];
-        unsigned cq = cost > 0xffffffull ? 0xffffffu : (unsigned)cost;
-        keys[o + k] = 0xffffffu - cq;     // ascending sort = longest first
+        // CTA-sized items first, longest first; then the warp-sized ones
+        unsigned long long cost = ((unsigned long long)it.ni * jcount[g]) >> 2;
+        unsigned cq = cost > 0x7fffffull ? 0x7fffffu : (unsigned)cost;
+        const bool small = it.ni <= kWarpItemNi;
+        keys[o + k] = ((small ? 1u : 0u) << 23) | (0x7fffffu - cq);
         vals[o + k] = o + k;
+        if (!small) atomicAdd(ncta, 1u);
     }
 }
 
@@ -642,8 +880,9 @@ cudaError_t launch_cell_build(const double4 *jrec, long long n, double box, int 
     // unused item slots sort last
     cudaMemsetAsync(sort.keys[0], 0xff, s.item_cap * sizeof(unsigned), st);
     k_fill_iota<<<(unsigned)((s.item_cap + 255) / 256), 256, 0, st>>>(sort.vals[0], s.item_cap);
+    cudaMemsetAsync(s.ncta, 0, sizeof(unsigned), st);
     k_cell_items<<<gc, 256, 0, st>>>(s.start, ncell, Bi, s.ioff, s.jcount, s.items_raw,
-                                     sort.keys[0], sort.vals[0]);
+                                     sort.keys[0], sort.vals[0], s.ncta);
     unsigned *order;
     if ((e = launch_radix_sort(sort.keys[0], sort.vals[0], s.item_cap, 24, sort, &ko, &order, st)) !=
         cudaSuccess)

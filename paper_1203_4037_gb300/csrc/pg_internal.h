@@ -79,6 +79,8 @@ struct GroupArgs {
     const double4 *gctr;   // FP64 centre of each group
     int nitems;            // item count, or -1: read *nitems_dev
     const unsigned *nitems_dev;
+    int warp_from;         // first warp-mode item (items after are small), -1: *warp_from_dev
+    const unsigned *warp_from_dev;
     int *queue;            // work counter (reset to 0 before each launch)
     long long nj;          // number of j records (bounds check)
     float eps2;
@@ -180,6 +182,7 @@ struct CellScratch {
     double4 *ctr;          // ncell cell centres
     long long item_cap;
     unsigned long long *pairs;   // evaluated pairs of the build (device)
+    unsigned *ncta;        // number of CTA-mode items (they sort first)
 };
 cudaError_t launch_cell_build(const double4 *jrec, long long n, double box, int nc, int Bi,
                               double scale, CellScratch &s, SortScratch &sort, cudaStream_t st);
