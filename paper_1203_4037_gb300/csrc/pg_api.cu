@@ -85,8 +85,8 @@ struct pg_ctx {
 
     // periodic cell list
     CellScratch cells{};
-    DevBuf c_wrapped, c_xs, c_xo, c_perm, c_start, c_jcount, c_icount, c_joff32, c_joff, c_ioff,
-        c_jlist, c_items_raw, c_items, c_ctr, c_pairs;
+    DevBuf c_wrapped, c_xs, c_xo, c_perm, c_start, c_jcount, c_icount, c_ioff, c_items_raw,
+        c_items, c_pairs;
     bool pairs_on_device = false;
 
     // backward
@@ -342,8 +342,8 @@ void pg_destroy(pg_ctx *c)
                       &c->g_joff, &c->g_jlist, &c->g_items, &c->g_ctr, &c->g_queue, &c->g_jhl,
                       &c->g_ihl,
                       &c->c_wrapped, &c->c_xs, &c->c_xo, &c->c_perm, &c->c_start, &c->c_jcount,
-                      &c->c_icount, &c->c_joff32, &c->c_joff, &c->c_ioff, &c->c_jlist,
-                      &c->c_items_raw, &c->c_items, &c->c_ctr, &c->c_pairs, &c->bw_wj,
+                      &c->c_icount, &c->c_ioff,
+                      &c->c_items_raw, &c->c_items, &c->c_pairs, &c->bw_wj,
                       &c->bw_wt, &c->bw_dv};
     for (DevBuf *b : bufs) free_dev(*b);
     free_pin(c->pin_j);
@@ -814,18 +814,18 @@ int upload_group_items(pg_ctx *c)
             cost.push_back((long long)it.ni * nj);
         }
     }
-    // CTA-sized items first, longest first, then the warp-sized ones
-    // (at most 32 i-particles), longest first
-    const int kWarpNi = 32;
+    // CTA-sized items first, longest first, then the warp-sized ones (at
+    // most 32 i-particles and 32768 pairs), longest first
+    auto warp_sized = [&](size_t k) { return items[k].ni <= 32 && cost[k] <= 32768; };
     std::vector<size_t> order(items.size());
     for (size_t k = 0; k < order.size(); ++k) order[k] = k;
     std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
-        bool sa = items[a].ni <= kWarpNi, sb = items[b].ni <= kWarpNi;
+        bool sa = warp_sized(a), sb = warp_sized(b);
         if (sa != sb) return !sa;
         return cost[a] > cost[b];
     });
     c->g_warp_from = 0;
-    for (const GroupItem &it : items) c->g_warp_from += it.ni > kWarpNi ? 1 : 0;
+    for (size_t k = 0; k < items.size(); ++k) c->g_warp_from += warp_sized(k) ? 0 : 1;
     std::vector<GroupItem> sorted(items.size());
     for (size_t k = 0; k < order.size(); ++k) sorted[k] = items[order[k]];
     int rc;
@@ -926,17 +926,16 @@ int enqueue_cells(pg_ctx *c, double *acc, double *pot)
         (rc = ensure(c, c->c_xo, n * 16)) ||
         (rc = ensure(c, c->c_perm, n * 4)) || (rc = ensure(c, c->c_start, (ncell + 1) * 4)) ||
         (rc = ensure(c, c->c_jcount, ncell * 4)) || (rc = ensure(c, c->c_icount, ncell * 4)) ||
-        (rc = ensure(c, c->c_joff32, (ncell + 1) * 4)) || (rc = ensure(c, c->c_joff, (ncell + 1) * 8)) ||
-        (rc = ensure(c, c->c_ioff, (ncell + 1) * 4)) || (rc = ensure(c, c->c_jlist, 27 * n * 4)) ||
+        (rc = ensure(c, c->c_ioff, (ncell + 1) * 4)) ||
         (rc = ensure(c, c->c_items_raw, item_cap * sizeof(GroupItem))) ||
         (rc = ensure(c, c->c_items, item_cap * sizeof(GroupItem))) ||
-        (rc = ensure(c, c->c_ctr, ncell * 32)) || (rc = ensure(c, c->c_pairs, 16)) ||
+        (rc = ensure(c, c->c_pairs, 16)) ||
         (rc = ensure(c, c->skeys0, sn * 4)) || (rc = ensure(c, c->skeys1, sn * 4)) ||
         (rc = ensure(c, c->svals0, sn * 4)) || (rc = ensure(c, c->svals1, sn * 4)) ||
         (rc = ensure(c, c->shist, hn * 4)) || (rc = ensure(c, c->ssums, nb * 4)) ||
         (rc = ensure(c, c->g_queue, 16)))
         return rc;
-    if (27 * n >= (1LL << 31)) return fail(c, PG_EINVAL, "too many particles for the cell lists");
+    if (n >= (1LL << 31)) return fail(c, PG_EINVAL, "too many particles for the cell path");
     s.wrapped = (double4 *)c->c_wrapped.p;
     s.xs = (double4 *)c->c_xs.p;
     s.xo = (float4 *)c->c_xo.p;
@@ -944,13 +943,9 @@ int enqueue_cells(pg_ctx *c, double *acc, double *pot)
     s.start = (unsigned *)c->c_start.p;
     s.jcount = (unsigned *)c->c_jcount.p;
     s.icount = (unsigned *)c->c_icount.p;
-    s.joff32 = (unsigned *)c->c_joff32.p;
-    s.joff = (long long *)c->c_joff.p;
     s.ioff = (unsigned *)c->c_ioff.p;
-    s.jlist = (int *)c->c_jlist.p;
     s.items_raw = (GroupItem *)c->c_items_raw.p;
     s.items = (GroupItem *)c->c_items.p;
-    s.ctr = (double4 *)c->c_ctr.p;
     s.item_cap = item_cap;
     s.pairs = (unsigned long long *)c->c_pairs.p;
     s.ncta = (unsigned *)((char *)c->c_pairs.p + 8);
@@ -962,14 +957,21 @@ int enqueue_cells(pg_ctx *c, double *acc, double *pot)
     c->sort.sums = (unsigned *)c->ssums.p;
     PG_CUDA(c, launch_cell_build((const double4 *)c->jrec.p, n, c->box, nc, Bi, c->scale, s,
                                  c->sort, c->stream));
-    c->last_launches += 30;
+    // kernels of the build: key, count, gather, sizes, pairs, iota, items,
+    // permute (8), two scans (6), the 24-bit item sort (15) and the cell
+    // sort (5 per 8 key bits)
+    int cell_bits = 0;
+    while ((1LL << cell_bits) < ncell) ++cell_bits;
+    c->last_launches += 29 + 5 * ((cell_bits + 7) / 8);
     GroupArgs g = group_args(c);
     g.xi = s.xs;
     g.jrec = s.xs;
-    g.j_off = s.joff;
-    g.jlist = s.jlist;
+    g.j_off = nullptr;
+    g.jlist = nullptr;
+    g.cstart = s.start;
+    g.nc = nc;
     g.items = s.items;
-    g.gctr = s.ctr;
+    g.gctr = nullptr;
     g.nitems = -1;
     g.nitems_dev = s.ioff + ncell;
     g.warp_from = -1;

@@ -4,12 +4,13 @@
 // the cutoff force into the same shape of work.
 //
 // One persistent launch: every CTA takes work items (group, i-chunk) from an
-// atomic queue ordered longest-first, gathers the group's j records by index
-// into shared memory (converted once per record to FP32 offsets from the
-// group's FP64 centre, with the periodic image shift applied in FP64), and
-// evaluates the Newton or tabulated pair term with the i-particles in
-// registers. A small group splits each set of i-particles across L lanes,
-// each taking every L-th j, and combines the lanes with warp shuffles.
+// atomic queue ordered longest-first, gathers the group's j records into
+// shared memory (converted once per record to FP32 offsets in the group's
+// frame), and evaluates the Newton or tabulated pair term with the
+// i-particles in registers. A small group splits each set of i-particles
+// across L lanes, each taking every L-th j, and combines the lanes with warp
+// shuffles. The smallest items (few i-particles and short lists) come last
+// and run one per warp instead of one per CTA.
 #include "pg_device.cuh"
 
 namespace pg {
@@ -25,10 +26,11 @@ constexpr int kPerThread = kTJG / kNT;
 //    rounding as differencing in FP64 and rounding once, without FP64
 //    instructions (GB300 runs FP64 at about two operations per SM-clock).
 //  CELL = true: the periodic cell list's FP32 record (o, m), o = the
-//    particle's offset from its cell's corner in scaled units; a j-list entry
-//    carries the direction (dx, dy, dz) in {-1, 0, 1}^3 from the i-cell to the
-//    j-cell, so the j offset in the i-cell's frame is o_j + (dx, dy, dz) h~ --
-//    FP32 only, with the periodic wrap already in the direction.
+//    particle's offset from its cell's corner in scaled units. The j-list of
+//    a cell is the 27 neighbour cells' runs of the cell-sorted records, each
+//    with its direction (dx, dy, dz) in {-1, 0, 1}^3 from the i-cell, so the
+//    j offset in the i-cell's frame is o_j + (dx, dy, dz) h~ -- FP32 only,
+//    with the periodic wrap already in the direction.
 //
 // Thread layout of an item: nsets sets of 2*NP i-particles; each set owns L
 // consecutive lanes of one warp (any L from 1 to 32, sets never straddle a
@@ -90,12 +92,65 @@ __device__ __forceinline__ float2 tab_at(unsigned tbase, unsigned bits, int shif
     return v;
 }
 
+// Cell mode. The j-list of cell g is the particles of its 27 neighbour cells
+// (itself included), direction d = 9 (dx + 1) + 3 (dy + 1) + (dz + 1), each a
+// contiguous run of the cell-sorted arrays. One warp writes the runs as a
+// prefix table cr[0..63]: cr[d] = entries before run d (cr[27..31] = the
+// total), cr[32 + d] = first particle of run d minus cr[d], so that list
+// position p of run d is particle cr[32 + d] + p.
+constexpr int kCellTab = 64;
+
+__device__ __forceinline__ void cell_ranges(const GroupArgs &a, int g, int lane32, int *cr)
+{
+    int first = 0, cnt = 0;
+    if (lane32 < 27) {
+        const int nc = a.nc;
+        const int cz = g % nc, cxy = g / nc;
+        const int cy = cxy % nc, cx = cxy / nc;
+        int x = cx + lane32 / 9 - 1, y = cy + (lane32 / 3) % 3 - 1, z = cz + lane32 % 3 - 1;
+        x = x < 0 ? x + nc : x >= nc ? x - nc : x;
+        y = y < 0 ? y + nc : y >= nc ? y - nc : y;
+        z = z < 0 ? z + nc : z >= nc ? z - nc : z;
+        const long long nb = ((long long)x * nc + y) * nc + z;
+        first = (int)a.cstart[nb];
+        cnt = (int)(a.cstart[nb + 1] - (unsigned)first);
+    }
+    int inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane32 >= o) inc += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, inc, 26);
+    const int exc = inc - cnt;
+    cr[lane32] = lane32 < 27 ? exc : total;
+    if (lane32 < 27) cr[32 + lane32] = first - exc;
+}
+
+// run holding list position p (0 <= p < total): the largest d with cr[d] <= p
+__device__ __forceinline__ int cell_find(const int *cr, int p)
+{
+    int d = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1)
+        if (cr[d + step] <= p) d += step;
+    return d;
+}
+
 template <int NP, bool TABLE, bool CELL, bool ZSAFE>
 __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &it, const ItemShape sh,
-                                           u64 *cvt, u64 *run, const float2 *tab, const float4 *dirt,
-                                           int tid)
+                                           u64 *cvt, u64 *run, int *cr, const float2 *tab,
+                                           const float4 *dirt, int tid)
 {
-    const long long jb = a.j_off[it.group], je = a.j_off[it.group + 1];
+    long long jb = 0, je = 0;
+    if (CELL) {
+        if (tid < 32) cell_ranges(a, it.group, tid, cr);
+        __syncthreads();
+        je = cr[27];
+    } else {
+        jb = a.j_off[it.group];
+        je = a.j_off[it.group + 1];
+    }
     double4 c = make_double4(0, 0, 0, 0);
     float chx = 0, chy = 0, chz = 0, clx = 0, cly = 0, clz = 0;   // centre as hi + lo
     if (!CELL) {
@@ -154,15 +209,19 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
         for (int r = 0; r < kPerThread; ++r) {
             long long e = t0 + r * kNT + tid;
             bool ok = e < je;
-            int raw = ok ? a.jlist[e] : 0;
-            long long j = raw & 0x07ffffff;
-            if (ok && j >= a.nj) {         // bad index: record it, contribute nothing
+            long long j;
+            if (CELL) {
+                code[r] = cell_find(cr, (int)e);
+                j = (long long)cr[32 + code[r]] + e;
+            } else {
+                j = (ok ? a.jlist[e] : 0) & 0x07ffffff;
+            }
+            if (ok && (j < 0 || j >= a.nj)) {   // bad index: record it, contribute nothing
                 report(a.status, kStatusBadIndex, 2);
                 ok = false;
             }
             if (CELL) {
                 rc32[r] = ok ? __ldg(a.xo + j) : make_float4(0, 0, 0, -1.0f);
-                code[r] = (int)(((unsigned)raw) >> 27);
             } else {
                 rc32[r] = ok ? __ldg(a.jhl + 2 * j) : make_float4(0, 0, 0, -1.0f);
                 rlo[r] = ok ? __ldg(a.jhl + 2 * j + 1) : make_float4(0, 0, 0, 0);
@@ -304,25 +363,32 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
     }
 }
 
-// Warp mode: one warp evaluates one small item (at most kWarpItemNi
+// Warp mode: one warp evaluates one small item at a time (at most 64
 // i-particles per pass, one i-pair per lane) with its own 4 KB slice of the
 // staging buffer and warp-level synchronisation only, so the warps of a CTA
 // work through small items independently instead of meeting at CTA barriers.
+// Small items are short, so the warp pipelines across them: the queue claim
+// for the item after next, the next item's record, its j range, its
+// i-particles and its first j tile are all in flight while the current
+// item's last tile is evaluated.
 constexpr int kWarpTJ = 128;        // j entries per warp-staged tile
-constexpr int kWarpItemNi = 32;     // items up to this size go to warp mode
+constexpr int kWarpItemNi = 32;     // items up to this size (i-particles)
+constexpr long long kWarpItemPairs = 32768;   // and this many pairs go to warp mode
 
 template <bool TABLE, bool CELL, bool ZSAFE>
-__device__ __forceinline__ void warp_item(const GroupArgs &a, const GroupItem &it, u64 *wcvt,
-                                          const float2 *tab, const float4 *dirt, int lane32)
+__device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cur, int held,
+                                          u64 *wcvt, int *wcr, const float2 *tab,
+                                          const float4 *dirt, int lane32)
 {
-    const long long jb = a.j_off[it.group], je = a.j_off[it.group + 1];
-    float chx = 0, chy = 0, chz = 0, clx = 0, cly = 0, clz = 0;
-    if (!CELL) {
-        const double4 c = a.gctr[it.group];
-        chx = (float)c.x; clx = (float)(c.x - (double)chx);
-        chy = (float)c.y; cly = (float)(c.y - (double)chy);
-        chz = (float)c.z; clz = (float)(c.z - (double)chz);
+    constexpr unsigned kFull = 0xffffffffu;
+    int pend = 0;                       // lane 0: the claim in flight
+    if (lane32 == 0) pend = held >= 0 ? held : atomicAdd(a.queue, 1);
+    if (cur < 0) {
+        cur = __shfl_sync(kFull, pend, 0);
+        if (lane32 == 0 && cur < nitems) pend = atomicAdd(a.queue, 1);
     }
+    if (cur >= nitems) return;
+
     const float c0 = TABLE ? 2.0f : a.eps2;
     const u64 c0v = pk2(c0, c0);
     const float scf = TABLE && !CELL ? (float)a.tab.scale : 1.0f;
@@ -331,138 +397,270 @@ __device__ __forceinline__ void warp_item(const GroupArgs &a, const GroupItem &i
     ulonglong2 *sxy = reinterpret_cast<ulonglong2 *>(wcvt);            // [kWarpTJ]
     ulonglong2 *szm = sxy + kWarpTJ;                                   // [kWarpTJ]
 
-    for (int i0 = 0; i0 < it.ni; i0 += 2 * 32) {
-        const int ni = min(2 * 32, it.ni - i0);
+    // j range of an item (cell mode: its run table, written to cr)
+    auto setup = [&](const GroupItem &it, int *cr, long long &jb, long long &je) {
+        if (CELL) {
+            cell_ranges(a, it.group, lane32, cr);
+            __syncwarp();
+            jb = 0;
+            je = cr[27];
+        } else {
+            jb = a.j_off[it.group];
+            je = a.j_off[it.group + 1];
+        }
+    };
+
+    // register prefetch of one j tile (kR records per lane)
+    constexpr int kR = kWarpTJ / 32;
+    float4 rc32[kR];
+    float4 rlo[CELL ? 1 : kR];
+    int code[CELL ? kR : 1];
+    auto fetch = [&](long long t0, long long je, const int *cr) {
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            const long long e = t0 + r * 32 + lane32;
+            bool ok = e < je;
+            long long j;
+            if (CELL) {
+                code[r] = cell_find(cr, (int)e);
+                j = (long long)cr[32 + code[r]] + e;
+            } else {
+                j = (ok ? a.jlist[e] : 0) & 0x07ffffff;
+            }
+            if (ok && (j < 0 || j >= a.nj)) {
+                report(a.status, kStatusBadIndex, 4);
+                ok = false;
+            }
+            if (CELL) {
+                rc32[r] = ok ? __ldg(a.xo + j) : make_float4(0, 0, 0, -1.0f);
+            } else {
+                rc32[r] = ok ? __ldg(a.jhl + 2 * j) : make_float4(0, 0, 0, -1.0f);
+                rlo[r] = ok ? __ldg(a.jhl + 2 * j + 1) : make_float4(0, 0, 0, 0);
+            }
+        }
+    };
+
+    // lane layout of a pass over ni i-particles: sets of L lanes, one i-pair
+    // per set
+    struct Shape {
+        int L, set, lane;
+        bool active;
+    };
+    auto shape_of = [&](int ni) {
+        Shape sp;
         const int nsets = (ni + 1) / 2;
         int L = div_small(32, nsets);
-        L = L < 1 ? 1 : L;
-        const int spw = div_small(32, L);
-        const int set = div_small(lane32, L), lane = lane32 - set * L;
-        const bool active = lane32 < spw * L && set < nsets;
-        float fx[2] = {0, 0}, fy[2] = {0, 0}, fz[2] = {0, 0};
+        sp.L = L < 1 ? 1 : L;
+        const int spw = div_small(32, sp.L);
+        sp.set = div_small(lane32, sp.L);
+        sp.lane = lane32 - sp.set * sp.L;
+        sp.active = lane32 < spw * sp.L && sp.set < nsets;
+        return sp;
+    };
+    // raw i records of a pass (converted once the item starts)
+    float4 ih[2], il[CELL ? 1 : 2];
+    auto load_i = [&](const GroupItem &it, int i0, const Shape &sp) {
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            const int k = i0 + 2 * set + q;
-            if (active && k < it.ni) {
-                if (CELL) {
-                    const float4 o = a.xo[it.i0 + k];
-                    fx[q] = o.x; fy[q] = o.y; fz[q] = o.z;
-                } else {
-                    const float4 h = a.ihl[2 * (it.i0 + k)], l = a.ihl[2 * (it.i0 + k) + 1];
-                    fx[q] = ((h.x - chx) + (l.x - clx)) * scf;
-                    fy[q] = ((h.y - chy) + (l.y - cly)) * scf;
-                    fz[q] = ((h.z - chz) + (l.z - clz)) * scf;
-                }
+            const int k = i0 + 2 * sp.set + q;
+            const bool ok = sp.active && k < it.ni;
+            if (CELL) {
+                ih[q] = ok ? a.xo[it.i0 + k] : make_float4(0, 0, 0, 0);
+            } else {
+                ih[q] = ok ? a.ihl[2 * (it.i0 + k)] : make_float4(0, 0, 0, 0);
+                il[q] = ok ? a.ihl[2 * (it.i0 + k) + 1] : make_float4(0, 0, 0, 0);
             }
         }
-        const u64 xi = pk2(fx[0], fx[1]), yi = pk2(fy[0], fy[1]), zi = pk2(fz[0], fz[1]);
-        u64 hx = 0, hy = 0, hz = 0, hp = 0, lx = 0, ly = 0, lz = 0, lp = 0;
+    };
 
-        for (long long t0 = jb; t0 < je; t0 += kWarpTJ) {
-            const long long nv = min((long long)kWarpTJ, je - t0);
-#pragma unroll
-            for (int r = 0; r < kWarpTJ / 32; ++r) {
-                const int e = r * 32 + lane32;
-                float x = 1.0e4f, y = 1.0e4f, z = 1.0e4f, m = 0.0f;   // padding adds 0
-                if (e < nv) {
-                    const int raw = a.jlist[t0 + e];
-                    const long long j = raw & 0x07ffffff;
-                    if (j >= a.nj) {
-                        report(a.status, kStatusBadIndex, 4);
-                    } else if (CELL) {
-                        const float4 o = __ldg(a.xo + j);
-                        const float4 dv = dirt[((unsigned)raw) >> 27];
-                        x = o.x + dv.x; y = o.y + dv.y; z = o.z + dv.z; m = o.w;
-                    } else {
-                        const float4 h = __ldg(a.jhl + 2 * j), l = __ldg(a.jhl + 2 * j + 1);
-                        x = ((h.x - chx) + (l.x - clx)) * scf;
-                        y = ((h.y - chy) + (l.y - cly)) * scf;
-                        z = ((h.z - chz) + (l.z - clz)) * scf;
-                        m = h.w;
-                    }
-                }
-                sxy[e] = make_ulonglong2(pk2(x, x), pk2(y, y));
-                szm[e] = make_ulonglong2(pk2(z, z), pk2(m, m));
-            }
-            __syncwarp();
-            if (active) {
-                u64 ax = 0, ay = 0, az = 0, ph = 0;
-                const int nvl = (int)nv;
-#pragma unroll 4
-                for (int e = lane; e < nvl; e += L) {
-                    const ulonglong2 xy = sxy[e], zm = szm[e];
-                    const u64 dx = f2sub(xy.x, xi), dy = f2sub(xy.y, yi), dz = f2sub(zm.x, zi);
-                    u64 r2 = f2fma(dx, dx, c0v);
-                    r2 = f2fma(dy, dy, r2);
-                    r2 = f2fma(dz, dz, r2);
-                    float ra, rb;
-                    up2(r2, ra, rb);
-                    if (!TABLE) {
-                        float qa = rsq(ra), qb = rsq(rb);
-                        if (ZSAFE) {
-                            qa = ra > 0.0f ? qa : 0.0f;
-                            qb = rb > 0.0f ? qb : 0.0f;
-                        }
-                        const u64 q = pk2(qa, qb);
-                        const u64 mq = f2mul(zm.y, q);
-                        const u64 mq3 = f2mul(mq, f2mul(q, q));
-                        ph = f2sub(ph, mq);
-                        ax = f2fma(mq3, dx, ax);
-                        ay = f2fma(mq3, dy, ay);
-                        az = f2fma(mq3, dz, az);
-                    } else {
-                        ra = fminf(ra, a.tab.s_max);
-                        rb = fminf(rb, a.tab.s_max);
-                        const float2 ta = tab_at(tb0, __float_as_uint(ra), sh3);
-                        const float2 tb = tab_at(tb0, __float_as_uint(rb), sh3);
-                        const u64 g = pk2(__fmaf_rn(ra, ta.y, ta.x), __fmaf_rn(rb, tb.y, tb.x));
-                        const u64 mg = f2mul(zm.y, g);
-                        ax = f2fma(mg, dx, ax);
-                        ay = f2fma(mg, dy, ay);
-                        az = f2fma(mg, dz, az);
-                    }
-                }
-                fold2(hx, lx, ax);
-                fold2(hy, ly, ay);
-                fold2(hz, lz, az);
-                if (!TABLE) fold2(hp, lp, ph);
-            }
-            __syncwarp();
-        }
+    GroupItem it = a.items[cur];
+    int slot = 0;
+    long long jb, je;
+    setup(it, wcr, jb, je);
+    fetch(jb, je, wcr);
+    Shape sp = shape_of(min(64, it.ni));
+    load_i(it, 0, sp);
+    for (;;) {
+        // the next item: take the claim in flight, claim the one after it,
+        // start loading its record
+        const int nxt = __shfl_sync(kFull, pend, 0);
+        const bool more = nxt < nitems;
+        if (lane32 == 0 && more) pend = atomicAdd(a.queue, 1);
+        GroupItem itn = it;
+        if (more) itn = a.items[nxt];
+        const int *crc = wcr + slot * kCellTab;
+        int *crn = wcr + (slot ^ 1) * kCellTab;
+        long long jbn = 0, jen = 0;
+        Shape spn = sp;
+        bool staged = false;
 
-        // segmented reduction of the set's lanes, first lane writes
-        float h[8], l[8];
-        up2(hx, h[0], h[1]); up2(hy, h[2], h[3]); up2(hz, h[4], h[5]); up2(hp, h[6], h[7]);
-        up2(lx, l[0], l[1]); up2(ly, l[2], l[3]); up2(lz, l[4], l[5]); up2(lp, l[6], l[7]);
-        for (int off = 1; off < L; off <<= 1) {
-            const bool take = lane + off < L;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                if (TABLE && (k == 6 || k == 7)) continue;
-                const float oh = __shfl_down_sync(0xffffffffu, h[k], off);
-                const float ol = __shfl_down_sync(0xffffffffu, l[k], off);
-                if (take) {
-                    float sm, er;
-                    two_sum(h[k], oh, sm, er);
-                    h[k] = sm;
-                    l[k] = __fadd_rn(l[k], __fadd_rn(ol, er));
-                }
-            }
+        float chx = 0, chy = 0, chz = 0, clx = 0, cly = 0, clz = 0;
+        if (!CELL) {
+            const double4 c = a.gctr[it.group];
+            chx = (float)c.x; clx = (float)(c.x - (double)chx);
+            chy = (float)c.y; cly = (float)(c.y - (double)chy);
+            chz = (float)c.z; clz = (float)(c.z - (double)chz);
         }
-        if (active && lane == 0) {
+        for (int i0 = 0; i0 < it.ni; i0 += 64) {
+            const bool last_pass = i0 + 64 >= it.ni;
+            if (i0 > 0) {          // a further pass restarts the j-list
+                sp = shape_of(min(64, it.ni - i0));
+                load_i(it, i0, sp);
+                fetch(jb, je, crc);
+            }
+            float fx[2], fy[2], fz[2];
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
-                const int k = i0 + 2 * set + q;
-                if (k < it.ni) {
-                    const long long i = it.i0 + k;
+                if (CELL) {
+                    fx[q] = ih[q].x; fy[q] = ih[q].y; fz[q] = ih[q].z;
+                } else {
+                    fx[q] = ((ih[q].x - chx) + (il[q].x - clx)) * scf;
+                    fy[q] = ((ih[q].y - chy) + (il[q].y - cly)) * scf;
+                    fz[q] = ((ih[q].z - chz) + (il[q].z - clz)) * scf;
+                }
+            }
+            const u64 xi = pk2(fx[0], fx[1]), yi = pk2(fy[0], fy[1]), zi = pk2(fz[0], fz[1]);
+            const int L = sp.L, lane = sp.lane;
+            const bool active = sp.active;
+            u64 hx = 0, hy = 0, hz = 0, hp = 0, lx = 0, ly = 0, lz = 0, lp = 0;
+
+            for (long long t0 = jb; t0 < je; t0 += kWarpTJ) {
+#pragma unroll
+                for (int r = 0; r < kR; ++r) {
+                    const int e = r * 32 + lane32;
+                    float x, y, z, m;
+                    if (rc32[r].w >= 0.0f && CELL) {
+                        const float4 dv = dirt[code[r]];
+                        x = rc32[r].x + dv.x; y = rc32[r].y + dv.y; z = rc32[r].z + dv.z;
+                        m = rc32[r].w;
+                    } else if (rc32[r].w >= 0.0f) {
+                        x = ((rc32[r].x - chx) + (rlo[r].x - clx)) * scf;
+                        y = ((rc32[r].y - chy) + (rlo[r].y - cly)) * scf;
+                        z = ((rc32[r].z - chz) + (rlo[r].z - clz)) * scf;
+                        m = rc32[r].w;
+                    } else {   // padding adds exactly 0
+                        x = y = z = 1.0e4f;
+                        m = 0.0f;
+                    }
+                    sxy[e] = make_ulonglong2(pk2(x, x), pk2(y, y));
+                    szm[e] = make_ulonglong2(pk2(z, z), pk2(m, m));
+                }
+                __syncwarp();
+                // loads in flight during the compute: this item's next tile,
+                // or the next item's range, i-particles and first tile
+                if (t0 + kWarpTJ < je) {
+                    fetch(t0 + kWarpTJ, je, crc);
+                } else if (last_pass && more) {
+                    setup(itn, crn, jbn, jen);
+                    fetch(jbn, jen, crn);
+                    spn = shape_of(min(64, itn.ni));
+                    load_i(itn, 0, spn);
+                    staged = true;
+                }
+                if (active) {
+                    u64 ax = 0, ay = 0, az = 0, ph = 0;
+                    const int nvl = (int)min((long long)kWarpTJ, je - t0);
+#pragma unroll 4
+                    for (int e = lane; e < nvl; e += L) {
+                        const ulonglong2 xy = sxy[e], zm = szm[e];
+                        const u64 dx = f2sub(xy.x, xi), dy = f2sub(xy.y, yi), dz = f2sub(zm.x, zi);
+                        u64 r2 = f2fma(dx, dx, c0v);
+                        r2 = f2fma(dy, dy, r2);
+                        r2 = f2fma(dz, dz, r2);
+                        float ra, rb;
+                        up2(r2, ra, rb);
+                        if (!TABLE) {
+                            float qa = rsq(ra), qb = rsq(rb);
+                            if (ZSAFE) {
+                                qa = ra > 0.0f ? qa : 0.0f;
+                                qb = rb > 0.0f ? qb : 0.0f;
+                            }
+                            const u64 q = pk2(qa, qb);
+                            const u64 mq = f2mul(zm.y, q);
+                            const u64 mq3 = f2mul(mq, f2mul(q, q));
+                            ph = f2sub(ph, mq);
+                            ax = f2fma(mq3, dx, ax);
+                            ay = f2fma(mq3, dy, ay);
+                            az = f2fma(mq3, dz, az);
+                        } else {
+                            ra = fminf(ra, a.tab.s_max);
+                            rb = fminf(rb, a.tab.s_max);
+                            const float2 ta = tab_at(tb0, __float_as_uint(ra), sh3);
+                            const float2 tb = tab_at(tb0, __float_as_uint(rb), sh3);
+                            const u64 g = pk2(__fmaf_rn(ra, ta.y, ta.x), __fmaf_rn(rb, tb.y, tb.x));
+                            const u64 mg = f2mul(zm.y, g);
+                            ax = f2fma(mg, dx, ax);
+                            ay = f2fma(mg, dy, ay);
+                            az = f2fma(mg, dz, az);
+                        }
+                    }
+                    fold2(hx, lx, ax);
+                    fold2(hy, ly, ay);
+                    fold2(hz, lz, az);
+                    if (!TABLE) fold2(hp, lp, ph);
+                }
+                __syncwarp();
+            }
+
+            // segmented reduction of the set's lanes, first lane writes
+            float h[8], l[8];
+            up2(hx, h[0], h[1]); up2(hy, h[2], h[3]); up2(hz, h[4], h[5]); up2(hp, h[6], h[7]);
+            up2(lx, l[0], l[1]); up2(ly, l[2], l[3]); up2(lz, l[4], l[5]); up2(lp, l[6], l[7]);
+            for (int off = 1; off < L; off <<= 1) {
+                const bool take = lane + off < L;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    if (TABLE && (k == 6 || k == 7)) continue;
+                    const float oh = __shfl_down_sync(kFull, h[k], off);
+                    const float ol = __shfl_down_sync(kFull, l[k], off);
+                    if (take) {
+                        float sm, er;
+                        two_sum(h[k], oh, sm, er);
+                        h[k] = sm;
+                        l[k] = __fadd_rn(l[k], __fadd_rn(ol, er));
+                    }
+                }
+            }
+            // spread the results over the lanes, one (i, component) each,
+            // so that the FP64 conversion runs on every lane of the warp
+            const int nout = min(64, it.ni - i0) * 4;        // x, y, z, potential
+            for (int o0 = 0; o0 < nout; o0 += 32) {
+                const int oi = o0 + lane32;
+                const int ip = oi >> 2, comp = oi & 3, src = (ip >> 1) * L, want = 2 * comp + (ip & 1);
+                float vh = 0.0f, vl = 0.0f;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    if (TABLE && (k == 6 || k == 7)) continue;
+                    const float th = __shfl_sync(kFull, h[k], src & 31);
+                    const float tl = __shfl_sync(kFull, l[k], src & 31);
+                    if (k == want) {
+                        vh = th;
+                        vl = tl;
+                    }
+                }
+                if (oi < nout) {
+                    const long long i = it.i0 + i0 + ip;
                     const long long o = a.perm ? (long long)a.perm[i] : i;
-                    a.acc[3 * o] = ((double)h[0 + q] + (double)l[0 + q]) * a.accscale;
-                    a.acc[3 * o + 1] = ((double)h[2 + q] + (double)l[2 + q]) * a.accscale;
-                    a.acc[3 * o + 2] = ((double)h[4 + q] + (double)l[4 + q]) * a.accscale;
-                    if (a.pot) a.pot[o] = TABLE ? 0.0 : (double)h[6 + q] + (double)l[6 + q];
+                    const double v = (double)vh + (double)vl;
+                    if (comp < 3)
+                        a.acc[3 * o + comp] = v * a.accscale;
+                    else if (a.pot)
+                        a.pot[o] = v;     // zero in table mode
                 }
             }
         }
+        if (!more) return;
+        if (!staged) {             // the item had no j tile to overlap with
+            setup(itn, crn, jbn, jen);
+            fetch(jbn, jen, crn);
+            spn = shape_of(min(64, itn.ni));
+            load_i(itn, 0, spn);
+        }
+        it = itn;
+        jb = jbn;
+        je = jen;
+        sp = spn;
+        slot ^= 1;
     }
 }
 
@@ -476,7 +674,8 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
     u64 *run = cvt + 4 * kTJG;                                           // [8 NPMAX][kNT]
     float4 *dirt = reinterpret_cast<float4 *>(run + 8 * NPMAX * kNT);    // [27] cell mode
     int *sh = reinterpret_cast<int *>(dirt + 28);                        // item slot
-    float2 *tab = reinterpret_cast<float2 *>(sh + 4);
+    int *cr = sh + 4;                                                    // [4][2][kCellTab] cell mode
+    float2 *tab = reinterpret_cast<float2 *>(cr + 8 * kCellTab);
 
     const int tid = threadIdx.x;
     if (TABLE)
@@ -512,44 +711,29 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
             const ItemShape small = item_shape(it.ni, NPMAX / 2);
             if (small.nsets <= 4 * small.spw && small.nsets * small.L > big.nsets * big.L) {
                 group_item<(NPMAX > 1 ? NPMAX / 2 : 1), TABLE, CELL, ZSAFE>(a, it, small, cvt, run,
-                                                                             tab, dirt, tid);
+                                                                             cr, tab, dirt, tid);
                 continue;
             }
         }
-        group_item<NPMAX, TABLE, CELL, ZSAFE>(a, it, item_shape(it.ni, NPMAX), cvt, run, tab, dirt,
-                                              tid);
+        group_item<NPMAX, TABLE, CELL, ZSAFE>(a, it, item_shape(it.ni, NPMAX), cvt, run, cr, tab,
+                                              dirt, tid);
     }
 
     // warp mode: warp 0 takes the item that ended CTA mode and thread 0's
     // prefetched claim; every warp then claims its own items
     __syncthreads();   // no warp still reads the CTA-wide staging buffer
     const int w = tid >> 5, lane32 = tid & 31;
-    u64 *wcvt = cvt + w * (2 * 2 * kWarpTJ);
-    int cur = w == 0 ? first_small : -1;
-    int held = (w == 0 && lane32 == 0) ? next : -1;
-    for (;;) {
-        if (cur < 0) {
-            int c2 = 0;
-            if (lane32 == 0) {
-                if (held >= 0) {
-                    c2 = held;
-                    held = -1;
-                } else {
-                    c2 = atomicAdd(a.queue, 1);
-                }
-            }
-            cur = __shfl_sync(0xffffffffu, c2, 0);
-        }
-        if (cur >= nitems) break;
-        warp_item<TABLE, CELL, ZSAFE>(a, a.items[cur], wcvt, tab, dirt, lane32);
-        cur = -1;
-    }
+    warp_loop<TABLE, CELL, ZSAFE>(a, nitems, w == 0 ? first_small : -1,
+                                  (w == 0 && lane32 == 0) ? next : -1,
+                                  cvt + w * (2 * 2 * kWarpTJ), cr + w * 2 * kCellTab, tab, dirt,
+                                  lane32);
 }
 
 // ------------------------------------------------------------------ host
 size_t groups_smem(int np, bool table, int ntab)
 {
-    size_t s = kTJG * 4 * sizeof(u64) + 8 * np * kNT * sizeof(u64) + 28 * 16 + 16;
+    size_t s = kTJG * 4 * sizeof(u64) + 8 * np * kNT * sizeof(u64) + 28 * 16 + 16 +
+               8 * kCellTab * sizeof(int);
     if (table) s += (size_t)ntab * sizeof(float2);
     return s;
 }
@@ -679,31 +863,37 @@ cudaError_t launch_group_ctr(const double4 *xi, const long long *i_off, long lon
 }
 
 // ------------------------------------------------------------------ cell list
-// Periodic cube of side box, nc cells per axis (side box/nc >= r_cut).
-__device__ __forceinline__ int cell_axis(double x, double box, int nc)
+// Periodic cube of side box, nc cells per axis (side box/nc >= r_cut). The
+// FP64 pipe is narrow, so the per-particle work uses multiplies by the
+// host's 1/box and nc/box instead of divisions.
+__device__ __forceinline__ double wrap_box(double x, double box, double inv_box)
 {
-    double w = x - box * floor(x / box);          // wrap into [0, box)
-    int c = (int)(w * (nc / box));
-    return c < 0 ? 0 : c >= nc ? nc - 1 : c;
+    if (x >= 0.0 && x < box) return x;            // already inside: unchanged
+    double w = x - box * floor(x * inv_box);
+    if (w >= box) w -= box;                       // rounding can land on box
+    if (w < 0.0) w += box;                        // or just below 0
+    return w;
+}
+
+__device__ __forceinline__ int cell_axis(double w, double per_len, int nc)
+{
+    const int c = (int)(w * per_len);             // w >= 0: truncation is floor
+    return c >= nc ? nc - 1 : c;
 }
 
 // wrapped positions (x, y, z, m) and the cell key of every particle
-__global__ void k_cell_key(const double4 *__restrict__ jrec, long long n, double box, int nc,
-                           unsigned *__restrict__ key, unsigned *__restrict__ idx,
-                           double4 *__restrict__ wrapped)
+__global__ void k_cell_key(const double4 *__restrict__ jrec, long long n, double box,
+                           double inv_box, double per_len, int nc, unsigned *__restrict__ key,
+                           unsigned *__restrict__ idx, double4 *__restrict__ wrapped)
 {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double4 v = jrec[i];
-    double wx = v.x - box * floor(v.x / box);
-    double wy = v.y - box * floor(v.y / box);
-    double wz = v.z - box * floor(v.z / box);
-    // floor can leave w == box for tiny negative inputs; fold it back
-    if (wx >= box) wx -= box;
-    if (wy >= box) wy -= box;
-    if (wz >= box) wz -= box;
+    const double4 v = jrec[i];
+    const double wx = wrap_box(v.x, box, inv_box), wy = wrap_box(v.y, box, inv_box),
+                 wz = wrap_box(v.z, box, inv_box);
     wrapped[i] = make_double4(wx, wy, wz, v.w);
-    int cx = cell_axis(wx, box, nc), cy = cell_axis(wy, box, nc), cz = cell_axis(wz, box, nc);
+    const int cx = cell_axis(wx, per_len, nc), cy = cell_axis(wy, per_len, nc),
+              cz = cell_axis(wz, per_len, nc);
     key[i] = (unsigned)((cx * nc + cy) * nc + cz);
     idx[i] = (unsigned)i;
 }
@@ -717,7 +907,7 @@ __global__ void k_cell_count(const unsigned *__restrict__ key, long long n, unsi
 // particles in cell order, as FP32 offsets from their cell's corner in the
 // table's scaled units (the FP64 corner is implicit in the cell index)
 __global__ void k_cell_gather(const double4 *__restrict__ wrapped, const unsigned *__restrict__ perm,
-                              const unsigned *__restrict__ key, long long n, int nc, double box,
+                              const unsigned *__restrict__ key, long long n, int nc, double h,
                               double scale, double4 *__restrict__ xs, float4 *__restrict__ xo)
 {
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -726,9 +916,9 @@ __global__ void k_cell_gather(const double4 *__restrict__ wrapped, const unsigne
     xs[p] = w;
     unsigned c = key[p];
     int cx = (int)(c / ((unsigned)nc * nc)), cy = (int)((c / nc) % nc), cz = (int)(c % nc);
-    double h = box / nc;
-    xo[p] = make_float4((float)((w.x - cx * h) * scale), (float)((w.y - cy * h) * scale),
-                        (float)((w.z - cz * h) * scale), (float)w.w);
+    xo[p] = make_float4((float)(fma(-(double)cx, h, w.x) * scale),
+                        (float)(fma(-(double)cy, h, w.y) * scale),
+                        (float)(fma(-(double)cz, h, w.z) * scale), (float)w.w);
 }
 
 // per cell: number of j entries (27 neighbour cells) and number of items
@@ -752,12 +942,6 @@ __global__ void k_cell_sizes(const unsigned *__restrict__ start, int nc, int Bi,
     icount[g] = (ni + Bi - 1) / Bi;
 }
 
-__global__ void k_joff_widen(const unsigned *__restrict__ in, long long n, long long *__restrict__ out)
-{
-    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (k < n) out[k] = in[k];
-}
-
 __global__ void k_fill_iota(unsigned *__restrict__ v, long long n)
 {
     long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -774,30 +958,6 @@ __global__ void k_cell_pairs(const unsigned *__restrict__ start, const unsigned 
         s += (unsigned long long)(start[g + 1] - start[g]) * jcount[g];
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(pairs, s);
-}
-
-// one CTA per cell: its j-list, neighbour by neighbour, each entry carrying
-// the direction code of its neighbour cell
-__global__ void k_cell_lists(const unsigned *__restrict__ start, int nc,
-                             const unsigned *__restrict__ joff, int *__restrict__ jlist)
-{
-    long long g = blockIdx.x;
-    unsigned ni = start[g + 1] - start[g];
-    if (ni == 0) return;
-    int cx = (int)(g / (nc * nc)), cy = (int)((g / nc) % nc), cz = (int)(g % nc);
-    unsigned pos = joff[g];
-    for (int dx = -1; dx <= 1; ++dx)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dz = -1; dz <= 1; ++dz) {
-                int x = (cx + dx + nc) % nc, y = (cy + dy + nc) % nc, z = (cz + dz + nc) % nc;
-                long long nb = ((long long)x * nc + y) * nc + z;
-                // direction from the i-cell to the j-cell (the wrap is implicit in it)
-                int code = 9 * (dx + 1) + 3 * (dy + 1) + (dz + 1);
-                unsigned b = start[nb], cnt = start[nb + 1] - b;
-                for (unsigned k = threadIdx.x; k < cnt; k += blockDim.x)
-                    jlist[pos + k] = (int)((b + k) | ((unsigned)code << 27));
-                pos += cnt;
-            }
 }
 
 // one item per (cell, chunk of <= Bi i-particles), keyed longest-first
@@ -820,7 +980,7 @@ __global__ void k_cell_items(const unsigned *__restrict__ start, long long ncell
         // CTA-sized items first, longest first; then the warp-sized ones
         unsigned long long cost = ((unsigned long long)it.ni * jcount[g]) >> 2;
         unsigned cq = cost > 0x7fffffull ? 0x7fffffu : (unsigned)cost;
-        const bool small = it.ni <= kWarpItemNi;
+        const bool small = it.ni <= kWarpItemNi && (long long)it.ni * jcount[g] <= kWarpItemPairs;
         keys[o + k] = ((small ? 1u : 0u) << 23) | (0x7fffffu - cq);
         vals[o + k] = o + k;
         if (!small) atomicAdd(ncta, 1u);
@@ -834,23 +994,14 @@ __global__ void k_items_permute(const GroupItem *__restrict__ in, const unsigned
     if (k < (long long)*nitems) out[k] = in[order[k]];
 }
 
-__global__ void k_cell_ctr(int nc, double box, double4 *__restrict__ ctr)
-{
-    long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    long long ncell = (long long)nc * nc * nc;
-    if (g >= ncell) return;
-    int cx = (int)(g / (nc * nc)), cy = (int)((g / nc) % nc), cz = (int)(g % nc);
-    double h = box / nc;
-    ctr[g] = make_double4((cx + 0.5) * h, (cy + 0.5) * h, (cz + 0.5) * h, 0.0);
-}
-
 cudaError_t launch_cell_build(const double4 *jrec, long long n, double box, int nc, int Bi,
                               double scale, CellScratch &s, SortScratch &sort, cudaStream_t st)
 {
     long long ncell = (long long)nc * nc * nc;
     unsigned gb = (unsigned)((n + 255) / 256);
     unsigned gc = (unsigned)((ncell + 255) / 256);
-    k_cell_key<<<gb, 256, 0, st>>>(jrec, n, box, nc, sort.keys[0], sort.vals[0], s.wrapped);
+    k_cell_key<<<gb, 256, 0, st>>>(jrec, n, box, 1.0 / box, nc / box, nc, sort.keys[0], sort.vals[0],
+                                   s.wrapped);
     unsigned *ko, *perm;
     int bits = 0;
     while ((1LL << bits) < ncell) ++bits;
@@ -863,16 +1014,10 @@ cudaError_t launch_cell_build(const double4 *jrec, long long n, double box, int 
     cudaMemsetAsync(s.start, 0, (ncell + 1) * sizeof(unsigned), st);
     k_cell_count<<<gb, 256, 0, st>>>(ko, n, s.start);
     if ((e = launch_excl_scan(s.start, ncell + 1, sort.sums, st)) != cudaSuccess) return e;
-    k_cell_gather<<<gb, 256, 0, st>>>(s.wrapped, perm, ko, n, nc, box, scale, s.xs, s.xo);
+    k_cell_gather<<<gb, 256, 0, st>>>(s.wrapped, perm, ko, n, nc, box / nc, scale, s.xs, s.xo);
     k_cell_sizes<<<gc, 256, 0, st>>>(s.start, nc, Bi, s.jcount, s.icount);
     cudaMemsetAsync(s.pairs, 0, sizeof(unsigned long long), st);
     k_cell_pairs<<<gc < 1024 ? gc : 1024, 256, 0, st>>>(s.start, s.jcount, ncell, s.pairs);
-    // j offsets (exclusive scan of jcount, ncell + 1 entries with a zero tail)
-    cudaMemcpyAsync(s.joff32, s.jcount, ncell * sizeof(unsigned), cudaMemcpyDeviceToDevice, st);
-    cudaMemsetAsync(s.joff32 + ncell, 0, sizeof(unsigned), st);
-    if ((e = launch_excl_scan(s.joff32, ncell + 1, sort.sums, st)) != cudaSuccess) return e;
-    k_joff_widen<<<(unsigned)((ncell + 1 + 255) / 256), 256, 0, st>>>(s.joff32, ncell + 1, s.joff);
-    k_cell_lists<<<(unsigned)ncell, 128, 0, st>>>(s.start, nc, s.joff32, s.jlist);
     // items
     cudaMemcpyAsync(s.ioff, s.icount, ncell * sizeof(unsigned), cudaMemcpyDeviceToDevice, st);
     cudaMemsetAsync(s.ioff + ncell, 0, sizeof(unsigned), st);
@@ -889,7 +1034,6 @@ cudaError_t launch_cell_build(const double4 *jrec, long long n, double box, int 
         return e;
     k_items_permute<<<(unsigned)((s.item_cap + 255) / 256), 256, 0, st>>>(s.items_raw, order,
                                                                           s.ioff + ncell, s.items);
-    k_cell_ctr<<<gc, 256, 0, st>>>(nc, box, s.ctr);
     return cudaGetLastError();
 }
 

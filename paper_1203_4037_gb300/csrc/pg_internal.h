@@ -73,8 +73,8 @@ struct GroupItem {
 struct GroupArgs {
     const double4 *xi;     // i positions (x, y, z, -)
     const double4 *jrec;   // j records (x, y, z, m)
-    const long long *j_off;        // CSR offsets into jlist, ngroups + 1
-    const int *jlist;      // j indices; periodic: low 27 bits index, high 5 bits shift code
+    const long long *j_off;        // group mode: CSR offsets into jlist, ngroups + 1
+    const int *jlist;      // group mode: j indices (low 27 bits)
     const GroupItem *items;
     const double4 *gctr;   // FP64 centre of each group
     int nitems;            // item count, or -1: read *nitems_dev
@@ -89,6 +89,8 @@ struct GroupArgs {
     const float4 *ihl;     // FP64 mode: i positions as (hi, -), (lo, -) FP32 pairs
     const float4 *xo;      // cell mode: FP32 offset records (o, m) in scaled units
     float cell_h;          // cell mode: cell side in scaled units
+    const unsigned *cstart;        // cell mode: first particle of each cell, ncell + 1
+    int nc;                // cell mode: cells per box side (>= 3)
     const unsigned *perm;  // i index -> output index (nullptr: identity)
     double accscale;
     double *acc, *pot;
@@ -171,15 +173,11 @@ struct CellScratch {
     float4 *xo;            // n: FP32 offsets from the cell corner (scaled) + mass, cell order
     unsigned *perm;        // n: cell order -> input index (own copy)
     unsigned *start;       // ncell + 1: first particle of each cell
-    unsigned *jcount;      // ncell
-    unsigned *icount;      // ncell
-    unsigned *joff32;      // ncell + 1
-    long long *joff;       // ncell + 1
+    unsigned *jcount;      // ncell: particles in the 27 neighbour cells
+    unsigned *icount;      // ncell: items of each cell
     unsigned *ioff;        // ncell + 1 (ioff[ncell] = number of items)
-    int *jlist;            // 27 n entries
     GroupItem *items_raw;  // item_cap
     GroupItem *items;      // item_cap, longest first
-    double4 *ctr;          // ncell cell centres
     long long item_cap;
     unsigned long long *pairs;   // evaluated pairs of the build (device)
     unsigned *ncta;        // number of CTA-mode items (they sort first)

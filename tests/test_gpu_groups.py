@@ -59,8 +59,10 @@ def test_graph_replay_matches(pg, small):
 def test_ragged_and_empty_groups(pg, orc):
     rng = np.random.default_rng(3)
     xj, mj = gen.plummer(6000, 5)
-    sizes_i = [1, 15, 16, 17, 0, 511, 512, 513, 1500, 3]
-    sizes_j = [1, 7, 511, 512, 513, 3000, 0, 1025, 64, 6000]
+    # the last two are small items with empty lists, which run one after the
+    # other in warp mode
+    sizes_i = [1, 15, 16, 17, 0, 511, 512, 513, 1500, 3, 5, 2]
+    sizes_j = [1, 7, 511, 512, 513, 3000, 0, 1025, 64, 6000, 0, 0]
     i_off = np.concatenate([[0], np.cumsum(sizes_i)])
     j_off = np.concatenate([[0], np.cumsum(sizes_j)])
     jlist = np.concatenate([rng.integers(0, len(xj), k) for k in sizes_j]).astype(np.int32)
