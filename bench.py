@@ -252,6 +252,31 @@ def extra_rows(pg, torch, dev, peak_newton, headline_rate):
         rows["newton_plummer_4096"] = {"interactions_per_s": 4096 * 4096 / (ms * 1e-3),
                                        "us_per_call": ms * 1e3, "graph": True}
 
+    # individual time steps: the i-set is the n_i densest-core particles of the
+    # 2^20 mixed set (those with the shortest steps), j = all 2^20; per call
+    # through the device API with the path chosen automatically (narrow)
+    n = N_PART
+    x, m = gen.plummer_cube_mix(n, gen.CONFIG_SEEDS[2])
+    xd, md = torch.tensor(x, device=dev), torch.tensor(m, device=dev)
+    order = np.argsort(np.linalg.norm(x, axis=1))
+    steps = {}
+    for ni in (16, 64, 256, 1024):
+        xi = torch.tensor(x[order[:ni]], device=dev)
+        a = torch.empty_like(xi)
+        with pg.Context(idx) as c:
+            c.set_stream(st.cuda_stream)
+            c.set_eps(1e-3)
+            c.set_timing(True)
+            c.set_j_dev(xd, md)
+            c.set_i_dev(xi)
+            ms = _time_call(torch, lambda: c.run_dev(a), 50, warm=5)
+            kms = c.kernel_time()
+            steps[str(ni)] = {"us_per_call": ms * 1e3, "kernel_us": kms * 1e3,
+                              "interactions_per_s": ni * n / (ms * 1e-3),
+                              "j_chunks": c.info()["slots"]}
+    rows["individual_steps_ni_vs_2e20"] = steps
+    del xd, md
+
     # tabulated all-pairs: 65536 Plummer, Gaussian split, r_cut = 0.1, E=3, F=5
     n = 65536
     x, m = gen.plummer(n, gen.CONFIG_SEEDS[5])

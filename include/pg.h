@@ -57,6 +57,11 @@ typedef struct pg_ctx pg_ctx;
 #define PG_NEWTON 0
 #define PG_TABLE 1
 
+/* all-pairs paths (pg_set_allpairs_path) */
+#define PG_PATH_AUTO 0    /* narrow for ni <= 4096 against nj >= 64 ni, else tiled */
+#define PG_PATH_TILED 1   /* i tiles of 256 to 1024 particles, j split across CTAs */
+#define PG_PATH_NARROW 2  /* few i against many j: (i chunk, j chunk) items */
+
 /* Open a context on CUDA device `device` (g5_open, Section 3.6; no rsqrt
  * bias calibration: the GPU's rsqrt has a documented error bound instead).
  * *out receives the handle; destroy it with pg_destroy. The context starts
@@ -180,6 +185,20 @@ int pg_set_graph(pg_ctx *ctx, int on);
 /* Time the candidate launch shapes of the current workload (i per thread,
  * CTAs per SM) on the device and keep the fastest. Synchronises. */
 int pg_tune(pg_ctx *ctx);
+
+/* Path of the all-pairs force loop (no groups, no periodic box); both give
+ * the same sums up to FP32 rounding order. PG_PATH_TILED gives every CTA a
+ * tile of i-particles in registers and a share of the j records, combining
+ * the shares in FP64. PG_PATH_NARROW serves the individual time step regime
+ * (Section 5: a step evaluates only the particles due for an update, often
+ * tens to hundreds against all N): the i-set is cut into chunks and the j
+ * records into chunks of equal length, every (i chunk, j chunk) pair is one
+ * work item of the batched-group kernel (one warp per item when the i chunk
+ * and the j chunk are small), and each i's FP64 partial sums are added in
+ * j-chunk order. The path is chosen per call; pg_info's slots reports the
+ * number of j chunks on the narrow path. Returns PG_EINVAL for another
+ * value. */
+int pg_set_allpairs_path(pg_ctx *ctx, int path);
 
 /* Launch shape override: i per thread = 2*np (np in {1, 2, 4}; 0 = chosen
  * by problem size, the default),

@@ -22,6 +22,7 @@ from . import _build
 
 PG_OK, PG_EINVAL, PG_ESTATE, PG_ENOMEM, PG_ECUDA, PG_ETIMEOUT = 0, -1, -2, -3, -4, -5
 PG_NEWTON, PG_TABLE = 0, 1
+PG_PATH_AUTO, PG_PATH_TILED, PG_PATH_NARROW = 0, 1, 2
 
 STATUS_NAMES = {0: "PG_OK", -1: "PG_EINVAL", -2: "PG_ESTATE", -3: "PG_ENOMEM", -4: "PG_ECUDA",
                 -5: "PG_ETIMEOUT"}
@@ -63,6 +64,7 @@ SIGNATURES = {
     "pg_set_graph": (_I, [_P, _I]),
     "pg_tune": (_I, [_P]),
     "pg_set_shape": (_I, [_P, _I, _I, _I]),
+    "pg_set_allpairs_path": (_I, [_P, _I]),
     "pg_set_timing": (_I, [_P, _I]),
     "pg_kernel_time": (_I, [_P, C.POINTER(_D)]),
     "pg_info": (_I, [_P, C.POINTER(_LL), _I]),
@@ -253,6 +255,10 @@ def pg_tune(ctx):
     return _check(ctx, lib().pg_tune(ctx))
 
 
+def pg_set_allpairs_path(ctx, path):
+    return _check(ctx, lib().pg_set_allpairs_path(ctx, int(path)))
+
+
 def pg_set_shape(ctx, np_, ctas_per_sm=0, packed=-1):
     return _check(ctx, lib().pg_set_shape(ctx, int(np_), int(ctas_per_sm), int(packed)))
 
@@ -388,6 +394,9 @@ class Context:
 
     def set_graph(self, on=True):
         pg_set_graph(self.h, on)
+
+    def set_allpairs_path(self, path):
+        pg_set_allpairs_path(self.h, path)
 
     def set_shape(self, np_, ctas_per_sm=0, packed=-1):
         pg_set_shape(self.h, np_, ctas_per_sm, packed)

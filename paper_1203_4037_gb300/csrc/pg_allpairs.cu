@@ -430,10 +430,61 @@ __global__ void k_combine(CombineArgs c)
     if (c.pot) c.pot[k] = c.newton ? ph : 0.0;
 }
 
+// The same sum with a 128-thread block per i, for few i-particles with many
+// partial slots (a single thread per i would walk hundreds of dependent
+// loads): thread t adds slots t, t + 128, ..., a fixed butterfly adds each
+// warp's lanes and thread 0 the four warps in order, so the result does not
+// depend on the run.
+constexpr int kWideThreads = 128;
+
+__global__ void __launch_bounds__(kWideThreads) k_combine_wide(CombineArgs c)
+{
+    __shared__ double4 wsum[kWideThreads / 32];
+    const long long p = blockIdx.x;
+    const int lane = threadIdx.x & 31;
+    const long long t = p / c.Bi;
+    const int li = (int)(p % c.Bi);
+    double ax = 0, ay = 0, az = 0, ph = 0;
+    if (c.njsub > 0) {
+        const long long bf = stream_k_owner(t * c.njsub, c.grid, c.W);
+        const long long bl = stream_k_owner((t + 1) * c.njsub - 1, c.grid, c.W);
+        for (long long s = threadIdx.x; s <= bl - bf; s += kWideThreads) {
+            const double4 v = c.part[((size_t)t * c.smax_slots + (size_t)s) * c.Bi + li];
+            ax += v.x; ay += v.y; az += v.z; ph += v.w;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        az += __shfl_xor_sync(0xffffffffu, az, o);
+        ph += __shfl_xor_sync(0xffffffffu, ph, o);
+    }
+    if (lane == 0) wsum[threadIdx.x >> 5] = make_double4(ax, ay, az, ph);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    ax = ay = az = ph = 0;
+    for (int w = 0; w < kWideThreads / 32; ++w) {
+        ax += wsum[w].x; ay += wsum[w].y; az += wsum[w].z; ph += wsum[w].w;
+    }
+    const long long k = c.perm ? (long long)c.perm[p] : p;
+    if (c.newton && c.self && c.eps2 > 0.0f && c.njsub > 0) {
+        const float mk = (float)c.jrec[k].w;
+        ph += (double)__fmul_rn(mk, rsq(c.eps2));
+    }
+    c.acc[3 * k] = ax * c.accscale;
+    c.acc[3 * k + 1] = ay * c.accscale;
+    c.acc[3 * k + 2] = az * c.accscale;
+    if (c.pot) c.pot[k] = c.newton ? ph : 0.0;
+}
+
 cudaError_t launch_combine(const CombineArgs &c, cudaStream_t st)
 {
     if (c.ni <= 0) return cudaSuccess;
-    k_combine<<<(unsigned)((c.ni + 255) / 256), 256, 0, st>>>(c);
+    if (c.smax_slots >= 32)
+        k_combine_wide<<<(unsigned)c.ni, kWideThreads, 0, st>>>(c);
+    else
+        k_combine<<<(unsigned)((c.ni + 255) / 256), 256, 0, st>>>(c);
     return cudaGetLastError();
 }
 

@@ -137,6 +137,20 @@ __device__ __forceinline__ int cell_find(const int *cr, int p)
     return d;
 }
 
+// item k of the queue: stored, or for narrow all-pairs the (i chunk, j chunk)
+// pair k / nchunks, k mod nchunks
+__device__ __forceinline__ GroupItem item_at(const GroupArgs &a, int k)
+{
+    if (a.jchunk == 0) return a.items[k];
+    GroupItem it;
+    const int ic = k / a.nchunks;
+    it.group = ic;
+    it.i0 = ic * a.ichunk;
+    it.ni = (int)min((long long)a.ichunk, a.ni - it.i0);
+    it.pad = k - ic * a.nchunks;
+    return it;
+}
+
 template <int NP, bool TABLE, bool CELL, bool ZSAFE>
 __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &it, const ItemShape sh,
                                            u64 *cvt, u64 *run, int *cr, const float2 *tab,
@@ -147,6 +161,9 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
         if (tid < 32) cell_ranges(a, it.group, tid, cr);
         __syncthreads();
         je = cr[27];
+    } else if (a.jchunk > 0) {
+        jb = (long long)it.pad * a.jchunk;
+        je = min(jb + a.jchunk, a.nj);
     } else {
         jb = a.j_off[it.group];
         je = a.j_off[it.group + 1];
@@ -214,7 +231,7 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
                 code[r] = cell_find(cr, (int)e);
                 j = (long long)cr[32 + code[r]] + e;
             } else {
-                j = (ok ? a.jlist[e] : 0) & 0x07ffffff;
+                j = a.jlist ? (ok ? a.jlist[e] : 0) & 0x07ffffff : e;
             }
             if (ok && (j < 0 || j >= a.nj)) {   // bad index: record it, contribute nothing
                 report(a.status, kStatusBadIndex, 2);
@@ -352,6 +369,11 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
                 int k = set * 2 * NP + 2 * p + q;
                 if (k < it.ni) {
                     long long i = it.i0 + k;
+                    if (a.part) {          // one partial of a narrow all-pairs sum
+                        a.part[(long long)it.pad * a.part_stride + i] =
+                            make_double4(v[0 + q], v[2 + q], v[4 + q], TABLE ? 0.0 : v[6 + q]);
+                        continue;
+                    }
                     long long o = a.perm ? (long long)a.perm[i] : i;
                     a.acc[3 * o] = v[0 + q] * a.accscale;
                     a.acc[3 * o + 1] = v[2 + q] * a.accscale;
@@ -381,13 +403,19 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
                                           const float4 *dirt, int lane32)
 {
     constexpr unsigned kFull = 0xffffffffu;
-    int pend = 0;                       // lane 0: the claim in flight
-    if (lane32 == 0) pend = held >= 0 ? held : atomicAdd(a.queue, 1);
+    int pend = -1;                      // lane 0: a claimed item not yet started
+    if (lane32 == 0) pend = held;
     if (cur < 0) {
-        cur = __shfl_sync(kFull, pend, 0);
-        if (lane32 == 0 && cur < nitems) pend = atomicAdd(a.queue, 1);
+        int c2 = 0;
+        if (lane32 == 0) {
+            c2 = pend >= 0 ? pend : atomicAdd(a.queue, 1);
+            pend = -1;
+        }
+        cur = __shfl_sync(kFull, c2, 0);
     }
     if (cur >= nitems) return;
+    // claims run one item ahead while more than one item per warp is left
+    const int ahead_limit = nitems - (int)gridDim.x * (kNT / 32);
 
     const float c0 = TABLE ? 2.0f : a.eps2;
     const u64 c0v = pk2(c0, c0);
@@ -404,6 +432,9 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
             __syncwarp();
             jb = 0;
             je = cr[27];
+        } else if (a.jchunk > 0) {
+            jb = (long long)it.pad * a.jchunk;
+            je = min(jb + a.jchunk, a.nj);
         } else {
             jb = a.j_off[it.group];
             je = a.j_off[it.group + 1];
@@ -425,7 +456,7 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
                 code[r] = cell_find(cr, (int)e);
                 j = (long long)cr[32 + code[r]] + e;
             } else {
-                j = (ok ? a.jlist[e] : 0) & 0x07ffffff;
+                j = a.jlist ? (ok ? a.jlist[e] : 0) & 0x07ffffff : e;
             }
             if (ok && (j < 0 || j >= a.nj)) {
                 report(a.status, kStatusBadIndex, 4);
@@ -473,7 +504,7 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
         }
     };
 
-    GroupItem it = a.items[cur];
+    GroupItem it = item_at(a, cur);
     int slot = 0;
     long long jb, je;
     setup(it, wcr, jb, je);
@@ -481,13 +512,11 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
     Shape sp = shape_of(min(64, it.ni));
     load_i(it, 0, sp);
     for (;;) {
-        // the next item: take the claim in flight, claim the one after it,
-        // start loading its record
-        const int nxt = __shfl_sync(kFull, pend, 0);
-        const bool more = nxt < nitems;
-        if (lane32 == 0 && more) pend = atomicAdd(a.queue, 1);
+        // claim the next item now (its latency hides behind this one) while
+        // the queue is long; in its last stretch only once this one is done
+        if (lane32 == 0 && pend < 0 && cur < ahead_limit) pend = atomicAdd(a.queue, 1);
+        int nxt = nitems;
         GroupItem itn = it;
-        if (more) itn = a.items[nxt];
         const int *crc = wcr + slot * kCellTab;
         int *crn = wcr + (slot ^ 1) * kCellTab;
         long long jbn = 0, jen = 0;
@@ -550,12 +579,17 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
                 // or the next item's range, i-particles and first tile
                 if (t0 + kWarpTJ < je) {
                     fetch(t0 + kWarpTJ, je, crc);
-                } else if (last_pass && more) {
-                    setup(itn, crn, jbn, jen);
-                    fetch(jbn, jen, crn);
-                    spn = shape_of(min(64, itn.ni));
-                    load_i(itn, 0, spn);
-                    staged = true;
+                } else if (last_pass) {
+                    const int claimed = __shfl_sync(kFull, pend, 0);
+                    if (claimed >= 0 && claimed < nitems) {
+                        nxt = claimed;
+                        itn = item_at(a, nxt);
+                        setup(itn, crn, jbn, jen);
+                        fetch(jbn, jen, crn);
+                        spn = shape_of(min(64, itn.ni));
+                        load_i(itn, 0, spn);
+                        staged = true;
+                    }
                 }
                 if (active) {
                     u64 ax = 0, ay = 0, az = 0, ph = 0;
@@ -640,22 +674,32 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
                 }
                 if (oi < nout) {
                     const long long i = it.i0 + i0 + ip;
-                    const long long o = a.perm ? (long long)a.perm[i] : i;
                     const double v = (double)vh + (double)vl;
-                    if (comp < 3)
-                        a.acc[3 * o + comp] = v * a.accscale;
-                    else if (a.pot)
-                        a.pot[o] = v;     // zero in table mode
+                    if (a.part) {          // one partial of a narrow all-pairs sum
+                        reinterpret_cast<double *>(a.part + (long long)it.pad * a.part_stride + i)[comp] = v;
+                    } else {
+                        const long long o = a.perm ? (long long)a.perm[i] : i;
+                        if (comp < 3)
+                            a.acc[3 * o + comp] = v * a.accscale;
+                        else if (a.pot)
+                            a.pot[o] = v;     // zero in table mode
+                    }
                 }
             }
         }
-        if (!more) return;
-        if (!staged) {             // the item had no j tile to overlap with
+        if (!staged) {             // nothing claimed ahead, or no j tile to overlap with
+            int c2 = 0;
+            if (lane32 == 0) c2 = pend >= 0 ? pend : atomicAdd(a.queue, 1);
+            nxt = __shfl_sync(kFull, c2, 0);
+            if (nxt >= nitems) return;
+            itn = item_at(a, nxt);
             setup(itn, crn, jbn, jen);
             fetch(jbn, jen, crn);
             spn = shape_of(min(64, itn.ni));
             load_i(itn, 0, spn);
         }
+        if (lane32 == 0) pend = -1;
+        cur = nxt;
         it = itn;
         jb = jbn;
         je = jen;
@@ -687,16 +731,20 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
 
     const int warp_from = a.warp_from >= 0 ? a.warp_from : (int)*a.warp_from_dev;
 
-    // the next item is claimed while the current one runs (kept in a
-    // register of thread 0), so the queue's atomic latency overlaps work
-    int next = 0;
-    if (tid == 0) next = atomicAdd(a.queue, 1);
+    // Thread 0 claims the next item while the current one runs (kept in a
+    // register), so the queue's atomic latency overlaps work, as long as more
+    // than one item per CTA is left; in that last stretch it claims only once
+    // the current item is done, so that no CTA holds an item another could
+    // start.
+    int next = -1;
+    const int ahead_limit = nitems - (int)gridDim.x;
     int first_small = -1;
     for (;;) {
         __syncthreads();   // previous item fully done with shared memory
         if (tid == 0) {
-            sh[0] = next;
-            if (next < nitems) next = atomicAdd(a.queue, 1);
+            const int cur = next >= 0 ? next : atomicAdd(a.queue, 1);
+            sh[0] = cur;
+            next = cur < ahead_limit ? atomicAdd(a.queue, 1) : -1;
         }
         __syncthreads();
         const int item = sh[0];
@@ -705,7 +753,7 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
             first_small = item;
             break;
         }
-        const GroupItem it = a.items[item];
+        const GroupItem it = item_at(a, item);
         if (NPMAX > 1 && it.ni <= kNT * NPMAX) {
             const ItemShape big = item_shape(it.ni, NPMAX);
             const ItemShape small = item_shape(it.ni, NPMAX / 2);
@@ -808,6 +856,64 @@ cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, bool
     return cudaErrorInvalidValue;
 }
 
+// Narrow all-pairs: the sum over j chunks of each i's FP64 partials in a
+// fixed order (so the result does not depend on which CTA ran which item),
+// then the same self-pair correction and scaling as the tiled path.
+// One 128-thread block per i: thread t adds chunks t, t + 128, ..., a fixed
+// butterfly adds each warp's lanes and thread 0 the four warps in order
+// (hundreds of chunks would be a long chain of dependent loads for one
+// thread).
+constexpr int kCombineThreads = 128;
+
+__global__ void __launch_bounds__(kCombineThreads)
+k_group_partials_combine(const double4 *__restrict__ part, int nchunks, long long ni,
+                         double accscale, int newton, int self, float eps2,
+                         const double4 *__restrict__ jrec, double *__restrict__ acc,
+                         double *__restrict__ pot)
+{
+    __shared__ double4 wsum[kCombineThreads / 32];
+    const long long i = blockIdx.x;
+    const int t = threadIdx.x, lane = t & 31;
+    double ax = 0, ay = 0, az = 0, ph = 0;
+    for (int k = t; k < nchunks; k += kCombineThreads) {
+        const double4 v = part[(long long)k * ni + i];
+        ax += v.x; ay += v.y; az += v.z; ph += v.w;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        az += __shfl_xor_sync(0xffffffffu, az, o);
+        ph += __shfl_xor_sync(0xffffffffu, ph, o);
+    }
+    if (lane == 0) wsum[t >> 5] = make_double4(ax, ay, az, ph);
+    __syncthreads();
+    if (t != 0) return;
+    ax = ay = az = ph = 0;
+    for (int w = 0; w < kCombineThreads / 32; ++w) {
+        ax += wsum[w].x; ay += wsum[w].y; az += wsum[w].z; ph += wsum[w].w;
+    }
+    if (newton && self && eps2 > 0.0f) {
+        // the list held i's own pair (d = 0 exactly): it added -m_i rsqrt(eps^2)
+        ph += (double)__fmul_rn((float)jrec[i].w, rsq(eps2));
+    }
+    acc[3 * i] = ax * accscale;
+    acc[3 * i + 1] = ay * accscale;
+    acc[3 * i + 2] = az * accscale;
+    if (pot) pot[i] = newton ? ph : 0.0;
+}
+
+cudaError_t launch_group_partials_combine(const double4 *part, int nchunks, long long ni,
+                                          double accscale, bool newton, bool self, float eps2,
+                                          const double4 *jrec, double *acc, double *pot,
+                                          cudaStream_t st)
+{
+    if (ni <= 0) return cudaSuccess;
+    k_group_partials_combine<<<(unsigned)ni, kCombineThreads, 0, st>>>(
+        part, nchunks, ni, accscale, newton ? 1 : 0, self ? 1 : 0, eps2, jrec, acc, pot);
+    return cudaGetLastError();
+}
+
 // double-float records: (hi, m) then (lo, 0) per particle, lo = x - hi
 __global__ void k_pack_hilo(const double4 *__restrict__ in, long long n, float4 *__restrict__ out)
 {
@@ -829,14 +935,19 @@ cudaError_t launch_pack_hilo(const double4 *in, long long n, float4 *out, cudaSt
 
 // ------------------------------------------------------------------ prep
 // FP64 centre of each group: midpoint of its i-particles' bounding box
+// group g holds i_off[g] .. i_off[g + 1], or without offsets the chunk
+// g chunk .. min((g + 1) chunk, ni)
 __global__ void k_group_ctr(const double4 *__restrict__ xi, const long long *__restrict__ i_off,
-                            long long ngroups, double4 *__restrict__ ctr)
+                            long long ngroups, long long chunk, long long ni,
+                            double4 *__restrict__ ctr)
 {
     long long g = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
     int lane = threadIdx.x & 31;
     if (g >= ngroups) return;
+    const long long ib = i_off ? i_off[g] : g * chunk;
+    const long long ie = i_off ? i_off[g + 1] : min((g + 1) * chunk, ni);
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (long long i = i_off[g] + lane; i < i_off[g + 1]; i += 32) {
+    for (long long i = ib + lane; i < ie; i += 32) {
         double4 v = xi[i];
         lo[0] = fmin(lo[0], v.x); lo[1] = fmin(lo[1], v.y); lo[2] = fmin(lo[2], v.z);
         hi[0] = fmax(hi[0], v.x); hi[1] = fmax(hi[1], v.y); hi[2] = fmax(hi[2], v.z);
@@ -855,10 +966,10 @@ __global__ void k_group_ctr(const double4 *__restrict__ xi, const long long *__r
 }
 
 cudaError_t launch_group_ctr(const double4 *xi, const long long *i_off, long long ngroups,
-                             double4 *ctr, cudaStream_t st)
+                             long long chunk, long long ni, double4 *ctr, cudaStream_t st)
 {
     if (ngroups <= 0) return cudaSuccess;
-    k_group_ctr<<<(unsigned)((ngroups + 3) / 4), 128, 0, st>>>(xi, i_off, ngroups, ctr);
+    k_group_ctr<<<(unsigned)((ngroups + 3) / 4), 128, 0, st>>>(xi, i_off, ngroups, chunk, ni, ctr);
     return cudaGetLastError();
 }
 

@@ -91,6 +91,14 @@ struct GroupArgs {
     float cell_h;          // cell mode: cell side in scaled units
     const unsigned *cstart;        // cell mode: first particle of each cell, ncell + 1
     int nc;                // cell mode: cells per box side (>= 3)
+    int jchunk;            // narrow all-pairs: item k is i chunk k / nchunks (ichunk
+                           // particles from (k / nchunks) ichunk, up to ni) against the
+                           // j records [pad jchunk, (pad + 1) jchunk), pad = k mod
+                           // nchunks; items are not stored. 0: stored items, lists
+    int nchunks, ichunk;
+    long long ni;
+    double4 *part;         // narrow all-pairs: raw FP64 sums (a, phi) per item,
+    long long part_stride; //   at part[pad * part_stride + i]; nullptr: write acc
     const unsigned *perm;  // i index -> output index (nullptr: identity)
     double accscale;
     double *acc, *pot;
@@ -163,7 +171,7 @@ size_t groups_smem(int np, bool table, int ntab);
 int groups_bi(int np);
 int groups_max_blocks_per_sm(int np, bool table, int ntab, bool cell);
 cudaError_t launch_group_ctr(const double4 *xi, const long long *i_off, long long ngroups,
-                             double4 *ctr, cudaStream_t st);
+                             long long chunk, long long ni, double4 *ctr, cudaStream_t st);
 
 // periodic cell list: particles binned and sorted by cell, one group per
 // cell whose j-list is the 27 neighbour cells with image shift codes
@@ -182,6 +190,10 @@ struct CellScratch {
     unsigned long long *pairs;   // evaluated pairs of the build (device)
     unsigned *ncta;        // number of CTA-mode items (they sort first)
 };
+cudaError_t launch_group_partials_combine(const double4 *part, int nchunks, long long ni,
+                                          double accscale, bool newton, bool self, float eps2,
+                                          const double4 *jrec, double *acc, double *pot,
+                                          cudaStream_t st);
 cudaError_t launch_cell_build(const double4 *jrec, long long n, double box, int nc, int Bi,
                               double scale, CellScratch &s, SortScratch &sort, cudaStream_t st);
 cudaError_t launch_excl_scan(unsigned *a, long long n, unsigned *sums, cudaStream_t st);
