@@ -101,6 +101,25 @@ __device__ __forceinline__ void report(int *status, int code, int where)
 }
 
 // ---------------------------------------------------------------- mbarrier
+// one {A, G1} table entry for s in [2, s_max]: byte offset from the FP32
+// bits of s by shift and mask, then a shared load (no integer multiply);
+// tbase = the table's shared address minus 8 times the index of s = 2
+__device__ __forceinline__ float2 tab_at(unsigned tbase, unsigned bits, int shift3)
+{
+    float2 v;
+    const unsigned addr = tbase + ((bits >> shift3) & ~7u);
+    asm("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+    return v;
+}
+
+// min(s, s_max) for s > 0 as the integer minimum of the FP32 bit patterns
+// (positive floats order like their bits; a NaN also maps to s_max): the
+// clamp then runs on the ALU pipe instead of the busier FMA pipe
+__device__ __forceinline__ float clamp_pos(float s, unsigned smax_bits)
+{
+    return __uint_as_float(min(__float_as_uint(s), smax_bits));
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);

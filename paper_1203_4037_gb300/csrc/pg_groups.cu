@@ -16,6 +16,10 @@
 namespace pg {
 
 constexpr int kTJG = 512;          // j entries staged per step
+
+// unroll depth of a CTA-mode item's j loop (measured on GB300: 8 for the
+// table lookups, whose latency wants more terms in flight; 2 for Newton)
+template <bool TABLE> struct GroupsUnrollJ { static constexpr int value = TABLE ? 8 : 2; };
 constexpr int kPerThread = kTJG / kNT;
 
 // Records come in two forms.
@@ -80,16 +84,6 @@ __device__ __forceinline__ ItemShape item_shape(int ni, int np)
     s.L = L;
     s.spw = div_small(32, L);
     return s;
-}
-
-// one {A, G1} table entry for s in [2, s_max]: byte offset from the FP32
-// bits of s by shift and mask, then a shared load (no integer multiply)
-__device__ __forceinline__ float2 tab_at(unsigned tbase, unsigned bits, int shift3)
-{
-    float2 v;
-    const unsigned addr = tbase + ((bits >> shift3) & ~7u);
-    asm("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
-    return v;
 }
 
 // Cell mode. The j-list of cell g is the particles of its 27 neighbour cells
@@ -181,6 +175,7 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
     const float scf = TABLE && !CELL ? (float)a.tab.scale : 1.0f;
     const int sh3 = a.tab.shift - 3;
     const unsigned tb0 = smem_u32(tab) - (a.tab.base << 3);
+    const unsigned smax_bits = __float_as_uint(a.tab.s_max);
     auto RH = [&](int p, int k) -> u64 & { return run[(8 * p + k) * kNT + tid]; };
     auto RL = [&](int p, int k) -> u64 & { return run[(8 * p + 4 + k) * kNT + tid]; };
 
@@ -283,7 +278,7 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
 #pragma unroll
             for (int p = 0; p < NP; ++p) ax[p] = ay[p] = az[p] = ph[p] = 0ull;
             const int nv_lane = (int)nv;
-#pragma unroll 2
+#pragma unroll(GroupsUnrollJ<TABLE>::value)
             for (int e = lane; e < nv_lane; e += L) {
                 const ulonglong2 xy = reinterpret_cast<const ulonglong2 *>(cvt)[e];
                 const ulonglong2 zm = reinterpret_cast<const ulonglong2 *>(cvt)[kTJG + e];
@@ -311,8 +306,8 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
                         ay[p] = f2fma(mq3, dy, ay[p]);
                         az[p] = f2fma(mq3, dz, az[p]);
                     } else {
-                        ra = fminf(ra, a.tab.s_max);
-                        rb = fminf(rb, a.tab.s_max);
+                        ra = clamp_pos(ra, smax_bits);
+                        rb = clamp_pos(rb, smax_bits);
                         const float2 ta = tab_at(tb0, __float_as_uint(ra), sh3);
                         const float2 tb = tab_at(tb0, __float_as_uint(rb), sh3);
                         const u64 g = pk2(__fmaf_rn(ra, ta.y, ta.x), __fmaf_rn(rb, tb.y, tb.x));
@@ -422,6 +417,7 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
     const float scf = TABLE && !CELL ? (float)a.tab.scale : 1.0f;
     const int sh3 = a.tab.shift - 3;
     const unsigned tb0 = smem_u32(tab) - (a.tab.base << 3);
+    const unsigned smax_bits = __float_as_uint(a.tab.s_max);
     ulonglong2 *sxy = reinterpret_cast<ulonglong2 *>(wcvt);            // [kWarpTJ]
     ulonglong2 *szm = sxy + kWarpTJ;                                   // [kWarpTJ]
 
@@ -617,8 +613,8 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
                             ay = f2fma(mq3, dy, ay);
                             az = f2fma(mq3, dz, az);
                         } else {
-                            ra = fminf(ra, a.tab.s_max);
-                            rb = fminf(rb, a.tab.s_max);
+                            ra = clamp_pos(ra, smax_bits);
+                            rb = clamp_pos(rb, smax_bits);
                             const float2 ta = tab_at(tb0, __float_as_uint(ra), sh3);
                             const float2 tb = tab_at(tb0, __float_as_uint(rb), sh3);
                             const u64 g = pk2(__fmaf_rn(ra, ta.y, ta.x), __fmaf_rn(rb, tb.y, tb.x));
