@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--shape", default=None,
                     help="np,packed launch shape of the force kernel (default: the library's)")
     ap.add_argument("--workload", default="newton",
-                    choices=["newton", "table", "cells", "groups", "backward"],
+                    choices=["newton", "table", "cells", "groups", "backward", "narrow"],
                     help="newton: the headline; the others time one row of the path alone "
                          "(for profiling) and print its measurements")
     return ap.parse_args()
@@ -404,6 +404,25 @@ def run_row(args):
                 kms = _time_kernel(c, lambda: c.backward_dev(w, dx, dm), reps=args.steps,
                                    warm=args.warmup)
         out.update(n=n, kernel_ms=kms, interactions_per_s=n * n / (kms * 1e-3))
+    elif args.workload == "narrow":
+        # individual time steps: --n core particles of the 2^20 mixed set
+        # against all 2^20 (default 16), path chosen automatically
+        x, m = gen.plummer_cube_mix(N_PART, gen.CONFIG_SEEDS[2])
+        ni = 16 if args.n == N_PART else args.n
+        xi = x[np.argsort(np.linalg.norm(x, axis=1))[:ni]]
+        xd, md = torch.tensor(x, device=dev), torch.tensor(m, device=dev)
+        xid = torch.tensor(xi, device=dev)
+        a = torch.empty_like(xid)
+        with pg.Context(0) as c:
+            c.set_stream(st.cuda_stream)
+            c.set_eps(EPS)
+            c.set_timing(True)
+            c.set_j_dev(xd, md)
+            c.set_i_dev(xid)
+            kms = _time_kernel(c, lambda: c.run_dev(a), reps=args.steps, warm=args.warmup)
+            info = c.info()
+        out.update(ni=ni, nj=N_PART, kernel_ms=kms, interactions_per_s=ni * N_PART / (kms * 1e-3),
+                   j_chunks=info["slots"])
     elif args.workload == "cells":
         n = args.n if args.n != N_PART else 1 << 21
         x, m = gen.clustered_box(n, gen.CONFIG_SEEDS[3])
@@ -496,7 +515,8 @@ def main():
         ctx.set_i_dev(xi)            # i staging every step (positions change in a run)
         ctx.run_dev(acc, pot)
 
-    for _ in range(max(args.warmup, 3)):
+    warmup_done = max(args.warmup, 3)   # at least 3 untimed steps
+    for _ in range(warmup_done):
         step()
     torch.cuda.synchronize()
 
@@ -572,9 +592,10 @@ def main():
     kms = statistics.median(kern_ms)
     pairs_rank = ni * npart
     achieved = pairs_rank / (kms * 1e-3)
-    # DRAM bytes per launch of this kernel at this size (ncu, one pass, see
-    # profiles/k_allpairs_newton_2e20_dram.md); null for other sizes or shapes
-    traffic = 100.41e6 if (npart == N_PART and world == 1 and info["i_per_thread"] == 8) else None
+    # DRAM bytes of one headline launch of this kernel build, from one ncu
+    # pass (dram__bytes_read.sum + dram__bytes_write.sum = 78.96 MB + 21.90
+    # MB); null for other sizes or shapes
+    traffic = 100.86e6 if (npart == N_PART and world == 1 and info["i_per_thread"] == 8) else None
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_int / 1e9,
             "unit": "Ginteractions/s", "frac": achieved / peak_int, "traffic": traffic,
             "kernel": f"k_allpairs<np={info['i_per_thread'] // 2}, packed={info['packed']}>",
@@ -598,7 +619,7 @@ def main():
         cpu = cpu_baseline(x, m)
     line = {
         "metric": "interactions/s", "value": value, "unit": "interactions/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "steps": args.steps, "warmup": warmup_done, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": "newton-allpairs-2^20-plummer+cube" if npart == N_PART else

@@ -7,9 +7,10 @@ C-contiguous ``(n, 3)`` arrays; masses are FP64 ``(n,)`` arrays.
 The shapes follow the paper: Plummer spheres for the Newton accuracy and
 performance runs (Section 4.1, Section 5.1), log-spaced pair separations for
 the tabulated-force accuracy run (Section 4.2), and tree-style groups that
-share one interaction list (Section 5.1, the Ni/Nj study). The larger mixed,
-clustered and batched sets restate the benchmark configurations described in
-the design doc. Nothing here computes a force, a table or a distance bin.
+share one interaction list (Section 5.1, the Ni/Nj study). The larger sets
+are the benchmark workloads: a Plummer sphere mixed with a uniform cube, a
+clustered periodic box, and tree-style groups with particle and monopole
+lists. Nothing here computes a force, a table or a distance bin.
 """
 
 from __future__ import annotations
