@@ -24,7 +24,7 @@ _LIB = os.path.join(_HERE, "liborc.so")
 _lock = threading.Lock()
 _lib = None
 
-SHAPE_NEWTON, SHAPE_GAUSS_SPLIT, SHAPE_S2PP, SHAPE_LINEAR = 0, 1, 2, 3
+SHAPE_NEWTON, SHAPE_GAUSS_SPLIT, SHAPE_S2PP, SHAPE_LINEAR, SHAPE_NEWTON_POT = 0, 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:
@@ -61,6 +61,8 @@ _SIGS = {
     "orc_table_build": (_I, [_I, _I, _D, _I, _P, _P, _P]),
     "orc_table_eval": (_D, [_I, _I, _D, _P, _P, _D]),
     "orc_table_forces": (_I, [_LL, _P, _P, _LL, _P, _P, _I, _I, _D, _P, _P, _D, _D, _P, _P, _I]),
+    "orc_table_potential": (_I, [_LL, _P, _P, _LL, _P, _P, _I, _I, _D, _P, _P, _D, _D, _P, _P, _I]),
+    "orc_newton_epsi": (_I, [_LL, _P, _P, _P, _LL, _P, _P, _P, _P, _I]),
     "orc_shape_forces": (_I, [_LL, _P, _P, _LL, _P, _P, _I, _P, _D, _D, _D, _P, _P, _P, _I]),
     "orc_grad_newton": (_I, [_LL, _P, _P, _P, _D, _P, _P, _P, _I]),
     "orc_grad_newton_at": (_I, [_LL, _P, _P, _P, _D, _LL, _P, _P, _P, _I]),
@@ -117,6 +119,19 @@ def newton(xi, xj, mj, eps, skip=None, nthreads_=None):
     acc = np.empty((ni, 3)); pot = np.empty(ni)
     _chk(lib().orc_newton(ni, _ptr(xi), _ptr(sk), nj, _ptr(xj), _ptr(mj), float(eps),
                           _ptr(acc), _ptr(pot), nthreads_ or nthreads()))
+    return acc, pot
+
+
+def newton_epsi(xi, eps_i, xj, mj, skip=None, nthreads_=None):
+    """Eq. (1) with each i-particle's own softening eps_i (Section 3.1)."""
+    xi = _f64(xi, (-1, 3)); xj = _f64(xj, (-1, 3)); mj = _f64(mj); ei = _f64(eps_i)
+    ni, nj = len(xi), len(xj)
+    if len(ei) != ni:
+        raise ValueError("eps_i needs one value per i-particle")
+    sk = None if skip is None else np.ascontiguousarray(skip, dtype=np.int64)
+    acc = np.empty((ni, 3)); pot = np.empty(ni)
+    _chk(lib().orc_newton_epsi(ni, _ptr(xi), _ptr(ei), _ptr(sk), nj, _ptr(xj), _ptr(mj),
+                               _ptr(acc), _ptr(pot), nthreads_ or nthreads()))
     return acc, pot
 
 
@@ -221,6 +236,21 @@ def table_forces(xi, xj, mj, E, F, r_cut, G0, G1, box=0.0, skip=None, window=0.0
                                 float(r_cut), _ptr(G0), _ptr(G1), float(box), float(window),
                                 _ptr(acc), _ptr(amb), nthreads_ or nthreads()))
     return acc, amb
+
+
+def table_potential(xi, xj, mj, E, F, r_cut, P0, P1, box=0.0, skip=None, window=0.0,
+                    nthreads_=None):
+    """Table-mode potential: phi_i = sum_j m_j psi~(s_ij) through a second
+    table (P0, P1) of the same layout. Returns (phi, amb)."""
+    xi = _f64(xi, (-1, 3)); xj = _f64(xj, (-1, 3)); mj = _f64(mj)
+    P0 = np.ascontiguousarray(P0, dtype=np.float32); P1 = np.ascontiguousarray(P1, dtype=np.float32)
+    sk = None if skip is None else np.ascontiguousarray(skip, dtype=np.int64)
+    ni = len(xi)
+    phi = np.empty(ni); amb = np.empty(ni)
+    _chk(lib().orc_table_potential(ni, _ptr(xi), _ptr(sk), len(xj), _ptr(xj), _ptr(mj), E, F,
+                                   float(r_cut), _ptr(P0), _ptr(P1), float(box), float(window),
+                                   _ptr(phi), _ptr(amb), nthreads_ or nthreads()))
+    return phi, amb
 
 
 def shape_forces(xi, xj, mj, shape_id, par, r_cut, box=0.0, skip=None, window=0.0,

@@ -103,6 +103,7 @@ typedef struct {
     const double *xi; const long long *skip; long long nj;
     const double *xj; const double *mj; double eps2;
     double *acc; double *pot;
+    const double *eps_i;   /* per-i softening (Section 3.1), or NULL: eps2 */
 } newton_ctx;
 
 static void newton_body(long long lo, long long hi, void *p)
@@ -112,12 +113,14 @@ static void newton_body(long long lo, long long hi, void *p)
         nsum ax = {0, 0}, ay = {0, 0}, az = {0, 0}, ph = {0, 0};
         long long sk = c->skip ? c->skip[i] : -1;
         double xi = c->xi[3 * i], yi = c->xi[3 * i + 1], zi = c->xi[3 * i + 2];
+        /* the softening belongs to the i-particle: its own eps in the i record */
+        double e2 = c->eps_i ? c->eps_i[i] * c->eps_i[i] : c->eps2;
         for (long long j = 0; j < c->nj; ++j) {
             if (j == sk) continue;
             double dx = c->xj[3 * j] - xi;
             double dy = c->xj[3 * j + 1] - yi;
             double dz = c->xj[3 * j + 2] - zi;
-            double rh2 = dx * dx + dy * dy + dz * dz + c->eps2;   /* r^2 + eps^2 */
+            double rh2 = dx * dx + dy * dy + dz * dz + e2;        /* r^2 + eps_i^2 */
             double rh = sqrt(rh2);
             double m = c->mj[j];
             double k3 = m / (rh2 * rh);                           /* m / r_hat^3 */
@@ -140,7 +143,23 @@ int orc_newton(long long ni, const double *xi, const long long *skip,
                double *acc, double *pot, int nthreads)
 {
     if (ni < 0 || nj < 0 || eps < 0) return -1;
-    newton_ctx c = {xi, skip, nj, xj, mj, eps * eps, acc, pot};
+    newton_ctx c = {xi, skip, nj, xj, mj, eps * eps, acc, pot, NULL};
+    parallel_for(ni, nthreads, newton_body, &c);
+    return 0;
+}
+
+/* Eq. (1) with the softening of each i-particle: the i-particle structure
+ * of Section 3.1 carries eps^2 per i, and the kernel of Section 3.3 adds the
+ * i-particle's eps^2 to |d|^2.  a_i = sum_j m_j d_ij / (|d_ij|^2 + eps_i^2)^{3/2},
+ * phi_i = -sum_j m_j / (|d_ij|^2 + eps_i^2)^{1/2}, j != skip[i]. */
+int orc_newton_epsi(long long ni, const double *xi, const double *eps_i, const long long *skip,
+                    long long nj, const double *xj, const double *mj,
+                    double *acc, double *pot, int nthreads)
+{
+    if (ni < 0 || nj < 0 || !eps_i) return -1;
+    for (long long i = 0; i < ni; ++i)
+        if (!(eps_i[i] >= 0)) return -1;
+    newton_ctx c = {xi, skip, nj, xj, mj, 0.0, acc, pot, eps_i};
     parallel_for(ni, nthreads, newton_body, &c);
     return 0;
 }
@@ -237,7 +256,7 @@ double orc_scale2(int E, int F, double r_cut)
 /* closed-form force shapes g(r) = f(r) / r                             */
 /* ------------------------------------------------------------------ */
 enum { ORC_SHAPE_NEWTON = 0, ORC_SHAPE_GAUSS_SPLIT = 1, ORC_SHAPE_S2PP = 2,
-       ORC_SHAPE_LINEAR = 3 };
+       ORC_SHAPE_LINEAR = 3, ORC_SHAPE_NEWTON_POT = 4 };
 
 /* S2 force profile of Hockney & Eastwood divided by r (Eq. s2), with
  * xi = 2 r / a and the 35 a^2 denominator in both polynomial branches. */
@@ -270,7 +289,9 @@ double orc_s2_profile(double r, double a)
  *   GAUSS_SPLIT  par = {r_s, eps}: [erfc(r / 2 r_s) + r/(r_s sqrt(pi)) exp(-r^2 / 4 r_s^2)]
  *                                   (r^2 + eps^2)^(-3/2)   (TreePM short-range part)
  *   S2PP         par = {eps, r_cut}: [R(r, eps) - R(r, r_cut)] / r   (Eq. s2pp)
- *   LINEAR       par = {alpha, beta}: alpha + beta r^2 */
+ *   LINEAR       par = {alpha, beta}: alpha + beta r^2
+ *   NEWTON_POT   par = {eps}: -(r^2 + eps^2)^(-1/2), a potential rather than f/r
+ *                (tabulated the same way for the table-mode potential) */
 double orc_shape(int id, const double *par, double r)
 {
     switch (id) {
@@ -289,6 +310,8 @@ double orc_shape(int id, const double *par, double r)
         return s2_over_r(r, par[0]) - s2_over_r(r, par[1]);
     case ORC_SHAPE_LINEAR:
         return par[0] + par[1] * r * r;
+    case ORC_SHAPE_NEWTON_POT:
+        return -1.0 / sqrt(r * r + par[0] * par[0]);
     default:
         return NAN;
     }
@@ -427,6 +450,56 @@ int orc_table_forces(long long ni, const double *xi, const long long *skip,
     c.E = E; c.F = F; c.sc2 = orc_scale2(E, F, r_cut); c.smax = orc_s_max(E, F);
     c.G0 = G0; c.G1 = G1; c.window = window; c.acc = acc; c.amb = amb;
     parallel_for(ni, nthreads, table_body, &c);
+    return 0;
+}
+
+/* Table-mode potential, an extension: the tabulated kernel of Section 3.4.2
+ * stores accelerations only. A second table of the same layout holds a
+ * potential shape psi(r) (P0, P1 built from its knot values exactly as G0,
+ * G1 are, so it too is zero at and beyond r_cut), and
+ *   phi_i = sum_{j != skip[i]} m_j psi~(s_ij),
+ * psi~ the same interpolant in s as the force's g~. amb[i] receives the size
+ * of the terms within window relative distance of s_max in s (either side of
+ * the cutoff is a correct reading at rounding distance). */
+static void tpot_body(long long lo, long long hi, void *p)
+{
+    tab_ctx *c = (tab_ctx *)p;
+    long long nlast = orc_table_size(c->E, c->F) - 1;
+    double s_prev = orc_knot(c->E, c->F, nlast - 1);
+    for (long long i = lo; i < hi; ++i) {
+        nsum ph = {0, 0}, am = {0, 0};
+        long long sk = c->skip ? c->skip[i] : -1;
+        for (long long j = 0; j < c->nj; ++j) {
+            if (j == sk) continue;
+            double dx = wrap(c->xj[3 * j] - c->xi[3 * i], c->box);
+            double dy = wrap(c->xj[3 * j + 1] - c->xi[3 * i + 1], c->box);
+            double dz = wrap(c->xj[3 * j + 2] - c->xi[3 * i + 2], c->box);
+            double s = (dx * dx + dy * dy + dz * dz) * c->sc2 + 2.0;
+            double m = c->mj[j];
+            nadd(&ph, m * table_eval_s(c->E, c->F, c->smax, c->G0, c->G1, s, NULL));
+            if (c->amb && fabs(s - c->smax) <= c->window * c->smax) {
+                double sl = s < c->smax ? s : c->smax;
+                double pl = (double)c->G0[nlast - 1] + (sl - s_prev) * (double)c->G1[nlast - 1];
+                nadd(&am, m * fabs(pl));
+            }
+        }
+        c->acc[i] = nval(&ph);
+        if (c->amb) c->amb[i] = nval(&am);
+    }
+}
+
+int orc_table_potential(long long ni, const double *xi, const long long *skip,
+                        long long nj, const double *xj, const double *mj,
+                        int E, int F, double r_cut, const float *P0, const float *P1,
+                        double box, double window, double *phi, double *amb, int nthreads)
+{
+    if (ni < 0 || nj < 0 || r_cut <= 0 || E < 0 || F < 0 || E + F > 20) return -1;
+    tab_ctx c;
+    memset(&c, 0, sizeof c);
+    c.xi = xi; c.skip = skip; c.nj = nj; c.xj = xj; c.mj = mj; c.box = box;
+    c.E = E; c.F = F; c.sc2 = orc_scale2(E, F, r_cut); c.smax = orc_s_max(E, F);
+    c.G0 = P0; c.G1 = P1; c.window = window; c.acc = phi; c.amb = amb;
+    parallel_for(ni, nthreads, tpot_body, &c);
     return 0;
 }
 

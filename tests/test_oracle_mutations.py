@@ -10,12 +10,24 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "pg_oracle.c")
-PINS = ["tests/test_oracle_newton.py", "tests/test_oracle_table.py", "tests/test_oracle_grad.py"]
+PINS = ["tests/test_oracle_newton.py", "tests/test_oracle_table.py", "tests/test_oracle_grad.py",
+        "tests/test_oracle_ext.py"]
 
 MUTATIONS = {
     "potential sign": ("nadd(&ph, -m / rh);", "nadd(&ph, m / rh);", 0),
     "list-mode potential sign": ("nadd(&ph, -m / rh);", "nadd(&ph, m / rh);", 1),
-    "softening dropped": ("dz * dz + c->eps2;   /* r^2 + eps^2 */", "dz * dz;"),
+    "softening dropped": ("dz * dz + e2;        /* r^2 + eps_i^2 */", "dz * dz;"),
+    "list-mode softening dropped": ("double rh2 = dx * dx + dy * dy + dz * dz + c->eps2;",
+                                    "double rh2 = dx * dx + dy * dy + dz * dz;"),
+    "per-i softening not squared": ("double e2 = c->eps_i ? c->eps_i[i] * c->eps_i[i] : c->eps2;",
+                                    "double e2 = c->eps_i ? c->eps_i[i] : c->eps2;"),
+    "softening of the j-particle": ("double e2 = c->eps_i ? c->eps_i[i] * c->eps_i[i] : c->eps2;",
+                                    "double e2 = c->eps_i && c->nj > 1 ? c->eps_i[1 - (i & 1)] * "
+                                    "c->eps_i[1 - (i & 1)] : c->eps2;"),
+    "table potential sign": ("nadd(&ph, m * table_eval_s(c->E, c->F, c->smax, c->G0, c->G1, s, NULL));",
+                             "nadd(&ph, -m * table_eval_s(c->E, c->F, c->smax, c->G0, c->G1, s, NULL));"),
+    "table potential of r, not s": ("double s = (dx * dx + dy * dy + dz * dz) * c->sc2 + 2.0;",
+                                    "double s = sqrt(dx * dx + dy * dy + dz * dz) * c->sc2 + 2.0;"),
     "difference transposed": ("double dx = c->xj[3 * j] - xi;", "double dx = xi - c->xj[3 * j];", 0),
     "list-mode difference transposed": ("double dx = c->xj[3 * j] - xi;",
                                         "double dx = xi - c->xj[3 * j];", 1),
