@@ -29,7 +29,10 @@
  *     context's stream;
  *   - calls are asynchronous on the context's stream unless stated; the
  *     library never synchronises the device except in pg_get_force,
- *     pg_get_table, pg_sync and pg_tune;
+ *     pg_get_table, pg_sync and pg_tune, and in the setters that copy from
+ *     host arrays through pageable memory (pg_set_table, pg_set_table_values,
+ *     pg_set_table_pot, pg_set_table_pot_values, pg_set_eps_i), which wait
+ *     for the context's stream before they return;
  *   - a context is not thread-safe; use one per host thread;
  *   - every function returns PG_OK (0) or a negative status; it never aborts
  *     the process and never traps the GPU. pg_last_error() describes the last
@@ -81,6 +84,20 @@ int pg_set_stream(pg_ctx *ctx, void *cuda_stream);
  * at zero distance contributes nothing. */
 int pg_set_eps(pg_ctx *ctx, double eps);
 
+/* Softening per i-particle: the i-particle structure of Section 3.1 carries
+ * eps^2 per particle, and the Newton kernel of Section 3.3 adds the
+ * i-particle's eps^2 to |d|^2. eps: host double[n], finite and >= 0 (copied;
+ * PG_EINVAL otherwise). n must equal the i count of pg_set_i when pg_run runs
+ * (PG_ESTATE otherwise). In self mode the left-out own pair is the one with
+ * the i-particle's eps. NULL or n = 0 returns to the global eps of
+ * pg_set_eps. PG_NEWTON only (pg_run returns PG_ESTATE in PG_TABLE mode); the
+ * backward pass refuses it (PG_ESTATE). Waits for the context's stream. */
+int pg_set_eps_i(pg_ctx *ctx, const double *eps, long long n);
+
+/* The same from a device array (double[n]; a negative value acts as its
+ * absolute value), copied in stream order. */
+int pg_set_eps_i_dev(pg_ctx *ctx, const double *eps, long long n);
+
 /* Select PG_NEWTON (default) or PG_TABLE. */
 int pg_set_mode(pg_ctx *ctx, int mode);
 
@@ -109,6 +126,22 @@ int pg_set_table_values_dev(pg_ctx *ctx, const float *v, long long n, double r_c
 
 /* Copy the stored table (G0, G1: FP32 host arrays of n = 2^(E+F)). Syncs. */
 int pg_get_table(pg_ctx *ctx, float *G0, float *G1, long long n);
+
+/* Potential in PG_TABLE mode, an extension: the tabulated kernel of Section
+ * 3.4.2 stores accelerations only. psi(r, user) is tabulated on the force
+ * table's knots (same r_cut, E, F) and built the same way, including the
+ * cutoff reading: psi~ = 0 at and beyond r_cut, and the last interior bin
+ * runs to psi(r_cut) from below. Then phi_i = sum_j m_j psi~(s_ij); in self
+ * mode without the own pair. Needs the force table first (PG_ESTATE);
+ * p = NULL drops the potential (phi is zero again). A later force table with
+ * the same r_cut, E, F keeps the potential; another geometry drops it. The
+ * table in shared memory doubles (16 B per knot). Waits for the stream. */
+int pg_set_table_pot(pg_ctx *ctx, double (*p)(double r, void *user), void *user);
+
+/* The same from knot values v[0 .. n-1] (host FP32, n = 2^(E+F) of the force
+ * table; v[n-1] is psi at r_cut from below). PG_EINVAL for another n or a
+ * value that is not finite. */
+int pg_set_table_pot_values(pg_ctx *ctx, const float *v, long long n);
 
 /* Number of j-particles used by pg_run (g5_set_n). Without it, pg_run uses
  * the highest address written by pg_set_j / pg_set_j_dev. */

@@ -65,6 +65,10 @@ SIGNATURES = {
     "pg_tune": (_I, [_P]),
     "pg_set_shape": (_I, [_P, _I, _I, _I]),
     "pg_set_allpairs_path": (_I, [_P, _I]),
+    "pg_set_eps_i": (_I, [_P, _P, _LL]),
+    "pg_set_eps_i_dev": (_I, [_P, _P, _LL]),
+    "pg_set_table_pot": (_I, [_P, GFUNC, _P]),
+    "pg_set_table_pot_values": (_I, [_P, _P, _LL]),
     "pg_set_timing": (_I, [_P, _I]),
     "pg_kernel_time": (_I, [_P, C.POINTER(_D)]),
     "pg_info": (_I, [_P, C.POINTER(_LL), _I]),
@@ -164,6 +168,30 @@ def pg_set_table_values(ctx, v, r_cut, E, F):
 def pg_set_table_values_dev(ctx, v, n, r_cut, E, F):
     return _check(ctx, lib().pg_set_table_values_dev(ctx, _ptr(v), int(n), float(r_cut), int(E),
                                                      int(F)))
+
+
+def pg_set_table_pot(ctx, p, user=None):
+    """p(r) -> psi(r), the potential shape, at the force table's knots;
+    None drops the potential."""
+    cb = GFUNC(lambda r, _u: float(p(r))) if p is not None else GFUNC()
+    return _check(ctx, lib().pg_set_table_pot(ctx, cb, user))
+
+
+def pg_set_table_pot_values(ctx, v):
+    v = np.ascontiguousarray(v, dtype=np.float32)
+    return _check(ctx, lib().pg_set_table_pot_values(ctx, _ptr(v), len(v)))
+
+
+def pg_set_eps_i(ctx, eps):
+    """Softening per i-particle (host array), or None for the global eps."""
+    if eps is None:
+        return _check(ctx, lib().pg_set_eps_i(ctx, None, 0))
+    e = np.ascontiguousarray(eps, dtype=np.float64)
+    return _check(ctx, lib().pg_set_eps_i(ctx, _ptr(e), len(e)))
+
+
+def pg_set_eps_i_dev(ctx, eps, n):
+    return _check(ctx, lib().pg_set_eps_i_dev(ctx, _ptr(eps), int(n)))
 
 
 def pg_get_table(ctx, n):
@@ -353,6 +381,19 @@ class Context:
 
     def set_table(self, g, r_cut, E, F):
         pg_set_table(self.h, g, r_cut, E, F)
+
+    def set_table_pot(self, p):
+        pg_set_table_pot(self.h, p)
+
+    def set_table_pot_values(self, v):
+        pg_set_table_pot_values(self.h, v)
+
+    def set_eps_i(self, eps):
+        pg_set_eps_i(self.h, eps)
+
+    def set_eps_i_dev(self, eps):
+        _require_dev(eps)
+        pg_set_eps_i_dev(self.h, eps, eps.shape[0])
 
     def set_table_values(self, v, r_cut, E, F):
         pg_set_table_values(self.h, v, r_cut, E, F)

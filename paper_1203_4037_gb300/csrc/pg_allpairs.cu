@@ -21,6 +21,14 @@
 //    FP32 once per (j, tile) while staging; the pair loop runs in FP32 with
 //    the MUFU rsqrt; each sub-tile's FP32 partial is folded into a TwoSum
 //    (hi, lo) pair; the per-CTA partials are combined in FP64.
+//
+// EXT selects the extended form of each mode: in Newton mode the softening
+// of each i-particle read from its record (w = eps_i^2: the i-particle
+// structure of Section 3.1 carries eps^2 per i), with a guard that gives a
+// coincident pair at eps_i = 0 no contribution; in table mode a potential
+// phi_i += m_j psi~(s) from a second table on the same knots, interleaved
+// with the force table as {A, G1, A_p, P1} (the paper's tabulated kernel
+// stores accelerations only).
 #include "pg_device.cuh"
 
 namespace pg {
@@ -111,7 +119,7 @@ struct MinBlocks {
                                : TABLE ? PG_TABLE_NP4_MIN_BLOCKS : PG_NP4_MIN_BLOCKS;
 };
 
-template <int NP, bool TABLE, bool ZSAFE, bool PK>
+template <int NP, bool TABLE, bool EXT, bool PK>
 __global__ void __launch_bounds__(kNT, MinBlocks<NP, TABLE>::value) k_allpairs(AllPairsArgs a)
 {
     using V = Lanes<PK>;
@@ -120,9 +128,9 @@ __global__ void __launch_bounds__(kNT, MinBlocks<NP, TABLE>::value) k_allpairs(A
     double4 *raw = reinterpret_cast<double4 *>(smem);                       // [2][kTJ]
     u64 *cvt = reinterpret_cast<u64 *>(smem + 2 * kTJ * sizeof(double4));   // [kTJ][4]
     // compensated running sums (hi, lo) of every thread's i, [2 kComp NP][kNT]
-    // (kComp = 4: a and phi; 3 in table mode, which has no potential): they
+    // (kComp = 4: a and phi; 3 in table mode without a potential): they
     // change once per sub-tile, so they live in shared memory
-    constexpr int kComp = TABLE ? 3 : 4;
+    constexpr int kComp = TABLE && !EXT ? 3 : 4;
     u64 *run = cvt + kTJ * 4;
     uint64_t *bar = reinterpret_cast<uint64_t *>(run + 2 * kComp * NP * kNT);
     int *flag = reinterpret_cast<int *>(bar + 2);
@@ -139,8 +147,10 @@ __global__ void __launch_bounds__(kNT, MinBlocks<NP, TABLE>::value) k_allpairs(A
         mbar_init(&bar[1], 1);
         mbar_fence_init();
     }
-    if (TABLE)
+    if (TABLE && !EXT)
         for (int k = tid; k < a.tab.n; k += kNT) tab[k] = a.tab.AG1[k];
+    if (TABLE && EXT)
+        for (int k = tid; k < a.tab.n; k += kNT) reinterpret_cast<float4 *>(tab)[k] = a.tab.AGP[k];
     __syncthreads();
 
     // prefetch the first two sub-tiles
@@ -157,6 +167,7 @@ __global__ void __launch_bounds__(kNT, MinBlocks<NP, TABLE>::value) k_allpairs(A
 
     // per-thread state
     u64 xi[NP], yi[NP], zi[NP];
+    u64 e2i[NP];                                 // Newton EXT: each i-pair's eps^2
     u64 ax[NP], ay[NP], az[NP], ph[NP];          // sub-tile partials
     // running sum k of pair p: hi at run[(2 kComp p + k) kNT + tid], lo at k + kComp
     auto RH = [&](int p, int k) -> u64 & { return run[(2 * kComp * p + k) * kNT + tid]; };
@@ -169,8 +180,8 @@ __global__ void __launch_bounds__(kNT, MinBlocks<NP, TABLE>::value) k_allpairs(A
     const u64 c0v = pk2(c0, c0);
     const double sc = TABLE ? a.tab.scale : 1.0;
     const unsigned smax_bits = __float_as_uint(a.tab.s_max);
-    const int sh3 = a.tab.shift - 3;
-    const unsigned tb0 = smem_u32(tab) - (a.tab.base << 3);
+    const int sh3 = a.tab.shift - (EXT ? 4 : 3);
+    const unsigned tb0 = smem_u32(tab) - (a.tab.base << (EXT ? 4 : 3));
     bool failed = false;
 
     auto flush = [&](long long t) {
@@ -207,7 +218,7 @@ __global__ void __launch_bounds__(kNT, MinBlocks<NP, TABLE>::value) k_allpairs(A
             cx = c.x; cy = c.y; cz = c.z;
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
-                float fx[2], fy[2], fz[2];
+                float fx[2], fy[2], fz[2], fe[2];
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
                     long long i = t * Bi + (2 * p + q) * kNT + tid;
@@ -216,13 +227,15 @@ __global__ void __launch_bounds__(kNT, MinBlocks<NP, TABLE>::value) k_allpairs(A
                         fx[q] = (float)((v.x - cx) * sc);
                         fy[q] = (float)((v.y - cy) * sc);
                         fz[q] = (float)((v.z - cz) * sc);
+                        fe[q] = (float)v.w;
                     } else {
-                        fx[q] = fy[q] = fz[q] = 0.0f;
+                        fx[q] = fy[q] = fz[q] = fe[q] = 0.0f;
                     }
                 }
                 xi[p] = pk2(fx[0], fx[1]);
                 yi[p] = pk2(fy[0], fy[1]);
                 zi[p] = pk2(fz[0], fz[1]);
+                e2i[p] = pk2(fe[0], fe[1]);
 #pragma unroll
                 for (int k = 0; k < kComp; ++k) RH(p, k) = RL(p, k) = zero2;
             }
@@ -283,14 +296,14 @@ __global__ void __launch_bounds__(kNT, MinBlocks<NP, TABLE>::value) k_allpairs(A
                 const u64 dx = V::sub(xy.x, xi[p]);
                 const u64 dy = V::sub(xy.y, yi[p]);
                 const u64 dz = V::sub(zm.x, zi[p]);
-                u64 r2 = V::fma(dx, dx, c0v);
+                u64 r2 = V::fma(dx, dx, !TABLE && EXT ? e2i[p] : c0v);
                 r2 = V::fma(dy, dy, r2);
                 r2 = V::fma(dz, dz, r2);
                 float ra, rb;
                 up2(r2, ra, rb);
                 if (!TABLE) {
                     float qa = rsq(ra), qb = rsq(rb);
-                    if (ZSAFE) {   // eps = 0: a coincident pair contributes nothing
+                    if (EXT) {     // eps_i = 0: a coincident pair contributes nothing
                         qa = ra > 0.0f ? qa : 0.0f;
                         qb = rb > 0.0f ? qb : 0.0f;
                     }
@@ -306,12 +319,21 @@ __global__ void __launch_bounds__(kNT, MinBlocks<NP, TABLE>::value) k_allpairs(A
                     ra = clamp_pos(ra, smax_bits);
                     rb = clamp_pos(rb, smax_bits);
                     // the entry's shared address by shift and mask of the
-                    // bits (7 % faster than indexing on GB300)
-                    const float2 ta = tab_at(tb0, __float_as_uint(ra), sh3);
-                    const float2 tb = tab_at(tb0, __float_as_uint(rb), sh3);
-                    // each lane's {A, G1} arrives as a pair: two scalar FMAs
-                    // write the packed g without register moves
-                    const u64 g = pk2(__fmaf_rn(ra, ta.y, ta.x), __fmaf_rn(rb, tb.y, tb.x));
+                    // bits (7 % faster than indexing on GB300); each lane's
+                    // {A, G1} arrives as a pair: two scalar FMAs write the
+                    // packed g without register moves
+                    u64 g;
+                    if (EXT) {
+                        const float4 ta = tab4_at(tb0, __float_as_uint(ra), sh3);
+                        const float4 tb = tab4_at(tb0, __float_as_uint(rb), sh3);
+                        g = pk2(__fmaf_rn(ra, ta.y, ta.x), __fmaf_rn(rb, tb.y, tb.x));
+                        const u64 pp = pk2(__fmaf_rn(ra, ta.w, ta.z), __fmaf_rn(rb, tb.w, tb.z));
+                        ph[p] = V::fma(zm.y, pp, ph[p]);
+                    } else {
+                        const float2 ta = tab_at(tb0, __float_as_uint(ra), sh3);
+                        const float2 tb = tab_at(tb0, __float_as_uint(rb), sh3);
+                        g = pk2(__fmaf_rn(ra, ta.y, ta.x), __fmaf_rn(rb, tb.y, tb.x));
+                    }
                     const u64 mg = V::mul(zm.y, g);
                     ax[p] = V::fma(mg, dx, ax[p]);
                     ay[p] = V::fma(mg, dy, ay[p]);
@@ -324,7 +346,7 @@ __global__ void __launch_bounds__(kNT, MinBlocks<NP, TABLE>::value) k_allpairs(A
             fold2(RH(p, 0), RL(p, 0), ax[p]);
             fold2(RH(p, 1), RL(p, 1), ay[p]);
             fold2(RH(p, 2), RL(p, 2), az[p]);
-            if (!TABLE) fold2(RH(p, 3), RL(p, 3), ph[p]);
+            if (!TABLE || EXT) fold2(RH(p, 3), RL(p, 3), ph[p]);
         }
     }
 
@@ -342,80 +364,87 @@ __global__ void __launch_bounds__(kNT, MinBlocks<NP, TABLE>::value) k_allpairs(A
 
 // ------------------------------------------------------------------ host
 
-size_t allpairs_smem(int np, bool table, int ntab)
+size_t allpairs_smem(int np, bool table, int ntab, bool ext)
 {
     size_t s = 2 * kTJ * sizeof(double4) + kTJ * 4 * sizeof(u64) +
-               2 * (table ? 3 : 4) * np * kNT * sizeof(u64) + 4 * sizeof(uint64_t);
+               2 * (table && !ext ? 3 : 4) * np * kNT * sizeof(u64) + 4 * sizeof(uint64_t);
     if (table) s += (size_t)ntab * sizeof(float2);
     return s;
 }
 
 // raise the kernel's dynamic shared memory limit once (outside any capture)
-template <int NP, bool TABLE, bool ZSAFE, bool PK>
+template <int NP, bool TABLE, bool EXT, bool PK>
 static cudaError_t configure_one()
 {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_allpairs<NP, TABLE, ZSAFE, PK>,
+    cudaError_t e = cudaFuncSetAttribute(k_allpairs<NP, TABLE, EXT, PK>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)allpairs_smem(NP, TABLE, 1 << 13));
+                                         (int)allpairs_smem(NP, TABLE, 2 << 13, EXT));
     done = e == cudaSuccess;
     return e;
 }
 
-template <int NP, bool TABLE, bool ZSAFE, bool PK>
+template <int NP, bool TABLE, bool EXT, bool PK>
 static cudaError_t launch_one(const AllPairsArgs &a, int grid, size_t smem, cudaStream_t st)
 {
-    cudaError_t e = configure_one<NP, TABLE, ZSAFE, PK>();
+    cudaError_t e = configure_one<NP, TABLE, EXT, PK>();
     if (e != cudaSuccess) return e;
-    k_allpairs<NP, TABLE, ZSAFE, PK><<<grid, kNT, smem, st>>>(a);
+    k_allpairs<NP, TABLE, EXT, PK><<<grid, kNT, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int NP, bool TABLE, bool PK>
+template <int NP, bool TABLE, bool EXT, bool PK>
 static int occupancy_one(size_t smem)
 {
-    auto k = k_allpairs<NP, TABLE, false, PK>;
-    if (configure_one<NP, TABLE, false, PK>() != cudaSuccess) return 1;
+    auto k = k_allpairs<NP, TABLE, EXT, PK>;
+    if (configure_one<NP, TABLE, EXT, PK>() != cudaSuccess) return 1;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kNT, smem) != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
 }
 
-template <int NP>
-static int occupancy_np(bool table, bool packed, size_t smem)
+template <int NP, bool PK>
+static int occupancy_pk(bool table, bool ext, size_t smem)
 {
-    if (table) return packed ? occupancy_one<NP, true, true>(smem) : occupancy_one<NP, true, false>(smem);
-    return packed ? occupancy_one<NP, false, true>(smem) : occupancy_one<NP, false, false>(smem);
+    if (table) return ext ? occupancy_one<NP, true, true, PK>(smem) : occupancy_one<NP, true, false, PK>(smem);
+    return ext ? occupancy_one<NP, false, true, PK>(smem) : occupancy_one<NP, false, false, PK>(smem);
 }
 
-int allpairs_max_blocks_per_sm(int np, bool table, int ntab, bool packed)
+template <int NP>
+static int occupancy_np(bool table, bool packed, bool ext, size_t smem)
 {
-    size_t smem = allpairs_smem(np, table, ntab);
-    return np == 1 ? occupancy_np<1>(table, packed, smem)
-         : np == 4 ? occupancy_np<4>(table, packed, smem)
-                   : occupancy_np<2>(table, packed, smem);
+    return packed ? occupancy_pk<NP, true>(table, ext, smem) : occupancy_pk<NP, false>(table, ext, smem);
+}
+
+int allpairs_max_blocks_per_sm(int np, bool table, int ntab, bool packed, bool ext)
+{
+    size_t smem = allpairs_smem(np, table, ntab, ext);
+    return np == 1 ? occupancy_np<1>(table, packed, ext, smem)
+         : np == 4 ? occupancy_np<4>(table, packed, ext, smem)
+                   : occupancy_np<2>(table, packed, ext, smem);
 }
 
 template <int NP, bool PK>
-static cudaError_t launch_np(const AllPairsArgs &a, int grid, bool table, bool zsafe, size_t smem,
+static cudaError_t launch_np(const AllPairsArgs &a, int grid, bool table, bool ext, size_t smem,
                              cudaStream_t st)
 {
-    if (table) return launch_one<NP, true, false, PK>(a, grid, smem, st);
-    if (zsafe) return launch_one<NP, false, true, PK>(a, grid, smem, st);
-    return launch_one<NP, false, false, PK>(a, grid, smem, st);
+    if (table) return ext ? launch_one<NP, true, true, PK>(a, grid, smem, st)
+                          : launch_one<NP, true, false, PK>(a, grid, smem, st);
+    return ext ? launch_one<NP, false, true, PK>(a, grid, smem, st)
+               : launch_one<NP, false, false, PK>(a, grid, smem, st);
 }
 
-cudaError_t launch_allpairs(const AllPairsArgs &a, int grid, int np, bool table, bool zsafe,
+cudaError_t launch_allpairs(const AllPairsArgs &a, int grid, int np, bool table, bool ext,
                             bool packed, size_t smem, cudaStream_t st)
 {
     if (grid <= 0) return cudaSuccess;
-    if (np == 1) return packed ? launch_np<1, true>(a, grid, table, zsafe, smem, st)
-                               : launch_np<1, false>(a, grid, table, zsafe, smem, st);
-    if (np == 2) return packed ? launch_np<2, true>(a, grid, table, zsafe, smem, st)
-                               : launch_np<2, false>(a, grid, table, zsafe, smem, st);
-    if (np == 4) return packed ? launch_np<4, true>(a, grid, table, zsafe, smem, st)
-                               : launch_np<4, false>(a, grid, table, zsafe, smem, st);
+    if (np == 1) return packed ? launch_np<1, true>(a, grid, table, ext, smem, st)
+                               : launch_np<1, false>(a, grid, table, ext, smem, st);
+    if (np == 2) return packed ? launch_np<2, true>(a, grid, table, ext, smem, st)
+                               : launch_np<2, false>(a, grid, table, ext, smem, st);
+    if (np == 4) return packed ? launch_np<4, true>(a, grid, table, ext, smem, st)
+                               : launch_np<4, false>(a, grid, table, ext, smem, st);
     return cudaErrorInvalidValue;
 }
 
@@ -438,15 +467,11 @@ __global__ void k_combine(CombineArgs c)
         }
     }
     long long k = c.perm ? (long long)c.perm[p] : p;
-    if (c.newton && c.self && c.eps2 > 0.0f && c.njsub > 0) {
-        // the loop added -m_k rsqrt(eps^2) for i's own pair (d = 0 exactly)
-        float mk = (float)c.jrec[k].w;
-        ph += (double)__fmul_rn(mk, rsq(c.eps2));
-    }
+    if (c.self && c.njsub > 0) ph -= self_potential(c, k);
     c.acc[3 * k] = ax * c.accscale;
     c.acc[3 * k + 1] = ay * c.accscale;
     c.acc[3 * k + 2] = az * c.accscale;
-    if (c.pot) c.pot[k] = c.newton ? ph : 0.0;
+    if (c.pot) c.pot[k] = c.newton || c.tabpot ? ph : 0.0;
 }
 
 // The same sum with a 128-thread block per i, for few i-particles with many
@@ -487,14 +512,11 @@ __global__ void __launch_bounds__(kWideThreads) k_combine_wide(CombineArgs c)
         ax += wsum[w].x; ay += wsum[w].y; az += wsum[w].z; ph += wsum[w].w;
     }
     const long long k = c.perm ? (long long)c.perm[p] : p;
-    if (c.newton && c.self && c.eps2 > 0.0f && c.njsub > 0) {
-        const float mk = (float)c.jrec[k].w;
-        ph += (double)__fmul_rn(mk, rsq(c.eps2));
-    }
+    if (c.self && c.njsub > 0) ph -= self_potential(c, k);
     c.acc[3 * k] = ax * c.accscale;
     c.acc[3 * k + 1] = ay * c.accscale;
     c.acc[3 * k + 2] = az * c.accscale;
-    if (c.pot) c.pot[k] = c.newton ? ph : 0.0;
+    if (c.pot) c.pot[k] = c.newton || c.tabpot ? ph : 0.0;
 }
 
 cudaError_t launch_combine(const CombineArgs &c, cudaStream_t st)

@@ -41,9 +41,17 @@ struct pg_ctx {
 
     // table
     bool have_table = false;
+    // table-mode potential: P0/P1 from psi's knot values, interleaved with
+    // the force table as {A, G1, A_p, P1} (pot_* = the geometry it was built on)
+    bool have_pot = false;
+    int pot_E = -1, pot_F = -1;
+    double pot_rcut = 0.0;
+    // per-i softening (device eps per i; written into the i records' w)
+    bool have_epsi = false, epsi_applied = false, w_dirty = false;
+    long long n_epsi = 0;
     int E = 0, F = 0, ntab = 0;
     double r_cut = 0.0, scale = 1.0, s_max = 0.0;
-    DevBuf G0, G1, AG1;
+    DevBuf G0, G1, AG1, P0, P1, AGP, epsi;
 
     // j
     long long nj_n = -1;          // pg_set_n, -1: unset
@@ -243,6 +251,20 @@ void set_geometry(pg_ctx *c, double r_cut, int E, int F)
     c->scale = std::sqrt(c->s_max - 2.0) / r_cut;
 }
 
+// after the force table changed: rebuild the interleaved table with the
+// potential on the same knots, or drop the potential if the knots moved
+int remerge_pot(pg_ctx *c)
+{
+    if (!c->have_pot) return PG_OK;
+    if (c->pot_E != c->E || c->pot_F != c->F || c->pot_rcut != c->r_cut) {
+        c->have_pot = false;
+        return PG_OK;
+    }
+    PG_CUDA(c, launch_table_merge((const float2 *)c->AG1.p, (const float *)c->P0.p,
+                                  (const float *)c->P1.p, (float4 *)c->AGP.p, c->E, c->F, c->stream));
+    return PG_OK;
+}
+
 // G0/G1 from host knot values; then the device copies and the {A, G1} form
 int upload_table(pg_ctx *c, const std::vector<float> &v)
 {
@@ -266,9 +288,43 @@ int upload_table(pg_ctx *c, const std::vector<float> &v)
     PG_CUDA(c, cudaMemcpyAsync(c->G1.p, g1.data(), n * 4, cudaMemcpyHostToDevice, c->stream));
     PG_CUDA(c, launch_table_prep((float *)c->G0.p, (float *)c->G1.p, (float2 *)c->AG1.p, c->E,
                                  c->F, c->stream));
+    if ((rc = remerge_pot(c))) return rc;
     // the host vectors go out of scope: wait for the copies
     PG_CUDA(c, cudaStreamSynchronize(c->stream));
     c->have_table = true;
+    drop_graph(c);
+    return PG_OK;
+}
+
+// P0/P1 of a potential shape from host knot values (the same construction
+// and cutoff reading as the force table), then the interleaved table
+int upload_pot(pg_ctx *c, const std::vector<float> &v)
+{
+    int n = c->ntab;
+    std::vector<float> p0(n), p1(n);
+    for (int k = 0; k < n; ++k) {
+        if (k < n - 1) {
+            double ds = (double)knot_s(k + 1, c->F) - (double)knot_s(k, c->F);
+            p0[k] = v[k];
+            p1[k] = (float)(((double)v[k + 1] - (double)v[k]) / ds);
+        } else {
+            p0[k] = 0.0f;
+            p1[k] = 0.0f;
+        }
+    }
+    int rc;
+    if ((rc = ensure(c, c->P0, n * 4)) || (rc = ensure(c, c->P1, n * 4)) ||
+        (rc = ensure(c, c->AGP, (size_t)n * 16)))
+        return rc;
+    PG_CUDA(c, cudaMemcpyAsync(c->P0.p, p0.data(), n * 4, cudaMemcpyHostToDevice, c->stream));
+    PG_CUDA(c, cudaMemcpyAsync(c->P1.p, p1.data(), n * 4, cudaMemcpyHostToDevice, c->stream));
+    PG_CUDA(c, launch_table_merge((const float2 *)c->AG1.p, (const float *)c->P0.p,
+                                  (const float *)c->P1.p, (float4 *)c->AGP.p, c->E, c->F, c->stream));
+    PG_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->have_pot = true;
+    c->pot_E = c->E;
+    c->pot_F = c->F;
+    c->pot_rcut = c->r_cut;
     drop_graph(c);
     return PG_OK;
 }
@@ -277,6 +333,7 @@ TableDev table_dev(const pg_ctx *c)
 {
     TableDev t{};
     t.AG1 = (const float2 *)c->AG1.p;
+    t.AGP = c->have_pot ? (const float4 *)c->AGP.p : nullptr;
     t.n = c->ntab;
     t.shift = 23 - c->F;
     t.base = 0x40000000u >> (23 - c->F);
@@ -351,7 +408,7 @@ void pg_destroy(pg_ctx *c)
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     drop_graph(c);
-    DevBuf *bufs[] = {&c->G0, &c->G1, &c->AG1, &c->jrec, &c->stage, &c->xi, &c->xt, &c->ctr,
+    DevBuf *bufs[] = {&c->G0, &c->G1, &c->AG1, &c->P0, &c->P1, &c->AGP, &c->epsi, &c->jrec, &c->stage, &c->xi, &c->xt, &c->ctr,
                       &c->skeys0, &c->skeys1, &c->svals0, &c->svals1, &c->shist, &c->ssums,
                       &c->sbbox, &c->acc, &c->pot, &c->part, &c->status, &c->g_ioff,
                       &c->g_joff, &c->g_jlist, &c->g_items, &c->g_ctr, &c->g_queue, &c->g_jhl,
@@ -449,6 +506,7 @@ int pg_set_table_values_dev(pg_ctx *c, const float *v, long long n, double r_cut
     PG_CUDA(c, launch_table_from_values(v, (float *)c->G0.p, (float *)c->G1.p, E, F, c->stream));
     PG_CUDA(c, launch_table_prep((float *)c->G0.p, (float *)c->G1.p, (float2 *)c->AG1.p, E, F,
                                  c->stream));
+    if ((rc = remerge_pot(c))) return rc;
     c->have_table = true;
     if (!same) drop_graph(c);
     return PG_OK;
@@ -462,6 +520,83 @@ int pg_get_table(pg_ctx *c, float *G0, float *G1, long long n)
     PG_CUDA(c, cudaMemcpyAsync(G0, c->G0.p, n * 4, cudaMemcpyDeviceToHost, c->stream));
     PG_CUDA(c, cudaMemcpyAsync(G1, c->G1.p, n * 4, cudaMemcpyDeviceToHost, c->stream));
     PG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return PG_OK;
+}
+
+int pg_set_table_pot(pg_ctx *c, double (*p)(double, void *), void *user)
+{
+    if (!c) return PG_EINVAL;
+    if (!p) {
+        if (c->have_pot) drop_graph(c);
+        c->have_pot = false;
+        return PG_OK;
+    }
+    if (!c->have_table) return fail(c, PG_ESTATE, "set the force table first");
+    double sc2 = (c->s_max - 2.0) / (c->r_cut * c->r_cut);
+    std::vector<float> v(c->ntab);
+    for (int k = 0; k < c->ntab; ++k) {
+        double r = std::sqrt(((double)knot_s(k, c->F) - 2.0) / sc2);
+        double pv = p(r, user);
+        if (!std::isfinite(pv)) return fail(c, PG_EINVAL, "psi(r) is not finite at a knot");
+        v[k] = (float)pv;
+    }
+    return upload_pot(c, v);
+}
+
+int pg_set_table_pot_values(pg_ctx *c, const float *v, long long n)
+{
+    if (!c) return PG_EINVAL;
+    if (!c->have_table) return fail(c, PG_ESTATE, "set the force table first");
+    if (!v) return fail(c, PG_EINVAL, "v is NULL");
+    if (n != c->ntab) return fail(c, PG_EINVAL, "n must be 2^(E+F) of the force table");
+    for (long long k = 0; k < n; ++k)
+        if (!std::isfinite(v[k])) return fail(c, PG_EINVAL, "a knot value is not finite");
+    return upload_pot(c, std::vector<float>(v, v + n));
+}
+
+static int clear_epsi(pg_ctx *c)
+{
+    if (c->have_epsi) {
+        c->w_dirty = true;     // the i records still carry eps^2
+        drop_graph(c);
+    }
+    c->have_epsi = false;
+    c->n_epsi = 0;
+    return PG_OK;
+}
+
+int pg_set_eps_i(pg_ctx *c, const double *eps, long long n)
+{
+    if (!c) return PG_EINVAL;
+    if (n < 0) return fail(c, PG_EINVAL, "n must be >= 0");
+    if (!eps || n == 0) return clear_epsi(c);
+    for (long long k = 0; k < n; ++k)
+        if (!(eps[k] >= 0.0) || !std::isfinite(eps[k]))
+            return fail(c, PG_EINVAL, "every eps must be finite and >= 0");
+    int rc;
+    if ((rc = ensure(c, c->epsi, (size_t)n * 8))) return rc;
+    // a previous run may still read the buffer; the host array may go away
+    PG_CUDA(c, cudaStreamSynchronize(c->stream));
+    PG_CUDA(c, cudaMemcpy(c->epsi.p, eps, (size_t)n * 8, cudaMemcpyHostToDevice));
+    if (!c->have_epsi) drop_graph(c);
+    c->have_epsi = true;
+    c->epsi_applied = false;
+    c->n_epsi = n;
+    return PG_OK;
+}
+
+int pg_set_eps_i_dev(pg_ctx *c, const double *eps, long long n)
+{
+    if (!c) return PG_EINVAL;
+    if (n < 0) return fail(c, PG_EINVAL, "n must be >= 0");
+    if (!eps || n == 0) return clear_epsi(c);
+    int rc;
+    if ((rc = ensure(c, c->epsi, (size_t)n * 8))) return rc;
+    PG_CUDA(c, cudaMemcpyAsync(c->epsi.p, eps, (size_t)n * 8, cudaMemcpyDeviceToDevice, c->stream));
+    if (!c->have_epsi) drop_graph(c);
+    c->have_epsi = true;
+    c->epsi_applied = false;
+    c->n_epsi = n;
     return PG_OK;
 }
 
@@ -549,6 +684,7 @@ int pg_set_i(pg_ctx *c, long long ni, const double *x)
     if (ni != c->ni) drop_graph(c);
     c->ni = ni;
     c->i_dirty = true;
+    c->epsi_applied = false;   // new i records: eps^2 not yet in them
     if (ni == 0) return PG_OK;
     size_t bx = (size_t)ni * 24;
     if ((rc = ensure_pin(c, c->pin_i, bx))) return rc;
@@ -572,6 +708,7 @@ int pg_set_i_dev(pg_ctx *c, long long ni, const double *x)
     if (ni != c->ni) drop_graph(c);
     c->ni = ni;
     c->i_dirty = true;
+    c->epsi_applied = false;   // new i records: eps^2 not yet in them
     if (ni > 0) PG_CUDA(c, launch_pack_i(x, (double4 *)c->xi.p, ni, c->stream));
     return PG_OK;
 }
@@ -681,6 +818,28 @@ struct Plan {
 // the SMs) for small ones
 int auto_np(long long ni) { return ni >= 65536 ? 4 : ni >= 8192 ? 2 : 1; }
 
+// the kernels' EXT variant: Newton with per-i softening or eps = 0 (a zero
+// guard), table mode with the potential table
+bool use_ext(const pg_ctx *c)
+{
+    if (c->mode == PG_TABLE) return c->have_pot;
+    return c->have_epsi || (float)(c->eps * c->eps) == 0.0f;
+}
+
+// the table's size as staged in shared memory, in float2 units
+int tab_units(const pg_ctx *c) { return c->have_pot ? 2 * c->ntab : c->ntab; }
+
+// the combine's fields for the self term and the potential
+void combine_ext(const pg_ctx *c, CombineArgs &cb)
+{
+    const bool table = c->mode == PG_TABLE;
+    cb.newton = !table;
+    cb.tabpot = table && c->have_pot;
+    cb.agp = c->have_pot ? (const float4 *)c->AGP.p : nullptr;
+    cb.epsi = !table && c->have_epsi;
+    cb.xi = (const double4 *)c->xi.p;
+}
+
 int plan_allpairs(pg_ctx *c, Plan &p)
 {
     p.ni = c->ni;
@@ -690,7 +849,8 @@ int plan_allpairs(pg_ctx *c, Plan &p)
     p.ntiles = (int)((p.ni + p.Bi - 1) / p.Bi);
     p.njsub = (int)((p.nj + kTJ - 1) / kTJ);
     p.W = (long long)p.ntiles * p.njsub;
-    int occ = allpairs_max_blocks_per_sm(p.np, c->mode == PG_TABLE, c->ntab, c->packed != 0);
+    int occ = allpairs_max_blocks_per_sm(p.np, c->mode == PG_TABLE, tab_units(c), c->packed != 0,
+                                         use_ext(c));
     int per = c->ctas_per_sm > 0 ? std::min(c->ctas_per_sm, occ) : occ;
     long long g = (long long)c->sms * per;
     p.grid = (int)std::max<long long>(0, std::min<long long>(g, p.W));
@@ -762,12 +922,12 @@ int enqueue_allpairs(pg_ctx *c, const Plan &p, double *acc, double *pot)
     if (table) a.tab = table_dev(c);
     a.part = (double4 *)c->part.p;
     a.status = (int *)c->status.p;
-    bool zsafe = !table && a.eps2 == 0.0f;
-    size_t smem = allpairs_smem(p.np, table, c->ntab);
+    const bool ext = use_ext(c);
+    size_t smem = allpairs_smem(p.np, table, tab_units(c), ext);
     c->last_np = p.np;
     if (p.grid > 0) {
         if (c->timing) PG_CUDA(c, record_timing(c, c->tk0));
-        PG_CUDA(c, launch_allpairs(a, p.grid, p.np, table, zsafe, c->packed != 0, smem, c->stream));
+        PG_CUDA(c, launch_allpairs(a, p.grid, p.np, table, ext, c->packed != 0, smem, c->stream));
         if (c->timing) PG_CUDA(c, record_timing(c, c->tk1));
         c->timed = c->timing;
         c->last_launches += 1;
@@ -783,7 +943,7 @@ int enqueue_allpairs(pg_ctx *c, const Plan &p, double *acc, double *pot)
     cb.grid = std::max(p.grid, 1);
     cb.W = std::max<long long>(p.W, 1);
     cb.self = c->self;
-    cb.newton = !table;
+    combine_ext(c, cb);
     cb.eps2 = a.eps2;
     cb.accscale = table ? 1.0 / c->scale : 1.0;
     cb.acc = acc;
@@ -800,6 +960,11 @@ int check_run_state(pg_ctx *c)
 {
     if (c->ni < 0) return fail(c, PG_ESTATE, "pg_set_i has not been called");
     if (c->mode == PG_TABLE && !c->have_table) return fail(c, PG_ESTATE, "table mode without a table");
+    if (c->have_epsi) {
+        if (c->mode != PG_NEWTON) return fail(c, PG_ESTATE, "per-i softening is for PG_NEWTON");
+        if (c->n_epsi != c->ni)
+            return fail(c, PG_ESTATE, "per-i softening needs one eps per i-particle of pg_set_i");
+    }
     if (c->have_groups) {
         if (c->h_ioff.back() > c->ni)
             return fail(c, PG_ESTATE, "groups cover more i-particles than pg_set_i gave");
@@ -881,13 +1046,14 @@ int launch_group_kernel(pg_ctx *c, const GroupArgs &g, bool cell)
     bool table = c->mode == PG_TABLE;
     int np = groups_np(c);
     c->last_np = np;
-    int occ = groups_max_blocks_per_sm(np, table, c->ntab, cell);
+    const bool ext = use_ext(c);
+    int occ = groups_max_blocks_per_sm(np, table, tab_units(c), cell, ext);
     int per = c->ctas_per_sm > 0 ? std::min(c->ctas_per_sm, occ) : occ;
     int grid = c->sms * per;
     PG_CUDA(c, cudaMemsetAsync(c->g_queue.p, 0, sizeof(int), c->stream));
     if (c->timing) PG_CUDA(c, record_timing(c, c->tk0));
-    PG_CUDA(c, launch_groups(g, grid, np, table, cell, !table && g.eps2 == 0.0f,
-                             groups_smem(np, table, c->ntab), c->stream));
+    PG_CUDA(c, launch_groups(g, grid, np, table, cell, ext, groups_smem(np, table, tab_units(c)),
+                             c->stream));
     if (c->timing) PG_CUDA(c, record_timing(c, c->tk1));
     c->timed = c->timing;
     c->last_grid = grid;
@@ -939,7 +1105,7 @@ int enqueue_narrow(pg_ctx *c, double *acc, double *pot)
     const int np = groups_np(c);
     const int Bi = groups_bi(np);
     const int nic = (int)((ni + Bi - 1) / Bi);
-    const int occ = groups_max_blocks_per_sm(np, table, c->ntab, false);
+    const int occ = groups_max_blocks_per_sm(np, table, tab_units(c), false, use_ext(c));
     const long long warps = (long long)c->sms * occ * 4;
     const long long per = std::max<long long>(1, warps / nic);
     long long jc = (nj + per - 1) / per;
@@ -983,9 +1149,17 @@ int enqueue_narrow(pg_ctx *c, double *acc, double *pot)
     g.acc = acc;
     g.pot = pot;
     if ((rc = launch_group_kernel(c, g, false))) return rc;
-    PG_CUDA(c, launch_group_partials_combine((const double4 *)c->n_part.p, (int)nch, ni,
-                                             g.accscale, !table, c->self != 0, g.eps2,
-                                             (const double4 *)c->jrec.p, acc, pot, c->stream));
+    CombineArgs cb{};
+    cb.part = (const double4 *)c->n_part.p;
+    cb.jrec = (const double4 *)c->jrec.p;
+    cb.ni = ni;
+    cb.self = c->self;
+    combine_ext(c, cb);
+    cb.eps2 = g.eps2;
+    cb.accscale = g.accscale;
+    cb.acc = acc;
+    cb.pot = pot;
+    PG_CUDA(c, launch_group_partials_combine(cb, (int)nch, c->stream));
     c->last_launches += 1;
     c->last_slots = nch;
     return PG_OK;
@@ -1113,6 +1287,19 @@ int enqueue_cells(pg_ctx *c, double *acc, double *pot)
 int enqueue_run(pg_ctx *c, double *acc, double *pot)
 {
     c->last_launches = 0;
+    // per-i softening lives in the i records' w (read by every path); a
+    // captured graph writes it on every replay, as the records may be new
+    if (c->have_epsi && (c->capturing || !c->epsi_applied)) {
+        PG_CUDA(c, launch_set_w((double4 *)c->xi.p, (const double *)c->epsi.p, c->ni, c->stream));
+        c->epsi_applied = true;
+        c->i_dirty = true;
+        c->last_launches += 1;
+    } else if (!c->have_epsi && c->w_dirty) {
+        PG_CUDA(c, launch_set_w((double4 *)c->xi.p, nullptr, c->ni, c->stream));
+        c->w_dirty = false;
+        c->i_dirty = true;
+        c->last_launches += 1;
+    }
     if (c->have_groups) return enqueue_groups(c, acc, pot);
     if (c->box > 0.0) return enqueue_cells(c, acc, pot);
     if (use_narrow(c)) return enqueue_narrow(c, acc, pot);
@@ -1132,7 +1319,7 @@ int run_into(pg_ctx *c, double *acc, double *pot)
              (int)c->have_groups, c->mode, c->box, c->ni, nj_of(c), c->np, c->packed,
              c->ctas_per_sm, c->eps, c->self,
              (void *)acc, (void *)pot, c->jrec.p, c->xi.p, c->sort_mode, (int)c->timing,
-             c->g_nitems, c->ngroups, c->path);
+             c->g_nitems, c->ngroups, c->path * 4 + (c->have_epsi ? 2 : 0) + (c->have_pot ? 1 : 0));
     if (!c->gexec || c->gkey != key) {
         drop_graph(c);
         // this call runs uncaptured, which also makes every allocation the
@@ -1281,6 +1468,8 @@ int pg_backward_dev(pg_ctx *c, const double *w, double *dx, double *dm, float *d
     if (c->mode == PG_TABLE && !c->have_table) return fail(c, PG_ESTATE, "table mode without a table");
     if (!c->self || c->have_groups || c->box > 0.0 || c->ni < 0 || c->ni != nj_of(c))
         return fail(c, PG_ESTATE, "the backward pass needs the all-pairs self mode with ni == nj");
+    if (c->have_epsi && c->mode == PG_NEWTON)
+        return fail(c, PG_ESTATE, "the backward pass has no per-i softening");
     bool table = c->mode == PG_TABLE;
     long long n = c->ni;
     if (n == 0) return PG_OK;
@@ -1380,8 +1569,10 @@ int pg_tune(pg_ctx *c)
     for (int pk = groups_path ? 1 : 0; pk <= 1 && !rc; ++pk)
     for (int np : nps) {
         int occ = groups_path
-                      ? groups_max_blocks_per_sm(np, c->mode == PG_TABLE, c->ntab, !c->have_groups)
-                      : allpairs_max_blocks_per_sm(np, c->mode == PG_TABLE, c->ntab, pk != 0);
+                      ? groups_max_blocks_per_sm(np, c->mode == PG_TABLE, tab_units(c), !c->have_groups,
+                                                 use_ext(c))
+                      : allpairs_max_blocks_per_sm(np, c->mode == PG_TABLE, tab_units(c), pk != 0,
+                                                   use_ext(c));
         for (int cta = occ; cta <= occ; ++cta) {     // the occupancy limit of each shape
             c->np = np;
             c->packed = pk;

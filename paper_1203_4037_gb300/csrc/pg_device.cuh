@@ -112,6 +112,18 @@ __device__ __forceinline__ float2 tab_at(unsigned tbase, unsigned bits, int shif
     return v;
 }
 
+// the same for a table with a potential half: {A, G1, A_p, P1} per knot,
+// 16 bytes; tbase = the table's shared address minus 16 times the index of
+// s = 2
+__device__ __forceinline__ float4 tab4_at(unsigned tbase, unsigned bits, int shift4)
+{
+    float4 v;
+    const unsigned addr = tbase + ((bits >> shift4) & ~15u);
+    asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+    return v;
+}
+
 // min(s, s_max) for s > 0 as the integer minimum of the FP32 bit patterns
 // (positive floats order like their bits; a NaN also maps to s_max): the
 // clamp then runs on the ALU pipe instead of the busier FMA pipe
@@ -193,6 +205,25 @@ __device__ __forceinline__ double4 ldg_d4(const double4 *p)
     double2 a = __ldg(q), b = __ldg(q + 1);
     r.x = a.x; r.y = a.y; r.z = b.x; r.w = b.y;
     return r;
+}
+
+// The potential term i's own pair added in the loop (d = 0 exactly), as the
+// loop computed it, so that subtracting it leaves no cancellation error:
+// Newton -m_k rsqrt(eps^2) (eps of the global setting or of i itself; at
+// eps = 0 the pair added nothing); table with a potential m_k psi~(s = 2),
+// knot 0's value A_p + 2 P1.
+__device__ __forceinline__ double self_potential(const CombineArgs &c, long long k)
+{
+    const float mk = (float)c.jrec[k].w;
+    if (c.newton) {
+        const float e2 = c.epsi ? (float)c.xi[k].w : c.eps2;
+        return e2 > 0.0f ? -(double)__fmul_rn(mk, rsq(e2)) : 0.0;
+    }
+    if (c.tabpot) {
+        const float4 t0 = c.agp[0];
+        return (double)__fmul_rn(mk, __fmaf_rn(2.0f, t0.w, t0.z));
+    }
+    return 0.0;
 }
 
 }  // namespace pg

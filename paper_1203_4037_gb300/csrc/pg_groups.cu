@@ -145,7 +145,58 @@ __device__ __forceinline__ GroupItem item_at(const GroupArgs &a, int k)
     return it;
 }
 
-template <int NP, bool TABLE, bool CELL, bool ZSAFE>
+// Cell mode with a potential: particle i (cell order) is in its own cell's
+// list, so the sum holds its own pair at s = 2 (d = 0): m_i psi~(2), the
+// value of knot 0. Subtracted in FP64 from the computed FP32 product.
+__device__ __forceinline__ double cell_self_pot(const GroupArgs &a, const float2 *tab, long long i)
+{
+    const float4 t0 = reinterpret_cast<const float4 *>(tab)[0];
+    return (double)__fmul_rn(a.xo[i].w, __fmaf_rn(2.0f, t0.w, t0.z));
+}
+
+// One packed pair term (two interactions) from r2 = (ra, rb): Newton with
+// the MUFU rsqrt (EXT: zero for a coincident pair at eps = 0), or the
+// table's interpolant at s = min(r2, s_max) (EXT: with the potential half).
+template <bool TABLE, bool EXT>
+__device__ __forceinline__ void pair_term(float ra, float rb, u64 dx, u64 dy, u64 dz, u64 m,
+                                          unsigned tb0, int sh3, unsigned smax_bits, u64 &ax,
+                                          u64 &ay, u64 &az, u64 &ph)
+{
+    if (!TABLE) {
+        float qa = rsq(ra), qb = rsq(rb);
+        if (EXT) {
+            qa = ra > 0.0f ? qa : 0.0f;
+            qb = rb > 0.0f ? qb : 0.0f;
+        }
+        const u64 q = pk2(qa, qb);
+        const u64 mq = f2mul(m, q);
+        const u64 mq3 = f2mul(mq, f2mul(q, q));
+        ph = f2sub(ph, mq);
+        ax = f2fma(mq3, dx, ax);
+        ay = f2fma(mq3, dy, ay);
+        az = f2fma(mq3, dz, az);
+    } else {
+        ra = clamp_pos(ra, smax_bits);
+        rb = clamp_pos(rb, smax_bits);
+        u64 g;
+        if (EXT) {
+            const float4 ta = tab4_at(tb0, __float_as_uint(ra), sh3);
+            const float4 tb = tab4_at(tb0, __float_as_uint(rb), sh3);
+            g = pk2(__fmaf_rn(ra, ta.y, ta.x), __fmaf_rn(rb, tb.y, tb.x));
+            ph = f2fma(m, pk2(__fmaf_rn(ra, ta.w, ta.z), __fmaf_rn(rb, tb.w, tb.z)), ph);
+        } else {
+            const float2 ta = tab_at(tb0, __float_as_uint(ra), sh3);
+            const float2 tb = tab_at(tb0, __float_as_uint(rb), sh3);
+            g = pk2(__fmaf_rn(ra, ta.y, ta.x), __fmaf_rn(rb, tb.y, tb.x));
+        }
+        const u64 mg = f2mul(m, g);
+        ax = f2fma(mg, dx, ax);
+        ay = f2fma(mg, dy, ay);
+        az = f2fma(mg, dz, az);
+    }
+}
+
+template <int NP, bool TABLE, bool CELL, bool EXT>
 __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &it, const ItemShape sh,
                                            u64 *cvt, u64 *run, int *cr, const float2 *tab,
                                            const float4 *dirt, int tid)
@@ -173,8 +224,8 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
     const float c0 = TABLE ? 2.0f : a.eps2;
     const u64 c0v = pk2(c0, c0);
     const float scf = TABLE && !CELL ? (float)a.tab.scale : 1.0f;
-    const int sh3 = a.tab.shift - 3;
-    const unsigned tb0 = smem_u32(tab) - (a.tab.base << 3);
+    const int sh3 = a.tab.shift - (EXT ? 4 : 3);
+    const unsigned tb0 = smem_u32(tab) - (a.tab.base << (EXT ? 4 : 3));
     const unsigned smax_bits = __float_as_uint(a.tab.s_max);
     auto RH = [&](int p, int k) -> u64 & { return run[(8 * p + k) * kNT + tid]; };
     auto RL = [&](int p, int k) -> u64 & { return run[(8 * p + 4 + k) * kNT + tid]; };
@@ -186,10 +237,11 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
     const bool active = wl < sh.spw * L && set < sh.nsets;
 
     u64 xi[NP], yi[NP], zi[NP];
+    u64 e2i[NP];                       // Newton EXT: each i-pair's own eps^2
     u64 ax[NP], ay[NP], az[NP], ph[NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        float fx[2] = {0, 0}, fy[2] = {0, 0}, fz[2] = {0, 0};
+        float fx[2] = {0, 0}, fy[2] = {0, 0}, fz[2] = {0, 0}, fe[2] = {0, 0};
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             int k = set * 2 * NP + 2 * p + q;
@@ -202,12 +254,14 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
                     fx[q] = ((h.x - chx) + (l.x - clx)) * scf;
                     fy[q] = ((h.y - chy) + (l.y - cly)) * scf;
                     fz[q] = ((h.z - chz) + (l.z - clz)) * scf;
+                    fe[q] = l.w;
                 }
             }
         }
         xi[p] = pk2(fx[0], fx[1]);
         yi[p] = pk2(fy[0], fy[1]);
         zi[p] = pk2(fz[0], fz[1]);
+        e2i[p] = pk2(fe[0], fe[1]);
 #pragma unroll
         for (int k = 0; k < 4; ++k) RH(p, k) = RL(p, k) = 0ull;
     }
@@ -287,35 +341,13 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
                     const u64 dx = f2sub(xy.x, xi[p]);
                     const u64 dy = f2sub(xy.y, yi[p]);
                     const u64 dz = f2sub(zm.x, zi[p]);
-                    u64 r2 = f2fma(dx, dx, c0v);
+                    u64 r2 = f2fma(dx, dx, !TABLE && EXT ? e2i[p] : c0v);
                     r2 = f2fma(dy, dy, r2);
                     r2 = f2fma(dz, dz, r2);
                     float ra, rb;
                     up2(r2, ra, rb);
-                    if (!TABLE) {
-                        float qa = rsq(ra), qb = rsq(rb);
-                        if (ZSAFE) {   // eps = 0: a coincident pair adds nothing
-                            qa = ra > 0.0f ? qa : 0.0f;
-                            qb = rb > 0.0f ? qb : 0.0f;
-                        }
-                        const u64 q = pk2(qa, qb);
-                        const u64 mq = f2mul(zm.y, q);
-                        const u64 mq3 = f2mul(mq, f2mul(q, q));
-                        ph[p] = f2sub(ph[p], mq);
-                        ax[p] = f2fma(mq3, dx, ax[p]);
-                        ay[p] = f2fma(mq3, dy, ay[p]);
-                        az[p] = f2fma(mq3, dz, az[p]);
-                    } else {
-                        ra = clamp_pos(ra, smax_bits);
-                        rb = clamp_pos(rb, smax_bits);
-                        const float2 ta = tab_at(tb0, __float_as_uint(ra), sh3);
-                        const float2 tb = tab_at(tb0, __float_as_uint(rb), sh3);
-                        const u64 g = pk2(__fmaf_rn(ra, ta.y, ta.x), __fmaf_rn(rb, tb.y, tb.x));
-                        const u64 mg = f2mul(zm.y, g);
-                        ax[p] = f2fma(mg, dx, ax[p]);
-                        ay[p] = f2fma(mg, dy, ay[p]);
-                        az[p] = f2fma(mg, dz, az[p]);
-                    }
+                    pair_term<TABLE, EXT>(ra, rb, dx, dy, dz, zm.y, tb0, sh3, smax_bits,
+                                          ax[p], ay[p], az[p], ph[p]);
                 }
             }
 #pragma unroll
@@ -323,7 +355,7 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
                 fold2(RH(p, 0), RL(p, 0), ax[p]);
                 fold2(RH(p, 1), RL(p, 1), ay[p]);
                 fold2(RH(p, 2), RL(p, 2), az[p]);
-                if (!TABLE) fold2(RH(p, 3), RL(p, 3), ph[p]);
+                if (!TABLE || EXT) fold2(RH(p, 3), RL(p, 3), ph[p]);
             }
         }
         __syncthreads();   // everyone done with this tile before it is overwritten
@@ -344,7 +376,7 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
             const bool take = lane + off < L;
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-                if (TABLE && (k == 6 || k == 7)) continue;   // no potential
+                if (TABLE && !EXT && (k == 6 || k == 7)) continue;   // no potential
                 const float oh = __shfl_down_sync(0xffffffffu, h[k], off);
                 const float ol = __shfl_down_sync(0xffffffffu, l[k], off);
                 if (take) {
@@ -364,16 +396,17 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
                 int k = set * 2 * NP + 2 * p + q;
                 if (k < it.ni) {
                     long long i = it.i0 + k;
+                    const double phi = TABLE && !EXT ? 0.0 : v[6 + q];
                     if (a.part) {          // one partial of a narrow all-pairs sum
                         a.part[(long long)it.pad * a.part_stride + i] =
-                            make_double4(v[0 + q], v[2 + q], v[4 + q], TABLE ? 0.0 : v[6 + q]);
+                            make_double4(v[0 + q], v[2 + q], v[4 + q], phi);
                         continue;
                     }
                     long long o = a.perm ? (long long)a.perm[i] : i;
                     a.acc[3 * o] = v[0 + q] * a.accscale;
                     a.acc[3 * o + 1] = v[2 + q] * a.accscale;
                     a.acc[3 * o + 2] = v[4 + q] * a.accscale;
-                    if (a.pot) a.pot[o] = TABLE ? 0.0 : v[6 + q];
+                    if (a.pot) a.pot[o] = CELL && EXT ? phi - cell_self_pot(a, tab, i) : phi;
                 }
             }
         }
@@ -392,7 +425,7 @@ constexpr int kWarpTJ = 128;        // j entries per warp-staged tile
 constexpr int kWarpItemNi = 32;     // items up to this size (i-particles)
 constexpr long long kWarpItemPairs = 32768;   // and this many pairs go to warp mode
 
-template <bool TABLE, bool CELL, bool ZSAFE>
+template <bool TABLE, bool CELL, bool EXT>
 __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cur, int held,
                                           u64 *wcvt, int *wcr, const float2 *tab,
                                           const float4 *dirt, int lane32)
@@ -415,8 +448,8 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
     const float c0 = TABLE ? 2.0f : a.eps2;
     const u64 c0v = pk2(c0, c0);
     const float scf = TABLE && !CELL ? (float)a.tab.scale : 1.0f;
-    const int sh3 = a.tab.shift - 3;
-    const unsigned tb0 = smem_u32(tab) - (a.tab.base << 3);
+    const int sh3 = a.tab.shift - (EXT ? 4 : 3);
+    const unsigned tb0 = smem_u32(tab) - (a.tab.base << (EXT ? 4 : 3));
     const unsigned smax_bits = __float_as_uint(a.tab.s_max);
     ulonglong2 *sxy = reinterpret_cast<ulonglong2 *>(wcvt);            // [kWarpTJ]
     ulonglong2 *szm = sxy + kWarpTJ;                                   // [kWarpTJ]
@@ -533,7 +566,7 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
                 load_i(it, i0, sp);
                 fetch(jb, je, crc);
             }
-            float fx[2], fy[2], fz[2];
+            float fx[2], fy[2], fz[2], fe[2] = {0.0f, 0.0f};
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 if (CELL) {
@@ -542,9 +575,11 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
                     fx[q] = ((ih[q].x - chx) + (il[q].x - clx)) * scf;
                     fy[q] = ((ih[q].y - chy) + (il[q].y - cly)) * scf;
                     fz[q] = ((ih[q].z - chz) + (il[q].z - clz)) * scf;
+                    fe[q] = il[q].w;
                 }
             }
             const u64 xi = pk2(fx[0], fx[1]), yi = pk2(fy[0], fy[1]), zi = pk2(fz[0], fz[1]);
+            const u64 r0 = !TABLE && EXT ? pk2(fe[0], fe[1]) : c0v;   // eps^2 (or 2 in table units)
             const int L = sp.L, lane = sp.lane;
             const bool active = sp.active;
             u64 hx = 0, hy = 0, hz = 0, hp = 0, lx = 0, ly = 0, lz = 0, lp = 0;
@@ -594,40 +629,18 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
                     for (int e = lane; e < nvl; e += L) {
                         const ulonglong2 xy = sxy[e], zm = szm[e];
                         const u64 dx = f2sub(xy.x, xi), dy = f2sub(xy.y, yi), dz = f2sub(zm.x, zi);
-                        u64 r2 = f2fma(dx, dx, c0v);
+                        u64 r2 = f2fma(dx, dx, r0);
                         r2 = f2fma(dy, dy, r2);
                         r2 = f2fma(dz, dz, r2);
                         float ra, rb;
                         up2(r2, ra, rb);
-                        if (!TABLE) {
-                            float qa = rsq(ra), qb = rsq(rb);
-                            if (ZSAFE) {
-                                qa = ra > 0.0f ? qa : 0.0f;
-                                qb = rb > 0.0f ? qb : 0.0f;
-                            }
-                            const u64 q = pk2(qa, qb);
-                            const u64 mq = f2mul(zm.y, q);
-                            const u64 mq3 = f2mul(mq, f2mul(q, q));
-                            ph = f2sub(ph, mq);
-                            ax = f2fma(mq3, dx, ax);
-                            ay = f2fma(mq3, dy, ay);
-                            az = f2fma(mq3, dz, az);
-                        } else {
-                            ra = clamp_pos(ra, smax_bits);
-                            rb = clamp_pos(rb, smax_bits);
-                            const float2 ta = tab_at(tb0, __float_as_uint(ra), sh3);
-                            const float2 tb = tab_at(tb0, __float_as_uint(rb), sh3);
-                            const u64 g = pk2(__fmaf_rn(ra, ta.y, ta.x), __fmaf_rn(rb, tb.y, tb.x));
-                            const u64 mg = f2mul(zm.y, g);
-                            ax = f2fma(mg, dx, ax);
-                            ay = f2fma(mg, dy, ay);
-                            az = f2fma(mg, dz, az);
-                        }
+                        pair_term<TABLE, EXT>(ra, rb, dx, dy, dz, zm.y, tb0, sh3, smax_bits, ax, ay,
+                                              az, ph);
                     }
                     fold2(hx, lx, ax);
                     fold2(hy, ly, ay);
                     fold2(hz, lz, az);
-                    if (!TABLE) fold2(hp, lp, ph);
+                    if (!TABLE || EXT) fold2(hp, lp, ph);
                 }
                 __syncwarp();
             }
@@ -640,7 +653,7 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
                 const bool take = lane + off < L;
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
-                    if (TABLE && (k == 6 || k == 7)) continue;
+                    if (TABLE && !EXT && (k == 6 || k == 7)) continue;
                     const float oh = __shfl_down_sync(kFull, h[k], off);
                     const float ol = __shfl_down_sync(kFull, l[k], off);
                     if (take) {
@@ -660,7 +673,7 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
                 float vh = 0.0f, vl = 0.0f;
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
-                    if (TABLE && (k == 6 || k == 7)) continue;
+                    if (TABLE && !EXT && (k == 6 || k == 7)) continue;
                     const float th = __shfl_sync(kFull, h[k], src & 31);
                     const float tl = __shfl_sync(kFull, l[k], src & 31);
                     if (k == want) {
@@ -677,8 +690,8 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
                         const long long o = a.perm ? (long long)a.perm[i] : i;
                         if (comp < 3)
                             a.acc[3 * o + comp] = v * a.accscale;
-                        else if (a.pot)
-                            a.pot[o] = v;     // zero in table mode
+                        else if (a.pot)       // zero in table mode without a potential
+                            a.pot[o] = CELL && EXT ? v - cell_self_pot(a, tab, i) : v;
                     }
                 }
             }
@@ -706,7 +719,7 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
 
 // NPMAX: the largest i-pair count per thread; items whose shape uses the
 // threads better with half of it run with NPMAX / 2
-template <int NPMAX, bool TABLE, bool CELL, bool ZSAFE>
+template <int NPMAX, bool TABLE, bool CELL, bool EXT>
 __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -718,8 +731,10 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
     float2 *tab = reinterpret_cast<float2 *>(cr + 8 * kCellTab);
 
     const int tid = threadIdx.x;
-    if (TABLE)
+    if (TABLE && !EXT)
         for (int k = tid; k < a.tab.n; k += kNT) tab[k] = a.tab.AG1[k];
+    if (TABLE && EXT)
+        for (int k = tid; k < a.tab.n; k += kNT) reinterpret_cast<float4 *>(tab)[k] = a.tab.AGP[k];
     if (CELL && tid < 27)
         dirt[tid] = make_float4((float)(tid / 9 - 1) * a.cell_h, (float)((tid / 3) % 3 - 1) * a.cell_h,
                                 (float)(tid % 3 - 1) * a.cell_h, 0.0f);
@@ -754,12 +769,12 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
             const ItemShape big = item_shape(it.ni, NPMAX);
             const ItemShape small = item_shape(it.ni, NPMAX / 2);
             if (small.nsets <= 4 * small.spw && small.nsets * small.L > big.nsets * big.L) {
-                group_item<(NPMAX > 1 ? NPMAX / 2 : 1), TABLE, CELL, ZSAFE>(a, it, small, cvt, run,
+                group_item<(NPMAX > 1 ? NPMAX / 2 : 1), TABLE, CELL, EXT>(a, it, small, cvt, run,
                                                                              cr, tab, dirt, tid);
                 continue;
             }
         }
-        group_item<NPMAX, TABLE, CELL, ZSAFE>(a, it, item_shape(it.ni, NPMAX), cvt, run, cr, tab,
+        group_item<NPMAX, TABLE, CELL, EXT>(a, it, item_shape(it.ni, NPMAX), cvt, run, cr, tab,
                                               dirt, tid);
     }
 
@@ -767,7 +782,7 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
     // prefetched claim; every warp then claims its own items
     __syncthreads();   // no warp still reads the CTA-wide staging buffer
     const int w = tid >> 5, lane32 = tid & 31;
-    warp_loop<TABLE, CELL, ZSAFE>(a, nitems, w == 0 ? first_small : -1,
+    warp_loop<TABLE, CELL, EXT>(a, nitems, w == 0 ? first_small : -1,
                                   (w == 0 && lane32 == 0) ? next : -1,
                                   cvt + w * (2 * 2 * kWarpTJ), cr + w * 2 * kCellTab, tab, dirt,
                                   lane32);
@@ -784,71 +799,74 @@ size_t groups_smem(int np, bool table, int ntab)
 
 int groups_bi(int np) { return kNT * 2 * np; }
 
-template <int NP, bool TABLE, bool CELL, bool ZSAFE>
+template <int NP, bool TABLE, bool CELL, bool EXT>
 static cudaError_t configure_g()
 {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_groups<NP, TABLE, CELL, ZSAFE>,
+    cudaError_t e = cudaFuncSetAttribute(k_groups<NP, TABLE, CELL, EXT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)groups_smem(NP, TABLE, 1 << 13));
+                                         (int)groups_smem(NP, TABLE, 2 << 13));
     done = e == cudaSuccess;
     return e;
 }
 
-template <int NP, bool TABLE, bool CELL, bool ZSAFE>
+template <int NP, bool TABLE, bool CELL, bool EXT>
 static int occ_g(size_t smem)
 {
-    if (configure_g<NP, TABLE, CELL, ZSAFE>() != cudaSuccess) return 1;
+    if (configure_g<NP, TABLE, CELL, EXT>() != cudaSuccess) return 1;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_groups<NP, TABLE, CELL, ZSAFE>, kNT,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_groups<NP, TABLE, CELL, EXT>, kNT,
                                                       smem) != cudaSuccess)
         return 1;
     return nb > 0 ? nb : 1;
 }
 
 template <int NP>
-static int occ_np(bool table, bool cell, size_t smem)
+static int occ_np(bool table, bool cell, bool ext, size_t smem)
 {
-    if (!table) return occ_g<NP, false, false, false>(smem);
-    return cell ? occ_g<NP, true, true, false>(smem) : occ_g<NP, true, false, false>(smem);
+    if (!table) return ext ? occ_g<NP, false, false, true>(smem) : occ_g<NP, false, false, false>(smem);
+    if (cell) return ext ? occ_g<NP, true, true, true>(smem) : occ_g<NP, true, true, false>(smem);
+    return ext ? occ_g<NP, true, false, true>(smem) : occ_g<NP, true, false, false>(smem);
 }
 
-int groups_max_blocks_per_sm(int np, bool table, int ntab, bool cell)
+int groups_max_blocks_per_sm(int np, bool table, int ntab, bool cell, bool ext)
 {
     size_t smem = groups_smem(np, table, ntab);
-    return np == 1 ? occ_np<1>(table, cell, smem)
-         : np == 4 ? occ_np<4>(table, cell, smem)
-                   : occ_np<2>(table, cell, smem);
+    return np == 1 ? occ_np<1>(table, cell, ext, smem)
+         : np == 4 ? occ_np<4>(table, cell, ext, smem)
+                   : occ_np<2>(table, cell, ext, smem);
 }
 
-template <int NP, bool TABLE, bool CELL, bool ZSAFE>
+template <int NP, bool TABLE, bool CELL, bool EXT>
 static cudaError_t launch_g(const GroupArgs &g, int grid, size_t smem, cudaStream_t st)
 {
-    cudaError_t e = configure_g<NP, TABLE, CELL, ZSAFE>();
+    cudaError_t e = configure_g<NP, TABLE, CELL, EXT>();
     if (e != cudaSuccess) return e;
-    k_groups<NP, TABLE, CELL, ZSAFE><<<grid, kNT, smem, st>>>(g);
+    k_groups<NP, TABLE, CELL, EXT><<<grid, kNT, smem, st>>>(g);
     return cudaGetLastError();
 }
 
 template <int NP>
-static cudaError_t launch_gnp(const GroupArgs &g, int grid, bool table, bool cell, bool zsafe,
+static cudaError_t launch_gnp(const GroupArgs &g, int grid, bool table, bool cell, bool ext,
                               size_t smem, cudaStream_t st)
 {
-    if (!table) return zsafe ? launch_g<NP, false, false, true>(g, grid, smem, st)
-                             : launch_g<NP, false, false, false>(g, grid, smem, st);
-    return cell ? launch_g<NP, true, true, false>(g, grid, smem, st)
-                : launch_g<NP, true, false, false>(g, grid, smem, st);
+    if (!table) return ext ? launch_g<NP, false, false, true>(g, grid, smem, st)
+                           : launch_g<NP, false, false, false>(g, grid, smem, st);
+    if (cell) return ext ? launch_g<NP, true, true, true>(g, grid, smem, st)
+                         : launch_g<NP, true, true, false>(g, grid, smem, st);
+    return ext ? launch_g<NP, true, false, true>(g, grid, smem, st)
+               : launch_g<NP, true, false, false>(g, grid, smem, st);
 }
 
-cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, bool cell, bool zsafe,
+cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, bool cell, bool ext,
                           size_t smem, cudaStream_t st)
 {
     if (grid <= 0) return cudaSuccess;
     if (cell && !table) return cudaErrorInvalidValue;
-    if (np == 1) return launch_gnp<1>(g, grid, table, cell, zsafe, smem, st);
-    if (np == 2) return launch_gnp<2>(g, grid, table, cell, zsafe, smem, st);
-    if (np == 4) return launch_gnp<4>(g, grid, table, cell, zsafe, smem, st);
+    if (np == 1) return launch_gnp<1>(g, grid, table, cell, ext, smem, st);
+    if (np == 2) return launch_gnp<2>(g, grid, table, cell, ext, smem, st);
+    if (np == 4) return launch_gnp<4>(g, grid, table, cell, ext, smem, st);
     return cudaErrorInvalidValue;
 }
 
@@ -862,17 +880,14 @@ cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, bool
 constexpr int kCombineThreads = 128;
 
 __global__ void __launch_bounds__(kCombineThreads)
-k_group_partials_combine(const double4 *__restrict__ part, int nchunks, long long ni,
-                         double accscale, int newton, int self, float eps2,
-                         const double4 *__restrict__ jrec, double *__restrict__ acc,
-                         double *__restrict__ pot)
+k_group_partials_combine(CombineArgs c, int nchunks)
 {
     __shared__ double4 wsum[kCombineThreads / 32];
     const long long i = blockIdx.x;
     const int t = threadIdx.x, lane = t & 31;
     double ax = 0, ay = 0, az = 0, ph = 0;
     for (int k = t; k < nchunks; k += kCombineThreads) {
-        const double4 v = part[(long long)k * ni + i];
+        const double4 v = c.part[(long long)k * c.ni + i];
         ax += v.x; ay += v.y; az += v.z; ph += v.w;
     }
 #pragma unroll
@@ -889,28 +904,23 @@ k_group_partials_combine(const double4 *__restrict__ part, int nchunks, long lon
     for (int w = 0; w < kCombineThreads / 32; ++w) {
         ax += wsum[w].x; ay += wsum[w].y; az += wsum[w].z; ph += wsum[w].w;
     }
-    if (newton && self && eps2 > 0.0f) {
-        // the list held i's own pair (d = 0 exactly): it added -m_i rsqrt(eps^2)
-        ph += (double)__fmul_rn((float)jrec[i].w, rsq(eps2));
-    }
-    acc[3 * i] = ax * accscale;
-    acc[3 * i + 1] = ay * accscale;
-    acc[3 * i + 2] = az * accscale;
-    if (pot) pot[i] = newton ? ph : 0.0;
+    if (c.self) ph -= self_potential(c, i);   // the list held i's own pair (d = 0)
+    c.acc[3 * i] = ax * c.accscale;
+    c.acc[3 * i + 1] = ay * c.accscale;
+    c.acc[3 * i + 2] = az * c.accscale;
+    if (c.pot) c.pot[i] = c.newton || c.tabpot ? ph : 0.0;
 }
 
-cudaError_t launch_group_partials_combine(const double4 *part, int nchunks, long long ni,
-                                          double accscale, bool newton, bool self, float eps2,
-                                          const double4 *jrec, double *acc, double *pot,
-                                          cudaStream_t st)
+cudaError_t launch_group_partials_combine(const CombineArgs &c, int nchunks, cudaStream_t st)
 {
-    if (ni <= 0) return cudaSuccess;
-    k_group_partials_combine<<<(unsigned)ni, kCombineThreads, 0, st>>>(
-        part, nchunks, ni, accscale, newton ? 1 : 0, self ? 1 : 0, eps2, jrec, acc, pot);
+    if (c.ni <= 0) return cudaSuccess;
+    k_group_partials_combine<<<(unsigned)c.ni, kCombineThreads, 0, st>>>(c, nchunks);
     return cudaGetLastError();
 }
 
-// double-float records: (hi, m) then (lo, 0) per particle, lo = x - hi
+// double-float records: (hi, w) then (lo, w) per particle, lo = x - hi, w
+// the record's fourth value (the mass of a j record; eps^2 of an i record
+// with per-i softening, else 0)
 __global__ void k_pack_hilo(const double4 *__restrict__ in, long long n, float4 *__restrict__ out)
 {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -919,7 +929,7 @@ __global__ void k_pack_hilo(const double4 *__restrict__ in, long long n, float4 
     float hx = (float)v.x, hy = (float)v.y, hz = (float)v.z;
     out[2 * i] = make_float4(hx, hy, hz, (float)v.w);
     out[2 * i + 1] = make_float4((float)(v.x - (double)hx), (float)(v.y - (double)hy),
-                                 (float)(v.z - (double)hz), 0.0f);
+                                 (float)(v.z - (double)hz), (float)v.w);
 }
 
 cudaError_t launch_pack_hilo(const double4 *in, long long n, float4 *out, cudaStream_t st)

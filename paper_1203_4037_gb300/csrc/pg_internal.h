@@ -23,6 +23,7 @@ constexpr int kStatusBadIndex = 2;
 // Interpolation constants of the bit-pattern table, as the kernels use them.
 struct TableDev {
     const float2 *AG1;     // per knot {A_k = G0_k - s_k G1_k, G1_k}, 2^(E+F) entries
+    const float4 *AGP;     // with a potential table: {A_k, G1_k, A_p,k, P1_k}, else nullptr
     int n;                 // 2^(E+F)
     int shift;             // 23 - F
     unsigned base;         // bit pattern of 2.0f >> shift (index of s = 2)
@@ -56,6 +57,10 @@ struct CombineArgs {
     long long W;
     int self;              // leave out i's own pair (i index k == j index k)
     int newton;            // 1: Newton (has potential), 0: table
+    int tabpot;            // table mode with a potential table (agp set)
+    const float4 *agp;     // the {A, G1, A_p, P1} table (its knot 0 gives the self term)
+    int epsi;              // per-i softening: eps_k^2 in xi[k].w
+    const double4 *xi;     // caller-order i records (for the per-i self term)
     float eps2;
     double accscale;       // table: r_cut / sqrt(s_max - 2); Newton: 1
     double *acc;           // out: (ni, 3)
@@ -151,11 +156,13 @@ cudaError_t launch_radix_sort(unsigned *keys, unsigned *vals, long long n, int k
 cudaError_t launch_tile_prep(const double4 *xi, const unsigned *perm, long long n, int Bi,
                              double4 *xi_tiled, double4 *ctr, cudaStream_t st);
 
-cudaError_t launch_allpairs(const AllPairsArgs &a, int grid, int np, bool table, bool zsafe,
+cudaError_t launch_allpairs(const AllPairsArgs &a, int grid, int np, bool table, bool ext,
                             bool packed, size_t smem, cudaStream_t st);
 int allpairs_bi(int np);
-size_t allpairs_smem(int np, bool table, int ntab);
-int allpairs_max_blocks_per_sm(int np, bool table, int ntab, bool packed);
+// ntab: the table's size in float2 units (twice the knot count with a
+// potential table)
+size_t allpairs_smem(int np, bool table, int ntab, bool ext = false);
+int allpairs_max_blocks_per_sm(int np, bool table, int ntab, bool packed, bool ext = false);
 cudaError_t launch_combine(const CombineArgs &c, cudaStream_t st);
 long long stream_k_first(long long u, int grid, long long W);
 
@@ -164,12 +171,15 @@ cudaError_t launch_table_prep(const float *G0, const float *G1, float2 *AG1, int
 cudaError_t launch_table_from_values(const float *v, float *G0, float *G1, int E, int F,
                                      cudaStream_t st);
 
-cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, bool cell, bool zsafe,
+cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, bool cell, bool ext,
                           size_t smem, cudaStream_t st);
 cudaError_t launch_pack_hilo(const double4 *in, long long n, float4 *out, cudaStream_t st);
-size_t groups_smem(int np, bool table, int ntab);
+size_t groups_smem(int np, bool table, int ntab);   // ntab in float2 units, as above
 int groups_bi(int np);
-int groups_max_blocks_per_sm(int np, bool table, int ntab, bool cell);
+int groups_max_blocks_per_sm(int np, bool table, int ntab, bool cell, bool ext = false);
+cudaError_t launch_table_merge(const float2 *AG1, const float *P0, const float *P1, float4 *AGP,
+                               int E, int F, cudaStream_t st);
+cudaError_t launch_set_w(double4 *x, const double *eps, long long n, cudaStream_t st);
 cudaError_t launch_group_ctr(const double4 *xi, const long long *i_off, long long ngroups,
                              long long chunk, long long ni, double4 *ctr, cudaStream_t st);
 
@@ -190,10 +200,9 @@ struct CellScratch {
     unsigned long long *pairs;   // evaluated pairs of the build (device)
     unsigned *ncta;        // number of CTA-mode items (they sort first)
 };
-cudaError_t launch_group_partials_combine(const double4 *part, int nchunks, long long ni,
-                                          double accscale, bool newton, bool self, float eps2,
-                                          const double4 *jrec, double *acc, double *pot,
-                                          cudaStream_t st);
+// narrow all-pairs: part[k ni + i] for j chunks k = 0 .. nchunks - 1 (the
+// tile fields of c are unused)
+cudaError_t launch_group_partials_combine(const CombineArgs &c, int nchunks, cudaStream_t st);
 cudaError_t launch_cell_build(const double4 *jrec, long long n, double box, int nc, int Bi,
                               double scale, CellScratch &s, SortScratch &sort, cudaStream_t st);
 cudaError_t launch_excl_scan(unsigned *a, long long n, unsigned *sums, cudaStream_t st);

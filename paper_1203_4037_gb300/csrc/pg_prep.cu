@@ -20,6 +20,22 @@ __global__ void k_pack_j(const double *__restrict__ x, const double *__restrict_
     out[i] = make_double4(x[3 * i], x[3 * i + 1], x[3 * i + 2], m ? m[i] : 0.0);
 }
 
+// i records' fourth value: eps_k^2 with per-i softening (eps == nullptr: 0)
+__global__ void k_set_w(double4 *__restrict__ x, const double *__restrict__ eps, long long n)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double e = eps ? eps[i] : 0.0;
+    x[i].w = e * e;
+}
+
+cudaError_t launch_set_w(double4 *x, const double *eps, long long n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_set_w<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, eps, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pack_j(const double *x, const double *m, double4 *jrec, long long n,
                           cudaStream_t st)
 {

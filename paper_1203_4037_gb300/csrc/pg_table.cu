@@ -60,4 +60,26 @@ cudaError_t launch_table_from_values(const float *v, float *G0, float *G1, int E
     return cudaGetLastError();
 }
 
+// The force table and a potential table on the same knots, interleaved as
+// {A_k, G1_k, A_p,k, P1_k} (A_p,k = P0_k - s_k P1_k), so that one 16-byte
+// shared load gives both interpolants: g = A + s G1, psi = A_p + s P1.
+__global__ void k_table_merge(const float2 *__restrict__ AG1, const float *__restrict__ P0,
+                              const float *__restrict__ P1, float4 *__restrict__ AGP, int n,
+                              int shift)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float2 f = AG1[k];
+    const float p1 = P1[k];
+    AGP[k] = make_float4(f.x, f.y, fmaf(-knot_s(k, shift), p1, P0[k]), p1);
+}
+
+cudaError_t launch_table_merge(const float2 *AG1, const float *P0, const float *P1, float4 *AGP,
+                               int E, int F, cudaStream_t st)
+{
+    int n = 1 << (E + F);
+    k_table_merge<<<(n + 255) / 256, 256, 0, st>>>(AG1, P0, P1, AGP, n, 23 - F);
+    return cudaGetLastError();
+}
+
 }  // namespace pg
