@@ -293,8 +293,25 @@ def extra_rows(pg, torch, dev, peak_newton, headline_rate):
         c.set_i_dev(xd)
         kms = _time_kernel(c, lambda: c.run_dev(a))
         rate = n * n / (kms * 1e-3)
+        # the same with the potential table (psi = -(r^2 + eps^2)^(-1/2))
+        c.set_table_pot(lambda r: -1.0 / math.sqrt(r * r + (1 / 64) ** 2))
+        kms_p = _time_kernel(c, lambda: c.run_dev(a))
         rows["table_allpairs_65536_E3F5"] = {"interactions_per_s": rate, "kernel_ms": kms,
-                                             "frac_fp32_peak": rate / peak_table}
+                                             "frac_fp32_peak": rate / peak_table,
+                                             "with_potential_kernel_ms": kms_p,
+                                             "with_potential_interactions_per_s": n * n / (kms_p * 1e-3)}
+        # Newton with a softening per particle (log-uniform in [1/256, 1/16])
+        c.set_mode(pg.PG_NEWTON)
+        c.set_table_pot(None)
+        e = np.exp(np.random.default_rng(9).uniform(np.log(1 / 256), np.log(1 / 16), n))
+        c.set_eps_i(e)
+        kms_e = _time_kernel(c, lambda: c.run_dev(a))
+        c.set_eps_i(None)
+        c.set_eps(1 / 64)
+        kms_g = _time_kernel(c, lambda: c.run_dev(a))
+        rows["newton_per_i_softening_65536"] = {"kernel_ms": kms_e,
+                                                "interactions_per_s": n * n / (kms_e * 1e-3),
+                                                "global_eps_kernel_ms": kms_g}
 
     # backward on the same set: Newton (eps = 1/64) and the table
     from paper_1203_4037_gb300 import autograd  # noqa: F401  (binding used by users)
