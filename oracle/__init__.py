@@ -2,8 +2,10 @@
 
 TEST INFRASTRUCTURE. Only the tests, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import this package. It wraps the plain C
-file ``pg_oracle.c`` (built with gcc into ``liborc.so`` beside it) and shares
-no code with the CUDA library in ``paper_1203_4037_gb300``.
+files ``pg_oracle.c`` (the force loops, tables and gradients) and
+``pg_tree.c`` (the grouped tree of the tree usage), built with gcc into
+``liborc.so`` beside them, and shares no code with the CUDA library in
+``paper_1203_4037_gb300``.
 
 Every function takes and returns numpy FP64 arrays: positions ``(n, 3)``,
 masses ``(n,)``. ``d_ij = x_j - x_i`` and G = 1 throughout.
@@ -20,6 +22,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pg_oracle.c")
+_SRC_TREE = os.path.join(_HERE, "pg_tree.c")
 _LIB = os.path.join(_HERE, "liborc.so")
 _lock = threading.Lock()
 _lib = None
@@ -28,11 +31,15 @@ SHAPE_NEWTON, SHAPE_GAUSS_SPLIT, SHAPE_S2PP, SHAPE_LINEAR, SHAPE_NEWTON_POT = 0,
 
 
 def build(force: bool = False) -> str:
-    """Compile pg_oracle.c into liborc.so (plain gcc, -O2, no fast-math)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    """Compile pg_oracle.c and pg_tree.c into liborc.so (plain gcc, -O2, no
+    fast-math, no contraction of multiply-add: every FP64 operation rounds
+    on its own)."""
+    srcs = [_SRC, _SRC_TREE]
+    if force or not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(f)
+                                               for f in srcs):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm", "-lpthread"],
-                       check=True)
+        subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, *srcs,
+                        "-lm", "-lpthread"], check=True)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -63,6 +70,11 @@ _SIGS = {
     "orc_table_forces": (_I, [_LL, _P, _P, _LL, _P, _P, _I, _I, _D, _P, _P, _D, _D, _P, _P, _I]),
     "orc_table_potential": (_I, [_LL, _P, _P, _LL, _P, _P, _I, _I, _D, _P, _P, _D, _D, _P, _P, _I]),
     "orc_newton_epsi": (_I, [_LL, _P, _P, _P, _LL, _P, _P, _P, _P, _I]),
+    "orc_tree_build": (_P, [_LL, _P, _P, _D, _I, _I]),
+    "orc_tree_free": (None, [_P]),
+    "orc_tree_sizes": (None, [_P, _P]),
+    "orc_tree_get": (None, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "orc_tree_forces": (_I, [_P, _D, _P, _P]),
     "orc_shape_forces": (_I, [_LL, _P, _P, _LL, _P, _P, _I, _P, _D, _D, _D, _P, _P, _P, _I]),
     "orc_grad_newton": (_I, [_LL, _P, _P, _P, _D, _P, _P, _P, _I]),
     "orc_grad_newton_at": (_I, [_LL, _P, _P, _P, _D, _LL, _P, _P, _P, _I]),
@@ -347,3 +359,47 @@ def fd_table_v(x, m, w, E, F, r_cut, v, bidx, h=1e-6, box=0.0, nthreads_=None):
                               float(r_cut), _ptr(v), len(bidx), _ptr(bidx), float(h),
                               _ptr(out), nthreads_ or nthreads()))
     return out
+
+
+# ---------------------------------------------------------------- tree
+def tree_build(x, m, theta, ncrit, nleaf):
+    """The grouped Barnes-Hut tree of Section 5.1 (monopoles). Returns a dict
+    with the key order ``perm``, the groups (``g_i0``, ``g_ni``, ``g_node``,
+    in key order), the lists (``j_off``, ``jlist``: k < n is sorted particle
+    k, n + t is node t), the node moments (``nM``, ``nS``) and levels."""
+    x = _f64(x, (-1, 3)); m = _f64(m)
+    n = len(x)
+    h = lib().orc_tree_build(n, _ptr(x), _ptr(m), float(theta), int(ncrit), int(nleaf))
+    if not h:
+        raise ValueError("tree build failed")
+    try:
+        sz = np.zeros(4, dtype=np.int64)
+        lib().orc_tree_sizes(h, _ptr(sz))
+        n, nnodes, ng, nlist = (int(v) for v in sz)
+        out = dict(perm=np.empty(n, np.int64), g_i0=np.empty(ng, np.int64),
+                   g_ni=np.empty(ng, np.int64), g_node=np.empty(ng, np.int64),
+                   j_off=np.empty(ng + 1, np.int64), jlist=np.empty(max(nlist, 1), np.int64),
+                   nM=np.empty(nnodes), nS=np.empty((nnodes, 3)),
+                   nlevel=np.empty(nnodes, np.int32))
+        lib().orc_tree_get(h, *(_ptr(out[k]) for k in ("perm", "g_i0", "g_ni", "g_node", "j_off",
+                                                      "jlist", "nM", "nS", "nlevel")))
+        out["jlist"] = out["jlist"][:nlist]
+        return out
+    finally:
+        lib().orc_tree_free(h)
+
+
+def tree_forces(x, m, eps, theta, ncrit, nleaf):
+    """Forces and potentials of all particles (input order) from the grouped
+    tree's lists, each particle's own entry left out."""
+    x = _f64(x, (-1, 3)); m = _f64(m)
+    n = len(x)
+    h = lib().orc_tree_build(n, _ptr(x), _ptr(m), float(theta), int(ncrit), int(nleaf))
+    if not h:
+        raise ValueError("tree build failed")
+    try:
+        acc = np.empty((n, 3)); pot = np.empty(n)
+        _chk(lib().orc_tree_forces(h, float(eps), _ptr(acc), _ptr(pot)))
+        return acc, pot
+    finally:
+        lib().orc_tree_free(h)

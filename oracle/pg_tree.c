@@ -1,0 +1,376 @@
+/* pg_tree.c -- FP64 CPU oracle of the tree front end: a Barnes-Hut tree
+ * whose i-particles are taken in groups that traverse the tree once and
+ * share the resulting interaction list (the tree usage of Section 5.1,
+ * vacuum boundary, monopole moments), and the forces of all particles from
+ * those lists.
+ *
+ * TEST INFRASTRUCTURE: only the tests, the smoke check and the CPU baseline
+ * of the bench use it. It shares no code with the CUDA library.
+ *
+ * Readings (the paper names the method, not these details):
+ *  - the root is the smallest axis-aligned cube holding all particles, with
+ *    its low corner at the per-axis minimum and side span = the largest
+ *    extent (1 if all particles coincide);
+ *  - 10 bits per axis: q_a = floor((x_a - lo_a) / span * 1024), clamped to
+ *    1023, interleaved with bit b of x at bit 3b+2 of the key; a node of
+ *    level L (0 .. 10) is a run of particles, in key order, with equal
+ *    3L-bit key prefix, and its side is span / 2^L;
+ *  - monopoles: M = sum of m, S = sum of m x, summed from the particles in
+ *    key order for level 10 and from the children in order above it; the
+ *    centre of mass is S / M;
+ *  - groups: the nodes with at most ncrit particles whose parent has more
+ *    (the root if it has at most ncrit), and the level-10 nodes whose
+ *    parent has more than ncrit; in particle order;
+ *  - opening: a group with bounding box [blo, bhi] accepts node N as one
+ *    pseudo-particle if N holds none of the group's particles and
+ *    side(N)^2 < theta^2 d^2, d the distance from N's centre of mass to the
+ *    box (0 inside it); otherwise a leaf (at most nleaf particles, or level
+ *    10) gives its particles and an internal node is opened, children in
+ *    key order, depth first (a node holding the group is always opened: its
+ *    centre of mass may lie far from the group when the mass is elsewhere);
+ *  - list entries: k < n is sorted particle k; n + t is node t, with nodes
+ *    numbered level by level and in key order within a level.
+ * Every FP64 operation is written out (separate multiply and add), so that
+ * an implementation that rounds each operation the same way takes the same
+ * decisions; the file is compiled without contraction. */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { TREE_LEVELS = 11, TREE_BITS = 10 };
+
+typedef struct {
+    long long n, nnodes, ngroups, nlist;
+    long long *perm;        /* key order -> input index */
+    unsigned *key;          /* keys in key order */
+    double *xs, *ms;        /* particles in key order */
+    long long lev_off[TREE_LEVELS + 1];   /* node index range of each level */
+    long long *nfirst, *ncount, *nchild0, *nchildn;
+    int *nlevel;
+    double *nM, *nS;        /* mass, first moment (3 per node) */
+    double span, lo[3];
+    long long *g_node, *g_i0, *g_ni;      /* groups */
+    long long *j_off, *jlist;
+} orc_tree_t;
+
+static unsigned spread10(unsigned v)
+{
+    unsigned r = 0;
+    for (int b = 0; b < TREE_BITS; ++b) r |= ((v >> b) & 1u) << (3 * b);
+    return r;
+}
+
+typedef struct { unsigned key; long long idx; } kv_t;
+
+static int kv_cmp(const void *a, const void *b)
+{
+    const kv_t *x = (const kv_t *)a, *y = (const kv_t *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return x->idx < y->idx ? -1 : x->idx > y->idx;
+}
+
+void orc_tree_free(orc_tree_t *t)
+{
+    if (!t) return;
+    free(t->perm); free(t->key); free(t->xs); free(t->ms);
+    free(t->nfirst); free(t->ncount); free(t->nchild0); free(t->nchildn); free(t->nlevel);
+    free(t->nM); free(t->nS);
+    free(t->g_node); free(t->g_i0); free(t->g_ni); free(t->j_off); free(t->jlist);
+    free(t);
+}
+
+/* squared distance from point c to the box [lo, hi] */
+static double box_d2(const double c[3], const double lo[3], const double hi[3])
+{
+    double d2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double d = 0.0;
+        if (c[a] < lo[a]) d = lo[a] - c[a];
+        else if (c[a] > hi[a]) d = c[a] - hi[a];
+        double dd = d * d;
+        d2 = d2 + dd;
+    }
+    return d2;
+}
+
+static int is_leaf(const orc_tree_t *t, long long k, int nleaf)
+{
+    return t->nlevel[k] == TREE_LEVELS - 1 || t->ncount[k] <= nleaf;
+}
+
+/* the walk of group g: calls emit(list entry) in order; returns the count */
+static long long walk(const orc_tree_t *t, long long g, double theta2, int nleaf,
+                      long long *out)
+{
+    long long i0 = t->g_i0[g], ni = t->g_ni[g];
+    double blo[3], bhi[3];
+    for (int a = 0; a < 3; ++a) { blo[a] = t->xs[3 * i0 + a]; bhi[a] = blo[a]; }
+    for (long long i = i0; i < i0 + ni; ++i)
+        for (int a = 0; a < 3; ++a) {
+            double v = t->xs[3 * i + a];
+            if (v < blo[a]) blo[a] = v;
+            if (v > bhi[a]) bhi[a] = v;
+        }
+    long long stack[8 * TREE_LEVELS + 8];
+    int sp = 0;
+    long long cnt = 0;
+    stack[sp++] = 0;    /* the root */
+    while (sp > 0) {
+        long long k = stack[--sp];
+        double c[3];
+        for (int a = 0; a < 3; ++a) c[a] = t->nS[3 * k + a] / t->nM[k];
+        double side = ldexp(t->span, -t->nlevel[k]);
+        double side2 = side * side;
+        double d2 = box_d2(c, blo, bhi);
+        double lim = theta2 * d2;
+        int holds = t->nfirst[k] <= i0 && i0 < t->nfirst[k] + t->ncount[k];
+        if (!holds && side2 < lim) {
+            if (out) out[cnt] = t->n + k;
+            ++cnt;
+        } else if (is_leaf(t, k, nleaf)) {
+            for (long long j = t->nfirst[k]; j < t->nfirst[k] + t->ncount[k]; ++j) {
+                if (out) out[cnt] = j;
+                ++cnt;
+            }
+        } else {
+            for (long long ch = t->nchild0[k] + t->nchildn[k] - 1; ch >= t->nchild0[k]; --ch)
+                stack[sp++] = ch;
+        }
+    }
+    return cnt;
+}
+
+orc_tree_t *orc_tree_build(long long n, const double *x, const double *m, double theta,
+                           int ncrit, int nleaf)
+{
+    if (n <= 0 || !(theta >= 0.0) || ncrit < 1 || nleaf < 1) return NULL;
+    orc_tree_t *t = (orc_tree_t *)calloc(1, sizeof *t);
+    if (!t) return NULL;
+    t->n = n;
+    /* root cube */
+    double hi[3];
+    for (int a = 0; a < 3; ++a) { t->lo[a] = x[a]; hi[a] = x[a]; }
+    for (long long i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            if (x[3 * i + a] < t->lo[a]) t->lo[a] = x[3 * i + a];
+            if (x[3 * i + a] > hi[a]) hi[a] = x[3 * i + a];
+        }
+    double span = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double e = hi[a] - t->lo[a];
+        if (e > span) span = e;
+    }
+    if (!(span > 0.0)) span = 1.0;
+    t->span = span;
+    /* keys and stable order */
+    kv_t *kv = (kv_t *)malloc(sizeof(kv_t) * (size_t)n);
+    t->perm = (long long *)malloc(sizeof(long long) * (size_t)n);
+    t->key = (unsigned *)malloc(sizeof(unsigned) * (size_t)n);
+    t->xs = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    t->ms = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!kv || !t->perm || !t->key || !t->xs || !t->ms) { free(kv); orc_tree_free(t); return NULL; }
+    for (long long i = 0; i < n; ++i) {
+        unsigned k = 0;
+        for (int a = 0; a < 3; ++a) {
+            double u = (x[3 * i + a] - t->lo[a]) / span;
+            double s = u * 1024.0;
+            double f = floor(s);
+            unsigned q = f >= 1023.0 ? 1023u : (unsigned)f;
+            k |= spread10(q) << (2 - a);
+        }
+        kv[i].key = k;
+        kv[i].idx = i;
+    }
+    qsort(kv, (size_t)n, sizeof(kv_t), kv_cmp);
+    for (long long i = 0; i < n; ++i) {
+        t->perm[i] = kv[i].idx;
+        t->key[i] = kv[i].key;
+        for (int a = 0; a < 3; ++a) t->xs[3 * i + a] = x[3 * kv[i].idx + a];
+        t->ms[i] = m[kv[i].idx];
+    }
+    free(kv);
+    /* nodes: runs of equal prefix at every level */
+    long long total = 0;
+    for (int L = 0; L < TREE_LEVELS; ++L) {
+        int sh = 3 * (TREE_BITS - L);
+        long long runs = 0;
+        for (long long i = 0; i < n; ++i)
+            if (i == 0 || (t->key[i] >> sh) != (t->key[i - 1] >> sh)) ++runs;
+        t->lev_off[L] = total;
+        total += runs;
+    }
+    t->lev_off[TREE_LEVELS] = total;
+    t->nnodes = total;
+    t->nfirst = (long long *)malloc(sizeof(long long) * (size_t)total);
+    t->ncount = (long long *)malloc(sizeof(long long) * (size_t)total);
+    t->nchild0 = (long long *)calloc((size_t)total, sizeof(long long));
+    t->nchildn = (long long *)calloc((size_t)total, sizeof(long long));
+    t->nlevel = (int *)malloc(sizeof(int) * (size_t)total);
+    t->nM = (double *)malloc(sizeof(double) * (size_t)total);
+    t->nS = (double *)malloc(sizeof(double) * 3 * (size_t)total);
+    if (!t->nfirst || !t->ncount || !t->nchild0 || !t->nchildn || !t->nlevel || !t->nM || !t->nS) {
+        orc_tree_free(t);
+        return NULL;
+    }
+    for (int L = 0; L < TREE_LEVELS; ++L) {
+        int sh = 3 * (TREE_BITS - L);
+        long long k = t->lev_off[L] - 1;
+        for (long long i = 0; i < n; ++i) {
+            if (i == 0 || (t->key[i] >> sh) != (t->key[i - 1] >> sh)) {
+                ++k;
+                t->nfirst[k] = i;
+                t->ncount[k] = 0;
+                t->nlevel[k] = L;
+            }
+            ++t->ncount[k];
+        }
+    }
+    /* children: the runs of the next level inside each node */
+    for (int L = 0; L + 1 < TREE_LEVELS; ++L) {
+        long long c = t->lev_off[L + 1];
+        for (long long k = t->lev_off[L]; k < t->lev_off[L + 1]; ++k) {
+            t->nchild0[k] = c;
+            long long end = t->nfirst[k] + t->ncount[k];
+            while (c < t->lev_off[L + 2] && t->nfirst[c] < end) ++c;
+            t->nchildn[k] = c - t->nchild0[k];
+        }
+    }
+    /* monopoles, bottom-up */
+    for (long long k = t->lev_off[TREE_LEVELS - 1]; k < total; ++k) {
+        double M = 0.0, S[3] = {0.0, 0.0, 0.0};
+        for (long long i = t->nfirst[k]; i < t->nfirst[k] + t->ncount[k]; ++i) {
+            M = M + t->ms[i];
+            for (int a = 0; a < 3; ++a) {
+                double p = t->ms[i] * t->xs[3 * i + a];
+                S[a] = S[a] + p;
+            }
+        }
+        t->nM[k] = M;
+        for (int a = 0; a < 3; ++a) t->nS[3 * k + a] = S[a];
+    }
+    for (int L = TREE_LEVELS - 2; L >= 0; --L)
+        for (long long k = t->lev_off[L]; k < t->lev_off[L + 1]; ++k) {
+            double M = 0.0, S[3] = {0.0, 0.0, 0.0};
+            for (long long ch = t->nchild0[k]; ch < t->nchild0[k] + t->nchildn[k]; ++ch) {
+                M = M + t->nM[ch];
+                for (int a = 0; a < 3; ++a) S[a] = S[a] + t->nS[3 * ch + a];
+            }
+            t->nM[k] = M;
+            for (int a = 0; a < 3; ++a) t->nS[3 * k + a] = S[a];
+        }
+    /* groups, in particle order */
+    long long ng = 0;
+    t->g_node = (long long *)malloc(sizeof(long long) * (size_t)n);
+    t->g_i0 = (long long *)malloc(sizeof(long long) * (size_t)n);
+    t->g_ni = (long long *)malloc(sizeof(long long) * (size_t)n);
+    if (!t->g_node || !t->g_i0 || !t->g_ni) { orc_tree_free(t); return NULL; }
+    {
+        long long *gat = (long long *)malloc(sizeof(long long) * (size_t)n);
+        if (!gat) { orc_tree_free(t); return NULL; }
+        for (long long i = 0; i < n; ++i) gat[i] = -1;
+        /* parent of each node: the node of the previous level holding its
+         * first particle (runs are nested and in order: one pass per level) */
+        for (int L = 0; L < TREE_LEVELS; ++L) {
+            long long p = L > 0 ? t->lev_off[L - 1] : 0;
+            for (long long k = t->lev_off[L]; k < t->lev_off[L + 1]; ++k) {
+                long long pc = -1;
+                if (L > 0) {
+                    while (t->nfirst[p] + t->ncount[p] <= t->nfirst[k]) ++p;
+                    pc = t->ncount[p];
+                }
+                int grp = (t->ncount[k] <= ncrit && (L == 0 || pc > ncrit)) ||
+                          (L == TREE_LEVELS - 1 && pc > ncrit);
+                if (grp) gat[t->nfirst[k]] = k;
+            }
+        }
+        for (long long i = 0; i < n; ++i)
+            if (gat[i] >= 0) {
+                t->g_node[ng] = gat[i];
+                t->g_i0[ng] = i;
+                t->g_ni[ng] = t->ncount[gat[i]];
+                ++ng;
+            }
+        free(gat);
+    }
+    t->ngroups = ng;
+    /* lists: counts, offsets, entries */
+    double theta2 = theta * theta;
+    t->j_off = (long long *)malloc(sizeof(long long) * (size_t)(ng + 1));
+    if (!t->j_off) { orc_tree_free(t); return NULL; }
+    t->j_off[0] = 0;
+    for (long long g = 0; g < ng; ++g) t->j_off[g + 1] = t->j_off[g] + walk(t, g, theta2, nleaf, NULL);
+    t->nlist = t->j_off[ng];
+    t->jlist = (long long *)malloc(sizeof(long long) * (size_t)(t->nlist > 0 ? t->nlist : 1));
+    if (!t->jlist) { orc_tree_free(t); return NULL; }
+    for (long long g = 0; g < ng; ++g) walk(t, g, theta2, nleaf, t->jlist + t->j_off[g]);
+    return t;
+}
+
+void orc_tree_sizes(const orc_tree_t *t, long long *out4)
+{
+    out4[0] = t->n;
+    out4[1] = t->nnodes;
+    out4[2] = t->ngroups;
+    out4[3] = t->nlist;
+}
+
+/* copies out: perm[n], group i0/ni/node [ngroups], j_off[ngroups + 1],
+ * jlist[nlist], node mass, first moment and level [nnodes], [3 nnodes], [nnodes] */
+void orc_tree_get(const orc_tree_t *t, long long *perm, long long *g_i0, long long *g_ni,
+                  long long *g_node, long long *j_off, long long *jlist, double *nM, double *nS,
+                  int *nlevel)
+{
+    memcpy(nlevel, t->nlevel, sizeof(int) * (size_t)t->nnodes);
+    memcpy(perm, t->perm, sizeof(long long) * (size_t)t->n);
+    memcpy(g_i0, t->g_i0, sizeof(long long) * (size_t)t->ngroups);
+    memcpy(g_ni, t->g_ni, sizeof(long long) * (size_t)t->ngroups);
+    memcpy(g_node, t->g_node, sizeof(long long) * (size_t)t->ngroups);
+    memcpy(j_off, t->j_off, sizeof(long long) * (size_t)(t->ngroups + 1));
+    memcpy(jlist, t->jlist, sizeof(long long) * (size_t)t->nlist);
+    memcpy(nM, t->nM, sizeof(double) * (size_t)t->nnodes);
+    memcpy(nS, t->nS, sizeof(double) * 3 * (size_t)t->nnodes);
+}
+
+/* Eq. (1) over each group's list, in input order: a particle's own entry
+ * (d = 0) is left out; a pseudo-particle sits at its node's centre of mass
+ * with the node's mass. FP64, list order, Neumaier-compensated. */
+int orc_tree_forces(const orc_tree_t *t, double eps, double *acc, double *pot)
+{
+    if (!(eps >= 0.0)) return -1;
+    double e2 = eps * eps;
+    for (long long g = 0; g < t->ngroups; ++g)
+        for (long long i = t->g_i0[g]; i < t->g_i0[g] + t->g_ni[g]; ++i) {
+            double s[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
+            for (long long e = t->j_off[g]; e < t->j_off[g + 1]; ++e) {
+                long long j = t->jlist[e];
+                if (j == i) continue;
+                double xj[3], mj;
+                if (j < t->n) {
+                    for (int a = 0; a < 3; ++a) xj[a] = t->xs[3 * j + a];
+                    mj = t->ms[j];
+                } else {
+                    long long k = j - t->n;
+                    for (int a = 0; a < 3; ++a) xj[a] = t->nS[3 * k + a] / t->nM[k];
+                    mj = t->nM[k];
+                }
+                double d[3], r2 = e2;
+                for (int a = 0; a < 3; ++a) {
+                    d[a] = xj[a] - t->xs[3 * i + a];
+                    r2 += d[a] * d[a];
+                }
+                double rh = sqrt(r2);
+                double v[4] = {mj * d[0] / (r2 * rh), mj * d[1] / (r2 * rh), mj * d[2] / (r2 * rh),
+                               -mj / rh};
+                for (int q = 0; q < 4; ++q) {       /* Neumaier */
+                    double tt = s[q] + v[q];
+                    if (fabs(s[q]) >= fabs(v[q])) c[q] += (s[q] - tt) + v[q];
+                    else c[q] += (v[q] - tt) + s[q];
+                    s[q] = tt;
+                }
+            }
+            long long o = t->perm[i];
+            for (int a = 0; a < 3; ++a) acc[3 * o + a] = s[a] + c[a];
+            if (pot) pot[o] = s[3] + c[3];
+        }
+    return 0;
+}

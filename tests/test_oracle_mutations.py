@@ -10,8 +10,9 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "pg_oracle.c")
+SRC_TREE = os.path.join(ROOT, "oracle", "pg_tree.c")
 PINS = ["tests/test_oracle_newton.py", "tests/test_oracle_table.py", "tests/test_oracle_grad.py",
-        "tests/test_oracle_ext.py"]
+        "tests/test_oracle_ext.py", "tests/test_oracle_tree.py"]
 
 MUTATIONS = {
     "potential sign": ("nadd(&ph, -m / rh);", "nadd(&ph, m / rh);", 0),
@@ -55,6 +56,45 @@ MUTATIONS = {
 }
 
 
+# mistakes planted in the tree oracle (pg_tree.c)
+TREE_MUTATIONS = {
+    "tree opening compares side, not its square": ("if (!holds && side2 < lim) {",
+                                                   "if (!holds && side < lim) {"),
+    "tree node holding the group accepted": ("if (!holds && side2 < lim) {", "if (side2 < lim) {"),
+    "tree centre of mass undivided": ("for (int a = 0; a < 3; ++a) c[a] = t->nS[3 * k + a] / t->nM[k];",
+                                      "for (int a = 0; a < 3; ++a) c[a] = t->nS[3 * k + a];"),
+    "tree leaf drops its last particle": (
+        "for (long long j = t->nfirst[k]; j < t->nfirst[k] + t->ncount[k]; ++j) {\n                if (out)",
+        "for (long long j = t->nfirst[k]; j < t->nfirst[k] + t->ncount[k] - 1; ++j) {\n                if (out)"),
+    "tree pseudo-particle mass halved": ("mj = t->nM[k];", "mj = 0.5 * t->nM[k];"),
+    "tree finest-level moment skips mass": ("            M = M + t->ms[i];\n", "\n"),
+    "tree own particle kept": ("if (j == i) continue;\n                double xj[3], mj;",
+                               "double xj[3], mj;"),
+}
+
+
+def _run_pins(tmp_path, name, oracle_src, tree_src):
+    mut = tmp_path / "pg_oracle_mut.c"
+    mut.write_text(oracle_src)
+    mtree = tmp_path / "pg_tree_mut.c"
+    mtree.write_text(tree_src)
+    so = tmp_path / "liborc_mut.so"
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(so), str(mut),
+                    str(mtree), "-lm", "-lpthread"], check=True)
+    env = dict(os.environ, PG_ORACLE_LIB=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
+
+
+@pytest.mark.parametrize("name", sorted(TREE_MUTATIONS))
+def test_pins_catch_tree_mutation(name, tmp_path):
+    old, new = TREE_MUTATIONS[name]
+    src = open(SRC_TREE).read()
+    assert src.count(old) == 1, f"mutation anchor not unique for {name}"
+    _run_pins(tmp_path, name, open(SRC).read(), src.replace(old, new))
+
+
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
 def test_pins_catch_mutation(name, tmp_path):
     old, new, *which = MUTATIONS[name]
@@ -67,12 +107,4 @@ def test_pins_catch_mutation(name, tmp_path):
     else:
         assert src.count(old) == 1, f"mutation anchor not unique for {name}"
         src = src.replace(old, new)
-    mut = tmp_path / "pg_oracle_mut.c"
-    mut.write_text(src)
-    so = tmp_path / "liborc_mut.so"
-    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-o", str(so), str(mut), "-lm", "-lpthread"],
-                   check=True)
-    env = dict(os.environ, PG_ORACLE_LIB=str(so))
-    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS],
-                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-    assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
+    _run_pins(tmp_path, name, src, open(SRC_TREE).read())
