@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--shape", default=None,
                     help="np,packed launch shape of the force kernel (default: the library's)")
     ap.add_argument("--workload", default="newton",
-                    choices=["newton", "table", "cells", "groups", "backward", "narrow"],
+                    choices=["newton", "table", "cells", "groups", "backward", "narrow", "tree"],
                     help="newton: the headline; the others time one row of the path alone "
                          "(for profiling) and print its measurements")
     return ap.parse_args()
@@ -277,6 +277,32 @@ def extra_rows(pg, torch, dev, peak_newton, headline_rate):
     rows["individual_steps_ni_vs_2e20"] = steps
     del xd, md
 
+    # tree front end (Section 5.1's tree usage): 2^20 Plummer, theta = 0.75,
+    # groups of at most 64, leaves of at most 8, eps = 1e-3; per call (tree
+    # build, walk, lists, forces) and the force kernel alone
+    n = N_PART
+    x, m = gen.plummer(n, gen.CONFIG_SEEDS[2])
+    xd, md = torch.tensor(x, device=dev), torch.tensor(m, device=dev)
+    a, p = torch.empty_like(xd), torch.empty_like(md)
+    with pg.Context(idx) as c:
+        c.set_stream(st.cuda_stream)
+        c.set_eps(EPS)
+        c.set_self(True)
+        c.set_timing(True)
+        c.set_tree(0.75, 64, 8)
+        c.set_j_dev(xd, md)
+        c.set_i_dev(xd)
+        ms = _time_call(torch, lambda: c.run_dev(a, p), 5, warm=2)
+        kms = c.kernel_time()
+        info = c.info()
+        t = c.get_tree()
+        rows["tree_plummer_2e20_theta075"] = {
+            "ms_per_call": ms, "force_kernel_ms": kms, "pairs": info["pairs"],
+            "interactions_per_s_kernel": info["pairs"] / (kms * 1e-3),
+            "nodes": t["nnodes"], "groups": t["ngroups"], "list_entries": t["nlist"],
+            "direct_sum_equivalent_speedup": (n * n / headline_rate) / (ms * 1e-3)}
+    del xd, md, a, p
+
     # tabulated all-pairs: 65536 Plummer, Gaussian split, r_cut = 0.1, E=3, F=5
     n = 65536
     x, m = gen.plummer(n, gen.CONFIG_SEEDS[5])
@@ -421,6 +447,24 @@ def run_row(args):
                 kms = _time_kernel(c, lambda: c.backward_dev(w, dx, dm), reps=args.steps,
                                    warm=args.warmup)
         out.update(n=n, kernel_ms=kms, interactions_per_s=n * n / (kms * 1e-3))
+    elif args.workload == "tree":
+        # the tree front end on a Plummer sphere of --n particles (default 2^20)
+        n = args.n
+        x, m = gen.plummer(n, gen.CONFIG_SEEDS[2])
+        xd, md = torch.tensor(x, device=dev), torch.tensor(m, device=dev)
+        a = torch.empty_like(xd)
+        with pg.Context(0) as c:
+            c.set_stream(st.cuda_stream)
+            c.set_eps(EPS)
+            c.set_self(True)
+            c.set_timing(True)
+            c.set_tree(0.75, 64, 8)
+            c.set_j_dev(xd, md)
+            c.set_i_dev(xd)
+            kms = _time_kernel(c, lambda: c.run_dev(a), reps=args.steps, warm=args.warmup)
+            info = c.info()
+        out.update(n=n, pairs=info["pairs"], kernel_ms=kms,
+                   interactions_per_s=info["pairs"] / (kms * 1e-3))
     elif args.workload == "narrow":
         # individual time steps: --n core particles of the 2^20 mixed set
         # against all 2^20 (default 16), path chosen automatically

@@ -127,6 +127,37 @@ int pg_set_table_values_dev(pg_ctx *ctx, const float *v, long long n, double r_c
 /* Copy the stored table (G0, G1: FP32 host arrays of n = 2^(E+F)). Syncs. */
 int pg_get_table(pg_ctx *ctx, float *G0, float *G1, long long n);
 
+/* Tree front end: the tree usage of Section 5.1 (a Barnes-Hut tree, vacuum
+ * boundary, monopole moments; i-particles in groups that traverse the tree
+ * once and share one interaction list). With theta >= 0 every later pg_run
+ * computes the forces and potentials of all particles this way: the tree is
+ * built over the j-particles on the GPU, each group of at most ncrit
+ * particles (a tree node) collects its list of particles and node
+ * pseudo-particles, and the batched-group kernel evaluates the lists; a
+ * particle's own pair is left out. Construction and opening rule:
+ *   - nodes are the runs of equal 3L-bit prefix of a 30-bit Morton key
+ *     (10 bits per axis over the bounding cube), levels 0 .. 10;
+ *   - a node holding none of the group's particles is accepted as one
+ *     pseudo-particle (its mass at its centre of mass) if
+ *     side^2 < theta^2 d^2, d from its centre of mass to the group's box;
+ *   - otherwise a leaf (at most nleaf particles, or level 10) gives its
+ *     particles and other nodes are opened.
+ * theta = 0 reproduces the direct sum. Needs PG_NEWTON, the self mode with
+ * ni == nj, no groups, no periodic box and the global eps (PG_ESTATE
+ * otherwise). A tree run reads counts back between its stages, so it
+ * synchronises and is not captured in a graph. theta < 0 turns it off.
+ * PG_EINVAL for a theta that is not finite, ncrit outside 1 .. 2^20 or
+ * nleaf < 1. */
+int pg_set_tree(pg_ctx *ctx, double theta, int ncrit, int nleaf);
+
+/* The last tree run's structure, for inspection: sizes[5] = {n, nodes,
+ * groups, list entries, work items}; then (each may be NULL) perm[n] (key
+ * order -> input index), the groups' first particle and size in key order
+ * [groups], j_off[groups + 1] and jlist[list entries] (k < n: particle k in
+ * key order; n + t: node t, nodes numbered level by level). Syncs. */
+int pg_get_tree(pg_ctx *ctx, long long *sizes, long long *perm, long long *g_i0,
+                long long *g_ni, long long *j_off, long long *jlist);
+
 /* Potential in PG_TABLE mode, an extension: the tabulated kernel of Section
  * 3.4.2 stores accelerations only. psi(r, user) is tabulated on the force
  * table's knots (same r_cut, E, F) and built the same way, including the

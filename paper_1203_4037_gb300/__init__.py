@@ -69,6 +69,8 @@ SIGNATURES = {
     "pg_set_eps_i_dev": (_I, [_P, _P, _LL]),
     "pg_set_table_pot": (_I, [_P, GFUNC, _P]),
     "pg_set_table_pot_values": (_I, [_P, _P, _LL]),
+    "pg_set_tree": (_I, [_P, _D, _I, _I]),
+    "pg_get_tree": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "pg_set_timing": (_I, [_P, _I]),
     "pg_kernel_time": (_I, [_P, C.POINTER(_D)]),
     "pg_info": (_I, [_P, C.POINTER(_LL), _I]),
@@ -180,6 +182,25 @@ def pg_set_table_pot(ctx, p, user=None):
 def pg_set_table_pot_values(ctx, v):
     v = np.ascontiguousarray(v, dtype=np.float32)
     return _check(ctx, lib().pg_set_table_pot_values(ctx, _ptr(v), len(v)))
+
+
+def pg_set_tree(ctx, theta, ncrit=64, nleaf=8):
+    return _check(ctx, lib().pg_set_tree(ctx, float(theta), int(ncrit), int(nleaf)))
+
+
+def pg_get_tree(ctx):
+    """The last tree run: dict of sizes, perm, g_i0, g_ni, j_off, jlist."""
+    sizes = np.zeros(5, dtype=np.int64)
+    _check(ctx, lib().pg_get_tree(ctx, _ptr(sizes), None, None, None, None, None))
+    n, nnodes, ng, nl, nitems = (int(v) for v in sizes)
+    out = dict(n=n, nnodes=nnodes, ngroups=ng, nlist=nl, nitems=nitems,
+               perm=np.empty(n, np.int64), g_i0=np.empty(ng, np.int64),
+               g_ni=np.empty(ng, np.int64), j_off=np.empty(ng + 1, np.int64),
+               jlist=np.empty(max(nl, 1), np.int64))
+    _check(ctx, lib().pg_get_tree(ctx, _ptr(sizes), _ptr(out["perm"]), _ptr(out["g_i0"]),
+                                  _ptr(out["g_ni"]), _ptr(out["j_off"]), _ptr(out["jlist"])))
+    out["jlist"] = out["jlist"][:nl]
+    return out
 
 
 def pg_set_eps_i(ctx, eps):
@@ -390,6 +411,12 @@ class Context:
 
     def set_eps_i(self, eps):
         pg_set_eps_i(self.h, eps)
+
+    def set_tree(self, theta, ncrit=64, nleaf=8):
+        pg_set_tree(self.h, theta, ncrit, nleaf)
+
+    def get_tree(self):
+        return pg_get_tree(self.h)
 
     def set_eps_i_dev(self, eps):
         _require_dev(eps)

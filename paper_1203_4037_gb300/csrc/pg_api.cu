@@ -82,6 +82,17 @@ struct pg_ctx {
     // groups (host copies of the CSR offsets rebuild the items when the
     // launch shape changes)
     bool have_groups = false;
+
+    // tree front end (theta >= 0: on); device buffers by role, sizes of the
+    // last build {n, nodes, groups, list entries, items}
+    bool tree_on = false;
+    double tree_theta = 0.75;
+    int tree_ncrit = 64, tree_nleaf = 8;
+    enum { TB_BBOX, TB_GEO, TB_KEY, TB_PERM, TB_XS, TB_XI0, TB_SCAN, TB_RUNS, TB_FIRST, TB_COUNT,
+           TB_CHILD0, TB_CHILDN, TB_LEV, TB_M, TB_S, TB_GAT, TB_GSCAN, TB_GI0, TB_GNI, TB_GBOX,
+           TB_IOFF, TB_JCOUNT, TB_JOFF, TB_JLIST, TB_JREC2, TB_ITEMOFF, TB_ITEMS, TB_PAIRS, TB_N };
+    DevBuf tb[TB_N];
+    long long tree_sizes[5] = {0, 0, 0, 0, 0};
     long long ngroups = 0;
     std::vector<long long> h_ioff, h_joff;
     DevBuf g_ioff, g_joff, g_jlist, g_items, g_ctr, g_queue, g_jhl, g_ihl;
@@ -418,6 +429,7 @@ void pg_destroy(pg_ctx *c)
                       &c->c_items_raw, &c->c_items, &c->c_pairs, &c->n_part, &c->bw_wj,
                       &c->bw_wt, &c->bw_dv};
     for (DevBuf *b : bufs) free_dev(*b);
+    for (DevBuf &b : c->tb) free_dev(b);
     free_pin(c->pin_j);
     free_pin(c->pin_i);
     free_pin(c->pin_o);
@@ -520,6 +532,49 @@ int pg_get_table(pg_ctx *c, float *G0, float *G1, long long n)
     PG_CUDA(c, cudaMemcpyAsync(G0, c->G0.p, n * 4, cudaMemcpyDeviceToHost, c->stream));
     PG_CUDA(c, cudaMemcpyAsync(G1, c->G1.p, n * 4, cudaMemcpyDeviceToHost, c->stream));
     PG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return PG_OK;
+}
+
+int pg_set_tree(pg_ctx *c, double theta, int ncrit, int nleaf)
+{
+    if (!c) return PG_EINVAL;
+    if (!(theta >= 0.0)) {
+        c->tree_on = false;
+        return PG_OK;
+    }
+    if (!std::isfinite(theta) || ncrit < 1 || nleaf < 1 || ncrit > (1 << 20))
+        return fail(c, PG_EINVAL, "need finite theta >= 0, 1 <= ncrit <= 2^20, nleaf >= 1");
+    c->tree_on = true;
+    c->tree_theta = theta;
+    c->tree_ncrit = ncrit;
+    c->tree_nleaf = nleaf;
+    drop_graph(c);
+    return PG_OK;
+}
+
+int pg_get_tree(pg_ctx *c, long long *sizes, long long *perm, long long *g_i0, long long *g_ni,
+                long long *j_off, long long *jlist)
+{
+    if (!c || !sizes) return PG_EINVAL;
+    PG_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < 5; ++k) sizes[k] = c->tree_sizes[k];
+    const long long n = c->tree_sizes[0], ng = c->tree_sizes[2], nl = c->tree_sizes[3];
+    if (n == 0) return PG_OK;
+    auto copy32 = [&](int b, long long cnt, long long *out, bool is_signed) -> int {
+        if (!out || cnt <= 0) return PG_OK;
+        std::vector<unsigned> h((size_t)cnt);
+        PG_CUDA(c, cudaMemcpy(h.data(), c->tb[b].p, (size_t)cnt * 4, cudaMemcpyDeviceToHost));
+        for (long long k = 0; k < cnt; ++k)
+            out[k] = is_signed ? (long long)(int)h[(size_t)k] : (long long)h[(size_t)k];
+        return PG_OK;
+    };
+    int rc;
+    if ((rc = copy32(pg_ctx::TB_PERM, n, perm, false)) || (rc = copy32(pg_ctx::TB_GI0, ng, g_i0, true)) ||
+        (rc = copy32(pg_ctx::TB_GNI, ng, g_ni, true)) || (rc = copy32(pg_ctx::TB_JLIST, nl, jlist, true)))
+        return rc;
+    if (j_off)
+        PG_CUDA(c, cudaMemcpy(j_off, c->tb[pg_ctx::TB_JOFF].p, (size_t)(ng + 1) * 8,
+                              cudaMemcpyDeviceToHost));
     return PG_OK;
 }
 
@@ -965,6 +1020,15 @@ int check_run_state(pg_ctx *c)
         if (c->n_epsi != c->ni)
             return fail(c, PG_ESTATE, "per-i softening needs one eps per i-particle of pg_set_i");
     }
+    if (c->tree_on) {
+        if (c->mode != PG_NEWTON) return fail(c, PG_ESTATE, "the tree is for PG_NEWTON");
+        if (!c->self || c->ni != nj_of(c) || c->have_groups || c->box > 0.0 || c->have_epsi)
+            return fail(c, PG_ESTATE, "the tree needs the self mode with ni == nj, no groups, no "
+                                      "periodic box and the global eps");
+        if (c->ni + 16 * c->ni >= (1LL << 31))
+            return fail(c, PG_EINVAL, "too many particles for the tree");
+        return PG_OK;
+    }
     if (c->have_groups) {
         if (c->h_ioff.back() > c->ni)
             return fail(c, PG_ESTATE, "groups cover more i-particles than pg_set_i gave");
@@ -986,7 +1050,7 @@ int check_run_state(pg_ctx *c)
 // host items for the groups: chunks of at most Bi i-particles, longest first
 // largest i-pairs per thread of the groups kernel (items may use half of it):
 // 4 for tree groups of up to hundreds of particles, 2 for the small cells
-int groups_np(const pg_ctx *c) { return c->np ? c->np : (c->have_groups ? 4 : 2); }
+int groups_np(const pg_ctx *c) { return c->np ? c->np : (c->have_groups || c->tree_on ? 4 : 2); }
 
 int upload_group_items(pg_ctx *c)
 {
@@ -1165,6 +1229,130 @@ int enqueue_narrow(pg_ctx *c, double *acc, double *pot)
     return PG_OK;
 }
 
+// device address of tree buffer b, grown to `bytes`
+template <typename T>
+int tbuf(pg_ctx *c, int b, size_t bytes, T *&out)
+{
+    int rc = ensure(c, c->tb[b], std::max<size_t>(bytes, 16));
+    out = (T *)c->tb[b].p;
+    return rc;
+}
+
+int read_dev(pg_ctx *c, void *dst, const void *src, size_t bytes)
+{
+    PG_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream));
+    PG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return PG_OK;
+}
+
+// The tree front end (Section 5.1's tree usage): build the tree over the
+// particles, walk it per group, and evaluate the lists in the batched-group
+// kernel. The stages size their buffers from counts read back in between,
+// so a tree run synchronises and is never captured in a graph.
+int enqueue_tree(pg_ctx *c, double *acc, double *pot)
+{
+    int rc;
+    const long long n = c->ni;
+    c->last_pairs = 0;
+    if (n == 0) return PG_OK;
+    TreeScratch t{};
+    size_t hn = sort_hist_entries(n);
+    size_t nb = (std::max<size_t>(hn, (size_t)n + 1) + 4095) / 4096 + 1;
+    if ((rc = ensure(c, c->skeys0, n * 4)) || (rc = ensure(c, c->skeys1, n * 4)) ||
+        (rc = ensure(c, c->svals0, n * 4)) || (rc = ensure(c, c->svals1, n * 4)) ||
+        (rc = ensure(c, c->shist, hn * 4)) || (rc = ensure(c, c->ssums, nb * 4)) ||
+        (rc = tbuf(c, pg_ctx::TB_BBOX, 48, t.bbox)) || (rc = tbuf(c, pg_ctx::TB_GEO, 32, t.geo)) ||
+        (rc = tbuf(c, pg_ctx::TB_KEY, n * 4, t.key)) || (rc = tbuf(c, pg_ctx::TB_PERM, n * 4, t.perm)) ||
+        (rc = tbuf(c, pg_ctx::TB_XS, n * 32, t.xs)) || (rc = tbuf(c, pg_ctx::TB_XI0, n * 32, t.xi0)) ||
+        (rc = tbuf(c, pg_ctx::TB_SCAN, 11 * (n + 1) * 4, t.scan)) ||
+        (rc = tbuf(c, pg_ctx::TB_RUNS, 64, t.runs_dev)))
+        return rc;
+    c->sort.keys[0] = (unsigned *)c->skeys0.p;
+    c->sort.keys[1] = (unsigned *)c->skeys1.p;
+    c->sort.vals[0] = (unsigned *)c->svals0.p;
+    c->sort.vals[1] = (unsigned *)c->svals1.p;
+    c->sort.hist = (unsigned *)c->shist.p;
+    c->sort.sums = (unsigned *)c->ssums.p;
+    PG_CUDA(c, tree_stage_keys((const double4 *)c->jrec.p, n, t, c->sort, c->stream));
+    unsigned runs[16] = {0};
+    if ((rc = read_dev(c, runs, t.runs_dev, 11 * sizeof(unsigned)))) return rc;
+    long long lev_off[12] = {0};
+    for (int L = 0; L < 11; ++L) lev_off[L + 1] = lev_off[L] + runs[L];
+    const long long nnodes = lev_off[11];
+    if (n + nnodes >= (1LL << 31)) return fail(c, PG_EINVAL, "too many tree nodes");
+    if ((rc = tbuf(c, pg_ctx::TB_FIRST, nnodes * 4, t.first)) ||
+        (rc = tbuf(c, pg_ctx::TB_COUNT, nnodes * 4, t.count)) ||
+        (rc = tbuf(c, pg_ctx::TB_CHILD0, nnodes * 4, t.child0)) ||
+        (rc = tbuf(c, pg_ctx::TB_CHILDN, nnodes * 4, t.childn)) ||
+        (rc = tbuf(c, pg_ctx::TB_LEV, nnodes, t.lev)) || (rc = tbuf(c, pg_ctx::TB_M, nnodes * 8, t.M)) ||
+        (rc = tbuf(c, pg_ctx::TB_S, nnodes * 24, t.S)) || (rc = tbuf(c, pg_ctx::TB_GAT, n * 4, t.gat)) ||
+        (rc = tbuf(c, pg_ctx::TB_GSCAN, (n + 1) * 4, t.gscan)) ||
+        (rc = tbuf(c, pg_ctx::TB_GI0, n * 4, t.g_i0)) || (rc = tbuf(c, pg_ctx::TB_GNI, n * 4, t.g_ni)) ||
+        (rc = tbuf(c, pg_ctx::TB_GBOX, n * 48, t.gbox)) ||
+        (rc = tbuf(c, pg_ctx::TB_IOFF, (n + 1) * 8, t.i_off)))
+        return rc;
+    PG_CUDA(c, tree_stage_nodes(n, lev_off, c->tree_ncrit, t, c->sort, c->stream));
+    if ((rc = read_dev(c, runs + 11, t.runs_dev + 11, sizeof(unsigned)))) return rc;
+    const long long ng = runs[11];
+    if ((rc = tbuf(c, pg_ctx::TB_JCOUNT, (ng + 1) * 4, t.jcount)) ||
+        (rc = tbuf(c, pg_ctx::TB_JOFF, (ng + 1) * 8, t.j_off)))
+        return rc;
+    PG_CUDA(c, tree_stage_walk(n, ng, c->tree_theta, c->tree_nleaf, false, t, c->sort,
+                               (int *)c->status.p, c->stream));
+    long long nlist = 0;
+    if ((rc = read_dev(c, &nlist, t.j_off + ng, sizeof(long long)))) return rc;
+    if ((rc = tbuf(c, pg_ctx::TB_JLIST, nlist * 4, t.jlist))) return rc;
+    PG_CUDA(c, tree_stage_walk(n, ng, c->tree_theta, c->tree_nleaf, true, t, c->sort,
+                               (int *)c->status.p, c->stream));
+    const int Bi = groups_bi(groups_np(c));
+    if ((rc = tbuf(c, pg_ctx::TB_JREC2, (n + nnodes) * 32, t.jrec2)) ||
+        (rc = tbuf(c, pg_ctx::TB_ITEMOFF, (ng + 1) * 4, t.item_off)) ||
+        (rc = tbuf(c, pg_ctx::TB_ITEMS, (ng + n / Bi + 1) * sizeof(GroupItem), t.items)) ||
+        (rc = tbuf(c, pg_ctx::TB_PAIRS, 8, t.pairs)))
+        return rc;
+    PG_CUDA(c, tree_stage_records(n, nnodes, ng, Bi, t, c->sort, c->stream));
+    unsigned long long pairs = 0;
+    if ((rc = read_dev(c, runs + 12, t.runs_dev + 12, sizeof(unsigned))) ||
+        (rc = read_dev(c, &pairs, t.pairs, 8)))
+        return rc;
+    const long long nitems = runs[12];
+    const long long nj = n + nnodes;
+    if ((rc = ensure(c, c->g_jhl, (size_t)nj * 32)) || (rc = ensure(c, c->g_ihl, (size_t)n * 32)) ||
+        (rc = ensure(c, c->g_ctr, (size_t)std::max<long long>(ng, 1) * 32)) ||
+        (rc = ensure(c, c->g_queue, 16)))
+        return rc;
+    PG_CUDA(c, launch_pack_hilo(t.jrec2, nj, (float4 *)c->g_jhl.p, c->stream));
+    c->jhl_n = -1;      // the buffer now holds the tree's records
+    PG_CUDA(c, launch_pack_hilo(t.xi0, n, (float4 *)c->g_ihl.p, c->stream));
+    PG_CUDA(c, launch_group_ctr(t.xi0, t.i_off, ng, 0, 0, (double4 *)c->g_ctr.p, c->stream));
+    GroupArgs g = group_args(c);
+    g.xi = t.xi0;
+    g.jrec = t.jrec2;
+    g.j_off = t.j_off;
+    g.jlist = t.jlist;
+    g.items = t.items;
+    g.gctr = (const double4 *)c->g_ctr.p;
+    g.jhl = (const float4 *)c->g_jhl.p;
+    g.ihl = (const float4 *)c->g_ihl.p;
+    g.nitems = (int)nitems;
+    g.warp_from = (int)nitems;       // lists are long: every item in CTA mode
+    g.nj = nj;
+    g.perm = t.perm;
+    g.list_self = 1;
+    g.acc = acc;
+    g.pot = pot;
+    if ((rc = launch_group_kernel(c, g, false))) return rc;
+    c->last_pairs = (long long)pairs;
+    c->last_slots = ng;
+    c->last_launches += 60;
+    c->tree_sizes[0] = n;
+    c->tree_sizes[1] = nnodes;
+    c->tree_sizes[2] = ng;
+    c->tree_sizes[3] = nlist;
+    c->tree_sizes[4] = nitems;
+    return PG_OK;
+}
+
 int enqueue_groups(pg_ctx *c, double *acc, double *pot)
 {
     int rc;
@@ -1300,6 +1488,7 @@ int enqueue_run(pg_ctx *c, double *acc, double *pot)
         c->i_dirty = true;
         c->last_launches += 1;
     }
+    if (c->tree_on) return enqueue_tree(c, acc, pot);
     if (c->have_groups) return enqueue_groups(c, acc, pot);
     if (c->box > 0.0) return enqueue_cells(c, acc, pot);
     if (use_narrow(c)) return enqueue_narrow(c, acc, pot);
@@ -1312,7 +1501,7 @@ int run_into(pg_ctx *c, double *acc, double *pot)
 {
     int rc = check_run_state(c);
     if (rc) return rc;
-    if (!c->use_graph) return enqueue_run(c, acc, pot);
+    if (!c->use_graph || c->tree_on) return enqueue_run(c, acc, pot);   // a tree run reads counts back
 
     char key[320];
     snprintf(key, sizeof key, "%d|%d|%g|%lld|%lld|%d|%d|%d|%g|%d|%p|%p|%p|%p|%d|%d|%d|%lld|%d",

@@ -145,6 +145,13 @@ __device__ __forceinline__ GroupItem item_at(const GroupArgs &a, int k)
     return it;
 }
 
+// A list that holds i itself (the tree): the loop added -m_i rsqrt(eps^2)
+// for the own pair (d = 0); nothing at eps = 0 (the zero guard)
+__device__ __forceinline__ double list_self_pot(const GroupArgs &a, long long i)
+{
+    return a.eps2 > 0.0f ? -(double)__fmul_rn(a.jhl[2 * i].w, rsq(a.eps2)) : 0.0;
+}
+
 // Cell mode with a potential: particle i (cell order) is in its own cell's
 // list, so the sum holds its own pair at s = 2 (d = 0): m_i psi~(2), the
 // value of knot 0. Subtracted in FP64 from the computed FP32 product.
@@ -406,7 +413,9 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
                     a.acc[3 * o] = v[0 + q] * a.accscale;
                     a.acc[3 * o + 1] = v[2 + q] * a.accscale;
                     a.acc[3 * o + 2] = v[4 + q] * a.accscale;
-                    if (a.pot) a.pot[o] = CELL && EXT ? phi - cell_self_pot(a, tab, i) : phi;
+                    if (a.pot)
+                        a.pot[o] = CELL && EXT ? phi - cell_self_pot(a, tab, i)
+                                 : !TABLE && a.list_self ? phi - list_self_pot(a, i) : phi;
                 }
             }
         }
@@ -691,7 +700,8 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
                         if (comp < 3)
                             a.acc[3 * o + comp] = v * a.accscale;
                         else if (a.pot)       // zero in table mode without a potential
-                            a.pot[o] = CELL && EXT ? v - cell_self_pot(a, tab, i) : v;
+                            a.pot[o] = CELL && EXT ? v - cell_self_pot(a, tab, i)
+                                     : !TABLE && a.list_self ? v - list_self_pot(a, i) : v;
                     }
                 }
             }

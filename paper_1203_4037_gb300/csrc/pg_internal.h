@@ -104,6 +104,8 @@ struct GroupArgs {
     long long ni;
     double4 *part;         // narrow all-pairs: raw FP64 sums (a, phi) per item,
     long long part_stride; //   at part[pad * part_stride + i]; nullptr: write acc
+    int list_self;         // Newton lists that hold each i itself as j record i
+                           // (the tree): its own pair is removed at the output
     const unsigned *perm;  // i index -> output index (nullptr: identity)
     double accscale;
     double *acc, *pot;
@@ -200,6 +202,39 @@ struct CellScratch {
     unsigned long long *pairs;   // evaluated pairs of the build (device)
     unsigned *ncta;        // number of CTA-mode items (they sort first)
 };
+// the tree front end (device buffers; sizes in the comments)
+struct TreeScratch {
+    unsigned long long *bbox;   // 6: ordered-int min and max per axis
+    double *geo;                // 4: root corner and span
+    unsigned *key, *perm;       // n: keys in key order, key order -> input index
+    double4 *xs, *xi0;          // n: particles in key order (x, m), (x, 0)
+    unsigned *scan;             // 11 (n + 1): run starts per level, exclusive scans
+    unsigned *runs_dev;         // 16: runs per level, then groups, items
+    int *first, *count, *child0, *childn;   // nnodes
+    unsigned char *lev;         // nnodes
+    double *M, *S;              // nnodes, 3 nnodes
+    int *gat;                   // n: group node at its first particle, else -1
+    unsigned *gscan;            // n + 1
+    int *g_i0, *g_ni;           // groups
+    double *gbox;               // 6 per group
+    long long *i_off;           // groups + 1
+    unsigned *jcount;           // groups + 1
+    long long *j_off;           // groups + 1
+    int *jlist;                 // list entries
+    double4 *jrec2;             // n + nnodes: particles, then pseudo-particles
+    unsigned *item_off;         // groups + 1
+    GroupItem *items;
+    unsigned long long *pairs;  // 1
+};
+cudaError_t tree_stage_keys(const double4 *jrec, long long n, TreeScratch &t, SortScratch &sort,
+                            cudaStream_t st);
+cudaError_t tree_stage_nodes(long long n, const long long *lev_off, int ncrit, TreeScratch &t,
+                             SortScratch &sort, cudaStream_t st);
+cudaError_t tree_stage_walk(long long n, long long ngroups, double theta, int nleaf, bool fill,
+                            TreeScratch &t, SortScratch &sort, int *status, cudaStream_t st);
+cudaError_t tree_stage_records(long long n, long long nnodes, long long ngroups, int Bi,
+                               TreeScratch &t, SortScratch &sort, cudaStream_t st);
+
 // narrow all-pairs: part[k ni + i] for j chunks k = 0 .. nchunks - 1 (the
 // tile fields of c are unused)
 cudaError_t launch_group_partials_combine(const CombineArgs &c, int nchunks, cudaStream_t st);

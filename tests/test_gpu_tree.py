@@ -1,0 +1,117 @@
+"""The tree front end (the tree usage of Section 5.1, monopole moments) on
+the GPU against the oracle's tree:
+
+- The key order, the groups and every interaction list are identical, bit
+  for bit (index work).
+- Forces and potentials from those lists agree within the Newton
+  tolerances (median <= 2e-6, max <= 1e-4).
+- theta = 0 reproduces the direct sum.
+Covered: a Plummer sphere, a clustered set with dense finest-level cells, the
+paper's theta = 0.75, several ncrit and nleaf, and the errors.
+"""
+
+import numpy as np
+import pytest
+
+import gen
+from pgtest import assert_parity, need_cuda, rel_scalar, rel_vec
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pg():
+    return need_cuda()
+
+
+def gpu_tree(pg, x, m, eps, theta, ncrit, nleaf):
+    with pg.Context(0) as c:
+        c.set_eps(eps)
+        c.set_self(True)
+        c.set_tree(theta, ncrit, nleaf)
+        a, p = c.forces(x, x, m)
+        t = c.get_tree()
+        info = c.info()
+    return a, p, t, info
+
+
+def same_lists(t, o):
+    assert np.array_equal(t["perm"], o["perm"])
+    assert np.array_equal(t["g_i0"], o["g_i0"]) and np.array_equal(t["g_ni"], o["g_ni"])
+    assert np.array_equal(t["j_off"], o["j_off"])
+    assert np.array_equal(t["jlist"], o["jlist"])
+
+
+@pytest.mark.parametrize("theta,ncrit,nleaf", [(0.75, 64, 8), (0.5, 32, 4), (1.0, 128, 16)])
+def test_plummer_lists_and_forces(pg, orc, theta, ncrit, nleaf):
+    x, m = gen.plummer(20000, 81)
+    a, p, t, info = gpu_tree(pg, x, m, 1e-3, theta, ncrit, nleaf)
+    o = orc.tree_build(x, m, theta, ncrit, nleaf)
+    same_lists(t, o)
+    assert t["nnodes"] == len(o["nM"]) and t["ngroups"] == len(o["g_i0"])
+    assert info["pairs"] == int(np.sum(o["g_ni"] * np.diff(o["j_off"])))
+    ao, po = orc.tree_forces(x, m, 1e-3, theta, ncrit, nleaf)
+    assert_parity(rel_vec(a, ao), what="a")
+    assert_parity(rel_scalar(p, po), what="phi")
+
+
+def test_clustered_set_with_dense_cells(pg, orc):
+    # clumps far narrower than a finest cell: groups larger than ncrit
+    x, m = gen.clustered_box(30000, 82, nclump=40, sigma=2e-4, periodic=False)
+    m = m * np.random.default_rng(3).uniform(0.5, 2.0, len(m))
+    a, p, t, _ = gpu_tree(pg, x, m, 1e-4, 0.75, 32, 8)
+    o = orc.tree_build(x, m, 0.75, 32, 8)
+    same_lists(t, o)
+    assert np.max(o["g_ni"]) > 32
+    ao, po = orc.tree_forces(x, m, 1e-4, 0.75, 32, 8)
+    assert_parity(rel_vec(a, ao), what="a")
+    assert_parity(rel_scalar(p, po), what="phi")
+
+
+def test_theta_zero_is_the_direct_sum(pg, orc):
+    x, m = gen.plummer(6000, 83)
+    a, p, _, _ = gpu_tree(pg, x, m, 0.01, 0.0, 64, 8)
+    ao, po = orc.newton_allpairs(x, m, 0.01)
+    assert_parity(rel_vec(a, ao), what="a")
+    assert_parity(rel_scalar(p, po), what="phi")
+
+
+def test_eps_zero_and_repeat_runs(pg, orc):
+    x, m = gen.plummer(5000, 84)
+    with pg.Context(0) as c:
+        c.set_eps(0.0)
+        c.set_self(True)
+        c.set_tree(0.75, 64, 8)
+        c.set_j(x, m)
+        c.set_i(x)
+        c.run()
+        a1, p1 = c.get_force(len(x))
+        c.run()
+        a2, p2 = c.get_force(len(x))
+    assert np.array_equal(a1, a2) and np.array_equal(p1, p2)
+    ao, po = orc.tree_forces(x, m, 0.0, 0.75, 64, 8)
+    assert_parity(rel_vec(a1, ao), what="a")
+    assert_parity(rel_scalar(p1, po), what="phi")
+
+
+def test_tree_errors(pg):
+    x, m = gen.plummer(100, 85)
+    with pg.Context(0) as c:
+        with pytest.raises(pg.PGError) as e:
+            c.set_tree(0.5, 0, 8)
+        assert e.value.code == pg.PG_EINVAL
+        c.set_tree(0.5, 16, 4)
+        c.set_j(x, m)
+        c.set_i(x)
+        with pytest.raises(pg.PGError) as e:      # not the self mode
+            c.run()
+        assert e.value.code == pg.PG_ESTATE
+        c.set_self(True)
+        c.set_mode(pg.PG_TABLE)
+        c.set_table(lambda r: 1.0, 0.3, 3, 5)
+        with pytest.raises(pg.PGError) as e:      # tree is Newton only
+            c.run()
+        assert e.value.code == pg.PG_ESTATE
+        c.set_mode(pg.PG_NEWTON)
+        c.set_tree(-1.0)                          # off: the all-pairs path again
+        c.run()
