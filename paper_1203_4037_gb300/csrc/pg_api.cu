@@ -1295,8 +1295,10 @@ int enqueue_tree(pg_ctx *c, double *acc, double *pot)
     if ((rc = read_dev(c, runs + 11, t.runs_dev + 11, sizeof(unsigned)))) return rc;
     const long long ng = runs[11];
     if ((rc = tbuf(c, pg_ctx::TB_JCOUNT, (ng + 1) * 4, t.jcount)) ||
-        (rc = tbuf(c, pg_ctx::TB_JOFF, (ng + 1) * 8, t.j_off)))
+        (rc = tbuf(c, pg_ctx::TB_JOFF, (ng + 1) * 8, t.j_off)) ||
+        (rc = tbuf(c, pg_ctx::TB_JREC2, (n + nnodes) * 32, t.jrec2)))
         return rc;
+    PG_CUDA(c, tree_stage_jrec(n, nnodes, t, c->stream));
     PG_CUDA(c, tree_stage_walk(n, ng, c->tree_theta, c->tree_nleaf, false, t, c->sort,
                                (int *)c->status.p, c->stream));
     long long nlist = 0;
@@ -1305,8 +1307,7 @@ int enqueue_tree(pg_ctx *c, double *acc, double *pot)
     PG_CUDA(c, tree_stage_walk(n, ng, c->tree_theta, c->tree_nleaf, true, t, c->sort,
                                (int *)c->status.p, c->stream));
     const int Bi = groups_bi(groups_np(c));
-    if ((rc = tbuf(c, pg_ctx::TB_JREC2, (n + nnodes) * 32, t.jrec2)) ||
-        (rc = tbuf(c, pg_ctx::TB_ITEMOFF, (ng + 1) * 4, t.item_off)) ||
+    if ((rc = tbuf(c, pg_ctx::TB_ITEMOFF, (ng + 1) * 4, t.item_off)) ||
         (rc = tbuf(c, pg_ctx::TB_ITEMS, (ng + n / Bi + 1) * sizeof(GroupItem), t.items)) ||
         (rc = tbuf(c, pg_ctx::TB_PAIRS, 8, t.pairs)))
         return rc;

@@ -230,6 +230,7 @@ cudaError_t tree_stage_keys(const double4 *jrec, long long n, TreeScratch &t, So
                             cudaStream_t st);
 cudaError_t tree_stage_nodes(long long n, const long long *lev_off, int ncrit, TreeScratch &t,
                              SortScratch &sort, cudaStream_t st);
+cudaError_t tree_stage_jrec(long long n, long long nnodes, TreeScratch &t, cudaStream_t st);
 cudaError_t tree_stage_walk(long long n, long long ngroups, double theta, int nleaf, bool fill,
                             TreeScratch &t, SortScratch &sort, int *status, cudaStream_t st);
 cudaError_t tree_stage_records(long long n, long long nnodes, long long ngroups, int Bi,

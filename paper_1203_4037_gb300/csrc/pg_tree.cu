@@ -281,7 +281,7 @@ struct WalkArgs {
     const double *gbox;
     const int *first, *count, *child0, *childn;
     const unsigned char *lev;
-    const double *M, *S;
+    const double4 *com;        // per node: centre of mass S / M, mass
     const double *geo;         // {lo, span}
     double theta2;
     int nleaf;
@@ -314,8 +314,9 @@ __global__ void k_tree_walk(WalkArgs w)
     while (sp > 0) {
         const int k = stack[--sp];
         double d2 = 0.0;
+        const double4 cm = w.com[k];
         for (int a = 0; a < 3; ++a) {
-            const double c = __ddiv_rn(w.S[3 * k + a], w.M[k]);
+            const double c = a == 0 ? cm.x : a == 1 ? cm.y : cm.z;
             double d = 0.0;
             if (c < blo[a]) d = __dsub_rn(blo[a], c);
             else if (c > bhi[a]) d = __dsub_rn(c, bhi[a]);
@@ -486,8 +487,7 @@ cudaError_t tree_stage_walk(long long n, long long ngroups, double theta, int nl
     w.child0 = t.child0;
     w.childn = t.childn;
     w.lev = t.lev;
-    w.M = t.M;
-    w.S = t.S;
+    w.com = t.jrec2 + n;       // the pseudo-particles, written before the walk
     w.theta2 = theta * theta;
     w.nleaf = nleaf;
     w.status = status;
@@ -507,11 +507,18 @@ cudaError_t tree_stage_walk(long long n, long long ngroups, double theta, int nl
     return cudaGetLastError();
 }
 
-cudaError_t tree_stage_records(long long n, long long nnodes, long long ngroups, int Bi,
-                               TreeScratch &t, SortScratch &sort, cudaStream_t st)
+// the j records: particles in key order, then one pseudo-particle per node
+// (centre of mass S / M, mass); the walk reads the centres from here
+cudaError_t tree_stage_jrec(long long n, long long nnodes, TreeScratch &t, cudaStream_t st)
 {
     cudaMemcpyAsync(t.jrec2, t.xs, n * sizeof(double4), cudaMemcpyDeviceToDevice, st);
     k_tree_pseudo<<<blocks_of(nnodes), 256, 0, st>>>(t.M, t.S, nnodes, t.jrec2 + n);
+    return cudaGetLastError();
+}
+
+cudaError_t tree_stage_records(long long n, long long nnodes, long long ngroups, int Bi,
+                               TreeScratch &t, SortScratch &sort, cudaStream_t st)
+{
     k_tree_item_counts<<<blocks_of(ngroups + 1), 256, 0, st>>>(t.g_ni, ngroups, Bi, t.item_off);
     cudaError_t e = launch_excl_scan(t.item_off, ngroups + 1, sort.sums, st);
     if (e != cudaSuccess) return e;
