@@ -25,9 +25,14 @@
  *    pseudo-particle if N holds none of the group's particles and
  *    side(N)^2 < theta^2 d^2, d the distance from N's centre of mass to the
  *    box (0 inside it); otherwise a leaf (at most nleaf particles, or level
- *    10) gives its particles and an internal node is opened, children in
- *    key order, depth first (a node holding the group is always opened: its
- *    centre of mass may lie far from the group when the mass is elsewhere);
+ *    10) gives its particles and an internal node is opened (a node holding
+ *    the group is always opened: its centre of mass may lie far from the
+ *    group when the mass is elsewhere);
+ *  - list order: breadth first. Every node of level L is decided before any
+ *    node of level L + 1, the nodes of one level in key order, and each
+ *    decision appends its entries (the node, or a leaf's particles in key
+ *    order). The paper fixes the list as a set; the order only changes the
+ *    rounding of the sums;
  *  - list entries: k < n is sorted particle k; n + t is node t, with nodes
  *    numbered level by level and in key order within a level.
  * Every FP64 operation is written out (separate multiply and add), so that
@@ -98,9 +103,12 @@ static int is_leaf(const orc_tree_t *t, long long k, int nleaf)
     return t->nlevel[k] == TREE_LEVELS - 1 || t->ncount[k] <= nleaf;
 }
 
-/* the walk of group g: calls emit(list entry) in order; returns the count */
+/* the walk of group g, breadth first through a FIFO queue (children are
+ * queued in key order, so the queue runs level by level and in key order
+ * within a level); writes the entries to out when given and returns their
+ * count. queue has room for every node: each enters at most once. */
 static long long walk(const orc_tree_t *t, long long g, double theta2, int nleaf,
-                      long long *out)
+                      long long *queue, long long *out)
 {
     long long i0 = t->g_i0[g], ni = t->g_ni[g];
     double blo[3], bhi[3];
@@ -111,12 +119,10 @@ static long long walk(const orc_tree_t *t, long long g, double theta2, int nleaf
             if (v < blo[a]) blo[a] = v;
             if (v > bhi[a]) bhi[a] = v;
         }
-    long long stack[8 * TREE_LEVELS + 8];
-    int sp = 0;
-    long long cnt = 0;
-    stack[sp++] = 0;    /* the root */
-    while (sp > 0) {
-        long long k = stack[--sp];
+    long long head = 0, tail = 0, cnt = 0;
+    queue[tail++] = 0;  /* the root */
+    while (head < tail) {
+        long long k = queue[head++];
         double c[3];
         for (int a = 0; a < 3; ++a) c[a] = t->nS[3 * k + a] / t->nM[k];
         double side = ldexp(t->span, -t->nlevel[k]);
@@ -133,8 +139,8 @@ static long long walk(const orc_tree_t *t, long long g, double theta2, int nleaf
                 ++cnt;
             }
         } else {
-            for (long long ch = t->nchild0[k] + t->nchildn[k] - 1; ch >= t->nchild0[k]; --ch)
-                stack[sp++] = ch;
+            for (long long ch = t->nchild0[k]; ch < t->nchild0[k] + t->nchildn[k]; ++ch)
+                queue[tail++] = ch;
         }
     }
     return cnt;
@@ -297,12 +303,16 @@ orc_tree_t *orc_tree_build(long long n, const double *x, const double *m, double
     double theta2 = theta * theta;
     t->j_off = (long long *)malloc(sizeof(long long) * (size_t)(ng + 1));
     if (!t->j_off) { orc_tree_free(t); return NULL; }
+    long long *queue = (long long *)malloc(sizeof(long long) * (size_t)t->nnodes);
+    if (!queue) { orc_tree_free(t); return NULL; }
     t->j_off[0] = 0;
-    for (long long g = 0; g < ng; ++g) t->j_off[g + 1] = t->j_off[g] + walk(t, g, theta2, nleaf, NULL);
+    for (long long g = 0; g < ng; ++g)
+        t->j_off[g + 1] = t->j_off[g] + walk(t, g, theta2, nleaf, queue, NULL);
     t->nlist = t->j_off[ng];
     t->jlist = (long long *)malloc(sizeof(long long) * (size_t)(t->nlist > 0 ? t->nlist : 1));
-    if (!t->jlist) { orc_tree_free(t); return NULL; }
-    for (long long g = 0; g < ng; ++g) walk(t, g, theta2, nleaf, t->jlist + t->j_off[g]);
+    if (!t->jlist) { free(queue); orc_tree_free(t); return NULL; }
+    for (long long g = 0; g < ng; ++g) walk(t, g, theta2, nleaf, queue, t->jlist + t->j_off[g]);
+    free(queue);
     return t;
 }
 

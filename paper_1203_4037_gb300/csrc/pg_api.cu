@@ -90,7 +90,9 @@ struct pg_ctx {
     int tree_ncrit = 64, tree_nleaf = 8;
     enum { TB_BBOX, TB_GEO, TB_KEY, TB_PERM, TB_XS, TB_XI0, TB_SCAN, TB_RUNS, TB_FIRST, TB_COUNT,
            TB_CHILD0, TB_CHILDN, TB_LEV, TB_M, TB_S, TB_GAT, TB_GSCAN, TB_GI0, TB_GNI, TB_GBOX,
-           TB_IOFF, TB_JCOUNT, TB_JOFF, TB_JLIST, TB_JREC2, TB_ITEMOFF, TB_ITEMS, TB_PAIRS, TB_N };
+           TB_IOFF, TB_JCOUNT, TB_JOFF, TB_JLIST, TB_JREC2, TB_ITEMOFF, TB_ITEMS, TB_PAIRS,
+           TB_VG, TB_VK, TB_VE, TB_VC, TB_VSUMS, TB_SEG, TB_BASE, TB_ETOT, TB_GBOXF, TB_NODEW,
+           TB_FILT, TB_N };
     DevBuf tb[TB_N];
     long long tree_sizes[5] = {0, 0, 0, 0, 0};
     long long ngroups = 0;
@@ -1238,6 +1240,55 @@ int tbuf(pg_ctx *c, int b, size_t bytes, T *&out)
     return rc;
 }
 
+// grows buffer b of the tree scratch to hold bytes, keeping its first keep
+// bytes (a larger buffer is allocated, the kept part copied, the old freed)
+int tgrow(pg_ctx *c, int b, size_t bytes, size_t keep)
+{
+    DevBuf &d = c->tb[b];
+    if (bytes <= d.cap) return PG_OK;
+    const size_t want = std::max(bytes, d.cap + d.cap / 2);
+    void *p = nullptr;
+    if (cudaMalloc(&p, want) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(c, PG_ENOMEM, "device allocation of " + std::to_string(want) + " bytes failed");
+    }
+    if (d.p) {
+        cudaError_t e = keep ? cudaMemcpyAsync(p, d.p, keep, cudaMemcpyDeviceToDevice, c->stream)
+                             : cudaSuccess;
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        cudaFree(d.p);
+        if (e != cudaSuccess) {
+            cudaFree(p);
+            d.p = nullptr;
+            d.cap = 0;
+            return cuda_fail(c, e, "tree scratch growth");
+        }
+    }
+    d.p = p;
+    d.cap = want;
+    return PG_OK;
+}
+
+// room for the walk's visits (with nf_keep + 1 scanned children of the
+// current level kept), and the pointers into it
+int walk_room(pg_ctx *c, TreeScratch &t, long long visits, long long v_keep, long long c_keep)
+{
+    const size_t v = (size_t)visits + 1;
+    int rc;
+    if ((rc = tgrow(c, pg_ctx::TB_VG, v * 4, (size_t)v_keep * 4)) ||
+        (rc = tgrow(c, pg_ctx::TB_VK, v * 4, (size_t)v_keep * 4)) ||
+        (rc = tgrow(c, pg_ctx::TB_VE, v * 4, (size_t)v_keep * 4)) ||
+        (rc = tgrow(c, pg_ctx::TB_VC, v * 4, (size_t)c_keep * 4)) ||
+        (rc = tgrow(c, pg_ctx::TB_VSUMS, (v / 4096 + 2) * 4, 0)))
+        return rc;
+    t.vg = (int *)c->tb[pg_ctx::TB_VG].p;
+    t.vk = (int *)c->tb[pg_ctx::TB_VK].p;
+    t.ve = (unsigned *)c->tb[pg_ctx::TB_VE].p;
+    t.vc = (unsigned *)c->tb[pg_ctx::TB_VC].p;
+    t.vsums = (unsigned *)c->tb[pg_ctx::TB_VSUMS].p;
+    return PG_OK;
+}
+
 int read_dev(pg_ctx *c, void *dst, const void *src, size_t bytes)
 {
     PG_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream));
@@ -1296,16 +1347,45 @@ int enqueue_tree(pg_ctx *c, double *acc, double *pot)
     const long long ng = runs[11];
     if ((rc = tbuf(c, pg_ctx::TB_JCOUNT, (ng + 1) * 4, t.jcount)) ||
         (rc = tbuf(c, pg_ctx::TB_JOFF, (ng + 1) * 8, t.j_off)) ||
-        (rc = tbuf(c, pg_ctx::TB_JREC2, (n + nnodes) * 32, t.jrec2)))
+        (rc = tbuf(c, pg_ctx::TB_JREC2, (n + nnodes) * 32, t.jrec2)) ||
+        (rc = tbuf(c, pg_ctx::TB_SEG, 2 * 11 * ng * 4, t.seg)) ||
+        (rc = tbuf(c, pg_ctx::TB_BASE, 11 * ng * 8, t.base)) ||
+        (rc = tbuf(c, pg_ctx::TB_ETOT, 8, t.etot)) ||
+        (rc = tbuf(c, pg_ctx::TB_GBOXF, ng * 32, t.gboxf)) ||
+        (rc = tbuf(c, pg_ctx::TB_NODEW, nnodes * sizeof(TreeNodeW), t.nodew)) ||
+        (rc = tbuf(c, pg_ctx::TB_FILT, sizeof(WalkFilter), t.filt)) ||
+        (rc = walk_room(c, t, std::max(8 * n, 2 * ng), 0, 0)))
         return rc;
     PG_CUDA(c, tree_stage_jrec(n, nnodes, t, c->stream));
-    PG_CUDA(c, tree_stage_walk(n, ng, c->tree_theta, c->tree_nleaf, false, t, c->sort,
-                               (int *)c->status.p, c->stream));
+    // the walk, one level at a time; the next frontier's size comes back
+    // to size its room
+    long long lev_v[12] = {0, ng};
+    int nlev = 1;
+    PG_CUDA(c, tree_walk_init(ng, c->tree_theta, t, c->stream));
+    for (int L = 0; L < 11; ++L) {
+        const long long o = lev_v[L], nf = lev_v[L + 1] - o;
+        if (nf > (1LL << 28))
+            return fail(c, PG_EINVAL, "tree walk frontier too large: raise theta or ncrit");
+        PG_CUDA(c, tree_walk_level(n, ng, L, o, nf, c->tree_theta, c->tree_nleaf, t, c->stream));
+        if (L == 10) break;       // the finest level opens nothing
+        unsigned nnext = 0;
+        if ((rc = read_dev(c, &nnext, t.vc + nf, sizeof(unsigned)))) return rc;
+        if (nnext == 0) break;
+        if ((rc = walk_room(c, t, lev_v[L + 1] + nnext, lev_v[L + 1], nf + 1))) return rc;
+        PG_CUDA(c, tree_walk_expand(o, nf, t, c->stream));
+        lev_v[L + 2] = lev_v[L + 1] + nnext;
+        nlev = L + 2;
+    }
+    PG_CUDA(c, tree_walk_lists(ng, lev_v, nlev, t, c->sort, c->stream));
     long long nlist = 0;
-    if ((rc = read_dev(c, &nlist, t.j_off + ng, sizeof(long long)))) return rc;
+    unsigned long long etot = 0;
+    if ((rc = read_dev(c, &nlist, t.j_off + ng, sizeof(long long))) ||
+        (rc = read_dev(c, &etot, t.etot, sizeof etot)))
+        return rc;
+    if (etot >= (1ull << 32) || (unsigned long long)nlist != etot)
+        return fail(c, PG_EINVAL, "tree interaction lists too long: raise theta or lower ncrit");
     if ((rc = tbuf(c, pg_ctx::TB_JLIST, nlist * 4, t.jlist))) return rc;
-    PG_CUDA(c, tree_stage_walk(n, ng, c->tree_theta, c->tree_nleaf, true, t, c->sort,
-                               (int *)c->status.p, c->stream));
+    PG_CUDA(c, tree_walk_fill(n, ng, lev_v, nlev, t, (int *)c->status.p, c->stream));
     const int Bi = groups_bi(groups_np(c));
     if ((rc = tbuf(c, pg_ctx::TB_ITEMOFF, (ng + 1) * 4, t.item_off)) ||
         (rc = tbuf(c, pg_ctx::TB_ITEMS, (ng + n / Bi + 1) * sizeof(GroupItem), t.items)) ||
@@ -1345,7 +1425,7 @@ int enqueue_tree(pg_ctx *c, double *acc, double *pot)
     if ((rc = launch_group_kernel(c, g, false))) return rc;
     c->last_pairs = (long long)pairs;
     c->last_slots = ng;
-    c->last_launches += 60;
+    c->last_launches += t.launches + 3;     // the stages, then two packs and the centres
     c->tree_sizes[0] = n;
     c->tree_sizes[1] = nnodes;
     c->tree_sizes[2] = ng;

@@ -203,6 +203,23 @@ struct CellScratch {
     unsigned *ncta;        // number of CTA-mode items (they sort first)
 };
 // the tree front end (device buffers; sizes in the comments)
+// a node as the walk reads it: centre of mass rounded to FP32, and its
+// particles and children
+struct alignas(16) TreeNodeW {
+    float cx, cy, cz, pad;
+    int first, count, child0, childn;
+};
+
+// the walk's FP32 pre-test of the opening criterion: bounds that decide it
+// for certain, else the FP64 test decides (see the walk kernel)
+struct WalkFilter {
+    double s2[11];              // side^2 per level, as the FP64 test rounds it
+    float s2lo[11], s2hi[11];   // s2 rounded down and up to FP32
+    float e;                    // bound on the FP32 per-axis distance error
+    float t2lo, t2hi;           // theta^2 rounded down and up
+    int on;                     // magnitudes in the range the bounds assume
+};
+
 struct TreeScratch {
     unsigned long long *bbox;   // 6: ordered-int min and max per axis
     double *geo;                // 4: root corner and span
@@ -217,6 +234,9 @@ struct TreeScratch {
     unsigned *gscan;            // n + 1
     int *g_i0, *g_ni;           // groups
     double *gbox;               // 6 per group
+    float4 *gboxf;              // 2 per group: the box rounded to FP32
+    TreeNodeW *nodew;           // nnodes
+    WalkFilter *filt;           // 1
     long long *i_off;           // groups + 1
     unsigned *jcount;           // groups + 1
     long long *j_off;           // groups + 1
@@ -225,14 +245,34 @@ struct TreeScratch {
     unsigned *item_off;         // groups + 1
     GroupItem *items;
     unsigned long long *pairs;  // 1
+    // the walk: one (group, node) pair per visit, all levels
+    int *vg, *vk;               // visits: group, node (~node once accepted)
+    unsigned *ve;               // visits + 1: entries per decision, then scanned
+    unsigned *vc;               // one level + 1: children opened, then scanned
+    unsigned *vsums;            // scan sums for the visit arrays
+    unsigned *seg;              // 2 * 11 * groups: visit span [first, end) per level and group
+    long long *base;            // 11 * groups: list position shift per group and level
+    unsigned long long *etot;   // 1: 64-bit total of the entries
+    int launches;               // kernels the stages launched
 };
 cudaError_t tree_stage_keys(const double4 *jrec, long long n, TreeScratch &t, SortScratch &sort,
                             cudaStream_t st);
 cudaError_t tree_stage_nodes(long long n, const long long *lev_off, int ncrit, TreeScratch &t,
                              SortScratch &sort, cudaStream_t st);
 cudaError_t tree_stage_jrec(long long n, long long nnodes, TreeScratch &t, cudaStream_t st);
-cudaError_t tree_stage_walk(long long n, long long ngroups, double theta, int nleaf, bool fill,
-                            TreeScratch &t, SortScratch &sort, int *status, cudaStream_t st);
+// the walk, level by level: init takes the groups' boxes and puts every
+// group at the root; level L
+// decides its frontier (visits [o, o + nf)) and scans the opened children,
+// whose count is vc[nf]; expand writes them after the frontier; lists
+// places every entry (offsets j_off), fill writes jlist
+cudaError_t tree_walk_init(long long ngroups, double theta, TreeScratch &t, cudaStream_t st);
+cudaError_t tree_walk_level(long long n, long long ngroups, int L, long long o, long long nf,
+                            double theta, int nleaf, TreeScratch &t, cudaStream_t st);
+cudaError_t tree_walk_expand(long long o, long long nf, TreeScratch &t, cudaStream_t st);
+cudaError_t tree_walk_lists(long long ngroups, const long long *lev_v, int nlev, TreeScratch &t,
+                            SortScratch &sort, cudaStream_t st);
+cudaError_t tree_walk_fill(long long n, long long ngroups, const long long *lev_v, int nlev,
+                           TreeScratch &t, int *status, cudaStream_t st);
 cudaError_t tree_stage_records(long long n, long long nnodes, long long ngroups, int Bi,
                                TreeScratch &t, SortScratch &sort, cudaStream_t st);
 

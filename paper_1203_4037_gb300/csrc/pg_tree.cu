@@ -20,11 +20,15 @@
 //  - a group with box [blo, bhi] accepts node N as one pseudo-particle if N
 //    holds none of the group's particles and side^2 < theta^2 d^2 (d from
 //    N's centre of mass to the box); else a leaf (at most nleaf particles,
-//    or the finest level) gives its particles, else N is opened, children
-//    in order, depth first.
+//    or the finest level) gives its particles, else N is opened;
+//  - a list is breadth first: the entries of level 0's decisions, then
+//    level 1's, ..., each level's in key order (the paper fixes the list as
+//    a set; the order only changes the rounding of the sums).
 // Every FP64 operation of the decisions uses an explicitly rounded
 // intrinsic (no fused multiply-add), so the lists are reproducible bit for
 // bit by any implementation that rounds the same operations the same way.
+#include <algorithm>
+
 #include "pg_device.cuh"
 
 namespace pg {
@@ -33,7 +37,6 @@ namespace {
 
 constexpr int kLevels = 11;      // levels 0 .. 10
 constexpr int kBits = 10;        // key bits per axis
-constexpr int kStack = 8 * kLevels + 8;
 
 // order-preserving map of a double onto 64-bit unsigned integers
 __device__ __forceinline__ unsigned long long ord_of(double v)
@@ -247,21 +250,31 @@ __global__ void k_tree_group_flags(const int *__restrict__ gat, long long n, uns
 
 // groups in particle order with their boxes; i_off[g] (ngroups + 1 entries)
 __global__ void k_tree_groups(const int *__restrict__ gat, const unsigned *__restrict__ gscan,
-                              long long n, const int *__restrict__ count,
-                              const double4 *__restrict__ xs, int *__restrict__ g_i0,
-                              int *__restrict__ g_ni, double *__restrict__ gbox,
-                              long long *__restrict__ i_off)
+                              long long n, const int *__restrict__ count, int *__restrict__ g_i0,
+                              int *__restrict__ g_ni, long long *__restrict__ i_off)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i == n) i_off[gscan[n]] = n;
     if (i >= n || gat[i] < 0) return;
     const unsigned g = gscan[i];
-    const int ni = count[gat[i]];
     g_i0[g] = (int)i;
-    g_ni[g] = ni;
+    g_ni[g] = count[gat[i]];
     i_off[g] = i;
-    double lo[3] = {xs[i].x, xs[i].y, xs[i].z}, hi[3] = {lo[0], lo[1], lo[2]};
-    for (long long k = i; k < i + ni; ++k) {
+}
+
+// a group's bounding box, one warp per group: FP64, and rounded to nearest
+// FP32 for the walk's pre-test
+__global__ void k_tree_gbox(const int *__restrict__ g_i0, const int *__restrict__ g_ni,
+                            long long ngroups, const double4 *__restrict__ xs,
+                            double *__restrict__ gbox, float4 *__restrict__ gboxf)
+{
+    const long long g = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (g >= ngroups) return;
+    const int i0 = g_i0[g], ni = g_ni[g];
+    const double4 v0 = xs[i0];
+    double lo[3] = {v0.x, v0.y, v0.z}, hi[3] = {v0.x, v0.y, v0.z};
+    for (int k = i0 + lane; k < i0 + ni; k += 32) {
         const double4 v = xs[k];
         const double c[3] = {v.x, v.y, v.z};
         for (int a = 0; a < 3; ++a) {
@@ -269,107 +282,266 @@ __global__ void k_tree_groups(const int *__restrict__ gat, const unsigned *__res
             if (c[a] > hi[a]) hi[a] = c[a];
         }
     }
-    for (int a = 0; a < 3; ++a) {
-        gbox[6 * g + a] = lo[a];
-        gbox[6 * g + 3 + a] = hi[a];
+    for (int s = 16; s; s >>= 1)
+        for (int a = 0; a < 3; ++a) {
+            const double l = __shfl_xor_sync(0xffffffffu, lo[a], s);
+            const double h = __shfl_xor_sync(0xffffffffu, hi[a], s);
+            if (l < lo[a]) lo[a] = l;
+            if (h > hi[a]) hi[a] = h;
+        }
+    if (lane == 0) {
+        for (int a = 0; a < 3; ++a) {
+            gbox[6 * g + a] = lo[a];
+            gbox[6 * g + 3 + a] = hi[a];
+        }
+        gboxf[2 * g] = make_float4(__double2float_rn(lo[0]), __double2float_rn(lo[1]),
+                                   __double2float_rn(lo[2]), 0.f);
+        gboxf[2 * g + 1] = make_float4(__double2float_rn(hi[0]), __double2float_rn(hi[1]),
+                                       __double2float_rn(hi[2]), 0.f);
     }
 }
 
-struct WalkArgs {
+// The walk runs level by level over all groups at once. The frontier of
+// level L is a run of (group, node) pairs, sorted by group and then node,
+// stored with every other level's frontier ("visits"); one thread decides
+// one pair, a scan of the opened children places the next level's
+// frontier, and the decisions' entries are placed afterwards. A group's
+// list comes out breadth first: its level-0 entries, then level 1, ..., in
+// key order within a level.
+//
+// The opening test is decided in FP32 where that is certain. With every
+// coordinate (particles, centres of mass, box corners) at most R in
+// magnitude and u = 2^-24, the FP32 distance per axis, from operands rounded
+// to nearest, is within 4.1 u R of the exact one; e = 8 u R bounds it.
+// Intervals for d^2 and theta^2 d^2 taken with round-down and round-up
+// arithmetic (and a 2^-23 relative widening, far above the FP64 test's own
+// rounding) then contain the FP64 test's theta^2 d^2. If side^2 lies
+// outside the interval the answer is the FP64 test's; inside, the FP64 test
+// runs. The bounds assume magnitudes where nothing overflows or falls below
+// the normal range; elsewhere every test is FP64.
+struct LevelArgs {
     long long n, ngroups;
-    const int *g_i0, *g_ni;
+    long long o, nf;           // this level's frontier: visits [o, o + nf)
+    int L;
+    const int *g_i0;
     const double *gbox;
-    const int *first, *count, *child0, *childn;
-    const unsigned char *lev;
-    const double4 *com;        // per node: centre of mass S / M, mass
-    const double *geo;         // {lo, span}
-    double theta2;
+    const float4 *gboxf;
+    const TreeNodeW *nodew;
+    const double4 *com;        // per node: centre of mass S / M, mass (FP64)
+    const WalkFilter *filt;
     int nleaf;
-    const long long *j_off;    // fill pass: offsets; count pass: nullptr
-    unsigned *jcount;          // count pass output
-    int *jlist;                // fill pass output
-    int *status;
+    const int *vg;             // visits: group
+    int *vk;                   // visits: node, ~node once accepted
+    unsigned *ve;              // visits: entries the decision emits
+    unsigned *vc;              // this level: children the decision opens (nf + 1)
+    unsigned *seg;             // per level and group: visits [first, end)
+    unsigned long long *etot;  // 64-bit sum of the entries
+    double theta2;
 };
 
-// one thread per group, depth first with an explicit stack
-__global__ void k_tree_walk(WalkArgs w)
+__global__ void k_walk_filter(const double *geo, double theta2, WalkFilter *f)
+{
+    if (threadIdx.x != 0) return;
+    const double span = geo[3];
+    double R = 0.0;
+    for (int a = 0; a < 3; ++a) R = fmax(R, fabs(geo[a]) + span);
+    R = R * (1.0 + 0x1p-20);
+    for (int L = 0; L < kLevels; ++L) {
+        const double side = ldexp(span, -L);
+        const double s2 = __dmul_rn(side, side);
+        f->s2[L] = s2;
+        f->s2lo[L] = __double2float_rd(s2);
+        f->s2hi[L] = __double2float_ru(s2);
+    }
+    f->e = __double2float_ru(R * 0x1p-21);
+    f->t2lo = __double2float_rd(theta2);
+    f->t2hi = __double2float_ru(theta2);
+    f->on = R >= 0x1p-20 && R <= 0x1p60 && span >= R * 0x1p-30 &&
+            (theta2 == 0.0 || (theta2 >= 0x1p-40 && theta2 <= 0x1p40));
+}
+
+__global__ void k_walk_init(long long ngroups, int *vg, int *vk, unsigned long long *etot)
 {
     const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (g >= w.ngroups) return;
-    const int i0 = w.g_i0[g];
-    const double span = w.geo[3];
-    double blo[3], bhi[3];
-    for (int a = 0; a < 3; ++a) {
-        blo[a] = w.gbox[6 * g + a];
-        bhi[a] = w.gbox[6 * g + 3 + a];
+    if (g < ngroups) {
+        vg[g] = (int)g;
+        vk[g] = 0;          // the root
     }
-    int stack[kStack];
-    int sp = 0;
-    stack[sp++] = 0;
-    long long cnt = 0;
-    const long long base = w.j_off ? w.j_off[g] : 0;
-    // the fill pass writes exactly what the count pass counted; the bound
-    // turns any disagreement into a reported error instead of a stray write
-    const long long cap = w.j_off ? w.j_off[g + 1] - base : 0;
-    while (sp > 0) {
-        const int k = stack[--sp];
-        double d2 = 0.0;
-        const double4 cm = w.com[k];
-        for (int a = 0; a < 3; ++a) {
-            const double c = a == 0 ? cm.x : a == 1 ? cm.y : cm.z;
-            double d = 0.0;
-            if (c < blo[a]) d = __dsub_rn(blo[a], c);
-            else if (c > bhi[a]) d = __dsub_rn(c, bhi[a]);
-            d2 = __dadd_rn(d2, __dmul_rn(d, d));
-        }
-        const double side = ldexp(span, -(int)w.lev[k]);
-        const double side2 = __dmul_rn(side, side);
-        const double lim = __dmul_rn(w.theta2, d2);
-        const bool holds = w.first[k] <= i0 && i0 < w.first[k] + w.count[k];
-        if (!holds && side2 < lim) {
-            if (w.jlist) {
-                if (cnt >= cap) {
-                    report(w.status, kStatusBadIndex, 10);
-                    break;
-                }
-                w.jlist[base + cnt] = (int)(w.n + k);
-            }
-            ++cnt;
-        } else if (w.lev[k] == kLevels - 1 || w.count[k] <= w.nleaf) {
-            if (w.jlist && cnt + w.count[k] > cap) {
-                report(w.status, kStatusBadIndex, 10);
-                break;
-            }
-            for (int j = w.first[k]; j < w.first[k] + w.count[k]; ++j) {
-                if (w.jlist) w.jlist[base + cnt] = j;
-                ++cnt;
-            }
-        } else {
-            if (sp + w.childn[k] > kStack) {       // cannot happen: at most 8 per level
-                report(w.status, kStatusBadIndex, 9);
-                break;
-            }
-            for (int c = w.child0[k] + w.childn[k] - 1; c >= w.child0[k]; --c) stack[sp++] = c;
-        }
-    }
-    if (w.jcount) w.jcount[g] = (unsigned)cnt;
+    if (g == 0) *etot = 0ull;
 }
 
-__global__ void k_tree_widen(const unsigned *__restrict__ in, long long n, long long *__restrict__ out)
+// the FP32 bounds of one axis' squared distance, added into [lo2, hi2]
+__device__ __forceinline__ void axis_bounds(float c, float lo, float hi, float e, float &lo2,
+                                            float &hi2)
 {
-    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (k < n) out[k] = in[k];
+    const float d = c < lo ? lo - c : c > hi ? c - hi : 0.f;
+    const float dl = fmaxf(__fsub_rd(d, e), 0.f), dh = __fadd_ru(d, e);
+    lo2 = __fadd_rd(lo2, __fmul_rd(dl, dl));
+    hi2 = __fadd_ru(hi2, __fmul_ru(dh, dh));
 }
 
-// the pseudo-particles: (S / M, M), after the n particles of the j records
+__global__ void k_walk_test(LevelArgs a)
+{
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    unsigned long long e64 = 0;
+    if (q < a.nf) {
+        const long long v = a.o + q;
+        const int g = a.vg[v], k = a.vk[v];
+        const TreeNodeW nd = a.nodew[k];
+        const int i0 = a.g_i0[g];
+        const bool holds = nd.first <= i0 && i0 < nd.first + nd.count;
+        bool accept = false;
+        if (!holds) {
+            const WalkFilter &F = *a.filt;
+            int verdict = 0;                   // 1 accept, -1 not, 0 undecided
+            if (F.on) {
+                const float4 bl = a.gboxf[2 * (long long)g], bh = a.gboxf[2 * (long long)g + 1];
+                float lo2 = 0.f, hi2 = 0.f;
+                axis_bounds(nd.cx, bl.x, bh.x, F.e, lo2, hi2);
+                axis_bounds(nd.cy, bl.y, bh.y, F.e, lo2, hi2);
+                axis_bounds(nd.cz, bl.z, bh.z, F.e, lo2, hi2);
+                const float limlo = __fmul_rd(__fmul_rd(F.t2lo, lo2), 0x1.fffffcp-1f);
+                const float limhi = __fmul_ru(__fmul_ru(F.t2hi, hi2), 0x1.000002p+0f);
+                if (F.s2hi[a.L] < limlo) verdict = 1;
+                else if (F.s2lo[a.L] >= limhi) verdict = -1;
+            }
+            if (verdict == 0) {
+                // the FP64 test, rounded operation by operation
+                const double *bx = a.gbox + 6 * (long long)g;
+                const double4 cm = a.com[k];
+                double d2 = 0.0;
+                for (int x = 0; x < 3; ++x) {
+                    const double c = x == 0 ? cm.x : x == 1 ? cm.y : cm.z;
+                    const double lo = bx[x], hi = bx[3 + x];
+                    double d = 0.0;
+                    if (c < lo) d = __dsub_rn(lo, c);
+                    else if (c > hi) d = __dsub_rn(c, hi);
+                    d2 = __dadd_rn(d2, __dmul_rn(d, d));
+                }
+                verdict = F.s2[a.L] < __dmul_rn(a.theta2, d2) ? 1 : -1;
+            }
+            accept = verdict > 0;
+        }
+        unsigned e = 0, c = 0;
+        if (accept) {
+            e = 1;
+            a.vk[v] = ~k;
+        } else if (a.L == kLevels - 1 || nd.count <= a.nleaf) {
+            e = (unsigned)nd.count;
+        } else {
+            c = (unsigned)nd.childn;
+        }
+        a.ve[v] = e;
+        a.vc[q] = c;
+        e64 = e;
+        // the group's run of visits in this level
+        unsigned *sg = a.seg + (2 * (long long)a.L) * a.ngroups;
+        if (q == 0 || a.vg[v - 1] != g) sg[g] = (unsigned)v;
+        if (q + 1 == a.nf || a.vg[v + 1] != g) sg[a.ngroups + g] = (unsigned)(v + 1);
+    } else if (q == a.nf) {
+        a.vc[q] = 0u;
+    }
+    for (int s = 16; s; s >>= 1) e64 += __shfl_xor_sync(0xffffffffu, e64, s);
+    if ((threadIdx.x & 31) == 0 && e64) atomicAdd(a.etot, e64);
+}
+
+// the opened nodes' children, in order, after this level's frontier
+__global__ void k_walk_expand(const TreeNodeW *__restrict__ nodew, long long o, long long nf,
+                              const unsigned *__restrict__ vc, int *vg, int *vk)
+{
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= nf) return;
+    const unsigned c = vc[q + 1] - vc[q];
+    if (!c) return;
+    const long long v = o + q, dst = o + nf + vc[q];
+    const int g = vg[v], ch0 = nodew[vk[v]].child0;
+    for (unsigned t = 0; t < c; ++t) {
+        vg[dst + t] = g;
+        vk[dst + t] = ch0 + (int)t;
+    }
+}
+
+// entries per group: its visits' entries over all levels (ve scanned)
+__global__ void k_walk_count(long long ngroups, int nlev, const unsigned *__restrict__ seg,
+                             const unsigned *__restrict__ ve, unsigned *__restrict__ jcount)
+{
+    const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (g > ngroups) return;
+    unsigned s = 0;
+    if (g < ngroups)
+        for (int L = 0; L < nlev; ++L)
+            s += ve[seg[(2 * L + 1) * ngroups + g]] - ve[seg[(2 * L) * ngroups + g]];
+    jcount[g] = s;
+}
+
+// list offsets, and per group and level the shift from the scanned visit
+// order to the list position
+__global__ void k_walk_base(long long ngroups, int nlev, const unsigned *__restrict__ jscan,
+                            const unsigned *__restrict__ seg, const unsigned *__restrict__ ve,
+                            long long *__restrict__ j_off, long long *__restrict__ base)
+{
+    const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (g > ngroups) return;
+    long long off = jscan[g];
+    j_off[g] = off;
+    if (g == ngroups) return;
+    for (int L = 0; L < nlev; ++L) {
+        const unsigned s0 = ve[seg[(2 * L) * ngroups + g]], s1 = ve[seg[(2 * L + 1) * ngroups + g]];
+        base[L * ngroups + g] = off - (long long)s0;
+        off += s1 - s0;
+    }
+}
+
+// the entries of level L's visits [o, o + nf)
+__global__ void k_walk_fill(int L, long long o, long long nf, long long n, long long ngroups,
+                            const int *__restrict__ vg, const int *__restrict__ vk,
+                            const unsigned *__restrict__ ve, const long long *__restrict__ base,
+                            const long long *__restrict__ j_off, const TreeNodeW *__restrict__ nodew,
+                            int *__restrict__ jlist, int *status)
+{
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= nf) return;
+    const long long v = o + q;
+    const unsigned e = ve[v + 1] - ve[v];
+    if (!e) return;
+    const int g = vg[v], k = vk[v];
+    const long long dst = base[L * ngroups + g] + ve[v];
+    // the entries stay inside the group's list; anything else is reported
+    if (dst < j_off[g] || dst + e > j_off[g + 1] || (k < 0 && e != 1)) {
+        report(status, kStatusBadIndex, 10);
+        return;
+    }
+    if (k < 0) {
+        jlist[dst] = (int)(n + ~k);
+    } else {
+        const int f = nodew[k].first;
+        for (unsigned t = 0; t < e; ++t) jlist[dst + t] = f + (int)t;
+    }
+}
+
+// the pseudo-particles: (S / M, M), after the n particles of the j records;
+// and the walk's node records
 __global__ void k_tree_pseudo(const double *__restrict__ M, const double *__restrict__ S,
-                              long long nnodes, double4 *__restrict__ out)
+                              const int *__restrict__ first, const int *__restrict__ count,
+                              const int *__restrict__ child0, const int *__restrict__ childn,
+                              long long nnodes, double4 *__restrict__ out, TreeNodeW *__restrict__ nodew)
 {
     const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (k >= nnodes) return;
     const double m = M[k];
-    out[k] = make_double4(__ddiv_rn(S[3 * k], m), __ddiv_rn(S[3 * k + 1], m),
-                          __ddiv_rn(S[3 * k + 2], m), m);
+    const double4 c = make_double4(__ddiv_rn(S[3 * k], m), __ddiv_rn(S[3 * k + 1], m),
+                                   __ddiv_rn(S[3 * k + 2], m), m);
+    out[k] = c;
+    TreeNodeW w;
+    w.cx = __double2float_rn(c.x);
+    w.cy = __double2float_rn(c.y);
+    w.cz = __double2float_rn(c.z);
+    w.pad = 0.f;
+    w.first = first[k];
+    w.count = count[k];
+    w.child0 = child0[k];
+    w.childn = childn[k];
+    nodew[k] = w;
 }
 
 // items: the groups cut into chunks of at most Bi particles; pairs = sum ni nj
@@ -405,7 +577,14 @@ __global__ void k_tree_item_counts(const int *__restrict__ g_ni, long long ngrou
     c[g] = g < ngroups ? (unsigned)((g_ni[g] + Bi - 1) / Bi) : 0u;
 }
 
-unsigned blocks_of(long long n) { return (unsigned)((n + 255) / 256); }
+unsigned blocks_of(long long n) { return (unsigned)((std::max(n, 1LL) + 255) / 256); }
+
+// an exclusive scan in place, counted in the stage's launches (three kernels)
+cudaError_t scan(TreeScratch &t, unsigned *a, long long n, unsigned *sums, cudaStream_t st)
+{
+    if (n > 0) t.launches += 3;
+    return launch_excl_scan(a, n, sums, st);
+}
 
 }  // namespace
 
@@ -419,6 +598,7 @@ cudaError_t tree_stage_keys(const double4 *jrec, long long n, TreeScratch &t, So
     unsigned *ko = nullptr, *perm = nullptr;
     cudaError_t e = launch_radix_sort(sort.keys[0], sort.vals[0], n, 3 * kBits, sort, &ko, &perm, st);
     if (e != cudaSuccess) return e;
+    t.launches += 4 + (n > 0 ? (3 * kBits + 7) / 8 * 5 : 0) + 1 + kLevels;   // with the gather below
     cudaMemcpyAsync(t.key, ko, n * sizeof(unsigned), cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(t.perm, perm, n * sizeof(unsigned), cudaMemcpyDeviceToDevice, st);
     k_tree_gather<<<blocks_of(n), 256, 0, st>>>(jrec, t.perm, n, t.xs, t.xi0);
@@ -426,7 +606,7 @@ cudaError_t tree_stage_keys(const double4 *jrec, long long n, TreeScratch &t, So
     for (int L = 0; L < kLevels; ++L) {
         unsigned *sc = t.scan + (size_t)L * (n + 1);
         k_tree_flags<<<blocks_of(n + 1), 256, 0, st>>>(t.key, n, 3 * (kBits - L), sc);
-        if ((e = launch_excl_scan(sc, n + 1, sort.sums, st)) != cudaSuccess) return e;
+        if ((e = scan(t, sc, n + 1, sort.sums, st)) != cudaSuccess) return e;
         cudaMemcpyAsync(t.runs_dev + L, sc + n, sizeof(unsigned), cudaMemcpyDeviceToDevice, st);
     }
     return cudaGetLastError();
@@ -465,44 +645,84 @@ cudaError_t tree_stage_nodes(long long n, const long long *lev_off, int ncrit, T
                                                             t.count, ncrit, t.gat);
     }
     k_tree_group_flags<<<blocks_of(n + 1), 256, 0, st>>>(t.gat, n, t.gscan);
-    cudaError_t e = launch_excl_scan(t.gscan, n + 1, sort.sums, st);
+    t.launches += 4 * kLevels + 2;     // starts, nodes, moments, marks; flags and groups
+    cudaError_t e = scan(t, t.gscan, n + 1, sort.sums, st);
     if (e != cudaSuccess) return e;
-    k_tree_groups<<<blocks_of(n + 1), 256, 0, st>>>(t.gat, t.gscan, n, t.count, t.xs, t.g_i0, t.g_ni,
-                                                    t.gbox, t.i_off);
+    k_tree_groups<<<blocks_of(n + 1), 256, 0, st>>>(t.gat, t.gscan, n, t.count, t.g_i0, t.g_ni,
+                                                    t.i_off);
     cudaMemcpyAsync(t.runs_dev + kLevels, t.gscan + n, sizeof(unsigned), cudaMemcpyDeviceToDevice, st);
     return cudaGetLastError();
 }
 
-cudaError_t tree_stage_walk(long long n, long long ngroups, double theta, int nleaf, bool fill,
-                            TreeScratch &t, SortScratch &sort, int *status, cudaStream_t st)
+cudaError_t tree_walk_init(long long ngroups, double theta, TreeScratch &t, cudaStream_t st)
 {
-    WalkArgs w{};
-    w.n = n;
-    w.ngroups = ngroups;
-    w.g_i0 = t.g_i0;
-    w.g_ni = t.g_ni;
-    w.gbox = t.gbox;
-    w.first = t.first;
-    w.count = t.count;
-    w.child0 = t.child0;
-    w.childn = t.childn;
-    w.lev = t.lev;
-    w.com = t.jrec2 + n;       // the pseudo-particles, written before the walk
-    w.theta2 = theta * theta;
-    w.nleaf = nleaf;
-    w.status = status;
-    w.geo = t.geo;
-    cudaError_t e = cudaSuccess;
-    if (!fill) {
-        w.jcount = t.jcount;
-        k_tree_walk<<<blocks_of(ngroups), 256, 0, st>>>(w);
-        cudaMemsetAsync(t.jcount + ngroups, 0, sizeof(unsigned), st);
-        if ((e = launch_excl_scan(t.jcount, ngroups + 1, sort.sums, st)) != cudaSuccess) return e;
-        k_tree_widen<<<blocks_of(ngroups + 1), 256, 0, st>>>(t.jcount, ngroups + 1, t.j_off);
-    } else {
-        w.j_off = t.j_off;
-        w.jlist = t.jlist;
-        k_tree_walk<<<blocks_of(ngroups), 256, 0, st>>>(w);
+    k_tree_gbox<<<(unsigned)((ngroups + 7) / 8), 256, 0, st>>>(t.g_i0, t.g_ni, ngroups, t.xs, t.gbox,
+                                                               t.gboxf);
+    k_walk_filter<<<1, 32, 0, st>>>(t.geo, theta * theta, t.filt);
+    cudaMemsetAsync(t.seg, 0, 2 * (size_t)kLevels * ngroups * sizeof(unsigned), st);
+    k_walk_init<<<blocks_of(ngroups), 256, 0, st>>>(ngroups, t.vg, t.vk, t.etot);
+    t.launches += 3;
+    return cudaGetLastError();
+}
+
+cudaError_t tree_walk_level(long long n, long long ngroups, int L, long long o, long long nf,
+                            double theta, int nleaf, TreeScratch &t, cudaStream_t st)
+{
+    LevelArgs a{};
+    a.n = n;
+    a.ngroups = ngroups;
+    a.o = o;
+    a.nf = nf;
+    a.L = L;
+    a.g_i0 = t.g_i0;
+    a.gbox = t.gbox;
+    a.gboxf = t.gboxf;
+    a.nodew = t.nodew;
+    a.com = t.jrec2 + n;       // the pseudo-particles, written before the walk
+    a.filt = t.filt;
+    a.nleaf = nleaf;
+    a.vg = t.vg;
+    a.vk = t.vk;
+    a.ve = t.ve;
+    a.vc = t.vc;
+    a.seg = t.seg;
+    a.etot = t.etot;
+    a.theta2 = theta * theta;
+    k_walk_test<<<blocks_of(nf + 1), 256, 0, st>>>(a);
+    ++t.launches;
+    return scan(t, t.vc, nf + 1, t.vsums, st);
+}
+
+cudaError_t tree_walk_expand(long long o, long long nf, TreeScratch &t, cudaStream_t st)
+{
+    k_walk_expand<<<blocks_of(nf), 256, 0, st>>>(t.nodew, o, nf, t.vc, t.vg, t.vk);
+    ++t.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t tree_walk_lists(long long ngroups, const long long *lev_v, int nlev, TreeScratch &t,
+                            SortScratch &sort, cudaStream_t st)
+{
+    const long long nv = lev_v[nlev];
+    cudaMemsetAsync(t.ve + nv, 0, sizeof(unsigned), st);
+    cudaError_t e = scan(t, t.ve, nv + 1, t.vsums, st);
+    if (e != cudaSuccess) return e;
+    k_walk_count<<<blocks_of(ngroups + 1), 256, 0, st>>>(ngroups, nlev, t.seg, t.ve, t.jcount);
+    if ((e = scan(t, t.jcount, ngroups + 1, sort.sums, st)) != cudaSuccess) return e;
+    k_walk_base<<<blocks_of(ngroups + 1), 256, 0, st>>>(ngroups, nlev, t.jcount, t.seg, t.ve, t.j_off,
+                                                        t.base);
+    t.launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t tree_walk_fill(long long n, long long ngroups, const long long *lev_v, int nlev,
+                           TreeScratch &t, int *status, cudaStream_t st)
+{
+    for (int L = 0; L < nlev; ++L) {
+        const long long o = lev_v[L], nf = lev_v[L + 1] - o;
+        k_walk_fill<<<blocks_of(nf), 256, 0, st>>>(L, o, nf, n, ngroups, t.vg, t.vk, t.ve, t.base, t.j_off,
+                                                   t.nodew, t.jlist, status);
+        ++t.launches;
     }
     return cudaGetLastError();
 }
@@ -512,7 +732,9 @@ cudaError_t tree_stage_walk(long long n, long long ngroups, double theta, int nl
 cudaError_t tree_stage_jrec(long long n, long long nnodes, TreeScratch &t, cudaStream_t st)
 {
     cudaMemcpyAsync(t.jrec2, t.xs, n * sizeof(double4), cudaMemcpyDeviceToDevice, st);
-    k_tree_pseudo<<<blocks_of(nnodes), 256, 0, st>>>(t.M, t.S, nnodes, t.jrec2 + n);
+    k_tree_pseudo<<<blocks_of(nnodes), 256, 0, st>>>(t.M, t.S, t.first, t.count, t.child0, t.childn,
+                                                    nnodes, t.jrec2 + n, t.nodew);
+    ++t.launches;
     return cudaGetLastError();
 }
 
@@ -520,7 +742,8 @@ cudaError_t tree_stage_records(long long n, long long nnodes, long long ngroups,
                                TreeScratch &t, SortScratch &sort, cudaStream_t st)
 {
     k_tree_item_counts<<<blocks_of(ngroups + 1), 256, 0, st>>>(t.g_ni, ngroups, Bi, t.item_off);
-    cudaError_t e = launch_excl_scan(t.item_off, ngroups + 1, sort.sums, st);
+    t.launches += 2;      // with the items below
+    cudaError_t e = scan(t, t.item_off, ngroups + 1, sort.sums, st);
     if (e != cudaSuccess) return e;
     cudaMemsetAsync(t.pairs, 0, sizeof(unsigned long long), st);
     k_tree_items<<<blocks_of(ngroups), 256, 0, st>>>(t.g_i0, t.g_ni, t.item_off, t.j_off, ngroups, Bi,

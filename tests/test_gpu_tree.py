@@ -115,3 +115,32 @@ def test_tree_errors(pg):
         c.set_mode(pg.PG_NEWTON)
         c.set_tree(-1.0)                          # off: the all-pairs path again
         c.run()
+
+
+@pytest.mark.parametrize("rel", [-1e-12, 1e-12])
+def test_opening_at_the_threshold(pg, orc, rel):
+    # a probe and a 4-particle cluster whose level-1 node is accepted exactly
+    # when span / 2 < theta |c|; theta within 1e-12 of that value leaves the
+    # FP32 pre-test undecided, so the FP64 test takes the decision
+    h = 1.0 / 64.0
+    c = np.array([0.75, 0.75, 0.5])
+    x = np.array([[0.0, 0.0, 0.0], c + [h, h, 0], c + [-h, h, 0], c + [h, -h, 0], c + [-h, -h, 0]])
+    m = np.ones(5)
+    theta = (0.75 + h) / 2 / np.linalg.norm(c) * (1.0 + rel)
+    _, _, t, _ = gpu_tree(pg, x, m, 0.0, theta, 1, 1)
+    same_lists(t, orc.tree_build(x, m, theta, 1, 1))
+
+
+@pytest.mark.parametrize("scale", [1e-9, 1e6, 1e25])
+def test_scaled_sets(pg, orc, scale):
+    # tiny and huge coordinates: outside the FP32 pre-test's range every
+    # decision is FP64; inside it the bounds must still give the same lists
+    x, m = gen.plummer(8000, 86)
+    x = (x + np.array([0.3, -0.2, 0.1])) * scale
+    a, p, t, _ = gpu_tree(pg, x, m, 1e-3 * scale, 0.75, 64, 8)
+    same_lists(t, orc.tree_build(x, m, 0.75, 64, 8))
+    if scale > 1e18:
+        return          # the FP32 pair arithmetic overflows at r^2 ~ 1e50
+    ao, po = orc.tree_forces(x, m, 1e-3 * scale, 0.75, 64, 8)
+    assert_parity(rel_vec(a, ao), what="a")
+    assert_parity(rel_scalar(p, po), what="phi")

@@ -114,3 +114,20 @@ def test_opening_decision_at_the_threshold(orc):
         nodes = lst[lst >= len(x)] - len(x)
         assert len(nodes) == 1 and t["nlevel"][nodes[0]] == level
         assert t["nS"][nodes[0]] / t["nM"][nodes[0]] == pytest.approx(c, abs=1e-15)
+
+
+def test_lists_are_breadth_first(orc):
+    # every list runs level by level and in key order within a level: its
+    # node entries rise in (level, index); a list holds each particle or
+    # node once
+    x, m = gen.plummer(4000, 14)
+    n = len(x)
+    t = orc.tree_build(x, m, 0.6, 48, 6)
+    lev = t["nlevel"]
+    for g in range(0, len(t["g_i0"]), 5):
+        lst = t["jlist"][t["j_off"][g]:t["j_off"][g + 1]]
+        assert len(np.unique(lst)) == len(lst)
+        nodes = lst[lst >= n] - n
+        assert len(np.unique(lev[nodes])) >= 2
+        key = lev[nodes].astype(np.int64) * (1 << 40) + nodes
+        assert np.all(np.diff(key) > 0)
