@@ -70,10 +70,11 @@ _SIGS = {
     "orc_table_forces": (_I, [_LL, _P, _P, _LL, _P, _P, _I, _I, _D, _P, _P, _D, _D, _P, _P, _I]),
     "orc_table_potential": (_I, [_LL, _P, _P, _LL, _P, _P, _I, _I, _D, _P, _P, _D, _D, _P, _P, _I]),
     "orc_newton_epsi": (_I, [_LL, _P, _P, _P, _LL, _P, _P, _P, _P, _I]),
-    "orc_tree_build": (_P, [_LL, _P, _P, _D, _I, _I]),
+    "orc_tree_build": (_P, [_LL, _P, _P, _D, _I, _I, _I]),
     "orc_tree_free": (None, [_P]),
     "orc_tree_sizes": (None, [_P, _P]),
     "orc_tree_get": (None, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "orc_tree_get_nodes": (None, [_P, _P, _P, _P, _P]),
     "orc_tree_forces": (_I, [_P, _D, _P, _P]),
     "orc_shape_forces": (_I, [_LL, _P, _P, _LL, _P, _P, _I, _P, _D, _D, _D, _P, _P, _P, _I]),
     "orc_grad_newton": (_I, [_LL, _P, _P, _P, _D, _P, _P, _P, _I]),
@@ -362,20 +363,25 @@ def fd_table_v(x, m, w, E, F, r_cut, v, bidx, h=1e-6, box=0.0, nthreads_=None):
 
 
 # ---------------------------------------------------------------- tree
-def tree_build(x, m, theta, ncrit, nleaf):
-    """The grouped Barnes-Hut tree of Section 5.1 (monopoles). Returns a dict
-    with the key order ``perm``, the groups (``g_i0``, ``g_ni``, ``g_node``,
-    in key order), the lists (``j_off``, ``jlist``: k < n is sorted particle
-    k, n + t is node t), the node moments (``nM``, ``nS``) and levels."""
+def tree_build(x, m, theta, ncrit, nleaf, quadrupole=False):
+    """The grouped Barnes-Hut tree of Section 5.1. Returns a dict with the
+    key order ``perm``, the groups (``g_i0``, ``g_ni``, ``g_node``, in key
+    order), the lists (``j_off``, ``jlist``: k < n is sorted particle k,
+    n + P t + q is pseudo-particle q of node t), per node the moments
+    (``nM``, ``nS``, the second moment ``nT`` as xx, xy, xz, yy, yz, zz),
+    ``nlevel``, ``nfirst``, ``ncount``, and the pseudo-particles
+    (``pseudo``: x, y, z, m; ``npseudo`` = P, 1 for monopoles, 3 with
+    quadrupoles)."""
     x = _f64(x, (-1, 3)); m = _f64(m)
     n = len(x)
-    h = lib().orc_tree_build(n, _ptr(x), _ptr(m), float(theta), int(ncrit), int(nleaf))
+    h = lib().orc_tree_build(n, _ptr(x), _ptr(m), float(theta), int(ncrit), int(nleaf),
+                             int(bool(quadrupole)))
     if not h:
         raise ValueError("tree build failed")
     try:
-        sz = np.zeros(4, dtype=np.int64)
+        sz = np.zeros(5, dtype=np.int64)
         lib().orc_tree_sizes(h, _ptr(sz))
-        n, nnodes, ng, nlist = (int(v) for v in sz)
+        n, nnodes, ng, nlist, npseudo = (int(v) for v in sz)
         out = dict(perm=np.empty(n, np.int64), g_i0=np.empty(ng, np.int64),
                    g_ni=np.empty(ng, np.int64), g_node=np.empty(ng, np.int64),
                    j_off=np.empty(ng + 1, np.int64), jlist=np.empty(max(nlist, 1), np.int64),
@@ -384,17 +390,22 @@ def tree_build(x, m, theta, ncrit, nleaf):
         lib().orc_tree_get(h, *(_ptr(out[k]) for k in ("perm", "g_i0", "g_ni", "g_node", "j_off",
                                                       "jlist", "nM", "nS", "nlevel")))
         out["jlist"] = out["jlist"][:nlist]
+        out.update(nfirst=np.empty(nnodes, np.int64), ncount=np.empty(nnodes, np.int64),
+                   nT=np.empty((nnodes, 6)), pseudo=np.empty((nnodes * npseudo, 4)),
+                   npseudo=npseudo)
+        lib().orc_tree_get_nodes(h, *(_ptr(out[k]) for k in ("nfirst", "ncount", "nT", "pseudo")))
         return out
     finally:
         lib().orc_tree_free(h)
 
 
-def tree_forces(x, m, eps, theta, ncrit, nleaf):
+def tree_forces(x, m, eps, theta, ncrit, nleaf, quadrupole=False):
     """Forces and potentials of all particles (input order) from the grouped
     tree's lists, each particle's own entry left out."""
     x = _f64(x, (-1, 3)); m = _f64(m)
     n = len(x)
-    h = lib().orc_tree_build(n, _ptr(x), _ptr(m), float(theta), int(ncrit), int(nleaf))
+    h = lib().orc_tree_build(n, _ptr(x), _ptr(m), float(theta), int(ncrit), int(nleaf),
+                             int(bool(quadrupole)))
     if not h:
         raise ValueError("tree build failed")
     try:

@@ -33,8 +33,21 @@
  *    decision appends its entries (the node, or a leaf's particles in key
  *    order). The paper fixes the list as a set; the order only changes the
  *    rounding of the sums;
- *  - list entries: k < n is sorted particle k; n + t is node t, with nodes
- *    numbered level by level and in key order within a level.
+ *  - list entries: k < n is sorted particle k; n + P t + q is pseudo-particle
+ *    q of node t, with nodes numbered level by level and in key order within
+ *    a level and P pseudo-particles per node;
+ *  - monopole (P = 1): one pseudo-particle of mass M at the centre of mass c;
+ *  - quadrupole (P = 3; the pseudo-particle multipole method of Kawai and
+ *    Makino that the paper cites for its quadrupole runs): with
+ *    T = sum m (x - c)(x - c)^T over the node's particles, its eigenvalues
+ *    l1 >= l2 >= l3 and unit eigenvectors e1, e2, a = sqrt(2 (l1 - l3) / M)
+ *    and b = sqrt(2 (l2 - l3) / M), three pseudo-particles of mass M / 3 at
+ *    c + a e1 and c - a/2 e1 +- (sqrt 3 / 2) b e2. They carry the node's
+ *    mass, a zero dipole about c and T - l3 I, whose trace-free part is
+ *    T's: the potential is the node's through the quadrupole term. e1's
+ *    sign makes its largest-magnitude component positive (the lower axis on
+ *    a tie); e2's sign does not change the set. With l1 = l2 > l3 exactly
+ *    the angle of the triangle in its plane is the eigen-solver's choice.
  * Every FP64 operation is written out (separate multiply and add), so that
  * an implementation that rounds each operation the same way takes the same
  * decisions; the file is compiled without contraction. */
@@ -53,6 +66,10 @@ typedef struct {
     long long *nfirst, *ncount, *nchild0, *nchildn;
     int *nlevel;
     double *nM, *nS;        /* mass, first moment (3 per node) */
+    double *nT;             /* second moment about the centre of mass (6 per node:
+                             * xx, xy, xz, yy, yz, zz) */
+    int npseudo;            /* pseudo-particles per node: 1 or 3 */
+    double *pseudo;         /* 4 per pseudo-particle: x, y, z, m */
     double span, lo[3];
     long long *g_node, *g_i0, *g_ni;      /* groups */
     long long *j_off, *jlist;
@@ -79,7 +96,7 @@ void orc_tree_free(orc_tree_t *t)
     if (!t) return;
     free(t->perm); free(t->key); free(t->xs); free(t->ms);
     free(t->nfirst); free(t->ncount); free(t->nchild0); free(t->nchildn); free(t->nlevel);
-    free(t->nM); free(t->nS);
+    free(t->nM); free(t->nS); free(t->nT); free(t->pseudo);
     free(t->g_node); free(t->g_i0); free(t->g_ni); free(t->j_off); free(t->jlist);
     free(t);
 }
@@ -101,6 +118,107 @@ static double box_d2(const double c[3], const double lo[3], const double hi[3])
 static int is_leaf(const orc_tree_t *t, long long k, int nleaf)
 {
     return t->nlevel[k] == TREE_LEVELS - 1 || t->ncount[k] <= nleaf;
+}
+
+/* eigen-decomposition of a symmetric 3x3 matrix by cyclic Jacobi rotations
+ * (each rotation zeroes one off-diagonal element; sweeps repeat until the
+ * off-diagonal part is negligible): A = V diag(lam) V^T, V's columns the
+ * eigenvectors. A is overwritten. */
+static void sym3_eig(double A[3][3], double V[3][3], double lam[3])
+{
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) V[a][b] = a == b ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 50; ++sweep) {
+        double off = fabs(A[0][1]) + fabs(A[0][2]) + fabs(A[1][2]);
+        double diag = fabs(A[0][0]) + fabs(A[1][1]) + fabs(A[2][2]);
+        if (off == 0.0 || off <= 1e-300 || off <= 1e-18 * diag) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                if (A[p][q] == 0.0) continue;
+                /* rotation angle phi with tan(2 phi) = 2 A_pq / (A_qq - A_pp);
+                 * t = tan(phi) is the smaller root of t^2 + 2 h t - 1 = 0 */
+                double h = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+                double tt = (h >= 0.0 ? 1.0 : -1.0) / (fabs(h) + sqrt(h * h + 1.0));
+                double c = 1.0 / sqrt(tt * tt + 1.0), sn = tt * c;
+                /* A <- J^T A J with J the rotation in the (p, q) plane */
+                for (int k = 0; k < 3; ++k) {
+                    double akp = A[k][p], akq = A[k][q];
+                    A[k][p] = c * akp - sn * akq;
+                    A[k][q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    double apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = c * apk - sn * aqk;
+                    A[q][k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = c * vkp - sn * vkq;
+                    V[k][q] = sn * vkp + c * vkq;
+                }
+            }
+    }
+    for (int a = 0; a < 3; ++a) lam[a] = A[a][a];
+}
+
+/* second moments about each node's centre of mass, from the definition
+ * (the node's particles), and the pseudo-particles */
+static int make_pseudo(orc_tree_t *t)
+{
+    long long nn = t->nnodes;
+    t->nT = (double *)calloc((size_t)(6 * nn), sizeof(double));
+    t->pseudo = (double *)calloc((size_t)(4 * t->npseudo * nn), sizeof(double));
+    if (!t->nT || !t->pseudo) return -1;
+    for (long long k = 0; k < nn; ++k) {
+        double M = t->nM[k], c[3];
+        for (int a = 0; a < 3; ++a) c[a] = t->nS[3 * k + a] / M;
+        double T[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (long long i = t->nfirst[k]; i < t->nfirst[k] + t->ncount[k]; ++i) {
+            double y[3];
+            for (int a = 0; a < 3; ++a) y[a] = t->xs[3 * i + a] - c[a];
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) T[a][b] += t->ms[i] * y[a] * y[b];
+        }
+        double *nt = t->nT + 6 * k;
+        nt[0] = T[0][0]; nt[1] = T[0][1]; nt[2] = T[0][2];
+        nt[3] = T[1][1]; nt[4] = T[1][2]; nt[5] = T[2][2];
+        double *ps = t->pseudo + 4 * t->npseudo * k;
+        if (t->npseudo == 1) {
+            for (int a = 0; a < 3; ++a) ps[a] = c[a];
+            ps[3] = M;
+            continue;
+        }
+        double A[3][3], V[3][3], lam[3];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) A[a][b] = T[a][b];
+        sym3_eig(A, V, lam);
+        /* order: i1 the largest eigenvalue, i3 the smallest, i2 the other */
+        int i1 = 0, i3 = 0;
+        for (int e = 1; e < 3; ++e) {
+            if (lam[e] > lam[i1]) i1 = e;
+            if (lam[e] < lam[i3]) i3 = e;
+        }
+        if (i1 == i3) i3 = (i1 + 1) % 3;      /* all equal */
+        int i2 = 3 - i1 - i3;
+        double e1[3], e2[3];
+        for (int a = 0; a < 3; ++a) { e1[a] = V[a][i1]; e2[a] = V[a][i2]; }
+        int big = 0;
+        for (int a = 1; a < 3; ++a)
+            if (fabs(e1[a]) > fabs(e1[big])) big = a;
+        if (e1[big] < 0.0)
+            for (int a = 0; a < 3; ++a) e1[a] = -e1[a];
+        double d13 = lam[i1] - lam[i3], d23 = lam[i2] - lam[i3];
+        double al = sqrt(2.0 * (d13 > 0.0 ? d13 : 0.0) / M);
+        double be = sqrt(2.0 * (d23 > 0.0 ? d23 : 0.0) / M);
+        double h = sqrt(3.0) / 2.0;
+        for (int a = 0; a < 3; ++a) {
+            ps[a] = c[a] + al * e1[a];
+            ps[4 + a] = c[a] - 0.5 * al * e1[a] + h * be * e2[a];
+            ps[8 + a] = c[a] - 0.5 * al * e1[a] - h * be * e2[a];
+        }
+        ps[3] = ps[7] = ps[11] = M / 3.0;
+    }
+    return 0;
 }
 
 /* the walk of group g, breadth first through a FIFO queue (children are
@@ -131,8 +249,10 @@ static long long walk(const orc_tree_t *t, long long g, double theta2, int nleaf
         double lim = theta2 * d2;
         int holds = t->nfirst[k] <= i0 && i0 < t->nfirst[k] + t->ncount[k];
         if (!holds && side2 < lim) {
-            if (out) out[cnt] = t->n + k;
-            ++cnt;
+            for (int q = 0; q < t->npseudo; ++q) {
+                if (out) out[cnt] = t->n + t->npseudo * k + q;
+                ++cnt;
+            }
         } else if (is_leaf(t, k, nleaf)) {
             for (long long j = t->nfirst[k]; j < t->nfirst[k] + t->ncount[k]; ++j) {
                 if (out) out[cnt] = j;
@@ -147,12 +267,13 @@ static long long walk(const orc_tree_t *t, long long g, double theta2, int nleaf
 }
 
 orc_tree_t *orc_tree_build(long long n, const double *x, const double *m, double theta,
-                           int ncrit, int nleaf)
+                           int ncrit, int nleaf, int quadrupole)
 {
     if (n <= 0 || !(theta >= 0.0) || ncrit < 1 || nleaf < 1) return NULL;
     orc_tree_t *t = (orc_tree_t *)calloc(1, sizeof *t);
     if (!t) return NULL;
     t->n = n;
+    t->npseudo = quadrupole ? 3 : 1;
     /* root cube */
     double hi[3];
     for (int a = 0; a < 3; ++a) { t->lo[a] = x[a]; hi[a] = x[a]; }
@@ -264,6 +385,7 @@ orc_tree_t *orc_tree_build(long long n, const double *x, const double *m, double
             t->nM[k] = M;
             for (int a = 0; a < 3; ++a) t->nS[3 * k + a] = S[a];
         }
+    if (make_pseudo(t)) { orc_tree_free(t); return NULL; }
     /* groups, in particle order */
     long long ng = 0;
     t->g_node = (long long *)malloc(sizeof(long long) * (size_t)n);
@@ -316,12 +438,24 @@ orc_tree_t *orc_tree_build(long long n, const double *x, const double *m, double
     return t;
 }
 
-void orc_tree_sizes(const orc_tree_t *t, long long *out4)
+void orc_tree_sizes(const orc_tree_t *t, long long *out5)
 {
-    out4[0] = t->n;
-    out4[1] = t->nnodes;
-    out4[2] = t->ngroups;
-    out4[3] = t->nlist;
+    out5[0] = t->n;
+    out5[1] = t->nnodes;
+    out5[2] = t->ngroups;
+    out5[3] = t->nlist;
+    out5[4] = t->npseudo;
+}
+
+/* copies out per node: first particle and count [nnodes], second moment
+ * [6 nnodes], and the pseudo-particles [4 npseudo nnodes] */
+void orc_tree_get_nodes(const orc_tree_t *t, long long *nfirst, long long *ncount, double *nT,
+                        double *pseudo)
+{
+    memcpy(nfirst, t->nfirst, sizeof(long long) * (size_t)t->nnodes);
+    memcpy(ncount, t->ncount, sizeof(long long) * (size_t)t->nnodes);
+    memcpy(nT, t->nT, sizeof(double) * 6 * (size_t)t->nnodes);
+    memcpy(pseudo, t->pseudo, sizeof(double) * 4 * (size_t)(t->npseudo * t->nnodes));
 }
 
 /* copies out: perm[n], group i0/ni/node [ngroups], j_off[ngroups + 1],
@@ -342,8 +476,8 @@ void orc_tree_get(const orc_tree_t *t, long long *perm, long long *g_i0, long lo
 }
 
 /* Eq. (1) over each group's list, in input order: a particle's own entry
- * (d = 0) is left out; a pseudo-particle sits at its node's centre of mass
- * with the node's mass. FP64, list order, Neumaier-compensated. */
+ * (d = 0) is left out; pseudo-particles as the build placed them. FP64,
+ * list order, Neumaier-compensated. */
 int orc_tree_forces(const orc_tree_t *t, double eps, double *acc, double *pot)
 {
     if (!(eps >= 0.0)) return -1;
@@ -359,9 +493,9 @@ int orc_tree_forces(const orc_tree_t *t, double eps, double *acc, double *pot)
                     for (int a = 0; a < 3; ++a) xj[a] = t->xs[3 * j + a];
                     mj = t->ms[j];
                 } else {
-                    long long k = j - t->n;
-                    for (int a = 0; a < 3; ++a) xj[a] = t->nS[3 * k + a] / t->nM[k];
-                    mj = t->nM[k];
+                    const double *ps = t->pseudo + 4 * (j - t->n);
+                    for (int a = 0; a < 3; ++a) xj[a] = ps[a];
+                    mj = ps[3];
                 }
                 double d[3], r2 = e2;
                 for (int a = 0; a < 3; ++a) {

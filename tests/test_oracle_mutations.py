@@ -66,7 +66,17 @@ TREE_MUTATIONS = {
     "tree leaf drops its last particle": (
         "for (long long j = t->nfirst[k]; j < t->nfirst[k] + t->ncount[k]; ++j) {\n                if (out)",
         "for (long long j = t->nfirst[k]; j < t->nfirst[k] + t->ncount[k] - 1; ++j) {\n                if (out)"),
-    "tree pseudo-particle mass halved": ("mj = t->nM[k];", "mj = 0.5 * t->nM[k];"),
+    "tree pseudo-particle mass halved": ("            ps[3] = M;\n", "            ps[3] = 0.5 * M;\n"),
+    "quadrupole spread without the factor 2": ("double al = sqrt(2.0 * (d13 > 0.0 ? d13 : 0.0) / M);",
+                                               "double al = sqrt((d13 > 0.0 ? d13 : 0.0) / M);"),
+    "quadrupole pseudo-particle mass M / 4": ("ps[3] = ps[7] = ps[11] = M / 3.0;",
+                                              "ps[3] = ps[7] = ps[11] = M / 4.0;"),
+    "quadrupole triangle half-height": ("double h = sqrt(3.0) / 2.0;", "double h = 0.5;"),
+    "quadrupole spread from the middle eigenvalue": ("d23 = lam[i2] - lam[i3];", "d23 = lam[i1] - lam[i3];"),
+    "quadrupole moments about the origin": ("y[a] = t->xs[3 * i + a] - c[a];", "y[a] = t->xs[3 * i + a];"),
+    "quadrupole rotation sign": ("A[k][p] = c * akp - sn * akq;", "A[k][p] = c * akp + sn * akq;"),
+    "quadrupole eigenvectors transposed": ("e1[a] = V[a][i1]; e2[a] = V[a][i2];", "e1[a] = V[i1][a]; e2[a] = V[i2][a];"),
+    "quadrupole sign convention dropped": ("        if (e1[big] < 0.0)\n", "        if (0)\n"),
     "tree finest-level moment skips mass": ("            M = M + t->ms[i];\n", "\n"),
     "tree own particle kept": ("if (j == i) continue;\n                double xj[3], mj;",
                                "double xj[3], mj;"),

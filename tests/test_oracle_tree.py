@@ -131,3 +131,94 @@ def test_lists_are_breadth_first(orc):
         assert len(np.unique(lev[nodes])) >= 2
         key = lev[nodes].astype(np.int64) * (1 << 40) + nodes
         assert np.all(np.diff(key) > 0)
+
+
+def test_quadrupole_pseudo_particles_carry_the_moments(orc):
+    # each node's three pseudo-particles have its mass, a zero dipole about
+    # its centre of mass and second moment T - l3 I (T and its smallest
+    # eigenvalue l3 computed here from the node's particles), so the same
+    # trace-free quadrupole; the first lies along the principal axis of the
+    # largest eigenvalue, on the side where that axis' largest component is
+    # positive; a one-particle node's three sit on the particle
+    x, m = gen.clustered_box(2500, 15, nclump=8, sigma=0.03, periodic=False)
+    m = m * np.random.default_rng(5).uniform(0.5, 2.0, len(m))
+    t = orc.tree_build(x, m, 0.7, 40, 6, quadrupole=True)
+    assert t["npseudo"] == 3
+    xs, ms = x[t["perm"]], m[t["perm"]]
+    ps = t["pseudo"].reshape(-1, 3, 4)
+    nn = len(t["nM"])
+    singles = spread = 0
+    for k in range(0, nn, 3):
+        f, c_ = t["nfirst"][k], t["ncount"][k]
+        y, w = xs[f:f + c_], ms[f:f + c_]
+        M = w.sum()
+        com = (w[:, None] * y).sum(axis=0) / M
+        T = np.einsum("i,ia,ib->ab", w, y - com, y - com)
+        scale = max(np.trace(T), 1e-300)
+        assert np.allclose(t["nT"][k], T[[0, 0, 0, 1, 1, 2], [0, 1, 2, 1, 2, 2]], rtol=1e-9,
+                           atol=1e-12 * scale)
+        lam, V = np.linalg.eigh(T)
+        p, pm = ps[k, :, :3], ps[k, :, 3]
+        # positions round to the coordinates' ulp: spreads below it are lost
+        ulp = 4.0 * np.spacing(np.abs(com).max())
+        assert pm.sum() == pytest.approx(M, rel=1e-14) and np.all(pm == pm[0])
+        assert np.allclose((pm[:, None] * (p - com)).sum(axis=0), 0.0,
+                           atol=1e-12 * np.sqrt(scale * M) + M * ulp)
+        Tp = np.einsum("q,qa,qb->ab", pm, p - com, p - com)
+        assert np.allclose(Tp, T - lam[0] * np.eye(3), rtol=1e-9,
+                           atol=1e-10 * scale + M * ulp * (ulp + np.sqrt(scale / M)))
+        alpha = np.sqrt(2.0 * max(lam[2] - lam[0], 0.0) / M)
+        if lam[2] - lam[1] > 1e-6 * scale and lam[2] - lam[0] > 1e-3 * scale and alpha > 1e6 * ulp:
+            spread += 1
+            d0 = p[0] - com
+            e1 = V[:, 2] * np.sign(V[np.argmax(np.abs(V[:, 2])), 2])
+            assert np.allclose(d0 / np.linalg.norm(d0), e1, atol=1e-8)
+        if c_ == 1:
+            singles += 1
+            assert np.allclose(p, y[0], rtol=0, atol=1e-15 * np.abs(y[0]).max())
+    assert singles > 0 and spread > 100
+
+
+def _far_error(pos, mass, src, msrc, d, dirs):
+    pts = d * dirs
+    exact = -np.sum(msrc[None, :] / np.linalg.norm(pts[:, None, :] - src[None], axis=2), axis=1)
+    approx = -np.sum(mass[None, :] / np.linalg.norm(pts[:, None, :] - pos[None], axis=2), axis=1)
+    return np.mean(np.abs(approx - exact))
+
+
+def test_quadrupole_far_field_order(orc):
+    # a lopsided cluster of size ~0.1 seen from distance d: the potential
+    # error of the monopole falls as d^-3 (the quadrupole term is missing),
+    # that of the four pseudo-particles as d^-4 (the octupole term)
+    rng = np.random.default_rng(16)
+    src = rng.normal(size=(300, 3)) * [0.05, 0.03, 0.02] + [0.02, 0.0, 0.0] * rng.random((300, 1))
+    msrc = rng.uniform(0.5, 1.5, 300)
+    dirs = rng.normal(size=(128, 3))
+    dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+    errs = {}
+    for quad in (False, True):
+        t = orc.tree_build(src, msrc, 0.5, 1000, 1000, quadrupole=quad)
+        root = t["pseudo"][:t["npseudo"]]       # node 0 holds every particle
+        c = (msrc[:, None] * src).sum(axis=0) / msrc.sum()
+        assert np.allclose(root[:, :3].mean(axis=0), c, atol=1e-15)
+        errs[quad] = [_far_error(root[:, :3] - c, root[:, 3], src - c, msrc, d, dirs)
+                      for d in (4.0, 8.0)]
+    mono, quad = errs[False], errs[True]
+    assert 6.0 < mono[0] / mono[1] < 10.5           # 2^3
+    assert 12.0 < quad[0] / quad[1] < 21.0          # 2^4
+    assert quad[0] < 0.1 * mono[0]
+
+
+def test_quadrupole_tree_is_more_accurate(orc):
+    # against the direct sum, the quadrupole pseudo-particles cut the force
+    # error of the monopole tree several fold at the same lists' nodes
+    x, m = gen.plummer(3000, 17)
+    ad, pd = orc.newton_allpairs(x, m, 0.01)
+    for theta, gain in ((0.5, 0.35), (0.75, 0.55)):
+        med = {}
+        for quad in (False, True):
+            a, p = orc.tree_forces(x, m, 0.01, theta, 64, 8, quadrupole=quad)
+            med[quad] = np.median(np.linalg.norm(a - ad, axis=1) / np.linalg.norm(ad, axis=1))
+        assert med[True] < gain * med[False]
+    a, p = orc.tree_forces(x, m, 0.01, 0.0, 64, 8, quadrupole=True)     # theta 0: direct
+    assert np.allclose(a, ad, rtol=1e-12, atol=1e-14 * np.abs(ad).max())
