@@ -137,9 +137,10 @@ int pg_get_table(pg_ctx *ctx, float *G0, float *G1, long long n);
  * particle's own pair is left out. Construction and opening rule:
  *   - nodes are the runs of equal 3L-bit prefix of a 30-bit Morton key
  *     (10 bits per axis over the bounding cube), levels 0 .. 10;
- *   - a node holding none of the group's particles is accepted as one
- *     pseudo-particle (its mass at its centre of mass) if
- *     side^2 < theta^2 d^2, d from its centre of mass to the group's box;
+ *   - a node holding none of the group's particles is accepted if
+ *     side^2 < theta^2 d^2, d from its centre of mass to the group's box,
+ *     and enters the list as its pseudo-particles (see
+ *     pg_set_tree_quadrupole);
  *   - otherwise a leaf (at most nleaf particles, or level 10) gives its
  *     particles and other nodes are opened.
  * theta = 0 reproduces the direct sum. Needs PG_NEWTON, the self mode with
@@ -150,13 +151,33 @@ int pg_get_table(pg_ctx *ctx, float *G0, float *G1, long long n);
  * nleaf < 1. */
 int pg_set_tree(pg_ctx *ctx, double theta, int ncrit, int nleaf);
 
-/* The last tree run's structure, for inspection: sizes[5] = {n, nodes,
- * groups, list entries, work items}; then (each may be NULL) perm[n] (key
- * order -> input index), the groups' first particle and size in key order
- * [groups], j_off[groups + 1] and jlist[list entries] (k < n: particle k in
- * key order; n + t: node t, nodes numbered level by level). Syncs. */
+/* The pseudo-particles of an accepted tree node (the paper's monopole and
+ * quadrupole tree runs, Section 5.1). on = 0 (the default): one, the node's
+ * mass at its centre of mass c. on != 0: the pseudo-particle multipole
+ * method of Kawai and Makino at quadrupole order, three of mass M / 3 at
+ * c + a e1 and c - a/2 e1 +- (sqrt 3 / 2) b e2, where e1, e2 are the unit
+ * principal axes of the node's second moment T = sum m (x - c)(x - c)^T
+ * with its two largest eigenvalues l1 >= l2 (l3 the smallest; e1's
+ * largest component positive), a = sqrt(2 (l1 - l3) / M) and
+ * b = sqrt(2 (l2 - l3) / M): they carry the node's mass, a zero dipole and
+ * the trace-free part of T. Moments in FP64; the opening test is the same.
+ * Takes effect at the next run. */
+int pg_set_tree_quadrupole(pg_ctx *ctx, int on);
+
+/* The last tree run's structure, for inspection: sizes[6] = {n, nodes,
+ * groups, list entries, work items, P pseudo-particles per node}; then
+ * (each may be NULL) perm[n] (key order -> input index), the groups' first
+ * particle and size in key order [groups], j_off[groups + 1] and
+ * jlist[list entries] (k < n: particle k in key order; n + P t + q:
+ * pseudo-particle q of node t, nodes numbered level by level; a list runs
+ * breadth first, level by level and in key order within a level). Syncs. */
 int pg_get_tree(pg_ctx *ctx, long long *sizes, long long *perm, long long *g_i0,
                 long long *g_ni, long long *j_off, long long *jlist);
+
+/* The last tree run's pseudo-particles: rec[4 P nodes] = x, y, z, m (FP64)
+ * of pseudo-particle q of node t at 4 (P t + q), host memory the caller
+ * owns. Syncs. */
+int pg_get_tree_pseudo(pg_ctx *ctx, double *rec);
 
 /* Potential in PG_TABLE mode, an extension: the tabulated kernel of Section
  * 3.4.2 stores accelerations only. psi(r, user) is tabulated on the force

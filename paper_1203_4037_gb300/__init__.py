@@ -70,6 +70,8 @@ SIGNATURES = {
     "pg_set_table_pot": (_I, [_P, GFUNC, _P]),
     "pg_set_table_pot_values": (_I, [_P, _P, _LL]),
     "pg_set_tree": (_I, [_P, _D, _I, _I]),
+    "pg_set_tree_quadrupole": (_I, [_P, _I]),
+    "pg_get_tree_pseudo": (_I, [_P, _P]),
     "pg_get_tree": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "pg_set_timing": (_I, [_P, _I]),
     "pg_kernel_time": (_I, [_P, C.POINTER(_D)]),
@@ -188,12 +190,16 @@ def pg_set_tree(ctx, theta, ncrit=64, nleaf=8):
     return _check(ctx, lib().pg_set_tree(ctx, float(theta), int(ncrit), int(nleaf)))
 
 
+def pg_set_tree_quadrupole(ctx, on):
+    return _check(ctx, lib().pg_set_tree_quadrupole(ctx, int(bool(on))))
+
+
 def pg_get_tree(ctx):
     """The last tree run: dict of sizes, perm, g_i0, g_ni, j_off, jlist."""
-    sizes = np.zeros(5, dtype=np.int64)
+    sizes = np.zeros(6, dtype=np.int64)
     _check(ctx, lib().pg_get_tree(ctx, _ptr(sizes), None, None, None, None, None))
-    n, nnodes, ng, nl, nitems = (int(v) for v in sizes)
-    out = dict(n=n, nnodes=nnodes, ngroups=ng, nlist=nl, nitems=nitems,
+    n, nnodes, ng, nl, nitems, npseudo = (int(v) for v in sizes)
+    out = dict(n=n, nnodes=nnodes, ngroups=ng, nlist=nl, nitems=nitems, npseudo=npseudo,
                perm=np.empty(n, np.int64), g_i0=np.empty(ng, np.int64),
                g_ni=np.empty(ng, np.int64), j_off=np.empty(ng + 1, np.int64),
                jlist=np.empty(max(nl, 1), np.int64))
@@ -201,6 +207,13 @@ def pg_get_tree(ctx):
                                   _ptr(out["g_ni"]), _ptr(out["j_off"]), _ptr(out["jlist"])))
     out["jlist"] = out["jlist"][:nl]
     return out
+
+
+def pg_get_tree_pseudo(ctx, nnodes, npseudo):
+    """The last tree run's pseudo-particles, (nnodes * npseudo, 4): x, y, z, m."""
+    out = np.empty((max(nnodes * npseudo, 1), 4))
+    _check(ctx, lib().pg_get_tree_pseudo(ctx, _ptr(out)))
+    return out[:nnodes * npseudo]
 
 
 def pg_set_eps_i(ctx, eps):
@@ -412,11 +425,14 @@ class Context:
     def set_eps_i(self, eps):
         pg_set_eps_i(self.h, eps)
 
-    def set_tree(self, theta, ncrit=64, nleaf=8):
+    def set_tree(self, theta, ncrit=64, nleaf=8, quadrupole=False):
         pg_set_tree(self.h, theta, ncrit, nleaf)
+        pg_set_tree_quadrupole(self.h, quadrupole)
 
     def get_tree(self):
-        return pg_get_tree(self.h)
+        t = pg_get_tree(self.h)
+        t["pseudo"] = pg_get_tree_pseudo(self.h, t["nnodes"], t["npseudo"])
+        return t
 
     def set_eps_i_dev(self, eps):
         _require_dev(eps)

@@ -84,17 +84,19 @@ struct pg_ctx {
     bool have_groups = false;
 
     // tree front end (theta >= 0: on); device buffers by role, sizes of the
-    // last build {n, nodes, groups, list entries, items}
+    // last build {n, nodes, groups, list entries, items, pseudo-particles per
+    // node}
     bool tree_on = false;
+    bool tree_quad = false;
     double tree_theta = 0.75;
     int tree_ncrit = 64, tree_nleaf = 8;
     enum { TB_BBOX, TB_GEO, TB_KEY, TB_PERM, TB_XS, TB_XI0, TB_SCAN, TB_RUNS, TB_FIRST, TB_COUNT,
            TB_CHILD0, TB_CHILDN, TB_LEV, TB_M, TB_S, TB_GAT, TB_GSCAN, TB_GI0, TB_GNI, TB_GBOX,
            TB_IOFF, TB_JCOUNT, TB_JOFF, TB_JLIST, TB_JREC2, TB_ITEMOFF, TB_ITEMS, TB_PAIRS,
            TB_VG, TB_VK, TB_VE, TB_VC, TB_VSUMS, TB_SEG, TB_BASE, TB_ETOT, TB_GBOXF, TB_NODEW,
-           TB_FILT, TB_N };
+           TB_FILT, TB_COM, TB_T, TB_N };
     DevBuf tb[TB_N];
-    long long tree_sizes[5] = {0, 0, 0, 0, 0};
+    long long tree_sizes[6] = {0, 0, 0, 0, 0, 0};
     long long ngroups = 0;
     std::vector<long long> h_ioff, h_joff;
     DevBuf g_ioff, g_joff, g_jlist, g_items, g_ctr, g_queue, g_jhl, g_ihl;
@@ -554,12 +556,30 @@ int pg_set_tree(pg_ctx *c, double theta, int ncrit, int nleaf)
     return PG_OK;
 }
 
+int pg_set_tree_quadrupole(pg_ctx *c, int on)
+{
+    if (!c) return PG_EINVAL;
+    c->tree_quad = on != 0;
+    return PG_OK;
+}
+
+int pg_get_tree_pseudo(pg_ctx *c, double *rec)
+{
+    if (!c || !rec) return PG_EINVAL;
+    PG_CUDA(c, cudaStreamSynchronize(c->stream));
+    const long long n = c->tree_sizes[0], cnt = c->tree_sizes[1] * c->tree_sizes[5];
+    if (cnt <= 0) return PG_OK;
+    PG_CUDA(c, cudaMemcpy(rec, (const double4 *)c->tb[pg_ctx::TB_JREC2].p + n, (size_t)cnt * 32,
+                          cudaMemcpyDeviceToHost));
+    return PG_OK;
+}
+
 int pg_get_tree(pg_ctx *c, long long *sizes, long long *perm, long long *g_i0, long long *g_ni,
                 long long *j_off, long long *jlist)
 {
     if (!c || !sizes) return PG_EINVAL;
     PG_CUDA(c, cudaStreamSynchronize(c->stream));
-    for (int k = 0; k < 5; ++k) sizes[k] = c->tree_sizes[k];
+    for (int k = 0; k < 6; ++k) sizes[k] = c->tree_sizes[k];
     const long long n = c->tree_sizes[0], ng = c->tree_sizes[2], nl = c->tree_sizes[3];
     if (n == 0) return PG_OK;
     auto copy32 = [&](int b, long long cnt, long long *out, bool is_signed) -> int {
@@ -1330,7 +1350,8 @@ int enqueue_tree(pg_ctx *c, double *acc, double *pot)
     long long lev_off[12] = {0};
     for (int L = 0; L < 11; ++L) lev_off[L + 1] = lev_off[L] + runs[L];
     const long long nnodes = lev_off[11];
-    if (n + nnodes >= (1LL << 31)) return fail(c, PG_EINVAL, "too many tree nodes");
+    t.npseudo = c->tree_quad ? 3 : 1;
+    if (n + t.npseudo * nnodes >= (1LL << 31)) return fail(c, PG_EINVAL, "too many tree nodes");
     if ((rc = tbuf(c, pg_ctx::TB_FIRST, nnodes * 4, t.first)) ||
         (rc = tbuf(c, pg_ctx::TB_COUNT, nnodes * 4, t.count)) ||
         (rc = tbuf(c, pg_ctx::TB_CHILD0, nnodes * 4, t.child0)) ||
@@ -1347,7 +1368,9 @@ int enqueue_tree(pg_ctx *c, double *acc, double *pot)
     const long long ng = runs[11];
     if ((rc = tbuf(c, pg_ctx::TB_JCOUNT, (ng + 1) * 4, t.jcount)) ||
         (rc = tbuf(c, pg_ctx::TB_JOFF, (ng + 1) * 8, t.j_off)) ||
-        (rc = tbuf(c, pg_ctx::TB_JREC2, (n + nnodes) * 32, t.jrec2)) ||
+        (rc = tbuf(c, pg_ctx::TB_JREC2, (n + t.npseudo * nnodes) * 32, t.jrec2)) ||
+        (rc = tbuf(c, pg_ctx::TB_COM, nnodes * 32, t.com)) ||
+        (rc = tbuf(c, pg_ctx::TB_T, (t.npseudo == 3 ? nnodes : 1) * 48, t.T)) ||
         (rc = tbuf(c, pg_ctx::TB_SEG, 2 * 11 * ng * 4, t.seg)) ||
         (rc = tbuf(c, pg_ctx::TB_BASE, 11 * ng * 8, t.base)) ||
         (rc = tbuf(c, pg_ctx::TB_ETOT, 8, t.etot)) ||
@@ -1356,7 +1379,7 @@ int enqueue_tree(pg_ctx *c, double *acc, double *pot)
         (rc = tbuf(c, pg_ctx::TB_FILT, sizeof(WalkFilter), t.filt)) ||
         (rc = walk_room(c, t, std::max(8 * n, 2 * ng), 0, 0)))
         return rc;
-    PG_CUDA(c, tree_stage_jrec(n, nnodes, t, c->stream));
+    PG_CUDA(c, tree_stage_jrec(n, nnodes, lev_off, t, c->stream));
     // the walk, one level at a time; the next frontier's size comes back
     // to size its room
     long long lev_v[12] = {0, ng};
@@ -1397,7 +1420,7 @@ int enqueue_tree(pg_ctx *c, double *acc, double *pot)
         (rc = read_dev(c, &pairs, t.pairs, 8)))
         return rc;
     const long long nitems = runs[12];
-    const long long nj = n + nnodes;
+    const long long nj = n + t.npseudo * nnodes;
     if ((rc = ensure(c, c->g_jhl, (size_t)nj * 32)) || (rc = ensure(c, c->g_ihl, (size_t)n * 32)) ||
         (rc = ensure(c, c->g_ctr, (size_t)std::max<long long>(ng, 1) * 32)) ||
         (rc = ensure(c, c->g_queue, 16)))
@@ -1431,6 +1454,7 @@ int enqueue_tree(pg_ctx *c, double *acc, double *pot)
     c->tree_sizes[2] = ng;
     c->tree_sizes[3] = nlist;
     c->tree_sizes[4] = nitems;
+    c->tree_sizes[5] = t.npseudo;
     return PG_OK;
 }
 

@@ -236,12 +236,15 @@ struct TreeScratch {
     double *gbox;               // 6 per group
     float4 *gboxf;              // 2 per group: the box rounded to FP32
     TreeNodeW *nodew;           // nnodes
+    double4 *com;               // nnodes: centre of mass (S / M, M)
+    double *T;                  // 6 nnodes: second moments (quadrupole pseudo-particles)
+    int npseudo;                // pseudo-particles per node: 1 or 3
     WalkFilter *filt;           // 1
     long long *i_off;           // groups + 1
     unsigned *jcount;           // groups + 1
     long long *j_off;           // groups + 1
     int *jlist;                 // list entries
-    double4 *jrec2;             // n + nnodes: particles, then pseudo-particles
+    double4 *jrec2;             // n + P nnodes: particles, then pseudo-particles
     unsigned *item_off;         // groups + 1
     GroupItem *items;
     unsigned long long *pairs;  // 1
@@ -259,7 +262,8 @@ cudaError_t tree_stage_keys(const double4 *jrec, long long n, TreeScratch &t, So
                             cudaStream_t st);
 cudaError_t tree_stage_nodes(long long n, const long long *lev_off, int ncrit, TreeScratch &t,
                              SortScratch &sort, cudaStream_t st);
-cudaError_t tree_stage_jrec(long long n, long long nnodes, TreeScratch &t, cudaStream_t st);
+cudaError_t tree_stage_jrec(long long n, long long nnodes, const long long *lev_off, TreeScratch &t,
+                            cudaStream_t st);
 // the walk, level by level: init takes the groups' boxes and puts every
 // group at the root; level L
 // decides its frontier (visits [o, o + nf)) and scans the opened children,

@@ -263,7 +263,9 @@ __global__ void k_tree_groups(const int *__restrict__ gat, const unsigned *__res
 }
 
 // a group's bounding box, one warp per group: FP64, and rounded to nearest
-// FP32 for the walk's pre-test
+// FP32 for the walk's pre-test. Minima and maxima are taken on the
+// order-preserving integer images of the coordinates (integer compares run
+// at full rate; FP64 compares do not)
 __global__ void k_tree_gbox(const int *__restrict__ g_i0, const int *__restrict__ g_ni,
                             long long ngroups, const double4 *__restrict__ xs,
                             double *__restrict__ gbox, float4 *__restrict__ gboxf)
@@ -272,32 +274,34 @@ __global__ void k_tree_gbox(const int *__restrict__ g_i0, const int *__restrict_
     const int lane = threadIdx.x & 31;
     if (g >= ngroups) return;
     const int i0 = g_i0[g], ni = g_ni[g];
-    const double4 v0 = xs[i0];
-    double lo[3] = {v0.x, v0.y, v0.z}, hi[3] = {v0.x, v0.y, v0.z};
+    unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
     for (int k = i0 + lane; k < i0 + ni; k += 32) {
         const double4 v = xs[k];
-        const double c[3] = {v.x, v.y, v.z};
+        const unsigned long long c[3] = {ord_of(v.x), ord_of(v.y), ord_of(v.z)};
         for (int a = 0; a < 3; ++a) {
-            if (c[a] < lo[a]) lo[a] = c[a];
-            if (c[a] > hi[a]) hi[a] = c[a];
+            lo[a] = c[a] < lo[a] ? c[a] : lo[a];
+            hi[a] = c[a] > hi[a] ? c[a] : hi[a];
         }
     }
     for (int s = 16; s; s >>= 1)
         for (int a = 0; a < 3; ++a) {
-            const double l = __shfl_xor_sync(0xffffffffu, lo[a], s);
-            const double h = __shfl_xor_sync(0xffffffffu, hi[a], s);
-            if (l < lo[a]) lo[a] = l;
-            if (h > hi[a]) hi[a] = h;
+            const unsigned long long l = __shfl_xor_sync(0xffffffffu, lo[a], s);
+            const unsigned long long h = __shfl_xor_sync(0xffffffffu, hi[a], s);
+            lo[a] = l < lo[a] ? l : lo[a];
+            hi[a] = h > hi[a] ? h : hi[a];
         }
     if (lane == 0) {
+        double dl[3], dh[3];
         for (int a = 0; a < 3; ++a) {
-            gbox[6 * g + a] = lo[a];
-            gbox[6 * g + 3 + a] = hi[a];
+            dl[a] = val_of(lo[a]);
+            dh[a] = val_of(hi[a]);
+            gbox[6 * g + a] = dl[a];
+            gbox[6 * g + 3 + a] = dh[a];
         }
-        gboxf[2 * g] = make_float4(__double2float_rn(lo[0]), __double2float_rn(lo[1]),
-                                   __double2float_rn(lo[2]), 0.f);
-        gboxf[2 * g + 1] = make_float4(__double2float_rn(hi[0]), __double2float_rn(hi[1]),
-                                       __double2float_rn(hi[2]), 0.f);
+        gboxf[2 * g] = make_float4(__double2float_rn(dl[0]), __double2float_rn(dl[1]),
+                                   __double2float_rn(dl[2]), 0.f);
+        gboxf[2 * g + 1] = make_float4(__double2float_rn(dh[0]), __double2float_rn(dh[1]),
+                                       __double2float_rn(dh[2]), 0.f);
     }
 }
 
@@ -330,6 +334,7 @@ struct LevelArgs {
     const double4 *com;        // per node: centre of mass S / M, mass (FP64)
     const WalkFilter *filt;
     int nleaf;
+    int npseudo;               // entries of an accepted node: 1 or 3
     const int *vg;             // visits: group
     int *vk;                   // visits: node, ~node once accepted
     unsigned *ve;              // visits: entries the decision emits
@@ -424,7 +429,7 @@ __global__ void k_walk_test(LevelArgs a)
         }
         unsigned e = 0, c = 0;
         if (accept) {
-            e = 1;
+            e = (unsigned)a.npseudo;
             a.vk[v] = ~k;
         } else if (a.L == kLevels - 1 || nd.count <= a.nleaf) {
             e = (unsigned)nd.count;
@@ -494,7 +499,7 @@ __global__ void k_walk_base(long long ngroups, int nlev, const unsigned *__restr
 
 // the entries of level L's visits [o, o + nf)
 __global__ void k_walk_fill(int L, long long o, long long nf, long long n, long long ngroups,
-                            const int *__restrict__ vg, const int *__restrict__ vk,
+                            int npseudo, const int *__restrict__ vg, const int *__restrict__ vk,
                             const unsigned *__restrict__ ve, const long long *__restrict__ base,
                             const long long *__restrict__ j_off, const TreeNodeW *__restrict__ nodew,
                             int *__restrict__ jlist, int *status)
@@ -507,31 +512,35 @@ __global__ void k_walk_fill(int L, long long o, long long nf, long long n, long 
     const int g = vg[v], k = vk[v];
     const long long dst = base[L * ngroups + g] + ve[v];
     // the entries stay inside the group's list; anything else is reported
-    if (dst < j_off[g] || dst + e > j_off[g + 1] || (k < 0 && e != 1)) {
+    if (dst < j_off[g] || dst + e > j_off[g + 1] || (k < 0 && e != (unsigned)npseudo)) {
         report(status, kStatusBadIndex, 10);
         return;
     }
     if (k < 0) {
-        jlist[dst] = (int)(n + ~k);
+        const int p0 = (int)(n + (long long)npseudo * ~k);
+        for (int q = 0; q < npseudo; ++q) jlist[dst + q] = p0 + q;
     } else {
         const int f = nodew[k].first;
         for (unsigned t = 0; t < e; ++t) jlist[dst + t] = f + (int)t;
     }
 }
 
-// the pseudo-particles: (S / M, M), after the n particles of the j records;
-// and the walk's node records
+// per node: the centre of mass (S / M, M), the walk's node record, and
+// with monopoles the pseudo-particle itself (mono, after the n particles of
+// the j records; nullptr with quadrupoles)
 __global__ void k_tree_pseudo(const double *__restrict__ M, const double *__restrict__ S,
                               const int *__restrict__ first, const int *__restrict__ count,
                               const int *__restrict__ child0, const int *__restrict__ childn,
-                              long long nnodes, double4 *__restrict__ out, TreeNodeW *__restrict__ nodew)
+                              long long nnodes, double4 *__restrict__ com, double4 *__restrict__ mono,
+                              TreeNodeW *__restrict__ nodew)
 {
     const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (k >= nnodes) return;
     const double m = M[k];
     const double4 c = make_double4(__ddiv_rn(S[3 * k], m), __ddiv_rn(S[3 * k + 1], m),
                                    __ddiv_rn(S[3 * k + 2], m), m);
-    out[k] = c;
+    com[k] = c;
+    if (mono) mono[k] = c;
     TreeNodeW w;
     w.cx = __double2float_rn(c.x);
     w.cy = __double2float_rn(c.y);
@@ -542,6 +551,135 @@ __global__ void k_tree_pseudo(const double *__restrict__ M, const double *__rest
     w.child0 = child0[k];
     w.childn = childn[k];
     nodew[k] = w;
+}
+
+// second moments about the centre of mass, T = sum m (x - c)(x - c)^T as
+// {xx, xy, xz, yy, yz, zz}: the finest level from its particles ...
+__global__ void k_tree_second_leaf(long long off, long long runs, const int *__restrict__ first,
+                                   const int *__restrict__ count, const double4 *__restrict__ xs,
+                                   const double4 *__restrict__ com, double *__restrict__ T)
+{
+    const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (r >= runs) return;
+    const long long k = off + r;
+    const double4 c = com[k];
+    double t[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = first[k]; i < first[k] + count[k]; ++i) {
+        const double4 v = xs[i];
+        const double y0 = v.x - c.x, y1 = v.y - c.y, y2 = v.z - c.z;
+        t[0] += v.w * y0 * y0;
+        t[1] += v.w * y0 * y1;
+        t[2] += v.w * y0 * y2;
+        t[3] += v.w * y1 * y1;
+        t[4] += v.w * y1 * y2;
+        t[5] += v.w * y2 * y2;
+    }
+    for (int q = 0; q < 6; ++q) T[6 * k + q] = t[q];
+}
+
+// ... and the levels above from their children, moved to the parent's
+// centre (the parallel-axis rule: T = sum T_ch + M_ch (c_ch - c)(c_ch - c)^T)
+__global__ void k_tree_second_up(long long off, long long runs, const int *__restrict__ child0,
+                                 const int *__restrict__ childn, const double4 *__restrict__ com,
+                                 double *__restrict__ T)
+{
+    const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (r >= runs) return;
+    const long long k = off + r;
+    const double4 c = com[k];
+    double t[6] = {0, 0, 0, 0, 0, 0};
+    for (int ch = child0[k]; ch < child0[k] + childn[k]; ++ch) {
+        const double4 cc = com[ch];
+        const double y0 = cc.x - c.x, y1 = cc.y - c.y, y2 = cc.z - c.z;
+        const double *tc = T + 6 * (long long)ch;
+        t[0] += tc[0] + cc.w * y0 * y0;
+        t[1] += tc[1] + cc.w * y0 * y1;
+        t[2] += tc[2] + cc.w * y0 * y2;
+        t[3] += tc[3] + cc.w * y1 * y1;
+        t[4] += tc[4] + cc.w * y1 * y2;
+        t[5] += tc[5] + cc.w * y2 * y2;
+    }
+    for (int q = 0; q < 6; ++q) T[6 * k + q] = t[q];
+}
+
+// Jacobi rotation zeroing a[p][q] of the symmetric 3x3 a (r the third
+// index), with the update written element by element; v accumulates the
+// rotations in its columns
+__device__ __forceinline__ void jacobi_rotate(double (&a)[3][3], double (&v)[3][3], int p, int q, int r)
+{
+    const double apq = a[p][q];
+    if (apq == 0.0) return;
+    const double h = 0.5 * (a[q][q] - a[p][p]) / apq;
+    const double t = copysign(1.0, h) / (fabs(h) + sqrt(fma(h, h, 1.0)));
+    const double c = rsqrt(fma(t, t, 1.0)), s = t * c;
+    a[p][p] -= t * apq;
+    a[q][q] += t * apq;
+    a[p][q] = a[q][p] = 0.0;
+    const double arp = a[r][p], arq = a[r][q];
+    a[r][p] = a[p][r] = c * arp - s * arq;
+    a[r][q] = a[q][r] = s * arp + c * arq;
+    for (int k = 0; k < 3; ++k) {
+        const double vkp = v[k][p], vkq = v[k][q];
+        v[k][p] = c * vkp - s * vkq;
+        v[k][q] = s * vkp + c * vkq;
+    }
+}
+
+// the quadrupole pseudo-particles (Kawai and Makino's three): with T's
+// eigenvalues l1 >= l2 >= l3 and unit eigenvectors e1, e2 (e1's largest
+// component positive), mass M / 3 at c + a e1 and c - a/2 e1 +- (sqrt 3 / 2)
+// b e2, a = sqrt(2 (l1 - l3) / M), b = sqrt(2 (l2 - l3) / M); they carry M,
+// a zero dipole and T - l3 I (the trace-free quadrupole of T)
+__global__ void k_tree_quad(long long nnodes, const double4 *__restrict__ com,
+                            const double *__restrict__ T, double4 *__restrict__ out)
+{
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= nnodes) return;
+    const double4 c = com[k];
+    const double *t = T + 6 * k;
+    double a[3][3] = {{t[0], t[1], t[2]}, {t[1], t[3], t[4]}, {t[2], t[4], t[5]}};
+    double v[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        const double off = fabs(a[0][1]) + fabs(a[0][2]) + fabs(a[1][2]);
+        if (!(off > 1e-18 * (fabs(a[0][0]) + fabs(a[1][1]) + fabs(a[2][2])))) break;
+        jacobi_rotate(a, v, 0, 1, 2);
+        jacobi_rotate(a, v, 0, 2, 1);
+        jacobi_rotate(a, v, 1, 2, 0);
+    }
+    // selects instead of indexing keep the arrays in registers
+    const double lam0 = a[0][0], lam1 = a[1][1], lam2 = a[2][2];
+    int i1 = 0, i3 = 0;
+    if (lam1 > lam0) i1 = 1;
+    if (lam2 > (i1 ? lam1 : lam0)) i1 = 2;
+    if (lam1 < lam0) i3 = 1;
+    if (lam2 < (i3 ? lam1 : lam0)) i3 = 2;
+    if (i1 == i3) i3 = i1 == 2 ? 0 : i1 + 1;
+    const int i2 = 3 - i1 - i3;
+    auto pick = [](int i, double x0, double x1, double x2) { return i == 0 ? x0 : i == 1 ? x1 : x2; };
+    const double l1 = pick(i1, lam0, lam1, lam2), l2 = pick(i2, lam0, lam1, lam2),
+                 l3 = pick(i3, lam0, lam1, lam2);
+    double e1x = pick(i1, v[0][0], v[0][1], v[0][2]), e1y = pick(i1, v[1][0], v[1][1], v[1][2]),
+           e1z = pick(i1, v[2][0], v[2][1], v[2][2]);
+    const double e2x = pick(i2, v[0][0], v[0][1], v[0][2]), e2y = pick(i2, v[1][0], v[1][1], v[1][2]),
+                 e2z = pick(i2, v[2][0], v[2][1], v[2][2]);
+    double big = e1x;
+    if (fabs(e1y) > fabs(big)) big = e1y;
+    if (fabs(e1z) > fabs(big)) big = e1z;
+    if (big < 0.0) {
+        e1x = -e1x;
+        e1y = -e1y;
+        e1z = -e1z;
+    }
+    const double M = c.w;
+    const double al = sqrt(2.0 * fmax(l1 - l3, 0.0) / M);
+    const double be = sqrt(2.0 * fmax(l2 - l3, 0.0) / M);
+    const double hb = 0.8660254037844386 * be;      // sqrt(3) / 2, rounded
+    const double m3 = M / 3.0;
+    const double ax = al * e1x, ay = al * e1y, az = al * e1z;
+    const double bx = hb * e2x, by = hb * e2y, bz = hb * e2z;
+    out[3 * k] = make_double4(c.x + ax, c.y + ay, c.z + az, m3);
+    out[3 * k + 1] = make_double4(c.x - 0.5 * ax + bx, c.y - 0.5 * ay + by, c.z - 0.5 * az + bz, m3);
+    out[3 * k + 2] = make_double4(c.x - 0.5 * ax - bx, c.y - 0.5 * ay - by, c.z - 0.5 * az - bz, m3);
 }
 
 // items: the groups cut into chunks of at most Bi particles; pairs = sum ni nj
@@ -678,9 +816,10 @@ cudaError_t tree_walk_level(long long n, long long ngroups, int L, long long o, 
     a.gbox = t.gbox;
     a.gboxf = t.gboxf;
     a.nodew = t.nodew;
-    a.com = t.jrec2 + n;       // the pseudo-particles, written before the walk
+    a.com = t.com;
     a.filt = t.filt;
     a.nleaf = nleaf;
+    a.npseudo = t.npseudo;
     a.vg = t.vg;
     a.vk = t.vk;
     a.ve = t.ve;
@@ -720,21 +859,38 @@ cudaError_t tree_walk_fill(long long n, long long ngroups, const long long *lev_
 {
     for (int L = 0; L < nlev; ++L) {
         const long long o = lev_v[L], nf = lev_v[L + 1] - o;
-        k_walk_fill<<<blocks_of(nf), 256, 0, st>>>(L, o, nf, n, ngroups, t.vg, t.vk, t.ve, t.base, t.j_off,
-                                                   t.nodew, t.jlist, status);
+        k_walk_fill<<<blocks_of(nf), 256, 0, st>>>(L, o, nf, n, ngroups, t.npseudo, t.vg, t.vk, t.ve,
+                                                   t.base, t.j_off, t.nodew, t.jlist, status);
         ++t.launches;
     }
     return cudaGetLastError();
 }
 
-// the j records: particles in key order, then one pseudo-particle per node
-// (centre of mass S / M, mass); the walk reads the centres from here
-cudaError_t tree_stage_jrec(long long n, long long nnodes, TreeScratch &t, cudaStream_t st)
+// the j records: particles in key order, then P pseudo-particles per node
+// (monopoles: the centre of mass and mass; quadrupoles: three from the
+// second moments, which are summed bottom-up first); the walk's centres
+cudaError_t tree_stage_jrec(long long n, long long nnodes, const long long *lev_off, TreeScratch &t,
+                            cudaStream_t st)
 {
+    const bool quad = t.npseudo == 3;
     cudaMemcpyAsync(t.jrec2, t.xs, n * sizeof(double4), cudaMemcpyDeviceToDevice, st);
     k_tree_pseudo<<<blocks_of(nnodes), 256, 0, st>>>(t.M, t.S, t.first, t.count, t.child0, t.childn,
-                                                    nnodes, t.jrec2 + n, t.nodew);
+                                                    nnodes, t.com, quad ? nullptr : t.jrec2 + n, t.nodew);
     ++t.launches;
+    if (quad) {
+        {
+            const long long L = kLevels - 1, runs = lev_off[L + 1] - lev_off[L];
+            k_tree_second_leaf<<<blocks_of(runs), 256, 0, st>>>(lev_off[L], runs, t.first, t.count, t.xs,
+                                                                t.com, t.T);
+        }
+        for (int L = kLevels - 2; L >= 0; --L) {
+            const long long runs = lev_off[L + 1] - lev_off[L];
+            k_tree_second_up<<<blocks_of(runs), 256, 0, st>>>(lev_off[L], runs, t.child0, t.childn, t.com,
+                                                              t.T);
+        }
+        k_tree_quad<<<blocks_of(nnodes), 256, 0, st>>>(nnodes, t.com, t.T, t.jrec2 + n);
+        t.launches += kLevels + 1;
+    }
     return cudaGetLastError();
 }
 

@@ -7,7 +7,9 @@ the GPU against the oracle's tree:
   tolerances (median <= 2e-6, max <= 1e-4).
 - theta = 0 reproduces the direct sum.
 Covered: a Plummer sphere, a clustered set with dense finest-level cells, the
-paper's theta = 0.75, several ncrit and nleaf, and the errors.
+paper's theta = 0.75, several ncrit and nleaf, monopole and quadrupole
+pseudo-particles, opening decisions at the threshold, scaled coordinates, and
+the errors.
 """
 
 import numpy as np
@@ -24,15 +26,29 @@ def pg():
     return need_cuda()
 
 
-def gpu_tree(pg, x, m, eps, theta, ncrit, nleaf):
+def gpu_tree(pg, x, m, eps, theta, ncrit, nleaf, quadrupole=False):
     with pg.Context(0) as c:
         c.set_eps(eps)
         c.set_self(True)
-        c.set_tree(theta, ncrit, nleaf)
+        c.set_tree(theta, ncrit, nleaf, quadrupole=quadrupole)
         a, p = c.forces(x, x, m)
         t = c.get_tree()
         info = c.info()
     return a, p, t, info
+
+
+def same_pseudo(t, o):
+    # the same pseudo-particles up to the rounding of the moments: a spread
+    # from a difference of eigenvalues that is zero in exact arithmetic (two-
+    # or three-particle nodes) is sqrt(rounding) of the node's spread, so the
+    # bound is relative to that spread sqrt(tr T / M), plus the coordinates'
+    # own rounding
+    P = o["npseudo"]
+    spread = np.sqrt(np.maximum(o["nT"][:, [0, 3, 5]].sum(axis=1), 0) / o["nM"])
+    tol = np.repeat(1e-6 * spread, P) + 1e-13 * np.abs(o["pseudo"][:, :3]).max()
+    d = np.abs(t["pseudo"][:, :3] - o["pseudo"][:, :3]).max(axis=1)
+    assert np.all(d <= tol), f"{np.count_nonzero(d > tol)} pseudo-particles differ"
+    assert np.allclose(t["pseudo"][:, 3], o["pseudo"][:, 3], rtol=1e-13, atol=0)
 
 
 def same_lists(t, o):
@@ -142,5 +158,34 @@ def test_scaled_sets(pg, orc, scale):
     if scale > 1e18:
         return          # the FP32 pair arithmetic overflows at r^2 ~ 1e50
     ao, po = orc.tree_forces(x, m, 1e-3 * scale, 0.75, 64, 8)
+    assert_parity(rel_vec(a, ao), what="a")
+    assert_parity(rel_scalar(p, po), what="phi")
+
+
+@pytest.mark.parametrize("theta,ncrit,nleaf", [(0.75, 64, 8), (0.5, 32, 4)])
+def test_quadrupole_lists_and_forces(pg, orc, theta, ncrit, nleaf):
+    x, m = gen.plummer(20000, 87)
+    m = m * np.random.default_rng(7).uniform(0.5, 2.0, len(m))
+    a, p, t, info = gpu_tree(pg, x, m, 1e-3, theta, ncrit, nleaf, quadrupole=True)
+    o = orc.tree_build(x, m, theta, ncrit, nleaf, quadrupole=True)
+    assert t["npseudo"] == 3
+    same_lists(t, o)
+    same_pseudo(t, o)
+    assert info["pairs"] == int(np.sum(o["g_ni"] * np.diff(o["j_off"])))
+    ao, po = orc.tree_forces(x, m, 1e-3, theta, ncrit, nleaf, quadrupole=True)
+    assert_parity(rel_vec(a, ao), what="a")
+    assert_parity(rel_scalar(p, po), what="phi")
+
+
+def test_quadrupole_clustered_and_direct(pg, orc):
+    x, m = gen.clustered_box(30000, 88, nclump=40, sigma=2e-4, periodic=False)
+    a, p, t, _ = gpu_tree(pg, x, m, 1e-4, 0.75, 32, 8, quadrupole=True)
+    same_lists(t, orc.tree_build(x, m, 0.75, 32, 8, quadrupole=True))
+    ao, po = orc.tree_forces(x, m, 1e-4, 0.75, 32, 8, quadrupole=True)
+    assert_parity(rel_vec(a, ao), what="a")
+    assert_parity(rel_scalar(p, po), what="phi")
+    x, m = gen.plummer(6000, 89)
+    a, p, _, _ = gpu_tree(pg, x, m, 0.01, 0.0, 64, 8, quadrupole=True)
+    ao, po = orc.newton_allpairs(x, m, 0.01)
     assert_parity(rel_vec(a, ao), what="a")
     assert_parity(rel_scalar(p, po), what="phi")
