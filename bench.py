@@ -39,6 +39,15 @@ EPS = 1e-3
 NEWTON_OPS = 13          # FP32-pipe lane-ops per Newton interaction (f32x2 counts 2)
 FP32_LANES_PER_SM = 128
 PAPER_FLOPS_PER_INT = 38
+TREE_NCRIT = 256         # group size bound of the tree rows
+
+
+def tree_model(model, n):
+    """The tree runs' particle sets (Section 5.1): a Plummer sphere or a King
+    model with W0 = 9, equal masses."""
+    if model == "king":
+        return gen.king(n, gen.CONFIG_SEEDS[2], W0=9.0)
+    return gen.plummer(n, gen.CONFIG_SEEDS[2])
 
 
 def parse():
@@ -59,6 +68,11 @@ def parse():
                     choices=["newton", "table", "cells", "groups", "backward", "narrow", "tree"],
                     help="newton: the headline; the others time one row of the path alone "
                          "(for profiling) and print its measurements")
+    ap.add_argument("--model", default="plummer", choices=["plummer", "king"],
+                    help="tree workload: the particle set")
+    ap.add_argument("--quadrupole", action="store_true",
+                    help="tree workload: quadrupole pseudo-particles")
+    ap.add_argument("--ncrit", type=int, default=TREE_NCRIT, help="tree workload: group size bound")
     return ap.parse_args()
 
 
@@ -277,31 +291,36 @@ def extra_rows(pg, torch, dev, peak_newton, headline_rate):
     rows["individual_steps_ni_vs_2e20"] = steps
     del xd, md
 
-    # tree front end (Section 5.1's tree usage): 2^20 Plummer, theta = 0.75,
-    # groups of at most 64, leaves of at most 8, eps = 1e-3; per call (tree
-    # build, walk, lists, forces) and the force kernel alone
+    # tree front end (Section 5.1's tree usage): 2^20-particle Plummer and
+    # King (W0 = 9) models, theta = 0.75, monopole and quadrupole
+    # pseudo-particles, groups of at most 256, leaves of at most 8,
+    # eps = 1e-3; per call (tree build, walk, lists, forces) and the force
+    # kernel alone
     n = N_PART
-    x, m = gen.plummer(n, gen.CONFIG_SEEDS[2])
-    xd, md = torch.tensor(x, device=dev), torch.tensor(m, device=dev)
-    a, p = torch.empty_like(xd), torch.empty_like(md)
-    with pg.Context(idx) as c:
-        c.set_stream(st.cuda_stream)
-        c.set_eps(EPS)
-        c.set_self(True)
-        c.set_timing(True)
-        c.set_tree(0.75, 64, 8)
-        c.set_j_dev(xd, md)
-        c.set_i_dev(xd)
-        ms = _time_call(torch, lambda: c.run_dev(a, p), 5, warm=2)
-        kms = c.kernel_time()
-        info = c.info()
-        t = c.get_tree()
-        rows["tree_plummer_2e20_theta075"] = {
-            "ms_per_call": ms, "force_kernel_ms": kms, "pairs": info["pairs"],
-            "interactions_per_s_kernel": info["pairs"] / (kms * 1e-3),
-            "nodes": t["nnodes"], "groups": t["ngroups"], "list_entries": t["nlist"],
-            "direct_sum_equivalent_speedup": (n * n / headline_rate) / (ms * 1e-3)}
-    del xd, md, a, p
+    for model in ("plummer", "king"):
+        x, m = tree_model(model, n)
+        xd, md = torch.tensor(x, device=dev), torch.tensor(m, device=dev)
+        a, p = torch.empty_like(xd), torch.empty_like(md)
+        for quad in (False, True):
+            with pg.Context(idx) as c:
+                c.set_stream(st.cuda_stream)
+                c.set_eps(EPS)
+                c.set_self(True)
+                c.set_timing(True)
+                c.set_tree(0.75, TREE_NCRIT, 8, quadrupole=quad)
+                c.set_j_dev(xd, md)
+                c.set_i_dev(xd)
+                ms = _time_call(torch, lambda: c.run_dev(a, p), 5, warm=2)
+                kms = c.kernel_time()
+                info = c.info()
+                t = c.get_tree()
+                rows[f"tree_{model}_2e20_theta075_{'quadrupole' if quad else 'monopole'}"] = {
+                    "ms_per_call": ms, "force_kernel_ms": kms, "pairs": info["pairs"],
+                    "interactions_per_s_kernel": info["pairs"] / (kms * 1e-3),
+                    "nodes": t["nnodes"], "groups": t["ngroups"], "list_entries": t["nlist"],
+                    "ncrit": TREE_NCRIT,
+                    "direct_sum_equivalent_speedup": (n * n / headline_rate) / (ms * 1e-3)}
+        del xd, md, a, p
 
     # tabulated all-pairs: 65536 Plummer, Gaussian split, r_cut = 0.1, E=3, F=5
     n = 65536
@@ -448,9 +467,9 @@ def run_row(args):
                                    warm=args.warmup)
         out.update(n=n, kernel_ms=kms, interactions_per_s=n * n / (kms * 1e-3))
     elif args.workload == "tree":
-        # the tree front end on a Plummer sphere of --n particles (default 2^20)
+        # the tree front end on --n particles (default 2^20) of --model
         n = args.n
-        x, m = gen.plummer(n, gen.CONFIG_SEEDS[2])
+        x, m = tree_model(args.model, n)
         xd, md = torch.tensor(x, device=dev), torch.tensor(m, device=dev)
         a = torch.empty_like(xd)
         with pg.Context(0) as c:
@@ -458,12 +477,13 @@ def run_row(args):
             c.set_eps(EPS)
             c.set_self(True)
             c.set_timing(True)
-            c.set_tree(0.75, 64, 8)
+            c.set_tree(0.75, args.ncrit, 8, quadrupole=args.quadrupole)
             c.set_j_dev(xd, md)
             c.set_i_dev(xd)
             kms = _time_kernel(c, lambda: c.run_dev(a), reps=args.steps, warm=args.warmup)
             info = c.info()
-        out.update(n=n, pairs=info["pairs"], kernel_ms=kms,
+        out.update(n=n, model=args.model, quadrupole=args.quadrupole, ncrit=args.ncrit,
+                   pairs=info["pairs"], kernel_ms=kms,
                    interactions_per_s=info["pairs"] / (kms * 1e-3))
     elif args.workload == "narrow":
         # individual time steps: --n core particles of the 2^20 mixed set

@@ -7,6 +7,8 @@ produces, and neither imports the other.
 
 from .workloads import (  # noqa: F401
     plummer,
+    king,
+    king_profile,
     plummer_cube_mix,
     clustered_box,
     tree_groups,

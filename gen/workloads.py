@@ -54,6 +54,55 @@ def plummer(n: int, seed: int, a: float = 1.0, total_mass: float = 1.0,
     return np.ascontiguousarray(x), m
 
 
+def _king_density(W):
+    """King (1966) density in units of its value at W = 1 scale: zero for
+    W <= 0, else e^W erf(sqrt W) - sqrt(4 W / pi) (1 + 2 W / 3)."""
+    from scipy.special import erf
+    W = np.maximum(np.asarray(W, dtype=np.float64), 0.0)
+    return np.exp(W) * erf(np.sqrt(W)) - np.sqrt(4.0 * W / np.pi) * (1.0 + 2.0 * W / 3.0)
+
+
+def king_profile(W0: float = 9.0, npts: int = 4000):
+    """The King model's radial structure in King radii r0 (with
+    r0^2 = 9 sigma^2 / (4 pi G rho0)): integrates Poisson's equation
+    W'' + 2 W' / xi = -9 rho(W) / rho(W0) from W(0) = W0, W'(0) = 0 out to
+    the tidal radius where W = 0, with the enclosed mass alongside.
+    Returns (xi, W, mass fraction) on a grid from near 0 to xi_t."""
+    from scipy.integrate import solve_ivp
+    rho0 = float(_king_density(W0))
+
+    def rhs(xi, y):
+        W, dW, _ = y
+        rho = float(_king_density(W)) / rho0
+        return [dW, -9.0 * rho - 2.0 * dW / xi, xi * xi * rho]
+
+    def tidal(xi, y):
+        return y[0]
+    tidal.terminal = True
+    tidal.direction = -1
+    xi0 = 1e-6          # series start: W = W0 - 1.5 xi^2, M = xi^3 / 3
+    sol = solve_ivp(rhs, (xi0, 1e6), [W0 - 1.5 * xi0 ** 2, -3.0 * xi0, xi0 ** 3 / 3.0],
+                    events=tidal, dense_output=True, rtol=1e-10, atol=1e-13)
+    xt = float(sol.t_events[0][0])
+    xi = np.concatenate([[0.0], np.geomspace(xi0, xt, npts)])
+    y = sol.sol(np.maximum(xi, xi0))
+    mass = np.concatenate([[0.0], y[2, 1:]])
+    mass[-1] = max(mass[-1], mass[-2])
+    return xi, np.maximum(y[0], 0.0), mass / mass[-1]
+
+
+def king(n: int, seed: int, W0: float = 9.0, total_mass: float = 1.0):
+    """King (1966) model of central depth W0 (positions only): radii by
+    inverse-CDF sampling of the enclosed mass, in King radii, out to the
+    tidal radius; isotropic directions; equal masses."""
+    rng = _rng(seed)
+    xi, _, frac = king_profile(W0)
+    keep = np.concatenate([[True], np.diff(frac) > 0])
+    r = np.interp(rng.random(n), frac[keep], xi[keep])
+    x = r[:, None] * _isotropic(rng, n)
+    return np.ascontiguousarray(x), np.full(n, total_mass / n)
+
+
 def uniform_sphere(n: int, seed: int, radius: float = 1.0, total_mass: float = 1.0):
     """Uniform-density ball of the given radius, equal masses."""
     rng = _rng(seed)

@@ -1,15 +1,16 @@
-"""The tree front end (the tree usage of Section 5.1, monopole moments) on
-the GPU against the oracle's tree:
+"""The tree front end (the tree usage of Section 5.1) on the GPU against the
+oracle's tree:
 
 - The key order, the groups and every interaction list are identical, bit
   for bit (index work).
+- Quadrupole pseudo-particles agree up to the rounding of the moments.
 - Forces and potentials from those lists agree within the Newton
   tolerances (median <= 2e-6, max <= 1e-4).
 - theta = 0 reproduces the direct sum.
-Covered: a Plummer sphere, a clustered set with dense finest-level cells, the
-paper's theta = 0.75, several ncrit and nleaf, monopole and quadrupole
-pseudo-particles, opening decisions at the threshold, scaled coordinates, and
-the errors.
+Covered: a Plummer sphere, a King model (W0 = 9), a clustered set with dense
+finest-level cells, the paper's theta = 0.75, several ncrit and nleaf,
+monopole and quadrupole pseudo-particles, opening decisions at the
+threshold, scaled coordinates, and the errors.
 """
 
 import numpy as np
@@ -187,5 +188,20 @@ def test_quadrupole_clustered_and_direct(pg, orc):
     x, m = gen.plummer(6000, 89)
     a, p, _, _ = gpu_tree(pg, x, m, 0.01, 0.0, 64, 8, quadrupole=True)
     ao, po = orc.newton_allpairs(x, m, 0.01)
+    assert_parity(rel_vec(a, ao), what="a")
+    assert_parity(rel_scalar(p, po), what="phi")
+
+
+@pytest.mark.parametrize("quad", [False, True])
+def test_king_model(pg, orc, quad):
+    # the paper's other tree workload: a King model with W0 = 9, whose core
+    # packs many particles into finest-level cells
+    x, m = gen.king(20000, 90, W0=9.0)
+    a, p, t, _ = gpu_tree(pg, x, m, 1e-3, 0.75, 64, 8, quadrupole=quad)
+    o = orc.tree_build(x, m, 0.75, 64, 8, quadrupole=quad)
+    same_lists(t, o)
+    if quad:
+        same_pseudo(t, o)
+    ao, po = orc.tree_forces(x, m, 1e-3, 0.75, 64, 8, quadrupole=quad)
     assert_parity(rel_vec(a, ao), what="a")
     assert_parity(rel_scalar(p, po), what="phi")
