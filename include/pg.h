@@ -147,6 +147,8 @@ int pg_get_table(pg_ctx *ctx, float *G0, float *G1, long long n);
  * ni == nj, no groups, no periodic box and the global eps (PG_ESTATE
  * otherwise). A tree run reads counts back between its stages, so it
  * synchronises and is not captured in a graph. theta < 0 turns it off.
+ * A run returns PG_EINVAL when the particles plus pseudo-particles reach
+ * 2^27 (the list index width) or the lists reach 2^32 entries.
  * PG_EINVAL for a theta that is not finite, ncrit outside 1 .. 2^20 or
  * nleaf < 1. */
 int pg_set_tree(pg_ctx *ctx, double theta, int ncrit, int nleaf);

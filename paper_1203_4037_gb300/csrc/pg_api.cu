@@ -94,7 +94,7 @@ struct pg_ctx {
            TB_CHILD0, TB_CHILDN, TB_LEV, TB_M, TB_S, TB_GAT, TB_GSCAN, TB_GI0, TB_GNI, TB_GBOX,
            TB_IOFF, TB_JCOUNT, TB_JOFF, TB_JLIST, TB_JREC2, TB_ITEMOFF, TB_ITEMS, TB_PAIRS,
            TB_VG, TB_VK, TB_VE, TB_VC, TB_VSUMS, TB_SEG, TB_BASE, TB_ETOT, TB_GBOXF, TB_NODEW,
-           TB_FILT, TB_COM, TB_T, TB_N };
+           TB_FILT, TB_COM, TB_T, TB_BIG, TB_NBIG, TB_TSUMS, TB_N };
     DevBuf tb[TB_N];
     long long tree_sizes[6] = {0, 0, 0, 0, 0, 0};
     long long ngroups = 0;
@@ -1335,7 +1335,8 @@ int enqueue_tree(pg_ctx *c, double *acc, double *pot)
         (rc = tbuf(c, pg_ctx::TB_BBOX, 48, t.bbox)) || (rc = tbuf(c, pg_ctx::TB_GEO, 32, t.geo)) ||
         (rc = tbuf(c, pg_ctx::TB_KEY, n * 4, t.key)) || (rc = tbuf(c, pg_ctx::TB_PERM, n * 4, t.perm)) ||
         (rc = tbuf(c, pg_ctx::TB_XS, n * 32, t.xs)) || (rc = tbuf(c, pg_ctx::TB_XI0, n * 32, t.xi0)) ||
-        (rc = tbuf(c, pg_ctx::TB_SCAN, 11 * (n + 1) * 4, t.scan)) ||
+        (rc = tbuf(c, pg_ctx::TB_SCAN, (11 * (n + 1) + 1) * 4, t.scan)) ||
+        (rc = tbuf(c, pg_ctx::TB_TSUMS, ((11 * (n + 1) + 1) / 4096 + 2) * 4, t.tsums)) ||
         (rc = tbuf(c, pg_ctx::TB_RUNS, 64, t.runs_dev)))
         return rc;
     c->sort.keys[0] = (unsigned *)c->skeys0.p;
@@ -1351,7 +1352,9 @@ int enqueue_tree(pg_ctx *c, double *acc, double *pot)
     for (int L = 0; L < 11; ++L) lev_off[L + 1] = lev_off[L] + runs[L];
     const long long nnodes = lev_off[11];
     t.npseudo = c->tree_quad ? 3 : 1;
-    if (n + t.npseudo * nnodes >= (1LL << 31)) return fail(c, PG_EINVAL, "too many tree nodes");
+    // list entries index the j records in 27 bits (the batched kernel's limit)
+    if (n + t.npseudo * nnodes >= (1LL << 27))
+        return fail(c, PG_EINVAL, "tree too large: particles + pseudo-particles must stay below 2^27");
     if ((rc = tbuf(c, pg_ctx::TB_FIRST, nnodes * 4, t.first)) ||
         (rc = tbuf(c, pg_ctx::TB_COUNT, nnodes * 4, t.count)) ||
         (rc = tbuf(c, pg_ctx::TB_CHILD0, nnodes * 4, t.child0)) ||
@@ -1371,15 +1374,17 @@ int enqueue_tree(pg_ctx *c, double *acc, double *pot)
         (rc = tbuf(c, pg_ctx::TB_JREC2, (n + t.npseudo * nnodes) * 32, t.jrec2)) ||
         (rc = tbuf(c, pg_ctx::TB_COM, nnodes * 32, t.com)) ||
         (rc = tbuf(c, pg_ctx::TB_T, (t.npseudo == 3 ? nnodes : 1) * 48, t.T)) ||
+        (rc = tbuf(c, pg_ctx::TB_BIG, (t.npseudo == 3 ? nnodes : 1) * 4, t.big_list)) ||
+        (rc = tbuf(c, pg_ctx::TB_NBIG, 4, t.nbig)) ||
         (rc = tbuf(c, pg_ctx::TB_SEG, 2 * 11 * ng * 4, t.seg)) ||
         (rc = tbuf(c, pg_ctx::TB_BASE, 11 * ng * 8, t.base)) ||
-        (rc = tbuf(c, pg_ctx::TB_ETOT, 8, t.etot)) ||
+        (rc = tbuf(c, pg_ctx::TB_ETOT, 16, t.etot)) ||
         (rc = tbuf(c, pg_ctx::TB_GBOXF, ng * 32, t.gboxf)) ||
         (rc = tbuf(c, pg_ctx::TB_NODEW, nnodes * sizeof(TreeNodeW), t.nodew)) ||
         (rc = tbuf(c, pg_ctx::TB_FILT, sizeof(WalkFilter), t.filt)) ||
         (rc = walk_room(c, t, std::max(8 * n, 2 * ng), 0, 0)))
         return rc;
-    PG_CUDA(c, tree_stage_jrec(n, nnodes, lev_off, t, c->stream));
+    PG_CUDA(c, tree_stage_jrec(n, nnodes, lev_off, c->sms, t, c->stream));
     // the walk, one level at a time; the next frontier's size comes back
     // to size its room
     long long lev_v[12] = {0, ng};
@@ -1400,26 +1405,23 @@ int enqueue_tree(pg_ctx *c, double *acc, double *pot)
         nlev = L + 2;
     }
     PG_CUDA(c, tree_walk_lists(ng, lev_v, nlev, t, c->sort, c->stream));
-    long long nlist = 0;
-    unsigned long long etot = 0;
-    if ((rc = read_dev(c, &nlist, t.j_off + ng, sizeof(long long))) ||
-        (rc = read_dev(c, &etot, t.etot, sizeof etot)))
-        return rc;
-    if (etot >= (1ull << 32) || (unsigned long long)nlist != etot)
+    unsigned long long ent[2] = {0, 0};      // 64-bit entry sum, list length
+    if ((rc = read_dev(c, ent, t.etot, sizeof ent))) return rc;
+    const long long nlist = (long long)ent[1];
+    if (ent[0] >= (1ull << 32) || ent[1] != ent[0])
         return fail(c, PG_EINVAL, "tree interaction lists too long: raise theta or lower ncrit");
     if ((rc = tbuf(c, pg_ctx::TB_JLIST, nlist * 4, t.jlist))) return rc;
     PG_CUDA(c, tree_walk_fill(n, ng, lev_v, nlev, t, (int *)c->status.p, c->stream));
     const int Bi = groups_bi(groups_np(c));
     if ((rc = tbuf(c, pg_ctx::TB_ITEMOFF, (ng + 1) * 4, t.item_off)) ||
         (rc = tbuf(c, pg_ctx::TB_ITEMS, (ng + n / Bi + 1) * sizeof(GroupItem), t.items)) ||
-        (rc = tbuf(c, pg_ctx::TB_PAIRS, 8, t.pairs)))
+        (rc = tbuf(c, pg_ctx::TB_PAIRS, 16, t.pairs)))
         return rc;
     PG_CUDA(c, tree_stage_records(n, nnodes, ng, Bi, t, c->sort, c->stream));
-    unsigned long long pairs = 0;
-    if ((rc = read_dev(c, runs + 12, t.runs_dev + 12, sizeof(unsigned))) ||
-        (rc = read_dev(c, &pairs, t.pairs, 8)))
-        return rc;
-    const long long nitems = runs[12];
+    unsigned long long pi[2] = {0, 0};       // pairs, work items
+    if ((rc = read_dev(c, pi, t.pairs, sizeof pi))) return rc;
+    const unsigned long long pairs = pi[0];
+    const long long nitems = (long long)pi[1];
     const long long nj = n + t.npseudo * nnodes;
     if ((rc = ensure(c, c->g_jhl, (size_t)nj * 32)) || (rc = ensure(c, c->g_ihl, (size_t)n * 32)) ||
         (rc = ensure(c, c->g_ctr, (size_t)std::max<long long>(ng, 1) * 32)) ||

@@ -225,7 +225,8 @@ struct TreeScratch {
     double *geo;                // 4: root corner and span
     unsigned *key, *perm;       // n: keys in key order, key order -> input index
     double4 *xs, *xi0;          // n: particles in key order (x, m), (x, 0)
-    unsigned *scan;             // 11 (n + 1): run starts per level, exclusive scans
+    unsigned *scan;             // 11 (n + 1) + 1: run flags of every level, scanned into node indices
+    unsigned *tsums;            // scan sums for it
     unsigned *runs_dev;         // 16: runs per level, then groups, items
     int *first, *count, *child0, *childn;   // nnodes
     unsigned char *lev;         // nnodes
@@ -238,6 +239,8 @@ struct TreeScratch {
     TreeNodeW *nodew;           // nnodes
     double4 *com;               // nnodes: centre of mass (S / M, M)
     double *T;                  // 6 nnodes: second moments (quadrupole pseudo-particles)
+    int *big_list;              // nnodes: nodes of three or more particles (quadrupole)
+    unsigned *nbig;             // 1: their count
     int npseudo;                // pseudo-particles per node: 1 or 3
     WalkFilter *filt;           // 1
     long long *i_off;           // groups + 1
@@ -247,7 +250,7 @@ struct TreeScratch {
     double4 *jrec2;             // n + P nnodes: particles, then pseudo-particles
     unsigned *item_off;         // groups + 1
     GroupItem *items;
-    unsigned long long *pairs;  // 1
+    unsigned long long *pairs;  // 2: pairs, work items
     // the walk: one (group, node) pair per visit, all levels
     int *vg, *vk;               // visits: group, node (~node once accepted)
     unsigned *ve;               // visits + 1: entries per decision, then scanned
@@ -255,15 +258,15 @@ struct TreeScratch {
     unsigned *vsums;            // scan sums for the visit arrays
     unsigned *seg;              // 2 * 11 * groups: visit span [first, end) per level and group
     long long *base;            // 11 * groups: list position shift per group and level
-    unsigned long long *etot;   // 1: 64-bit total of the entries
+    unsigned long long *etot;   // 2: 64-bit total of the entries, list length
     int launches;               // kernels the stages launched
 };
 cudaError_t tree_stage_keys(const double4 *jrec, long long n, TreeScratch &t, SortScratch &sort,
                             cudaStream_t st);
 cudaError_t tree_stage_nodes(long long n, const long long *lev_off, int ncrit, TreeScratch &t,
                              SortScratch &sort, cudaStream_t st);
-cudaError_t tree_stage_jrec(long long n, long long nnodes, const long long *lev_off, TreeScratch &t,
-                            cudaStream_t st);
+cudaError_t tree_stage_jrec(long long n, long long nnodes, const long long *lev_off, int sms,
+                            TreeScratch &t, cudaStream_t st);
 // the walk, level by level: init takes the groups' boxes and puts every
 // group at the root; level L
 // decides its frontier (visits [o, o + nf)) and scans the opened children,

@@ -138,41 +138,65 @@ __global__ void k_tree_gather(const double4 *__restrict__ x, const unsigned *__r
 }
 
 // flag[i] = 1 where a run of equal 3L-bit prefix starts; flag[n] = 0
-__global__ void k_tree_flags(const unsigned *__restrict__ key, long long n, int sh,
-                             unsigned *__restrict__ flag)
+// Level L's run flags sit in scan[L (n + 1) .. L (n + 1) + n] (a 1 at each
+// run's first particle, 0 at position n), and one more 0 ends the array.
+// One exclusive scan over the whole array numbers every node: the entry at a
+// run's first particle is the runs of all lower levels plus the runs of its
+// own level before it, its node index.
+struct LevelOffsets {
+    long long o[kLevels + 1];  // nodes of level L: [o[L], o[L + 1])
+};
+
+__global__ void k_tree_flags(const unsigned *__restrict__ key, long long n, unsigned *__restrict__ scan)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int L = blockIdx.y;
     if (i > n) return;
+    const int sh = 3 * (kBits - L);
+    unsigned *flag = scan + (long long)L * (n + 1);
     flag[i] = i == n ? 0u : (i == 0 || (key[i] >> sh) != (key[i - 1] >> sh)) ? 1u : 0u;
+    if (L == kLevels - 1 && i == n) scan[(long long)kLevels * (n + 1)] = 0u;
 }
 
-// after the exclusive scan of the flags: each run's first particle, and
-// (below) the counts and children
+// runs per level, for the host
+__global__ void k_tree_level_runs(const unsigned *__restrict__ scan, long long n, unsigned *__restrict__ runs)
+{
+    const int L = threadIdx.x;
+    if (L < kLevels) runs[L] = scan[(long long)(L + 1) * (n + 1)] - scan[(long long)L * (n + 1)];
+}
+
+// each run's first particle, every level
 __global__ void k_tree_starts(const unsigned *__restrict__ key, const unsigned *__restrict__ scan,
-                              long long n, int sh, long long off, int *__restrict__ first)
+                              long long n, int *__restrict__ first)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int L = blockIdx.y;
     if (i >= n) return;
-    if (i == 0 || (key[i] >> sh) != (key[i - 1] >> sh)) first[off + scan[i]] = (int)i;
+    const int sh = 3 * (kBits - L);
+    if (i == 0 || (key[i] >> sh) != (key[i - 1] >> sh)) first[scan[(long long)L * (n + 1) + i]] = (int)i;
 }
 
-// run id at level L of particle i: the inclusive scan minus one = scan[i + 1] - 1
-__global__ void k_tree_nodes(long long off, long long runs, long long n,
-                             const unsigned *__restrict__ scan_next, long long off_next, int level,
+// counts, levels and children, every level: the children of a node with
+// particles [f, e) are the next level's runs from the one at f to the one
+// at e
+__global__ void k_tree_nodes(LevelOffsets lo, long long n, const unsigned *__restrict__ scan,
                              int *__restrict__ first, int *__restrict__ count,
                              int *__restrict__ child0, int *__restrict__ childn,
                              unsigned char *__restrict__ lev)
 {
     const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int L = blockIdx.y;
+    const long long runs = lo.o[L + 1] - lo.o[L];
     if (r >= runs) return;
-    const long long k = off + r;
+    const long long k = lo.o[L] + r;
     const int f = first[k];
     const int e = r + 1 < runs ? first[k + 1] : (int)n;
     count[k] = e - f;
-    lev[k] = (unsigned char)level;
-    if (scan_next) {
-        child0[k] = (int)(off_next + scan_next[f]);
-        childn[k] = (int)(scan_next[e] - scan_next[f]);
+    lev[k] = (unsigned char)L;
+    if (L + 1 < kLevels) {
+        const unsigned *next = scan + (long long)(L + 1) * (n + 1);
+        child0[k] = (int)next[f];
+        childn[k] = (int)(next[e] - next[f]);
     } else {
         child0[k] = 0;
         childn[k] = 0;
@@ -223,21 +247,24 @@ __global__ void k_tree_moments_up(long long off, long long runs, const int *__re
 }
 
 // group marks at their first particle: gat[i] = node, else -1 (set before)
-__global__ void k_tree_group_marks(long long off, long long runs, int level,
-                                   const unsigned *__restrict__ scan_prev, long long off_prev,
+// groups: nodes with at most ncrit particles whose parent (the previous
+// level's node holding the first particle) has more, and finest-level nodes
+// whose parent has more; marked at their first particle, every level
+__global__ void k_tree_group_marks(LevelOffsets lo, long long n, const unsigned *__restrict__ scan,
                                    const int *__restrict__ first, const int *__restrict__ count,
                                    int ncrit, int *__restrict__ gat)
 {
     const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (r >= runs) return;
-    const long long k = off + r;
+    const int L = blockIdx.y;
+    if (r >= lo.o[L + 1] - lo.o[L]) return;
+    const long long k = lo.o[L] + r;
     long long pc = -1;
-    if (level > 0) {
-        const long long p = off_prev + scan_prev[first[k] + 1] - 1;
+    if (L > 0) {
+        const long long p = (long long)scan[(long long)(L - 1) * (n + 1) + first[k] + 1] - 1;
         pc = count[p];
     }
-    const bool grp = (count[k] <= ncrit && (level == 0 || pc > ncrit)) ||
-                     (level == kLevels - 1 && pc > ncrit);
+    const bool grp = (count[k] <= ncrit && (L == 0 || pc > ncrit)) ||
+                     (L == kLevels - 1 && pc > ncrit);
     if (grp) gat[first[k]] = (int)k;
 }
 
@@ -483,13 +510,17 @@ __global__ void k_walk_count(long long ngroups, int nlev, const unsigned *__rest
 // order to the list position
 __global__ void k_walk_base(long long ngroups, int nlev, const unsigned *__restrict__ jscan,
                             const unsigned *__restrict__ seg, const unsigned *__restrict__ ve,
-                            long long *__restrict__ j_off, long long *__restrict__ base)
+                            long long *__restrict__ j_off, long long *__restrict__ base,
+                            unsigned long long *__restrict__ etot)
 {
     const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (g > ngroups) return;
     long long off = jscan[g];
     j_off[g] = off;
-    if (g == ngroups) return;
+    if (g == ngroups) {
+        etot[1] = (unsigned long long)off;    // the list length, beside the entry sum
+        return;
+    }
     for (int L = 0; L < nlev; ++L) {
         const unsigned s0 = ve[seg[(2 * L) * ngroups + g]], s1 = ve[seg[(2 * L + 1) * ngroups + g]];
         base[L * ngroups + g] = off - (long long)s0;
@@ -625,43 +656,13 @@ __device__ __forceinline__ void jacobi_rotate(double (&a)[3][3], double (&v)[3][
     }
 }
 
-// the quadrupole pseudo-particles (Kawai and Makino's three): with T's
-// eigenvalues l1 >= l2 >= l3 and unit eigenvectors e1, e2 (e1's largest
-// component positive), mass M / 3 at c + a e1 and c - a/2 e1 +- (sqrt 3 / 2)
-// b e2, a = sqrt(2 (l1 - l3) / M), b = sqrt(2 (l2 - l3) / M); they carry M,
-// a zero dipole and T - l3 I (the trace-free quadrupole of T)
-__global__ void k_tree_quad(long long nnodes, const double4 *__restrict__ com,
-                            const double *__restrict__ T, double4 *__restrict__ out)
+// the three pseudo-particles of node k from its centre c, the spreads a, b
+// along the unit principal axes e1, e2 (e1's sign set here: its largest
+// component positive), mass M / 3 each
+__device__ __forceinline__ void write_quad(double4 *out, long long k, double4 c, double al, double be,
+                                           double e1x, double e1y, double e1z, double e2x, double e2y,
+                                           double e2z)
 {
-    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (k >= nnodes) return;
-    const double4 c = com[k];
-    const double *t = T + 6 * k;
-    double a[3][3] = {{t[0], t[1], t[2]}, {t[1], t[3], t[4]}, {t[2], t[4], t[5]}};
-    double v[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
-    for (int sweep = 0; sweep < 12; ++sweep) {
-        const double off = fabs(a[0][1]) + fabs(a[0][2]) + fabs(a[1][2]);
-        if (!(off > 1e-18 * (fabs(a[0][0]) + fabs(a[1][1]) + fabs(a[2][2])))) break;
-        jacobi_rotate(a, v, 0, 1, 2);
-        jacobi_rotate(a, v, 0, 2, 1);
-        jacobi_rotate(a, v, 1, 2, 0);
-    }
-    // selects instead of indexing keep the arrays in registers
-    const double lam0 = a[0][0], lam1 = a[1][1], lam2 = a[2][2];
-    int i1 = 0, i3 = 0;
-    if (lam1 > lam0) i1 = 1;
-    if (lam2 > (i1 ? lam1 : lam0)) i1 = 2;
-    if (lam1 < lam0) i3 = 1;
-    if (lam2 < (i3 ? lam1 : lam0)) i3 = 2;
-    if (i1 == i3) i3 = i1 == 2 ? 0 : i1 + 1;
-    const int i2 = 3 - i1 - i3;
-    auto pick = [](int i, double x0, double x1, double x2) { return i == 0 ? x0 : i == 1 ? x1 : x2; };
-    const double l1 = pick(i1, lam0, lam1, lam2), l2 = pick(i2, lam0, lam1, lam2),
-                 l3 = pick(i3, lam0, lam1, lam2);
-    double e1x = pick(i1, v[0][0], v[0][1], v[0][2]), e1y = pick(i1, v[1][0], v[1][1], v[1][2]),
-           e1z = pick(i1, v[2][0], v[2][1], v[2][2]);
-    const double e2x = pick(i2, v[0][0], v[0][1], v[0][2]), e2y = pick(i2, v[1][0], v[1][1], v[1][2]),
-                 e2z = pick(i2, v[2][0], v[2][1], v[2][2]);
     double big = e1x;
     if (fabs(e1y) > fabs(big)) big = e1y;
     if (fabs(e1z) > fabs(big)) big = e1z;
@@ -670,16 +671,98 @@ __global__ void k_tree_quad(long long nnodes, const double4 *__restrict__ com,
         e1y = -e1y;
         e1z = -e1z;
     }
-    const double M = c.w;
-    const double al = sqrt(2.0 * fmax(l1 - l3, 0.0) / M);
-    const double be = sqrt(2.0 * fmax(l2 - l3, 0.0) / M);
     const double hb = 0.8660254037844386 * be;      // sqrt(3) / 2, rounded
-    const double m3 = M / 3.0;
+    const double m3 = c.w / 3.0;
     const double ax = al * e1x, ay = al * e1y, az = al * e1z;
     const double bx = hb * e2x, by = hb * e2y, bz = hb * e2z;
     out[3 * k] = make_double4(c.x + ax, c.y + ay, c.z + az, m3);
     out[3 * k + 1] = make_double4(c.x - 0.5 * ax + bx, c.y - 0.5 * ay + by, c.z - 0.5 * az + bz, m3);
     out[3 * k + 2] = make_double4(c.x - 0.5 * ax - bx, c.y - 0.5 * ay - by, c.z - 0.5 * az - bz, m3);
+}
+
+// The quadrupole pseudo-particles (Kawai and Makino's three): with T's
+// eigenvalues l1 >= l2 >= l3 and unit eigenvectors e1, e2, mass M / 3 at
+// c + a e1 and c - a/2 e1 +- (sqrt 3 / 2) b e2, a = sqrt(2 (l1 - l3) / M),
+// b = sqrt(2 (l2 - l3) / M); they carry M, a zero dipole and T - l3 I (the
+// trace-free quadrupole of T). Nodes of one or two particles have them in
+// closed form (one: T = 0, all three at c; two: T = (m1 m2 / M) d d^T with
+// d = x2 - x1, so e1 = d / |d|, a = |d| sqrt(2 m1 m2) / M, b = 0); the others
+// go to a list for the eigen-solver.
+__global__ void k_tree_quad_small(long long nnodes, const double4 *__restrict__ com,
+                                  const int *__restrict__ first, const int *__restrict__ count,
+                                  const double4 *__restrict__ xs, double4 *__restrict__ out,
+                                  int *__restrict__ big_list, unsigned *__restrict__ nbig)
+{
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    bool big = false;
+    if (k < nnodes) {
+        const double4 c = com[k];
+        const int cnt = count[k];
+        if (cnt == 1) {
+            write_quad(out, k, c, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0, 0.0);
+        } else if (cnt == 2) {
+            const double4 p = xs[first[k]], q = xs[first[k] + 1];
+            const double dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
+            const double dn = sqrt(dx * dx + dy * dy + dz * dz);
+            if (dn > 0.0) {
+                const double al = dn * sqrt(2.0 * p.w * q.w) / c.w;
+                write_quad(out, k, c, al, 0.0, dx / dn, dy / dn, dz / dn, 0.0, 0.0, 0.0);
+            } else {
+                write_quad(out, k, c, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0, 0.0);
+            }
+        } else {
+            big = true;
+        }
+    }
+    // append the other nodes to the list, one atomic per warp
+    const unsigned mask = __ballot_sync(0xffffffffu, big);
+    if (!mask) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(nbig, (unsigned)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (big) big_list[base + __popc(mask & ((1u << lane) - 1u))] = (int)k;
+}
+
+// the listed nodes: T's eigen-decomposition by cyclic Jacobi rotations
+// (grid-stride over the list, whose length is read on the device)
+__global__ void k_tree_quad_big(const int *__restrict__ big_list, const unsigned *__restrict__ nbig,
+                                const double4 *__restrict__ com, const double *__restrict__ T,
+                                double4 *__restrict__ out)
+{
+    const long long nb = *nbig;
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < nb;
+         w += (long long)gridDim.x * blockDim.x) {
+        const long long k = big_list[w];
+        const double4 c = com[k];
+        const double *t = T + 6 * k;
+        double a[3][3] = {{t[0], t[1], t[2]}, {t[1], t[3], t[4]}, {t[2], t[4], t[5]}};
+        double v[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+        for (int sweep = 0; sweep < 12; ++sweep) {
+            const double off = fabs(a[0][1]) + fabs(a[0][2]) + fabs(a[1][2]);
+            if (!(off > 1e-18 * (fabs(a[0][0]) + fabs(a[1][1]) + fabs(a[2][2])))) break;
+            jacobi_rotate(a, v, 0, 1, 2);
+            jacobi_rotate(a, v, 0, 2, 1);
+            jacobi_rotate(a, v, 1, 2, 0);
+        }
+        // selects instead of indexing keep the arrays in registers
+        const double lam0 = a[0][0], lam1 = a[1][1], lam2 = a[2][2];
+        int i1 = 0, i3 = 0;
+        if (lam1 > lam0) i1 = 1;
+        if (lam2 > (i1 ? lam1 : lam0)) i1 = 2;
+        if (lam1 < lam0) i3 = 1;
+        if (lam2 < (i3 ? lam1 : lam0)) i3 = 2;
+        if (i1 == i3) i3 = i1 == 2 ? 0 : i1 + 1;
+        const int i2 = 3 - i1 - i3;
+        auto pick = [](int i, double x0, double x1, double x2) { return i == 0 ? x0 : i == 1 ? x1 : x2; };
+        const double l1 = pick(i1, lam0, lam1, lam2), l2 = pick(i2, lam0, lam1, lam2),
+                     l3 = pick(i3, lam0, lam1, lam2);
+        const double al = sqrt(2.0 * fmax(l1 - l3, 0.0) / c.w);
+        const double be = sqrt(2.0 * fmax(l2 - l3, 0.0) / c.w);
+        write_quad(out, k, c, al, be, pick(i1, v[0][0], v[0][1], v[0][2]), pick(i1, v[1][0], v[1][1], v[1][2]),
+                   pick(i1, v[2][0], v[2][1], v[2][2]), pick(i2, v[0][0], v[0][1], v[0][2]),
+                   pick(i2, v[1][0], v[1][1], v[1][2]), pick(i2, v[2][0], v[2][1], v[2][2]));
+    }
 }
 
 // items: the groups cut into chunks of at most Bi particles; pairs = sum ni nj
@@ -736,34 +819,27 @@ cudaError_t tree_stage_keys(const double4 *jrec, long long n, TreeScratch &t, So
     unsigned *ko = nullptr, *perm = nullptr;
     cudaError_t e = launch_radix_sort(sort.keys[0], sort.vals[0], n, 3 * kBits, sort, &ko, &perm, st);
     if (e != cudaSuccess) return e;
-    t.launches += 4 + (n > 0 ? (3 * kBits + 7) / 8 * 5 : 0) + 1 + kLevels;   // with the gather below
+    t.launches += 4 + (n > 0 ? (3 * kBits + 7) / 8 * 5 : 0) + 3;   // with the gather, flags, runs
     cudaMemcpyAsync(t.key, ko, n * sizeof(unsigned), cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(t.perm, perm, n * sizeof(unsigned), cudaMemcpyDeviceToDevice, st);
     k_tree_gather<<<blocks_of(n), 256, 0, st>>>(jrec, t.perm, n, t.xs, t.xi0);
-    // the run flags and their scans, every level
-    for (int L = 0; L < kLevels; ++L) {
-        unsigned *sc = t.scan + (size_t)L * (n + 1);
-        k_tree_flags<<<blocks_of(n + 1), 256, 0, st>>>(t.key, n, 3 * (kBits - L), sc);
-        if ((e = scan(t, sc, n + 1, sort.sums, st)) != cudaSuccess) return e;
-        cudaMemcpyAsync(t.runs_dev + L, sc + n, sizeof(unsigned), cudaMemcpyDeviceToDevice, st);
-    }
+    // every level's run flags, one scan numbering all nodes
+    k_tree_flags<<<dim3(blocks_of(n + 1), kLevels), 256, 0, st>>>(t.key, n, t.scan);
+    if ((e = scan(t, t.scan, (long long)kLevels * (n + 1) + 1, t.tsums, st)) != cudaSuccess) return e;
+    k_tree_level_runs<<<1, 32, 0, st>>>(t.scan, n, t.runs_dev);
     return cudaGetLastError();
 }
 
 cudaError_t tree_stage_nodes(long long n, const long long *lev_off, int ncrit, TreeScratch &t,
                              SortScratch &sort, cudaStream_t st)
 {
-    for (int L = 0; L < kLevels; ++L) {
-        const unsigned *sc = t.scan + (size_t)L * (n + 1);
-        k_tree_starts<<<blocks_of(n), 256, 0, st>>>(t.key, sc, n, 3 * (kBits - L), lev_off[L], t.first);
-    }
-    for (int L = 0; L < kLevels; ++L) {
-        const long long runs = lev_off[L + 1] - lev_off[L];
-        const unsigned *next = L + 1 < kLevels ? t.scan + (size_t)(L + 1) * (n + 1) : nullptr;
-        k_tree_nodes<<<blocks_of(runs), 256, 0, st>>>(lev_off[L], runs, n, next,
-                                                      L + 1 < kLevels ? lev_off[L + 1] : 0, L,
-                                                      t.first, t.count, t.child0, t.childn, t.lev);
-    }
+    LevelOffsets lo;
+    long long widest = 1;
+    for (int L = 0; L <= kLevels; ++L) lo.o[L] = lev_off[L];
+    for (int L = 0; L < kLevels; ++L) widest = std::max(widest, lev_off[L + 1] - lev_off[L]);
+    k_tree_starts<<<dim3(blocks_of(n), kLevels), 256, 0, st>>>(t.key, t.scan, n, t.first);
+    k_tree_nodes<<<dim3(blocks_of(widest), kLevels), 256, 0, st>>>(lo, n, t.scan, t.first, t.count,
+                                                                    t.child0, t.childn, t.lev);
     {
         const long long L = kLevels - 1, runs = lev_off[L + 1] - lev_off[L];
         k_tree_moments_leaf<<<blocks_of(runs), 256, 0, st>>>(lev_off[L], runs, t.first, t.count, t.xs,
@@ -775,15 +851,10 @@ cudaError_t tree_stage_nodes(long long n, const long long *lev_off, int ncrit, T
                                                            t.M, t.S);
     }
     cudaMemsetAsync(t.gat, 0xff, n * sizeof(int), st);
-    for (int L = 0; L < kLevels; ++L) {
-        const long long runs = lev_off[L + 1] - lev_off[L];
-        const unsigned *prev = L > 0 ? t.scan + (size_t)(L - 1) * (n + 1) : nullptr;
-        k_tree_group_marks<<<blocks_of(runs), 256, 0, st>>>(lev_off[L], runs, L, prev,
-                                                            L > 0 ? lev_off[L - 1] : 0, t.first,
-                                                            t.count, ncrit, t.gat);
-    }
+    k_tree_group_marks<<<dim3(blocks_of(widest), kLevels), 256, 0, st>>>(lo, n, t.scan, t.first, t.count,
+                                                                          ncrit, t.gat);
     k_tree_group_flags<<<blocks_of(n + 1), 256, 0, st>>>(t.gat, n, t.gscan);
-    t.launches += 4 * kLevels + 2;     // starts, nodes, moments, marks; flags and groups
+    t.launches += kLevels + 5;         // starts, nodes, moments, marks, flags, groups
     cudaError_t e = scan(t, t.gscan, n + 1, sort.sums, st);
     if (e != cudaSuccess) return e;
     k_tree_groups<<<blocks_of(n + 1), 256, 0, st>>>(t.gat, t.gscan, n, t.count, t.g_i0, t.g_ni,
@@ -849,7 +920,7 @@ cudaError_t tree_walk_lists(long long ngroups, const long long *lev_v, int nlev,
     k_walk_count<<<blocks_of(ngroups + 1), 256, 0, st>>>(ngroups, nlev, t.seg, t.ve, t.jcount);
     if ((e = scan(t, t.jcount, ngroups + 1, sort.sums, st)) != cudaSuccess) return e;
     k_walk_base<<<blocks_of(ngroups + 1), 256, 0, st>>>(ngroups, nlev, t.jcount, t.seg, t.ve, t.j_off,
-                                                        t.base);
+                                                        t.base, t.etot);
     t.launches += 2;
     return cudaGetLastError();
 }
@@ -869,8 +940,8 @@ cudaError_t tree_walk_fill(long long n, long long ngroups, const long long *lev_
 // the j records: particles in key order, then P pseudo-particles per node
 // (monopoles: the centre of mass and mass; quadrupoles: three from the
 // second moments, which are summed bottom-up first); the walk's centres
-cudaError_t tree_stage_jrec(long long n, long long nnodes, const long long *lev_off, TreeScratch &t,
-                            cudaStream_t st)
+cudaError_t tree_stage_jrec(long long n, long long nnodes, const long long *lev_off, int sms,
+                            TreeScratch &t, cudaStream_t st)
 {
     const bool quad = t.npseudo == 3;
     cudaMemcpyAsync(t.jrec2, t.xs, n * sizeof(double4), cudaMemcpyDeviceToDevice, st);
@@ -888,8 +959,12 @@ cudaError_t tree_stage_jrec(long long n, long long nnodes, const long long *lev_
             k_tree_second_up<<<blocks_of(runs), 256, 0, st>>>(lev_off[L], runs, t.child0, t.childn, t.com,
                                                               t.T);
         }
-        k_tree_quad<<<blocks_of(nnodes), 256, 0, st>>>(nnodes, t.com, t.T, t.jrec2 + n);
-        t.launches += kLevels + 1;
+        cudaMemsetAsync(t.nbig, 0, sizeof(unsigned), st);
+        k_tree_quad_small<<<blocks_of(nnodes), 256, 0, st>>>(nnodes, t.com, t.first, t.count, t.xs,
+                                                             t.jrec2 + n, t.big_list, t.nbig);
+        k_tree_quad_big<<<(unsigned)std::max(1, 4 * sms), 128, 0, st>>>(t.big_list, t.nbig, t.com, t.T,
+                                                                       t.jrec2 + n);
+        t.launches += kLevels + 2;
     }
     return cudaGetLastError();
 }
@@ -901,11 +976,10 @@ cudaError_t tree_stage_records(long long n, long long nnodes, long long ngroups,
     t.launches += 2;      // with the items below
     cudaError_t e = scan(t, t.item_off, ngroups + 1, sort.sums, st);
     if (e != cudaSuccess) return e;
-    cudaMemsetAsync(t.pairs, 0, sizeof(unsigned long long), st);
+    cudaMemsetAsync(t.pairs, 0, 2 * sizeof(unsigned long long), st);
     k_tree_items<<<blocks_of(ngroups), 256, 0, st>>>(t.g_i0, t.g_ni, t.item_off, t.j_off, ngroups, Bi,
                                                     t.items, t.pairs);
-    cudaMemcpyAsync(t.runs_dev + kLevels + 1, t.item_off + ngroups, sizeof(unsigned),
-                    cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(t.pairs + 1, t.item_off + ngroups, sizeof(unsigned), cudaMemcpyDeviceToDevice, st);
     return cudaGetLastError();
 }
 
