@@ -4,7 +4,8 @@ TEST INFRASTRUCTURE. Only the tests, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import this package. It wraps the plain C
 files ``pg_oracle.c`` (the force loops, tables and gradients) and
 ``pg_tree.c`` (the grouped tree of the tree usage), built with gcc into
-``liborc.so`` beside them, and shares no code with the CUDA library in
+``liborc.so`` beside them, and the numpy module ``pm`` (the particle-mesh
+long-range force); it shares no code with the CUDA library in
 ``paper_1203_4037_gb300``.
 
 Every function takes and returns numpy FP64 arrays: positions ``(n, 3)``,
@@ -21,6 +22,17 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
+
+# PG_ORACLE_PM names another copy of pm.py (the mutation tests plant
+# mistakes in one), like PG_ORACLE_LIB for the compiled part
+if os.environ.get("PG_ORACLE_PM"):
+    import importlib.util as _ilu
+    import sys as _sys
+
+    _spec = _ilu.spec_from_file_location(__name__ + ".pm", os.environ["PG_ORACLE_PM"])
+    pm = _ilu.module_from_spec(_spec)
+    _sys.modules[__name__ + ".pm"] = pm
+    _spec.loader.exec_module(pm)
 _SRC = os.path.join(_HERE, "pg_oracle.c")
 _SRC_TREE = os.path.join(_HERE, "pg_tree.c")
 _LIB = os.path.join(_HERE, "liborc.so")

@@ -83,6 +83,36 @@ TREE_MUTATIONS = {
 }
 
 
+# mistakes planted in the PM oracle (pm.py), caught by its own pins
+PM_SRC = os.path.join(ROOT, "oracle", "pm.py")
+PM_MUTATIONS = {
+    "TSC centre weight": ("0.75 - d * d", "0.75 - d"),
+    "nearest mesh point floored": ("j0 = np.floor(u + 0.5)", "j0 = np.floor(u)"),
+    "assignment window not divided out": ("phik = rk * green / tsc_window(N)", "phik = rk * green"),
+    "gradient sign": ("np.fft.irfftn(-1j * kk * phik", "np.fft.irfftn(1j * kk * phik"),
+    "Green's function without 4 pi": ("-4.0 * np.pi * split_factor(np.sqrt(k2)", "-1.0 * split_factor(np.sqrt(k2)"),
+    "Gaussian split halved exponent": ("return np.exp(-(k * scale) ** 2)", "return np.exp(-(k * scale) ** 2 / 2)"),
+    "S2 form factor not squared": ("        return out ** 2", "        return out"),
+    "density not per cell volume": ("rho = rho.reshape(N, N, N) / h ** 3", "rho = rho.reshape(N, N, N)"),
+    "k-space sum sign": ("c = -4.0 * np.pi / L ** 3", "c = 4.0 * np.pi / L ** 3"),
+    "S2 series second term": ("qs ** 2 / 15.0", "qs ** 2 / 10.0"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PM_MUTATIONS))
+def test_pins_catch_pm_mutation(name, tmp_path):
+    old, new = PM_MUTATIONS[name]
+    src = open(PM_SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not unique for {name}"
+    mut = tmp_path / "pm_mut.py"
+    mut.write_text(src.replace(old, new))
+    env = dict(os.environ, PG_ORACLE_PM=str(mut))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        "tests/test_oracle_pm.py"], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
+
+
 def _run_pins(tmp_path, name, oracle_src, tree_src):
     mut = tmp_path / "pg_oracle_mut.c"
     mut.write_text(oracle_src)
