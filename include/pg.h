@@ -65,6 +65,10 @@ typedef struct pg_ctx pg_ctx;
 #define PG_PATH_TILED 1   /* i tiles of 256 to 1024 particles, j split across CTAs */
 #define PG_PATH_NARROW 2  /* few i against many j: (i chunk, j chunk) items */
 
+/* long-range split of the particle-mesh part (pg_set_pm) */
+#define PG_SPLIT_GAUSS 0  /* D(k) = exp(-k^2 r_s^2): the erf split of the Gaussian-split PP shape */
+#define PG_SPLIT_S2 1     /* D(k) = S(k a)^2: Hockney and Eastwood's S2 clouds of diameter a */
+
 /* Open a context on CUDA device `device` (g5_open, Section 3.6; no rsqrt
  * bias calibration: the GPU's rsqrt has a documented error bound instead).
  * *out receives the handle; destroy it with pg_destroy. The context starts
@@ -175,6 +179,33 @@ int pg_set_tree_quadrupole(pg_ctx *ctx, int on);
  * breadth first, level by level and in key order within a level). Syncs. */
 int pg_get_tree(pg_ctx *ctx, long long *sizes, long long *perm, long long *g_i0,
                 long long *g_ni, long long *j_off, long long *jlist);
+
+/* The particle-mesh (PM) long-range force of the PPPM and TreePM methods
+ * whose short-range part the arbitrary-shape force loop evaluates (Section
+ * 4.2: PP with f(r) = R(r, eps) - R(r, r_cut) plus PM with R(r, r_cut) make
+ * the full softened force). In the periodic cube of pg_set_periodic (side
+ * L), on an ngrid^3 mesh: TSC mass assignment, FFT, the Green's function
+ * -4 pi D(k) / k^2 with the split factor D (split = PG_SPLIT_GAUSS, scale
+ * = r_s; or PG_SPLIT_S2, scale = the S2 diameter a) divided twice by the
+ * TSC window, the k = 0 mode and the Nyquist planes dropped, spectral
+ * gradient, TSC interpolation. FP32 mesh and FFTs (cuFFT), FP64 in and out.
+ * Once set, a pg_run in the periodic (cell-list) mode returns PP + PM:
+ * the mesh forces at the i-particles from the j-particles are added to the
+ * PP forces (and the mesh potential, which includes each particle's own
+ * smoothed self-potential, to the PP potential). ngrid <= 0 turns it off.
+ * PG_EINVAL for an odd ngrid or one outside 8 .. 1024, another split, or a
+ * scale that is not finite and positive. */
+int pg_set_pm(pg_ctx *ctx, int ngrid, int split, double scale);
+
+/* The PM long-range acceleration a[3 n] and potential phi[n] (may be NULL)
+ * of n particles x[3 n], m[n] on each other, alone (positions are wrapped
+ * into the box). Host arrays; synchronises. PG_ESTATE without pg_set_pm or
+ * pg_set_periodic. */
+int pg_pm_forces(pg_ctx *ctx, const double *x, const double *m, long long n, double *a, double *phi);
+
+/* The same on device arrays (FP64), enqueued on the context's stream. */
+int pg_pm_forces_dev(pg_ctx *ctx, const double *x, const double *m, long long n, double *a,
+                     double *phi);
 
 /* The last tree run's pseudo-particles: rec[4 P nodes] = x, y, z, m (FP64)
  * of pseudo-particle q of node t at 4 (P t + q), host memory the caller

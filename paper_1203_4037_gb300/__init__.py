@@ -23,6 +23,7 @@ from . import _build
 PG_OK, PG_EINVAL, PG_ESTATE, PG_ENOMEM, PG_ECUDA, PG_ETIMEOUT = 0, -1, -2, -3, -4, -5
 PG_NEWTON, PG_TABLE = 0, 1
 PG_PATH_AUTO, PG_PATH_TILED, PG_PATH_NARROW = 0, 1, 2
+PG_SPLIT_GAUSS, PG_SPLIT_S2 = 0, 1
 
 STATUS_NAMES = {0: "PG_OK", -1: "PG_EINVAL", -2: "PG_ESTATE", -3: "PG_ENOMEM", -4: "PG_ECUDA",
                 -5: "PG_ETIMEOUT"}
@@ -72,6 +73,9 @@ SIGNATURES = {
     "pg_set_tree": (_I, [_P, _D, _I, _I]),
     "pg_set_tree_quadrupole": (_I, [_P, _I]),
     "pg_get_tree_pseudo": (_I, [_P, _P]),
+    "pg_set_pm": (_I, [_P, _I, _I, _D]),
+    "pg_pm_forces": (_I, [_P, _P, _P, _LL, _P, _P]),
+    "pg_pm_forces_dev": (_I, [_P, _P, _P, _LL, _P, _P]),
     "pg_get_tree": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "pg_set_timing": (_I, [_P, _I]),
     "pg_kernel_time": (_I, [_P, C.POINTER(_D)]),
@@ -214,6 +218,25 @@ def pg_get_tree_pseudo(ctx, nnodes, npseudo):
     out = np.empty((max(nnodes * npseudo, 1), 4))
     _check(ctx, lib().pg_get_tree_pseudo(ctx, _ptr(out)))
     return out[:nnodes * npseudo]
+
+
+def pg_set_pm(ctx, ngrid, split=PG_SPLIT_GAUSS, scale=0.0):
+    return _check(ctx, lib().pg_set_pm(ctx, int(ngrid), int(split), float(scale)))
+
+
+def pg_pm_forces(ctx, x, m):
+    """The PM long-range acceleration (n, 3) and potential (n,) of host arrays."""
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    m = np.ascontiguousarray(m, dtype=np.float64)
+    a = np.empty_like(x)
+    p = np.empty(len(x))
+    _check(ctx, lib().pg_pm_forces(ctx, _ptr(x), _ptr(m), len(x), _ptr(a), _ptr(p)))
+    return a, p
+
+
+def pg_pm_forces_dev(ctx, x, m, n, a, p=None):
+    return _check(ctx, lib().pg_pm_forces_dev(ctx, _ptr(x), _ptr(m), int(n), _ptr(a),
+                                              _ptr(p) if p is not None else None))
 
 
 def pg_set_eps_i(ctx, eps):
@@ -475,6 +498,16 @@ class Context:
 
     def set_periodic(self, box):
         pg_set_periodic(self.h, box)
+
+    def set_pm(self, ngrid, split=PG_SPLIT_GAUSS, scale=0.0):
+        pg_set_pm(self.h, ngrid, split, scale)
+
+    def pm_forces(self, x, m):
+        return pg_pm_forces(self.h, x, m)
+
+    def pm_forces_dev(self, x, m, a, p=None):
+        _require_dev(x, m, a, *([p] if p is not None else []))
+        pg_pm_forces_dev(self.h, x, m, x.shape[0], a, p)
 
     def set_graph(self, on=True):
         pg_set_graph(self.h, on)

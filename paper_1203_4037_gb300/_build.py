@@ -16,7 +16,7 @@ LIB = os.path.join(HERE, "libpg.so")
 OBJDIR = os.path.join(HERE, "_build")
 
 SOURCES = ["pg_api.cu", "pg_allpairs.cu", "pg_prep.cu", "pg_table.cu", "pg_groups.cu", "pg_tree.cu",
-           "pg_backward.cu", "pg_noalloc.cu", "pg_micro.cu"]
+           "pg_pm.cu", "pg_backward.cu", "pg_noalloc.cu", "pg_micro.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
                 "-I", INCLUDE, "-I", CSRC]
@@ -64,7 +64,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
+    r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcufft"], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)

@@ -86,6 +86,14 @@ struct pg_ctx {
     // tree front end (theta >= 0: on); device buffers by role, sizes of the
     // last build {n, nodes, groups, list entries, items, pseudo-particles per
     // node}
+    // particle-mesh long-range force (pm_n > 0: on): mesh size, split
+    // (0 Gaussian, 1 S2) and its scale; records and buffers of the
+    // stand-alone entry points
+    PmState *pm = nullptr;
+    int pm_n = 0, pm_split = 0;
+    double pm_scale = 0.0;
+    DevBuf pm_rec, pm_x, pm_m, pm_acc, pm_pot;
+
     bool tree_on = false;
     bool tree_quad = false;
     double tree_theta = 0.75;
@@ -434,6 +442,8 @@ void pg_destroy(pg_ctx *c)
                       &c->bw_wt, &c->bw_dv};
     for (DevBuf *b : bufs) free_dev(*b);
     for (DevBuf &b : c->tb) free_dev(b);
+    for (DevBuf *b : {&c->pm_rec, &c->pm_x, &c->pm_m, &c->pm_acc, &c->pm_pot}) free_dev(*b);
+    pm_destroy(c->pm);
     free_pin(c->pin_j);
     free_pin(c->pin_i);
     free_pin(c->pin_o);
@@ -560,6 +570,66 @@ int pg_set_tree_quadrupole(pg_ctx *c, int on)
 {
     if (!c) return PG_EINVAL;
     c->tree_quad = on != 0;
+    return PG_OK;
+}
+
+int pg_set_pm(pg_ctx *c, int ngrid, int split, double scale)
+{
+    if (!c) return PG_EINVAL;
+    if (ngrid <= 0) {
+        if (c->pm_n) drop_graph(c);
+        c->pm_n = 0;
+        return PG_OK;
+    }
+    if (ngrid < 8 || ngrid > 1024 || (ngrid & 1))
+        return fail(c, PG_EINVAL, "the PM mesh needs an even size from 8 to 1024");
+    if (split != PG_SPLIT_GAUSS && split != PG_SPLIT_S2)
+        return fail(c, PG_EINVAL, "split must be PG_SPLIT_GAUSS or PG_SPLIT_S2");
+    if (!(scale > 0.0) || !std::isfinite(scale)) return fail(c, PG_EINVAL, "scale must be finite and > 0");
+    if (!c->pm) c->pm = pm_create();
+    c->pm_n = ngrid;
+    c->pm_split = split;
+    c->pm_scale = scale;
+    drop_graph(c);
+    return PG_OK;
+}
+
+int pg_pm_forces_dev(pg_ctx *c, const double *x, const double *m, long long n, double *a, double *phi)
+{
+    if (!c) return PG_EINVAL;
+    if (n < 0 || (n > 0 && (!x || !m || !a))) return fail(c, PG_EINVAL, "bad arrays or count");
+    if (c->pm_n <= 0) return fail(c, PG_ESTATE, "pg_set_pm has not been called");
+    if (!(c->box > 0.0)) return fail(c, PG_ESTATE, "the PM force needs pg_set_periodic");
+    if (n == 0) return PG_OK;
+    int rc;
+    if ((rc = ensure(c, c->pm_rec, (size_t)n * 32))) return rc;
+    PG_CUDA(c, launch_pack_j(x, m, (double4 *)c->pm_rec.p, n, c->stream));
+    std::string err;
+    int launches = 1;
+    rc = pm_run(c->pm, (const double4 *)c->pm_rec.p, n, (const double4 *)c->pm_rec.p, n, c->box, c->pm_n,
+                c->pm_split, c->pm_scale, a, phi, false, c->stream, &launches, err);
+    if (rc) return fail(c, rc, err);
+    c->last_launches = launches;
+    return PG_OK;
+}
+
+int pg_pm_forces(pg_ctx *c, const double *x, const double *m, long long n, double *a, double *phi)
+{
+    if (!c) return PG_EINVAL;
+    if (n < 0 || (n > 0 && (!x || !m || !a))) return fail(c, PG_EINVAL, "bad arrays or count");
+    if (n == 0) return PG_OK;
+    int rc;
+    if ((rc = ensure(c, c->pm_x, (size_t)n * 24)) || (rc = ensure(c, c->pm_m, (size_t)n * 8)) ||
+        (rc = ensure(c, c->pm_acc, (size_t)n * 24)) || (rc = ensure(c, c->pm_pot, (size_t)n * 8)))
+        return rc;
+    PG_CUDA(c, cudaMemcpyAsync(c->pm_x.p, x, (size_t)n * 24, cudaMemcpyHostToDevice, c->stream));
+    PG_CUDA(c, cudaMemcpyAsync(c->pm_m.p, m, (size_t)n * 8, cudaMemcpyHostToDevice, c->stream));
+    if ((rc = pg_pm_forces_dev(c, (const double *)c->pm_x.p, (const double *)c->pm_m.p, n,
+                               (double *)c->pm_acc.p, phi ? (double *)c->pm_pot.p : nullptr)))
+        return rc;
+    PG_CUDA(c, cudaMemcpyAsync(a, c->pm_acc.p, (size_t)n * 24, cudaMemcpyDeviceToHost, c->stream));
+    if (phi) PG_CUDA(c, cudaMemcpyAsync(phi, c->pm_pot.p, (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream));
+    PG_CUDA(c, cudaStreamSynchronize(c->stream));
     return PG_OK;
 }
 
@@ -1597,7 +1667,18 @@ int enqueue_run(pg_ctx *c, double *acc, double *pot)
     }
     if (c->tree_on) return enqueue_tree(c, acc, pot);
     if (c->have_groups) return enqueue_groups(c, acc, pot);
-    if (c->box > 0.0) return enqueue_cells(c, acc, pot);
+    if (c->box > 0.0) {
+        int rc = enqueue_cells(c, acc, pot);
+        if (rc || c->pm_n <= 0 || c->ni <= 0) return rc;
+        // PPPM / TreePM: the mesh's long-range part added to the PP forces
+        std::string err;
+        int launches = 0;
+        rc = pm_run(c->pm, (const double4 *)c->jrec.p, nj_of(c), (const double4 *)c->xi.p, c->ni, c->box,
+                    c->pm_n, c->pm_split, c->pm_scale, acc, pot, true, c->stream, &launches, err);
+        if (rc) return fail(c, rc, err);
+        c->last_launches += launches;
+        return PG_OK;
+    }
     if (use_narrow(c)) return enqueue_narrow(c, acc, pot);
     Plan p;
     plan_allpairs(c, p);
@@ -1616,6 +1697,11 @@ int run_into(pg_ctx *c, double *acc, double *pot)
              c->ctas_per_sm, c->eps, c->self,
              (void *)acc, (void *)pot, c->jrec.p, c->xi.p, c->sort_mode, (int)c->timing,
              c->g_nitems, c->ngroups, c->path * 4 + (c->have_epsi ? 2 : 0) + (c->have_pot ? 1 : 0));
+    if (c->pm_n > 0) {
+        char pk[96];
+        snprintf(pk, sizeof pk, "|pm%d|%d|%.17g", c->pm_n, c->pm_split, c->pm_scale);
+        strncat(key, pk, sizeof key - strlen(key) - 1);
+    }
     if (!c->gexec || c->gkey != key) {
         drop_graph(c);
         // this call runs uncaptured, which also makes every allocation the

@@ -1,0 +1,149 @@
+"""The particle-mesh long-range force on the GPU against the PM oracle (the
+same method in FP64), and PP + PM against the Ewald sum.
+
+Tolerance: the GPU mesh is FP32 (atomic assignment, cuFFT, interpolation),
+so its error is a small multiple of 2^-24 times log2(N^3) of the field's
+typical size: per particle |a_gpu - a_oracle| is compared with the RMS
+acceleration, median <= 1e-5 and max <= 1e-4 (about 10 and 100 times the
+~1e-6 expected).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import gen
+from oracle import pm as opm
+from pgtest import need_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pg():
+    return need_cuda()
+
+
+def rms(a):
+    return float(np.sqrt(np.mean(np.sum(np.asarray(a).reshape(len(a), -1) ** 2, axis=1))))
+
+
+def assert_mesh_parity(a, ao, what):
+    err = np.linalg.norm((a - ao).reshape(len(a), -1), axis=1) / rms(ao)
+    med, mx = float(np.median(err)), float(err.max())
+    assert med <= 1e-5 and mx <= 1e-4, f"{what}: median {med:.2e} max {mx:.2e} of the RMS"
+
+
+@pytest.mark.parametrize("split,N,scale_cells,L", [("gauss", 64, 1.25, 1.0), ("s2", 32, 4.0, 1.0),
+                                                   ("gauss", 48, 1.5, 3.0)])
+def test_pm_matches_the_oracle(pg, split, N, scale_cells, L):
+    x, m = gen.clustered_box(20000, 61, nclump=30, sigma=0.03)
+    x = x * L
+    m = m * np.random.default_rng(3).uniform(0.5, 2.0, len(m))
+    scale = scale_cells * L / N
+    with pg.Context(0) as c:
+        c.set_periodic(L)
+        c.set_pm(N, pg.PG_SPLIT_GAUSS if split == "gauss" else pg.PG_SPLIT_S2, scale)
+        a, p = c.pm_forces(x, m)
+    ao, po = opm.mesh_forces(x, m, L, N, split, scale)
+    assert_mesh_parity(a, ao, "a")
+    assert_mesh_parity(p[:, None], po[:, None], "phi")
+
+
+def test_positions_outside_the_box_wrap(pg):
+    x, m = gen.clustered_box(5000, 62, nclump=10, sigma=0.02)
+    shift = np.random.default_rng(4).integers(-3, 4, size=x.shape).astype(np.float64)
+    with pg.Context(0) as c:
+        c.set_periodic(1.0)
+        c.set_pm(32, pg.PG_SPLIT_GAUSS, 1.25 / 32)
+        a0, _ = c.pm_forces(x, m)
+        a1, _ = c.pm_forces(x + shift, m)
+    assert_mesh_parity(a1, a0, "wrapped")
+
+
+def _table_run(pg, x, m, v, r_cut, E, F, pm_args=None):
+    with pg.Context(0) as c:
+        c.set_mode(pg.PG_TABLE)
+        c.set_table_values(v, r_cut, E, F)
+        c.set_self(True)
+        c.set_periodic(1.0)
+        if pm_args:
+            c.set_pm(*pm_args)
+        a, _ = c.forces(x, x, m)
+    return a
+
+
+def test_run_adds_the_mesh_to_the_pp_forces(pg, orc):
+    # a periodic table-mode run with the mesh set returns PP + PM: the
+    # difference from the PP-only run is the mesh force of the oracle
+    x, m = gen.clustered_box(1 << 15, 63, nclump=20, sigma=0.01)
+    N, rs = 128, 1.25 / 128
+    r_cut, E, F = 4.5 * rs, 4, 8
+    v = orc.table_values(E, F, r_cut, orc.SHAPE_GAUSS_SPLIT, [rs, rs / 16])
+    pp = _table_run(pg, x, m, v, r_cut, E, F)
+    tot = _table_run(pg, x, m, v, r_cut, E, F, (N, pg.PG_SPLIT_GAUSS, rs))
+    ao, _ = opm.mesh_forces(x, m, 1.0, N, "gauss", rs)
+    assert_mesh_parity(tot - pp, ao, "run - PP")
+
+
+def _pp_exact(x, m, shape, r_cut, L=1.0):
+    acc = np.zeros_like(x)
+    for i in range(len(x)):
+        d = x - x[i]
+        d -= L * np.round(d / L)
+        r = np.linalg.norm(d, axis=1)
+        s = (r > 0) & (r < r_cut)
+        acc[i] = np.sum((m[s] * np.array([shape(v) for v in r[s]]))[:, None] * d[s], axis=0)
+    return acc
+
+
+@pytest.mark.parametrize("split", ["gauss", "s2"])
+def test_pp_plus_pm_against_ewald(pg, orc, split):
+    # the paper's check of PP + PM (Section 4.2), here with random particles
+    # in a periodic box: the GPU's tabulated PP plus its mesh against the
+    # exact short-range sum plus the exact k-space sum
+    n, N = 1500, 64
+    rng = np.random.default_rng(64)
+    x = rng.random((n, 3))
+    m = rng.uniform(0.5, 1.5, n)
+    E, F = 4, 8
+    if split == "gauss":
+        rs = 1.25 / N
+        r_cut, scale, eps = 4.5 * rs, rs, rs / 16
+        v = orc.table_values(E, F, r_cut, orc.SHAPE_GAUSS_SPLIT, [rs, eps])
+        def shape(r):
+            return (math.erfc(r / (2 * rs)) + r / (rs * math.sqrt(math.pi)) * math.exp(-r * r / (4 * rs * rs))) / (r * r + eps * eps) ** 1.5
+        sp = pg.PG_SPLIT_GAUSS
+    else:
+        # an S2 diameter the mesh resolves (about 10 cells): the S2 form
+        # factor falls only as k^-8, so at 4 cells the modes beyond the
+        # mesh's Nyquist frequency still hold about 1e-3 of the force
+        r_cut = 0.15
+        scale, eps = r_cut, r_cut / 15
+        v = orc.table_values(E, F, r_cut, orc.SHAPE_S2PP, [eps, r_cut])
+        def shape(r):
+            return (orc.s2_profile(r, eps) - orc.s2_profile(r, r_cut)) / r
+        sp = pg.PG_SPLIT_S2
+    tot = _table_run(pg, x, m, v, r_cut, E, F, (N, sp, scale))
+    ak, _ = opm.kspace_forces(x, m, 1.0, split, scale, 32)
+    ref = _pp_exact(x, m, shape, r_cut) + ak
+    err = np.linalg.norm(tot - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert np.median(err) < 2e-3 and np.percentile(err, 99) < 2e-2
+
+
+def test_pm_errors(pg):
+    x, m = gen.clustered_box(100, 65)
+    with pg.Context(0) as c:
+        with pytest.raises(pg.PGError) as e:
+            c.pm_forces(x, m)                  # no mesh set
+        assert e.value.code == pg.PG_ESTATE
+        c.set_pm(32, pg.PG_SPLIT_GAUSS, 0.04)
+        with pytest.raises(pg.PGError) as e:
+            c.pm_forces(x, m)                  # no periodic box
+        assert e.value.code == pg.PG_ESTATE
+        for bad in ((33, pg.PG_SPLIT_GAUSS, 0.04), (32, 7, 0.04), (32, pg.PG_SPLIT_S2, 0.0), (4, 0, 0.1)):
+            with pytest.raises(pg.PGError) as e:
+                c.set_pm(*bad)
+            assert e.value.code == pg.PG_EINVAL
+        c.set_pm(0)                            # off
