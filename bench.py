@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--shape", default=None,
                     help="np,packed launch shape of the force kernel (default: the library's)")
     ap.add_argument("--workload", default="newton",
-                    choices=["newton", "table", "cells", "groups", "backward", "narrow", "tree"],
+                    choices=["newton", "table", "cells", "groups", "backward", "narrow", "tree", "pm"],
                     help="newton: the headline; the others time one row of the path alone "
                          "(for profiling) and print its measurements")
     ap.add_argument("--model", default="plummer", choices=["plummer", "king"],
@@ -405,6 +405,16 @@ def extra_rows(pg, torch, dev, peak_newton, headline_rate):
                                    "interactions_per_s": rate, "frac_fp32_peak": rate / peak_table,
                                    "call_ms_with_cell_build": call,
                                    "interactions_per_s_with_build": pairs / (call * 1e-3)}
+        # PPPM / TreePM: the same split's long range on a 256^3 mesh (r_s = h),
+        # alone and added to the cell-list PP in one run
+        p = torch.empty_like(md)
+        c.set_pm(256, pg.PG_SPLIT_GAUSS, rs)
+        call_pp_pm = _time_call(torch, lambda: c.run_dev(a), 5, warm=2)
+        pm_ms = _time_call(torch, lambda: c.pm_forces_dev(xd, md, a, p), 5, warm=2)
+        rows["pm_2e21_mesh256_gauss"] = {"ms_per_call": pm_ms, "particles_per_s": n / (pm_ms * 1e-3),
+                                         "mesh": 256, "r_s_over_h": 1.0}
+        rows["pp_plus_pm_2e21_E4F8_mesh256"] = {"ms_per_call": call_pp_pm,
+                                                "particles_per_s": n / (call_pp_pm * 1e-3)}
     del xd, md, a
 
     # 20000 tree-style groups on the clustered 2^22 set, eps = 1e-3
@@ -504,6 +514,19 @@ def run_row(args):
             info = c.info()
         out.update(ni=ni, nj=N_PART, kernel_ms=kms, interactions_per_s=ni * N_PART / (kms * 1e-3),
                    j_chunks=info["slots"])
+    elif args.workload == "pm":
+        # the particle-mesh long range alone on the 2^21 clustered box (or
+        # --n particles), Gaussian split r_s = 1/256 on a 256^3 mesh
+        n = args.n if args.n != N_PART else 1 << 21
+        x, m = gen.clustered_box(n, gen.CONFIG_SEEDS[3])
+        xd, md = torch.tensor(x, device=dev), torch.tensor(m, device=dev)
+        a, p = torch.empty_like(xd), torch.empty_like(md)
+        with pg.Context(0) as c:
+            c.set_stream(st.cuda_stream)
+            c.set_periodic(1.0)
+            c.set_pm(256, pg.PG_SPLIT_GAUSS, 1 / 256)
+            ms = _time_call(torch, lambda: c.pm_forces_dev(xd, md, a, p), args.steps, warm=args.warmup)
+        out.update(n=n, mesh=256, ms_per_call=ms, particles_per_s=n / (ms * 1e-3))
     elif args.workload == "cells":
         n = args.n if args.n != N_PART else 1 << 21
         x, m = gen.clustered_box(n, gen.CONFIG_SEEDS[3])

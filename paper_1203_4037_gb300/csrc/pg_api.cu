@@ -380,6 +380,8 @@ int read_status(pg_ctx *c)
     return PG_OK;
 }
 
+int prep_sort(pg_ctx *c, long long n);   // below, with the tree
+
 }  // namespace
 
 // ====================================================================== API
@@ -602,12 +604,12 @@ int pg_pm_forces_dev(pg_ctx *c, const double *x, const double *m, long long n, d
     if (!(c->box > 0.0)) return fail(c, PG_ESTATE, "the PM force needs pg_set_periodic");
     if (n == 0) return PG_OK;
     int rc;
-    if ((rc = ensure(c, c->pm_rec, (size_t)n * 32))) return rc;
+    if ((rc = ensure(c, c->pm_rec, (size_t)n * 32)) || (rc = prep_sort(c, n))) return rc;
     PG_CUDA(c, launch_pack_j(x, m, (double4 *)c->pm_rec.p, n, c->stream));
     std::string err;
     int launches = 1;
     rc = pm_run(c->pm, (const double4 *)c->pm_rec.p, n, (const double4 *)c->pm_rec.p, n, c->box, c->pm_n,
-                c->pm_split, c->pm_scale, a, phi, false, c->stream, &launches, err);
+                c->pm_split, c->pm_scale, a, phi, false, c->sort, c->stream, &launches, err);
     if (rc) return fail(c, rc, err);
     c->last_launches = launches;
     return PG_OK;
@@ -1386,6 +1388,25 @@ int read_dev(pg_ctx *c, void *dst, const void *src, size_t bytes)
     return PG_OK;
 }
 
+// the radix sort's scratch for n keys, in c->sort
+int prep_sort(pg_ctx *c, long long n)
+{
+    const size_t hn = sort_hist_entries(n);
+    const size_t nb = (std::max<size_t>(hn, (size_t)n + 1) + 4095) / 4096 + 1;
+    int rc;
+    if ((rc = ensure(c, c->skeys0, n * 4)) || (rc = ensure(c, c->skeys1, n * 4)) ||
+        (rc = ensure(c, c->svals0, n * 4)) || (rc = ensure(c, c->svals1, n * 4)) ||
+        (rc = ensure(c, c->shist, hn * 4)) || (rc = ensure(c, c->ssums, nb * 4)))
+        return rc;
+    c->sort.keys[0] = (unsigned *)c->skeys0.p;
+    c->sort.keys[1] = (unsigned *)c->skeys1.p;
+    c->sort.vals[0] = (unsigned *)c->svals0.p;
+    c->sort.vals[1] = (unsigned *)c->svals1.p;
+    c->sort.hist = (unsigned *)c->shist.p;
+    c->sort.sums = (unsigned *)c->ssums.p;
+    return PG_OK;
+}
+
 // The tree front end (Section 5.1's tree usage): build the tree over the
 // particles, walk it per group, and evaluate the lists in the batched-group
 // kernel. The stages size their buffers from counts read back in between,
@@ -1397,11 +1418,7 @@ int enqueue_tree(pg_ctx *c, double *acc, double *pot)
     c->last_pairs = 0;
     if (n == 0) return PG_OK;
     TreeScratch t{};
-    size_t hn = sort_hist_entries(n);
-    size_t nb = (std::max<size_t>(hn, (size_t)n + 1) + 4095) / 4096 + 1;
-    if ((rc = ensure(c, c->skeys0, n * 4)) || (rc = ensure(c, c->skeys1, n * 4)) ||
-        (rc = ensure(c, c->svals0, n * 4)) || (rc = ensure(c, c->svals1, n * 4)) ||
-        (rc = ensure(c, c->shist, hn * 4)) || (rc = ensure(c, c->ssums, nb * 4)) ||
+    if ((rc = prep_sort(c, n)) ||
         (rc = tbuf(c, pg_ctx::TB_BBOX, 48, t.bbox)) || (rc = tbuf(c, pg_ctx::TB_GEO, 32, t.geo)) ||
         (rc = tbuf(c, pg_ctx::TB_KEY, n * 4, t.key)) || (rc = tbuf(c, pg_ctx::TB_PERM, n * 4, t.perm)) ||
         (rc = tbuf(c, pg_ctx::TB_XS, n * 32, t.xs)) || (rc = tbuf(c, pg_ctx::TB_XI0, n * 32, t.xi0)) ||
@@ -1409,12 +1426,6 @@ int enqueue_tree(pg_ctx *c, double *acc, double *pot)
         (rc = tbuf(c, pg_ctx::TB_TSUMS, ((11 * (n + 1) + 1) / 4096 + 2) * 4, t.tsums)) ||
         (rc = tbuf(c, pg_ctx::TB_RUNS, 64, t.runs_dev)))
         return rc;
-    c->sort.keys[0] = (unsigned *)c->skeys0.p;
-    c->sort.keys[1] = (unsigned *)c->skeys1.p;
-    c->sort.vals[0] = (unsigned *)c->svals0.p;
-    c->sort.vals[1] = (unsigned *)c->svals1.p;
-    c->sort.hist = (unsigned *)c->shist.p;
-    c->sort.sums = (unsigned *)c->ssums.p;
     PG_CUDA(c, tree_stage_keys((const double4 *)c->jrec.p, n, t, c->sort, c->stream));
     unsigned runs[16] = {0};
     if ((rc = read_dev(c, runs, t.runs_dev, 11 * sizeof(unsigned)))) return rc;
@@ -1671,10 +1682,11 @@ int enqueue_run(pg_ctx *c, double *acc, double *pot)
         int rc = enqueue_cells(c, acc, pot);
         if (rc || c->pm_n <= 0 || c->ni <= 0) return rc;
         // PPPM / TreePM: the mesh's long-range part added to the PP forces
+        if ((rc = prep_sort(c, std::max<long long>(nj_of(c), c->ni)))) return rc;
         std::string err;
         int launches = 0;
         rc = pm_run(c->pm, (const double4 *)c->jrec.p, nj_of(c), (const double4 *)c->xi.p, c->ni, c->box,
-                    c->pm_n, c->pm_split, c->pm_scale, acc, pot, true, c->stream, &launches, err);
+                    c->pm_n, c->pm_split, c->pm_scale, acc, pot, true, c->sort, c->stream, &launches, err);
         if (rc) return fail(c, rc, err);
         c->last_launches += launches;
         return PG_OK;

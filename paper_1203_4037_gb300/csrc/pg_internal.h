@@ -131,20 +131,6 @@ struct BackwardArgs {
     int *status;
 };
 
-// ---------------------------------------------------------------- PM
-// The particle-mesh long-range force (pg_pm.cu): mesh, plans and tables,
-// kept between calls. pm_run assigns the ns source records (x, y, z, m) to
-// an N^3 mesh over the periodic cube of side L, solves with the split
-// (0: Gaussian exp(-k^2 scale^2), 1: S2 clouds of diameter scale), and
-// writes (or adds) the acceleration (3 per target) and potential (may be
-// null) at the nt target records. Returns a PG_* code, err says what failed.
-struct PmState;
-PmState *pm_create();
-void pm_destroy(PmState *s);
-int pm_run(PmState *s, const double4 *src, long long ns, const double4 *tgt, long long nt, double L, int N,
-           int split, double scale, double *acc, double *pot, bool add, cudaStream_t st, int *launches,
-           std::string &err);
-
 // ---------------------------------------------------------------- launchers
 // all return cudaError_t of the launch
 
@@ -168,6 +154,21 @@ cudaError_t launch_morton_sort(const double4 *xi, long long n, SortScratch &s, u
 cudaError_t launch_radix_sort(unsigned *keys, unsigned *vals, long long n, int key_bits,
                               SortScratch &s, unsigned **keys_out, unsigned **vals_out,
                               cudaStream_t st);
+
+// ---------------------------------------------------------------- PM
+// The particle-mesh long-range force (pg_pm.cu): mesh, plans and tables,
+// kept between calls. pm_run assigns the ns source records (x, y, z, m) to
+// an N^3 mesh over the periodic cube of side L, solves with the split
+// (0: Gaussian exp(-k^2 scale^2), 1: S2 clouds of diameter scale), and
+// writes (or adds) the acceleration (3 per target) and potential (may be
+// null) at the nt target records. Returns a PG_* code, err says what failed.
+struct PmState;
+PmState *pm_create();
+void pm_destroy(PmState *s);
+int pm_run(PmState *s, const double4 *src, long long ns, const double4 *tgt, long long nt, double L, int N,
+           int split, double scale, double *acc, double *pot, bool add, SortScratch &sort, cudaStream_t st,
+           int *launches, std::string &err);
+
 
 // gather i into tile order and compute tile centres
 cudaError_t launch_tile_prep(const double4 *xi, const unsigned *perm, long long n, int Bi,

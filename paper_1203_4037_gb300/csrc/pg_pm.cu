@@ -4,6 +4,8 @@
 // make the full softened force; the Gaussian split pairs the same way).
 //
 // In a periodic cube of side L on an N^3 mesh (points at j h, h = L / N):
+//  0. sources and targets put in mesh order (a radix sort on the nearest
+//     mesh point), so that the threads of a warp share stencil points;
 //  1. TSC assignment: around the nearest mesh point j0 = floor(u + 1/2) of
 //     u = x / h, offset d = u - j0, weights 1/2 (1/2 - d)^2, 3/4 - d^2,
 //     1/2 (1/2 + d)^2 per axis; density m w / h^3, FP32 atomics;
@@ -41,46 +43,91 @@ struct PmState {
     float *field = nullptr;      // 4 N^3
     float *gtab = nullptr;       // 3 (N/2)^2 + 1: G by n^2
     float *wtab = nullptr;       // N: 1 / sinc^6(pi n / N) by index
+    // mesh records (nearest point, FP32 offsets and mass), in input order and
+    // in mesh order
+    int4 *mj_raw = nullptr, *mj_src = nullptr, *mj_tgt = nullptr;
+    float4 *md_raw = nullptr, *md_src = nullptr, *md_tgt = nullptr;
+    unsigned *perm_tgt = nullptr;                     // mesh order -> target index
+    long long cap = 0;
 };
 
 namespace {
 
 __device__ __forceinline__ int wrap_index(int j, int N) { return j < 0 ? j + N : j >= N ? j - N : j; }
 
-// TSC stencil of one coordinate: the nearest point and the three weights
-__device__ __forceinline__ int tsc_axis(double x, double inv_h, int N, float w[3])
+// one coordinate in mesh units: the nearest mesh point j0 in [0, N) and the
+// offset d = u - j0 in [-1/2, 1/2] of u = x / h (FP64; the wrap into the
+// box costs a division only for a coordinate outside it)
+__device__ __forceinline__ int mesh_axis(double x, double inv_h, int N, float &d)
 {
     double u = x * inv_h;
-    u -= N * floor(u / N);                 // into [0, N)
+    if (u < 0.0 || u >= (double)N) u -= N * floor(u / N);
     const double j0 = floor(u + 0.5);
-    const float d = (float)(u - j0);
+    d = (float)(u - j0);
+    const int j = (int)j0;
+    return j >= N ? j - N : j;
+}
+
+__device__ __forceinline__ void tsc_weights(float d, float w[3])
+{
     w[0] = 0.5f * (0.5f - d) * (0.5f - d);
     w[1] = 0.75f - d * d;
     w[2] = 0.5f * (0.5f + d) * (0.5f + d);
-    return (int)j0;                        // 0 .. N
 }
 
-__global__ void k_pm_assign(const double4 *__restrict__ rec, long long n, double inv_h, int N, float vinv,
-                            float *__restrict__ rho)
+__global__ void k_pm_assign(const int4 *__restrict__ mj, const float4 *__restrict__ md, long long n, int N,
+                            float vinv, float *__restrict__ rho)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int4 j = mj[i];
+    const float4 d = md[i];
+    float wx[3], wy[3], wz[3];
+    tsc_weights(d.x, wx);
+    tsc_weights(d.y, wy);
+    tsc_weights(d.z, wz);
+    const float mv = d.w * vinv;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const long long ix = wrap_index(j.x + a - 1, N);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const long long row = (ix * N + wrap_index(j.y + b - 1, N)) * N;
+            const float wab = mv * wx[a] * wy[b];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) atomicAdd(rho + row + wrap_index(j.z + c - 1, N), wab * wz[c]);
+        }
+    }
+}
+
+// mesh order: a record's key is the row-major index of its nearest mesh
+// point, so that neighbouring threads share stencil points; the mesh record
+// (point; offsets and mass) is written here once, in input order
+__global__ void k_pm_keys(const double4 *__restrict__ rec, long long n, double inv_h, int N,
+                          unsigned *__restrict__ keys, unsigned *__restrict__ vals, int4 *__restrict__ mj,
+                          float4 *__restrict__ md)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double4 v = rec[i];
-    float wx[3], wy[3], wz[3];
-    const int jx = tsc_axis(v.x, inv_h, N, wx), jy = tsc_axis(v.y, inv_h, N, wy),
-              jz = tsc_axis(v.z, inv_h, N, wz);
-    const float mv = (float)v.w * vinv;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const long long ix = wrap_index(jx + a - 1, N);
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            const long long row = (ix * N + wrap_index(jy + b - 1, N)) * N;
-            const float wab = mv * wx[a] * wy[b];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) atomicAdd(rho + row + wrap_index(jz + c - 1, N), wab * wz[c]);
-        }
-    }
+    float dx, dy, dz;
+    const int jx = mesh_axis(v.x, inv_h, N, dx), jy = mesh_axis(v.y, inv_h, N, dy),
+              jz = mesh_axis(v.z, inv_h, N, dz);
+    keys[i] = ((unsigned)jx * (unsigned)N + (unsigned)jy) * (unsigned)N + (unsigned)jz;
+    vals[i] = (unsigned)i;
+    mj[i] = make_int4(jx, jy, jz, 0);
+    md[i] = make_float4(dx, dy, dz, (float)v.w);
+}
+
+__global__ void k_pm_gather(const int4 *__restrict__ mj, const float4 *__restrict__ md,
+                            const unsigned *__restrict__ perm, long long n, int4 *__restrict__ mj_out,
+                            float4 *__restrict__ md_out)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const unsigned p = perm[i];
+    mj_out[i] = mj[p];
+    md_out[i] = md[p];
 }
 
 // the four spectra of every mode (index t over N x N x (N/2 + 1), z fastest)
@@ -108,16 +155,20 @@ __global__ void k_pm_green(const float2 *__restrict__ rk, int N, float kf, const
     spec[3 * M + t] = make_float2(pr, pi);
 }
 
-__global__ void k_pm_interp(const double4 *__restrict__ rec, long long n, double inv_h, int N,
+__global__ void k_pm_interp(const int4 *__restrict__ mj, const float4 *__restrict__ md,
+                            const unsigned *__restrict__ perm, long long n, int N,
                             const float *__restrict__ field, double *__restrict__ acc,
                             double *__restrict__ pot, int add)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double4 v = rec[i];
+    const int4 j = mj[i];
+    const float4 d = md[i];
     float wx[3], wy[3], wz[3];
-    const int jx = tsc_axis(v.x, inv_h, N, wx), jy = tsc_axis(v.y, inv_h, N, wy),
-              jz = tsc_axis(v.z, inv_h, N, wz);
+    tsc_weights(d.x, wx);
+    tsc_weights(d.y, wy);
+    tsc_weights(d.z, wz);
+    const int jx = j.x, jy = j.y, jz = j.z;
     const long long N3 = (long long)N * N * N;
     float s[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -136,8 +187,9 @@ __global__ void k_pm_interp(const double4 *__restrict__ rec, long long n, double
             }
         }
     }
-    for (int q = 0; q < 3; ++q) acc[3 * i + q] = add ? acc[3 * i + q] + (double)s[q] : (double)s[q];
-    if (pot) pot[i] = add ? pot[i] + (double)s[3] : (double)s[3];
+    const long long o = perm[i];             // the target's own index
+    for (int q = 0; q < 3; ++q) acc[3 * o + q] = add ? acc[3 * o + q] + (double)s[q] : (double)s[q];
+    if (pot) pot[o] = add ? pot[o] + (double)s[3] : (double)s[3];
 }
 
 unsigned blocks256(long long n) { return (unsigned)((std::max(n, 1LL) + 255) / 256); }
@@ -148,11 +200,16 @@ void release(PmState &s)
     if (s.have_c2r) cufftDestroy(s.c2r);
     s.have_r2c = s.have_c2r = false;
     for (void *p : {(void *)s.rho, (void *)s.rk, (void *)s.spec, (void *)s.field, (void *)s.gtab,
-                    (void *)s.wtab})
+                    (void *)s.wtab, (void *)s.mj_raw, (void *)s.mj_src, (void *)s.mj_tgt, (void *)s.md_raw,
+                    (void *)s.md_src, (void *)s.md_tgt, (void *)s.perm_tgt})
         if (p) cudaFree(p);
     s.rho = nullptr;
     s.rk = s.spec = nullptr;
     s.field = s.gtab = s.wtab = nullptr;
+    s.mj_raw = s.mj_src = s.mj_tgt = nullptr;
+    s.md_raw = s.md_src = s.md_tgt = nullptr;
+    s.perm_tgt = nullptr;
+    s.cap = 0;
     s.N = 0;
     s.split = -1;
 }
@@ -177,8 +234,8 @@ void pm_destroy(PmState *s)
 }
 
 int pm_run(PmState *s, const double4 *src, long long ns, const double4 *tgt, long long nt, double L, int N,
-           int split, double scale, double *acc, double *pot, bool add, cudaStream_t st, int *launches,
-           std::string &err)
+           int split, double scale, double *acc, double *pot, bool add, SortScratch &sort, cudaStream_t st,
+           int *launches, std::string &err)
 {
     const int nz2 = N / 2 + 1;
     const long long N3 = (long long)N * N * N, M = (long long)N * N * nz2;
@@ -244,14 +301,62 @@ int pm_run(PmState *s, const double4 *src, long long ns, const double4 *tgt, lon
         s->scale = scale;
         s->L = L;
     }
+    const long long need = std::max(ns, nt);
+    if (need > s->cap) {
+        for (void *p : {(void *)s->mj_raw, (void *)s->mj_src, (void *)s->mj_tgt, (void *)s->md_raw,
+                        (void *)s->md_src, (void *)s->md_tgt, (void *)s->perm_tgt})
+            if (p) cudaFree(p);
+        s->mj_raw = s->mj_src = s->mj_tgt = nullptr;
+        s->md_raw = s->md_src = s->md_tgt = nullptr;
+        s->perm_tgt = nullptr;
+        s->cap = 0;
+        bool ok = true;
+        for (int4 **p : {&s->mj_raw, &s->mj_src, &s->mj_tgt})
+            ok = ok && cudaMalloc(p, need * sizeof(int4)) == cudaSuccess;
+        for (float4 **p : {&s->md_raw, &s->md_src, &s->md_tgt})
+            ok = ok && cudaMalloc(p, need * sizeof(float4)) == cudaSuccess;
+        ok = ok && cudaMalloc(&s->perm_tgt, need * sizeof(unsigned)) == cudaSuccess;
+        if (!ok) {
+            (void)cudaGetLastError();
+            err = "PM record allocation failed";
+            return PG_ENOMEM;
+        }
+        s->cap = need;
+    }
     const double inv_h = N / L;
     const float vinv = (float)((double)N3 / (L * L * L));     // 1 / h^3
+    int key_bits = 1;
+    while (key_bits < 32 && (1ull << key_bits) < (unsigned long long)N3) ++key_bits;
+    // sources and targets in mesh order (one sort when they are the same records)
+    auto order = [&](const double4 *rec, long long n, int4 *mj_out, float4 *md_out,
+                     unsigned *perm_keep) -> cudaError_t {
+        k_pm_keys<<<blocks256(n), 256, 0, st>>>(rec, n, inv_h, N, sort.keys[0], sort.vals[0], s->mj_raw,
+                                                s->md_raw);
+        unsigned *ko = nullptr, *perm = nullptr;
+        cudaError_t e = launch_radix_sort(sort.keys[0], sort.vals[0], n, key_bits, sort, &ko, &perm, st);
+        if (e != cudaSuccess) return e;
+        k_pm_gather<<<blocks256(n), 256, 0, st>>>(s->mj_raw, s->md_raw, perm, n, mj_out, md_out);
+        if (perm_keep) cudaMemcpyAsync(perm_keep, perm, n * sizeof(unsigned), cudaMemcpyDeviceToDevice, st);
+        if (launches) *launches += 2 + (key_bits + 7) / 8 * 5;
+        return cudaGetLastError();
+    };
+    const bool same = src == tgt && ns == nt;
+    cudaError_t oe = order(src, ns, s->mj_src, s->md_src, same ? s->perm_tgt : nullptr);
+    if (oe == cudaSuccess && !same) oe = order(tgt, nt, s->mj_tgt, s->md_tgt, s->perm_tgt);
+    if (oe != cudaSuccess) {
+        err = cudaGetErrorString(oe);
+        return PG_ECUDA;
+    }
     if (cufftSetStream(s->r2c, st) != CUFFT_SUCCESS || cufftSetStream(s->c2r, st) != CUFFT_SUCCESS) {
         err = "cufftSetStream failed";
         return PG_ECUDA;
     }
     cudaMemsetAsync(s->rho, 0, N3 * sizeof(float), st);
-    k_pm_assign<<<blocks256(ns), 256, 0, st>>>(src, ns, inv_h, N, vinv, s->rho);
+    // the deposit reads the sources in input order (raw records from the
+    // last order() of the sources): in mesh order neighbouring threads add
+    // to the same cells and the atomics serialise
+    k_pm_assign<<<blocks256(ns), 256, 0, st>>>(same ? s->mj_raw : s->mj_src, same ? s->md_raw : s->md_src, ns,
+                                               N, vinv, s->rho);
     if (cufftExecR2C(s->r2c, s->rho, (cufftComplex *)s->rk) != CUFFT_SUCCESS) {
         err = "cufftExecR2C failed";
         return PG_ECUDA;
@@ -261,7 +366,8 @@ int pm_run(PmState *s, const double4 *src, long long ns, const double4 *tgt, lon
         err = "cufftExecC2R failed";
         return PG_ECUDA;
     }
-    k_pm_interp<<<blocks256(nt), 256, 0, st>>>(tgt, nt, inv_h, N, s->field, acc, pot, add ? 1 : 0);
+    k_pm_interp<<<blocks256(nt), 256, 0, st>>>(same ? s->mj_src : s->mj_tgt, same ? s->md_src : s->md_tgt,
+                                               s->perm_tgt, nt, N, s->field, acc, pot, add ? 1 : 0);
     if (launches) *launches += 3;      // the library's FFT kernels are not counted
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
