@@ -147,3 +147,21 @@ def test_pm_errors(pg):
                 c.set_pm(*bad)
             assert e.value.code == pg.PG_EINVAL
         c.set_pm(0)                            # off
+
+
+def test_pm_edge_cases(pg):
+    with pg.Context(0) as c:
+        c.set_periodic(1.0)
+        c.set_pm(16, pg.PG_SPLIT_GAUSS, 1.25 / 16)
+        a, p = c.pm_forces(np.zeros((0, 3)), np.zeros(0))      # no particles
+        assert a.shape == (0, 3)
+        # zero masses: no field anywhere
+        x, _ = gen.clustered_box(500, 66)
+        a, p = c.pm_forces(x, np.zeros(500))
+        assert np.all(a == 0) and np.all(p == 0)
+        # one particle: the oracle's mesh gives the same (tiny) self-force
+        x1, m1 = np.array([[0.37, 0.52, 0.81]]), np.array([1.0])
+        a, p = c.pm_forces(x1, m1)
+    ao, po = opm.mesh_forces(x1, m1, 1.0, 16, "gauss", 1.25 / 16)
+    assert np.allclose(a, ao, rtol=1e-4, atol=1e-5 * np.abs(po).max())
+    assert np.allclose(p, po, rtol=1e-4)

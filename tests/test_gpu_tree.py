@@ -205,3 +205,27 @@ def test_king_model(pg, orc, quad):
     ao, po = orc.tree_forces(x, m, 1e-3, 0.75, 64, 8, quadrupole=quad)
     assert_parity(rel_vec(a, ao), what="a")
     assert_parity(rel_scalar(p, po), what="phi")
+
+
+@pytest.mark.parametrize("quad", [False, True])
+def test_tiny_and_degenerate_sets(pg, orc, quad):
+    # one particle (no force), two, all coincident (zero extent: the root
+    # side falls back to 1 and one finest cell holds every particle), and a
+    # huge theta (every node that may be accepted is)
+    cases = [(np.array([[0.3, -0.2, 0.1]]), np.array([2.0]), 0.75),
+             (np.array([[0.0, 0.0, 0.0], [0.5, 0.25, -0.5]]), np.array([1.0, 3.0]), 0.75),
+             (np.tile(np.array([[0.1, 0.2, 0.3]]), (300, 1)), np.full(300, 1.0 / 300), 0.75)]
+    x, m = gen.plummer(3000, 91)
+    cases.append((x, m, 50.0))
+    for x, m, theta in cases:
+        a, p, t, _ = gpu_tree(pg, x, m, 0.01, theta, 16, 4, quadrupole=quad)
+        o = orc.tree_build(x, m, theta, 16, 4, quadrupole=quad)
+        same_lists(t, o)
+        ao, po = orc.tree_forces(x, m, 0.01, theta, 16, 4, quadrupole=quad)
+        if len(x) == 1 or np.all(x == x[0]):
+            # no other particle, or every pair at distance 0: zero force
+            assert np.all(a == 0) and np.all(ao == 0)
+            assert np.allclose(p, po, rtol=1e-6, atol=1e-9)
+            continue
+        assert_parity(rel_vec(a, ao), what="a")
+        assert_parity(rel_scalar(p, po), what="phi")
