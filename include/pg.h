@@ -207,6 +207,19 @@ int pg_pm_forces(pg_ctx *ctx, const double *x, const double *m, long long n, dou
 int pg_pm_forces_dev(pg_ctx *ctx, const double *x, const double *m, long long n, double *a,
                      double *phi);
 
+/* The mesh force in two steps, for particles split across ranks (each rank
+ * deposits its own particles, the ranks sum the meshes, and each solves for
+ * its own). pg_pm_deposit_dev writes the density of n particles (device
+ * FP64 x[3 n], m[n]) into rho: ngrid^3 FP32 values in device memory the
+ * caller owns, row-major with z fastest, mass per cell volume.
+ * pg_pm_solve_dev takes such a mesh (summed over ranks; it is not changed)
+ * and writes the acceleration a[3 n] and potential phi[n] (may be NULL) at
+ * n positions x[3 n]. Deposit then solve on the same particles equals
+ * pg_pm_forces_dev. Enqueued on the context's stream; PG_ESTATE without
+ * pg_set_pm or pg_set_periodic. */
+int pg_pm_deposit_dev(pg_ctx *ctx, const double *x, const double *m, long long n, float *rho);
+int pg_pm_solve_dev(pg_ctx *ctx, const float *rho, const double *x, long long n, double *a, double *phi);
+
 /* The last tree run's pseudo-particles: rec[4 P nodes] = x, y, z, m (FP64)
  * of pseudo-particle q of node t at 4 (P t + q), host memory the caller
  * owns. Syncs. */

@@ -117,16 +117,21 @@ def tsc_window(N):
     return s6(f)[:, None, None] * s6(f)[None, :, None] * s6(fr)[None, None, :]
 
 
-def mesh_forces(x, m, L, N, split, scale):
-    """The PM long-range acceleration (n, 3) and potential (n,) of every
-    particle, FP64, by the steps listed in the module docstring."""
+def deposit(x, m, L, N):
+    """Step 1: the TSC density mesh (N, N, N) of particles x, m (mass per
+    cell volume)."""
     x = np.asarray(x, dtype=np.float64)
     m = np.asarray(m, dtype=np.float64)
     h = L / N
     idx, wt = _stencil(x, L, N)
     rho = np.zeros(N ** 3)
     np.add.at(rho, idx.ravel(), (wt * m[:, None]).ravel())
-    rho = rho.reshape(N, N, N) / h ** 3
+    return rho.reshape(N, N, N) / h ** 3
+
+
+def solve(rho, t, L, N, split, scale):
+    """Steps 2-5: from a density mesh to the acceleration (n, 3) and
+    potential (n,) at the points t."""
     rk = np.fft.rfftn(rho)
     n = np.fft.fftfreq(N) * N
     nr = np.arange(N // 2 + 1)
@@ -143,5 +148,12 @@ def mesh_forces(x, m, L, N, split, scale):
     phik = rk * green / tsc_window(N)
     fields = [np.fft.irfftn(-1j * kk * phik, s=(N, N, N), axes=(0, 1, 2)) for kk in (kx, ky, kz)]
     fields.append(np.fft.irfftn(phik, s=(N, N, N), axes=(0, 1, 2)))
+    idx, wt = _stencil(t, L, N)
     out = [np.sum(f.ravel()[idx] * wt, axis=1) for f in fields]
     return np.stack(out[:3], axis=1), out[3]
+
+
+def mesh_forces(x, m, L, N, split, scale):
+    """The PM long-range acceleration (n, 3) and potential (n,) of every
+    particle, FP64, by the steps listed in the module docstring."""
+    return solve(deposit(x, m, L, N), x, L, N, split, scale)

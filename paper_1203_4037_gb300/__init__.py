@@ -76,6 +76,8 @@ SIGNATURES = {
     "pg_set_pm": (_I, [_P, _I, _I, _D]),
     "pg_pm_forces": (_I, [_P, _P, _P, _LL, _P, _P]),
     "pg_pm_forces_dev": (_I, [_P, _P, _P, _LL, _P, _P]),
+    "pg_pm_deposit_dev": (_I, [_P, _P, _P, _LL, _P]),
+    "pg_pm_solve_dev": (_I, [_P, _P, _P, _LL, _P, _P]),
     "pg_get_tree": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "pg_set_timing": (_I, [_P, _I]),
     "pg_kernel_time": (_I, [_P, C.POINTER(_D)]),
@@ -237,6 +239,15 @@ def pg_pm_forces(ctx, x, m):
 def pg_pm_forces_dev(ctx, x, m, n, a, p=None):
     return _check(ctx, lib().pg_pm_forces_dev(ctx, _ptr(x), _ptr(m), int(n), _ptr(a),
                                               _ptr(p) if p is not None else None))
+
+
+def pg_pm_deposit_dev(ctx, x, m, n, rho):
+    return _check(ctx, lib().pg_pm_deposit_dev(ctx, _ptr(x), _ptr(m), int(n), _ptr(rho)))
+
+
+def pg_pm_solve_dev(ctx, rho, x, n, a, p=None):
+    return _check(ctx, lib().pg_pm_solve_dev(ctx, _ptr(rho), _ptr(x), int(n), _ptr(a),
+                                             _ptr(p) if p is not None else None))
 
 
 def pg_set_eps_i(ctx, eps):
@@ -508,6 +519,41 @@ class Context:
     def pm_forces_dev(self, x, m, a, p=None):
         _require_dev(x, m, a, *([p] if p is not None else []))
         pg_pm_forces_dev(self.h, x, m, x.shape[0], a, p)
+
+    def pm_deposit_dev(self, x, m, rho):
+        """Density mesh (ngrid^3 FP32 CUDA tensor) of these particles."""
+        _require_dev(x, m)
+        pg_pm_deposit_dev(self.h, x, m, x.shape[0], rho)
+
+    def pm_solve_dev(self, rho, x, a, p=None):
+        """Mesh forces at x from a density mesh (summed over ranks)."""
+        _require_dev(x, a, *([p] if p is not None else []))
+        pg_pm_solve_dev(self.h, rho, x, x.shape[0], a, p)
+
+    def pm_forces_sharded(self, x, m, ngrid, group=None):
+        """Mesh forces of this rank's particles (CUDA tensors) when the
+        particles are split across the ranks of torch.distributed: the
+        density meshes are summed with one all-reduce."""
+        import torch
+        import torch.distributed as dist
+        from .multirank import mesh_forces_sharded
+
+        def deposit(xl, ml):
+            rho = torch.empty(ngrid ** 3, dtype=torch.float32, device=xl.device)
+            self.pm_deposit_dev(xl, ml, rho)
+            return rho
+
+        def solve(rho, xl):
+            a = torch.empty_like(xl)
+            p = torch.empty(xl.shape[0], dtype=xl.dtype, device=xl.device)
+            self.pm_solve_dev(rho, xl, a, p)
+            return a, p
+
+        def all_reduce(rho):
+            if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+                dist.all_reduce(rho, group=group)
+
+        return mesh_forces_sharded(deposit, solve, all_reduce, x, m)
 
     def set_graph(self, on=True):
         pg_set_graph(self.h, on)

@@ -615,6 +615,44 @@ int pg_pm_forces_dev(pg_ctx *c, const double *x, const double *m, long long n, d
     return PG_OK;
 }
 
+int pg_pm_deposit_dev(pg_ctx *c, const double *x, const double *m, long long n, float *rho)
+{
+    if (!c) return PG_EINVAL;
+    if (n < 0 || (n > 0 && (!x || !m)) || !rho) return fail(c, PG_EINVAL, "bad arrays or count");
+    if (c->pm_n <= 0) return fail(c, PG_ESTATE, "pg_set_pm has not been called");
+    if (!(c->box > 0.0)) return fail(c, PG_ESTATE, "the PM force needs pg_set_periodic");
+    int rc;
+    const long long nn = std::max<long long>(n, 1);
+    if ((rc = ensure(c, c->pm_rec, (size_t)nn * 32)) || (rc = prep_sort(c, nn))) return rc;
+    if (n > 0) PG_CUDA(c, launch_pack_j(x, m, (double4 *)c->pm_rec.p, n, c->stream));
+    std::string err;
+    int launches = n > 0 ? 1 : 0;
+    rc = pm_deposit(c->pm, (const double4 *)c->pm_rec.p, n, c->box, c->pm_n, c->pm_split, c->pm_scale, rho,
+                    c->sort, c->stream, &launches, err);
+    if (rc) return fail(c, rc, err);
+    c->last_launches = launches;
+    return PG_OK;
+}
+
+int pg_pm_solve_dev(pg_ctx *c, const float *rho, const double *x, long long n, double *a, double *phi)
+{
+    if (!c) return PG_EINVAL;
+    if (n < 0 || (n > 0 && (!x || !a)) || !rho) return fail(c, PG_EINVAL, "bad arrays or count");
+    if (c->pm_n <= 0) return fail(c, PG_ESTATE, "pg_set_pm has not been called");
+    if (!(c->box > 0.0)) return fail(c, PG_ESTATE, "the PM force needs pg_set_periodic");
+    if (n == 0) return PG_OK;
+    int rc;
+    if ((rc = ensure(c, c->pm_rec, (size_t)n * 32)) || (rc = prep_sort(c, n))) return rc;
+    PG_CUDA(c, launch_pack_i(x, (double4 *)c->pm_rec.p, n, c->stream));
+    std::string err;
+    int launches = 1;
+    rc = pm_solve(c->pm, rho, (const double4 *)c->pm_rec.p, n, c->box, c->pm_n, c->pm_split, c->pm_scale, a,
+                  phi, false, c->sort, c->stream, &launches, err);
+    if (rc) return fail(c, rc, err);
+    c->last_launches = launches;
+    return PG_OK;
+}
+
 int pg_pm_forces(pg_ctx *c, const double *x, const double *m, long long n, double *a, double *phi)
 {
     if (!c) return PG_EINVAL;

@@ -168,6 +168,15 @@ void pm_destroy(PmState *s);
 int pm_run(PmState *s, const double4 *src, long long ns, const double4 *tgt, long long nt, double L, int N,
            int split, double scale, double *acc, double *pot, bool add, SortScratch &sort, cudaStream_t st,
            int *launches, std::string &err);
+// the same in two steps, for sources split across ranks: pm_deposit writes
+// the density mesh of its sources into rho (N^3 FP32, row-major, z fastest;
+// mass per cell volume), which the ranks sum; pm_solve computes the fields
+// from a (summed) mesh and interpolates them at its targets
+int pm_deposit(PmState *s, const double4 *src, long long ns, double L, int N, int split, double scale,
+               float *rho, SortScratch &sort, cudaStream_t st, int *launches, std::string &err);
+int pm_solve(PmState *s, const float *rho, const double4 *tgt, long long nt, double L, int N, int split,
+             double scale, double *acc, double *pot, bool add, SortScratch &sort, cudaStream_t st,
+             int *launches, std::string &err);
 
 
 // gather i into tile order and compute tile centres

@@ -45,8 +45,8 @@ struct PmState {
     float *wtab = nullptr;       // N: 1 / sinc^6(pi n / N) by index
     // mesh records (nearest point, FP32 offsets and mass), in input order and
     // in mesh order
-    int4 *mj_raw = nullptr, *mj_src = nullptr, *mj_tgt = nullptr;
-    float4 *md_raw = nullptr, *md_src = nullptr, *md_tgt = nullptr;
+    int4 *mj_raw = nullptr, *mj_tgt = nullptr;
+    float4 *md_raw = nullptr, *md_tgt = nullptr;
     unsigned *perm_tgt = nullptr;                     // mesh order -> target index
     long long cap = 0;
 };
@@ -200,14 +200,14 @@ void release(PmState &s)
     if (s.have_c2r) cufftDestroy(s.c2r);
     s.have_r2c = s.have_c2r = false;
     for (void *p : {(void *)s.rho, (void *)s.rk, (void *)s.spec, (void *)s.field, (void *)s.gtab,
-                    (void *)s.wtab, (void *)s.mj_raw, (void *)s.mj_src, (void *)s.mj_tgt, (void *)s.md_raw,
-                    (void *)s.md_src, (void *)s.md_tgt, (void *)s.perm_tgt})
+                    (void *)s.wtab, (void *)s.mj_raw, (void *)s.mj_tgt, (void *)s.md_raw, (void *)s.md_tgt,
+                    (void *)s.perm_tgt})
         if (p) cudaFree(p);
     s.rho = nullptr;
     s.rk = s.spec = nullptr;
     s.field = s.gtab = s.wtab = nullptr;
-    s.mj_raw = s.mj_src = s.mj_tgt = nullptr;
-    s.md_raw = s.md_src = s.md_tgt = nullptr;
+    s.mj_raw = s.mj_tgt = nullptr;
+    s.md_raw = s.md_tgt = nullptr;
     s.perm_tgt = nullptr;
     s.cap = 0;
     s.N = 0;
@@ -233,9 +233,10 @@ void pm_destroy(PmState *s)
     delete s;
 }
 
-int pm_run(PmState *s, const double4 *src, long long ns, const double4 *tgt, long long nt, double L, int N,
-           int split, double scale, double *acc, double *pot, bool add, SortScratch &sort, cudaStream_t st,
-           int *launches, std::string &err)
+namespace {
+
+// mesh, plans and tables for (N, split, scale, L); room for n records
+int ensure(PmState *s, double L, int N, int split, double scale, long long n, std::string &err)
 {
     const int nz2 = N / 2 + 1;
     const long long N3 = (long long)N * N * N, M = (long long)N * N * nz2;
@@ -301,80 +302,164 @@ int pm_run(PmState *s, const double4 *src, long long ns, const double4 *tgt, lon
         s->scale = scale;
         s->L = L;
     }
-    const long long need = std::max(ns, nt);
-    if (need > s->cap) {
-        for (void *p : {(void *)s->mj_raw, (void *)s->mj_src, (void *)s->mj_tgt, (void *)s->md_raw,
-                        (void *)s->md_src, (void *)s->md_tgt, (void *)s->perm_tgt})
+    if (n > s->cap) {
+        for (void *p : {(void *)s->mj_raw, (void *)s->mj_tgt, (void *)s->md_raw, (void *)s->md_tgt,
+                        (void *)s->perm_tgt})
             if (p) cudaFree(p);
-        s->mj_raw = s->mj_src = s->mj_tgt = nullptr;
-        s->md_raw = s->md_src = s->md_tgt = nullptr;
+        s->mj_raw = s->mj_tgt = nullptr;
+        s->md_raw = s->md_tgt = nullptr;
         s->perm_tgt = nullptr;
         s->cap = 0;
         bool ok = true;
-        for (int4 **p : {&s->mj_raw, &s->mj_src, &s->mj_tgt})
-            ok = ok && cudaMalloc(p, need * sizeof(int4)) == cudaSuccess;
-        for (float4 **p : {&s->md_raw, &s->md_src, &s->md_tgt})
-            ok = ok && cudaMalloc(p, need * sizeof(float4)) == cudaSuccess;
-        ok = ok && cudaMalloc(&s->perm_tgt, need * sizeof(unsigned)) == cudaSuccess;
+        for (int4 **p : {&s->mj_raw, &s->mj_tgt})
+            ok = ok && cudaMalloc(p, n * sizeof(int4)) == cudaSuccess;
+        for (float4 **p : {&s->md_raw, &s->md_tgt})
+            ok = ok && cudaMalloc(p, n * sizeof(float4)) == cudaSuccess;
+        ok = ok && cudaMalloc(&s->perm_tgt, n * sizeof(unsigned)) == cudaSuccess;
         if (!ok) {
             (void)cudaGetLastError();
             err = "PM record allocation failed";
             return PG_ENOMEM;
         }
-        s->cap = need;
+        s->cap = n;
     }
-    const double inv_h = N / L;
-    const float vinv = (float)((double)N3 / (L * L * L));     // 1 / h^3
-    int key_bits = 1;
-    while (key_bits < 32 && (1ull << key_bits) < (unsigned long long)N3) ++key_bits;
-    // sources and targets in mesh order (one sort when they are the same records)
-    auto order = [&](const double4 *rec, long long n, int4 *mj_out, float4 *md_out,
-                     unsigned *perm_keep) -> cudaError_t {
-        k_pm_keys<<<blocks256(n), 256, 0, st>>>(rec, n, inv_h, N, sort.keys[0], sort.vals[0], s->mj_raw,
-                                                s->md_raw);
-        unsigned *ko = nullptr, *perm = nullptr;
-        cudaError_t e = launch_radix_sort(sort.keys[0], sort.vals[0], n, key_bits, sort, &ko, &perm, st);
-        if (e != cudaSuccess) return e;
-        k_pm_gather<<<blocks256(n), 256, 0, st>>>(s->mj_raw, s->md_raw, perm, n, mj_out, md_out);
-        if (perm_keep) cudaMemcpyAsync(perm_keep, perm, n * sizeof(unsigned), cudaMemcpyDeviceToDevice, st);
-        if (launches) *launches += 2 + (key_bits + 7) / 8 * 5;
-        return cudaGetLastError();
-    };
-    const bool same = src == tgt && ns == nt;
-    cudaError_t oe = order(src, ns, s->mj_src, s->md_src, same ? s->perm_tgt : nullptr);
-    if (oe == cudaSuccess && !same) oe = order(tgt, nt, s->mj_tgt, s->md_tgt, s->perm_tgt);
-    if (oe != cudaSuccess) {
-        err = cudaGetErrorString(oe);
-        return PG_ECUDA;
-    }
+    return PG_OK;
+}
+
+int key_bits_of(int N)
+{
+    const unsigned long long N3 = (unsigned long long)N * N * N;
+    int b = 1;
+    while (b < 32 && (1ull << b) < N3) ++b;
+    return b;
+}
+
+// the mesh records of n records (input order, in mj_raw / md_raw); with
+// sorted, also in mesh order (mj_out / md_out) and perm_keep = mesh order ->
+// input index
+cudaError_t records(PmState *s, const double4 *rec, long long n, bool sorted, int4 *mj_out, float4 *md_out,
+                    unsigned *perm_keep, SortScratch &sort, cudaStream_t st, int *launches)
+{
+    const int N = s->N;
+    k_pm_keys<<<blocks256(n), 256, 0, st>>>(rec, n, N / s->L, N, sort.keys[0], sort.vals[0], s->mj_raw,
+                                            s->md_raw);
+    if (launches) *launches += 1;
+    if (!sorted) return cudaGetLastError();
+    const int kb = key_bits_of(N);
+    unsigned *ko = nullptr, *perm = nullptr;
+    cudaError_t e = launch_radix_sort(sort.keys[0], sort.vals[0], n, kb, sort, &ko, &perm, st);
+    if (e != cudaSuccess) return e;
+    k_pm_gather<<<blocks256(n), 256, 0, st>>>(s->mj_raw, s->md_raw, perm, n, mj_out, md_out);
+    cudaMemcpyAsync(perm_keep, perm, n * sizeof(unsigned), cudaMemcpyDeviceToDevice, st);
+    if (launches) *launches += 1 + (kb + 7) / 8 * 5;
+    return cudaGetLastError();
+}
+
+// the TSC deposit of n records into rho (cleared first). Records in input
+// order: in mesh order neighbouring threads add to the same cells and the
+// atomics serialise
+void deposit(PmState *s, const int4 *mj, const float4 *md, long long n, float *rho, cudaStream_t st,
+             int *launches)
+{
+    const int N = s->N;
+    const long long N3 = (long long)N * N * N;
+    const float vinv = (float)((double)N3 / (s->L * s->L * s->L));     // 1 / h^3
+    cudaMemsetAsync(rho, 0, N3 * sizeof(float), st);
+    k_pm_assign<<<blocks256(n), 256, 0, st>>>(mj, md, n, N, vinv, rho);
+    if (launches) *launches += 1;
+}
+
+// rho -> the four fields (FFT, Green's function, batched inverse FFT)
+int solve_fields(PmState *s, float *rho, cudaStream_t st, int *launches, std::string &err)
+{
+    const int N = s->N;
+    const long long M = (long long)N * N * (N / 2 + 1);
     if (cufftSetStream(s->r2c, st) != CUFFT_SUCCESS || cufftSetStream(s->c2r, st) != CUFFT_SUCCESS) {
         err = "cufftSetStream failed";
         return PG_ECUDA;
     }
-    cudaMemsetAsync(s->rho, 0, N3 * sizeof(float), st);
-    // the deposit reads the sources in input order (raw records from the
-    // last order() of the sources): in mesh order neighbouring threads add
-    // to the same cells and the atomics serialise
-    k_pm_assign<<<blocks256(ns), 256, 0, st>>>(same ? s->mj_raw : s->mj_src, same ? s->md_raw : s->md_src, ns,
-                                               N, vinv, s->rho);
-    if (cufftExecR2C(s->r2c, s->rho, (cufftComplex *)s->rk) != CUFFT_SUCCESS) {
+    if (cufftExecR2C(s->r2c, rho, (cufftComplex *)s->rk) != CUFFT_SUCCESS) {
         err = "cufftExecR2C failed";
         return PG_ECUDA;
     }
-    k_pm_green<<<blocks256(M), 256, 0, st>>>(s->rk, N, (float)(2.0 * M_PI / L), s->gtab, s->wtab, s->spec);
+    k_pm_green<<<blocks256(M), 256, 0, st>>>(s->rk, N, (float)(2.0 * M_PI / s->L), s->gtab, s->wtab, s->spec);
     if (cufftExecC2R(s->c2r, (cufftComplex *)s->spec, s->field) != CUFFT_SUCCESS) {
         err = "cufftExecC2R failed";
         return PG_ECUDA;
     }
-    k_pm_interp<<<blocks256(nt), 256, 0, st>>>(same ? s->mj_src : s->mj_tgt, same ? s->md_src : s->md_tgt,
-                                               s->perm_tgt, nt, N, s->field, acc, pot, add ? 1 : 0);
-    if (launches) *launches += 3;      // the library's FFT kernels are not counted
+    if (launches) *launches += 1;      // cuFFT's own kernels are not counted
+    return PG_OK;
+}
+
+int finish(std::string &err)
+{
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         err = cudaGetErrorString(e);
         return PG_ECUDA;
     }
     return PG_OK;
+}
+
+}  // namespace
+
+int pm_run(PmState *s, const double4 *src, long long ns, const double4 *tgt, long long nt, double L, int N,
+           int split, double scale, double *acc, double *pot, bool add, SortScratch &sort, cudaStream_t st,
+           int *launches, std::string &err)
+{
+    int rc = ensure(s, L, N, split, scale, std::max(ns, nt), err);
+    if (rc) return rc;
+    // the sources deposited in input order; the targets interpolated in mesh
+    // order (one set of records when they are the same particles)
+    const bool same = src == tgt && ns == nt;
+    cudaError_t e = records(s, src, ns, same, s->mj_tgt, s->md_tgt, s->perm_tgt, sort, st, launches);
+    if (e == cudaSuccess) {
+        deposit(s, s->mj_raw, s->md_raw, ns, s->rho, st, launches);
+        if (!same) e = records(s, tgt, nt, true, s->mj_tgt, s->md_tgt, s->perm_tgt, sort, st, launches);
+    }
+    if (e != cudaSuccess) {
+        err = cudaGetErrorString(e);
+        return PG_ECUDA;
+    }
+    if ((rc = solve_fields(s, s->rho, st, launches, err))) return rc;
+    k_pm_interp<<<blocks256(nt), 256, 0, st>>>(s->mj_tgt, s->md_tgt, s->perm_tgt, nt, N, s->field, acc, pot,
+                                               add ? 1 : 0);
+    if (launches) *launches += 1;
+    return finish(err);
+}
+
+int pm_deposit(PmState *s, const double4 *src, long long ns, double L, int N, int split, double scale,
+               float *rho, SortScratch &sort, cudaStream_t st, int *launches, std::string &err)
+{
+    int rc = ensure(s, L, N, split, scale, ns, err);
+    if (rc) return rc;
+    cudaError_t e = records(s, src, ns, false, nullptr, nullptr, nullptr, sort, st, launches);
+    if (e != cudaSuccess) {
+        err = cudaGetErrorString(e);
+        return PG_ECUDA;
+    }
+    deposit(s, s->mj_raw, s->md_raw, ns, rho, st, launches);
+    return finish(err);
+}
+
+int pm_solve(PmState *s, const float *rho, const double4 *tgt, long long nt, double L, int N, int split,
+             double scale, double *acc, double *pot, bool add, SortScratch &sort, cudaStream_t st,
+             int *launches, std::string &err)
+{
+    int rc = ensure(s, L, N, split, scale, nt, err);
+    if (rc) return rc;
+    // the caller's mesh is copied: the forward FFT may not leave its input
+    cudaMemcpyAsync(s->rho, rho, (size_t)N * N * N * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    cudaError_t e = records(s, tgt, nt, true, s->mj_tgt, s->md_tgt, s->perm_tgt, sort, st, launches);
+    if (e != cudaSuccess) {
+        err = cudaGetErrorString(e);
+        return PG_ECUDA;
+    }
+    if ((rc = solve_fields(s, s->rho, st, launches, err))) return rc;
+    k_pm_interp<<<blocks256(nt), 256, 0, st>>>(s->mj_tgt, s->md_tgt, s->perm_tgt, nt, N, s->field, acc, pot,
+                                               add ? 1 : 0);
+    if (launches) *launches += 1;
+    return finish(err);
 }
 
 }  // namespace pg

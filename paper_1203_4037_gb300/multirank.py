@@ -1,9 +1,14 @@
-"""Host logic of the i-range split across ranks (one process per GPU).
+"""Host logic of the work split across ranks (one process per GPU).
 
 Forces on different i-particles are independent, so ranks take contiguous
 i-ranges against the full j-set and exchange nothing on the data path. The
 job's time is the slowest rank's; results, when wanted on one rank, are
 gathered once at the end.
+
+The particle-mesh long range has one real exchange when the particles
+themselves are split: every mesh point takes mass from every rank's
+particles, so the ranks' density meshes are summed (one all-reduce of N^3
+values) before each rank solves for its own particles.
 """
 
 from __future__ import annotations
@@ -45,3 +50,12 @@ def gather_rows(local, n: int, device=None):
     for r, (lo, hi) in enumerate(sizes):
         parts[r] = outs[r][:hi - lo]
     return torch.cat(parts)
+
+
+def mesh_forces_sharded(deposit, solve, all_reduce, x, m):
+    """Mesh forces of this rank's particles x, m: deposit(x, m) gives this
+    rank's density mesh, all_reduce sums the meshes of all ranks in place,
+    and solve(mesh, x) gives the acceleration and potential at x."""
+    rho = deposit(x, m)
+    all_reduce(rho)
+    return solve(rho, x)

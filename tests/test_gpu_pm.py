@@ -165,3 +165,34 @@ def test_pm_edge_cases(pg):
     ao, po = opm.mesh_forces(x1, m1, 1.0, 16, "gauss", 1.25 / 16)
     assert np.allclose(a, ao, rtol=1e-4, atol=1e-5 * np.abs(po).max())
     assert np.allclose(p, po, rtol=1e-4)
+
+
+def test_deposit_and_solve_in_two_steps(pg):
+    # the two-step form of the multi-rank path on one GPU: the meshes of two
+    # halves, summed, solved for all particles, give the one-call forces
+    torch = pytest.importorskip("torch")
+    x, m = gen.clustered_box(20000, 67, nclump=20, sigma=0.02)
+    N = 64
+    dev = torch.device("cuda:0")
+    xd, md = torch.tensor(x, device=dev), torch.tensor(m, device=dev)
+    with pg.Context(0) as c:
+        c.set_periodic(1.0)
+        c.set_pm(N, pg.PG_SPLIT_GAUSS, 1.25 / N)
+        a1 = torch.empty_like(xd)
+        p1 = torch.empty_like(md)
+        c.pm_forces_dev(xd, md, a1, p1)
+        r0 = torch.empty(N ** 3, dtype=torch.float32, device=dev)
+        r1 = torch.empty_like(r0)
+        h = len(x) // 2
+        c.pm_deposit_dev(xd[:h].contiguous(), md[:h].contiguous(), r0)
+        c.pm_deposit_dev(xd[h:].contiguous(), md[h:].contiguous(), r1)
+        a2 = torch.empty_like(xd)
+        p2 = torch.empty_like(md)
+        c.pm_solve_dev(r0 + r1, xd, a2, p2)
+        # the sharded helper on a single rank is the one-call result too
+        a3, p3 = c.pm_forces_sharded(xd, md, N)
+        torch.cuda.synchronize()
+    a1, a2, a3 = a1.cpu().numpy(), a2.cpu().numpy(), a3.cpu().numpy()
+    assert_mesh_parity(a2, a1, "two steps")
+    assert_mesh_parity(p2.cpu().numpy()[:, None], p1.cpu().numpy()[:, None], "two steps phi")
+    assert_mesh_parity(a3, a1, "sharded helper")

@@ -63,3 +63,47 @@ def test_two_gloo_ranks_match_one(tmp_path, orc):
     a, p = orc.newton_allpairs(x, m, 0.05)
     assert np.array_equal(full[:, :3], a) and np.array_equal(full[:, 3], p)
     assert np.load(out + ".t.npy")[0] == 2.0
+
+
+def _pm_worker(rank, world, port, out):
+    # the particle-mesh long range with the particles split across ranks:
+    # each deposits its shard, the density meshes are summed (the one real
+    # exchange), each solves for its own particles; the FP64 mesh oracle
+    # stands in for the GPU steps
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import gen
+    from oracle import pm
+    from paper_1203_4037_gb300.multirank import mesh_forces_sharded
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    x, m = gen.clustered_box(3001, 31, nclump=10, sigma=0.02)
+    lo, hi = shard(len(x), rank, world)
+    N, rs = 32, 1.25 / 32
+
+    def deposit(xl, ml):
+        return torch.from_numpy(pm.deposit(xl, ml, 1.0, N).ravel().copy())
+
+    def solve(rho, xl):
+        return pm.solve(rho.numpy().reshape(N, N, N), xl, 1.0, N, "gauss", rs)
+
+    a, p = mesh_forces_sharded(deposit, solve, dist.all_reduce, x[lo:hi], m[lo:hi])
+    full = gather_rows(torch.tensor(np.concatenate([a, p[:, None]], axis=1)), len(x))
+    if rank == 0:
+        np.save(out, full.numpy())
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_mesh_matches_one_rank(tmp_path, world):
+    import gen
+    from oracle import pm
+    out = str(tmp_path / "pm.npy")
+    mp.spawn(_pm_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+    full = np.load(out)
+    x, m = gen.clustered_box(3001, 31, nclump=10, sigma=0.02)
+    a, p = pm.mesh_forces(x, m, 1.0, 32, "gauss", 1.25 / 32)
+    # only the order of the mesh sums differs
+    assert np.allclose(full[:, :3], a, rtol=1e-10, atol=1e-12 * np.abs(a).max())
+    assert np.allclose(full[:, 3], p, rtol=1e-10, atol=1e-12 * np.abs(p).max())

@@ -93,7 +93,7 @@ PM_MUTATIONS = {
     "Green's function without 4 pi": ("-4.0 * np.pi * split_factor(np.sqrt(k2)", "-1.0 * split_factor(np.sqrt(k2)"),
     "Gaussian split halved exponent": ("return np.exp(-(k * scale) ** 2)", "return np.exp(-(k * scale) ** 2 / 2)"),
     "S2 form factor not squared": ("        return out ** 2", "        return out"),
-    "density not per cell volume": ("rho = rho.reshape(N, N, N) / h ** 3", "rho = rho.reshape(N, N, N)"),
+    "density not per cell volume": ("return rho.reshape(N, N, N) / h ** 3", "return rho.reshape(N, N, N)"),
     "k-space sum sign": ("c = -4.0 * np.pi / L ** 3", "c = 4.0 * np.pi / L ** 3"),
     "S2 series second term": ("qs ** 2 / 15.0", "qs ** 2 / 10.0"),
 }
