@@ -102,7 +102,7 @@ struct pg_ctx {
            TB_CHILD0, TB_CHILDN, TB_LEV, TB_M, TB_S, TB_GAT, TB_GSCAN, TB_GI0, TB_GNI, TB_GBOX,
            TB_IOFF, TB_JCOUNT, TB_JOFF, TB_JLIST, TB_JREC2, TB_ITEMOFF, TB_ITEMS, TB_PAIRS,
            TB_VG, TB_VK, TB_VE, TB_VC, TB_VSUMS, TB_SEG, TB_BASE, TB_ETOT, TB_GBOXF, TB_NODEW,
-           TB_FILT, TB_COM, TB_T, TB_BIG, TB_NBIG, TB_TSUMS, TB_N };
+           TB_FILT, TB_COM, TB_T, TB_BIG, TB_NBIG, TB_TSUMS, TB_HL, TB_N };
     DevBuf tb[TB_N];
     long long tree_sizes[6] = {0, 0, 0, 0, 0, 0};
     long long ngroups = 0;
@@ -1566,7 +1566,14 @@ int enqueue_tree(pg_ctx *c, double *acc, double *pot)
     g.list_self = 1;
     g.acc = acc;
     g.pot = pot;
+    g.ni = n;
+    // the kernel writes FP32 (hi, lo) sums; the finish kernel converts them
+    // on full warps (the FP64 output from each set's first lane was a fifth
+    // of the kernel's pipe time on tree lists)
+    if ((rc = tbuf(c, pg_ctx::TB_HL, n * 32, g.hl))) return rc;
     if ((rc = launch_group_kernel(c, g, false))) return rc;
+    PG_CUDA(c, launch_groups_finish(g, c->stream));
+    c->last_launches += 1;
     c->last_pairs = (long long)pairs;
     c->last_slots = ng;
     c->last_launches += t.launches + 3;     // the stages, then two packs and the centres

@@ -203,7 +203,7 @@ __device__ __forceinline__ void pair_term(float ra, float rb, u64 dx, u64 dy, u6
     }
 }
 
-template <int NP, bool TABLE, bool CELL, bool EXT>
+template <int NP, bool TABLE, bool CELL, bool EXT, bool HL = false>
 __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &it, const ItemShape sh,
                                            u64 *cvt, u64 *run, int *cr, const float2 *tab,
                                            const float4 *dirt, int tid)
@@ -394,6 +394,21 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
                 }
             }
         }
+        if constexpr (HL) {
+            // FP32 (hi, lo) sums out; the finish kernel converts them on full warps
+            if (active && lane == 0) {
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int k_i = set * 2 * NP + 2 * p + q;
+                    if (k_i < it.ni) {
+                        const long long i = it.i0 + k_i;
+                        a.hl[2 * i] = make_float4(h[0 + q], h[2 + q], h[4 + q], h[6 + q]);
+                        a.hl[2 * i + 1] = make_float4(l[0 + q], l[2 + q], l[4 + q], l[6 + q]);
+                    }
+                }
+            }
+            continue;
+        }
         if (active && lane == 0) {
             double v[8];
 #pragma unroll
@@ -434,7 +449,7 @@ constexpr int kWarpTJ = 128;        // j entries per warp-staged tile
 constexpr int kWarpItemNi = 32;     // items up to this size (i-particles)
 constexpr long long kWarpItemPairs = 32768;   // and this many pairs go to warp mode
 
-template <bool TABLE, bool CELL, bool EXT>
+template <bool TABLE, bool CELL, bool EXT, bool HL = false>
 __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cur, int held,
                                           u64 *wcvt, int *wcr, const float2 *tab,
                                           const float4 *dirt, int lane32)
@@ -690,7 +705,12 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
                         vl = tl;
                     }
                 }
-                if (oi < nout) {
+                if (HL && oi < nout) {
+                    float *hlf = reinterpret_cast<float *>(a.hl);
+                    const long long i = it.i0 + i0 + ip;
+                    hlf[8 * i + comp] = vh;
+                    hlf[8 * i + 4 + comp] = vl;
+                } else if (oi < nout) {
                     const long long i = it.i0 + i0 + ip;
                     const double v = (double)vh + (double)vl;
                     if (a.part) {          // one partial of a narrow all-pairs sum
@@ -729,7 +749,7 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
 
 // NPMAX: the largest i-pair count per thread; items whose shape uses the
 // threads better with half of it run with NPMAX / 2
-template <int NPMAX, bool TABLE, bool CELL, bool EXT>
+template <int NPMAX, bool TABLE, bool CELL, bool EXT, bool HL = false>
 __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -779,12 +799,12 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
             const ItemShape big = item_shape(it.ni, NPMAX);
             const ItemShape small = item_shape(it.ni, NPMAX / 2);
             if (small.nsets <= 4 * small.spw && small.nsets * small.L > big.nsets * big.L) {
-                group_item<(NPMAX > 1 ? NPMAX / 2 : 1), TABLE, CELL, EXT>(a, it, small, cvt, run,
+                group_item<(NPMAX > 1 ? NPMAX / 2 : 1), TABLE, CELL, EXT, HL>(a, it, small, cvt, run,
                                                                              cr, tab, dirt, tid);
                 continue;
             }
         }
-        group_item<NPMAX, TABLE, CELL, EXT>(a, it, item_shape(it.ni, NPMAX), cvt, run, cr, tab,
+        group_item<NPMAX, TABLE, CELL, EXT, HL>(a, it, item_shape(it.ni, NPMAX), cvt, run, cr, tab,
                                               dirt, tid);
     }
 
@@ -792,7 +812,7 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
     // prefetched claim; every warp then claims its own items
     __syncthreads();   // no warp still reads the CTA-wide staging buffer
     const int w = tid >> 5, lane32 = tid & 31;
-    warp_loop<TABLE, CELL, EXT>(a, nitems, w == 0 ? first_small : -1,
+    warp_loop<TABLE, CELL, EXT, HL>(a, nitems, w == 0 ? first_small : -1,
                                   (w == 0 && lane32 == 0) ? next : -1,
                                   cvt + w * (2 * 2 * kWarpTJ), cr + w * 2 * kCellTab, tab, dirt,
                                   lane32);
@@ -809,12 +829,12 @@ size_t groups_smem(int np, bool table, int ntab)
 
 int groups_bi(int np) { return kNT * 2 * np; }
 
-template <int NP, bool TABLE, bool CELL, bool EXT>
+template <int NP, bool TABLE, bool CELL, bool EXT, bool HL = false>
 static cudaError_t configure_g()
 {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_groups<NP, TABLE, CELL, EXT>,
+    cudaError_t e = cudaFuncSetAttribute(k_groups<NP, TABLE, CELL, EXT, HL>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)groups_smem(NP, TABLE, 2 << 13));
     done = e == cudaSuccess;
@@ -848,12 +868,12 @@ int groups_max_blocks_per_sm(int np, bool table, int ntab, bool cell, bool ext)
                    : occ_np<2>(table, cell, ext, smem);
 }
 
-template <int NP, bool TABLE, bool CELL, bool EXT>
+template <int NP, bool TABLE, bool CELL, bool EXT, bool HL = false>
 static cudaError_t launch_g(const GroupArgs &g, int grid, size_t smem, cudaStream_t st)
 {
-    cudaError_t e = configure_g<NP, TABLE, CELL, EXT>();
+    cudaError_t e = configure_g<NP, TABLE, CELL, EXT, HL>();
     if (e != cudaSuccess) return e;
-    k_groups<NP, TABLE, CELL, EXT><<<grid, kNT, smem, st>>>(g);
+    k_groups<NP, TABLE, CELL, EXT, HL><<<grid, kNT, smem, st>>>(g);
     return cudaGetLastError();
 }
 
@@ -861,6 +881,11 @@ template <int NP>
 static cudaError_t launch_gnp(const GroupArgs &g, int grid, bool table, bool cell, bool ext,
                               size_t smem, cudaStream_t st)
 {
+    if (g.hl) {   // FP32 outputs: Newton lists only
+        if (table || cell) return cudaErrorInvalidValue;
+        return ext ? launch_g<NP, false, false, true, true>(g, grid, smem, st)
+                   : launch_g<NP, false, false, false, true>(g, grid, smem, st);
+    }
     if (!table) return ext ? launch_g<NP, false, false, true>(g, grid, smem, st)
                            : launch_g<NP, false, false, false>(g, grid, smem, st);
     if (cell) return ext ? launch_g<NP, true, true, true>(g, grid, smem, st)
@@ -878,6 +903,30 @@ cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, bool
     if (np == 2) return launch_gnp<2>(g, grid, table, cell, ext, smem, st);
     if (np == 4) return launch_gnp<4>(g, grid, table, cell, ext, smem, st);
     return cudaErrorInvalidValue;
+}
+
+// the FP64 outputs of a run with FP32 (hi, lo) sums: one thread per i, so
+// the conversions, the permutation and the stores run on full warps
+__global__ void k_groups_finish(GroupArgs a)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= a.ni) return;
+    const float4 h = a.hl[2 * i], l = a.hl[2 * i + 1];
+    const long long o = a.perm ? (long long)a.perm[i] : i;
+    a.acc[3 * o] = ((double)h.x + (double)l.x) * a.accscale;
+    a.acc[3 * o + 1] = ((double)h.y + (double)l.y) * a.accscale;
+    a.acc[3 * o + 2] = ((double)h.z + (double)l.z) * a.accscale;
+    if (a.pot) {
+        const double phi = (double)h.w + (double)l.w;
+        a.pot[o] = a.list_self ? phi - list_self_pot(a, i) : phi;
+    }
+}
+
+cudaError_t launch_groups_finish(const GroupArgs &g, cudaStream_t st)
+{
+    if (g.ni <= 0) return cudaSuccess;
+    k_groups_finish<<<(unsigned)((g.ni + 255) / 256), 256, 0, st>>>(g);
+    return cudaGetLastError();
 }
 
 // Narrow all-pairs: the sum over j chunks of each i's FP64 partials in a

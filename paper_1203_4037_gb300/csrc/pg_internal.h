@@ -111,6 +111,8 @@ struct GroupArgs {
     double accscale;
     double *acc, *pot;
     int *status;
+    float4 *hl = nullptr;  // Newton lists: the sums as FP32 (hi, lo) pairs, two float4 per i
+                           // (x, y, z, phi), converted by the finish kernel (nullptr: FP64 out)
 };
 
 // backward (all-pairs, self mode)
@@ -200,6 +202,8 @@ cudaError_t launch_table_from_values(const float *v, float *G0, float *G1, int E
 
 cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, bool cell, bool ext,
                           size_t smem, cudaStream_t st);
+// the FP64 outputs of a groups run made with g.hl set: one thread per i
+cudaError_t launch_groups_finish(const GroupArgs &g, cudaStream_t st);
 cudaError_t launch_pack_hilo(const double4 *in, long long n, float4 *out, cudaStream_t st);
 size_t groups_smem(int np, bool table, int ntab);   // ntab in float2 units, as above
 int groups_bi(int np);
