@@ -196,3 +196,25 @@ def test_deposit_and_solve_in_two_steps(pg):
     assert_mesh_parity(a2, a1, "two steps")
     assert_mesh_parity(p2.cpu().numpy()[:, None], p1.cpu().numpy()[:, None], "two steps phi")
     assert_mesh_parity(a3, a1, "sharded helper")
+
+
+def test_bench_size_mesh(pg):
+    # the bench's mesh workload (2^21 clustered particles, 256^3, r_s = h):
+    # the oracle's mesh from every particle, solved at a sample of them
+    torch = pytest.importorskip("torch")
+    x, m = gen.clustered_box(1 << 21, gen.CONFIG_SEEDS[3])
+    N, rs = 256, 1.0 / 256
+    dev = torch.device("cuda:0")
+    xd, md = torch.tensor(x, device=dev), torch.tensor(m, device=dev)
+    a = torch.empty_like(xd)
+    p = torch.empty_like(md)
+    with pg.Context(0) as c:
+        c.set_periodic(1.0)
+        c.set_pm(N, pg.PG_SPLIT_GAUSS, rs)
+        c.pm_forces_dev(xd, md, a, p)
+        torch.cuda.synchronize()
+    idx = np.random.default_rng(97).choice(len(x), 2000, replace=False)
+    ao, po = opm.solve(opm.deposit(x, m, 1.0, N), x[idx], 1.0, N, "gauss", rs)
+    a, p = a.cpu().numpy()[idx], p.cpu().numpy()[idx]
+    assert_mesh_parity(a, ao, "a")
+    assert_mesh_parity(p[:, None], po[:, None], "phi")

@@ -229,3 +229,43 @@ def test_tiny_and_degenerate_sets(pg, orc, quad):
             continue
         assert_parity(rel_vec(a, ao), what="a")
         assert_parity(rel_scalar(p, po), what="phi")
+
+
+def _sampled_list_forces(x, m, eps, o, idx):
+    # FP64 sums over each sampled particle's group list, from the oracle's
+    # lists and pseudo-particles (the particle's own entry left out)
+    n = len(x)
+    perm = o["perm"]
+    inv = np.empty(n, np.int64)
+    inv[perm] = np.arange(n)
+    xs, ms = x[perm], m[perm]
+    acc = np.zeros((len(idx), 3))
+    pot = np.zeros(len(idx))
+    for s, i0 in enumerate(idx):
+        k = inv[i0]
+        g = int(np.searchsorted(o["g_i0"], k, side="right") - 1)
+        lst = o["jlist"][o["j_off"][g]:o["j_off"][g + 1]]
+        lst = lst[lst != k]
+        part = lst < n
+        pj = np.where(part[:, None], xs[np.minimum(lst, n - 1)], o["pseudo"][np.maximum(lst - n, 0), :3])
+        mj = np.where(part, ms[np.minimum(lst, n - 1)], o["pseudo"][np.maximum(lst - n, 0), 3])
+        d = pj - xs[k]
+        r2 = np.sum(d * d, axis=1) + eps * eps
+        rinv = 1.0 / np.sqrt(r2)
+        acc[s] = np.sum((mj * rinv ** 3)[:, None] * d, axis=0)
+        pot[s] = -np.sum(mj * rinv)
+    return acc, pot
+
+
+@pytest.mark.parametrize("quad", [False, True])
+def test_large_tree(pg, orc, quad):
+    # 2^22 particles at the bench's settings (theta 0.75, groups of at most
+    # 256): every list bit for bit, forces on a sample of particles
+    x, m = gen.plummer(1 << 22, 95)
+    a, p, t, _ = gpu_tree(pg, x, m, 1e-3, 0.75, 256, 8, quadrupole=quad)
+    o = orc.tree_build(x, m, 0.75, 256, 8, quadrupole=quad)
+    same_lists(t, o)
+    idx = np.random.default_rng(96).choice(len(x), 1000, replace=False)
+    ao, po = _sampled_list_forces(x, m, 1e-3, o, idx)
+    assert_parity(rel_vec(a[idx], ao), what="a")
+    assert_parity(rel_scalar(p[idx], po), what="phi")
