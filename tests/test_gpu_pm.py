@@ -218,3 +218,27 @@ def test_bench_size_mesh(pg):
     a, p = a.cpu().numpy()[idx], p.cpu().numpy()[idx]
     assert_mesh_parity(a, ao, "a")
     assert_mesh_parity(p[:, None], po[:, None], "phi")
+
+
+def test_pp_plus_pm_under_a_graph(pg, orc):
+    # a periodic run with the mesh, captured in a CUDA graph and replayed,
+    # gives the forces of the uncaptured run (up to the FP32 atomics' order)
+    x, m = gen.clustered_box(1 << 14, 68, nclump=10, sigma=0.01)
+    N, rs = 64, 1.25 / 64
+    r_cut, E, F = 4.5 * rs, 4, 8
+    v = orc.table_values(E, F, r_cut, orc.SHAPE_GAUSS_SPLIT, [rs, rs / 16])
+    out = []
+    for graph in (False, True):
+        with pg.Context(0) as c:
+            c.set_mode(pg.PG_TABLE)
+            c.set_table_values(v, r_cut, E, F)
+            c.set_self(True)
+            c.set_periodic(1.0)
+            c.set_pm(N, pg.PG_SPLIT_GAUSS, rs)
+            c.set_graph(graph)
+            c.set_j(x, m)
+            c.set_i(x)
+            for _ in range(3):            # capture, then replays
+                c.run()
+            out.append(c.get_force(len(x))[0])
+    assert_mesh_parity(out[1], out[0], "graph")
