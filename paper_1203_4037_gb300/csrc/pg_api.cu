@@ -1483,23 +1483,23 @@ int enqueue_tree(pg_ctx *c, double *acc, double *pot)
         (rc = tbuf(c, pg_ctx::TB_GSCAN, (n + 1) * 4, t.gscan)) ||
         (rc = tbuf(c, pg_ctx::TB_GI0, n * 4, t.g_i0)) || (rc = tbuf(c, pg_ctx::TB_GNI, n * 4, t.g_ni)) ||
         (rc = tbuf(c, pg_ctx::TB_GBOX, n * 48, t.gbox)) ||
-        (rc = tbuf(c, pg_ctx::TB_IOFF, (n + 1) * 8, t.i_off)))
+        (rc = tbuf(c, pg_ctx::TB_IOFF, (n + 1) * 8, t.i_off)) ||
+        (rc = tbuf(c, pg_ctx::TB_JREC2, (n + t.npseudo * nnodes) * 32, t.jrec2)) ||
+        (rc = tbuf(c, pg_ctx::TB_COM, nnodes * 32, t.com)) ||
+        (rc = tbuf(c, pg_ctx::TB_T, (t.npseudo == 3 ? nnodes : 1) * 48, t.T)) ||
+        (rc = tbuf(c, pg_ctx::TB_NODEW, nnodes * sizeof(TreeNodeW), t.nodew)))
         return rc;
     PG_CUDA(c, tree_stage_nodes(n, lev_off, c->tree_ncrit, t, c->sort, c->stream));
     if ((rc = read_dev(c, runs + 11, t.runs_dev + 11, sizeof(unsigned)))) return rc;
     const long long ng = runs[11];
     if ((rc = tbuf(c, pg_ctx::TB_JCOUNT, (ng + 1) * 4, t.jcount)) ||
         (rc = tbuf(c, pg_ctx::TB_JOFF, (ng + 1) * 8, t.j_off)) ||
-        (rc = tbuf(c, pg_ctx::TB_JREC2, (n + t.npseudo * nnodes) * 32, t.jrec2)) ||
-        (rc = tbuf(c, pg_ctx::TB_COM, nnodes * 32, t.com)) ||
-        (rc = tbuf(c, pg_ctx::TB_T, (t.npseudo == 3 ? nnodes : 1) * 48, t.T)) ||
         (rc = tbuf(c, pg_ctx::TB_BIG, (t.npseudo == 3 ? nnodes : 1) * 4, t.big_list)) ||
         (rc = tbuf(c, pg_ctx::TB_NBIG, 4, t.nbig)) ||
         (rc = tbuf(c, pg_ctx::TB_SEG, 2 * 11 * ng * 4, t.seg)) ||
         (rc = tbuf(c, pg_ctx::TB_BASE, 11 * ng * 8, t.base)) ||
         (rc = tbuf(c, pg_ctx::TB_ETOT, 16, t.etot)) ||
         (rc = tbuf(c, pg_ctx::TB_GBOXF, ng * 32, t.gboxf)) ||
-        (rc = tbuf(c, pg_ctx::TB_NODEW, nnodes * sizeof(TreeNodeW), t.nodew)) ||
         (rc = tbuf(c, pg_ctx::TB_FILT, sizeof(WalkFilter), t.filt)) ||
         (rc = walk_room(c, t, std::max(8 * n, 2 * ng), 0, 0)))
         return rc;

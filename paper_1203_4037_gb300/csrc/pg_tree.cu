@@ -203,16 +203,48 @@ __global__ void k_tree_nodes(LevelOffsets lo, long long n, const unsigned *__res
     }
 }
 
-// monopoles of the finest level from the particles, in key order
+// Per node, once its mass M and first moment S are summed: the centre of
+// mass (S / M, M), the walk's record, with monopoles the pseudo-particle
+// itself, and with quadrupoles the second moment about the centre
+struct NodeOut {
+    double4 *com;        // centre of mass (S / M, M)
+    double4 *mono;       // monopole j records, or nullptr
+    TreeNodeW *nodew;    // the walk's records
+    double *T;           // second moments {xx, xy, xz, yy, yz, zz}, or nullptr
+};
+
+__device__ __forceinline__ double4 node_finish(long long k, double m, double s0, double s1, double s2,
+                                               const int *first, const int *count, const int *child0,
+                                               const int *childn, const NodeOut &o)
+{
+    const double4 c = make_double4(__ddiv_rn(s0, m), __ddiv_rn(s1, m), __ddiv_rn(s2, m), m);
+    o.com[k] = c;
+    if (o.mono) o.mono[k] = c;
+    TreeNodeW w;
+    w.cx = __double2float_rn(c.x);
+    w.cy = __double2float_rn(c.y);
+    w.cz = __double2float_rn(c.z);
+    w.pad = 0.f;
+    w.first = first[k];
+    w.count = count[k];
+    w.child0 = child0[k];
+    w.childn = childn[k];
+    o.nodew[k] = w;
+    return c;
+}
+
+// the finest level from its particles, in key order; T = sum m (x - c)(x - c)^T
 __global__ void k_tree_moments_leaf(long long off, long long runs, const int *__restrict__ first,
-                                    const int *__restrict__ count, const double4 *__restrict__ xs,
-                                    double *__restrict__ M, double *__restrict__ S)
+                                    const int *__restrict__ count, const int *__restrict__ child0,
+                                    const int *__restrict__ childn, const double4 *__restrict__ xs,
+                                    double *__restrict__ M, double *__restrict__ S, NodeOut o)
 {
     const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (r >= runs) return;
     const long long k = off + r;
     double m = 0.0, s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int i = first[k]; i < first[k] + count[k]; ++i) {
+    const int f = first[k], e = f + count[k];
+    for (int i = f; i < e; ++i) {
         const double4 v = xs[i];
         m = __dadd_rn(m, v.w);
         s0 = __dadd_rn(s0, __dmul_rn(v.w, v.x));
@@ -223,27 +255,59 @@ __global__ void k_tree_moments_leaf(long long off, long long runs, const int *__
     S[3 * k] = s0;
     S[3 * k + 1] = s1;
     S[3 * k + 2] = s2;
+    const double4 c = node_finish(k, m, s0, s1, s2, first, count, child0, childn, o);
+    if (!o.T) return;
+    double t[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = f; i < e; ++i) {
+        const double4 v = xs[i];
+        const double y0 = v.x - c.x, y1 = v.y - c.y, y2 = v.z - c.z;
+        t[0] += v.w * y0 * y0;
+        t[1] += v.w * y0 * y1;
+        t[2] += v.w * y0 * y2;
+        t[3] += v.w * y1 * y1;
+        t[4] += v.w * y1 * y2;
+        t[5] += v.w * y2 * y2;
+    }
+    for (int q = 0; q < 6; ++q) o.T[6 * k + q] = t[q];
 }
 
-// monopoles of a coarser level from the children, in order
-__global__ void k_tree_moments_up(long long off, long long runs, const int *__restrict__ child0,
+// the levels above from their children in order; T moved to the parent's
+// centre by the parallel-axis rule, T = sum T_ch + M_ch (c_ch - c)(c_ch - c)^T
+__global__ void k_tree_moments_up(long long off, long long runs, const int *__restrict__ first,
+                                  const int *__restrict__ count, const int *__restrict__ child0,
                                   const int *__restrict__ childn, double *__restrict__ M,
-                                  double *__restrict__ S)
+                                  double *__restrict__ S, NodeOut o)
 {
     const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (r >= runs) return;
     const long long k = off + r;
     double m = 0.0, s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int c = child0[k]; c < child0[k] + childn[k]; ++c) {
-        m = __dadd_rn(m, M[c]);
-        s0 = __dadd_rn(s0, S[3 * c]);
-        s1 = __dadd_rn(s1, S[3 * c + 1]);
-        s2 = __dadd_rn(s2, S[3 * c + 2]);
+    const int c0 = child0[k], c1 = c0 + childn[k];
+    for (int ch = c0; ch < c1; ++ch) {
+        m = __dadd_rn(m, M[ch]);
+        s0 = __dadd_rn(s0, S[3 * ch]);
+        s1 = __dadd_rn(s1, S[3 * ch + 1]);
+        s2 = __dadd_rn(s2, S[3 * ch + 2]);
     }
     M[k] = m;
     S[3 * k] = s0;
     S[3 * k + 1] = s1;
     S[3 * k + 2] = s2;
+    const double4 c = node_finish(k, m, s0, s1, s2, first, count, child0, childn, o);
+    if (!o.T) return;
+    double t[6] = {0, 0, 0, 0, 0, 0};
+    for (int ch = c0; ch < c1; ++ch) {
+        const double4 cc = o.com[ch];
+        const double y0 = cc.x - c.x, y1 = cc.y - c.y, y2 = cc.z - c.z;
+        const double *tc = o.T + 6 * (long long)ch;
+        t[0] += tc[0] + cc.w * y0 * y0;
+        t[1] += tc[1] + cc.w * y0 * y1;
+        t[2] += tc[2] + cc.w * y0 * y2;
+        t[3] += tc[3] + cc.w * y1 * y1;
+        t[4] += tc[4] + cc.w * y1 * y2;
+        t[5] += tc[5] + cc.w * y2 * y2;
+    }
+    for (int q = 0; q < 6; ++q) o.T[6 * k + q] = t[q];
 }
 
 // group marks at their first particle: gat[i] = node, else -1 (set before)
@@ -556,83 +620,6 @@ __global__ void k_walk_fill(int L, long long o, long long nf, long long n, long 
     }
 }
 
-// per node: the centre of mass (S / M, M), the walk's node record, and
-// with monopoles the pseudo-particle itself (mono, after the n particles of
-// the j records; nullptr with quadrupoles)
-__global__ void k_tree_pseudo(const double *__restrict__ M, const double *__restrict__ S,
-                              const int *__restrict__ first, const int *__restrict__ count,
-                              const int *__restrict__ child0, const int *__restrict__ childn,
-                              long long nnodes, double4 *__restrict__ com, double4 *__restrict__ mono,
-                              TreeNodeW *__restrict__ nodew)
-{
-    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (k >= nnodes) return;
-    const double m = M[k];
-    const double4 c = make_double4(__ddiv_rn(S[3 * k], m), __ddiv_rn(S[3 * k + 1], m),
-                                   __ddiv_rn(S[3 * k + 2], m), m);
-    com[k] = c;
-    if (mono) mono[k] = c;
-    TreeNodeW w;
-    w.cx = __double2float_rn(c.x);
-    w.cy = __double2float_rn(c.y);
-    w.cz = __double2float_rn(c.z);
-    w.pad = 0.f;
-    w.first = first[k];
-    w.count = count[k];
-    w.child0 = child0[k];
-    w.childn = childn[k];
-    nodew[k] = w;
-}
-
-// second moments about the centre of mass, T = sum m (x - c)(x - c)^T as
-// {xx, xy, xz, yy, yz, zz}: the finest level from its particles ...
-__global__ void k_tree_second_leaf(long long off, long long runs, const int *__restrict__ first,
-                                   const int *__restrict__ count, const double4 *__restrict__ xs,
-                                   const double4 *__restrict__ com, double *__restrict__ T)
-{
-    const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (r >= runs) return;
-    const long long k = off + r;
-    const double4 c = com[k];
-    double t[6] = {0, 0, 0, 0, 0, 0};
-    for (int i = first[k]; i < first[k] + count[k]; ++i) {
-        const double4 v = xs[i];
-        const double y0 = v.x - c.x, y1 = v.y - c.y, y2 = v.z - c.z;
-        t[0] += v.w * y0 * y0;
-        t[1] += v.w * y0 * y1;
-        t[2] += v.w * y0 * y2;
-        t[3] += v.w * y1 * y1;
-        t[4] += v.w * y1 * y2;
-        t[5] += v.w * y2 * y2;
-    }
-    for (int q = 0; q < 6; ++q) T[6 * k + q] = t[q];
-}
-
-// ... and the levels above from their children, moved to the parent's
-// centre (the parallel-axis rule: T = sum T_ch + M_ch (c_ch - c)(c_ch - c)^T)
-__global__ void k_tree_second_up(long long off, long long runs, const int *__restrict__ child0,
-                                 const int *__restrict__ childn, const double4 *__restrict__ com,
-                                 double *__restrict__ T)
-{
-    const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (r >= runs) return;
-    const long long k = off + r;
-    const double4 c = com[k];
-    double t[6] = {0, 0, 0, 0, 0, 0};
-    for (int ch = child0[k]; ch < child0[k] + childn[k]; ++ch) {
-        const double4 cc = com[ch];
-        const double y0 = cc.x - c.x, y1 = cc.y - c.y, y2 = cc.z - c.z;
-        const double *tc = T + 6 * (long long)ch;
-        t[0] += tc[0] + cc.w * y0 * y0;
-        t[1] += tc[1] + cc.w * y0 * y1;
-        t[2] += tc[2] + cc.w * y0 * y2;
-        t[3] += tc[3] + cc.w * y1 * y1;
-        t[4] += tc[4] + cc.w * y1 * y2;
-        t[5] += tc[5] + cc.w * y2 * y2;
-    }
-    for (int q = 0; q < 6; ++q) T[6 * k + q] = t[q];
-}
-
 // Jacobi rotation zeroing a[p][q] of the symmetric 3x3 a (r the third
 // index), with the update written element by element; v accumulates the
 // rotations in its columns
@@ -840,15 +827,18 @@ cudaError_t tree_stage_nodes(long long n, const long long *lev_off, int ncrit, T
     k_tree_starts<<<dim3(blocks_of(n), kLevels), 256, 0, st>>>(t.key, t.scan, n, t.first);
     k_tree_nodes<<<dim3(blocks_of(widest), kLevels), 256, 0, st>>>(lo, n, t.scan, t.first, t.count,
                                                                     t.child0, t.childn, t.lev);
+    // moments bottom-up, with each node's centre, walk record and (quadrupole)
+    // second moment
+    NodeOut no{t.com, t.npseudo == 1 ? t.jrec2 + n : nullptr, t.nodew, t.npseudo == 3 ? t.T : nullptr};
     {
         const long long L = kLevels - 1, runs = lev_off[L + 1] - lev_off[L];
-        k_tree_moments_leaf<<<blocks_of(runs), 256, 0, st>>>(lev_off[L], runs, t.first, t.count, t.xs,
-                                                             t.M, t.S);
+        k_tree_moments_leaf<<<blocks_of(runs), 256, 0, st>>>(lev_off[L], runs, t.first, t.count, t.child0,
+                                                             t.childn, t.xs, t.M, t.S, no);
     }
     for (int L = kLevels - 2; L >= 0; --L) {
         const long long runs = lev_off[L + 1] - lev_off[L];
-        k_tree_moments_up<<<blocks_of(runs), 256, 0, st>>>(lev_off[L], runs, t.child0, t.childn,
-                                                           t.M, t.S);
+        k_tree_moments_up<<<blocks_of(runs), 256, 0, st>>>(lev_off[L], runs, t.first, t.count, t.child0,
+                                                           t.childn, t.M, t.S, no);
     }
     cudaMemsetAsync(t.gat, 0xff, n * sizeof(int), st);
     k_tree_group_marks<<<dim3(blocks_of(widest), kLevels), 256, 0, st>>>(lo, n, t.scan, t.first, t.count,
@@ -938,33 +928,20 @@ cudaError_t tree_walk_fill(long long n, long long ngroups, const long long *lev_
 }
 
 // the j records: particles in key order, then P pseudo-particles per node
-// (monopoles: the centre of mass and mass; quadrupoles: three from the
-// second moments, which are summed bottom-up first); the walk's centres
+// (monopoles: written with the moments; quadrupoles: three from the second
+// moments)
 cudaError_t tree_stage_jrec(long long n, long long nnodes, const long long *lev_off, int sms,
                             TreeScratch &t, cudaStream_t st)
 {
-    const bool quad = t.npseudo == 3;
+    (void)lev_off;
     cudaMemcpyAsync(t.jrec2, t.xs, n * sizeof(double4), cudaMemcpyDeviceToDevice, st);
-    k_tree_pseudo<<<blocks_of(nnodes), 256, 0, st>>>(t.M, t.S, t.first, t.count, t.child0, t.childn,
-                                                    nnodes, t.com, quad ? nullptr : t.jrec2 + n, t.nodew);
-    ++t.launches;
-    if (quad) {
-        {
-            const long long L = kLevels - 1, runs = lev_off[L + 1] - lev_off[L];
-            k_tree_second_leaf<<<blocks_of(runs), 256, 0, st>>>(lev_off[L], runs, t.first, t.count, t.xs,
-                                                                t.com, t.T);
-        }
-        for (int L = kLevels - 2; L >= 0; --L) {
-            const long long runs = lev_off[L + 1] - lev_off[L];
-            k_tree_second_up<<<blocks_of(runs), 256, 0, st>>>(lev_off[L], runs, t.child0, t.childn, t.com,
-                                                              t.T);
-        }
+    if (t.npseudo == 3) {
         cudaMemsetAsync(t.nbig, 0, sizeof(unsigned), st);
         k_tree_quad_small<<<blocks_of(nnodes), 256, 0, st>>>(nnodes, t.com, t.first, t.count, t.xs,
                                                              t.jrec2 + n, t.big_list, t.nbig);
         k_tree_quad_big<<<(unsigned)std::max(1, 4 * sms), 128, 0, st>>>(t.big_list, t.nbig, t.com, t.T,
                                                                        t.jrec2 + n);
-        t.launches += kLevels + 2;
+        t.launches += 2;
     }
     return cudaGetLastError();
 }
