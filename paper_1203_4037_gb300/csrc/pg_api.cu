@@ -1246,14 +1246,21 @@ int launch_group_kernel(pg_ctx *c, const GroupArgs &g, bool cell)
     int occ = groups_max_blocks_per_sm(np, table, tab_units(c), cell, ext);
     int per = c->ctas_per_sm > 0 ? std::min(c->ctas_per_sm, occ) : occ;
     int grid = c->sms * per;
-    PG_CUDA(c, cudaMemsetAsync(c->g_queue.p, 0, sizeof(int), c->stream));
+    // cell lists: the warp-mode items (the small cells) in a second launch
+    // whose lighter blocks fit more warps on an SM
+    const int wper = cell && table ? groups_warp_blocks_per_sm(tab_units(c), ext) : 0;
+    GroupArgs gg = g;
+    if (wper > 0) gg.queue_w = (int *)c->g_queue.p + 1;
+    PG_CUDA(c, cudaMemsetAsync(c->g_queue.p, 0, 2 * sizeof(int), c->stream));
     if (c->timing) PG_CUDA(c, record_timing(c, c->tk0));
-    PG_CUDA(c, launch_groups(g, grid, np, table, cell, ext, groups_smem(np, table, tab_units(c)),
+    PG_CUDA(c, launch_groups(gg, grid, np, table, cell, ext, groups_smem(np, table, tab_units(c)),
                              c->stream));
+    if (wper > 0)
+        PG_CUDA(c, launch_groups_warp(gg, c->sms * wper, ext, tab_units(c), c->stream));
     if (c->timing) PG_CUDA(c, record_timing(c, c->tk1));
     c->timed = c->timing;
     c->last_grid = grid;
-    c->last_launches += 1;
+    c->last_launches += wper > 0 ? 2 : 1;
     return PG_OK;
 }
 

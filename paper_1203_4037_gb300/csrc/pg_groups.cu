@@ -449,10 +449,13 @@ constexpr int kWarpTJ = 128;        // j entries per warp-staged tile
 constexpr int kWarpItemNi = 32;     // items up to this size (i-particles)
 constexpr long long kWarpItemPairs = 32768;   // and this many pairs go to warp mode
 
+// Claims come from counter q: item qbase + (q's previous value); nwarps is
+// the number of warps of the launch claiming from it.
 template <bool TABLE, bool CELL, bool EXT, bool HL = false>
 __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cur, int held,
                                           u64 *wcvt, int *wcr, const float2 *tab,
-                                          const float4 *dirt, int lane32)
+                                          const float4 *dirt, int lane32, int *q, int qbase,
+                                          int nwarps)
 {
     constexpr unsigned kFull = 0xffffffffu;
     int pend = -1;                      // lane 0: a claimed item not yet started
@@ -460,14 +463,14 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
     if (cur < 0) {
         int c2 = 0;
         if (lane32 == 0) {
-            c2 = pend >= 0 ? pend : atomicAdd(a.queue, 1);
+            c2 = pend >= 0 ? pend : qbase + atomicAdd(q, 1);
             pend = -1;
         }
         cur = __shfl_sync(kFull, c2, 0);
     }
     if (cur >= nitems) return;
     // claims run one item ahead while more than one item per warp is left
-    const int ahead_limit = nitems - (int)gridDim.x * (kNT / 32);
+    const int ahead_limit = nitems - nwarps;
 
     const float c0 = TABLE ? 2.0f : a.eps2;
     const u64 c0v = pk2(c0, c0);
@@ -567,7 +570,7 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
     for (;;) {
         // claim the next item now (its latency hides behind this one) while
         // the queue is long; in its last stretch only once this one is done
-        if (lane32 == 0 && pend < 0 && cur < ahead_limit) pend = atomicAdd(a.queue, 1);
+        if (lane32 == 0 && pend < 0 && cur < ahead_limit) pend = qbase + atomicAdd(q, 1);
         int nxt = nitems;
         GroupItem itn = it;
         const int *crc = wcr + slot * kCellTab;
@@ -728,7 +731,7 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
         }
         if (!staged) {             // nothing claimed ahead, or no j tile to overlap with
             int c2 = 0;
-            if (lane32 == 0) c2 = pend >= 0 ? pend : atomicAdd(a.queue, 1);
+            if (lane32 == 0) c2 = pend >= 0 ? pend : qbase + atomicAdd(q, 1);
             nxt = __shfl_sync(kFull, c2, 0);
             if (nxt >= nitems) return;
             itn = item_at(a, nxt);
@@ -791,6 +794,7 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
         const int item = sh[0];
         if (item >= nitems) return;
         if (item >= warp_from) {   // the small items: continue in warp mode
+            if (a.queue_w) return;  // or leave them to the warp-mode kernel
             first_small = item;
             break;
         }
@@ -815,7 +819,43 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
     warp_loop<TABLE, CELL, EXT, HL>(a, nitems, w == 0 ? first_small : -1,
                                   (w == 0 && lane32 == 0) ? next : -1,
                                   cvt + w * (2 * 2 * kWarpTJ), cr + w * 2 * kCellTab, tab, dirt,
-                                  lane32);
+                                  lane32, a.queue, 0, (int)gridDim.x * (kNT / 32));
+}
+
+// The warp-mode items alone, in a launch of their own after the CTA-mode
+// items: without the CTA-mode item's registers and staging buffers, more
+// warps fit on an SM, which the short, latency-bound small items need. Every
+// warp claims items warp_from, warp_from + 1, ... from counter queue_w.
+// Two blocks of 256 threads per SM (16 warps, against 12 in the CTA-mode
+// kernel) at up to 128 registers a thread; three blocks (24 warps) cap the
+// registers at 80, and the spills made the uniform-cell half slower.
+constexpr int kWNT = 256;          // threads per block
+constexpr int kWMinBlocks = 2;     // resident blocks per SM wanted (register cap)
+
+template <bool TABLE, bool CELL, bool EXT, bool HL = false>
+__global__ void __launch_bounds__(kWNT, kWMinBlocks) k_groups_warp(GroupArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    u64 *wcvt = reinterpret_cast<u64 *>(smem);                             // [warps][4 kWarpTJ]
+    float4 *dirt = reinterpret_cast<float4 *>(wcvt + (kWNT / 32) * 4 * kWarpTJ);   // [28]
+    int *cr = reinterpret_cast<int *>(dirt + 28);                          // [warps][2][kCellTab]
+    float2 *tab = reinterpret_cast<float2 *>(cr + (kWNT / 32) * 2 * kCellTab);
+
+    const int tid = threadIdx.x;
+    if (TABLE && !EXT)
+        for (int k = tid; k < a.tab.n; k += kWNT) tab[k] = a.tab.AG1[k];
+    if (TABLE && EXT)
+        for (int k = tid; k < a.tab.n; k += kWNT) reinterpret_cast<float4 *>(tab)[k] = a.tab.AGP[k];
+    if (CELL && tid < 27)
+        dirt[tid] = make_float4((float)(tid / 9 - 1) * a.cell_h, (float)((tid / 3) % 3 - 1) * a.cell_h,
+                                (float)(tid % 3 - 1) * a.cell_h, 0.0f);
+    __syncthreads();
+    const int nitems = a.nitems >= 0 ? a.nitems : (int)*a.nitems_dev;
+    const int warp_from = a.warp_from >= 0 ? a.warp_from : (int)*a.warp_from_dev;
+    const int w = tid >> 5, lane32 = tid & 31;
+    warp_loop<TABLE, CELL, EXT, HL>(a, nitems, -1, -1, wcvt + w * (2 * 2 * kWarpTJ),
+                                  cr + w * 2 * kCellTab, tab, dirt, lane32, a.queue_w, warp_from,
+                                  (int)gridDim.x * (kWNT / 32));
 }
 
 // ------------------------------------------------------------------ host
@@ -892,6 +932,59 @@ static cudaError_t launch_gnp(const GroupArgs &g, int grid, bool table, bool cel
                          : launch_g<NP, true, true, false>(g, grid, smem, st);
     return ext ? launch_g<NP, true, false, true>(g, grid, smem, st)
                : launch_g<NP, true, false, false>(g, grid, smem, st);
+}
+
+size_t groups_warp_smem(bool table, int ntab)
+{
+    size_t s = (kWNT / 32) * 4 * kWarpTJ * sizeof(u64) + 28 * 16 +
+               (kWNT / 32) * 2 * kCellTab * sizeof(int);
+    if (table) s += (size_t)ntab * sizeof(float2);
+    return s;
+}
+
+template <bool EXT>
+static cudaError_t configure_gw()
+{
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_groups_warp<true, true, EXT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)groups_warp_smem(true, 2 << 13));
+    done = e == cudaSuccess;
+    return e;
+}
+
+// the warp-mode kernel of the cell list: blocks per SM for a table of ntab
+// float2 units (0 if the kernel cannot be configured)
+int groups_warp_blocks_per_sm(int ntab, bool ext)
+{
+    const size_t smem = groups_warp_smem(true, ntab);
+    int nb = 0;
+    if (ext) {
+        if (configure_gw<true>() != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_groups_warp<true, true, true>, kWNT,
+                                                          smem) != cudaSuccess)
+            return 0;
+    } else {
+        if (configure_gw<false>() != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_groups_warp<true, true, false>, kWNT,
+                                                          smem) != cudaSuccess)
+            return 0;
+    }
+    return nb;
+}
+
+cudaError_t launch_groups_warp(const GroupArgs &g, int grid, bool ext, int ntab, cudaStream_t st)
+{
+    if (grid <= 0 || !g.queue_w) return cudaErrorInvalidValue;
+    const size_t smem = groups_warp_smem(true, ntab);
+    cudaError_t e = ext ? configure_gw<true>() : configure_gw<false>();
+    if (e != cudaSuccess) return e;
+    if (ext)
+        k_groups_warp<true, true, true><<<grid, kWNT, smem, st>>>(g);
+    else
+        k_groups_warp<true, true, false><<<grid, kWNT, smem, st>>>(g);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, bool cell, bool ext,

@@ -88,6 +88,7 @@ struct GroupArgs {
     int warp_from;         // first warp-mode item (items after are small), -1: *warp_from_dev
     const unsigned *warp_from_dev;
     int *queue;            // work counter (reset to 0 before each launch)
+    int *queue_w = nullptr;   // set: the warp-mode items run in their own launch, claimed from this counter
     long long nj;          // number of j records (bounds check)
     float eps2;
     TableDev tab;
@@ -208,6 +209,10 @@ cudaError_t launch_pack_hilo(const double4 *in, long long n, float4 *out, cudaSt
 size_t groups_smem(int np, bool table, int ntab);   // ntab in float2 units, as above
 int groups_bi(int np);
 int groups_max_blocks_per_sm(int np, bool table, int ntab, bool cell, bool ext = false);
+// the cell list's warp-mode items in a launch of their own (table mode)
+size_t groups_warp_smem(bool table, int ntab);
+int groups_warp_blocks_per_sm(int ntab, bool ext);
+cudaError_t launch_groups_warp(const GroupArgs &g, int grid, bool ext, int ntab, cudaStream_t st);
 cudaError_t launch_table_merge(const float2 *AG1, const float *P0, const float *P1, float4 *AGP,
                                int E, int F, cudaStream_t st);
 cudaError_t launch_set_w(double4 *x, const double *eps, long long n, cudaStream_t st);
