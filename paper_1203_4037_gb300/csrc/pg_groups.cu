@@ -764,6 +764,8 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
     float2 *tab = reinterpret_cast<float2 *>(cr + 8 * kCellTab);
 
     const int tid = threadIdx.x;
+    // a cell-list launch lets its warp-mode kernel start as CTAs drain
+    if (CELL) asm volatile("griddepcontrol.launch_dependents;");
     if (TABLE && !EXT)
         for (int k = tid; k < a.tab.n; k += kNT) tab[k] = a.tab.AG1[k];
     if (TABLE && EXT)
@@ -856,6 +858,10 @@ __global__ void __launch_bounds__(kWNT, kWMinBlocks) k_groups_warp(GroupArgs a)
     warp_loop<TABLE, CELL, EXT, HL>(a, nitems, -1, -1, wcvt + w * (2 * 2 * kWarpTJ),
                                   cr + w * 2 * kCellTab, tab, dirt, lane32, a.queue_w, warp_from,
                                   (int)gridDim.x * (kWNT / 32));
+    // launched while the CTA-mode kernel may still run (programmatic
+    // dependent launch): its items are disjoint from this kernel's, and this
+    // kernel ends only after that one has, so later work sees both
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // ------------------------------------------------------------------ host
@@ -950,6 +956,12 @@ static cudaError_t configure_gw()
     cudaError_t e = cudaFuncSetAttribute(k_groups_warp<true, true, EXT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)groups_warp_smem(true, 2 << 13));
+    // the same shared-memory carveout as the CTA-mode kernel, so that its
+    // blocks can join an SM on which that kernel still runs
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_groups_warp<true, true, EXT>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
     done = e == cudaSuccess;
     return e;
 }
@@ -980,11 +992,20 @@ cudaError_t launch_groups_warp(const GroupArgs &g, int grid, bool ext, int ntab,
     const size_t smem = groups_warp_smem(true, ntab);
     cudaError_t e = ext ? configure_gw<true>() : configure_gw<false>();
     if (e != cudaSuccess) return e;
-    if (ext)
-        k_groups_warp<true, true, true><<<grid, kWNT, smem, st>>>(g);
-    else
-        k_groups_warp<true, true, false><<<grid, kWNT, smem, st>>>(g);
-    return cudaGetLastError();
+    // programmatic stream serialisation: the blocks may start once every
+    // block of the CTA-mode kernel before it has started
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kWNT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return ext ? cudaLaunchKernelEx(&cfg, k_groups_warp<true, true, true>, g)
+               : cudaLaunchKernelEx(&cfg, k_groups_warp<true, true, false>, g);
 }
 
 cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, bool cell, bool ext,
