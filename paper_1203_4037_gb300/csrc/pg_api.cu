@@ -1248,7 +1248,7 @@ int launch_group_kernel(pg_ctx *c, const GroupArgs &g, bool cell)
     int grid = c->sms * per;
     // cell lists: the warp-mode items (the small cells) in a second launch
     // whose lighter blocks fit more warps on an SM
-    const int wper = cell && table ? groups_warp_blocks_per_sm(tab_units(c), ext) : 0;
+    const int wper = cell && table ? groups_warp_blocks_per_sm(true, true, ext, tab_units(c)) : 0;
     GroupArgs gg = g;
     if (wper > 0) gg.queue_w = (int *)c->g_queue.p + 1;
     PG_CUDA(c, cudaMemsetAsync(c->g_queue.p, 0, 2 * sizeof(int), c->stream));
@@ -1256,11 +1256,32 @@ int launch_group_kernel(pg_ctx *c, const GroupArgs &g, bool cell)
     PG_CUDA(c, launch_groups(gg, grid, np, table, cell, ext, groups_smem(np, table, tab_units(c)),
                              c->stream));
     if (wper > 0)
-        PG_CUDA(c, launch_groups_warp(gg, c->sms * wper, ext, tab_units(c), c->stream));
+        PG_CUDA(c, launch_groups_warp(gg, c->sms * wper, true, true, ext, tab_units(c), true, c->stream));
     if (c->timing) PG_CUDA(c, record_timing(c, c->tk1));
     c->timed = c->timing;
     c->last_grid = grid;
     c->last_launches += wper > 0 ? 2 : 1;
+    return PG_OK;
+}
+
+// items that are all warp-sized (narrow all-pairs): the warp-mode kernel
+// alone, wper blocks per SM, claiming items 0, 1, ... from the second counter
+int launch_group_warp_kernel(pg_ctx *c, const GroupArgs &g, int wper)
+{
+    const bool table = c->mode == PG_TABLE;
+    const int per = c->ctas_per_sm > 0 ? std::min(c->ctas_per_sm, wper) : wper;
+    const int grid = c->sms * per;
+    GroupArgs gg = g;
+    gg.queue_w = (int *)c->g_queue.p + 1;
+    gg.warp_from = 0;
+    c->last_np = 1;                     // one i-pair per lane
+    PG_CUDA(c, cudaMemsetAsync(c->g_queue.p, 0, 2 * sizeof(int), c->stream));
+    if (c->timing) PG_CUDA(c, record_timing(c, c->tk0));
+    PG_CUDA(c, launch_groups_warp(gg, grid, table, false, use_ext(c), tab_units(c), false, c->stream));
+    if (c->timing) PG_CUDA(c, record_timing(c, c->tk1));
+    c->timed = c->timing;
+    c->last_grid = grid;
+    c->last_launches += 1;
     return PG_OK;
 }
 
@@ -1309,17 +1330,30 @@ int enqueue_narrow(pg_ctx *c, double *acc, double *pot)
     const int Bi = groups_bi(np);
     const int nic = (int)((ni + Bi - 1) / Bi);
     const int occ = groups_max_blocks_per_sm(np, table, tab_units(c), false, use_ext(c));
-    const long long warps = (long long)c->sms * occ * 4;
-    const long long per = std::max<long long>(1, warps / nic);
-    long long jc = (nj + per - 1) / per;
-    jc = std::max<long long>(128, (jc + 127) / 128 * 128);    // whole warp tiles
+    // j chunk: about one item per warp of the launch, whole warp tiles
+    auto chunk = [&](long long warps) {
+        const long long per = std::max<long long>(1, warps / nic);
+        const long long jc = (nj + per - 1) / per;
+        return std::max<long long>(128, (jc + 127) / 128 * 128);
+    };
+    // items are all alike: warp mode for all of them when an i chunk is
+    // small (one warp pass, at most 64 i) and short, else CTA mode.
+    // Warp-mode items run in the warp-mode kernel alone, which fits more
+    // warps on an SM; chunks are sized for it
+    const long long ich = std::min<long long>(Bi, ni);
+    const int wper = ich <= 64 ? groups_warp_blocks_per_sm(table, false, use_ext(c), tab_units(c)) : 0;
+    long long jc = chunk((long long)c->sms * occ * 4);
+    bool warp = false;
+    if (wper > 0) {
+        const long long jw = chunk((long long)c->sms * wper * groups_warp_warps_per_block());
+        if (ich * jw <= 32768) {
+            jc = jw;
+            warp = true;
+        }
+    }
     const long long nch = (nj + jc - 1) / jc;
     if ((long long)nic * nch >= (1LL << 31) || jc >= (1LL << 31))
         return fail(c, PG_EINVAL, "too many narrow items");
-    // items are all alike: warp mode for all of them when an i chunk is
-    // small and short, else CTA mode
-    const long long ich = std::min<long long>(Bi, ni);
-    const bool warp = ich <= 32 && ich * jc <= 32768;
     const long long nitems = (long long)nic * nch;
     if ((rc = ensure(c, c->g_ctr, (size_t)nic * sizeof(double4))) || (rc = ensure(c, c->g_queue, 16)) ||
         (rc = ensure(c, c->n_part, (size_t)nch * ni * sizeof(double4))) ||
@@ -1340,7 +1374,7 @@ int enqueue_narrow(pg_ctx *c, double *acc, double *pot)
     g.jhl = (const float4 *)c->g_jhl.p;
     g.ihl = (const float4 *)c->g_ihl.p;
     g.nitems = (int)nitems;
-    g.warp_from = warp ? 0 : (int)nitems;
+    g.warp_from = (int)nitems;
     g.nj = nj;
     g.perm = nullptr;
     g.jchunk = (int)jc;
@@ -1351,7 +1385,7 @@ int enqueue_narrow(pg_ctx *c, double *acc, double *pot)
     g.part_stride = ni;
     g.acc = acc;
     g.pot = pot;
-    if ((rc = launch_group_kernel(c, g, false))) return rc;
+    if ((rc = warp ? launch_group_warp_kernel(c, g, wper) : launch_group_kernel(c, g, false))) return rc;
     CombineArgs cb{};
     cb.part = (const double4 *)c->n_part.p;
     cb.jrec = (const double4 *)c->jrec.p;

@@ -858,9 +858,10 @@ __global__ void __launch_bounds__(kWNT, kWMinBlocks) k_groups_warp(GroupArgs a)
     warp_loop<TABLE, CELL, EXT, HL>(a, nitems, -1, -1, wcvt + w * (2 * 2 * kWarpTJ),
                                   cr + w * 2 * kCellTab, tab, dirt, lane32, a.queue_w, warp_from,
                                   (int)gridDim.x * (kWNT / 32));
-    // launched while the CTA-mode kernel may still run (programmatic
+    // when launched while the CTA-mode kernel may still run (programmatic
     // dependent launch): its items are disjoint from this kernel's, and this
-    // kernel ends only after that one has, so later work sees both
+    // kernel ends only after that one has, so later work sees both (a no-op
+    // after an ordinary launch)
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
@@ -948,52 +949,59 @@ size_t groups_warp_smem(bool table, int ntab)
     return s;
 }
 
-template <bool EXT>
+template <bool TABLE, bool CELL, bool EXT>
 static cudaError_t configure_gw()
 {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_groups_warp<true, true, EXT>,
+    cudaError_t e = cudaFuncSetAttribute(k_groups_warp<TABLE, CELL, EXT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)groups_warp_smem(true, 2 << 13));
+                                         (int)groups_warp_smem(TABLE, 2 << 13));
     // the same shared-memory carveout as the CTA-mode kernel, so that its
     // blocks can join an SM on which that kernel still runs
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_groups_warp<true, true, EXT>,
+        e = cudaFuncSetAttribute(k_groups_warp<TABLE, CELL, EXT>,
                                  cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
     done = e == cudaSuccess;
     return e;
 }
 
-// the warp-mode kernel of the cell list: blocks per SM for a table of ntab
-// float2 units (0 if the kernel cannot be configured)
-int groups_warp_blocks_per_sm(int ntab, bool ext)
+template <bool TABLE, bool CELL, bool EXT>
+static int occ_gw(size_t smem)
 {
-    const size_t smem = groups_warp_smem(true, ntab);
     int nb = 0;
-    if (ext) {
-        if (configure_gw<true>() != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_groups_warp<true, true, true>, kWNT,
-                                                          smem) != cudaSuccess)
-            return 0;
-    } else {
-        if (configure_gw<false>() != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_groups_warp<true, true, false>, kWNT,
-                                                          smem) != cudaSuccess)
-            return 0;
-    }
+    if (configure_gw<TABLE, CELL, EXT>() != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_groups_warp<TABLE, CELL, EXT>, kWNT, smem) !=
+            cudaSuccess)
+        return 0;
     return nb;
 }
 
-cudaError_t launch_groups_warp(const GroupArgs &g, int grid, bool ext, int ntab, cudaStream_t st)
+// blocks per SM of the warp-mode kernel for a table of ntab float2 units
+// (0 if the kernel cannot be configured; cell mode needs the table)
+int groups_warp_blocks_per_sm(bool table, bool cell, bool ext, int ntab)
 {
-    if (grid <= 0 || !g.queue_w) return cudaErrorInvalidValue;
-    const size_t smem = groups_warp_smem(true, ntab);
-    cudaError_t e = ext ? configure_gw<true>() : configure_gw<false>();
+    if (cell && !table) return 0;
+    const size_t smem = groups_warp_smem(table, ntab);
+    if (cell) return ext ? occ_gw<true, true, true>(smem) : occ_gw<true, true, false>(smem);
+    if (table) return ext ? occ_gw<true, false, true>(smem) : occ_gw<true, false, false>(smem);
+    return ext ? occ_gw<false, false, true>(smem) : occ_gw<false, false, false>(smem);
+}
+
+int groups_warp_warps_per_block() { return kWNT / 32; }
+
+template <bool TABLE, bool CELL, bool EXT>
+static cudaError_t launch_gw(const GroupArgs &g, int grid, size_t smem, bool pdl, cudaStream_t st)
+{
+    cudaError_t e = configure_gw<TABLE, CELL, EXT>();
     if (e != cudaSuccess) return e;
+    if (!pdl) {
+        k_groups_warp<TABLE, CELL, EXT><<<grid, kWNT, smem, st>>>(g);
+        return cudaGetLastError();
+    }
     // programmatic stream serialisation: the blocks may start once every
-    // block of the CTA-mode kernel before it has started
+    // block of the kernel before it has started
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(kWNT);
@@ -1004,8 +1012,20 @@ cudaError_t launch_groups_warp(const GroupArgs &g, int grid, bool ext, int ntab,
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return ext ? cudaLaunchKernelEx(&cfg, k_groups_warp<true, true, true>, g)
-               : cudaLaunchKernelEx(&cfg, k_groups_warp<true, true, false>, g);
+    return cudaLaunchKernelEx(&cfg, k_groups_warp<TABLE, CELL, EXT>, g);
+}
+
+cudaError_t launch_groups_warp(const GroupArgs &g, int grid, bool table, bool cell, bool ext, int ntab,
+                               bool pdl, cudaStream_t st)
+{
+    if (grid <= 0 || !g.queue_w || (cell && !table) || g.hl) return cudaErrorInvalidValue;
+    const size_t smem = groups_warp_smem(table, ntab);
+    if (cell) return ext ? launch_gw<true, true, true>(g, grid, smem, pdl, st)
+                         : launch_gw<true, true, false>(g, grid, smem, pdl, st);
+    if (table) return ext ? launch_gw<true, false, true>(g, grid, smem, pdl, st)
+                          : launch_gw<true, false, false>(g, grid, smem, pdl, st);
+    return ext ? launch_gw<false, false, true>(g, grid, smem, pdl, st)
+               : launch_gw<false, false, false>(g, grid, smem, pdl, st);
 }
 
 cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, bool cell, bool ext,

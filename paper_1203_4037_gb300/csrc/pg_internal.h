@@ -209,10 +209,15 @@ cudaError_t launch_pack_hilo(const double4 *in, long long n, float4 *out, cudaSt
 size_t groups_smem(int np, bool table, int ntab);   // ntab in float2 units, as above
 int groups_bi(int np);
 int groups_max_blocks_per_sm(int np, bool table, int ntab, bool cell, bool ext = false);
-// the cell list's warp-mode items in a launch of their own (table mode)
+// warp-mode items in a launch of their own (k_groups_warp): the cell list's
+// small cells after the CTA-mode kernel (pdl: programmatic dependent launch,
+// for a kernel whose inputs were complete before the CTA-mode kernel
+// started), and narrow all-pairs items (ordinary launch); g.queue_w set
 size_t groups_warp_smem(bool table, int ntab);
-int groups_warp_blocks_per_sm(int ntab, bool ext);
-cudaError_t launch_groups_warp(const GroupArgs &g, int grid, bool ext, int ntab, cudaStream_t st);
+int groups_warp_blocks_per_sm(bool table, bool cell, bool ext, int ntab);
+int groups_warp_warps_per_block();
+cudaError_t launch_groups_warp(const GroupArgs &g, int grid, bool table, bool cell, bool ext, int ntab,
+                               bool pdl, cudaStream_t st);
 cudaError_t launch_table_merge(const float2 *AG1, const float *P0, const float *P1, float4 *AGP,
                                int E, int F, cudaStream_t st);
 cudaError_t launch_set_w(double4 *x, const double *eps, long long n, cudaStream_t st);
