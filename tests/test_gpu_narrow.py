@@ -51,7 +51,9 @@ def core_set(ni, seed):
     return x[np.argsort(np.linalg.norm(x, axis=1))[:ni]]
 
 
-@pytest.mark.parametrize("ni", [1, 16, 33, 100, 513, 1000])
+# 64 and 65 straddle the switch from the warp-mode kernel (one warp pass of
+# at most 64 i) to CTA-mode items
+@pytest.mark.parametrize("ni", [1, 16, 33, 64, 65, 100, 513, 1000])
 def test_narrow_newton(pg, orc, jset, ni):
     xj, mj = jset
     xi = core_set(ni, 900 + ni)
