@@ -313,9 +313,22 @@ int pg_sync(pg_ctx *ctx);
  * on first use and replay it while sizes, mode and buffers are unchanged. */
 int pg_set_graph(pg_ctx *ctx, int on);
 
-/* Time the candidate launch shapes of the current workload (i per thread,
- * CTAs per SM) on the device and keep the fastest. Synchronises. */
+/* The autotuner: times the candidate launch shapes of the current workload
+ * on the device (one warm-up run and three timed runs each) and keeps the
+ * fastest in the context. Candidates: i per thread 2*np (np 1, 2, 4) on every
+ * path; with it, on the tiled all-pairs path packed or scalar pair
+ * arithmetic and CTAs per SM (the occupancy limit and one below); on the
+ * batched kernel (groups, tree lists, cell list) CTAs per SM; on the narrow
+ * path the split of the j records into 1, 2 or 4 items per warp of the
+ * launch. Threads per CTA and j-tile depths are compile-time constants.
+ * Synchronises. */
 int pg_tune(pg_ctx *ctx);
+
+/* Narrow all-pairs path: cut the j records into about items_per_warp work
+ * items per warp of the launch (1 to 8; 0 = the default, one). pg_info's
+ * out[6] reports the value a narrow run used. Returns PG_EINVAL outside
+ * 0 to 8. */
+int pg_set_split(pg_ctx *ctx, int items_per_warp);
 
 /* Path of the all-pairs force loop (no groups, no periodic box); both give
  * the same sums up to FP32 rounding order. PG_PATH_TILED gives every CTA a
@@ -348,7 +361,8 @@ int pg_kernel_time(pg_ctx *ctx, double *ms);
 /* Counters: out[0] pair evaluations enqueued by the last run, out[1] kernel
  * launches of the last run, out[2] i per thread, out[3] grid size of the
  * force kernel, out[4] partial slots per tile, out[5] 1 if the pair arithmetic
- * is packed FP32x2. Returns how many were written. */
+ * is packed FP32x2, out[6] items per warp of a narrow run (0 for other paths).
+ * Returns how many were written (at most 7). */
 int pg_info(pg_ctx *ctx, long long *out, int n);
 
 /* Measured ceilings on the current device for the roofline (a tool of this

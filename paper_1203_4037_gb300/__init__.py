@@ -65,6 +65,7 @@ SIGNATURES = {
     "pg_set_graph": (_I, [_P, _I]),
     "pg_tune": (_I, [_P]),
     "pg_set_shape": (_I, [_P, _I, _I, _I]),
+    "pg_set_split": (_I, [_P, _I]),
     "pg_set_allpairs_path": (_I, [_P, _I]),
     "pg_set_eps_i": (_I, [_P, _P, _LL]),
     "pg_set_eps_i_dev": (_I, [_P, _P, _LL]),
@@ -369,10 +370,14 @@ def pg_kernel_time(ctx):
     return ms.value
 
 
+def pg_set_split(ctx, items_per_warp):
+    return _check(ctx, lib().pg_set_split(ctx, int(items_per_warp)))
+
+
 def pg_info(ctx):
-    out = (_LL * 6)()
-    n = lib().pg_info(ctx, out, 6)
-    keys = ["pairs", "launches", "i_per_thread", "grid", "slots", "packed"]
+    out = (_LL * 7)()
+    n = lib().pg_info(ctx, out, 7)
+    keys = ["pairs", "launches", "i_per_thread", "grid", "slots", "packed", "split"]
     return dict(zip(keys[:n], list(out)[:n]))
 
 
@@ -563,6 +568,9 @@ class Context:
 
     def set_shape(self, np_, ctas_per_sm=0, packed=-1):
         pg_set_shape(self.h, np_, ctas_per_sm, packed)
+
+    def set_split(self, items_per_warp):
+        pg_set_split(self.h, items_per_warp)
 
     def set_timing(self, on=True):
         pg_set_timing(self.h, on)

@@ -133,6 +133,7 @@ struct pg_ctx {
     int np = 0;
     int ctas_per_sm = 0;
     int packed = 1;             // f32x2 pair arithmetic (0: scalar FP32)
+    int split = 0;              // narrow path: items per warp of the launch (0: one)
 
     // graph
     bool use_graph = false;
@@ -147,7 +148,7 @@ struct pg_ctx {
 
     // stats of the last run
     int last_np = 2;
-    long long last_pairs = 0, last_launches = 0, last_grid = 0, last_slots = 0;
+    long long last_pairs = 0, last_launches = 0, last_grid = 0, last_slots = 0, last_split = 0;
 
     std::string err;
 };
@@ -940,6 +941,16 @@ int pg_set_shape(pg_ctx *c, int np, int ctas_per_sm, int packed)
     return PG_OK;
 }
 
+int pg_set_split(pg_ctx *c, int items_per_warp)
+{
+    if (!c) return PG_EINVAL;
+    if (items_per_warp < 0 || items_per_warp > 8)
+        return fail(c, PG_EINVAL, "items per warp must be 0 to 8");
+    c->split = items_per_warp;
+    drop_graph(c);
+    return PG_OK;
+}
+
 int pg_info(pg_ctx *c, long long *out, int n)
 {
     if (!c || !out || n < 0) return PG_EINVAL;
@@ -950,9 +961,9 @@ int pg_info(pg_ctx *c, long long *out, int n)
         c->last_pairs = (long long)v;
         c->pairs_on_device = false;
     }
-    long long v[6] = {c->last_pairs, c->last_launches, 2LL * c->last_np, c->last_grid,
-                      c->last_slots, (long long)c->packed};
-    int k = std::min(n, 6);
+    long long v[7] = {c->last_pairs, c->last_launches, 2LL * c->last_np, c->last_grid,
+                      c->last_slots, (long long)c->packed, c->last_split};
+    int k = std::min(n, 7);
     for (int i = 0; i < k; ++i) out[i] = v[i];
     return k;
 }
@@ -1330,9 +1341,11 @@ int enqueue_narrow(pg_ctx *c, double *acc, double *pot)
     const int Bi = groups_bi(np);
     const int nic = (int)((ni + Bi - 1) / Bi);
     const int occ = groups_max_blocks_per_sm(np, table, tab_units(c), false, use_ext(c));
-    // j chunk: about one item per warp of the launch, whole warp tiles
+    // j chunk: about `split` items per warp of the launch, whole warp tiles
+    const long long spl = c->split > 0 ? c->split : 1;
+    c->last_split = spl;
     auto chunk = [&](long long warps) {
-        const long long per = std::max<long long>(1, warps / nic);
+        const long long per = std::max<long long>(1, warps * spl / nic);
         const long long jc = (nj + per - 1) / per;
         return std::max<long long>(128, (jc + 127) / 128 * 128);
     };
@@ -1749,6 +1762,7 @@ int enqueue_cells(pg_ctx *c, double *acc, double *pot)
 int enqueue_run(pg_ctx *c, double *acc, double *pot)
 {
     c->last_launches = 0;
+    c->last_split = 0;
     // per-i softening lives in the i records' w (read by every path); a
     // captured graph writes it on every replay, as the records may be new
     if (c->have_epsi && (c->capturing || !c->epsi_applied)) {
@@ -1794,7 +1808,8 @@ int run_into(pg_ctx *c, double *acc, double *pot)
              (int)c->have_groups, c->mode, c->box, c->ni, nj_of(c), c->np, c->packed,
              c->ctas_per_sm, c->eps, c->self,
              (void *)acc, (void *)pot, c->jrec.p, c->xi.p, c->sort_mode, (int)c->timing,
-             c->g_nitems, c->ngroups, c->path * 4 + (c->have_epsi ? 2 : 0) + (c->have_pot ? 1 : 0));
+             c->g_nitems, c->ngroups,
+             (c->path * 4 + (c->have_epsi ? 2 : 0) + (c->have_pot ? 1 : 0)) * 16 + c->split);
     if (c->pm_n > 0) {
         char pk[96];
         snprintf(pk, sizeof pk, "|pm%d|%d|%.17g", c->pm_n, c->pm_split, c->pm_scale);
@@ -2029,6 +2044,16 @@ int pg_backward_dev(pg_ctx *c, const double *w, double *dx, double *dm, float *d
     return PG_OK;
 }
 
+// The autotuner: runs the current workload once per candidate launch shape
+// (one warm-up run, then three timed ones on the context's stream) and keeps
+// the fastest. Candidates, per path:
+//   - all-pairs tiles: i per thread 2 np (np 1, 2, 4) x packed FP32x2 or
+//     scalar x CTAs per SM (the occupancy limit and one below);
+//   - the batched kernel (groups, tree lists, cell list): np x CTAs per SM;
+//   - narrow all-pairs: np x items per warp of the launch (1, 2, 4), the
+//     split of the j records into chunks.
+// Threads per CTA and j-tile depths are compile-time constants of the
+// kernels (register and shared-memory budgets follow from them).
 int pg_tune(pg_ctx *c)
 {
     if (!c) return PG_EINVAL;
@@ -2042,43 +2067,55 @@ int pg_tune(pg_ctx *c)
     cudaEvent_t e0, e1;
     PG_CUDA(c, cudaEventCreate(&e0));
     PG_CUDA(c, cudaEventCreate(&e1));
-    int best_np = c->np, best_cta = c->ctas_per_sm, best_pk = c->packed;
+    int best_np = c->np, best_cta = c->ctas_per_sm, best_pk = c->packed, best_split = c->split;
     float best = 1e30f;
-    const int nps[3] = {1, 2, 4};
-    bool groups_path = c->have_groups || c->box > 0.0;
-    for (int pk = groups_path ? 1 : 0; pk <= 1 && !rc; ++pk)
-    for (int np : nps) {
-        int occ = groups_path
-                      ? groups_max_blocks_per_sm(np, c->mode == PG_TABLE, tab_units(c), !c->have_groups,
-                                                 use_ext(c))
-                      : allpairs_max_blocks_per_sm(np, c->mode == PG_TABLE, tab_units(c), pk != 0,
-                                                   use_ext(c));
-        for (int cta = occ; cta <= occ; ++cta) {     // the occupancy limit of each shape
-            c->np = np;
-            c->packed = pk;
-            c->ctas_per_sm = cta;
-            c->i_dirty = true;
-            if ((rc = run_into(c, (double *)c->acc.p, (double *)c->pot.p))) break;
-            PG_CUDA(c, cudaEventRecord(e0, c->stream));
-            for (int r = 0; r < 3 && !rc; ++r) rc = run_into(c, (double *)c->acc.p, (double *)c->pot.p);
-            PG_CUDA(c, cudaEventRecord(e1, c->stream));
-            PG_CUDA(c, cudaEventSynchronize(e1));
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (!rc && ms < best) {
-                best = ms;
-                best_np = np;
-                best_cta = cta;
-                best_pk = pk;
-            }
+    const bool groups_path = c->have_groups || c->box > 0.0 || c->tree_on;
+    const bool narrow = !groups_path && use_narrow(c);
+    const bool table = c->mode == PG_TABLE;
+    auto chk = [&](cudaError_t e, const char *where) { return e == cudaSuccess ? PG_OK : cuda_fail(c, e, where); };
+    auto trial = [&](int np, int pk, int cta, int split) {
+        c->np = np;
+        c->packed = pk;
+        c->ctas_per_sm = cta;
+        c->split = split;
+        c->i_dirty = true;
+        if ((rc = run_into(c, (double *)c->acc.p, (double *)c->pot.p))) return;
+        if ((rc = chk(cudaEventRecord(e0, c->stream), "cudaEventRecord"))) return;
+        for (int r = 0; r < 3 && !rc; ++r) rc = run_into(c, (double *)c->acc.p, (double *)c->pot.p);
+        if (rc) return;
+        if ((rc = chk(cudaEventRecord(e1, c->stream), "cudaEventRecord"))) return;
+        if ((rc = chk(cudaEventSynchronize(e1), "cudaEventSynchronize"))) return;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_np = np;
+            best_cta = cta;
+            best_pk = pk;
+            best_split = split;
         }
+    };
+    const int nps[3] = {1, 2, 4};
+    for (int np : nps) {
         if (rc) break;
+        if (narrow) {
+            for (int split = 1; split <= 4 && !rc; split *= 2) trial(np, c->packed, 0, split);
+            continue;
+        }
+        for (int pk = groups_path ? 1 : 0; pk <= 1 && !rc; ++pk) {
+            const int occ = groups_path
+                                ? groups_max_blocks_per_sm(np, table, tab_units(c), c->box > 0.0 && !c->have_groups,
+                                                           use_ext(c))
+                                : allpairs_max_blocks_per_sm(np, table, tab_units(c), pk != 0, use_ext(c));
+            for (int cta = std::max(1, occ - 1); cta <= occ && !rc; ++cta) trial(np, pk, cta, c->split);
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->np = best_np;
     c->ctas_per_sm = best_cta;
     c->packed = best_pk;
+    c->split = best_split;
     c->i_dirty = true;
     c->use_graph = graph;
     drop_graph(c);

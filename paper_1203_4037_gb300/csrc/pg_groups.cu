@@ -446,6 +446,9 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
 // i-particles and its first j tile are all in flight while the current
 // item's last tile is evaluated.
 constexpr int kWarpTJ = 128;        // j entries per warp-staged tile
+// in the CTA-mode kernel the warps' staging slices (4 kWarpTJ words each)
+// are carved from the CTA staging buffer (4 kTJG words)
+static_assert(kTJG * 4 >= (kNT / 32) * 4 * kWarpTJ, "warp-mode slices must fit the CTA staging buffer");
 constexpr int kWarpItemNi = 32;     // items up to this size (i-particles)
 constexpr long long kWarpItemPairs = 32768;   // and this many pairs go to warp mode
 
