@@ -98,3 +98,46 @@ def test_split_range(pg):
                 c.set_split(bad)
             assert e.value.code == pg.PG_EINVAL
         c.set_split(0)
+
+
+def test_tune_tree(pg, orc):
+    x, m = gen.plummer(20000, 83)
+    with pg.Context(0) as c:
+        c.set_eps(1e-3)
+        c.set_self(True)
+        c.set_tree(0.75, 64, 8)
+        c.set_j(x, m)
+        c.set_i(x)
+        c.tune()
+        c.run()
+        a, p = c.get_force(len(x))
+        assert c.info()["i_per_thread"] in (2, 4, 8)
+    ao, po = orc.tree_forces(x, m, 1e-3, 0.75, 64, 8)
+    assert_parity(rel_vec(a, ao), what="a")
+    assert_parity(rel_scalar(p, po), what="phi")
+
+
+def test_tune_cell_list(pg, orc):
+    n = 1 << 14
+    x, m = gen.clustered_box(n, 84, nclump=10, sigma=0.01)
+    r_cut, E, F = 0.05, 4, 8
+    par = [r_cut / 4.5, r_cut / 72]
+    v = orc.table_values(E, F, r_cut, orc.SHAPE_GAUSS_SPLIT, par)
+    with pg.Context(0) as c:
+        c.set_mode(pg.PG_TABLE)
+        c.set_table_values(v, r_cut, E, F)
+        c.set_self(True)
+        c.set_periodic(1.0)
+        c.set_j(x, m)
+        c.set_i(x)
+        c.tune()
+        c.run()
+        a, _ = c.get_force(n)
+        assert c.info()["i_per_thread"] in (2, 4, 8)
+    idx = np.arange(0, n, 8)
+    G0, G1 = orc.table_from_values(E, F, v)
+    ao, amb = orc.table_forces(x[idx], x, m, E, F, r_cut, G0, G1, box=1.0, skip=idx, window=1e-6)
+    norm = np.linalg.norm(ao, axis=1)
+    ok = norm > 0
+    rel = np.maximum(np.linalg.norm(a[idx] - ao, axis=1) - amb, 0)[ok] / norm[ok]
+    assert_parity(rel, what="a vs table semantics")
