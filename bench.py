@@ -285,9 +285,13 @@ def extra_rows(pg, torch, dev, peak_newton, headline_rate):
             c.set_i_dev(xi)
             ms = _time_call(torch, lambda: c.run_dev(a), 50, warm=5)
             kms = c.kernel_time()
+            slots = c.info()["slots"]
+            c.set_graph(True)       # the same call replayed as a CUDA graph
+            ms_graph = _time_call(torch, lambda: c.run_dev(a), 50, warm=5)
             steps[str(ni)] = {"us_per_call": ms * 1e3, "kernel_us": kms * 1e3,
                               "interactions_per_s": ni * n / (ms * 1e-3),
-                              "j_chunks": c.info()["slots"]}
+                              "us_per_call_graph": ms_graph * 1e3,
+                              "j_chunks": slots}
     rows["individual_steps_ni_vs_2e20"] = steps
     del xd, md
 

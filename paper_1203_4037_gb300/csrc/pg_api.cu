@@ -139,6 +139,7 @@ struct pg_ctx {
     bool use_graph = false;
     cudaGraphExec_t gexec = nullptr;
     std::string gkey;
+    bool graph_jhl = false;     // the captured run reads the double-float j records
 
     // force-kernel timing (events recorded as graph nodes while capturing)
     bool capturing = false;
@@ -184,10 +185,15 @@ cudaError_t record_timing(pg_ctx *c, cudaEvent_t ev)
                         : cudaEventRecord(ev, c->stream);
 }
 
+void drop_graph(pg_ctx *c);
+
+// grows device buffer b to hold bytes; a captured graph holds the old
+// address, so a reallocation also drops it
 int ensure(pg_ctx *c, DevBuf &b, size_t bytes)
 {
     if (bytes <= b.cap) return PG_OK;
     if (b.p) {
+        drop_graph(c);
         cudaStreamSynchronize(c->stream);
         cudaFree(b.p);
         b.p = nullptr;
@@ -242,6 +248,7 @@ void drop_graph(pg_ctx *c)
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     c->gexec = nullptr;
     c->gkey.clear();
+    c->graph_jhl = false;
 }
 
 long long nj_of(const pg_ctx *c) { return c->nj_n >= 0 ? c->nj_n : c->nj_hw; }
@@ -1299,11 +1306,16 @@ int launch_group_warp_kernel(pg_ctx *c, const GroupArgs &g, int wper)
 }
 
 // the j records as double-float pairs for the groups kernel; repacked only
-// after the records changed, or always while a graph is being captured (the
-// replays must repack whatever the records then hold)
+// after the records changed. A captured graph does not hold the packing: the
+// uncaptured run just before the capture packed the records, and a replay
+// packs them first when they changed since (run_into)
 int pack_j_hilo(pg_ctx *c, long long nj)
 {
-    if (!c->capturing && c->jhl_n == nj) return PG_OK;
+    if (c->capturing) {
+        c->graph_jhl = true;
+        return PG_OK;
+    }
+    if (c->jhl_n == nj) return PG_OK;
     PG_CUDA(c, launch_pack_hilo((const double4 *)c->jrec.p, nj, (float4 *)c->g_jhl.p, c->stream));
     c->last_launches += 1;
     c->jhl_n = nj;
@@ -1850,6 +1862,11 @@ int run_into(pg_ctx *c, double *acc, double *pot)
         if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
         c->gkey = key;
         return PG_OK;
+    }
+    if (c->graph_jhl && c->jhl_n != nj_of(c)) {      // new j records since the capture
+        PG_CUDA(c, launch_pack_hilo((const double4 *)c->jrec.p, nj_of(c), (float4 *)c->g_jhl.p,
+                                    c->stream));
+        c->jhl_n = nj_of(c);
     }
     PG_CUDA(c, cudaGraphLaunch(c->gexec, c->stream));
     return PG_OK;

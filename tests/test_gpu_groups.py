@@ -56,6 +56,25 @@ def test_graph_replay_matches(pg, small):
     assert np.array_equal(a1, a2) and np.array_equal(p1, p2)
 
 
+def test_graph_replay_sees_new_j(pg, orc, small):
+    d = small
+    xj2 = d["xj"][:, [1, 2, 0]].copy()
+    with pg.Context(0) as c:
+        c.set_eps(1e-3)
+        c.set_graph(True)
+        c.set_j(d["xj"], d["mj"])
+        c.set_i(d["xi"])
+        c.set_groups(d["i_off"], d["j_off"], d["jlist"])
+        for _ in range(3):          # uncaptured, captured, replayed
+            c.run()
+        c.set_j(xj2, d["mj"])
+        c.run()                     # replay with new records
+        a, p = c.get_force(len(d["xi"]))
+    ao, po = orc.newton_groups(d["i_off"], d["j_off"], d["jlist"], d["xi"], xj2, d["mj"], 1e-3)
+    assert_parity(rel_vec(a, ao), what="a")
+    assert_parity(rel_scalar(p, po), what="phi")
+
+
 def test_ragged_and_empty_groups(pg, orc):
     rng = np.random.default_rng(3)
     xj, mj = gen.plummer(6000, 5)

@@ -158,6 +158,35 @@ def test_narrow_new_j_between_calls(pg, orc, jset):
     assert_parity(rel_vec(a, ao), what="a")
 
 
+def test_graph_replay_sees_new_j(pg, orc, jset):
+    # the double-float j packing is not part of the captured graph: a replay
+    # after new records (same count) packs them first
+    xj, mj = jset
+    xi = core_set(24, 9)
+    xj2 = xj[:, ::-1].copy()
+    with pg.Context(0) as c:
+        c.set_allpairs_path(pg.PG_PATH_NARROW)
+        c.set_eps(1e-3)
+        c.set_graph(True)
+        c.set_j(xj, mj)
+        c.set_i(xi)
+        for _ in range(3):          # uncaptured, captured, replayed
+            c.run()
+        a1, p1 = c.get_force(len(xi))
+        c.set_j(xj2, mj)
+        c.run()                     # replay with new records
+        a2, p2 = c.get_force(len(xi))
+        c.set_j(xj, mj)
+        c.run()
+        a3, p3 = c.get_force(len(xi))
+    ao, po = orc.newton(xi, xj, mj, 1e-3)
+    ao2, po2 = orc.newton(xi, xj2, mj, 1e-3)
+    assert_parity(rel_vec(a1, ao), what="a")
+    assert_parity(rel_vec(a2, ao2), what="a after new j")
+    assert_parity(rel_scalar(p2, po2), what="phi after new j")
+    assert np.array_equal(a1, a3) and np.array_equal(p1, p3)
+
+
 def test_narrow_empty_sets(pg):
     xj, mj = gen.plummer(5000, 2)
     with pg.Context(0) as c:
