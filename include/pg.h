@@ -29,8 +29,9 @@
  *     context's stream;
  *   - calls are asynchronous on the context's stream unless stated; the
  *     library never synchronises the device except in pg_get_force,
- *     pg_get_table, pg_sync and pg_tune, and in the setters that copy from
- *     host arrays through pageable memory (pg_set_table, pg_set_table_values,
+ *     pg_get_table, pg_sync, pg_tune and pg_selftest_wait, and in the
+ *     setters that copy from host arrays through pageable memory
+ *     (pg_set_table, pg_set_table_values,
  *     pg_set_table_pot, pg_set_table_pot_values, pg_set_eps_i), which wait
  *     for the context's stream before they return;
  *   - a context is not thread-safe; use one per host thread;
@@ -305,6 +306,14 @@ int pg_run_dev(pg_ctx *ctx, double *a, double *phi);
  * the knot values of the table (dv may be NULL). An extension: the paper has
  * no backward pass. */
 int pg_backward_dev(pg_ctx *ctx, const double *w, double *dx, double *dm, float *dv);
+
+/* The timeout path, checked on the device without a fault: one thread
+ * waits, with the library's time-bounded wait and a limit of limit_ms
+ * (0 < limit_ms <= 2000), on a barrier that nothing completes. The wait gives
+ * up, and the call returns PG_ETIMEOUT as a timed-out run does; the status is
+ * then cleared and the context stays usable. PG_OK would mean the wait did
+ * not give up (a defect). Synchronises. */
+int pg_selftest_wait(pg_ctx *ctx, double limit_ms);
 
 /* Wait for the context's stream and report device-side status. */
 int pg_sync(pg_ctx *ctx);

@@ -66,6 +66,7 @@ SIGNATURES = {
     "pg_tune": (_I, [_P]),
     "pg_set_shape": (_I, [_P, _I, _I, _I]),
     "pg_set_split": (_I, [_P, _I]),
+    "pg_selftest_wait": (_I, [_P, _D]),
     "pg_set_allpairs_path": (_I, [_P, _I]),
     "pg_set_eps_i": (_I, [_P, _P, _LL]),
     "pg_set_eps_i_dev": (_I, [_P, _P, _LL]),
@@ -370,6 +371,10 @@ def pg_kernel_time(ctx):
     return ms.value
 
 
+def pg_selftest_wait(ctx, limit_ms):
+    return _check(ctx, lib().pg_selftest_wait(ctx, float(limit_ms)))
+
+
 def pg_set_split(ctx, items_per_warp):
     return _check(ctx, lib().pg_set_split(ctx, int(items_per_warp)))
 
@@ -571,6 +576,9 @@ class Context:
 
     def set_split(self, items_per_warp):
         pg_set_split(self.h, items_per_warp)
+
+    def selftest_wait(self, limit_ms):
+        pg_selftest_wait(self.h, limit_ms)
 
     def set_timing(self, on=True):
         pg_set_timing(self.h, on)

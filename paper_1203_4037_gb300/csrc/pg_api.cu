@@ -1006,6 +1006,14 @@ int pg_sync(pg_ctx *c)
     return read_status(c);
 }
 
+int pg_selftest_wait(pg_ctx *c, double limit_ms)
+{
+    if (!c) return PG_EINVAL;
+    if (!(limit_ms > 0.0 && limit_ms <= 2000.0)) return fail(c, PG_EINVAL, "limit_ms must be in (0, 2000]");
+    PG_CUDA(c, launch_wait_selftest((int *)c->status.p, (unsigned long long)(limit_ms * 1e6), c->stream));
+    return read_status(c);
+}
+
 }  // extern "C"
 
 // ====================================================================== runs

@@ -205,6 +205,8 @@ cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, bool
                           size_t smem, cudaStream_t st);
 // the FP64 outputs of a groups run made with g.hl set: one thread per i
 cudaError_t launch_groups_finish(const GroupArgs &g, cudaStream_t st);
+// one device-side bounded wait that nothing ends (the timeout path's self-test)
+cudaError_t launch_wait_selftest(int *status, unsigned long long limit_ns, cudaStream_t st);
 cudaError_t launch_pack_hilo(const double4 *in, long long n, float4 *out, cudaStream_t st);
 size_t groups_smem(int np, bool table, int ntab);   // ntab in float2 units, as above
 int groups_bi(int np);

@@ -134,3 +134,29 @@ extern "C" int pg_microbench(int kind, double *per_sm_clock, double *per_second)
     *per_sm_clock = *per_second / ((double)sms * clk_khz * 1e3);
     return PG_OK;
 }
+
+namespace pg {
+
+// The failure path of a bounded device wait: one thread waits on a fresh
+// mbarrier that nothing arrives at, with the library's time-bounded wait and
+// the given limit; the wait gives up and records a timeout in the status
+// word, as a force kernel whose bulk copies never land would.
+__global__ void k_wait_selftest(int *status, unsigned long long limit_ns)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    mbar_fence_init();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (!mbar_wait(&bar, 0u, limit_ns)) report(status, kStatusTimeout, 9);
+        mbar_inval(&bar);
+    }
+}
+
+cudaError_t launch_wait_selftest(int *status, unsigned long long limit_ns, cudaStream_t st)
+{
+    k_wait_selftest<<<1, 32, 0, st>>>(status, limit_ns);
+    return cudaGetLastError();
+}
+
+}  // namespace pg
