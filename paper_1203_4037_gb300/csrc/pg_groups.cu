@@ -10,7 +10,9 @@
 // i-particles in registers. A small group splits each set of i-particles
 // across L lanes, each taking every L-th j, and combines the lanes with warp
 // shuffles. The smallest items (few i-particles and short lists) come last
-// and run one per warp instead of one per CTA.
+// and run one per warp instead of one per CTA: inside the same launch for the
+// caller's groups, in a second kernel (k_groups_warp) for the cell list and
+// the narrow all-pairs path.
 #include "pg_device.cuh"
 
 namespace pg {
@@ -827,10 +829,12 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
                                   lane32, a.queue, 0, (int)gridDim.x * (kNT / 32));
 }
 
-// The warp-mode items alone, in a launch of their own after the CTA-mode
-// items: without the CTA-mode item's registers and staging buffers, more
-// warps fit on an SM, which the short, latency-bound small items need. Every
-// warp claims items warp_from, warp_from + 1, ... from counter queue_w.
+// The warp-mode items alone, in a launch of their own: the cell list's small
+// cells (after the CTA-mode kernel, by programmatic dependent launch) and
+// every item of a narrow all-pairs run whose i chunks fit one warp pass.
+// Without the CTA-mode item's registers and staging buffers, more warps fit
+// on an SM, which the short, latency-bound small items need. Every warp
+// claims items warp_from, warp_from + 1, ... from counter queue_w.
 // Two blocks of 256 threads per SM (16 warps, against 12 in the CTA-mode
 // kernel) at up to 128 registers a thread; three blocks (24 warps) cap the
 // registers at 80, and the spills made the uniform-cell half slower.
