@@ -1294,6 +1294,7 @@ int launch_group_kernel(pg_ctx *c, const GroupArgs &g, bool cell)
 
 // items that are all warp-sized (narrow all-pairs): the warp-mode kernel
 // alone, wper blocks per SM, claiming items 0, 1, ... from the second counter
+// (zeroed by the narrow path's preparation kernel)
 int launch_group_warp_kernel(pg_ctx *c, const GroupArgs &g, int wper)
 {
     const bool table = c->mode == PG_TABLE;
@@ -1303,7 +1304,6 @@ int launch_group_warp_kernel(pg_ctx *c, const GroupArgs &g, int wper)
     gg.queue_w = (int *)c->g_queue.p + 1;
     gg.warp_from = 0;
     c->last_np = 1;                     // one i-pair per lane
-    PG_CUDA(c, cudaMemsetAsync(c->g_queue.p, 0, 2 * sizeof(int), c->stream));
     if (c->timing) PG_CUDA(c, record_timing(c, c->tk0));
     PG_CUDA(c, launch_groups_warp(gg, grid, table, false, use_ext(c), tab_units(c), false, c->stream));
     if (c->timing) PG_CUDA(c, record_timing(c, c->tk1));
@@ -1394,11 +1394,11 @@ int enqueue_narrow(pg_ctx *c, double *acc, double *pot)
         (rc = ensure(c, c->n_part, (size_t)nch * ni * sizeof(double4))) ||
         (rc = ensure(c, c->g_jhl, (size_t)nj * 32)) || (rc = ensure(c, c->g_ihl, (size_t)ni * 32)))
         return rc;
-    PG_CUDA(c, launch_group_ctr((const double4 *)c->xi.p, nullptr, nic, Bi, ni, (double4 *)c->g_ctr.p,
-                                c->stream));
+    // chunk centres, double-float i records and zeroed work counters in one launch
+    PG_CUDA(c, launch_narrow_prep((const double4 *)c->xi.p, ni, Bi, nic, (double4 *)c->g_ctr.p,
+                                  (float4 *)c->g_ihl.p, (int *)c->g_queue.p, c->stream));
     if ((rc = pack_j_hilo(c, nj))) return rc;
-    PG_CUDA(c, launch_pack_hilo((const double4 *)c->xi.p, ni, (float4 *)c->g_ihl.p, c->stream));
-    c->last_launches += 2;
+    c->last_launches += 1;
     GroupArgs g = group_args(c);
     g.xi = (const double4 *)c->xi.p;
     g.jrec = (const double4 *)c->jrec.p;

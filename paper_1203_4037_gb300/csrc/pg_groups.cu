@@ -1121,15 +1121,21 @@ cudaError_t launch_group_partials_combine(const CombineArgs &c, int nchunks, cud
 // double-float records: (hi, w) then (lo, w) per particle, lo = x - hi, w
 // the record's fourth value (the mass of a j record; eps^2 of an i record
 // with per-i softening, else 0)
-__global__ void k_pack_hilo(const double4 *__restrict__ in, long long n, float4 *__restrict__ out)
+__device__ __forceinline__ void pack_hilo_one(const double4 *__restrict__ in, long long i,
+                                              float4 *__restrict__ out)
 {
-    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= n) return;
     double4 v = in[i];
     float hx = (float)v.x, hy = (float)v.y, hz = (float)v.z;
     out[2 * i] = make_float4(hx, hy, hz, (float)v.w);
     out[2 * i + 1] = make_float4((float)(v.x - (double)hx), (float)(v.y - (double)hy),
                                  (float)(v.z - (double)hz), (float)v.w);
+}
+
+__global__ void k_pack_hilo(const double4 *__restrict__ in, long long n, float4 *__restrict__ out)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    pack_hilo_one(in, i, out);
 }
 
 cudaError_t launch_pack_hilo(const double4 *in, long long n, float4 *out, cudaStream_t st)
@@ -1143,13 +1149,11 @@ cudaError_t launch_pack_hilo(const double4 *in, long long n, float4 *out, cudaSt
 // FP64 centre of each group: midpoint of its i-particles' bounding box
 // group g holds i_off[g] .. i_off[g + 1], or without offsets the chunk
 // g chunk .. min((g + 1) chunk, ni)
-__global__ void k_group_ctr(const double4 *__restrict__ xi, const long long *__restrict__ i_off,
-                            long long ngroups, long long chunk, long long ni,
-                            double4 *__restrict__ ctr)
+__device__ __forceinline__ void group_ctr_warp(const double4 *__restrict__ xi,
+                                               const long long *__restrict__ i_off, long long g,
+                                               long long chunk, long long ni, int lane,
+                                               double4 *__restrict__ ctr)
 {
-    long long g = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
-    int lane = threadIdx.x & 31;
-    if (g >= ngroups) return;
     const long long ib = i_off ? i_off[g] : g * chunk;
     const long long ie = i_off ? i_off[g + 1] : min((g + 1) * chunk, ni);
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -1169,6 +1173,43 @@ __global__ void k_group_ctr(const double4 *__restrict__ xi, const long long *__r
                        : make_double4(0.5 * (lo[0] + hi[0]), 0.5 * (lo[1] + hi[1]),
                                       0.5 * (lo[2] + hi[2]), 0.0);
     }
+}
+
+__global__ void k_group_ctr(const double4 *__restrict__ xi, const long long *__restrict__ i_off,
+                            long long ngroups, long long chunk, long long ni,
+                            double4 *__restrict__ ctr)
+{
+    long long g = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (g >= ngroups) return;
+    group_ctr_warp(xi, i_off, g, chunk, ni, threadIdx.x & 31, ctr);
+}
+
+// The narrow path's preparation in one launch: the FP64 centre of each of
+// the nic i chunks (one warp each, blocks [0, cb)), the double-float i
+// records (blocks cb onwards, one thread each), and the two work counters
+// set to zero.
+__global__ void k_narrow_prep(const double4 *__restrict__ xi, long long ni, long long chunk, long long nic,
+                              long long cb, double4 *__restrict__ ctr, float4 *__restrict__ ihl,
+                              int *__restrict__ queue)
+{
+    if (blockIdx.x == 0 && threadIdx.x < 2) queue[threadIdx.x] = 0;
+    if (blockIdx.x < cb) {
+        const long long g = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
+        if (g < nic) group_ctr_warp(xi, nullptr, g, chunk, ni, threadIdx.x & 31, ctr);
+        return;
+    }
+    const long long i = (blockIdx.x - cb) * (long long)blockDim.x + threadIdx.x;
+    if (i < ni) pack_hilo_one(xi, i, ihl);
+}
+
+cudaError_t launch_narrow_prep(const double4 *xi, long long ni, long long chunk, long long nic,
+                              double4 *ctr, float4 *ihl, int *queue, cudaStream_t st)
+{
+    if (ni <= 0 || nic <= 0) return cudaErrorInvalidValue;
+    const long long cb = (nic + 3) / 4;                  // 4 warps of 128 threads
+    const long long pb = (ni + 127) / 128;
+    k_narrow_prep<<<(unsigned)(cb + pb), 128, 0, st>>>(xi, ni, chunk, nic, cb, ctr, ihl, queue);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_group_ctr(const double4 *xi, const long long *i_off, long long ngroups,

@@ -208,6 +208,10 @@ cudaError_t launch_groups_finish(const GroupArgs &g, cudaStream_t st);
 // one device-side bounded wait that nothing ends (the timeout path's self-test)
 cudaError_t launch_wait_selftest(int *status, unsigned long long limit_ns, cudaStream_t st);
 cudaError_t launch_pack_hilo(const double4 *in, long long n, float4 *out, cudaStream_t st);
+// narrow path: chunk centres (chunks of `chunk` i, nic of them), double-float
+// i records and the two work counters zeroed, in one launch
+cudaError_t launch_narrow_prep(const double4 *xi, long long ni, long long chunk, long long nic,
+                              double4 *ctr, float4 *ihl, int *queue, cudaStream_t st);
 size_t groups_smem(int np, bool table, int ntab);   // ntab in float2 units, as above
 int groups_bi(int np);
 int groups_max_blocks_per_sm(int np, bool table, int ntab, bool cell, bool ext = false);
