@@ -1807,8 +1807,11 @@ int enqueue_run(pg_ctx *c, double *acc, double *pot)
         if ((rc = prep_sort(c, std::max<long long>(nj_of(c), c->ni)))) return rc;
         std::string err;
         int launches = 0;
+        // the targets are the cell list's particles: its cell order keeps
+        // neighbours together for the interpolation, so no second sort
         rc = pm_run(c->pm, (const double4 *)c->jrec.p, nj_of(c), (const double4 *)c->xi.p, c->ni, c->box,
-                    c->pm_n, c->pm_split, c->pm_scale, acc, pot, true, c->sort, c->stream, &launches, err);
+                    c->pm_n, c->pm_split, c->pm_scale, acc, pot, true, c->sort, c->stream, &launches, err,
+                    c->cells.perm);
         if (rc) return fail(c, rc, err);
         c->last_launches += launches;
         return PG_OK;

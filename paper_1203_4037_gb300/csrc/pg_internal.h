@@ -168,9 +168,12 @@ cudaError_t launch_radix_sort(unsigned *keys, unsigned *vals, long long n, int k
 struct PmState;
 PmState *pm_create();
 void pm_destroy(PmState *s);
+// tgt_order: an interpolation order of the targets to use instead of sorting
+// them into mesh order (a permutation of 0 .. nt-1 that keeps neighbours
+// together; the cell list's cell order), or nullptr
 int pm_run(PmState *s, const double4 *src, long long ns, const double4 *tgt, long long nt, double L, int N,
            int split, double scale, double *acc, double *pot, bool add, SortScratch &sort, cudaStream_t st,
-           int *launches, std::string &err);
+           int *launches, std::string &err, const unsigned *tgt_order = nullptr);
 // the same in two steps, for sources split across ranks: pm_deposit writes
 // the density mesh of its sources into rho (N^3 FP32, row-major, z fastest;
 // mass per cell volume), which the ranks sum; pm_solve computes the fields

@@ -337,21 +337,31 @@ int key_bits_of(int N)
 // the mesh records of n records (input order, in mj_raw / md_raw); with
 // sorted, also in mesh order (mj_out / md_out) and perm_keep = mesh order ->
 // input index
+// mesh records of n particles; sorted: also gathered into an interpolation
+// order kept in perm_keep, mesh order by a radix sort of the keys, or the
+// caller's order (a permutation of 0 .. n-1 that already keeps neighbours
+// together, such as the cell list's) without a sort
 cudaError_t records(PmState *s, const double4 *rec, long long n, bool sorted, int4 *mj_out, float4 *md_out,
-                    unsigned *perm_keep, SortScratch &sort, cudaStream_t st, int *launches)
+                    unsigned *perm_keep, SortScratch &sort, cudaStream_t st, int *launches,
+                    const unsigned *order = nullptr)
 {
     const int N = s->N;
     k_pm_keys<<<blocks256(n), 256, 0, st>>>(rec, n, N / s->L, N, sort.keys[0], sort.vals[0], s->mj_raw,
                                             s->md_raw);
     if (launches) *launches += 1;
     if (!sorted) return cudaGetLastError();
-    const int kb = key_bits_of(N);
-    unsigned *ko = nullptr, *perm = nullptr;
-    cudaError_t e = launch_radix_sort(sort.keys[0], sort.vals[0], n, kb, sort, &ko, &perm, st);
-    if (e != cudaSuccess) return e;
+    const unsigned *perm = order;
+    if (!perm) {
+        const int kb = key_bits_of(N);
+        unsigned *ko = nullptr, *sp = nullptr;
+        cudaError_t e = launch_radix_sort(sort.keys[0], sort.vals[0], n, kb, sort, &ko, &sp, st);
+        if (e != cudaSuccess) return e;
+        perm = sp;
+        if (launches) *launches += (kb + 7) / 8 * 5;
+    }
     k_pm_gather<<<blocks256(n), 256, 0, st>>>(s->mj_raw, s->md_raw, perm, n, mj_out, md_out);
     cudaMemcpyAsync(perm_keep, perm, n * sizeof(unsigned), cudaMemcpyDeviceToDevice, st);
-    if (launches) *launches += 1 + (kb + 7) / 8 * 5;
+    if (launches) *launches += 1;
     return cudaGetLastError();
 }
 
@@ -405,17 +415,19 @@ int finish(std::string &err)
 
 int pm_run(PmState *s, const double4 *src, long long ns, const double4 *tgt, long long nt, double L, int N,
            int split, double scale, double *acc, double *pot, bool add, SortScratch &sort, cudaStream_t st,
-           int *launches, std::string &err)
+           int *launches, std::string &err, const unsigned *tgt_order)
 {
     int rc = ensure(s, L, N, split, scale, std::max(ns, nt), err);
     if (rc) return rc;
     // the sources deposited in input order; the targets interpolated in mesh
     // order (one set of records when they are the same particles)
     const bool same = src == tgt && ns == nt;
-    cudaError_t e = records(s, src, ns, same, s->mj_tgt, s->md_tgt, s->perm_tgt, sort, st, launches);
+    cudaError_t e = records(s, src, ns, same, s->mj_tgt, s->md_tgt, s->perm_tgt, sort, st, launches,
+                            same ? tgt_order : nullptr);
     if (e == cudaSuccess) {
         deposit(s, s->mj_raw, s->md_raw, ns, s->rho, st, launches);
-        if (!same) e = records(s, tgt, nt, true, s->mj_tgt, s->md_tgt, s->perm_tgt, sort, st, launches);
+        if (!same)
+            e = records(s, tgt, nt, true, s->mj_tgt, s->md_tgt, s->perm_tgt, sort, st, launches, tgt_order);
     }
     if (e != cudaSuccess) {
         err = cudaGetErrorString(e);
