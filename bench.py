@@ -240,6 +240,54 @@ def _time_call(torch, fn, reps, warm=3):
     return e0.elapsed_time(e1) / reps
 
 
+# Oracle comparisons of every result, deferred to the oracle leg of the run
+# (after all GPU timing, with the CPU baseline): each entry is (row name,
+# function of the oracle module returning the row's "error" block). Only
+# sampled GPU outputs are kept; the oracle recomputes from the same inputs.
+CHECKS = []
+
+ERR_NOTE = ("per-particle relative |da|/|a| (and |dphi|/|phi|) against the FP64 oracle of the "
+            "same inputs; Newton tolerance: median 2e-6, max 1e-4")
+
+
+def err_stats(a, ao, p=None, po=None, sample=None):
+    ea = np.linalg.norm(np.asarray(a) - ao, axis=1) / np.linalg.norm(ao, axis=1)
+    out = {"a_median": float(np.median(ea)), "a_max": float(np.max(ea))}
+    if p is not None and po is not None:
+        ep = np.abs(np.asarray(p) - po) / np.abs(po)
+        out.update(phi_median=float(np.median(ep)), phi_max=float(np.max(ep)))
+    if sample:
+        out["sample"] = sample
+    return out
+
+
+def err_ref(a, p, ref, sample=None):
+    """err_stats against an oracle result ref = (acc, pot)."""
+    return err_stats(a, ref[0], p, ref[1], sample)
+
+
+def table_err(orc, a, x, idx, m, E, F, r_cut, par, box=0.0):
+    """Tabulated forces at x[idx] against the table semantics (O-T2: the
+    paper's interpolant, per-particle relative, after the cutoff allowance
+    of pairs within 1e-6 of s_max) and the closed form (O-T1: error over the
+    sum of the pair terms' magnitudes, the per-pair bound of Section 4.2)."""
+    v = orc.table_values(E, F, r_cut, orc.SHAPE_GAUSS_SPLIT, par)
+    G0, G1 = orc.table_from_values(E, F, v)
+    ao, amb = orc.table_forces(x[idx], x, m, E, F, r_cut, G0, G1, box=box, skip=idx, window=1e-6)
+    norm = np.linalg.norm(ao, axis=1)
+    ok = norm > 0
+    rel = np.maximum(np.linalg.norm(a - ao, axis=1) - amb, 0)[ok] / norm[ok]
+    ac, ambc, absum = orc.shape_forces(x[idx], x, m, orc.SHAPE_GAUSS_SPLIT, par, r_cut, box=box,
+                                       skip=idx, window=1e-6, with_absum=True)
+    okc = absum > 0
+    relc = np.maximum(np.linalg.norm(a - ac, axis=1) - ambc, 0)[okc] / absum[okc]
+    return {"vs_table_semantics_median": float(np.median(rel)),
+            "vs_table_semantics_max": float(np.max(rel)),
+            "vs_closed_form_over_abs_sum_median": float(np.median(relc)),
+            "vs_closed_form_over_abs_sum_max": float(np.max(relc)),
+            "sample": f"{len(idx)} i against all {len(x)} j"}, ao
+
+
 def extra_rows(pg, torch, dev, peak_newton, headline_rate):
     """The other rows of the path, each timed on its own workload (not the
     headline): the 4096-body Plummer call (latency-bound, CUDA graph), the
@@ -265,6 +313,10 @@ def extra_rows(pg, torch, dev, peak_newton, headline_rate):
         ms = _time_call(torch, lambda: c.run_dev(a, p), 200, warm=20)
         rows["newton_plummer_4096"] = {"interactions_per_s": 4096 * 4096 / (ms * 1e-3),
                                        "us_per_call": ms * 1e3, "graph": True}
+        a4, p4 = a.cpu().numpy(), p.cpu().numpy()
+        CHECKS.append(("newton_plummer_4096",
+                       lambda orc, x=x, m=m, a4=a4, p4=p4: err_ref(
+                           a4, p4, orc.newton_allpairs(x, m, 1 / 64), "all 4096")))
 
     # individual time steps: the i-set is the n_i densest-core particles of the
     # 2^20 mixed set (those with the shortest steps), j = all 2^20; per call
@@ -292,6 +344,10 @@ def extra_rows(pg, torch, dev, peak_newton, headline_rate):
                               "interactions_per_s": ni * n / (ms * 1e-3),
                               "us_per_call_graph": ms_graph * 1e3,
                               "j_chunks": slots}
+            ai = a.cpu().numpy()
+            CHECKS.append((f"individual_steps_ni_vs_2e20/{ni}",
+                           lambda orc, xi=x[order[:ni]], ai=ai, x=x, m=m: err_stats(
+                               ai, orc.newton(xi, x, m, 1e-3)[0], sample=f"all {len(xi)} i")))
     rows["individual_steps_ni_vs_2e20"] = steps
     del xd, md
 
@@ -318,7 +374,15 @@ def extra_rows(pg, torch, dev, peak_newton, headline_rate):
                 kms = c.kernel_time()
                 info = c.info()
                 t = c.get_tree()
-                rows[f"tree_{model}_2e20_theta075_{'quadrupole' if quad else 'monopole'}"] = {
+                key = f"tree_{model}_2e20_theta075_{'quadrupole' if quad else 'monopole'}"
+                tidx = gen.sample_indices(n, 1024, 61)
+                at, pt = a[torch.tensor(tidx, device=dev)].cpu().numpy(), p[torch.tensor(tidx, device=dev)].cpu().numpy()
+                CHECKS.append((key, lambda orc, x=x, m=m, tidx=tidx, at=at, pt=pt: dict(
+                    err_ref(at, pt, orc.newton_subset(x, m, EPS, tidx),
+                            f"{len(tidx)} particles against the direct sum"),
+                    note="the tree method's own error against the direct sum (its lists are "
+                         "bit-identical to the oracle tree's, checked in the tests)")))
+                rows[key] = {
                     "ms_per_call": ms, "force_kernel_ms": kms, "pairs": info["pairs"],
                     "interactions_per_s_kernel": info["pairs"] / (kms * 1e-3),
                     "nodes": t["nnodes"], "groups": t["ngroups"], "list_entries": t["nlist"],
@@ -342,6 +406,11 @@ def extra_rows(pg, torch, dev, peak_newton, headline_rate):
         c.set_i_dev(xd)
         kms = _time_kernel(c, lambda: c.run_dev(a))
         rate = n * n / (kms * 1e-3)
+        tidx = gen.sample_indices(n, 1024, 62)
+        at = a[torch.tensor(tidx, device=dev)].cpu().numpy()
+        CHECKS.append(("table_allpairs_65536_E3F5",
+                       lambda orc, x=x, m=m, tidx=tidx, at=at: table_err(
+                           orc, at, x, tidx, m, 3, 5, r_cut, [r_cut / 4.5, 1 / 64])[0]))
         # the same with the potential table (psi = -(r^2 + eps^2)^(-1/2))
         c.set_table_pot(lambda r: -1.0 / math.sqrt(r * r + (1 / 64) ** 2))
         kms_p = _time_kernel(c, lambda: c.run_dev(a))
@@ -355,6 +424,11 @@ def extra_rows(pg, torch, dev, peak_newton, headline_rate):
         e = np.exp(np.random.default_rng(9).uniform(np.log(1 / 256), np.log(1 / 16), n))
         c.set_eps_i(e)
         kms_e = _time_kernel(c, lambda: c.run_dev(a))
+        ae = a[torch.tensor(tidx, device=dev)].cpu().numpy()
+        CHECKS.append(("newton_per_i_softening_65536",
+                       lambda orc, x=x, m=m, e=e, tidx=tidx, ae=ae: err_stats(
+                           ae, orc.newton_epsi(x[tidx], e[tidx], x, m, skip=tidx)[0],
+                           sample=f"{len(tidx)} i against all {len(x)} j")))
         c.set_eps_i(None)
         c.set_eps(1 / 64)
         kms_g = _time_kernel(c, lambda: c.run_dev(a))
@@ -379,6 +453,34 @@ def extra_rows(pg, torch, dev, peak_newton, headline_rate):
         c.set_table(lambda r: gauss_split(r, r_cut / 4.5, 1 / 64), r_cut, 3, 5)
         dv = torch.empty(256, dtype=torch.float32, device=dev)
         bwd_t = _time_kernel(c, lambda: c.backward_dev(w, dx, dm, dv))
+        gidx = gen.sample_indices(n, 64, 63)
+        gsel = torch.tensor(gidx, device=dev)
+        wn = w.cpu().numpy()
+        # the Newton gradients of the last Newton backward, recomputed here
+        c.set_mode(pg.PG_NEWTON)
+        c.backward_dev(w, dx, dm)
+        gdx_n, gdm_n = dx[gsel].cpu().numpy(), dm[gsel].cpu().numpy()
+        c.set_mode(pg.PG_TABLE)
+        c.backward_dev(w, dx, dm, dv)
+        gdx_t, gdm_t, gdv = dx[gsel].cpu().numpy(), dm[gsel].cpu().numpy(), dv.cpu().numpy()
+
+        def grad_err(orc, x=x, m=m, wn=wn, gidx=gidx, gdx_n=gdx_n, gdm_n=gdm_n, gdx_t=gdx_t,
+                     gdm_t=gdm_t, gdv=gdv):
+            ox, om = orc.grad_newton_at(x, m, wn, 1 / 64, gidx)
+            v = orc.table_values(3, 5, r_cut, orc.SHAPE_GAUSS_SPLIT, [r_cut / 4.5, 1 / 64])
+            tx, tm = orc.grad_table_at(x, m, wn, 3, 5, r_cut, v, gidx)
+            tv = orc.grad_table_v(x, m, wn, 3, 5, r_cut, v)
+            nz = tv != 0
+
+            def nrm(g, o):
+                return float(np.linalg.norm(np.ravel(g) - np.ravel(o)) / np.linalg.norm(np.ravel(o)))
+            return {"newton_dx": nrm(gdx_n, ox), "newton_dm": nrm(gdm_n, om),
+                    "table_dx": nrm(gdx_t, tx), "table_dm": nrm(gdm_t, tm),
+                    "table_dv": nrm(gdv[nz], tv[nz]),
+                    "sample": f"norm-wise relative against the oracle's analytic FP64 gradient "
+                              f"at {len(gidx)} particles (all knots with pairs for dv); "
+                              f"tolerance 1e-4"}
+        CHECKS.append(("backward_65536", grad_err))
         rows["backward_65536"] = {
             "newton_forward_kernel_ms": fwd, "newton_backward_kernel_ms": bwd,
             "newton_backward_interactions_per_s": n * n / (bwd * 1e-3),
@@ -409,12 +511,57 @@ def extra_rows(pg, torch, dev, peak_newton, headline_rate):
                                    "interactions_per_s": rate, "frac_fp32_peak": rate / peak_table,
                                    "call_ms_with_cell_build": call,
                                    "interactions_per_s_with_build": pairs / (call * 1e-3)}
+        try:
+            # ordered pairs i != j closer than r_cut: the useful part of the
+            # evaluated pairs (a k-d tree count with the periodic box)
+            from scipy.spatial import cKDTree
+            useful = int(cKDTree(x, boxsize=1.0).query_ball_point(
+                x, 4.5 * rs, return_length=True, workers=-1).sum()) - n
+            rows["cells_2e21_E4F8"].update(pairs_useful=useful,
+                                           useful_per_s=useful / (kms * 1e-3),
+                                           useful_fraction=useful / pairs)
+        except Exception as exc:  # report, do not hide
+            rows["cells_2e21_E4F8"]["pairs_useful_error"] = repr(exc)
+        cidx = gen.sample_indices(n, 1024, 64)
+        csel = torch.tensor(cidx, device=dev)
+        ac = a[csel].cpu().numpy()
+        cells_ref = {}
+
+        def cells_err(orc, x=x, m=m, cidx=cidx, ac=ac):
+            e, ao = table_err(orc, ac, x, cidx, m, 4, 8, 4.5 * rs, [rs, rs / 16], box=1.0)
+            cells_ref["pp"] = ao
+            return e
+        CHECKS.append(("cells_2e21_E4F8", cells_err))
         # PPPM / TreePM: the same split's long range on a 256^3 mesh (r_s = h),
         # alone and added to the cell-list PP in one run
         p = torch.empty_like(md)
         c.set_pm(256, pg.PG_SPLIT_GAUSS, rs)
         call_pp_pm = _time_call(torch, lambda: c.run_dev(a), 5, warm=2)
+        app = a[csel].cpu().numpy()
         pm_ms = _time_call(torch, lambda: c.pm_forces_dev(xd, md, a, p), 5, warm=2)
+        apm, ppm = a[csel].cpu().numpy(), p[csel].cpu().numpy()
+
+        def pm_err(orc, x=x, m=m, cidx=cidx, apm=apm, ppm=ppm, app=app):
+            from oracle import pm as opm
+            rho = opm.deposit(x, m, 1.0, 256)
+            ao, po = opm.solve(rho, x[cidx], 1.0, 256, "gauss", rs)
+            cells_ref["pm"] = ao
+            rms = float(np.sqrt(np.mean(np.sum(ao ** 2, axis=1))))
+            prms = float(np.sqrt(np.mean(po ** 2)))
+            ea = np.linalg.norm(apm - ao, axis=1) / rms
+            out = {"a_over_rms_median": float(np.median(ea)), "a_over_rms_max": float(ea.max()),
+                   "phi_over_rms_max": float(np.max(np.abs(ppm - po)) / prms),
+                   "sample": f"{len(cidx)} particles; tolerance median 1e-5, max 1e-4 of the RMS"}
+            return out
+
+        def pppm_err(orc, cidx=cidx, app=app):
+            ref = cells_ref["pp"] + cells_ref["pm"]
+            e = np.linalg.norm(app - ref, axis=1) / np.linalg.norm(ref, axis=1)
+            return {"a_median": float(np.median(e)), "a_max": float(np.max(e)),
+                    "sample": f"{len(cidx)} particles against the table-semantics PP plus the "
+                              "oracle mesh"}
+        CHECKS.append(("pm_2e21_mesh256_gauss", pm_err))
+        CHECKS.append(("pp_plus_pm_2e21_E4F8_mesh256", pppm_err))
         rows["pm_2e21_mesh256_gauss"] = {"ms_per_call": pm_ms, "particles_per_s": n / (pm_ms * 1e-3),
                                          "mesh": 256, "r_s_over_h": 1.0}
         rows["pp_plus_pm_2e21_E4F8_mesh256"] = {"ms_per_call": call_pp_pm,
@@ -442,6 +589,20 @@ def extra_rows(pg, torch, dev, peak_newton, headline_rate):
         c.set_graph(True)
         call = _time_call(torch, lambda: c.run_dev(a, p), 5, warm=2)
         rate = pairs / (kms * 1e-3)
+        # 400 groups of the 20000, their lists and i-particles, for the oracle
+        gsel = gen.sample_indices(len(d["i_off"]) - 1, 400, 65)
+        io, jo = d["i_off"], d["j_off"]
+        ii = np.concatenate([np.arange(io[g], io[g + 1]) for g in gsel])
+        s_ioff = np.concatenate([[0], np.cumsum(io[gsel + 1] - io[gsel])])
+        s_joff = np.concatenate([[0], np.cumsum(jo[gsel + 1] - jo[gsel])])
+        s_jl = np.concatenate([d["jlist"][jo[g]:jo[g + 1]] for g in gsel])
+        ag = a[torch.tensor(ii, device=dev)].cpu().numpy()
+        pgv = p[torch.tensor(ii, device=dev)].cpu().numpy()
+        CHECKS.append(("groups_20000",
+                       lambda orc, d=d, ii=ii, s_ioff=s_ioff, s_joff=s_joff, s_jl=s_jl, ag=ag, pgv=pgv:
+                       err_ref(ag, pgv, orc.newton_groups(s_ioff, s_joff, s_jl, d["xi"][ii], d["xj"],
+                                                          d["mj"], 1e-3),
+                               f"400 groups ({len(ii)} i) with their lists")))
         rows["groups_20000"] = {"pairs": pairs, "kernel_ms": kms, "interactions_per_s": rate,
                                 "frac_fp32_peak": rate / peak_newton,
                                 "call_ms_graph": call,
@@ -585,7 +746,7 @@ def main():
     import torch
     import torch.distributed as dist
     import paper_1203_4037_gb300 as pg
-    from paper_1203_4037_gb300.multirank import max_over_ranks, shard
+    from paper_1203_4037_gb300.multirank import ShardedAllPairs, max_over_ranks, shard
 
     rank, world, local = dist_env()
     if world > 1:
@@ -600,12 +761,16 @@ def main():
     if args.quick:
         args.no_rows = args.no_cpu_baseline = True
     x, m = gen.plummer_cube_mix(npart, gen.CONFIG_SEEDS[2])
+    if world > 1:
+        # domain decomposition: each rank owns a Morton-contiguous run of the
+        # particles, so its i-tiles are as compact as on one GPU
+        order = gen.morton_order(x)
+        x, m = x[order], m[order]
     lo, hi = shard(npart, rank, world)
     ni = hi - lo
     st = torch.cuda.current_stream()
-    xj = torch.tensor(x, device=dev)
-    mj = torch.tensor(m, device=dev)
-    xi = xj[lo:hi].contiguous()
+    xi = torch.tensor(x[lo:hi], device=dev)      # this rank's particles
+    mi = torch.tensor(m[lo:hi], device=dev)
     acc = torch.empty((ni, 3), dtype=torch.float64, device=dev)
     pot = torch.empty(ni, dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
@@ -614,18 +779,18 @@ def main():
     ctx.set_stream(st.cuda_stream)
     ctx.set_eps(EPS)
     ctx.set_timing(True)
-    ctx.set_j_dev(xj, mj)
-    # the i-particles of this rank are j-particles lo .. hi-1: self pairs drop
-    # out through the self mode only when the ranges coincide (world == 1)
-    ctx.set_self(world == 1)
-    ctx.set_i_dev(xi)
     if args.shape:
         np_, packed = (int(v) for v in args.shape.split(","))
         ctx.set_shape(np_, 0, packed)
+    # every step: this rank's records all-gathered from every rank (NCCL; a
+    # copy on one GPU), then its slice against all of them, own pairs left
+    # out through the self mode with the slice's offset
+    gather = (dist.all_gather_into_tensor if world > 1
+              else (lambda out, inp: out.copy_(inp)))
+    sharded = ShardedAllPairs(ctx, npart, rank, world, gather, device=dev)
 
     def step():
-        ctx.set_i_dev(xi)            # i staging every step (positions change in a run)
-        ctx.run_dev(acc, pot)
+        sharded.forces(xi, mi, acc, pot)
 
     warmup_done = max(args.warmup, 3)   # at least 3 untimed steps
     for _ in range(warmup_done):
@@ -653,16 +818,45 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = max_over_ranks(sum(step_ms), device=dev)
     info = ctx.info()
+    # the timed step's outputs at a fixed 4096-particle sample, kept for the
+    # oracle comparison (made after all GPU timing)
+    hidx = gen.sample_indices(ni, min(4096, ni), 4244)
+    hsel = torch.tensor(hidx, device=dev)
+    h_a, h_p = acc[hsel].cpu().numpy(), pot[hsel].cpu().numpy()
     pairs_job = npart * npart                      # all ranks together, one step
     value = pairs_job * args.steps / (total_ms * 1e-3)
 
     # end to end through the public host API: pinned-host inputs in, results out
     e2e = None
-    if rank == 0 and not args.quick:
+    if world > 1 and not args.quick:
+        # every rank: its slice from pinned host memory, the exchange and the
+        # force evaluation, its results back to the host
+        xh = torch.tensor(x[lo:hi]).pin_memory()
+        mh = torch.tensor(m[lo:hi]).pin_memory()
+        ah = torch.empty((ni, 3), dtype=torch.float64).pin_memory()
+        ph = torch.empty(ni, dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            xi.copy_(xh, non_blocking=True)
+            mi.copy_(mh, non_blocking=True)
+            sharded.forces(xi, mi, acc, pot)
+            ah.copy_(acc, non_blocking=True)
+            ph.copy_(pot, non_blocking=True)
+            st.synchronize()
+        e2e_step()
+        ne = max(2, min(args.steps, 3))
+        dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(ne):
+            e2e_step()
+        dt = max_over_ranks(time.perf_counter() - t0, device=dev)
+        e2e = {"value": npart * npart * ne / dt, "unit": "interactions/s",
+               "h2d_bytes_per_step": npart * 32, "d2h_bytes_per_step": npart * 32, "steps": ne}
+    elif rank == 0 and not args.quick:
         xh_i = np.ascontiguousarray(x[lo:hi])
         ctx2 = pg.Context(local)
         ctx2.set_eps(EPS)
-        ctx2.set_self(world == 1)
+        ctx2.set_self(True)
         for _ in range(2):
             ctx2.set_j(x, m)
             ctx2.set_i(xh_i)
@@ -727,20 +921,43 @@ def main():
     except Exception as exc:  # report, do not hide
         roof["microbench_error"] = repr(exc)
     cpu = None
+    error = None
     if not args.no_cpu_baseline:
+        # the oracle leg: the CPU baseline, then every result against the oracle
         cpu = cpu_baseline(x, m)
+        import oracle
+        try:
+            error = err_ref(h_a, h_p, oracle.newton_subset(x, m, EPS, lo + hidx),
+                            f"{len(hidx)} i (fixed sample) against all {npart} j")
+            error["note"] = ERR_NOTE
+        except Exception as exc:  # report, do not hide
+            error = {"error": repr(exc)}
+        if rows and "error" not in rows:
+            for key, fn in CHECKS:
+                parts = key.split("/")
+                dst = rows
+                for k in parts:
+                    dst = dst.setdefault(k, {})
+                try:
+                    dst["error"] = fn(oracle)
+                except Exception as exc:  # report, do not hide
+                    dst["error"] = {"error": repr(exc)}
     line = {
         "metric": "interactions/s", "value": value, "unit": "interactions/s", "n_gpus": world,
         "steps": args.steps, "warmup": warmup_done, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+        "exchange": ("one all-gather of the 32-byte j records per step (NCCL), inside the timed "
+                     "step" if world > 1 else "none (one GPU: the records are copied in place)"),
         "data": "synthetic",
         "config": {"workload": "newton-allpairs-2^20-plummer+cube" if npart == N_PART else
                    f"newton-allpairs-{npart}-plummer+cube", "n": npart, "eps": EPS,
                    "positions": "fp64 in, fp32 offsets from fp64 tile centres",
                    "accumulation": "fp32 per 256-j sub-tile, TwoSum across, fp64 combine",
                    "l2": "flushed between timed steps (256 MB write)",
-                   "parallelism": f"i-range split over {world} GPU(s)"},
+                   "parallelism": (f"particles split over {world} GPUs (Morton-contiguous slices), "
+                                   "j records all-gathered every step" if world > 1 else "1 GPU")},
         "gflops_at_38": value * PAPER_FLOPS_PER_INT / 1e9,
+        "error": error,
         "roofline": roof,
         "clocks": clk,
         "e2e": e2e,

@@ -66,6 +66,11 @@ typedef struct pg_ctx pg_ctx;
 #define PG_PATH_TILED 1   /* i tiles of 256 to 1024 particles, j split across CTAs */
 #define PG_PATH_NARROW 2  /* few i against many j: (i chunk, j chunk) items */
 
+/* how the all-pairs paths form pair differences (pg_set_differencing) */
+#define PG_DIFF_AUTO 0    /* double-float where i-tiles are not compact (the default) */
+#define PG_DIFF_SINGLE 1  /* one FP32 offset per particle from an FP64 tile centre */
+#define PG_DIFF_DOUBLE 2  /* double-float on every all-pairs run */
+
 /* long-range split of the particle-mesh part (pg_set_pm) */
 #define PG_SPLIT_GAUSS 0  /* D(k) = exp(-k^2 r_s^2): the erf split of the Gaussian-split PP shape */
 #define PG_SPLIT_S2 1     /* D(k) = S(k a)^2: Hockney and Eastwood's S2 clouds of diameter a */
@@ -253,6 +258,13 @@ int pg_set_j(pg_ctx *ctx, long long adr, long long nj, const double *x, const do
 /* Device twin of pg_set_j: x (device double[nj][3]), m (device double[nj]). */
 int pg_set_j_dev(pg_ctx *ctx, long long adr, long long nj, const double *x, const double *m);
 
+/* j-particles adr .. adr+nj-1 as packed records rec (device double[nj][4]:
+ * x, y, z, m per particle, the library's own record layout), copied in
+ * stream order with one device copy: for records that arrive packed, such
+ * as a buffer all-gathered from every rank's particles each step. An
+ * extension (the paper's API takes positions and masses apart). */
+int pg_set_j_rec_dev(pg_ctx *ctx, long long adr, long long nj, const double *rec);
+
 /* The i-particles of the next pg_run: x (host double[ni][3]). Copies. */
 int pg_set_i(pg_ctx *ctx, long long ni, const double *x);
 
@@ -264,6 +276,17 @@ int pg_set_i_dev(pg_ctx *ctx, long long ni, const double *x);
  * in the double-precision reference of Section 4.1. Requires ni <= nj and
  * bit-identical positions. on = 0 (default): every j counts. */
 int pg_set_self(pg_ctx *ctx, int on);
+
+/* Self mode with an offset, for an i-range that is part of the j-set:
+ * i-particle k is j-particle lo + k (positions bit-identical), and its own
+ * pair is left out of the sums as in pg_set_self. This is the self mode of
+ * one rank of a run whose particles are split across ranks (each rank's
+ * i-particles are its own slice of the all-gathered j records, which start
+ * at lo). Requires lo + ni <= nj at pg_run (PG_ESTATE otherwise) and the
+ * all-pairs paths (no groups, tree or periodic box: PG_ESTATE). lo = 0 is
+ * pg_set_self(ctx, 1); pg_set_self(ctx, 0) turns the mode off. PG_EINVAL
+ * for lo < 0. */
+int pg_set_self_offset(pg_ctx *ctx, long long lo);
 
 /* Batched tree-style lists (the usage of Section 5.1: each group of
  * i-particles shares one interaction list). Group g covers the i-particles
@@ -333,6 +356,24 @@ int pg_set_graph(pg_ctx *ctx, int on);
  * Synchronises. */
 int pg_tune(pg_ctx *ctx);
 
+/* Pair differences of the all-pairs paths (tiled and narrow). Positions are
+ * FP64 (the inputs of Section 4.1); the pair loop runs in FP32. PG_DIFF_SINGLE
+ * converts each particle once to an FP32 offset from its i-tile's FP64 centre
+ * and differences the offsets: 13 FP32-pipe operations per Newton
+ * interaction, with a difference error of about 2^-24 of the tile's extent,
+ * small against |d| only when tiles are compact next to their close pairs.
+ * PG_DIFF_DOUBLE also stages each offset's FP32 rounding residual and forms
+ * d = (x~_j - x~_i) + (e_j - e_i): 3 more operations per component, an error
+ * of a few 2^-24 of |d| itself whatever the tiles' extent. PG_DIFF_AUTO (the
+ * default) takes single on PG_NEWTON tiled runs whose i-particles are
+ * Morton-ordered (from 16384 on) and at least an eighth as many as the
+ * j-particles, and double on every other tiled run (PG_TABLE included: the
+ * shape's steep fall toward r_cut magnifies a difference's error) and on the
+ * narrow path. pg_info's out[7] reports
+ * what the last run used. Groups, tree lists and the cell list keep their
+ * own forms. PG_EINVAL for another mode. */
+int pg_set_differencing(pg_ctx *ctx, int mode);
+
 /* Narrow all-pairs path: cut the j records into about items_per_warp work
  * items per warp of the launch (1 to 8; 0 = the default, one). pg_info's
  * out[6] reports the value a narrow run used. Returns PG_EINVAL outside
@@ -370,14 +411,19 @@ int pg_kernel_time(pg_ctx *ctx, double *ms);
 /* Counters: out[0] pair evaluations enqueued by the last run, out[1] kernel
  * launches of the last run, out[2] i per thread, out[3] grid size of the
  * force kernel, out[4] partial slots per tile, out[5] 1 if the pair arithmetic
- * is packed FP32x2, out[6] items per warp of a narrow run (0 for other paths).
- * Returns how many were written (at most 7). */
+ * is packed FP32x2, out[6] items per warp of a narrow run (0 for other paths),
+ * out[7] 1 if the pair differences were formed in double-float (FP32 offset
+ * plus its FP32 residual: the narrow path, and tiled runs whose i-tiles are
+ * not compact), 0 if from one FP32 offset per particle.
+ * Returns how many were written (at most 8). */
 int pg_info(pg_ctx *ctx, long long *out, int n);
 
 /* Measured ceilings on the current device for the roofline (a tool of this
  * library; the paper quotes only its CPU's peak): kind 0 scalar FP32 FMA,
  * 1 packed FP32x2 FMA (lane operations), 2 MUFU rsqrt, 3 the Newton pair
- * term with every operand in registers (interactions). Writes the rate per
+ * term with every operand in registers (interactions), 4 random 8-byte
+ * gathers from a 4096-entry table in shared memory (lane gathers: the
+ * tabulated force's lookup when a warp's pairs hit random bins). Writes the rate per
  * SM per clock (at the device's maximum clock) and per second. Synchronises
  * the legacy default stream. */
 int pg_microbench(int kind, double *per_sm_clock, double *per_second);
@@ -396,6 +442,11 @@ int pg_microbench(int kind, double *per_sm_clock, double *per_second);
  *   x: device double[n][3], m: device double[n], a: device double[n][3] out,
  *   phi: device double[n] out or NULL; eps >= 0; cuda_stream: cudaStream_t
  *   (NULL: the legacy default stream); the current device is used.
+ * The i-particles keep the caller's order, so pair differences are formed
+ * in double-float (FP32 offset plus its FP32 residual), accurate to FP32
+ * relative to |d| however the particles are spread; eps = 0 gives a
+ * coincident pair no contribution. If a device-side wait of the force
+ * kernel gives up (bounded at two seconds), every output of the call is NaN.
  * Returns PG_EINVAL when n > PG_NOALLOC_MAX_N (or other bad arguments),
  * PG_ECUDA when a launch fails; asynchronous otherwise. The first call on a
  * device looks up the scratch array's device address: make it before any

@@ -24,6 +24,7 @@ PG_OK, PG_EINVAL, PG_ESTATE, PG_ENOMEM, PG_ECUDA, PG_ETIMEOUT = 0, -1, -2, -3, -
 PG_NEWTON, PG_TABLE = 0, 1
 PG_PATH_AUTO, PG_PATH_TILED, PG_PATH_NARROW = 0, 1, 2
 PG_SPLIT_GAUSS, PG_SPLIT_S2 = 0, 1
+PG_DIFF_AUTO, PG_DIFF_SINGLE, PG_DIFF_DOUBLE = 0, 1, 2
 
 STATUS_NAMES = {0: "PG_OK", -1: "PG_EINVAL", -2: "PG_ESTATE", -3: "PG_ENOMEM", -4: "PG_ECUDA",
                 -5: "PG_ETIMEOUT"}
@@ -54,6 +55,8 @@ SIGNATURES = {
     "pg_set_i": (_I, [_P, _LL, _P]),
     "pg_set_i_dev": (_I, [_P, _LL, _P]),
     "pg_set_self": (_I, [_P, _I]),
+    "pg_set_self_offset": (_I, [_P, _LL]),
+    "pg_set_j_rec_dev": (_I, [_P, _LL, _LL, _P]),
     "pg_set_groups": (_I, [_P, _LL, _P, _P, _P]),
     "pg_clear_groups": (_I, [_P]),
     "pg_set_periodic": (_I, [_P, _D]),
@@ -66,6 +69,7 @@ SIGNATURES = {
     "pg_tune": (_I, [_P]),
     "pg_set_shape": (_I, [_P, _I, _I, _I]),
     "pg_set_split": (_I, [_P, _I]),
+    "pg_set_differencing": (_I, [_P, _I]),
     "pg_selftest_wait": (_I, [_P, _D]),
     "pg_set_allpairs_path": (_I, [_P, _I]),
     "pg_set_eps_i": (_I, [_P, _P, _LL]),
@@ -293,6 +297,14 @@ def pg_set_j_dev(ctx, adr, nj, x, m):
     return _check(ctx, lib().pg_set_j_dev(ctx, int(adr), int(nj), _ptr(x), _ptr(m)))
 
 
+def pg_set_j_rec_dev(ctx, adr, nj, rec):
+    return _check(ctx, lib().pg_set_j_rec_dev(ctx, int(adr), int(nj), _ptr(rec)))
+
+
+def pg_set_self_offset(ctx, lo):
+    return _check(ctx, lib().pg_set_self_offset(ctx, int(lo)))
+
+
 def pg_set_i(ctx, x):
     x = _host_f64(x, 3)
     return _check(ctx, lib().pg_set_i(ctx, len(x), _ptr(x)))
@@ -379,16 +391,21 @@ def pg_set_split(ctx, items_per_warp):
     return _check(ctx, lib().pg_set_split(ctx, int(items_per_warp)))
 
 
+def pg_set_differencing(ctx, mode):
+    return _check(ctx, lib().pg_set_differencing(ctx, int(mode)))
+
+
 def pg_info(ctx):
-    out = (_LL * 7)()
-    n = lib().pg_info(ctx, out, 7)
-    keys = ["pairs", "launches", "i_per_thread", "grid", "slots", "packed", "split"]
+    out = (_LL * 8)()
+    n = lib().pg_info(ctx, out, 8)
+    keys = ["pairs", "launches", "i_per_thread", "grid", "slots", "packed", "split", "df"]
     return dict(zip(keys[:n], list(out)[:n]))
 
 
 def pg_microbench(kind):
     """(rate per SM per clock, rate per second) of: 0 FFMA, 1 FFMA2 lane ops,
-    2 MUFU rsqrt, 3 Newton pair-term interactions with register operands."""
+    2 MUFU rsqrt, 3 Newton pair-term interactions with register operands,
+    4 random 8-byte gathers from a 4096-entry shared-memory table."""
     a, b = C.c_double(), C.c_double()
     rc = lib().pg_microbench(int(kind), C.byref(a), C.byref(b))
     if rc != PG_OK:
@@ -511,6 +528,16 @@ class Context:
     def set_self(self, on=True):
         pg_set_self(self.h, on)
 
+    def set_self_offset(self, lo):
+        pg_set_self_offset(self.h, lo)
+
+    def set_j_rec_dev(self, rec, adr=0):
+        """j records as a CUDA float64 tensor (n, 4): x, y, z, m."""
+        _require_dev(rec)
+        if str(rec.dtype) != "torch.float64" or rec.dim() != 2 or rec.shape[1] != 4:
+            raise ValueError("rec must be a contiguous float64 (n, 4) tensor")
+        pg_set_j_rec_dev(self.h, adr, rec.shape[0], rec)
+
     def set_groups(self, i_off, j_off, jlist):
         pg_set_groups(self.h, i_off, j_off, jlist)
 
@@ -576,6 +603,9 @@ class Context:
 
     def set_split(self, items_per_warp):
         pg_set_split(self.h, items_per_warp)
+
+    def set_differencing(self, mode):
+        pg_set_differencing(self.h, mode)
 
     def selftest_wait(self, limit_ms):
         pg_selftest_wait(self.h, limit_ms)

@@ -22,6 +22,16 @@
 //    the MUFU rsqrt; each sub-tile's FP32 partial is folded into a TwoSum
 //    (hi, lo) pair; the per-CTA partials are combined in FP64.
 //
+// DF selects double-float differencing, for i-tiles that are not compact
+// (i-particles not in Morton order, or few i against many more j): each
+// FP32 offset x~ = fp32(x - c) is staged with its FP32 residual
+// e = fp32((x - c) - x~), and a pair's difference is formed as
+// (x~_j - x~_i) + (e_j - e_i). Its error is then a few units of FP32
+// rounding of |d| itself, whatever the tile's extent; with one FP32 offset
+// per particle it is a few units of the offsets' magnitude, which for a
+// close pair inside a wide tile is far more (3 more lane operations per
+// component and pair).
+//
 // EXT selects the extended form of each mode: in Newton mode the softening
 // of each i-particle read from its record (w = eps_i^2: the i-particle
 // structure of Section 3.1 carries eps^2 per i), with a guard that gives a
@@ -72,6 +82,7 @@ struct Lanes;
 template <>
 struct Lanes<true> {
     static __device__ __forceinline__ u64 fma(u64 a, u64 b, u64 c) { return f2fma(a, b, c); }
+    static __device__ __forceinline__ u64 add(u64 a, u64 b) { return f2add(a, b); }
     static __device__ __forceinline__ u64 sub(u64 a, u64 b) { return f2sub(a, b); }
     static __device__ __forceinline__ u64 mul(u64 a, u64 b) { return f2mul(a, b); }
 };
@@ -83,6 +94,12 @@ struct Lanes<false> {
         float a0, a1, b0, b1, c0, c1;
         up2(a, a0, a1); up2(b, b0, b1); up2(c, c0, c1);
         return pk2(__fmaf_rn(a0, b0, c0), __fmaf_rn(a1, b1, c1));
+    }
+    static __device__ __forceinline__ u64 add(u64 a, u64 b)
+    {
+        float a0, a1, b0, b1;
+        up2(a, a0, a1); up2(b, b0, b1);
+        return pk2(__fadd_rn(a0, b0), __fadd_rn(a1, b1));
     }
     static __device__ __forceinline__ u64 sub(u64 a, u64 b)
     {
@@ -113,25 +130,33 @@ struct Lanes<false> {
 #endif
 #define PG_STR_(x) #x
 #define PG_UNROLL(n) _Pragma(PG_STR_(unroll n))
-template <int NP, bool TABLE>
+// (the double-float variant holds three more i-pair registers per pair and
+// the residuals in flight: one block fewer, so that it does not spill)
+template <int NP, bool TABLE, bool DF>
 struct MinBlocks {
-    static constexpr int value = NP == 1 ? 8 : NP == 2 ? 5
+    static constexpr int value = DF ? (NP == 1 ? 6 : NP == 2 ? 4 : 2)
+                               : NP == 1 ? 8 : NP == 2 ? 5
                                : TABLE ? PG_TABLE_NP4_MIN_BLOCKS : PG_NP4_MIN_BLOCKS;
 };
 
-template <int NP, bool TABLE, bool EXT, bool PK>
-__global__ void __launch_bounds__(kNT, MinBlocks<NP, TABLE>::value) k_allpairs(AllPairsArgs a)
+// u64 words staged per j record: {x, y, z, m} (each value in both lanes),
+// with DF also {e_x, e_y, e_z, 0}
+template <bool DF> struct CvtWords { static constexpr int value = DF ? 8 : 4; };
+
+template <int NP, bool TABLE, bool EXT, bool PK, bool DF>
+__global__ void __launch_bounds__(kNT, MinBlocks<NP, TABLE, DF>::value) k_allpairs(AllPairsArgs a)
 {
     using V = Lanes<PK>;
     constexpr int Bi = Bi_of<NP>::value;
+    constexpr int kW = CvtWords<DF>::value;
     extern __shared__ __align__(128) unsigned char smem[];
     double4 *raw = reinterpret_cast<double4 *>(smem);                       // [2][kTJ]
-    u64 *cvt = reinterpret_cast<u64 *>(smem + 2 * kTJ * sizeof(double4));   // [kTJ][4]
+    u64 *cvt = reinterpret_cast<u64 *>(smem + 2 * kTJ * sizeof(double4));   // [kTJ][kW]
     // compensated running sums (hi, lo) of every thread's i, [2 kComp NP][kNT]
     // (kComp = 4: a and phi; 3 in table mode without a potential): they
     // change once per sub-tile, so they live in shared memory
     constexpr int kComp = TABLE && !EXT ? 3 : 4;
-    u64 *run = cvt + kTJ * 4;
+    u64 *run = cvt + kTJ * kW;
     uint64_t *bar = reinterpret_cast<uint64_t *>(run + 2 * kComp * NP * kNT);
     int *flag = reinterpret_cast<int *>(bar + 2);
     float2 *tab = reinterpret_cast<float2 *>(bar + 4);
@@ -167,6 +192,7 @@ __global__ void __launch_bounds__(kNT, MinBlocks<NP, TABLE>::value) k_allpairs(A
 
     // per-thread state
     u64 xi[NP], yi[NP], zi[NP];
+    u64 exi[DF ? NP : 1], eyi[DF ? NP : 1], ezi[DF ? NP : 1];   // DF: the offsets' residuals
     u64 e2i[NP];                                 // Newton EXT: each i-pair's eps^2
     u64 ax[NP], ay[NP], az[NP], ph[NP];          // sub-tile partials
     // running sum k of pair p: hi at run[(2 kComp p + k) kNT + tid], lo at k + kComp
@@ -218,23 +244,32 @@ __global__ void __launch_bounds__(kNT, MinBlocks<NP, TABLE>::value) k_allpairs(A
             cx = c.x; cy = c.y; cz = c.z;
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
-                float fx[2], fy[2], fz[2], fe[2];
+                float fx[2], fy[2], fz[2], fe[2], rx[2], ry[2], rz[2];
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
                     long long i = t * Bi + (2 * p + q) * kNT + tid;
                     if (i < a.ni) {
                         double4 v = a.xi[i];
-                        fx[q] = (float)((v.x - cx) * sc);
-                        fy[q] = (float)((v.y - cy) * sc);
-                        fz[q] = (float)((v.z - cz) * sc);
+                        const double ox = (v.x - cx) * sc, oy = (v.y - cy) * sc, oz = (v.z - cz) * sc;
+                        fx[q] = (float)ox;
+                        fy[q] = (float)oy;
+                        fz[q] = (float)oz;
+                        rx[q] = (float)(ox - (double)fx[q]);
+                        ry[q] = (float)(oy - (double)fy[q]);
+                        rz[q] = (float)(oz - (double)fz[q]);
                         fe[q] = (float)v.w;
                     } else {
-                        fx[q] = fy[q] = fz[q] = fe[q] = 0.0f;
+                        fx[q] = fy[q] = fz[q] = fe[q] = rx[q] = ry[q] = rz[q] = 0.0f;
                     }
                 }
                 xi[p] = pk2(fx[0], fx[1]);
                 yi[p] = pk2(fy[0], fy[1]);
                 zi[p] = pk2(fz[0], fz[1]);
+                if (DF) {
+                    exi[p] = pk2(rx[0], rx[1]);
+                    eyi[p] = pk2(ry[0], ry[1]);
+                    ezi[p] = pk2(rz[0], rz[1]);
+                }
                 e2i[p] = pk2(fe[0], fe[1]);
 #pragma unroll
                 for (int k = 0; k < kComp; ++k) RH(p, k) = RL(p, k) = zero2;
@@ -251,29 +286,42 @@ __global__ void __launch_bounds__(kNT, MinBlocks<NP, TABLE>::value) k_allpairs(A
         if (*flag == 0) { failed = true; break; }
         phase ^= 1u << buf;
 
-        // convert: FP64 record minus FP64 tile centre, rounded once to FP32;
-        // each value is stored twice so one 16-byte load yields f32x2 pairs
+        // convert: FP64 record minus FP64 tile centre, rounded once to FP32
+        // (DF: and the residual of that rounding); each value is stored
+        // twice so one 16-byte load yields f32x2 pairs
         {
             const long long j0 = (long long)s * kTJ;
             long long nv = a.nj - j0;
             if (nv > kTJ) nv = kTJ;
             const double4 *r = raw + buf * kTJ;
             for (int e = tid; e < kTJ; e += kNT) {
-                float x, y, z, m;
+                float x, y, z, m, rx = 0.0f, ry = 0.0f, rz = 0.0f;
                 if (e < nv) {
                     double4 v = r[e];
-                    x = (float)((v.x - cx) * sc);
-                    y = (float)((v.y - cy) * sc);
-                    z = (float)((v.z - cz) * sc);
+                    const double ox = (v.x - cx) * sc, oy = (v.y - cy) * sc, oz = (v.z - cz) * sc;
+                    x = (float)ox;
+                    y = (float)oy;
+                    z = (float)oz;
+                    if (DF) {
+                        rx = (float)(ox - (double)x);
+                        ry = (float)(oy - (double)y);
+                        rz = (float)(oz - (double)z);
+                    }
                     m = (float)v.w;
                 } else {   // padding: zero mass far away contributes exactly 0
                     x = y = z = 1.0e4f;
                     m = 0.0f;
                 }
-                cvt[4 * e + 0] = pk2(x, x);
-                cvt[4 * e + 1] = pk2(y, y);
-                cvt[4 * e + 2] = pk2(z, z);
-                cvt[4 * e + 3] = pk2(m, m);
+                cvt[kW * e + 0] = pk2(x, x);
+                cvt[kW * e + 1] = pk2(y, y);
+                cvt[kW * e + 2] = pk2(z, z);
+                cvt[kW * e + 3] = pk2(m, m);
+                if (DF) {
+                    cvt[kW * e + 4] = pk2(rx, rx);
+                    cvt[kW * e + 5] = pk2(ry, ry);
+                    cvt[kW * e + 6] = pk2(rz, rz);
+                    cvt[kW * e + 7] = 0ull;
+                }
             }
         }
         __syncthreads();
@@ -289,13 +337,23 @@ __global__ void __launch_bounds__(kNT, MinBlocks<NP, TABLE>::value) k_allpairs(A
 
         PG_UNROLL(PG_AP_UNROLL)
         for (int e = 0; e < kTJ; ++e) {
-            const ulonglong2 xy = reinterpret_cast<const ulonglong2 *>(cvt)[2 * e];
-            const ulonglong2 zm = reinterpret_cast<const ulonglong2 *>(cvt)[2 * e + 1];
+            const ulonglong2 xy = reinterpret_cast<const ulonglong2 *>(cvt)[(kW / 2) * e];
+            const ulonglong2 zm = reinterpret_cast<const ulonglong2 *>(cvt)[(kW / 2) * e + 1];
+            ulonglong2 rxy = make_ulonglong2(0ull, 0ull), rz0 = rxy;
+            if (DF) {
+                rxy = reinterpret_cast<const ulonglong2 *>(cvt)[(kW / 2) * e + 2];
+                rz0 = reinterpret_cast<const ulonglong2 *>(cvt)[(kW / 2) * e + 3];
+            }
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
-                const u64 dx = V::sub(xy.x, xi[p]);
-                const u64 dy = V::sub(xy.y, yi[p]);
-                const u64 dz = V::sub(zm.x, zi[p]);
+                u64 dx = V::sub(xy.x, xi[p]);
+                u64 dy = V::sub(xy.y, yi[p]);
+                u64 dz = V::sub(zm.x, zi[p]);
+                if (DF) {
+                    dx = V::add(dx, V::sub(rxy.x, exi[p]));
+                    dy = V::add(dy, V::sub(rxy.y, eyi[p]));
+                    dz = V::add(dz, V::sub(rz0.x, ezi[p]));
+                }
                 u64 r2 = V::fma(dx, dx, !TABLE && EXT ? e2i[p] : c0v);
                 r2 = V::fma(dy, dy, r2);
                 r2 = V::fma(dz, dz, r2);
@@ -364,87 +422,95 @@ __global__ void __launch_bounds__(kNT, MinBlocks<NP, TABLE>::value) k_allpairs(A
 
 // ------------------------------------------------------------------ host
 
-size_t allpairs_smem(int np, bool table, int ntab, bool ext)
+size_t allpairs_smem(int np, bool table, int ntab, bool ext, bool df)
 {
-    size_t s = 2 * kTJ * sizeof(double4) + kTJ * 4 * sizeof(u64) +
+    size_t s = 2 * kTJ * sizeof(double4) + (size_t)kTJ * (df ? 8 : 4) * sizeof(u64) +
                2 * (table && !ext ? 3 : 4) * np * kNT * sizeof(u64) + 4 * sizeof(uint64_t);
     if (table) s += (size_t)ntab * sizeof(float2);
     return s;
 }
 
-// raise the kernel's dynamic shared memory limit once (outside any capture)
-template <int NP, bool TABLE, bool EXT, bool PK>
+// raise the kernel's dynamic shared memory limit once per device (outside
+// any capture); the attribute belongs to the device's context
+template <int NP, bool TABLE, bool EXT, bool PK, bool DF>
 static cudaError_t configure_one()
 {
-    static bool done = false;
-    if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_allpairs<NP, TABLE, EXT, PK>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)allpairs_smem(NP, TABLE, 2 << 13, EXT));
-    done = e == cudaSuccess;
-    return e;
+    static bool done[kMaxDevices] = {};
+    return once_per_device(done, [] {
+        return cudaFuncSetAttribute(k_allpairs<NP, TABLE, EXT, PK, DF>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)allpairs_smem(NP, TABLE, 2 << 13, EXT, DF));
+    });
 }
 
-template <int NP, bool TABLE, bool EXT, bool PK>
+template <int NP, bool TABLE, bool EXT, bool PK, bool DF>
 static cudaError_t launch_one(const AllPairsArgs &a, int grid, size_t smem, cudaStream_t st)
 {
-    cudaError_t e = configure_one<NP, TABLE, EXT, PK>();
+    cudaError_t e = configure_one<NP, TABLE, EXT, PK, DF>();
     if (e != cudaSuccess) return e;
-    k_allpairs<NP, TABLE, EXT, PK><<<grid, kNT, smem, st>>>(a);
+    k_allpairs<NP, TABLE, EXT, PK, DF><<<grid, kNT, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int NP, bool TABLE, bool EXT, bool PK>
+template <int NP, bool TABLE, bool EXT, bool PK, bool DF>
 static int occupancy_one(size_t smem)
 {
-    auto k = k_allpairs<NP, TABLE, EXT, PK>;
-    if (configure_one<NP, TABLE, EXT, PK>() != cudaSuccess) return 1;
+    auto k = k_allpairs<NP, TABLE, EXT, PK, DF>;
+    if (configure_one<NP, TABLE, EXT, PK, DF>() != cudaSuccess) return 1;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kNT, smem) != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
 }
 
-template <int NP, bool PK>
+// the double-float variant exists in packed form only (the same roundings)
+template <int NP, bool PK, bool DF>
 static int occupancy_pk(bool table, bool ext, size_t smem)
 {
-    if (table) return ext ? occupancy_one<NP, true, true, PK>(smem) : occupancy_one<NP, true, false, PK>(smem);
-    return ext ? occupancy_one<NP, false, true, PK>(smem) : occupancy_one<NP, false, false, PK>(smem);
+    if (table) return ext ? occupancy_one<NP, true, true, PK, DF>(smem) : occupancy_one<NP, true, false, PK, DF>(smem);
+    return ext ? occupancy_one<NP, false, true, PK, DF>(smem) : occupancy_one<NP, false, false, PK, DF>(smem);
 }
 
 template <int NP>
-static int occupancy_np(bool table, bool packed, bool ext, size_t smem)
+static int occupancy_np(bool table, bool packed, bool ext, bool df, size_t smem)
 {
-    return packed ? occupancy_pk<NP, true>(table, ext, smem) : occupancy_pk<NP, false>(table, ext, smem);
+    if (df) return occupancy_pk<NP, true, true>(table, ext, smem);
+    return packed ? occupancy_pk<NP, true, false>(table, ext, smem) : occupancy_pk<NP, false, false>(table, ext, smem);
 }
 
-int allpairs_max_blocks_per_sm(int np, bool table, int ntab, bool packed, bool ext)
+int allpairs_max_blocks_per_sm(int np, bool table, int ntab, bool packed, bool ext, bool df)
 {
-    size_t smem = allpairs_smem(np, table, ntab, ext);
-    return np == 1 ? occupancy_np<1>(table, packed, ext, smem)
-         : np == 4 ? occupancy_np<4>(table, packed, ext, smem)
-                   : occupancy_np<2>(table, packed, ext, smem);
+    size_t smem = allpairs_smem(np, table, ntab, ext, df);
+    return np == 1 ? occupancy_np<1>(table, packed, ext, df, smem)
+         : np == 4 ? occupancy_np<4>(table, packed, ext, df, smem)
+                   : occupancy_np<2>(table, packed, ext, df, smem);
 }
 
-template <int NP, bool PK>
+template <int NP, bool PK, bool DF>
 static cudaError_t launch_np(const AllPairsArgs &a, int grid, bool table, bool ext, size_t smem,
                              cudaStream_t st)
 {
-    if (table) return ext ? launch_one<NP, true, true, PK>(a, grid, smem, st)
-                          : launch_one<NP, true, false, PK>(a, grid, smem, st);
-    return ext ? launch_one<NP, false, true, PK>(a, grid, smem, st)
-               : launch_one<NP, false, false, PK>(a, grid, smem, st);
+    if (table) return ext ? launch_one<NP, true, true, PK, DF>(a, grid, smem, st)
+                          : launch_one<NP, true, false, PK, DF>(a, grid, smem, st);
+    return ext ? launch_one<NP, false, true, PK, DF>(a, grid, smem, st)
+               : launch_one<NP, false, false, PK, DF>(a, grid, smem, st);
+}
+
+template <int NP>
+static cudaError_t launch_np_any(const AllPairsArgs &a, int grid, bool table, bool ext, bool packed,
+                                 bool df, size_t smem, cudaStream_t st)
+{
+    if (df) return launch_np<NP, true, true>(a, grid, table, ext, smem, st);
+    return packed ? launch_np<NP, true, false>(a, grid, table, ext, smem, st)
+                  : launch_np<NP, false, false>(a, grid, table, ext, smem, st);
 }
 
 cudaError_t launch_allpairs(const AllPairsArgs &a, int grid, int np, bool table, bool ext,
-                            bool packed, size_t smem, cudaStream_t st)
+                            bool packed, bool df, size_t smem, cudaStream_t st)
 {
     if (grid <= 0) return cudaSuccess;
-    if (np == 1) return packed ? launch_np<1, true>(a, grid, table, ext, smem, st)
-                               : launch_np<1, false>(a, grid, table, ext, smem, st);
-    if (np == 2) return packed ? launch_np<2, true>(a, grid, table, ext, smem, st)
-                               : launch_np<2, false>(a, grid, table, ext, smem, st);
-    if (np == 4) return packed ? launch_np<4, true>(a, grid, table, ext, smem, st)
-                               : launch_np<4, false>(a, grid, table, ext, smem, st);
+    if (np == 1) return launch_np_any<1>(a, grid, table, ext, packed, df, smem, st);
+    if (np == 2) return launch_np_any<2>(a, grid, table, ext, packed, df, smem, st);
+    if (np == 4) return launch_np_any<4>(a, grid, table, ext, packed, df, smem, st);
     return cudaErrorInvalidValue;
 }
 
@@ -468,6 +534,7 @@ __global__ void k_combine(CombineArgs c)
     }
     long long k = c.perm ? (long long)c.perm[p] : p;
     if (c.self && c.njsub > 0) ph -= self_potential(c, k);
+    if (c.fail_nan && *c.fail_nan != 0) ax = ay = az = ph = __longlong_as_double(0x7ff8000000000000ll);
     c.acc[3 * k] = ax * c.accscale;
     c.acc[3 * k + 1] = ay * c.accscale;
     c.acc[3 * k + 2] = az * c.accscale;
@@ -513,6 +580,7 @@ __global__ void __launch_bounds__(kWideThreads) k_combine_wide(CombineArgs c)
     }
     const long long k = c.perm ? (long long)c.perm[p] : p;
     if (c.self && c.njsub > 0) ph -= self_potential(c, k);
+    if (c.fail_nan && *c.fail_nan != 0) ax = ay = az = ph = __longlong_as_double(0x7ff8000000000000ll);
     c.acc[3 * k] = ax * c.accscale;
     c.acc[3 * k + 1] = ay * c.accscale;
     c.acc[3 * k + 2] = az * c.accscale;

@@ -74,6 +74,8 @@ struct pg_ctx {
 
     // outputs and partials
     DevBuf acc, pot, part;
+    DevBuf tickets;               // the small path's per-tile tickets (kept at zero between runs)
+    size_t tickets_zeroed = 0;    // bytes of it known to be zero
     DevBuf status;                // 2 ints
 
     // host staging
@@ -125,6 +127,7 @@ struct pg_ctx {
     int path = PG_PATH_AUTO;
     DevBuf n_part;
     long long jhl_n = -1;         // j records in g_jhl as double-float pairs (-1: stale)
+    long long ihl_n = -1;         // i-particles in g_ihl as double-float pairs, caller order (-1: stale)
 
     // backward
     DevBuf bw_wj, bw_wt, bw_dv;
@@ -149,6 +152,9 @@ struct pg_ctx {
 
     // stats of the last run
     int last_np = 2;
+    int diff_mode = 0;            // PG_DIFF_AUTO / SINGLE / DOUBLE (all-pairs paths)
+    long long self_off = 0;       // self mode: i-particle k is j-particle self_off + k
+    bool last_df = false;         // the last force kernel differenced in double-float
     long long last_pairs = 0, last_launches = 0, last_grid = 0, last_slots = 0, last_split = 0;
 
     std::string err;
@@ -194,10 +200,12 @@ int ensure(pg_ctx *c, DevBuf &b, size_t bytes)
     if (bytes <= b.cap) return PG_OK;
     if (b.p) {
         drop_graph(c);
-        cudaStreamSynchronize(c->stream);
+        // a fault of earlier work surfaces here, not at a later call
+        const cudaError_t se = cudaStreamSynchronize(c->stream);
         cudaFree(b.p);
         b.p = nullptr;
         b.cap = 0;
+        if (se != cudaSuccess) return cuda_fail(c, se, "synchronisation before a buffer reallocation");
     }
     size_t want = std::max<size_t>(bytes, 256);
     if (cudaMalloc(&b.p, want) != cudaSuccess) {
@@ -389,6 +397,7 @@ int read_status(pg_ctx *c)
 }
 
 int prep_sort(pg_ctx *c, long long n);   // below, with the tree
+int pack_j_hilo(pg_ctx *c, long long nj); // below, with the groups
 
 }  // namespace
 
@@ -449,7 +458,7 @@ void pg_destroy(pg_ctx *c)
                       &c->c_wrapped, &c->c_xs, &c->c_xo, &c->c_perm, &c->c_start, &c->c_jcount,
                       &c->c_icount, &c->c_ioff,
                       &c->c_items_raw, &c->c_items, &c->c_pairs, &c->n_part, &c->bw_wj,
-                      &c->bw_wt, &c->bw_dv};
+                      &c->bw_wt, &c->bw_dv, &c->tickets};
     for (DevBuf *b : bufs) free_dev(*b);
     for (DevBuf &b : c->tb) free_dev(b);
     for (DevBuf *b : {&c->pm_rec, &c->pm_x, &c->pm_m, &c->pm_acc, &c->pm_pot}) free_dev(*b);
@@ -849,6 +858,21 @@ int pg_set_j(pg_ctx *c, long long adr, long long nj, const double *x, const doub
     return PG_OK;
 }
 
+int pg_set_j_rec_dev(pg_ctx *c, long long adr, long long nj, const double *rec)
+{
+    if (!c) return PG_EINVAL;
+    if (adr < 0 || nj < 0) return fail(c, PG_EINVAL, "adr and nj must be >= 0");
+    if (nj > 0 && !rec) return fail(c, PG_EINVAL, "rec is NULL");
+    if (nj == 0) return PG_OK;
+    int rc;
+    if ((rc = grow_j(c, adr + nj))) return rc;
+    PG_CUDA(c, cudaMemcpyAsync((double4 *)c->jrec.p + adr, rec, (size_t)nj * sizeof(double4),
+                               cudaMemcpyDeviceToDevice, c->stream));
+    c->nj_hw = std::max(c->nj_hw, adr + nj);
+    c->jhl_n = -1;
+    return PG_OK;
+}
+
 int pg_set_j_dev(pg_ctx *c, long long adr, long long nj, const double *x, const double *m)
 {
     if (!c) return PG_EINVAL;
@@ -863,10 +887,13 @@ int pg_set_j_dev(pg_ctx *c, long long adr, long long nj, const double *x, const 
     return PG_OK;
 }
 
+// the i records and their double-float pairs (written together by set_i)
 static int grow_i(pg_ctx *c, long long ni)
 {
-    if ((size_t)ni * sizeof(double4) > c->xi.cap) drop_graph(c);
-    return ensure(c, c->xi, (size_t)std::max<long long>(ni, 1) * sizeof(double4));
+    if ((size_t)ni * sizeof(double4) > c->xi.cap || (size_t)ni * 32 > c->g_ihl.cap) drop_graph(c);
+    int rc = ensure(c, c->xi, (size_t)std::max<long long>(ni, 1) * sizeof(double4));
+    if (!rc) rc = ensure(c, c->g_ihl, (size_t)std::max<long long>(ni, 1) * 32);
+    return rc;
 }
 
 int pg_set_i(pg_ctx *c, long long ni, const double *x)
@@ -889,7 +916,9 @@ int pg_set_i(pg_ctx *c, long long ni, const double *x)
     std::memcpy(c->pin_i.p, x, bx);
     PG_CUDA(c, cudaMemcpyAsync(c->stage.p, c->pin_i.p, bx, cudaMemcpyHostToDevice, c->stream));
     PG_CUDA(c, cudaEventRecord(c->pin_i.done, c->stream));
-    PG_CUDA(c, launch_pack_i((const double *)c->stage.p, (double4 *)c->xi.p, ni, c->stream));
+    PG_CUDA(c, launch_pack_i((const double *)c->stage.p, (double4 *)c->xi.p, ni, c->stream,
+                             (float4 *)c->g_ihl.p));
+    c->ihl_n = ni;
     return PG_OK;
 }
 
@@ -904,15 +933,27 @@ int pg_set_i_dev(pg_ctx *c, long long ni, const double *x)
     c->ni = ni;
     c->i_dirty = true;
     c->epsi_applied = false;   // new i records: eps^2 not yet in them
-    if (ni > 0) PG_CUDA(c, launch_pack_i(x, (double4 *)c->xi.p, ni, c->stream));
+    if (ni > 0) PG_CUDA(c, launch_pack_i(x, (double4 *)c->xi.p, ni, c->stream, (float4 *)c->g_ihl.p));
+    c->ihl_n = ni;
     return PG_OK;
 }
 
 int pg_set_self(pg_ctx *c, int on)
 {
     if (!c) return PG_EINVAL;
-    if ((on != 0) != (c->self != 0)) drop_graph(c);
+    if ((on != 0) != (c->self != 0) || c->self_off != 0) drop_graph(c);
     c->self = on != 0;
+    c->self_off = 0;
+    return PG_OK;
+}
+
+int pg_set_self_offset(pg_ctx *c, long long lo)
+{
+    if (!c) return PG_EINVAL;
+    if (lo < 0) return fail(c, PG_EINVAL, "the self offset must be >= 0");
+    if (!c->self || lo != c->self_off) drop_graph(c);
+    c->self = 1;
+    c->self_off = lo;
     return PG_OK;
 }
 
@@ -948,6 +989,16 @@ int pg_set_shape(pg_ctx *c, int np, int ctas_per_sm, int packed)
     return PG_OK;
 }
 
+int pg_set_differencing(pg_ctx *c, int mode)
+{
+    if (!c) return PG_EINVAL;
+    if (mode != PG_DIFF_AUTO && mode != PG_DIFF_SINGLE && mode != PG_DIFF_DOUBLE)
+        return fail(c, PG_EINVAL, "differencing mode must be PG_DIFF_AUTO, PG_DIFF_SINGLE or PG_DIFF_DOUBLE");
+    if (mode != c->diff_mode) drop_graph(c);
+    c->diff_mode = mode;
+    return PG_OK;
+}
+
 int pg_set_split(pg_ctx *c, int items_per_warp)
 {
     if (!c) return PG_EINVAL;
@@ -968,9 +1019,10 @@ int pg_info(pg_ctx *c, long long *out, int n)
         c->last_pairs = (long long)v;
         c->pairs_on_device = false;
     }
-    long long v[7] = {c->last_pairs, c->last_launches, 2LL * c->last_np, c->last_grid,
-                      c->last_slots, (long long)c->packed, c->last_split};
-    int k = std::min(n, 7);
+    long long v[8] = {c->last_pairs, c->last_launches, 2LL * c->last_np, c->last_grid,
+                      c->last_slots, c->last_df ? 1LL : (long long)c->packed, c->last_split,
+                      (long long)c->last_df};
+    int k = std::min(n, 8);
     for (int i = 0; i < k; ++i) out[i] = v[i];
     return k;
 }
@@ -1024,6 +1076,7 @@ struct Plan {
     long long ni, nj;
     int np, Bi, ntiles, njsub, grid, slots;
     long long W;
+    bool df;               // double-float differencing (tiles not compact)
 };
 
 // i-particles per thread / 2 when not fixed by pg_set_shape: more per thread
@@ -1041,6 +1094,34 @@ bool use_ext(const pg_ctx *c)
 
 // the table's size as staged in shared memory, in float2 units
 int tab_units(const pg_ctx *c) { return c->have_pot ? 2 * c->ntab : c->ntab; }
+
+// the tiled path puts its i-particles in Morton order (compact tiles) from
+// 16384 on, where the sort pays for itself
+bool tiles_sorted(const pg_ctx *c, long long ni)
+{
+    return c->sort_mode == 1 || (c->sort_mode < 0 && ni >= 16384);
+}
+
+// Double-float differencing on the tiled path. One FP32 offset per particle
+// from the tile's FP64 centre carries an error of about 2^-24 of the tile's
+// extent, which for a close pair in a wide tile is not small against |d|.
+// Tiles are compact only when the i-particles are Morton-ordered and dense in
+// the j-set (at most eight j per i: a tile of B i spans about (8 B)^(1/3) j
+// spacings, twice the extent of an i-set that is the j-set); every
+// other tiled run differences in double-float (3 more lane operations per
+// component and pair). pg_set_differencing overrides the choice.
+bool tiled_df(const pg_ctx *c, long long ni, long long nj)
+{
+    if (c->diff_mode == PG_DIFF_SINGLE) return false;
+    if (c->diff_mode == PG_DIFF_DOUBLE) return true;
+    // the tabulated shape falls steeply toward r_cut, which multiplies a
+    // difference's relative error into the interpolant: double-float there
+    return c->mode == PG_TABLE || !tiles_sorted(c, ni) || nj > 8 * ni;
+}
+
+// the narrow path's i chunks are the caller's i-particles in the caller's
+// order, as spread as they come: double-float unless single is asked for
+bool narrow_df(const pg_ctx *c) { return c->diff_mode != PG_DIFF_SINGLE; }
 
 // the combine's fields for the self term and the potential
 void combine_ext(const pg_ctx *c, CombineArgs &cb)
@@ -1062,8 +1143,9 @@ int plan_allpairs(pg_ctx *c, Plan &p)
     p.ntiles = (int)((p.ni + p.Bi - 1) / p.Bi);
     p.njsub = (int)((p.nj + kTJ - 1) / kTJ);
     p.W = (long long)p.ntiles * p.njsub;
+    p.df = tiled_df(c, p.ni, p.nj);
     int occ = allpairs_max_blocks_per_sm(p.np, c->mode == PG_TABLE, tab_units(c), c->packed != 0,
-                                         use_ext(c));
+                                         use_ext(c), p.df);
     int per = c->ctas_per_sm > 0 ? std::min(c->ctas_per_sm, occ) : occ;
     long long g = (long long)c->sms * per;
     p.grid = (int)std::max<long long>(0, std::min<long long>(g, p.W));
@@ -1084,7 +1166,7 @@ int enqueue_tiles(pg_ctx *c, const Plan &p)
     if ((rc = ensure(c, c->xt, (size_t)std::max<long long>(n, 1) * sizeof(double4))) ||
         (rc = ensure(c, c->ctr, (size_t)std::max(p.ntiles, 1) * sizeof(double4))))
         return rc;
-    bool do_sort = c->sort_mode == 1 || (c->sort_mode < 0 && n >= 16384);
+    bool do_sort = tiles_sorted(c, n);
     c->perm = nullptr;
     if (do_sort && n > 1) {
         size_t hn = sort_hist_entries(n);
@@ -1111,10 +1193,81 @@ int enqueue_tiles(pg_ctx *c, const Plan &p)
     return PG_OK;
 }
 
+// The small path: a Newton run on an i-set below the Morton threshold (tiles
+// in the caller's order, double-float differences) whose j records fit
+// chunks of at most kSmallMaxChunk, with the launch shape left to the
+// library. One launch does the pair loop and the combine (pg_small.cu).
+// Sets its chunk count and size (about four blocks per SM).
+bool use_small(const pg_ctx *c, const Plan &p, int &nchunk, int &jchunk)
+{
+    if (c->mode != PG_NEWTON || c->np != 0 || p.ni <= 0 || p.nj <= 0 || tiles_sorted(c, p.ni) || !p.df)
+        return false;
+    const long long ntiles = (p.ni + small_bi() - 1) / small_bi();
+    long long nc = std::max<long long>(1, ((long long)c->sms * 4 + ntiles / 2) / ntiles);
+    long long jc = (p.nj + nc - 1) / nc;
+    if (jc > kSmallMaxChunk) jc = kSmallMaxChunk;
+    nc = (p.nj + jc - 1) / jc;
+    if (ntiles * nc > (long long)c->sms * 64) return false;   // more blocks than one pass wants
+    nchunk = (int)nc;
+    jchunk = (int)jc;
+    return true;
+}
+
+int enqueue_small(pg_ctx *c, const Plan &p, int nchunk, int jchunk, double *acc, double *pot)
+{
+    int rc;
+    const long long ntiles = (p.ni + small_bi() - 1) / small_bi();
+    if ((rc = ensure(c, c->part, (size_t)ntiles * nchunk * small_bi() * 32)) ||
+        (rc = ensure(c, c->tickets, (size_t)ntiles * sizeof(unsigned))) ||
+        (rc = ensure(c, c->g_jhl, (size_t)p.nj * 32)) || (rc = ensure(c, c->g_ihl, (size_t)p.ni * 32)))
+        return rc;
+    if (c->tickets_zeroed < c->tickets.cap) {
+        PG_CUDA(c, cudaMemsetAsync(c->tickets.p, 0, c->tickets.cap, c->stream));
+        c->tickets_zeroed = c->tickets.cap;
+    }
+    // double-float records: j repacked only after new j records; i written by
+    // set_i (repacked here only if another path reused the buffer since)
+    if ((rc = pack_j_hilo(c, p.nj))) return rc;
+    if (c->ihl_n != p.ni) {
+        PG_CUDA(c, launch_pack_hilo((const double4 *)c->xi.p, p.ni, (float4 *)c->g_ihl.p, c->stream));
+        c->ihl_n = p.ni;
+        c->last_launches += 1;
+    }
+    SmallArgs a{};
+    a.ihl = (const float4 *)c->g_ihl.p;
+    a.xi = (const double4 *)c->xi.p;
+    a.jhl = (const float4 *)c->g_jhl.p;
+    a.ni = p.ni;
+    a.nj = p.nj;
+    a.nchunk = nchunk;
+    a.jchunk = jchunk;
+    a.eps2 = (float)(c->eps * c->eps);
+    a.epsi = c->have_epsi;
+    a.self = c->self;
+    a.self_off = c->self_off;
+    a.part = (float4 *)c->part.p;
+    a.ticket = (unsigned *)c->tickets.p;
+    a.acc = acc;
+    a.pot = pot;
+    if (c->timing) PG_CUDA(c, record_timing(c, c->tk0));
+    PG_CUDA(c, launch_small(a, use_ext(c), c->stream));
+    if (c->timing) PG_CUDA(c, record_timing(c, c->tk1));
+    c->timed = c->timing;
+    c->last_launches += 1;
+    c->last_np = 1;
+    c->last_df = true;
+    c->last_pairs = p.ni * p.nj;
+    c->last_grid = (int)(ntiles * nchunk);
+    c->last_slots = nchunk;
+    return PG_OK;
+}
+
 int enqueue_allpairs(pg_ctx *c, const Plan &p, double *acc, double *pot)
 {
     int rc;
     bool table = c->mode == PG_TABLE;
+    int nchunk = 0, jchunk = 0;
+    if (use_small(c, p, nchunk, jchunk)) return enqueue_small(c, p, nchunk, jchunk, acc, pot);
     if (p.ni > 0 && (c->i_dirty || c->use_graph || c->tiled_np != p.np)) {
         if ((rc = enqueue_tiles(c, p))) return rc;
         c->i_dirty = false;
@@ -1136,11 +1289,12 @@ int enqueue_allpairs(pg_ctx *c, const Plan &p, double *acc, double *pot)
     a.part = (double4 *)c->part.p;
     a.status = (int *)c->status.p;
     const bool ext = use_ext(c);
-    size_t smem = allpairs_smem(p.np, table, tab_units(c), ext);
+    size_t smem = allpairs_smem(p.np, table, tab_units(c), ext, p.df);
     c->last_np = p.np;
+    c->last_df = p.df;
     if (p.grid > 0) {
         if (c->timing) PG_CUDA(c, record_timing(c, c->tk0));
-        PG_CUDA(c, launch_allpairs(a, p.grid, p.np, table, ext, c->packed != 0, smem, c->stream));
+        PG_CUDA(c, launch_allpairs(a, p.grid, p.np, table, ext, c->packed != 0, p.df, smem, c->stream));
         if (c->timing) PG_CUDA(c, record_timing(c, c->tk1));
         c->timed = c->timing;
         c->last_launches += 1;
@@ -1156,6 +1310,7 @@ int enqueue_allpairs(pg_ctx *c, const Plan &p, double *acc, double *pot)
     cb.grid = std::max(p.grid, 1);
     cb.W = std::max<long long>(p.W, 1);
     cb.self = c->self;
+    cb.self_off = c->self_off;
     combine_ext(c, cb);
     cb.eps2 = a.eps2;
     cb.accscale = table ? 1.0 / c->scale : 1.0;
@@ -1178,6 +1333,8 @@ int check_run_state(pg_ctx *c)
         if (c->n_epsi != c->ni)
             return fail(c, PG_ESTATE, "per-i softening needs one eps per i-particle of pg_set_i");
     }
+    if (c->self_off != 0 && (c->tree_on || c->have_groups || c->box > 0.0))
+        return fail(c, PG_ESTATE, "a self offset is for the all-pairs paths");
     if (c->tree_on) {
         if (c->mode != PG_NEWTON) return fail(c, PG_ESTATE, "the tree is for PG_NEWTON");
         if (!c->self || c->ni != nj_of(c) || c->have_groups || c->box > 0.0 || c->have_epsi)
@@ -1200,8 +1357,8 @@ int check_run_state(pg_ctx *c)
         if (c->r_cut * 3.0 > c->box) return fail(c, PG_ESTATE, "periodic path needs r_cut <= box / 3");
         return PG_OK;
     }
-    if (c->self && c->ni > nj_of(c))
-        return fail(c, PG_ESTATE, "self mode needs ni <= nj (i-particle k is j-particle k)");
+    if (c->self && c->self_off + c->ni > nj_of(c))
+        return fail(c, PG_ESTATE, "self mode needs offset + ni <= nj (i-particle k is j-particle offset + k)");
     return PG_OK;
 }
 
@@ -1265,26 +1422,29 @@ GroupArgs group_args(pg_ctx *c)
     return g;
 }
 
-int launch_group_kernel(pg_ctx *c, const GroupArgs &g, bool cell)
+// df: double-float differencing (the narrow path's items)
+int launch_group_kernel(pg_ctx *c, const GroupArgs &g, bool cell, bool df = false)
 {
     bool table = c->mode == PG_TABLE;
     int np = groups_np(c);
     c->last_np = np;
+    c->last_df = df;
     const bool ext = use_ext(c);
-    int occ = groups_max_blocks_per_sm(np, table, tab_units(c), cell, ext);
+    int occ = groups_max_blocks_per_sm(np, table, tab_units(c), cell, ext, df);
     int per = c->ctas_per_sm > 0 ? std::min(c->ctas_per_sm, occ) : occ;
     int grid = c->sms * per;
     // cell lists: the warp-mode items (the small cells) in a second launch
     // whose lighter blocks fit more warps on an SM
-    const int wper = cell && table ? groups_warp_blocks_per_sm(true, true, ext, tab_units(c)) : 0;
+    const int wper = cell && table ? groups_warp_blocks_per_sm(true, true, ext, tab_units(c), false) : 0;
     GroupArgs gg = g;
     if (wper > 0) gg.queue_w = (int *)c->g_queue.p + 1;
     PG_CUDA(c, cudaMemsetAsync(c->g_queue.p, 0, 2 * sizeof(int), c->stream));
     if (c->timing) PG_CUDA(c, record_timing(c, c->tk0));
-    PG_CUDA(c, launch_groups(gg, grid, np, table, cell, ext, groups_smem(np, table, tab_units(c)),
+    PG_CUDA(c, launch_groups(gg, grid, np, table, cell, ext, df, groups_smem(np, table, tab_units(c), df),
                              c->stream));
     if (wper > 0)
-        PG_CUDA(c, launch_groups_warp(gg, c->sms * wper, true, true, ext, tab_units(c), true, c->stream));
+        PG_CUDA(c, launch_groups_warp(gg, c->sms * wper, true, true, ext, tab_units(c), true, false,
+                                      c->stream));
     if (c->timing) PG_CUDA(c, record_timing(c, c->tk1));
     c->timed = c->timing;
     c->last_grid = grid;
@@ -1295,7 +1455,7 @@ int launch_group_kernel(pg_ctx *c, const GroupArgs &g, bool cell)
 // items that are all warp-sized (narrow all-pairs): the warp-mode kernel
 // alone, wper blocks per SM, claiming items 0, 1, ... from the second counter
 // (zeroed by the narrow path's preparation kernel)
-int launch_group_warp_kernel(pg_ctx *c, const GroupArgs &g, int wper)
+int launch_group_warp_kernel(pg_ctx *c, const GroupArgs &g, int wper, bool df)
 {
     const bool table = c->mode == PG_TABLE;
     const int per = c->ctas_per_sm > 0 ? std::min(c->ctas_per_sm, wper) : wper;
@@ -1304,8 +1464,9 @@ int launch_group_warp_kernel(pg_ctx *c, const GroupArgs &g, int wper)
     gg.queue_w = (int *)c->g_queue.p + 1;
     gg.warp_from = 0;
     c->last_np = 1;                     // one i-pair per lane
+    c->last_df = df;
     if (c->timing) PG_CUDA(c, record_timing(c, c->tk0));
-    PG_CUDA(c, launch_groups_warp(gg, grid, table, false, use_ext(c), tab_units(c), false, c->stream));
+    PG_CUDA(c, launch_groups_warp(gg, grid, table, false, use_ext(c), tab_units(c), false, df, c->stream));
     if (c->timing) PG_CUDA(c, record_timing(c, c->tk1));
     c->timed = c->timing;
     c->last_grid = grid;
@@ -1362,7 +1523,8 @@ int enqueue_narrow(pg_ctx *c, double *acc, double *pot)
     const int np = groups_np(c);
     const int Bi = groups_bi(np);
     const int nic = (int)((ni + Bi - 1) / Bi);
-    const int occ = groups_max_blocks_per_sm(np, table, tab_units(c), false, use_ext(c));
+    const bool df = narrow_df(c);
+    const int occ = groups_max_blocks_per_sm(np, table, tab_units(c), false, use_ext(c), df);
     // j chunk: about `split` items per warp of the launch, whole warp tiles
     const long long spl = c->split > 0 ? c->split : 1;
     c->last_split = spl;
@@ -1376,7 +1538,7 @@ int enqueue_narrow(pg_ctx *c, double *acc, double *pot)
     // Warp-mode items run in the warp-mode kernel alone, which fits more
     // warps on an SM; chunks are sized for it
     const long long ich = std::min<long long>(Bi, ni);
-    const int wper = ich <= 64 ? groups_warp_blocks_per_sm(table, false, use_ext(c), tab_units(c)) : 0;
+    const int wper = ich <= 64 ? groups_warp_blocks_per_sm(table, false, use_ext(c), tab_units(c), df) : 0;
     long long jc = chunk((long long)c->sms * occ * 4);
     bool warp = false;
     if (wper > 0) {
@@ -1397,6 +1559,7 @@ int enqueue_narrow(pg_ctx *c, double *acc, double *pot)
     // chunk centres, double-float i records and zeroed work counters in one launch
     PG_CUDA(c, launch_narrow_prep((const double4 *)c->xi.p, ni, Bi, nic, (double4 *)c->g_ctr.p,
                                   (float4 *)c->g_ihl.p, (int *)c->g_queue.p, c->stream));
+    c->ihl_n = ni;
     if ((rc = pack_j_hilo(c, nj))) return rc;
     c->last_launches += 1;
     GroupArgs g = group_args(c);
@@ -1420,12 +1583,13 @@ int enqueue_narrow(pg_ctx *c, double *acc, double *pot)
     g.part_stride = ni;
     g.acc = acc;
     g.pot = pot;
-    if ((rc = warp ? launch_group_warp_kernel(c, g, wper) : launch_group_kernel(c, g, false))) return rc;
+    if ((rc = warp ? launch_group_warp_kernel(c, g, wper, df) : launch_group_kernel(c, g, false, df))) return rc;
     CombineArgs cb{};
     cb.part = (const double4 *)c->n_part.p;
     cb.jrec = (const double4 *)c->jrec.p;
     cb.ni = ni;
     cb.self = c->self;
+    cb.self_off = c->self_off;
     combine_ext(c, cb);
     cb.eps2 = g.eps2;
     cb.accscale = g.accscale;
@@ -1625,6 +1789,7 @@ int enqueue_tree(pg_ctx *c, double *acc, double *pot)
     PG_CUDA(c, launch_pack_hilo(t.jrec2, nj, (float4 *)c->g_jhl.p, c->stream));
     c->jhl_n = -1;      // the buffer now holds the tree's records
     PG_CUDA(c, launch_pack_hilo(t.xi0, n, (float4 *)c->g_ihl.p, c->stream));
+    c->ihl_n = -1;      // and the i buffer the particles in key order
     PG_CUDA(c, launch_group_ctr(t.xi0, t.i_off, ng, 0, 0, (double4 *)c->g_ctr.p, c->stream));
     GroupArgs g = group_args(c);
     g.xi = t.xi0;
@@ -1682,6 +1847,7 @@ int enqueue_groups(pg_ctx *c, double *acc, double *pot)
         return rc;
     if ((rc = pack_j_hilo(c, nj))) return rc;
     PG_CUDA(c, launch_pack_hilo((const double4 *)c->xi.p, c->ni, (float4 *)c->g_ihl.p, c->stream));
+    c->ihl_n = c->ni;
     c->last_launches += 2;
     GroupArgs g = group_args(c);
     g.xi = (const double4 *)c->xi.p;
@@ -1835,6 +2001,11 @@ int run_into(pg_ctx *c, double *acc, double *pot)
              (void *)acc, (void *)pot, c->jrec.p, c->xi.p, c->sort_mode, (int)c->timing,
              c->g_nitems, c->ngroups,
              (c->path * 4 + (c->have_epsi ? 2 : 0) + (c->have_pot ? 1 : 0)) * 16 + c->split);
+    {
+        char sk[64];
+        snprintf(sk, sizeof sk, "|so%lld|df%d", c->self_off, c->diff_mode);
+        strncat(key, sk, sizeof key - strlen(key) - 1);
+    }
     if (c->pm_n > 0) {
         char pk[96];
         snprintf(pk, sizeof pk, "|pm%d|%d|%.17g", c->pm_n, c->pm_split, c->pm_scale);
@@ -1991,7 +2162,7 @@ int pg_backward_dev(pg_ctx *c, const double *w, double *dx, double *dm, float *d
     if (!c) return PG_EINVAL;
     if (!w || !dx || !dm) return fail(c, PG_EINVAL, "w, dx and dm must be device pointers");
     if (c->mode == PG_TABLE && !c->have_table) return fail(c, PG_ESTATE, "table mode without a table");
-    if (!c->self || c->have_groups || c->box > 0.0 || c->ni < 0 || c->ni != nj_of(c))
+    if (!c->self || c->self_off != 0 || c->have_groups || c->box > 0.0 || c->ni < 0 || c->ni != nj_of(c))
         return fail(c, PG_ESTATE, "the backward pass needs the all-pairs self mode with ni == nj");
     if (c->have_epsi && c->mode == PG_NEWTON)
         return fail(c, PG_ESTATE, "the backward pass has no per-i softening");
@@ -2058,6 +2229,7 @@ int pg_backward_dev(pg_ctx *c, const double *w, double *dx, double *dm, float *d
     if (table) a.tab = table_dev(c);
     a.part = (double4 *)c->part.p;
     a.dv = (table && dv) ? (double *)c->bw_dv.p : nullptr;
+    a.perm = c->perm;
     a.status = (int *)c->status.p;
     if (c->timing) PG_CUDA(c, record_timing(c, c->tk0));
     PG_CUDA(c, launch_backward(a, grid, table, backward_smem(table, c->ntab), c->stream));
@@ -2132,11 +2304,13 @@ int pg_tune(pg_ctx *c)
             for (int split = 1; split <= 4 && !rc; split *= 2) trial(np, c->packed, 0, split);
             continue;
         }
-        for (int pk = groups_path ? 1 : 0; pk <= 1 && !rc; ++pk) {
+        // the double-float tiled variant is packed only
+        const bool df = !groups_path && tiled_df(c, c->ni, nj_of(c));
+        for (int pk = groups_path || df ? 1 : 0; pk <= 1 && !rc; ++pk) {
             const int occ = groups_path
                                 ? groups_max_blocks_per_sm(np, table, tab_units(c), c->box > 0.0 && !c->have_groups,
-                                                           use_ext(c))
-                                : allpairs_max_blocks_per_sm(np, table, tab_units(c), pk != 0, use_ext(c));
+                                                           use_ext(c), false)
+                                : allpairs_max_blocks_per_sm(np, table, tab_units(c), pk != 0, use_ext(c), df);
             for (int cta = std::max(1, occ - 1); cta <= occ && !rc; ++cta) trial(np, pk, cta, c->split);
         }
     }

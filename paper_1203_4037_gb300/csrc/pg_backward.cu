@@ -13,7 +13,9 @@
 // carry one factor 1/scale, applied at the end.
 //
 // Layout as the forward all-pairs kernel: stream-K units of (i-tile,
-// j-sub-tile), i in registers (KI per thread, scalar FP32), j positions,
+// j-sub-tile), i in registers (KI per thread; scalar FP32 for the table,
+// whose per-lane knot gathers and histogram atomics do not pack; packed
+// FP32x2 for Newton, k_backward_newton below), j positions,
 // masses and weights bulk-copied to shared memory and converted to FP32
 // offsets from the FP64 tile centre, TwoSum folding per sub-tile, FP64
 // combine. The knot gradient goes through a per-CTA shared-memory histogram
@@ -237,6 +239,230 @@ __global__ void __launch_bounds__(kNT) k_backward(BackwardArgs a)
     }
 }
 
+// ---------------------------------------------------------------- Newton, packed
+// The Newton backward in packed FP32x2, two i-pairs per thread. With
+// d = x_j - x_k, q = (r^2 + eps^2)^(-1/2), K = q^3 and u = m_k w_j - m_j w_k,
+// J(d) u = K u - 3 K q^2 (d . u) d, so
+//   dL/dx_k = m_k A_k - w_k B_k - 3 C_k,   dL/dm_k = -G_k,
+//   A = sum_j K w_j, B = sum_j m_j K, C = sum_j K q^2 (d . u) d,
+//   G = sum_j K (d . w_j), with d . u = m_k (d . w_j) - m_j (d . w_k):
+// 26 FP32-pipe lane operations per interaction (difference 3, r^2 3,
+// d . w_j 3, d . w_k 3, d . u 2, q^2 and K 2, K q^2 (d . u) 2, A 3, B 1,
+// C 3, G 1) and one MUFU rsqrt, against 33 for J(d) u formed from u. The
+// own pair (j index = i's index) is left out by zeroing its q, so its large
+// K never enters the FP32 sums; a coincident pair at eps = 0 likewise.
+constexpr int kNPB = 2;                       // i-pairs per thread
+static_assert(2 * kNPB == kKI, "the packed kernel keeps the tile of the scalar one");
+
+__global__ void __launch_bounds__(kNT, 2) k_backward_newton(BackwardArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    double4 *rawx = reinterpret_cast<double4 *>(smem);                 // [2][kTJ]
+    double4 *raww = rawx + 2 * kTJ;                                     // [2][kTJ]
+    u64 *cvt = reinterpret_cast<u64 *>(raww + 2 * kTJ);                 // [kTJ][8]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(cvt + 8 * kTJ);
+    int *flag = reinterpret_cast<int *>(bar + 2);
+
+    const int tid = threadIdx.x;
+    const long long G = gridDim.x, b = blockIdx.x;
+    const long long u0 = b * a.W / G, u1 = (b + 1) * a.W / G;
+    if (u0 >= u1) return;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    unsigned pending = 0, phase = 0;
+    if (tid == 0) {
+        issue_bw(a.jx, a.jwv, a.n, (int)(u0 % a.njsub), rawx, raww, &bar[0]);
+        pending = 1u;
+        if (u0 + 1 < u1) {
+            issue_bw(a.jx, a.jwv, a.n, (int)((u0 + 1) % a.njsub), rawx + kTJ, raww + kTJ, &bar[1]);
+            pending |= 2u;
+        }
+    }
+
+    const u64 c0v = pk2(a.eps2, a.eps2);
+    u64 xi[kNPB], yi[kNPB], zi[kNPB], mk[kNPB], wkx[kNPB], wky[kNPB], wkz[kNPB];
+    int self0[kNPB], self1[kNPB];
+    // compensated sums (hi, lo) of A (3), B, C (3), G per i-pair
+    u64 sh[kNPB][8], sl[kNPB][8];
+    double cx = 0, cy = 0, cz = 0;
+    long long cur = -1;
+    bool failed = false;
+
+    auto flush = [&](long long t) {
+        long long slot = b - sk_owner(t * a.njsub, G, a.W);
+        double4 *dst = a.part + ((size_t)t * a.smax_slots + (size_t)slot) * kBiB;
+#pragma unroll
+        for (int p = 0; p < kNPB; ++p) {
+            float h[16], l[16];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                up2(sh[p][k], h[2 * k], h[2 * k + 1]);
+                up2(sl[p][k], l[2 * k], l[2 * k + 1]);
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int li = (2 * p + q) * kNT + tid;
+                const long long i = t * kBiB + li;
+                if (i >= a.n) continue;
+                double v[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) v[k] = (double)h[2 * k + q] + (double)l[2 * k + q];
+                const double m = a.xi[i].w;
+                const double4 w = a.wv[i];
+                // v[3] holds -B (the staged masses are negated)
+                dst[li] = make_double4(m * v[0] + w.x * v[3] - 3.0 * v[4],
+                                       m * v[1] + w.y * v[3] - 3.0 * v[5],
+                                       m * v[2] + w.z * v[3] - 3.0 * v[6], -v[7]);
+            }
+        }
+    };
+
+    for (long long u = u0; u < u1; ++u) {
+        const long long t = u / a.njsub;
+        const int s = (int)(u % a.njsub);
+        const int buf = (int)((u - u0) & 1);
+        if (t != cur) {
+            if (cur >= 0) flush(cur);
+            cur = t;
+            const double4 c = a.ctr[t];
+            cx = c.x; cy = c.y; cz = c.z;
+#pragma unroll
+            for (int p = 0; p < kNPB; ++p) {
+                float fx[2], fy[2], fz[2], fm[2], gx[2], gy[2], gz[2];
+                int sf[2];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const long long i = t * kBiB + (2 * p + q) * kNT + tid;
+                    if (i < a.n) {
+                        const double4 v = a.xi[i], w = a.wv[i];
+                        fx[q] = (float)(v.x - cx);
+                        fy[q] = (float)(v.y - cy);
+                        fz[q] = (float)(v.z - cz);
+                        fm[q] = (float)v.w;
+                        gx[q] = (float)w.x; gy[q] = (float)w.y; gz[q] = (float)w.z;
+                        sf[q] = a.perm ? (int)a.perm[i] : (int)i;
+                    } else {
+                        fx[q] = fy[q] = fz[q] = fm[q] = gx[q] = gy[q] = gz[q] = 0.0f;
+                        sf[q] = -1;
+                    }
+                }
+                xi[p] = pk2(fx[0], fx[1]);
+                yi[p] = pk2(fy[0], fy[1]);
+                zi[p] = pk2(fz[0], fz[1]);
+                mk[p] = pk2(fm[0], fm[1]);
+                wkx[p] = pk2(gx[0], gx[1]);
+                wky[p] = pk2(gy[0], gy[1]);
+                wkz[p] = pk2(gz[0], gz[1]);
+                self0[p] = sf[0];
+                self1[p] = sf[1];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) sh[p][k] = sl[p][k] = 0ull;
+            }
+        }
+        if (tid == 0) {
+            bool ok = mbar_wait(&bar[buf], (phase >> buf) & 1u, kWaitLimitNs);
+            if (ok) pending &= ~(1u << buf);
+            *flag = ok ? 1 : 0;
+        }
+        __syncthreads();
+        if (*flag == 0) { failed = true; break; }
+        phase ^= 1u << buf;
+        const long long j0 = (long long)s * kTJ;
+        {
+            long long nv = a.n - j0;
+            if (nv > kTJ) nv = kTJ;
+            for (int e = tid; e < kTJ; e += kNT) {
+                float x = 1.0e4f, y = 1.0e4f, z = 1.0e4f, mn = 0.0f, wx = 0.0f, wy = 0.0f, wz = 0.0f;
+                if (e < nv) {
+                    const double4 v = rawx[buf * kTJ + e], ww = raww[buf * kTJ + e];
+                    x = (float)(v.x - cx);
+                    y = (float)(v.y - cy);
+                    z = (float)(v.z - cz);
+                    mn = -(float)v.w;
+                    wx = (float)ww.x; wy = (float)ww.y; wz = (float)ww.z;
+                }
+                cvt[8 * e + 0] = pk2(x, x);
+                cvt[8 * e + 1] = pk2(y, y);
+                cvt[8 * e + 2] = pk2(z, z);
+                cvt[8 * e + 3] = pk2(mn, mn);
+                cvt[8 * e + 4] = pk2(wx, wx);
+                cvt[8 * e + 5] = pk2(wy, wy);
+                cvt[8 * e + 6] = pk2(wz, wz);
+                cvt[8 * e + 7] = 0ull;
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && u + 2 < u1) {
+            fence_proxy_async();
+            issue_bw(a.jx, a.jwv, a.n, (int)((u + 2) % a.njsub), rawx + buf * kTJ, raww + buf * kTJ,
+                     &bar[buf]);
+            pending |= 1u << buf;
+        }
+        u64 acc[kNPB][8];
+#pragma unroll
+        for (int p = 0; p < kNPB; ++p)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[p][k] = 0ull;
+        const ulonglong2 *cv = reinterpret_cast<const ulonglong2 *>(cvt);
+        const int jb = (int)j0;
+#pragma unroll 4
+        for (int e = 0; e < kTJ; ++e) {
+            const ulonglong2 xy = cv[4 * e], zm = cv[4 * e + 1], wxy = cv[4 * e + 2], wz0 = cv[4 * e + 3];
+            const int j = jb + e;
+#pragma unroll
+            for (int p = 0; p < kNPB; ++p) {
+                const u64 dx = f2sub(xy.x, xi[p]), dy = f2sub(xy.y, yi[p]), dz = f2sub(zm.x, zi[p]);
+                u64 r2 = f2fma(dx, dx, c0v);
+                r2 = f2fma(dy, dy, r2);
+                r2 = f2fma(dz, dz, r2);
+                u64 wd = f2mul(dx, wxy.x);
+                wd = f2fma(dy, wxy.y, wd);
+                wd = f2fma(dz, wz0.x, wd);
+                u64 dk = f2mul(dx, wkx[p]);
+                dk = f2fma(dy, wky[p], dk);
+                dk = f2fma(dz, wkz[p], dk);
+                const u64 du = f2fma(mk[p], wd, f2mul(zm.y, dk));   // m_k d.w_j - m_j d.w_k
+                float ra, rb;
+                up2(r2, ra, rb);
+                float qa = rsq(ra), qb = rsq(rb);
+                qa = (ra > 0.0f && j != self0[p]) ? qa : 0.0f;
+                qb = (rb > 0.0f && j != self1[p]) ? qb : 0.0f;
+                const u64 q = pk2(qa, qb);
+                const u64 q2 = f2mul(q, q);
+                const u64 K = f2mul(q, q2);
+                const u64 tt = f2mul(f2mul(K, q2), du);
+                acc[p][0] = f2fma(K, wxy.x, acc[p][0]);
+                acc[p][1] = f2fma(K, wxy.y, acc[p][1]);
+                acc[p][2] = f2fma(K, wz0.x, acc[p][2]);
+                acc[p][3] = f2fma(zm.y, K, acc[p][3]);    // -sum m_j K
+                acc[p][4] = f2fma(tt, dx, acc[p][4]);
+                acc[p][5] = f2fma(tt, dy, acc[p][5]);
+                acc[p][6] = f2fma(tt, dz, acc[p][6]);
+                acc[p][7] = f2fma(K, wd, acc[p][7]);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < kNPB; ++p)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) fold2(sh[p][k], sl[p][k], acc[p][k]);
+    }
+    if (failed) {
+        if (tid == 0) {
+            report(a.status, kStatusTimeout, 3);
+            for (int k = 0; k < 2; ++k)
+                if (pending & (1u << k)) mbar_wait(&bar[k], (phase >> k) & 1u, kWaitLimitNs / 4);
+        }
+        return;
+    }
+    if (cur >= 0) flush(cur);
+}
+
+size_t backward_newton_smem() { return 4 * kTJ * sizeof(double4) + 8 * kTJ * sizeof(u64) + 4 * sizeof(uint64_t); }
+
 size_t backward_smem(bool table, int ntab)
 {
     size_t s = 4 * kTJ * sizeof(double4) + 2 * kTJ * sizeof(float4) + 4 * sizeof(uint64_t);
@@ -247,22 +473,32 @@ size_t backward_smem(bool table, int ntab)
 template <bool TABLE>
 static cudaError_t configure_b()
 {
-    static bool done = false;
-    if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_backward<TABLE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)backward_smem(TABLE, 1 << 13));
-    done = e == cudaSuccess;
-    return e;
+    static bool done[kMaxDevices] = {};
+    return once_per_device(done, [] {
+        return cudaFuncSetAttribute(k_backward<TABLE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)backward_smem(TABLE, 1 << 13));
+    });
 }
 
+static cudaError_t configure_bn()
+{
+    static bool done[kMaxDevices] = {};
+    return once_per_device(done, [] {
+        return cudaFuncSetAttribute(k_backward_newton, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)backward_newton_smem());
+    });
+}
+
+// Newton: the packed kernel; table: the scalar one with the knot histogram
 int backward_max_blocks_per_sm(bool table, int ntab)
 {
-    size_t smem = backward_smem(table, ntab);
-    cudaError_t e = table ? configure_b<true>() : configure_b<false>();
+    cudaError_t e = table ? configure_b<true>() : configure_bn();
     if (e != cudaSuccess) return 1;
     int nb = 0;
-    e = table ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_backward<true>, kNT, smem)
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_backward<false>, kNT, smem);
+    e = table ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_backward<true>, kNT,
+                                                             backward_smem(true, ntab))
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_backward_newton, kNT,
+                                                             backward_newton_smem());
     return (e == cudaSuccess && nb > 0) ? nb : 1;
 }
 
@@ -270,10 +506,10 @@ cudaError_t launch_backward(const BackwardArgs &a, int grid, bool table, size_t 
                             cudaStream_t st)
 {
     if (grid <= 0) return cudaSuccess;
-    cudaError_t e = table ? configure_b<true>() : configure_b<false>();
+    cudaError_t e = table ? configure_b<true>() : configure_bn();
     if (e != cudaSuccess) return e;
     if (table) k_backward<true><<<grid, kNT, smem, st>>>(a);
-    else k_backward<false><<<grid, kNT, smem, st>>>(a);
+    else k_backward_newton<<<grid, kNT, backward_newton_smem(), st>>>(a);
     return cudaGetLastError();
 }
 

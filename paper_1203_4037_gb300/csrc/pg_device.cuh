@@ -207,14 +207,15 @@ __device__ __forceinline__ double4 ldg_d4(const double4 *p)
     return r;
 }
 
-// The potential term i's own pair added in the loop (d = 0 exactly), as the
+// The potential term i's own pair added in the loop (d = 0 exactly; i-particle
+// k is j record k + self_off), as the
 // loop computed it, so that subtracting it leaves no cancellation error:
 // Newton -m_k rsqrt(eps^2) (eps of the global setting or of i itself; at
 // eps = 0 the pair added nothing); table with a potential m_k psi~(s = 2),
 // knot 0's value A_p + 2 P1.
 __device__ __forceinline__ double self_potential(const CombineArgs &c, long long k)
 {
-    const float mk = (float)c.jrec[k].w;
+    const float mk = (float)c.jrec[k + c.self_off].w;
     if (c.newton) {
         const float e2 = c.epsi ? (float)c.xi[k].w : c.eps2;
         return e2 > 0.0f ? -(double)__fmul_rn(mk, rsq(e2)) : 0.0;

@@ -38,6 +38,14 @@ constexpr int kPerThread = kTJG / kNT;
 //    j offset in the i-cell's frame is o_j + (dx, dy, dz) h~ -- FP32 only,
 //    with the periodic wrap already in the direction.
 //
+// DF (narrow all-pairs, whose i chunks can be spread over the whole system):
+// no FP32 offsets at all; a pair's difference is formed from the
+// double-float records as (hi_j - hi_i) + (lo_j - lo_i). The first
+// subtraction is rounded relative to |d| itself (exact when the two are
+// within a factor of two), the second is tiny, so d keeps FP32 precision
+// relative to |d| however far the chunk's i-particles are from each other.
+// Table mode scales d afterwards (one multiply, relative error 2^-24).
+//
 // Thread layout of an item: nsets sets of 2*NP i-particles; each set owns L
 // consecutive lanes of one warp (any L from 1 to 32, sets never straddle a
 // warp), lane l of a set takes the j with index = l (mod L), and the set's
@@ -205,11 +213,12 @@ __device__ __forceinline__ void pair_term(float ra, float rb, u64 dx, u64 dy, u6
     }
 }
 
-template <int NP, bool TABLE, bool CELL, bool EXT, bool HL = false>
+template <int NP, bool TABLE, bool CELL, bool EXT, bool HL = false, bool DF = false>
 __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &it, const ItemShape sh,
                                            u64 *cvt, u64 *run, int *cr, const float2 *tab,
                                            const float4 *dirt, int tid)
 {
+    static_assert(!(DF && CELL), "double-float differencing is for particle records");
     long long jb = 0, je = 0;
     if (CELL) {
         if (tid < 32) cell_ranges(a, it.group, tid, cr);
@@ -246,11 +255,14 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
     const bool active = wl < sh.spw * L && set < sh.nsets;
 
     u64 xi[NP], yi[NP], zi[NP];
+    u64 lxi[DF ? NP : 1], lyi[DF ? NP : 1], lzi[DF ? NP : 1];   // DF: the records' lo parts
     u64 e2i[NP];                       // Newton EXT: each i-pair's own eps^2
     u64 ax[NP], ay[NP], az[NP], ph[NP];
+    const u64 scf2 = pk2(scf, scf);
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         float fx[2] = {0, 0}, fy[2] = {0, 0}, fz[2] = {0, 0}, fe[2] = {0, 0};
+        float gx[2] = {0, 0}, gy[2] = {0, 0}, gz[2] = {0, 0};
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             int k = set * 2 * NP + 2 * p + q;
@@ -258,6 +270,11 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
                 if (CELL) {
                     float4 o = a.xo[it.i0 + k];
                     fx[q] = o.x; fy[q] = o.y; fz[q] = o.z;
+                } else if (DF) {
+                    const float4 h = a.ihl[2 * (it.i0 + k)], l = a.ihl[2 * (it.i0 + k) + 1];
+                    fx[q] = h.x; fy[q] = h.y; fz[q] = h.z;
+                    gx[q] = l.x; gy[q] = l.y; gz[q] = l.z;
+                    fe[q] = l.w;
                 } else {
                     const float4 h = a.ihl[2 * (it.i0 + k)], l = a.ihl[2 * (it.i0 + k) + 1];
                     fx[q] = ((h.x - chx) + (l.x - clx)) * scf;
@@ -270,6 +287,11 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
         xi[p] = pk2(fx[0], fx[1]);
         yi[p] = pk2(fy[0], fy[1]);
         zi[p] = pk2(fz[0], fz[1]);
+        if (DF) {
+            lxi[p] = pk2(gx[0], gx[1]);
+            lyi[p] = pk2(gy[0], gy[1]);
+            lzi[p] = pk2(gz[0], gz[1]);
+        }
         e2i[p] = pk2(fe[0], fe[1]);
 #pragma unroll
         for (int k = 0; k < 4; ++k) RH(p, k) = RL(p, k) = 0ull;
@@ -309,9 +331,13 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
 #pragma unroll
         for (int r = 0; r < kPerThread; ++r) {
             const int e = r * kNT + tid;
-            float x, y, z, m;
+            float x, y, z, m, lx = 0.0f, ly = 0.0f, lz = 0.0f;
             const bool real = rc32[r].w >= 0.0f;
-            if (real && CELL) {
+            if (real && DF) {
+                x = rc32[r].x; y = rc32[r].y; z = rc32[r].z;
+                lx = rlo[r].x; ly = rlo[r].y; lz = rlo[r].z;
+                m = rc32[r].w;
+            } else if (real && CELL) {
                 const float4 dv = dirt[code[r]];     // direction x cell side, scaled
                 x = rc32[r].x + dv.x;
                 y = rc32[r].y + dv.y;
@@ -332,6 +358,12 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
             cvt[2 * e + 1] = pk2(y, y);
             cvt[2 * kTJG + 2 * e + 0] = pk2(z, z);
             cvt[2 * kTJG + 2 * e + 1] = pk2(m, m);
+            if (DF) {
+                cvt[4 * kTJG + 2 * e + 0] = pk2(lx, lx);
+                cvt[4 * kTJG + 2 * e + 1] = pk2(ly, ly);
+                cvt[6 * kTJG + 2 * e + 0] = pk2(lz, lz);
+                cvt[6 * kTJG + 2 * e + 1] = 0ull;
+            }
         }
         __syncthreads();
         if (t0 + kTJG < je) fetch(t0 + kTJG);   // loads in flight during the compute
@@ -345,11 +377,26 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
             for (int e = lane; e < nv_lane; e += L) {
                 const ulonglong2 xy = reinterpret_cast<const ulonglong2 *>(cvt)[e];
                 const ulonglong2 zm = reinterpret_cast<const ulonglong2 *>(cvt)[kTJG + e];
+                ulonglong2 lxy = make_ulonglong2(0ull, 0ull), lz0 = lxy;
+                if (DF) {
+                    lxy = reinterpret_cast<const ulonglong2 *>(cvt)[2 * kTJG + e];
+                    lz0 = reinterpret_cast<const ulonglong2 *>(cvt)[3 * kTJG + e];
+                }
 #pragma unroll
                 for (int p = 0; p < NP; ++p) {
-                    const u64 dx = f2sub(xy.x, xi[p]);
-                    const u64 dy = f2sub(xy.y, yi[p]);
-                    const u64 dz = f2sub(zm.x, zi[p]);
+                    u64 dx = f2sub(xy.x, xi[p]);
+                    u64 dy = f2sub(xy.y, yi[p]);
+                    u64 dz = f2sub(zm.x, zi[p]);
+                    if (DF) {
+                        dx = f2add(dx, f2sub(lxy.x, lxi[p]));
+                        dy = f2add(dy, f2sub(lxy.y, lyi[p]));
+                        dz = f2add(dz, f2sub(lz0.x, lzi[p]));
+                        if (TABLE) {
+                            dx = f2mul(dx, scf2);
+                            dy = f2mul(dy, scf2);
+                            dz = f2mul(dz, scf2);
+                        }
+                    }
                     u64 r2 = f2fma(dx, dx, !TABLE && EXT ? e2i[p] : c0v);
                     r2 = f2fma(dy, dy, r2);
                     r2 = f2fma(dz, dz, r2);
@@ -456,12 +503,13 @@ constexpr long long kWarpItemPairs = 32768;   // and this many pairs go to warp 
 
 // Claims come from counter q: item qbase + (q's previous value); nwarps is
 // the number of warps of the launch claiming from it.
-template <bool TABLE, bool CELL, bool EXT, bool HL = false>
+template <bool TABLE, bool CELL, bool EXT, bool HL = false, bool DF = false>
 __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cur, int held,
                                           u64 *wcvt, int *wcr, const float2 *tab,
                                           const float4 *dirt, int lane32, int *q, int qbase,
                                           int nwarps)
 {
+    static_assert(!(DF && CELL), "double-float differencing is for particle records");
     constexpr unsigned kFull = 0xffffffffu;
     int pend = -1;                      // lane 0: a claimed item not yet started
     if (lane32 == 0) pend = held;
@@ -485,6 +533,9 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
     const unsigned smax_bits = __float_as_uint(a.tab.s_max);
     ulonglong2 *sxy = reinterpret_cast<ulonglong2 *>(wcvt);            // [kWarpTJ]
     ulonglong2 *szm = sxy + kWarpTJ;                                   // [kWarpTJ]
+    ulonglong2 *slxy = szm + kWarpTJ;                                  // DF: [kWarpTJ] lo x, y
+    ulonglong2 *slz = slxy + kWarpTJ;                                  // DF: [kWarpTJ] lo z
+    const u64 scf2 = pk2(scf, scf);
 
     // j range of an item (cell mode: its run table, written to cr)
     auto setup = [&](const GroupItem &it, int *cr, long long &jb, long long &je) {
@@ -599,10 +650,15 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
                 fetch(jb, je, crc);
             }
             float fx[2], fy[2], fz[2], fe[2] = {0.0f, 0.0f};
+            float gx[2] = {0.0f, 0.0f}, gy[2] = {0.0f, 0.0f}, gz[2] = {0.0f, 0.0f};
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 if (CELL) {
                     fx[q] = ih[q].x; fy[q] = ih[q].y; fz[q] = ih[q].z;
+                } else if (DF) {
+                    fx[q] = ih[q].x; fy[q] = ih[q].y; fz[q] = ih[q].z;
+                    gx[q] = il[q].x; gy[q] = il[q].y; gz[q] = il[q].z;
+                    fe[q] = il[q].w;
                 } else {
                     fx[q] = ((ih[q].x - chx) + (il[q].x - clx)) * scf;
                     fy[q] = ((ih[q].y - chy) + (il[q].y - cly)) * scf;
@@ -611,6 +667,7 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
                 }
             }
             const u64 xi = pk2(fx[0], fx[1]), yi = pk2(fy[0], fy[1]), zi = pk2(fz[0], fz[1]);
+            const u64 lxi = pk2(gx[0], gx[1]), lyi = pk2(gy[0], gy[1]), lzi = pk2(gz[0], gz[1]);
             const u64 r0 = !TABLE && EXT ? pk2(fe[0], fe[1]) : c0v;   // eps^2 (or 2 in table units)
             const int L = sp.L, lane = sp.lane;
             const bool active = sp.active;
@@ -620,8 +677,12 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
 #pragma unroll
                 for (int r = 0; r < kR; ++r) {
                     const int e = r * 32 + lane32;
-                    float x, y, z, m;
-                    if (rc32[r].w >= 0.0f && CELL) {
+                    float x, y, z, m, lx = 0.0f, ly = 0.0f, lz = 0.0f;
+                    if (rc32[r].w >= 0.0f && DF) {
+                        x = rc32[r].x; y = rc32[r].y; z = rc32[r].z;
+                        lx = rlo[r].x; ly = rlo[r].y; lz = rlo[r].z;
+                        m = rc32[r].w;
+                    } else if (rc32[r].w >= 0.0f && CELL) {
                         const float4 dv = dirt[code[r]];
                         x = rc32[r].x + dv.x; y = rc32[r].y + dv.y; z = rc32[r].z + dv.z;
                         m = rc32[r].w;
@@ -636,6 +697,10 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
                     }
                     sxy[e] = make_ulonglong2(pk2(x, x), pk2(y, y));
                     szm[e] = make_ulonglong2(pk2(z, z), pk2(m, m));
+                    if (DF) {
+                        slxy[e] = make_ulonglong2(pk2(lx, lx), pk2(ly, ly));
+                        slz[e] = make_ulonglong2(pk2(lz, lz), 0ull);
+                    }
                 }
                 __syncwarp();
                 // loads in flight during the compute: this item's next tile,
@@ -660,7 +725,18 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
 #pragma unroll 4
                     for (int e = lane; e < nvl; e += L) {
                         const ulonglong2 xy = sxy[e], zm = szm[e];
-                        const u64 dx = f2sub(xy.x, xi), dy = f2sub(xy.y, yi), dz = f2sub(zm.x, zi);
+                        u64 dx = f2sub(xy.x, xi), dy = f2sub(xy.y, yi), dz = f2sub(zm.x, zi);
+                        if (DF) {
+                            const ulonglong2 lxy = slxy[e], lz0 = slz[e];
+                            dx = f2add(dx, f2sub(lxy.x, lxi));
+                            dy = f2add(dy, f2sub(lxy.y, lyi));
+                            dz = f2add(dz, f2sub(lz0.x, lzi));
+                            if (TABLE) {
+                                dx = f2mul(dx, scf2);
+                                dy = f2mul(dy, scf2);
+                                dz = f2mul(dz, scf2);
+                            }
+                        }
                         u64 r2 = f2fma(dx, dx, r0);
                         r2 = f2fma(dy, dy, r2);
                         r2 = f2fma(dz, dz, r2);
@@ -757,12 +833,17 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
 
 // NPMAX: the largest i-pair count per thread; items whose shape uses the
 // threads better with half of it run with NPMAX / 2
-template <int NPMAX, bool TABLE, bool CELL, bool EXT, bool HL = false>
+// staging words per j entry: {x, y} and {z, m} in both lanes, with DF also
+// the lo parts {lx, ly} and {lz, 0}
+template <bool DF> struct GroupWords { static constexpr int value = DF ? 8 : 4; };
+
+template <int NPMAX, bool TABLE, bool CELL, bool EXT, bool HL = false, bool DF = false>
 __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
 {
+    constexpr int kW = GroupWords<DF>::value;
     extern __shared__ __align__(128) unsigned char smem[];
-    u64 *cvt = reinterpret_cast<u64 *>(smem);                            // [kTJG][4]
-    u64 *run = cvt + 4 * kTJG;                                           // [8 NPMAX][kNT]
+    u64 *cvt = reinterpret_cast<u64 *>(smem);                            // [kW][kTJG]
+    u64 *run = cvt + kW * kTJG;                                          // [8 NPMAX][kNT]
     float4 *dirt = reinterpret_cast<float4 *>(run + 8 * NPMAX * kNT);    // [27] cell mode
     int *sh = reinterpret_cast<int *>(dirt + 28);                        // item slot
     int *cr = sh + 4;                                                    // [4][2][kCellTab] cell mode
@@ -810,23 +891,23 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
             const ItemShape big = item_shape(it.ni, NPMAX);
             const ItemShape small = item_shape(it.ni, NPMAX / 2);
             if (small.nsets <= 4 * small.spw && small.nsets * small.L > big.nsets * big.L) {
-                group_item<(NPMAX > 1 ? NPMAX / 2 : 1), TABLE, CELL, EXT, HL>(a, it, small, cvt, run,
-                                                                             cr, tab, dirt, tid);
+                group_item<(NPMAX > 1 ? NPMAX / 2 : 1), TABLE, CELL, EXT, HL, DF>(a, it, small, cvt, run,
+                                                                                 cr, tab, dirt, tid);
                 continue;
             }
         }
-        group_item<NPMAX, TABLE, CELL, EXT, HL>(a, it, item_shape(it.ni, NPMAX), cvt, run, cr, tab,
-                                              dirt, tid);
+        group_item<NPMAX, TABLE, CELL, EXT, HL, DF>(a, it, item_shape(it.ni, NPMAX), cvt, run, cr, tab,
+                                                  dirt, tid);
     }
 
     // warp mode: warp 0 takes the item that ended CTA mode and thread 0's
     // prefetched claim; every warp then claims its own items
     __syncthreads();   // no warp still reads the CTA-wide staging buffer
     const int w = tid >> 5, lane32 = tid & 31;
-    warp_loop<TABLE, CELL, EXT, HL>(a, nitems, w == 0 ? first_small : -1,
-                                  (w == 0 && lane32 == 0) ? next : -1,
-                                  cvt + w * (2 * 2 * kWarpTJ), cr + w * 2 * kCellTab, tab, dirt,
-                                  lane32, a.queue, 0, (int)gridDim.x * (kNT / 32));
+    warp_loop<TABLE, CELL, EXT, HL, DF>(a, nitems, w == 0 ? first_small : -1,
+                                      (w == 0 && lane32 == 0) ? next : -1,
+                                      cvt + w * (kW * kWarpTJ), cr + w * 2 * kCellTab, tab, dirt,
+                                      lane32, a.queue, 0, (int)gridDim.x * (kNT / 32));
 }
 
 // The warp-mode items alone, in a launch of their own: the cell list's small
@@ -841,12 +922,13 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
 constexpr int kWNT = 256;          // threads per block
 constexpr int kWMinBlocks = 2;     // resident blocks per SM wanted (register cap)
 
-template <bool TABLE, bool CELL, bool EXT, bool HL = false>
+template <bool TABLE, bool CELL, bool EXT, bool HL = false, bool DF = false>
 __global__ void __launch_bounds__(kWNT, kWMinBlocks) k_groups_warp(GroupArgs a)
 {
+    constexpr int kW = GroupWords<DF>::value;
     extern __shared__ __align__(128) unsigned char smem[];
-    u64 *wcvt = reinterpret_cast<u64 *>(smem);                             // [warps][4 kWarpTJ]
-    float4 *dirt = reinterpret_cast<float4 *>(wcvt + (kWNT / 32) * 4 * kWarpTJ);   // [28]
+    u64 *wcvt = reinterpret_cast<u64 *>(smem);                             // [warps][kW kWarpTJ]
+    float4 *dirt = reinterpret_cast<float4 *>(wcvt + (kWNT / 32) * kW * kWarpTJ);  // [28]
     int *cr = reinterpret_cast<int *>(dirt + 28);                          // [warps][2][kCellTab]
     float2 *tab = reinterpret_cast<float2 *>(cr + (kWNT / 32) * 2 * kCellTab);
 
@@ -862,9 +944,9 @@ __global__ void __launch_bounds__(kWNT, kWMinBlocks) k_groups_warp(GroupArgs a)
     const int nitems = a.nitems >= 0 ? a.nitems : (int)*a.nitems_dev;
     const int warp_from = a.warp_from >= 0 ? a.warp_from : (int)*a.warp_from_dev;
     const int w = tid >> 5, lane32 = tid & 31;
-    warp_loop<TABLE, CELL, EXT, HL>(a, nitems, -1, -1, wcvt + w * (2 * 2 * kWarpTJ),
-                                  cr + w * 2 * kCellTab, tab, dirt, lane32, a.queue_w, warp_from,
-                                  (int)gridDim.x * (kWNT / 32));
+    warp_loop<TABLE, CELL, EXT, HL, DF>(a, nitems, -1, -1, wcvt + w * (kW * kWarpTJ),
+                                      cr + w * 2 * kCellTab, tab, dirt, lane32, a.queue_w, warp_from,
+                                      (int)gridDim.x * (kWNT / 32));
     // when launched while the CTA-mode kernel may still run (programmatic
     // dependent launch): its items are disjoint from this kernel's, and this
     // kernel ends only after that one has, so later work sees both (a no-op
@@ -873,9 +955,9 @@ __global__ void __launch_bounds__(kWNT, kWMinBlocks) k_groups_warp(GroupArgs a)
 }
 
 // ------------------------------------------------------------------ host
-size_t groups_smem(int np, bool table, int ntab)
+size_t groups_smem(int np, bool table, int ntab, bool df)
 {
-    size_t s = kTJG * 4 * sizeof(u64) + 8 * np * kNT * sizeof(u64) + 28 * 16 + 16 +
+    size_t s = (size_t)kTJG * (df ? 8 : 4) * sizeof(u64) + 8 * np * kNT * sizeof(u64) + 28 * 16 + 16 +
                8 * kCellTab * sizeof(int);
     if (table) s += (size_t)ntab * sizeof(float2);
     return s;
@@ -883,62 +965,72 @@ size_t groups_smem(int np, bool table, int ntab)
 
 int groups_bi(int np) { return kNT * 2 * np; }
 
-template <int NP, bool TABLE, bool CELL, bool EXT, bool HL = false>
+template <int NP, bool TABLE, bool CELL, bool EXT, bool HL = false, bool DF = false>
 static cudaError_t configure_g()
 {
-    static bool done = false;
-    if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_groups<NP, TABLE, CELL, EXT, HL>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)groups_smem(NP, TABLE, 2 << 13));
-    done = e == cudaSuccess;
-    return e;
+    static bool done[kMaxDevices] = {};
+    return once_per_device(done, [] {
+        return cudaFuncSetAttribute(k_groups<NP, TABLE, CELL, EXT, HL, DF>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)groups_smem(NP, TABLE, 2 << 13, DF));
+    });
 }
 
-template <int NP, bool TABLE, bool CELL, bool EXT>
+template <int NP, bool TABLE, bool CELL, bool EXT, bool DF = false>
 static int occ_g(size_t smem)
 {
-    if (configure_g<NP, TABLE, CELL, EXT>() != cudaSuccess) return 1;
+    if (configure_g<NP, TABLE, CELL, EXT, false, DF>() != cudaSuccess) return 1;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_groups<NP, TABLE, CELL, EXT>, kNT,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_groups<NP, TABLE, CELL, EXT, false, DF>, kNT,
                                                       smem) != cudaSuccess)
         return 1;
     return nb > 0 ? nb : 1;
 }
 
 template <int NP>
-static int occ_np(bool table, bool cell, bool ext, size_t smem)
+static int occ_np(bool table, bool cell, bool ext, bool df, size_t smem)
 {
+    if (df && !cell) {
+        if (!table) return ext ? occ_g<NP, false, false, true, true>(smem) : occ_g<NP, false, false, false, true>(smem);
+        return ext ? occ_g<NP, true, false, true, true>(smem) : occ_g<NP, true, false, false, true>(smem);
+    }
     if (!table) return ext ? occ_g<NP, false, false, true>(smem) : occ_g<NP, false, false, false>(smem);
     if (cell) return ext ? occ_g<NP, true, true, true>(smem) : occ_g<NP, true, true, false>(smem);
     return ext ? occ_g<NP, true, false, true>(smem) : occ_g<NP, true, false, false>(smem);
 }
 
-int groups_max_blocks_per_sm(int np, bool table, int ntab, bool cell, bool ext)
+int groups_max_blocks_per_sm(int np, bool table, int ntab, bool cell, bool ext, bool df)
 {
-    size_t smem = groups_smem(np, table, ntab);
-    return np == 1 ? occ_np<1>(table, cell, ext, smem)
-         : np == 4 ? occ_np<4>(table, cell, ext, smem)
-                   : occ_np<2>(table, cell, ext, smem);
+    size_t smem = groups_smem(np, table, ntab, df && !cell);
+    return np == 1 ? occ_np<1>(table, cell, ext, df, smem)
+         : np == 4 ? occ_np<4>(table, cell, ext, df, smem)
+                   : occ_np<2>(table, cell, ext, df, smem);
 }
 
-template <int NP, bool TABLE, bool CELL, bool EXT, bool HL = false>
+template <int NP, bool TABLE, bool CELL, bool EXT, bool HL = false, bool DF = false>
 static cudaError_t launch_g(const GroupArgs &g, int grid, size_t smem, cudaStream_t st)
 {
-    cudaError_t e = configure_g<NP, TABLE, CELL, EXT, HL>();
+    cudaError_t e = configure_g<NP, TABLE, CELL, EXT, HL, DF>();
     if (e != cudaSuccess) return e;
-    k_groups<NP, TABLE, CELL, EXT, HL><<<grid, kNT, smem, st>>>(g);
+    k_groups<NP, TABLE, CELL, EXT, HL, DF><<<grid, kNT, smem, st>>>(g);
     return cudaGetLastError();
 }
 
 template <int NP>
-static cudaError_t launch_gnp(const GroupArgs &g, int grid, bool table, bool cell, bool ext,
+static cudaError_t launch_gnp(const GroupArgs &g, int grid, bool table, bool cell, bool ext, bool df,
                               size_t smem, cudaStream_t st)
 {
     if (g.hl) {   // FP32 outputs: Newton lists only
-        if (table || cell) return cudaErrorInvalidValue;
+        if (table || cell || df) return cudaErrorInvalidValue;
         return ext ? launch_g<NP, false, false, true, true>(g, grid, smem, st)
                    : launch_g<NP, false, false, false, true>(g, grid, smem, st);
+    }
+    if (df) {     // double-float differencing: particle records (no cells)
+        if (cell) return cudaErrorInvalidValue;
+        if (!table) return ext ? launch_g<NP, false, false, true, false, true>(g, grid, smem, st)
+                               : launch_g<NP, false, false, false, false, true>(g, grid, smem, st);
+        return ext ? launch_g<NP, true, false, true, false, true>(g, grid, smem, st)
+                   : launch_g<NP, true, false, false, false, true>(g, grid, smem, st);
     }
     if (!table) return ext ? launch_g<NP, false, false, true>(g, grid, smem, st)
                            : launch_g<NP, false, false, false>(g, grid, smem, st);
@@ -948,63 +1040,67 @@ static cudaError_t launch_gnp(const GroupArgs &g, int grid, bool table, bool cel
                : launch_g<NP, true, false, false>(g, grid, smem, st);
 }
 
-size_t groups_warp_smem(bool table, int ntab)
+size_t groups_warp_smem(bool table, int ntab, bool df)
 {
-    size_t s = (kWNT / 32) * 4 * kWarpTJ * sizeof(u64) + 28 * 16 +
+    size_t s = (kWNT / 32) * (df ? 8 : 4) * kWarpTJ * sizeof(u64) + 28 * 16 +
                (kWNT / 32) * 2 * kCellTab * sizeof(int);
     if (table) s += (size_t)ntab * sizeof(float2);
     return s;
 }
 
-template <bool TABLE, bool CELL, bool EXT>
+template <bool TABLE, bool CELL, bool EXT, bool DF = false>
 static cudaError_t configure_gw()
 {
-    static bool done = false;
-    if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_groups_warp<TABLE, CELL, EXT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)groups_warp_smem(TABLE, 2 << 13));
-    // the same shared-memory carveout as the CTA-mode kernel, so that its
-    // blocks can join an SM on which that kernel still runs
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_groups_warp<TABLE, CELL, EXT>,
-                                 cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 (int)cudaSharedmemCarveoutMaxShared);
-    done = e == cudaSuccess;
-    return e;
+    static bool done[kMaxDevices] = {};
+    return once_per_device(done, [] {
+        cudaError_t e = cudaFuncSetAttribute(k_groups_warp<TABLE, CELL, EXT, false, DF>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)groups_warp_smem(TABLE, 2 << 13, DF));
+        // the same shared-memory carveout as the CTA-mode kernel, so that its
+        // blocks can join an SM on which that kernel still runs
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_groups_warp<TABLE, CELL, EXT, false, DF>,
+                                     cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
+        return e;
+    });
 }
 
-template <bool TABLE, bool CELL, bool EXT>
+template <bool TABLE, bool CELL, bool EXT, bool DF = false>
 static int occ_gw(size_t smem)
 {
     int nb = 0;
-    if (configure_gw<TABLE, CELL, EXT>() != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_groups_warp<TABLE, CELL, EXT>, kWNT, smem) !=
-            cudaSuccess)
+    if (configure_gw<TABLE, CELL, EXT, DF>() != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_groups_warp<TABLE, CELL, EXT, false, DF>, kWNT,
+                                                      smem) != cudaSuccess)
         return 0;
     return nb;
 }
 
 // blocks per SM of the warp-mode kernel for a table of ntab float2 units
 // (0 if the kernel cannot be configured; cell mode needs the table)
-int groups_warp_blocks_per_sm(bool table, bool cell, bool ext, int ntab)
+int groups_warp_blocks_per_sm(bool table, bool cell, bool ext, int ntab, bool df)
 {
-    if (cell && !table) return 0;
-    const size_t smem = groups_warp_smem(table, ntab);
+    if (cell && (!table || df)) return 0;
+    const size_t smem = groups_warp_smem(table, ntab, df);
     if (cell) return ext ? occ_gw<true, true, true>(smem) : occ_gw<true, true, false>(smem);
+    if (df) {
+        if (table) return ext ? occ_gw<true, false, true, true>(smem) : occ_gw<true, false, false, true>(smem);
+        return ext ? occ_gw<false, false, true, true>(smem) : occ_gw<false, false, false, true>(smem);
+    }
     if (table) return ext ? occ_gw<true, false, true>(smem) : occ_gw<true, false, false>(smem);
     return ext ? occ_gw<false, false, true>(smem) : occ_gw<false, false, false>(smem);
 }
 
 int groups_warp_warps_per_block() { return kWNT / 32; }
 
-template <bool TABLE, bool CELL, bool EXT>
+template <bool TABLE, bool CELL, bool EXT, bool DF = false>
 static cudaError_t launch_gw(const GroupArgs &g, int grid, size_t smem, bool pdl, cudaStream_t st)
 {
-    cudaError_t e = configure_gw<TABLE, CELL, EXT>();
+    cudaError_t e = configure_gw<TABLE, CELL, EXT, DF>();
     if (e != cudaSuccess) return e;
     if (!pdl) {
-        k_groups_warp<TABLE, CELL, EXT><<<grid, kWNT, smem, st>>>(g);
+        k_groups_warp<TABLE, CELL, EXT, false, DF><<<grid, kWNT, smem, st>>>(g);
         return cudaGetLastError();
     }
     // programmatic stream serialisation: the blocks may start once every
@@ -1019,30 +1115,36 @@ static cudaError_t launch_gw(const GroupArgs &g, int grid, size_t smem, bool pdl
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_groups_warp<TABLE, CELL, EXT>, g);
+    return cudaLaunchKernelEx(&cfg, k_groups_warp<TABLE, CELL, EXT, false, DF>, g);
 }
 
 cudaError_t launch_groups_warp(const GroupArgs &g, int grid, bool table, bool cell, bool ext, int ntab,
-                               bool pdl, cudaStream_t st)
+                               bool pdl, bool df, cudaStream_t st)
 {
-    if (grid <= 0 || !g.queue_w || (cell && !table) || g.hl) return cudaErrorInvalidValue;
-    const size_t smem = groups_warp_smem(table, ntab);
+    if (grid <= 0 || !g.queue_w || (cell && (!table || df)) || g.hl) return cudaErrorInvalidValue;
+    const size_t smem = groups_warp_smem(table, ntab, df);
     if (cell) return ext ? launch_gw<true, true, true>(g, grid, smem, pdl, st)
                          : launch_gw<true, true, false>(g, grid, smem, pdl, st);
+    if (df) {
+        if (table) return ext ? launch_gw<true, false, true, true>(g, grid, smem, pdl, st)
+                              : launch_gw<true, false, false, true>(g, grid, smem, pdl, st);
+        return ext ? launch_gw<false, false, true, true>(g, grid, smem, pdl, st)
+                   : launch_gw<false, false, false, true>(g, grid, smem, pdl, st);
+    }
     if (table) return ext ? launch_gw<true, false, true>(g, grid, smem, pdl, st)
                           : launch_gw<true, false, false>(g, grid, smem, pdl, st);
     return ext ? launch_gw<false, false, true>(g, grid, smem, pdl, st)
                : launch_gw<false, false, false>(g, grid, smem, pdl, st);
 }
 
-cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, bool cell, bool ext,
+cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, bool cell, bool ext, bool df,
                           size_t smem, cudaStream_t st)
 {
     if (grid <= 0) return cudaSuccess;
     if (cell && !table) return cudaErrorInvalidValue;
-    if (np == 1) return launch_gnp<1>(g, grid, table, cell, ext, smem, st);
-    if (np == 2) return launch_gnp<2>(g, grid, table, cell, ext, smem, st);
-    if (np == 4) return launch_gnp<4>(g, grid, table, cell, ext, smem, st);
+    if (np == 1) return launch_gnp<1>(g, grid, table, cell, ext, df, smem, st);
+    if (np == 2) return launch_gnp<2>(g, grid, table, cell, ext, df, smem, st);
+    if (np == 4) return launch_gnp<4>(g, grid, table, cell, ext, df, smem, st);
     return cudaErrorInvalidValue;
 }
 

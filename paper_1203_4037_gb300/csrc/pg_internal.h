@@ -14,6 +14,8 @@ namespace pg {
 constexpr int kTJ = 256;
 // threads per CTA of the all-pairs and group kernels
 constexpr int kNT = 128;
+// devices a process may use (per-device set-up flags)
+constexpr int kMaxDevices = 256;
 // time limit of any device-side wait, in nanoseconds
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 
@@ -56,7 +58,8 @@ struct CombineArgs {
     long long ni;
     int Bi, njsub, smax_slots, grid;
     long long W;
-    int self;              // leave out i's own pair (i index k == j index k)
+    int self;              // leave out i's own pair (i index k == j index k + self_off)
+    long long self_off;    // j index of i-particle 0 in self mode
     int newton;            // 1: Newton (has potential), 0: table
     int tabpot;            // table mode with a potential table (agp set)
     const float4 *agp;     // the {A, G1, A_p, P1} table (its knot 0 gives the self term)
@@ -66,7 +69,32 @@ struct CombineArgs {
     double accscale;       // table: r_cut / sqrt(s_max - 2); Newton: 1
     double *acc;           // out: (ni, 3)
     double *pot;           // out: (ni), may be null
+    const int *fail_nan = nullptr;   // set: a nonzero word here (a force kernel's failure
+                                     // status) makes every output NaN
 };
+
+// the all-pairs Newton loop of a small i-set in one launch (pg_small.cu):
+// tiles of small_bi() i in caller order times nchunk chunks of jchunk j
+// records, pair differences in double-float; the last block of each tile
+// combines its partials
+constexpr int kSmallMaxChunk = 1024;   // j records per chunk (staged in shared memory)
+struct SmallArgs {
+    const float4 *ihl;     // i positions as double-float pairs (hi, -), (lo, -), caller order
+    const double4 *xi;     // i records (w: eps_i^2 with per-i softening)
+    const float4 *jhl;     // j records as double-float pairs (hi, m), (lo, m)
+    long long ni, nj;
+    int nchunk, jchunk;
+    float eps2;
+    int epsi;              // per-i softening: eps_i^2 in xi[i].w
+    int self;              // leave out i's own pair, j index i + self_off
+    long long self_off;
+    float4 *part;          // [ntiles][nchunk][small_bi()] FP32 (hi, lo) partials, 2 float4 each
+    unsigned *ticket;      // [ntiles], zero between calls
+    double *acc, *pot;     // out: caller order; pot may be null
+};
+int small_bi();
+size_t small_smem(int jchunk);
+cudaError_t launch_small(const SmallArgs &a, bool ext, cudaStream_t st);
 
 // batched groups: one work item = (group, i-range of at most Bi)
 struct GroupItem {
@@ -131,15 +159,34 @@ struct BackwardArgs {
     TableDev tab;
     double4 *part;         // partials [ntiles][slots][Bi] {gx, gy, gz, gm}
     double *dv;            // knot-gradient accumulators (FP64, 2^(E+F)), may be null
+    const unsigned *perm;  // tile order -> particle index (nullptr: identity): the own pair
     int *status;
 };
+
+// Run a kernel's one-time set-up f (a function attribute) once on each
+// device: attributes belong to the device's context, so a process that uses
+// a second GPU sets them there too. `done` is the caller's per-kernel flags.
+template <typename F>
+inline cudaError_t once_per_device(bool (&done)[kMaxDevices], F f)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const bool slot = dev >= 0 && dev < kMaxDevices;
+    if (slot && done[dev]) return cudaSuccess;
+    e = f();
+    if (e == cudaSuccess && slot) done[dev] = true;
+    return e;
+}
 
 // ---------------------------------------------------------------- launchers
 // all return cudaError_t of the launch
 
 cudaError_t launch_pack_j(const double *x, const double *m, double4 *jrec, long long n,
                           cudaStream_t st);
-cudaError_t launch_pack_i(const double *x, double4 *xi, long long n, cudaStream_t st);
+// i records, and with ihl set also their double-float pairs (hi, 0), (lo, 0)
+cudaError_t launch_pack_i(const double *x, double4 *xi, long long n, cudaStream_t st,
+                          float4 *ihl = nullptr);
 
 // spatial ordering of i: Morton keys in the bounding box, LSD radix sort
 struct SortScratch {
@@ -189,13 +236,15 @@ int pm_solve(PmState *s, const float *rho, const double4 *tgt, long long nt, dou
 cudaError_t launch_tile_prep(const double4 *xi, const unsigned *perm, long long n, int Bi,
                              double4 *xi_tiled, double4 *ctr, cudaStream_t st);
 
+// df: double-float differencing (i-tiles that are not compact; packed
+// arithmetic whatever `packed` says)
 cudaError_t launch_allpairs(const AllPairsArgs &a, int grid, int np, bool table, bool ext,
-                            bool packed, size_t smem, cudaStream_t st);
+                            bool packed, bool df, size_t smem, cudaStream_t st);
 int allpairs_bi(int np);
 // ntab: the table's size in float2 units (twice the knot count with a
 // potential table)
-size_t allpairs_smem(int np, bool table, int ntab, bool ext = false);
-int allpairs_max_blocks_per_sm(int np, bool table, int ntab, bool packed, bool ext = false);
+size_t allpairs_smem(int np, bool table, int ntab, bool ext, bool df);
+int allpairs_max_blocks_per_sm(int np, bool table, int ntab, bool packed, bool ext, bool df);
 cudaError_t launch_combine(const CombineArgs &c, cudaStream_t st);
 long long stream_k_first(long long u, int grid, long long W);
 
@@ -204,7 +253,8 @@ cudaError_t launch_table_prep(const float *G0, const float *G1, float2 *AG1, int
 cudaError_t launch_table_from_values(const float *v, float *G0, float *G1, int E, int F,
                                      cudaStream_t st);
 
-cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, bool cell, bool ext,
+// df: double-float differencing of particle records (narrow all-pairs)
+cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, bool cell, bool ext, bool df,
                           size_t smem, cudaStream_t st);
 // the FP64 outputs of a groups run made with g.hl set: one thread per i
 cudaError_t launch_groups_finish(const GroupArgs &g, cudaStream_t st);
@@ -215,18 +265,18 @@ cudaError_t launch_pack_hilo(const double4 *in, long long n, float4 *out, cudaSt
 // i records and the two work counters zeroed, in one launch
 cudaError_t launch_narrow_prep(const double4 *xi, long long ni, long long chunk, long long nic,
                               double4 *ctr, float4 *ihl, int *queue, cudaStream_t st);
-size_t groups_smem(int np, bool table, int ntab);   // ntab in float2 units, as above
+size_t groups_smem(int np, bool table, int ntab, bool df);   // ntab in float2 units, as above
 int groups_bi(int np);
-int groups_max_blocks_per_sm(int np, bool table, int ntab, bool cell, bool ext = false);
+int groups_max_blocks_per_sm(int np, bool table, int ntab, bool cell, bool ext, bool df);
 // warp-mode items in a launch of their own (k_groups_warp): the cell list's
 // small cells after the CTA-mode kernel (pdl: programmatic dependent launch,
 // for a kernel whose inputs were complete before the CTA-mode kernel
 // started), and narrow all-pairs items (ordinary launch); g.queue_w set
-size_t groups_warp_smem(bool table, int ntab);
-int groups_warp_blocks_per_sm(bool table, bool cell, bool ext, int ntab);
+size_t groups_warp_smem(bool table, int ntab, bool df);
+int groups_warp_blocks_per_sm(bool table, bool cell, bool ext, int ntab, bool df);
 int groups_warp_warps_per_block();
 cudaError_t launch_groups_warp(const GroupArgs &g, int grid, bool table, bool cell, bool ext, int ntab,
-                               bool pdl, cudaStream_t st);
+                               bool pdl, bool df, cudaStream_t st);
 cudaError_t launch_table_merge(const float2 *AG1, const float *P0, const float *P1, float4 *AGP,
                                int E, int F, cudaStream_t st);
 cudaError_t launch_set_w(double4 *x, const double *eps, long long n, cudaStream_t st);

@@ -1,7 +1,10 @@
 // pg_micro.cu -- measured ceilings for the roofline: throughput of scalar
-// FP32 FMA chains, packed FP32x2 FMA chains, MUFU rsqrt chains, and the
-// Newton pair term's exact instruction mix with every operand in registers
-// (no shared or global memory), each timed with CUDA events.
+// FP32 FMA chains, packed FP32x2 FMA chains, MUFU rsqrt chains, the Newton
+// pair term's exact instruction mix with every operand in registers (no
+// shared or global memory), and random 8-byte gathers from a 4096-entry
+// table in shared memory (the tabulated force's lookup, Section 3.4, with
+// indices spread like those of pairs inside the cutoff), each timed with
+// CUDA events.
 #include <cuda_runtime.h>
 
 #include "pg.h"
@@ -17,12 +20,35 @@ constexpr int kSinkSize = 8192;
 // destination of the (practically never taken) store that keeps the work alive
 __device__ float g_micro_sink[kSinkSize];
 
-// kind 0: scalar FFMA; 1: packed FFMA2; 2: MUFU rsqrt; 3: the Newton pair mix
+constexpr int kGatherTable = 4096;   // entries of the gather table (float2, 32 KB)
+
+// kind 0: scalar FFMA; 1: packed FFMA2; 2: MUFU rsqrt; 3: the Newton pair
+// mix; 4: random 8-byte shared-memory gathers (kGatherTable entries)
 __global__ void __launch_bounds__(kMicroThreads) k_micro(int kind, int iters, float seed)
 {
+    extern __shared__ float2 gtab[];
     const float s = seed + threadIdx.x * 1e-7f;
     float acc = 0.0f;
-    if (kind == 0) {
+    if (kind == 4) {
+        for (int k = threadIdx.x; k < kGatherTable; k += kMicroThreads)
+            gtab[k] = make_float2(1e-30f * k, 0.0f);
+        __syncthreads();
+        // kChains independent chains per thread; each gather's index comes
+        // from a per-lane pseudo-random sequence mixed with the value just
+        // loaded (zero here), so no load can be hoisted or merged
+        unsigned h[kChains];
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) h[c] = (threadIdx.x + 1) * 2654435761u + c * 40503u + blockIdx.x;
+        float sum = 0.0f;
+        for (int it = 0; it < iters; ++it)
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) {
+                const float2 v = gtab[(h[c] >> 12) & (kGatherTable - 1)];
+                h[c] = h[c] * 1664525u + 1013904223u + __float_as_uint(v.y);
+                sum += v.x;
+            }
+        acc = sum;
+    } else if (kind == 0) {
         float x[kChains];
 #pragma unroll
         for (int c = 0; c < kChains; ++c) x[c] = s + c;
@@ -104,24 +130,25 @@ using namespace pg;
 
 extern "C" int pg_microbench(int kind, double *per_sm_clock, double *per_second)
 {
-    if (kind < 0 || kind > 3 || !per_sm_clock || !per_second) return PG_EINVAL;
+    if (kind < 0 || kind > 4 || !per_sm_clock || !per_second) return PG_EINVAL;
     int dev = 0, sms = 0, clk_khz = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { (void)cudaGetLastError(); return PG_ECUDA; }
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
     const int blocks = sms * 8;
-    const int iters = kind == 2 ? 4096 : 16384;
+    const int iters = kind == 2 || kind == 4 ? 4096 : 16384;
     // lane operations per thread per iteration: FFMA 8, FFMA2 16, rsqrt 8,
-    // Newton mix: 8 interactions (4 pairs x 2 lanes)
-    const double per_iter = kind == 0 ? 8.0 : kind == 1 ? 16.0 : kind == 2 ? 8.0 : 8.0;
+    // Newton mix: 8 interactions (4 pairs x 2 lanes), gathers 8
+    const double per_iter = kind == 0 ? 8.0 : kind == 1 ? 16.0 : 8.0;
+    const size_t smem = kind == 4 ? kGatherTable * sizeof(float2) : 0;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         (void)cudaGetLastError();
         return PG_ECUDA;
     }
-    k_micro<<<blocks, kMicroThreads>>>(kind, 64, 0.5f);   // warm-up
+    k_micro<<<blocks, kMicroThreads, smem>>>(kind, 64, 0.5f);   // warm-up
     cudaEventRecord(e0);
-    k_micro<<<blocks, kMicroThreads>>>(kind, iters, 0.5f);
+    k_micro<<<blocks, kMicroThreads, smem>>>(kind, iters, 0.5f);
     cudaEventRecord(e1);
     cudaError_t e = cudaEventSynchronize(e1);
     float ms = 0;

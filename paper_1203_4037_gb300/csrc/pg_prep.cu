@@ -13,11 +13,18 @@ namespace pg {
 
 // ---------------------------------------------------------------- packing
 __global__ void k_pack_j(const double *__restrict__ x, const double *__restrict__ m,
-                         double4 *__restrict__ out, long long n)
+                         double4 *__restrict__ out, long long n, float4 *__restrict__ hl)
 {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    out[i] = make_double4(x[3 * i], x[3 * i + 1], x[3 * i + 2], m ? m[i] : 0.0);
+    const double4 v = make_double4(x[3 * i], x[3 * i + 1], x[3 * i + 2], m ? m[i] : 0.0);
+    out[i] = v;
+    if (hl) {   // double-float pairs: hi = fp32(x), lo = fp32(x - hi)
+        const float hx = (float)v.x, hy = (float)v.y, hz = (float)v.z;
+        hl[2 * i] = make_float4(hx, hy, hz, (float)v.w);
+        hl[2 * i + 1] = make_float4((float)(v.x - (double)hx), (float)(v.y - (double)hy),
+                                    (float)(v.z - (double)hz), (float)v.w);
+    }
 }
 
 // i records' fourth value: eps_k^2 with per-i softening (eps == nullptr: 0)
@@ -40,13 +47,15 @@ cudaError_t launch_pack_j(const double *x, const double *m, double4 *jrec, long 
                           cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    k_pack_j<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, m, jrec, n);
+    k_pack_j<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, m, jrec, n, nullptr);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack_i(const double *x, double4 *xi, long long n, cudaStream_t st)
+cudaError_t launch_pack_i(const double *x, double4 *xi, long long n, cudaStream_t st, float4 *ihl)
 {
-    return launch_pack_j(x, nullptr, xi, n, st);
+    if (n <= 0) return cudaSuccess;
+    k_pack_j<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, nullptr, xi, n, ihl);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- bbox

@@ -1,6 +1,7 @@
 """The roofline microbenchmark returns plausible ceilings on the device:
-FP32 FMA lane rates near 128 per SM per clock, MUFU rsqrt near 16, and the
-Newton pair term in registers between the MUFU and FP32 bounds."""
+FP32 FMA lane rates near 128 per SM per clock, MUFU rsqrt near 16, the
+Newton pair term in registers between the MUFU and FP32 bounds, and random
+8-byte shared-memory gathers below the conflict-free 16 per SM per clock."""
 
 import pytest
 
@@ -19,3 +20,5 @@ def test_microbench_ceilings():
     assert 32 < ffma < 140 and 32 < ffma2 < 140
     assert 4 < mufu < 20
     assert 2 < mix < 11 and mix_s > 1e11
+    gather, _ = pg.pg_microbench(4)
+    assert 1 < gather <= 16.5

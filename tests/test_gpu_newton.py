@@ -100,11 +100,13 @@ def test_partial_j_updates_and_set_n(pg, orc):
 
 
 def test_eps_zero_leaves_coincident_pair_out(pg, orc):
+    # unsoftened close pairs of an unordered set: the double-float
+    # differences keep them at the usual tolerances
     x, m = gen.plummer(2000, 41)
     a, p = run_allpairs(pg, x, m, 0.0)
     ao, po = orc.newton_allpairs(x, m, 0.0)
     assert np.all(np.isfinite(a)) and np.all(np.isfinite(p))
-    assert_parity(rel_vec(a, ao), max_tol=1e-3, what="a")
+    assert_parity(rel_vec(a, ao), what="a")
     assert_parity(rel_scalar(p, po), what="phi")
 
 
