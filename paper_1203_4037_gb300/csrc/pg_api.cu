@@ -75,6 +75,7 @@ struct pg_ctx {
     // outputs and partials
     DevBuf acc, pot, part;
     DevBuf tickets;               // the small path's per-tile tickets (kept at zero between runs)
+    int small_clusters[2] = {-1, -1};   // its resident clusters (without, with EXT; -1: not asked)
     size_t tickets_zeroed = 0;    // bytes of it known to be zero
     DevBuf status;                // 2 ints
 
@@ -1197,17 +1198,25 @@ int enqueue_tiles(pg_ctx *c, const Plan &p)
 // in the caller's order, double-float differences) whose j records fit
 // chunks of at most kSmallMaxChunk, with the launch shape left to the
 // library. One launch does the pair loop and the combine (pg_small.cu).
-// Sets its chunk count and size (about four blocks per SM).
-bool use_small(const pg_ctx *c, const Plan &p, int &nchunk, int &jchunk)
+// Sets its chunk count (a multiple of the cluster size, as many clusters as
+// fit on the device at once: one wave) and chunk size.
+bool use_small(pg_ctx *c, const Plan &p, int &nchunk, int &jchunk)
 {
     if (c->mode != PG_NEWTON || c->np != 0 || p.ni <= 0 || p.nj <= 0 || tiles_sorted(c, p.ni) || !p.df)
         return false;
+    const bool ext = use_ext(c);
+    int &clusters = c->small_clusters[ext ? 1 : 0];
+    if (clusters < 0) clusters = small_max_clusters(ext);
+    if (clusters <= 0) return false;
     const long long ntiles = (p.ni + small_bi() - 1) / small_bi();
-    long long nc = std::max<long long>(1, ((long long)c->sms * 4 + ntiles / 2) / ntiles);
+    const long long cs = small_cluster();
+    long long nc = cs * std::max<long long>(1, clusters / ntiles);
     long long jc = (p.nj + nc - 1) / nc;
-    if (jc > kSmallMaxChunk) jc = kSmallMaxChunk;
-    nc = (p.nj + jc - 1) / jc;
-    if (ntiles * nc > (long long)c->sms * 64) return false;   // more blocks than one pass wants
+    if (jc > kSmallMaxChunk) {
+        jc = kSmallMaxChunk;
+        nc = ((p.nj + jc - 1) / jc + cs - 1) / cs * cs;
+    }
+    if (ntiles * nc > (long long)clusters * cs * 4) return false;   // more than a few waves
     nchunk = (int)nc;
     jchunk = (int)jc;
     return true;
@@ -1217,7 +1226,7 @@ int enqueue_small(pg_ctx *c, const Plan &p, int nchunk, int jchunk, double *acc,
 {
     int rc;
     const long long ntiles = (p.ni + small_bi() - 1) / small_bi();
-    if ((rc = ensure(c, c->part, (size_t)ntiles * nchunk * small_bi() * 32)) ||
+    if ((rc = ensure(c, c->part, (size_t)ntiles * (nchunk / small_cluster()) * 8 * small_bi() * sizeof(float))) ||
         (rc = ensure(c, c->tickets, (size_t)ntiles * sizeof(unsigned))) ||
         (rc = ensure(c, c->g_jhl, (size_t)p.nj * 32)) || (rc = ensure(c, c->g_ihl, (size_t)p.ni * 32)))
         return rc;
@@ -1245,7 +1254,7 @@ int enqueue_small(pg_ctx *c, const Plan &p, int nchunk, int jchunk, double *acc,
     a.epsi = c->have_epsi;
     a.self = c->self;
     a.self_off = c->self_off;
-    a.part = (float4 *)c->part.p;
+    a.part = (float *)c->part.p;
     a.ticket = (unsigned *)c->tickets.p;
     a.acc = acc;
     a.pot = pot;

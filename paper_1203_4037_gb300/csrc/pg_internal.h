@@ -75,8 +75,9 @@ struct CombineArgs {
 
 // the all-pairs Newton loop of a small i-set in one launch (pg_small.cu):
 // tiles of small_bi() i in caller order times nchunk chunks of jchunk j
-// records, pair differences in double-float; the last block of each tile
-// combines its partials
+// records (nchunk a multiple of small_cluster()), pair differences in
+// double-float; each cluster sums its chunks in distributed shared memory,
+// the last block of each tile adds the clusters' sums
 constexpr int kSmallMaxChunk = 1024;   // j records per chunk (staged in shared memory)
 struct SmallArgs {
     const float4 *ihl;     // i positions as double-float pairs (hi, -), (lo, -), caller order
@@ -88,11 +89,15 @@ struct SmallArgs {
     int epsi;              // per-i softening: eps_i^2 in xi[i].w
     int self;              // leave out i's own pair, j index i + self_off
     long long self_off;
-    float4 *part;          // [ntiles][nchunk][small_bi()] FP32 (hi, lo) partials, 2 float4 each
+    float *part;           // [ntiles][nchunk / small_cluster()][8][small_bi()]: each cluster's
+                           // FP32 sums, hi of x, y, z, phi then lo
     unsigned *ticket;      // [ntiles], zero between calls
     double *acc, *pot;     // out: caller order; pot may be null
 };
 int small_bi();
+int small_cluster();                   // blocks per thread-block cluster (chunks of one tile)
+int small_max_clusters(bool ext);      // clusters resident at once on the current device
+int small_blocks_per_sm();
 size_t small_smem(int jchunk);
 cudaError_t launch_small(const SmallArgs &a, bool ext, cudaStream_t st);
 

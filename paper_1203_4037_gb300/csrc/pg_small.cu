@@ -6,9 +6,12 @@
 // separate launches for tile preparation, the force loop and the combine
 // cost more than the work. Here one kernel does all of it:
 //
-//  * the i-particles (caller order, 256 per tile: 128 threads, one packed
-//    pair of i each) and the j records are cut into ntiles x nchunk blocks,
-//    nchunk chosen so that the grid fills the SMs;
+//  * the i-particles (caller order, 256 per tile) and the j records are cut
+//    into ntiles x nchunk blocks, about two per SM; each of a block's four
+//    warps holds all 256 i of its tile (four packed i-pairs per lane, the
+//    independent work the pair loop needs to hide its latencies) and takes
+//    every fourth j of the block's chunk; the warps' sums are added in
+//    shared memory in warp order;
 //  * positions arrive as double-float records (FP32 hi, FP32 lo = x - hi,
 //    packed once when they are set), and a pair's difference is formed as
 //    (hi_j - hi_i) + (lo_j - lo_i): FP32 precision relative to |d| itself,
@@ -33,9 +36,18 @@ namespace pg {
 
 namespace {
 
-constexpr int kSmallNT = 128;              // threads: one i-pair each
-constexpr int kSmallBi = 2 * kSmallNT;     // i per tile
-constexpr int kSmallSub = 256;             // j per compensated sub-tile
+constexpr int kSmallNT = 128;              // threads: four warps
+constexpr int kSmallWarps = kSmallNT / 32;
+constexpr int kSmallNP = 4;                // i-pairs per lane
+constexpr int kSmallBi = 64 * kSmallNP;    // i per tile: every warp holds all of them
+constexpr int kSmallBlocksPerSM = 3;       // resident blocks per SM (the register limit)
+// blocks per cluster (chunks of one tile): 4 pack three blocks on every
+// SM of GB300 (measured: with 8, 48 clusters fit at once, 384 blocks, and
+// the SMs holding three of them set the time)
+constexpr int kSmallCluster = 4;
+constexpr int kSliceI = kSmallBi / kSmallCluster;          // i reduced by each block of a cluster
+static_assert(kSmallBi % kSmallCluster == 0 && (kSliceI * 4) % kSmallNT == 0,
+              "a block reduces its cluster's slice, (i, component) pairs spread over its threads");
 
 // the own pair's potential as the loop added it (d = 0 exactly): -m rsqrt(eps^2),
 // nothing at eps = 0
@@ -45,45 +57,83 @@ __device__ __forceinline__ double small_self_pot(const SmallArgs &a, long long k
     return e2 > 0.0f ? -(double)__fmul_rn(mk, rsq(e2)) : 0.0;
 }
 
+// the cluster (distributed shared memory) primitives
+__device__ __forceinline__ unsigned cluster_rank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// every thread of every block of the cluster arrives; shared-memory writes
+// before it are visible to the cluster's blocks after it
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// the float at this block's shared address p, in the shared memory of the
+// cluster's block `rank`
+__device__ __forceinline__ float ld_cluster(const float *p, unsigned rank)
+{
+    const unsigned a = smem_u32(p);
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(r) : "memory");
+    return v;
+}
+
+// Lane l of every warp holds the tile's i-particles i0 + 64 p + l and
+// i0 + 64 p + 32 + l (p < kSmallNP) as packed pairs; warp w takes every
+// kSmallWarps-th staged j from w on. The kSmallCluster blocks of a cluster
+// hold consecutive chunks of one tile (nchunk is a multiple of it).
 template <bool EXT>
-__global__ void __launch_bounds__(kSmallNT) k_small(SmallArgs a)
+__global__ void __launch_bounds__(kSmallNT, kSmallBlocksPerSM) k_small(SmallArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     ulonglong2 *cv = reinterpret_cast<ulonglong2 *>(smem);    // [jchunk][4]
+    float *red = reinterpret_cast<float *>(smem);             // reuse: [warps][4][kSmallBi]
+    __shared__ float bp[8 * kSmallBi];                        // the block's sums: hi [4][Bi], lo [4][Bi]
     __shared__ int last;
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long tile = blockIdx.x / a.nchunk;
     const int chunk = (int)(blockIdx.x - tile * a.nchunk);
     const long long i0 = tile * kSmallBi;
+    const int ncl = a.nchunk / kSmallCluster;                 // clusters per tile
+    const int cl = chunk / kSmallCluster;                     // this block's cluster in the tile
 
-    // this thread's i-pair and each i's eps^2
-    float hx[2], hy[2], hz[2], lx[2], ly[2], lz[2], fe[2];
+    // this lane's i-pairs: double-float positions, each i's eps^2
+    u64 xi[kSmallNP], yi[kSmallNP], zi[kSmallNP], exi[kSmallNP], eyi[kSmallNP], ezi[kSmallNP];
+    u64 r0[kSmallNP];
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const long long i = i0 + q * kSmallNT + tid;
-        float4 h = make_float4(0.0f, 0.0f, 0.0f, 0.0f), l = h;
-        fe[q] = a.eps2;
-        if (i < a.ni) {
-            h = a.ihl[2 * i];
-            l = a.ihl[2 * i + 1];
-            if (EXT && a.epsi) fe[q] = (float)a.xi[i].w;
+    for (int p = 0; p < kSmallNP; ++p) {
+        float hx[2], hy[2], hz[2], lx[2], ly[2], lz[2], fe[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const long long i = i0 + 64 * p + 32 * q + lane;
+            float4 h = make_float4(0.0f, 0.0f, 0.0f, 0.0f), l = h;
+            fe[q] = a.eps2;
+            if (i < a.ni) {
+                h = a.ihl[2 * i];
+                l = a.ihl[2 * i + 1];
+                if (EXT && a.epsi) fe[q] = (float)a.xi[i].w;
+            }
+            hx[q] = h.x; hy[q] = h.y; hz[q] = h.z;
+            lx[q] = l.x; ly[q] = l.y; lz[q] = l.z;
         }
-        hx[q] = h.x; hy[q] = h.y; hz[q] = h.z;
-        lx[q] = l.x; ly[q] = l.y; lz[q] = l.z;
+        xi[p] = pk2(hx[0], hx[1]); yi[p] = pk2(hy[0], hy[1]); zi[p] = pk2(hz[0], hz[1]);
+        exi[p] = pk2(lx[0], lx[1]); eyi[p] = pk2(ly[0], ly[1]); ezi[p] = pk2(lz[0], lz[1]);
+        r0[p] = pk2(fe[0], fe[1]);
     }
-    const u64 xi = pk2(hx[0], hx[1]), yi = pk2(hy[0], hy[1]), zi = pk2(hz[0], hz[1]);
-    const u64 exi = pk2(lx[0], lx[1]), eyi = pk2(ly[0], ly[1]), ezi = pk2(lz[0], lz[1]);
-    const u64 r0 = pk2(fe[0], fe[1]);
 
     // stage the chunk's j records: {hi_x, hi_y}, {hi_z, m}, {lo_x, lo_y},
-    // {lo_z, 0}, each value in both lanes (padding: zero mass far away, an
-    // exact zero term)
+    // {lo_z, 0}, each value in both lanes (padding, and chunks past the last
+    // j: zero mass far away, an exact zero term)
     const long long jb = (long long)chunk * a.jchunk;
     long long je = jb + a.jchunk;
     if (je > a.nj) je = a.nj;
-    const int nv = (int)(je - jb);
-    const int nvp = (nv + 15) & ~15;             // the loop's unroll
+    const int nv = je > jb ? (int)(je - jb) : 0;
+    const int nvp = (nv + 4 * kSmallWarps - 1) & ~(4 * kSmallWarps - 1);   // the warps' unroll
     for (int e = tid; e < nvp; e += kSmallNT) {
         float4 h = make_float4(1.0e4f, 1.0e4f, 1.0e4f, 0.0f), l = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (e < nv) {
@@ -95,21 +145,22 @@ __global__ void __launch_bounds__(kSmallNT) k_small(SmallArgs a)
         cv[4 * e + 2] = make_ulonglong2(pk2(l.x, l.x), pk2(l.y, l.y));
         cv[4 * e + 3] = make_ulonglong2(pk2(l.z, l.z), 0ull);
     }
-
     __syncthreads();
 
-    // the pair loop, compensated per sub-tile
-    u64 sh[4] = {0, 0, 0, 0}, sl[4] = {0, 0, 0, 0};
-    for (int s0 = 0; s0 < nvp; s0 += kSmallSub) {
-        const int s1 = min(nvp, s0 + kSmallSub);
-        u64 ax = 0, ay = 0, az = 0, ph = 0;
-#pragma unroll 16
-        for (int e = s0; e < s1; ++e) {
-            const ulonglong2 hxy = cv[4 * e], hzm = cv[4 * e + 1], lxy = cv[4 * e + 2], lz0 = cv[4 * e + 3];
-            const u64 dx = f2add(f2sub(hxy.x, xi), f2sub(lxy.x, exi));
-            const u64 dy = f2add(f2sub(hxy.y, yi), f2sub(lxy.y, eyi));
-            const u64 dz = f2add(f2sub(hzm.x, zi), f2sub(lz0.x, ezi));
-            u64 r2 = f2fma(dx, dx, r0);
+    // the pair loop: at most kSmallMaxChunk / kSmallWarps = 256 j per warp,
+    // one FP32 sum each
+    u64 ax[kSmallNP], ay[kSmallNP], az[kSmallNP], ph[kSmallNP];
+#pragma unroll
+    for (int p = 0; p < kSmallNP; ++p) ax[p] = ay[p] = az[p] = ph[p] = 0ull;
+#pragma unroll 4
+    for (int e = warp; e < nvp; e += kSmallWarps) {
+        const ulonglong2 hxy = cv[4 * e], hzm = cv[4 * e + 1], lxy = cv[4 * e + 2], lz0 = cv[4 * e + 3];
+#pragma unroll
+        for (int p = 0; p < kSmallNP; ++p) {
+            const u64 dx = f2add(f2sub(hxy.x, xi[p]), f2sub(lxy.x, exi[p]));
+            const u64 dy = f2add(f2sub(hxy.y, yi[p]), f2sub(lxy.y, eyi[p]));
+            const u64 dz = f2add(f2sub(hzm.x, zi[p]), f2sub(lz0.x, ezi[p]));
+            u64 r2 = f2fma(dx, dx, r0[p]);
             r2 = f2fma(dy, dy, r2);
             r2 = f2fma(dz, dz, r2);
             float ra, rb;
@@ -122,78 +173,104 @@ __global__ void __launch_bounds__(kSmallNT) k_small(SmallArgs a)
             const u64 q = pk2(qa, qb);
             const u64 mq = f2mul(hzm.y, q);
             const u64 mq3 = f2mul(mq, f2mul(q, q));
-            ph = f2sub(ph, mq);
-            ax = f2fma(mq3, dx, ax);
-            ay = f2fma(mq3, dy, ay);
-            az = f2fma(mq3, dz, az);
+            ph[p] = f2sub(ph[p], mq);
+            ax[p] = f2fma(mq3, dx, ax[p]);
+            ay[p] = f2fma(mq3, dy, ay[p]);
+            az[p] = f2fma(mq3, dz, az[p]);
         }
-        fold2(sh[0], sl[0], ax);
-        fold2(sh[1], sl[1], ay);
-        fold2(sh[2], sl[2], az);
-        fold2(sh[3], sl[3], ph);
     }
+    __syncthreads();           // every warp done with the staged records
 
-    // this block's (hi, lo) partials, then a ticket of the tile
-    {
-        float h[8], l[8];
+    // the warps' sums: red[w][k][i], k = x, y, z, phi
+#pragma unroll
+    for (int p = 0; p < kSmallNP; ++p) {
+        float v[8];
+        up2(ax[p], v[0], v[1]); up2(ay[p], v[2], v[3]); up2(az[p], v[4], v[5]); up2(ph[p], v[6], v[7]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+                red[(warp * 4 + k) * kSmallBi + 64 * p + 32 * q + lane] = v[2 * k + q];
+    }
+    __syncthreads();
+    // the block's sums, warps in order with TwoSum: bp[k][i] hi, bp[4 + k][i] lo
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int li = q * kSmallNT + tid;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            up2(sh[k], h[2 * k], h[2 * k + 1]);
-            up2(sl[k], l[2 * k], l[2 * k + 1]);
-        }
-        float4 *dst = a.part + 2 * (((size_t)tile * a.nchunk + chunk) * kSmallBi);
+            float H = 0.0f, L = 0.0f;
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int li = q * kSmallNT + tid;
-            dst[2 * li] = make_float4(h[q], h[2 + q], h[4 + q], h[6 + q]);
-            dst[2 * li + 1] = make_float4(l[q], l[2 + q], l[4 + q], l[6 + q]);
+            for (int w = 0; w < kSmallWarps; ++w) {
+                float s2, e2;
+                two_sum(H, red[(w * 4 + k) * kSmallBi + li], s2, e2);
+                H = s2;
+                L = __fadd_rn(L, e2);
+            }
+            bp[k * kSmallBi + li] = H;
+            bp[(4 + k) * kSmallBi + li] = L;
         }
     }
-    __threadfence();           // this thread's partials visible before the ticket
+
+    // the cluster's sum: block rank r adds the tile's i-slice
+    // [r kSliceI, (r + 1) kSliceI) over the cluster's blocks in rank order
+    // (distributed shared memory, (i, component) pairs spread over the
+    // threads) and stores it as this cluster's partial of those i
+    cluster_sync();
+    {
+        const unsigned r = cluster_rank();
+        float *dst = a.part + 8 * ((size_t)(tile * ncl + cl) * kSmallBi);
+#pragma unroll
+        for (int t = tid; t < 4 * kSliceI; t += kSmallNT) {
+            const int li = (int)r * kSliceI + (t % kSliceI);
+            const int k = t / kSliceI;
+            float H = 0.0f, L = 0.0f;
+#pragma unroll
+            for (unsigned b = 0; b < (unsigned)kSmallCluster; ++b) {
+                const float h = ld_cluster(bp + k * kSmallBi + li, b);
+                const float l = ld_cluster(bp + (4 + k) * kSmallBi + li, b);
+                float s2, e2;
+                two_sum(H, h, s2, e2);
+                H = s2;
+                L = __fadd_rn(L, __fadd_rn(l, e2));
+            }
+            dst[k * kSmallBi + li] = H;
+            dst[(4 + k) * kSmallBi + li] = L;
+        }
+    }
+    cluster_sync();            // no block leaves while another reads its shared memory
+
+    __threadfence();           // this thread's partial visible before the ticket
     __syncthreads();
     if (tid == 0) last = atomicAdd(a.ticket + tile, 1u) == (unsigned)(a.nchunk - 1);
     __syncthreads();
     if (!last) return;
     __threadfence();
 
-    // the last block of the tile: the partials in chunk order (TwoSum), FP64 out
+    // the last block of the tile: the clusters' partials in order (TwoSum), FP64 out
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-        const long long i = i0 + q * kSmallNT + tid;
+        const int li = q * kSmallNT + tid;
+        const long long i = i0 + li;
         if (i >= a.ni) continue;
         float H[4] = {0, 0, 0, 0}, L[4] = {0, 0, 0, 0};
-        const float4 *src = a.part + 2 * ((size_t)tile * a.nchunk * kSmallBi + q * kSmallNT + tid);
-        // eight chunks' partials in flight at a time (L2 reads: other blocks
-        // wrote them), added in chunk order
-        constexpr int kBatch = 8;
-        for (int c0 = 0; c0 < a.nchunk; c0 += kBatch) {
-            float4 vh[kBatch], vl[kBatch];
+        for (int c = 0; c < ncl; ++c) {
+            const float *src = a.part + 8 * ((size_t)(tile * ncl + c) * kSmallBi);
 #pragma unroll
-            for (int b = 0; b < kBatch; ++b) {
-                const int c = c0 + b < a.nchunk ? c0 + b : c0;
-                vh[b] = __ldcg(src + 2 * (size_t)c * kSmallBi);
-                vl[b] = __ldcg(src + 2 * (size_t)c * kSmallBi + 1);
-            }
-#pragma unroll
-            for (int b = 0; b < kBatch; ++b) {
-                if (c0 + b >= a.nchunk) break;
-                const float ph[4] = {vh[b].x, vh[b].y, vh[b].z, vh[b].w};
-                const float pl[4] = {vl[b].x, vl[b].y, vl[b].z, vl[b].w};
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    float s, e;
-                    two_sum(H[k], ph[k], s, e);
-                    H[k] = s;
-                    L[k] = __fadd_rn(L[k], __fadd_rn(pl[k], e));
-                }
+            for (int k = 0; k < 4; ++k) {
+                float s2, e2;
+                two_sum(H[k], __ldcg(src + k * kSmallBi + li), s2, e2);
+                H[k] = s2;
+                L[k] = __fadd_rn(L[k], __fadd_rn(__ldcg(src + (4 + k) * kSmallBi + li), e2));
             }
         }
-        double ph = (double)H[3] + (double)L[3];
-        if (a.self) ph -= small_self_pot(a, i, fe[q]);
+        const float e2i = EXT && a.epsi ? (float)a.xi[i].w : a.eps2;
+        double phv = (double)H[3] + (double)L[3];
+        if (a.self) phv -= small_self_pot(a, i, e2i);
         a.acc[3 * i] = (double)H[0] + (double)L[0];
         a.acc[3 * i + 1] = (double)H[1] + (double)L[1];
         a.acc[3 * i + 2] = (double)H[2] + (double)L[2];
-        if (a.pot) a.pot[i] = ph;
+        if (a.pot) a.pot[i] = phv;
     }
     if (tid == 0) a.ticket[tile] = 0u;   // ready for the next call
 }
@@ -203,8 +280,12 @@ cudaError_t configure_small()
 {
     static bool done[kMaxDevices] = {};
     return once_per_device(done, [] {
-        return cudaFuncSetAttribute(k_small<EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)small_smem(kSmallMaxChunk));
+        cudaError_t e = cudaFuncSetAttribute(k_small<EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)small_smem(kSmallMaxChunk));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_small<EXT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
+        return e;
     });
 }
 
@@ -213,27 +294,72 @@ cudaError_t launch_small_one(const SmallArgs &a, int grid, size_t smem, cudaStre
 {
     cudaError_t e = configure_small<EXT>();
     if (e != cudaSuccess) return e;
-    k_small<EXT><<<grid, kSmallNT, smem, st>>>(a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kSmallNT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kSmallCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_small<EXT>, a);
+}
+
+// clusters of kSmallCluster blocks resident at once on this device
+template <bool EXT>
+int clusters_one(size_t smem)
+{
+    if (configure_small<EXT>() != cudaSuccess) return 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kSmallCluster);
+    cfg.blockDim = dim3(kSmallNT);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kSmallCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_small<EXT>, &cfg) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return n;
 }
 
 }  // namespace
 
 int small_bi() { return kSmallBi; }
+int small_cluster() { return kSmallCluster; }
+int small_max_clusters(bool ext)
+{
+    const size_t smem = small_smem(kSmallMaxChunk);
+    return ext ? clusters_one<true>(smem) : clusters_one<false>(smem);
+}
 
-// Shared memory per block: the staged chunk, but at least a quarter of an
-// SM's shared memory less the per-block reserve, so that at most four blocks
-// share an SM. The grid is about four blocks per SM and fits in one wave; left
-// to the register limit (nine blocks), the block scheduler stacked up to 2.3
-// times the average work on some SMs (measured: busiest SM 75k cycles
-// against 33k on average for the 4096-body call).
-constexpr size_t kSmallMinSmem = 50 * 1024;
+// Shared memory per block: the staged chunk and the warps' sums after it,
+// but at least kSmallMinSmem so that at most small_blocks_per_sm() blocks
+// share an SM. The grid is that many blocks per SM, in one wave; left to the
+// register limit the block scheduler placed one to three blocks on an SM
+// (measured: busiest SM 57k cycles against 31k on average for the 4096-body
+// call), and the busiest SM sets the time.
+constexpr size_t kSmallMinSmem = 60 * 1024;          // 4 x (60 KB + reserve) > 228 KB
+
+int small_blocks_per_sm() { return kSmallBlocksPerSM; }
 
 size_t small_smem(int jchunk)
 {
-    const int nvp = (jchunk + 15) & ~15;
-    const size_t need = (size_t)nvp * 8 * sizeof(u64);
-    return need > kSmallMinSmem ? need : kSmallMinSmem;
+    const int nvp = (jchunk + 4 * kSmallWarps - 1) & ~(4 * kSmallWarps - 1);
+    size_t s = (size_t)nvp * 8 * sizeof(u64);
+    const size_t red = (size_t)kSmallWarps * 4 * kSmallBi * sizeof(float);
+    if (s < red) s = red;
+    return s > kSmallMinSmem ? s : kSmallMinSmem;
 }
 
 cudaError_t launch_small(const SmallArgs &a, bool ext, cudaStream_t st)
@@ -241,7 +367,8 @@ cudaError_t launch_small(const SmallArgs &a, bool ext, cudaStream_t st)
     const long long ntiles = (a.ni + kSmallBi - 1) / kSmallBi;
     const long long grid = ntiles * a.nchunk;
     if (grid <= 0) return cudaSuccess;
-    if (a.jchunk < 1 || a.jchunk > kSmallMaxChunk || grid >= (1LL << 31)) return cudaErrorInvalidValue;
+    if (a.jchunk < 1 || a.jchunk > kSmallMaxChunk || grid >= (1LL << 31) || a.nchunk % kSmallCluster != 0)
+        return cudaErrorInvalidValue;
     const size_t smem = small_smem(a.jchunk);
     return ext ? launch_small_one<true>(a, (int)grid, smem, st) : launch_small_one<false>(a, (int)grid, smem, st);
 }
