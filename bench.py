@@ -608,6 +608,8 @@ def extra_rows(pg, torch, dev, peak_newton, headline_rate):
                                 "call_ms_graph": call,
                                 "ratio_to_allpairs": rate / headline_rate,
                                 "tuned_shape": {"i_per_thread": info["i_per_thread"],
+                                                "j_tile": info.get("j_tile"),
+                                                "block_threads": info.get("block_threads"),
                                                 "grid": info["grid"]}}
     return rows
 

@@ -350,10 +350,11 @@ int pg_set_graph(pg_ctx *ctx, int on);
  * fastest in the context. Candidates: i per thread 2*np (np 1, 2, 4) on every
  * path; with it, on the tiled all-pairs path packed or scalar pair
  * arithmetic and CTAs per SM (the occupancy limit and one below); on the
- * batched kernel (groups, tree lists, cell list) CTAs per SM; on the narrow
- * path the split of the j records into 1, 2 or 4 items per warp of the
- * launch. Threads per CTA and j-tile depths are compile-time constants.
- * Synchronises. */
+ * batched kernel (groups, tree lists, cell list) CTAs per SM, and for the
+ * caller's Newton groups (eps > 0, no per-i softening) also the kernel's
+ * j-tile depth and threads per CTA (the shapes of pg_set_groups_tile); on
+ * the narrow path the split of the j records into 1, 2 or 4 items per warp
+ * of the launch. Synchronises. */
 int pg_tune(pg_ctx *ctx);
 
 /* Pair differences of the all-pairs paths (tiled and narrow). Positions are
@@ -373,6 +374,15 @@ int pg_tune(pg_ctx *ctx);
  * what the last run used. Groups, tree lists and the cell list keep their
  * own forms. PG_EINVAL for another mode. */
 int pg_set_differencing(pg_ctx *ctx, int mode);
+
+/* The batched kernel's j-tile depth (j records staged in shared memory per
+ * step) and threads per CTA for the caller's Newton groups (pg_set_groups;
+ * eps > 0, no per-i softening): (512, 128) (the default, and the only shape
+ * of every other batched run), (256, 128), (1024, 256) or (512, 256); (0, 0)
+ * returns to the default. The group lists are cut into work items of at most
+ * 2 np x threads i-particles. pg_info's out[8], out[9] report the shape of the
+ * last batched launch. PG_EINVAL for a shape that is not compiled. */
+int pg_set_groups_tile(pg_ctx *ctx, int tj, int nt);
 
 /* Narrow all-pairs path: cut the j records into about items_per_warp work
  * items per warp of the launch (1 to 8; 0 = the default, one). pg_info's
@@ -414,8 +424,10 @@ int pg_kernel_time(pg_ctx *ctx, double *ms);
  * is packed FP32x2, out[6] items per warp of a narrow run (0 for other paths),
  * out[7] 1 if the pair differences were formed in double-float (FP32 offset
  * plus its FP32 residual: the narrow path, and tiled runs whose i-tiles are
- * not compact), 0 if from one FP32 offset per particle.
- * Returns how many were written (at most 8). */
+ * not compact), 0 if from one FP32 offset per particle, out[8] and out[9]
+ * the j-tile depth and threads per CTA of the batched kernel (0 when the run
+ * did not use it).
+ * Returns how many were written (at most 10). */
 int pg_info(pg_ctx *ctx, long long *out, int n);
 
 /* Measured ceilings on the current device for the roofline (a tool of this

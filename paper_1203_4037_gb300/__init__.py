@@ -70,6 +70,7 @@ SIGNATURES = {
     "pg_set_shape": (_I, [_P, _I, _I, _I]),
     "pg_set_split": (_I, [_P, _I]),
     "pg_set_differencing": (_I, [_P, _I]),
+    "pg_set_groups_tile": (_I, [_P, _I, _I]),
     "pg_selftest_wait": (_I, [_P, _D]),
     "pg_set_allpairs_path": (_I, [_P, _I]),
     "pg_set_eps_i": (_I, [_P, _P, _LL]),
@@ -395,10 +396,15 @@ def pg_set_differencing(ctx, mode):
     return _check(ctx, lib().pg_set_differencing(ctx, int(mode)))
 
 
+def pg_set_groups_tile(ctx, tj, nt):
+    return _check(ctx, lib().pg_set_groups_tile(ctx, int(tj), int(nt)))
+
+
 def pg_info(ctx):
-    out = (_LL * 8)()
-    n = lib().pg_info(ctx, out, 8)
-    keys = ["pairs", "launches", "i_per_thread", "grid", "slots", "packed", "split", "df"]
+    out = (_LL * 10)()
+    n = lib().pg_info(ctx, out, 10)
+    keys = ["pairs", "launches", "i_per_thread", "grid", "slots", "packed", "split", "df",
+            "j_tile", "block_threads"]
     return dict(zip(keys[:n], list(out)[:n]))
 
 
@@ -606,6 +612,9 @@ class Context:
 
     def set_differencing(self, mode):
         pg_set_differencing(self.h, mode)
+
+    def set_groups_tile(self, tj, nt):
+        pg_set_groups_tile(self.h, tj, nt)
 
     def selftest_wait(self, limit_ms):
         pg_selftest_wait(self.h, limit_ms)

@@ -113,7 +113,9 @@ struct pg_ctx {
     DevBuf g_ioff, g_joff, g_jlist, g_items, g_ctr, g_queue, g_jhl, g_ihl;
     int g_nitems = 0;
     int g_warp_from = 0;
-    int g_items_np = 0;
+    int g_items_np = 0, g_items_nt = 0;   // the shape the stored items were cut for
+    int g_tj = 0, g_nt = 0;       // batched kernel's j-tile depth and threads per CTA (0: default)
+    int last_tj = 0, last_nt = 0; // those of the last batched launch
     long long g_pairs = 0;
     long long g_maxj = -1;       // largest j index listed
 
@@ -990,6 +992,22 @@ int pg_set_shape(pg_ctx *c, int np, int ctas_per_sm, int packed)
     return PG_OK;
 }
 
+int pg_set_groups_tile(pg_ctx *c, int tj, int nt)
+{
+    if (!c) return PG_EINVAL;
+    if (tj == 0 && nt == 0) {
+        if (c->g_tj || c->g_nt) drop_graph(c);
+        c->g_tj = c->g_nt = 0;
+        return PG_OK;
+    }
+    if (!groups_tile_ok(tj, nt, true))
+        return fail(c, PG_EINVAL, "no batched kernel of that j-tile depth and block size is compiled");
+    if (tj != c->g_tj || nt != c->g_nt) drop_graph(c);
+    c->g_tj = tj;
+    c->g_nt = nt;
+    return PG_OK;
+}
+
 int pg_set_differencing(pg_ctx *c, int mode)
 {
     if (!c) return PG_EINVAL;
@@ -1020,10 +1038,10 @@ int pg_info(pg_ctx *c, long long *out, int n)
         c->last_pairs = (long long)v;
         c->pairs_on_device = false;
     }
-    long long v[8] = {c->last_pairs, c->last_launches, 2LL * c->last_np, c->last_grid,
-                      c->last_slots, c->last_df ? 1LL : (long long)c->packed, c->last_split,
-                      (long long)c->last_df};
-    int k = std::min(n, 8);
+    long long v[10] = {c->last_pairs, c->last_launches, 2LL * c->last_np, c->last_grid,
+                       c->last_slots, c->last_df ? 1LL : (long long)c->packed, c->last_split,
+                       (long long)c->last_df, c->last_tj, c->last_nt};
+    int k = std::min(n, 10);
     for (int i = 0; i < k; ++i) out[i] = v[i];
     return k;
 }
@@ -1378,9 +1396,15 @@ int check_run_state(pg_ctx *c)
 // measured 1.29 against 1.42 ms on 2^20 Plummer, monopoles) and the cells
 int groups_np(const pg_ctx *c) { return c->np ? c->np : (c->have_groups ? 4 : 2); }
 
+// the caller's plain Newton lists (no per-i softening, eps > 0) can run any
+// compiled tile shape of the batched kernel; everything else the default
+bool groups_plain(const pg_ctx *c) { return c->mode == PG_NEWTON && !use_ext(c); }
+int groups_tj(const pg_ctx *c) { return c->g_tj && groups_plain(c) ? c->g_tj : kGroupsTJ; }
+int groups_nt(const pg_ctx *c) { return c->g_nt && groups_plain(c) ? c->g_nt : kGroupsNT; }
+
 int upload_group_items(pg_ctx *c)
 {
-    int Bi = groups_bi(groups_np(c));
+    int Bi = groups_bi(groups_np(c), groups_nt(c));
     std::vector<GroupItem> items;
     std::vector<long long> cost;
     for (long long g = 0; g < c->ngroups; ++g) {
@@ -1417,6 +1441,7 @@ int upload_group_items(pg_ctx *c)
                               cudaMemcpyHostToDevice));
     c->g_nitems = (int)sorted.size();
     c->g_items_np = groups_np(c);
+    c->g_items_nt = groups_nt(c);
     return PG_OK;
 }
 
@@ -1431,15 +1456,19 @@ GroupArgs group_args(pg_ctx *c)
     return g;
 }
 
-// df: double-float differencing (the narrow path's items)
-int launch_group_kernel(pg_ctx *c, const GroupArgs &g, bool cell, bool df = false)
+// df: double-float differencing (the narrow path's items); tj, nt: the
+// kernel's j-tile depth and threads per CTA (the caller's plain lists only)
+int launch_group_kernel(pg_ctx *c, const GroupArgs &g, bool cell, bool df = false, int tj = kGroupsTJ,
+                        int nt = kGroupsNT)
 {
     bool table = c->mode == PG_TABLE;
     int np = groups_np(c);
     c->last_np = np;
     c->last_df = df;
+    c->last_tj = tj;
+    c->last_nt = nt;
     const bool ext = use_ext(c);
-    int occ = groups_max_blocks_per_sm(np, table, tab_units(c), cell, ext, df);
+    int occ = groups_max_blocks_per_sm(np, table, tab_units(c), cell, ext, df, tj, nt);
     int per = c->ctas_per_sm > 0 ? std::min(c->ctas_per_sm, occ) : occ;
     int grid = c->sms * per;
     // cell lists: the warp-mode items (the small cells) in a second launch
@@ -1449,8 +1478,8 @@ int launch_group_kernel(pg_ctx *c, const GroupArgs &g, bool cell, bool df = fals
     if (wper > 0) gg.queue_w = (int *)c->g_queue.p + 1;
     PG_CUDA(c, cudaMemsetAsync(c->g_queue.p, 0, 2 * sizeof(int), c->stream));
     if (c->timing) PG_CUDA(c, record_timing(c, c->tk0));
-    PG_CUDA(c, launch_groups(gg, grid, np, table, cell, ext, df, groups_smem(np, table, tab_units(c), df),
-                             c->stream));
+    PG_CUDA(c, launch_groups(gg, grid, np, table, cell, ext, df, tj, nt,
+                             groups_smem(np, table, tab_units(c), df, tj, nt), c->stream));
     if (wper > 0)
         PG_CUDA(c, launch_groups_warp(gg, c->sms * wper, true, true, ext, tab_units(c), true, false,
                                       c->stream));
@@ -1839,7 +1868,8 @@ int enqueue_tree(pg_ctx *c, double *acc, double *pot)
 int enqueue_groups(pg_ctx *c, double *acc, double *pot)
 {
     int rc;
-    if (c->g_items_np != groups_np(c) && (rc = upload_group_items(c))) return rc;
+    if ((c->g_items_np != groups_np(c) || c->g_items_nt != groups_nt(c)) && (rc = upload_group_items(c)))
+        return rc;
     if ((rc = ensure(c, c->g_ctr, (size_t)std::max<long long>(c->ngroups, 1) * sizeof(double4))) ||
         (rc = ensure(c, c->g_queue, 16)))
         return rc;
@@ -1873,7 +1903,7 @@ int enqueue_groups(pg_ctx *c, double *acc, double *pot)
     g.perm = nullptr;
     g.acc = acc;
     g.pot = pot;
-    if ((rc = launch_group_kernel(c, g, false))) return rc;
+    if ((rc = launch_group_kernel(c, g, false, false, groups_tj(c), groups_nt(c)))) return rc;
     c->last_pairs = c->g_pairs;
     return PG_OK;
 }
@@ -1960,6 +1990,7 @@ int enqueue_run(pg_ctx *c, double *acc, double *pot)
 {
     c->last_launches = 0;
     c->last_split = 0;
+    c->last_tj = c->last_nt = 0;
     // per-i softening lives in the i records' w (read by every path); a
     // captured graph writes it on every replay, as the records may be new
     if (c->have_epsi && (c->capturing || !c->epsi_applied)) {
@@ -2279,16 +2310,21 @@ int pg_tune(pg_ctx *c)
     PG_CUDA(c, cudaEventCreate(&e0));
     PG_CUDA(c, cudaEventCreate(&e1));
     int best_np = c->np, best_cta = c->ctas_per_sm, best_pk = c->packed, best_split = c->split;
+    int best_tj = c->g_tj, best_nt = c->g_nt;
     float best = 1e30f;
     const bool groups_path = c->have_groups || c->box > 0.0 || c->tree_on;
     const bool narrow = !groups_path && use_narrow(c);
     const bool table = c->mode == PG_TABLE;
+    // the caller's plain Newton lists also try every compiled tile shape
+    const bool tiles = c->have_groups && !c->tree_on && groups_plain(c);
     auto chk = [&](cudaError_t e, const char *where) { return e == cudaSuccess ? PG_OK : cuda_fail(c, e, where); };
-    auto trial = [&](int np, int pk, int cta, int split) {
+    auto trial = [&](int np, int pk, int cta, int split, int tj, int nt) {
         c->np = np;
         c->packed = pk;
         c->ctas_per_sm = cta;
         c->split = split;
+        c->g_tj = tj;
+        c->g_nt = nt;
         c->i_dirty = true;
         if ((rc = run_into(c, (double *)c->acc.p, (double *)c->pot.p))) return;
         if ((rc = chk(cudaEventRecord(e0, c->stream), "cudaEventRecord"))) return;
@@ -2304,23 +2340,30 @@ int pg_tune(pg_ctx *c)
             best_cta = cta;
             best_pk = pk;
             best_split = split;
+            best_tj = tj;
+            best_nt = nt;
         }
     };
     const int nps[3] = {1, 2, 4};
+    const int shapes[4][2] = {{kGroupsTJ, kGroupsNT}, {256, 128}, {1024, 256}, {512, 256}};
     for (int np : nps) {
         if (rc) break;
         if (narrow) {
-            for (int split = 1; split <= 4 && !rc; split *= 2) trial(np, c->packed, 0, split);
+            for (int split = 1; split <= 4 && !rc; split *= 2) trial(np, c->packed, 0, split, c->g_tj, c->g_nt);
             continue;
         }
         // the double-float tiled variant is packed only
         const bool df = !groups_path && tiled_df(c, c->ni, nj_of(c));
-        for (int pk = groups_path || df ? 1 : 0; pk <= 1 && !rc; ++pk) {
-            const int occ = groups_path
-                                ? groups_max_blocks_per_sm(np, table, tab_units(c), c->box > 0.0 && !c->have_groups,
-                                                           use_ext(c), false)
-                                : allpairs_max_blocks_per_sm(np, table, tab_units(c), pk != 0, use_ext(c), df);
-            for (int cta = std::max(1, occ - 1); cta <= occ && !rc; ++cta) trial(np, pk, cta, c->split);
+        for (int sh = 0; sh < (tiles ? 4 : 1) && !rc; ++sh) {
+            const int tj = tiles ? shapes[sh][0] : c->g_tj, nt = tiles ? shapes[sh][1] : c->g_nt;
+            for (int pk = groups_path || df ? 1 : 0; pk <= 1 && !rc; ++pk) {
+                const int occ = groups_path
+                                    ? groups_max_blocks_per_sm(np, table, tab_units(c), c->box > 0.0 && !c->have_groups,
+                                                               use_ext(c), false, tj ? tj : kGroupsTJ,
+                                                               nt ? nt : kGroupsNT)
+                                    : allpairs_max_blocks_per_sm(np, table, tab_units(c), pk != 0, use_ext(c), df);
+                for (int cta = std::max(1, occ - 1); cta <= occ && !rc; ++cta) trial(np, pk, cta, c->split, tj, nt);
+            }
         }
     }
     cudaEventDestroy(e0);
@@ -2329,6 +2372,8 @@ int pg_tune(pg_ctx *c)
     c->ctas_per_sm = best_cta;
     c->packed = best_pk;
     c->split = best_split;
+    c->g_tj = best_tj;
+    c->g_nt = best_nt;
     c->i_dirty = true;
     c->use_graph = graph;
     drop_graph(c);

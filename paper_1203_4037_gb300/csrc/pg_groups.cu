@@ -13,6 +13,8 @@
 // and run one per warp instead of one per CTA: inside the same launch for the
 // caller's groups, in a second kernel (k_groups_warp) for the cell list and
 // the narrow all-pairs path.
+#include <algorithm>
+
 #include "pg_device.cuh"
 
 namespace pg {
@@ -22,7 +24,6 @@ constexpr int kTJG = 512;          // j entries staged per step
 // unroll depth of a CTA-mode item's j loop (measured on GB300: 8 for the
 // table lookups, whose latency wants more terms in flight; 2 for Newton)
 template <bool TABLE> struct GroupsUnrollJ { static constexpr int value = TABLE ? 8 : 2; };
-constexpr int kPerThread = kTJG / kNT;
 
 // Records come in two forms.
 //  CELL = false: any particle as a double-float pair, hi = (x, y, z, m) in
@@ -84,13 +85,14 @@ struct ItemShape {
     int nsets, L, spw;
 };
 
+template <int NT = kNT>
 __device__ __forceinline__ ItemShape item_shape(int ni, int np)
 {
     ItemShape s;
     s.nsets = (ni + 2 * np - 1) / (2 * np);
-    int L = div_small(kNT, s.nsets > 0 ? s.nsets : 1);
+    int L = div_small(NT, s.nsets > 0 ? s.nsets : 1);
     L = L > 32 ? 32 : L < 1 ? 1 : L;
-    while (L > 1 && (kNT / 32) * div_small(32, L) < s.nsets) --L;
+    while (L > 1 && (NT / 32) * div_small(32, L) < s.nsets) --L;
     s.L = L;
     s.spw = div_small(32, L);
     return s;
@@ -213,11 +215,13 @@ __device__ __forceinline__ void pair_term(float ra, float rb, u64 dx, u64 dy, u6
     }
 }
 
-template <int NP, bool TABLE, bool CELL, bool EXT, bool HL = false, bool DF = false>
+template <int NP, bool TABLE, bool CELL, bool EXT, bool HL = false, bool DF = false, int TJ = kTJG,
+          int NT = kNT>
 __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &it, const ItemShape sh,
                                            u64 *cvt, u64 *run, int *cr, const float2 *tab,
                                            const float4 *dirt, int tid)
 {
+    constexpr int kPT = TJ / NT;       // j records each thread stages per tile
     static_assert(!(DF && CELL), "double-float differencing is for particle records");
     long long jb = 0, je = 0;
     if (CELL) {
@@ -245,8 +249,8 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
     const int sh3 = a.tab.shift - (EXT ? 4 : 3);
     const unsigned tb0 = smem_u32(tab) - (a.tab.base << (EXT ? 4 : 3));
     const unsigned smax_bits = __float_as_uint(a.tab.s_max);
-    auto RH = [&](int p, int k) -> u64 & { return run[(8 * p + k) * kNT + tid]; };
-    auto RL = [&](int p, int k) -> u64 & { return run[(8 * p + 4 + k) * kNT + tid]; };
+    auto RH = [&](int p, int k) -> u64 & { return run[(8 * p + k) * NT + tid]; };
+    auto RL = [&](int p, int k) -> u64 & { return run[(8 * p + 4 + k) * NT + tid]; };
 
     const int L = sh.L;
     const int wl = tid & 31;
@@ -298,13 +302,13 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
     }
 
     // register prefetch of one tile of records
-    float4 rc32[kPerThread];
-    float4 rlo[CELL ? 1 : kPerThread];
-    int code[CELL ? kPerThread : 1];
+    float4 rc32[kPT];
+    float4 rlo[CELL ? 1 : kPT];
+    int code[CELL ? kPT : 1];
     auto fetch = [&](long long t0) {
 #pragma unroll
-        for (int r = 0; r < kPerThread; ++r) {
-            long long e = t0 + r * kNT + tid;
+        for (int r = 0; r < kPT; ++r) {
+            long long e = t0 + r * NT + tid;
             bool ok = e < je;
             long long j;
             if (CELL) {
@@ -326,11 +330,11 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
         }
     };
     fetch(jb);
-    for (long long t0 = jb; t0 < je; t0 += kTJG) {
+    for (long long t0 = jb; t0 < je; t0 += TJ) {
         // publish the prefetched tile as FP32 offsets in the i frame
 #pragma unroll
-        for (int r = 0; r < kPerThread; ++r) {
-            const int e = r * kNT + tid;
+        for (int r = 0; r < kPT; ++r) {
+            const int e = r * NT + tid;
             float x, y, z, m, lx = 0.0f, ly = 0.0f, lz = 0.0f;
             const bool real = rc32[r].w >= 0.0f;
             if (real && DF) {
@@ -356,19 +360,19 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
             // consecutive j then read consecutive 16-byte words
             cvt[2 * e + 0] = pk2(x, x);
             cvt[2 * e + 1] = pk2(y, y);
-            cvt[2 * kTJG + 2 * e + 0] = pk2(z, z);
-            cvt[2 * kTJG + 2 * e + 1] = pk2(m, m);
+            cvt[2 * TJ + 2 * e + 0] = pk2(z, z);
+            cvt[2 * TJ + 2 * e + 1] = pk2(m, m);
             if (DF) {
-                cvt[4 * kTJG + 2 * e + 0] = pk2(lx, lx);
-                cvt[4 * kTJG + 2 * e + 1] = pk2(ly, ly);
-                cvt[6 * kTJG + 2 * e + 0] = pk2(lz, lz);
-                cvt[6 * kTJG + 2 * e + 1] = 0ull;
+                cvt[4 * TJ + 2 * e + 0] = pk2(lx, lx);
+                cvt[4 * TJ + 2 * e + 1] = pk2(ly, ly);
+                cvt[6 * TJ + 2 * e + 0] = pk2(lz, lz);
+                cvt[6 * TJ + 2 * e + 1] = 0ull;
             }
         }
         __syncthreads();
-        if (t0 + kTJG < je) fetch(t0 + kTJG);   // loads in flight during the compute
+        if (t0 + TJ < je) fetch(t0 + TJ);   // loads in flight during the compute
         long long nv = je - t0;
-        if (nv > kTJG) nv = kTJG;
+        if (nv > TJ) nv = TJ;
         if (active) {
 #pragma unroll
             for (int p = 0; p < NP; ++p) ax[p] = ay[p] = az[p] = ph[p] = 0ull;
@@ -376,11 +380,11 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
 #pragma unroll(GroupsUnrollJ<TABLE>::value)
             for (int e = lane; e < nv_lane; e += L) {
                 const ulonglong2 xy = reinterpret_cast<const ulonglong2 *>(cvt)[e];
-                const ulonglong2 zm = reinterpret_cast<const ulonglong2 *>(cvt)[kTJG + e];
+                const ulonglong2 zm = reinterpret_cast<const ulonglong2 *>(cvt)[TJ + e];
                 ulonglong2 lxy = make_ulonglong2(0ull, 0ull), lz0 = lxy;
                 if (DF) {
-                    lxy = reinterpret_cast<const ulonglong2 *>(cvt)[2 * kTJG + e];
-                    lz0 = reinterpret_cast<const ulonglong2 *>(cvt)[3 * kTJG + e];
+                    lxy = reinterpret_cast<const ulonglong2 *>(cvt)[2 * TJ + e];
+                    lz0 = reinterpret_cast<const ulonglong2 *>(cvt)[3 * TJ + e];
                 }
 #pragma unroll
                 for (int p = 0; p < NP; ++p) {
@@ -495,9 +499,9 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
 // i-particles and its first j tile are all in flight while the current
 // item's last tile is evaluated.
 constexpr int kWarpTJ = 128;        // j entries per warp-staged tile
-// in the CTA-mode kernel the warps' staging slices (4 kWarpTJ words each)
-// are carved from the CTA staging buffer (4 kTJG words)
-static_assert(kTJG * 4 >= (kNT / 32) * 4 * kWarpTJ, "warp-mode slices must fit the CTA staging buffer");
+// in the CTA-mode kernel the warps' staging slices (kW kWarpTJ words each)
+// share the CTA staging buffer's space (kW TJ words), which is sized for
+// the larger of the two
 constexpr int kWarpItemNi = 32;     // items up to this size (i-particles)
 constexpr long long kWarpItemPairs = 32768;   // and this many pairs go to warp mode
 
@@ -837,25 +841,36 @@ __device__ __forceinline__ void warp_loop(const GroupArgs &a, int nitems, int cu
 // the lo parts {lx, ly} and {lz, 0}
 template <bool DF> struct GroupWords { static constexpr int value = DF ? 8 : 4; };
 
-template <int NPMAX, bool TABLE, bool CELL, bool EXT, bool HL = false, bool DF = false>
-__global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
+// the staging area of a CTA: the CTA-mode tile or, after it, the warps'
+// warp-mode slices, whichever is larger (u64 words)
+template <bool DF, int TJ, int NT>
+struct StageWords {
+    static constexpr int kW = GroupWords<DF>::value;
+    static constexpr int a = kW * TJ, b = (NT / 32) * kW * kWarpTJ;
+    static constexpr int value = a > b ? a : b;
+};
+
+template <int NPMAX, bool TABLE, bool CELL, bool EXT, bool HL = false, bool DF = false, int TJ = kTJG,
+          int NT = kNT>
+__global__ void __launch_bounds__(NT) k_groups(GroupArgs a)
 {
     constexpr int kW = GroupWords<DF>::value;
+    static_assert(TJ % NT == 0 && NT % 32 == 0, "j tile and block size");
     extern __shared__ __align__(128) unsigned char smem[];
-    u64 *cvt = reinterpret_cast<u64 *>(smem);                            // [kW][kTJG]
-    u64 *run = cvt + kW * kTJG;                                          // [8 NPMAX][kNT]
-    float4 *dirt = reinterpret_cast<float4 *>(run + 8 * NPMAX * kNT);    // [27] cell mode
+    u64 *cvt = reinterpret_cast<u64 *>(smem);                            // [kW][TJ], or warp slices
+    u64 *run = cvt + StageWords<DF, TJ, NT>::value;                      // [8 NPMAX][NT]
+    float4 *dirt = reinterpret_cast<float4 *>(run + 8 * NPMAX * NT);     // [27] cell mode
     int *sh = reinterpret_cast<int *>(dirt + 28);                        // item slot
-    int *cr = sh + 4;                                                    // [4][2][kCellTab] cell mode
-    float2 *tab = reinterpret_cast<float2 *>(cr + 8 * kCellTab);
+    int *cr = sh + 4;                                                    // [warps][2][kCellTab] cell mode
+    float2 *tab = reinterpret_cast<float2 *>(cr + (NT / 32) * 2 * kCellTab);
 
     const int tid = threadIdx.x;
     // a cell-list launch lets its warp-mode kernel start as CTAs drain
     if (CELL) asm volatile("griddepcontrol.launch_dependents;");
     if (TABLE && !EXT)
-        for (int k = tid; k < a.tab.n; k += kNT) tab[k] = a.tab.AG1[k];
+        for (int k = tid; k < a.tab.n; k += NT) tab[k] = a.tab.AG1[k];
     if (TABLE && EXT)
-        for (int k = tid; k < a.tab.n; k += kNT) reinterpret_cast<float4 *>(tab)[k] = a.tab.AGP[k];
+        for (int k = tid; k < a.tab.n; k += NT) reinterpret_cast<float4 *>(tab)[k] = a.tab.AGP[k];
     if (CELL && tid < 27)
         dirt[tid] = make_float4((float)(tid / 9 - 1) * a.cell_h, (float)((tid / 3) % 3 - 1) * a.cell_h,
                                 (float)(tid % 3 - 1) * a.cell_h, 0.0f);
@@ -887,16 +902,16 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
             break;
         }
         const GroupItem it = item_at(a, item);
-        if (NPMAX > 1 && it.ni <= kNT * NPMAX) {
-            const ItemShape big = item_shape(it.ni, NPMAX);
-            const ItemShape small = item_shape(it.ni, NPMAX / 2);
+        if (NPMAX > 1 && it.ni <= NT * NPMAX) {
+            const ItemShape big = item_shape<NT>(it.ni, NPMAX);
+            const ItemShape small = item_shape<NT>(it.ni, NPMAX / 2);
             if (small.nsets <= 4 * small.spw && small.nsets * small.L > big.nsets * big.L) {
-                group_item<(NPMAX > 1 ? NPMAX / 2 : 1), TABLE, CELL, EXT, HL, DF>(a, it, small, cvt, run,
+                group_item<(NPMAX > 1 ? NPMAX / 2 : 1), TABLE, CELL, EXT, HL, DF, TJ, NT>(a, it, small, cvt, run,
                                                                                  cr, tab, dirt, tid);
                 continue;
             }
         }
-        group_item<NPMAX, TABLE, CELL, EXT, HL, DF>(a, it, item_shape(it.ni, NPMAX), cvt, run, cr, tab,
+        group_item<NPMAX, TABLE, CELL, EXT, HL, DF, TJ, NT>(a, it, item_shape<NT>(it.ni, NPMAX), cvt, run, cr, tab,
                                                   dirt, tid);
     }
 
@@ -907,7 +922,7 @@ __global__ void __launch_bounds__(kNT) k_groups(GroupArgs a)
     warp_loop<TABLE, CELL, EXT, HL, DF>(a, nitems, w == 0 ? first_small : -1,
                                       (w == 0 && lane32 == 0) ? next : -1,
                                       cvt + w * (kW * kWarpTJ), cr + w * 2 * kCellTab, tab, dirt,
-                                      lane32, a.queue, 0, (int)gridDim.x * (kNT / 32));
+                                      lane32, a.queue, 0, (int)gridDim.x * (NT / 32));
 }
 
 // The warp-mode items alone, in a launch of their own: the cell list's small
@@ -955,41 +970,64 @@ __global__ void __launch_bounds__(kWNT, kWMinBlocks) k_groups_warp(GroupArgs a)
 }
 
 // ------------------------------------------------------------------ host
-size_t groups_smem(int np, bool table, int ntab, bool df)
+size_t groups_smem(int np, bool table, int ntab, bool df, int tj, int nt)
 {
-    size_t s = (size_t)kTJG * (df ? 8 : 4) * sizeof(u64) + 8 * np * kNT * sizeof(u64) + 28 * 16 + 16 +
-               8 * kCellTab * sizeof(int);
+    const size_t kw = df ? 8 : 4;
+    const size_t stage = std::max<size_t>((size_t)tj * kw, (size_t)(nt / 32) * kw * kWarpTJ);
+    size_t s = stage * sizeof(u64) + 8 * (size_t)np * nt * sizeof(u64) + 28 * 16 + 16 +
+               (size_t)(nt / 32) * 2 * kCellTab * sizeof(int);
     if (table) s += (size_t)ntab * sizeof(float2);
     return s;
 }
 
-int groups_bi(int np) { return kNT * 2 * np; }
+int groups_bi(int np, int nt) { return nt * 2 * np; }
 
-template <int NP, bool TABLE, bool CELL, bool EXT, bool HL = false, bool DF = false>
+// the compiled (j-tile depth, threads per CTA) shapes of the batched kernel:
+// every path has the first; the plain Newton lists (no table, cells, per-i
+// softening or double-float records) also the others, for the autotuner
+bool groups_tile_ok(int tj, int nt, bool plain)
+{
+    if (tj == kTJG && nt == kNT) return true;
+    if (!plain) return false;
+    return (tj == 256 && nt == 128) || (tj == 1024 && nt == 256) || (tj == 512 && nt == 256);
+}
+
+template <int NP, bool TABLE, bool CELL, bool EXT, bool HL = false, bool DF = false, int TJ = kTJG,
+          int NT = kNT>
 static cudaError_t configure_g()
 {
     static bool done[kMaxDevices] = {};
     return once_per_device(done, [] {
-        return cudaFuncSetAttribute(k_groups<NP, TABLE, CELL, EXT, HL, DF>,
+        return cudaFuncSetAttribute(k_groups<NP, TABLE, CELL, EXT, HL, DF, TJ, NT>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)groups_smem(NP, TABLE, 2 << 13, DF));
+                                    (int)groups_smem(NP, TABLE, 2 << 13, DF, TJ, NT));
     });
 }
 
-template <int NP, bool TABLE, bool CELL, bool EXT, bool DF = false>
+template <int NP, bool TABLE, bool CELL, bool EXT, bool DF = false, int TJ = kTJG, int NT = kNT>
 static int occ_g(size_t smem)
 {
-    if (configure_g<NP, TABLE, CELL, EXT, false, DF>() != cudaSuccess) return 1;
+    if (configure_g<NP, TABLE, CELL, EXT, false, DF, TJ, NT>() != cudaSuccess) return 1;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_groups<NP, TABLE, CELL, EXT, false, DF>, kNT,
-                                                      smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_groups<NP, TABLE, CELL, EXT, false, DF, TJ, NT>,
+                                                      NT, smem) != cudaSuccess)
         return 1;
     return nb > 0 ? nb : 1;
 }
 
 template <int NP>
-static int occ_np(bool table, bool cell, bool ext, bool df, size_t smem)
+static int occ_plain(int tj, int nt, size_t smem)
 {
+    if (tj == 256 && nt == 128) return occ_g<NP, false, false, false, false, 256, 128>(smem);
+    if (tj == 1024 && nt == 256) return occ_g<NP, false, false, false, false, 1024, 256>(smem);
+    if (tj == 512 && nt == 256) return occ_g<NP, false, false, false, false, 512, 256>(smem);
+    return occ_g<NP, false, false, false>(smem);
+}
+
+template <int NP>
+static int occ_np(bool table, bool cell, bool ext, bool df, int tj, int nt, size_t smem)
+{
+    if (!table && !cell && !ext && !df) return occ_plain<NP>(tj, nt, smem);
     if (df && !cell) {
         if (!table) return ext ? occ_g<NP, false, false, true, true>(smem) : occ_g<NP, false, false, false, true>(smem);
         return ext ? occ_g<NP, true, false, true, true>(smem) : occ_g<NP, true, false, false, true>(smem);
@@ -999,31 +1037,38 @@ static int occ_np(bool table, bool cell, bool ext, bool df, size_t smem)
     return ext ? occ_g<NP, true, false, true>(smem) : occ_g<NP, true, false, false>(smem);
 }
 
-int groups_max_blocks_per_sm(int np, bool table, int ntab, bool cell, bool ext, bool df)
+int groups_max_blocks_per_sm(int np, bool table, int ntab, bool cell, bool ext, bool df, int tj, int nt)
 {
-    size_t smem = groups_smem(np, table, ntab, df && !cell);
-    return np == 1 ? occ_np<1>(table, cell, ext, df, smem)
-         : np == 4 ? occ_np<4>(table, cell, ext, df, smem)
-                   : occ_np<2>(table, cell, ext, df, smem);
+    size_t smem = groups_smem(np, table, ntab, df && !cell, tj, nt);
+    return np == 1 ? occ_np<1>(table, cell, ext, df, tj, nt, smem)
+         : np == 4 ? occ_np<4>(table, cell, ext, df, tj, nt, smem)
+                   : occ_np<2>(table, cell, ext, df, tj, nt, smem);
 }
 
-template <int NP, bool TABLE, bool CELL, bool EXT, bool HL = false, bool DF = false>
+template <int NP, bool TABLE, bool CELL, bool EXT, bool HL = false, bool DF = false, int TJ = kTJG,
+          int NT = kNT>
 static cudaError_t launch_g(const GroupArgs &g, int grid, size_t smem, cudaStream_t st)
 {
-    cudaError_t e = configure_g<NP, TABLE, CELL, EXT, HL, DF>();
+    cudaError_t e = configure_g<NP, TABLE, CELL, EXT, HL, DF, TJ, NT>();
     if (e != cudaSuccess) return e;
-    k_groups<NP, TABLE, CELL, EXT, HL, DF><<<grid, kNT, smem, st>>>(g);
+    k_groups<NP, TABLE, CELL, EXT, HL, DF, TJ, NT><<<grid, NT, smem, st>>>(g);
     return cudaGetLastError();
 }
 
 template <int NP>
 static cudaError_t launch_gnp(const GroupArgs &g, int grid, bool table, bool cell, bool ext, bool df,
-                              size_t smem, cudaStream_t st)
+                              int tj, int nt, size_t smem, cudaStream_t st)
 {
     if (g.hl) {   // FP32 outputs: Newton lists only
         if (table || cell || df) return cudaErrorInvalidValue;
         return ext ? launch_g<NP, false, false, true, true>(g, grid, smem, st)
                    : launch_g<NP, false, false, false, true>(g, grid, smem, st);
+    }
+    if (!table && !cell && !ext && !df) {   // the plain Newton lists: every compiled tile shape
+        if (tj == 256 && nt == 128) return launch_g<NP, false, false, false, false, false, 256, 128>(g, grid, smem, st);
+        if (tj == 1024 && nt == 256) return launch_g<NP, false, false, false, false, false, 1024, 256>(g, grid, smem, st);
+        if (tj == 512 && nt == 256) return launch_g<NP, false, false, false, false, false, 512, 256>(g, grid, smem, st);
+        return launch_g<NP, false, false, false>(g, grid, smem, st);
     }
     if (df) {     // double-float differencing: particle records (no cells)
         if (cell) return cudaErrorInvalidValue;
@@ -1032,8 +1077,7 @@ static cudaError_t launch_gnp(const GroupArgs &g, int grid, bool table, bool cel
         return ext ? launch_g<NP, true, false, true, false, true>(g, grid, smem, st)
                    : launch_g<NP, true, false, false, false, true>(g, grid, smem, st);
     }
-    if (!table) return ext ? launch_g<NP, false, false, true>(g, grid, smem, st)
-                           : launch_g<NP, false, false, false>(g, grid, smem, st);
+    if (!table) return launch_g<NP, false, false, true>(g, grid, smem, st);
     if (cell) return ext ? launch_g<NP, true, true, true>(g, grid, smem, st)
                          : launch_g<NP, true, true, false>(g, grid, smem, st);
     return ext ? launch_g<NP, true, false, true>(g, grid, smem, st)
@@ -1138,13 +1182,14 @@ cudaError_t launch_groups_warp(const GroupArgs &g, int grid, bool table, bool ce
 }
 
 cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, bool cell, bool ext, bool df,
-                          size_t smem, cudaStream_t st)
+                          int tj, int nt, size_t smem, cudaStream_t st)
 {
     if (grid <= 0) return cudaSuccess;
     if (cell && !table) return cudaErrorInvalidValue;
-    if (np == 1) return launch_gnp<1>(g, grid, table, cell, ext, df, smem, st);
-    if (np == 2) return launch_gnp<2>(g, grid, table, cell, ext, df, smem, st);
-    if (np == 4) return launch_gnp<4>(g, grid, table, cell, ext, df, smem, st);
+    if (!groups_tile_ok(tj, nt, !table && !cell && !ext && !df && !g.hl)) return cudaErrorInvalidValue;
+    if (np == 1) return launch_gnp<1>(g, grid, table, cell, ext, df, tj, nt, smem, st);
+    if (np == 2) return launch_gnp<2>(g, grid, table, cell, ext, df, tj, nt, smem, st);
+    if (np == 4) return launch_gnp<4>(g, grid, table, cell, ext, df, tj, nt, smem, st);
     return cudaErrorInvalidValue;
 }
 

@@ -259,8 +259,9 @@ cudaError_t launch_table_from_values(const float *v, float *G0, float *G1, int E
                                      cudaStream_t st);
 
 // df: double-float differencing of particle records (narrow all-pairs)
+// tj, nt: the kernel's j-tile depth and threads per CTA (groups_tile_ok)
 cudaError_t launch_groups(const GroupArgs &g, int grid, int np, bool table, bool cell, bool ext, bool df,
-                          size_t smem, cudaStream_t st);
+                          int tj, int nt, size_t smem, cudaStream_t st);
 // the FP64 outputs of a groups run made with g.hl set: one thread per i
 cudaError_t launch_groups_finish(const GroupArgs &g, cudaStream_t st);
 // one device-side bounded wait that nothing ends (the timeout path's self-test)
@@ -270,9 +271,16 @@ cudaError_t launch_pack_hilo(const double4 *in, long long n, float4 *out, cudaSt
 // i records and the two work counters zeroed, in one launch
 cudaError_t launch_narrow_prep(const double4 *xi, long long ni, long long chunk, long long nic,
                               double4 *ctr, float4 *ihl, int *queue, cudaStream_t st);
-size_t groups_smem(int np, bool table, int ntab, bool df);   // ntab in float2 units, as above
-int groups_bi(int np);
-int groups_max_blocks_per_sm(int np, bool table, int ntab, bool cell, bool ext, bool df);
+// the batched kernel's j-tile depth and threads per CTA by default, and
+// whether (tj, nt) is compiled (every path: the default; plain Newton lists:
+// also 256 x 128, 1024 x 256 and 512 x 256)
+constexpr int kGroupsTJ = 512, kGroupsNT = 128;
+bool groups_tile_ok(int tj, int nt, bool plain);
+size_t groups_smem(int np, bool table, int ntab, bool df, int tj = kGroupsTJ,
+                   int nt = kGroupsNT);   // ntab in float2 units, as above
+int groups_bi(int np, int nt = kGroupsNT);
+int groups_max_blocks_per_sm(int np, bool table, int ntab, bool cell, bool ext, bool df,
+                             int tj = kGroupsTJ, int nt = kGroupsNT);
 // warp-mode items in a launch of their own (k_groups_warp): the cell list's
 // small cells after the CTA-mode kernel (pdl: programmatic dependent launch,
 // for a kernel whose inputs were complete before the CTA-mode kernel

@@ -1,6 +1,8 @@
 """The autotuner (pg_tune) on each path: it keeps one of its candidate launch
 shapes, later runs use it, and their forces match the oracle as untuned
-ones do. Also the split setter's range."""
+ones do. Every compiled j-tile depth x block size of the batched kernel at
+every i-per-thread count gives the oracle's group forces. Also the split and
+tile setters' ranges."""
 
 import numpy as np
 import pytest
@@ -86,9 +88,43 @@ def test_tune_groups(pg, orc):
         a, p = c.get_force(len(d["xi"]))
         info = c.info()
     assert info["i_per_thread"] in (2, 4, 8)
+    assert (info["j_tile"], info["block_threads"]) in ((512, 128), (256, 128), (1024, 256), (512, 256))
     ao, po = orc.newton_groups(d["i_off"], d["j_off"], d["jlist"], d["xi"], d["xj"], d["mj"], 1e-3)
     assert_parity(rel_vec(a, ao), what="a")
     assert_parity(rel_scalar(p, po), what="phi")
+
+
+@pytest.mark.parametrize("np_", [1, 2, 4])
+@pytest.mark.parametrize("tile", [(512, 128), (256, 128), (1024, 256), (512, 256)])
+def test_groups_every_tile_shape(pg, orc, tile, np_):
+    # lists from 64 to 3000 j and groups of every size: CTA-mode and
+    # warp-mode items, one- and multi-pass i sets
+    d = gen.tree_groups(gen.CONFIG_SEEDS[4] + 12, n=1 << 15, ngroups=300,
+                        n_monopoles=1 << 11, nj_range=(64, 3000))
+    with pg.Context(0) as c:
+        c.set_eps(1e-3)
+        c.set_shape(np_, 0, 1)
+        c.set_groups_tile(*tile)
+        c.set_j(d["xj"], d["mj"])
+        c.set_i(d["xi"])
+        c.set_groups(d["i_off"], d["j_off"], d["jlist"])
+        c.run()
+        a, p = c.get_force(len(d["xi"]))
+        info = c.info()
+    assert (info["j_tile"], info["block_threads"]) == tile
+    assert info["i_per_thread"] == 2 * np_
+    ao, po = orc.newton_groups(d["i_off"], d["j_off"], d["jlist"], d["xi"], d["xj"], d["mj"], 1e-3)
+    assert_parity(rel_vec(a, ao), what=f"a {tile} np={np_}")
+    assert_parity(rel_scalar(p, po), what=f"phi {tile} np={np_}")
+
+
+def test_groups_tile_range(pg):
+    with pg.Context(0) as c:
+        for bad in ((128, 128), (512, 64), (2048, 256)):
+            with pytest.raises(pg.PGError) as e:
+                c.set_groups_tile(*bad)
+            assert e.value.code == pg.PG_EINVAL
+        c.set_groups_tile(0, 0)
 
 
 def test_split_range(pg):
