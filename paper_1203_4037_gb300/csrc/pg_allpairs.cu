@@ -43,16 +43,17 @@
 
 namespace pg {
 
-// Bulk-copy raw FP64 j records of unit u into buffer slot.
-__device__ __forceinline__ void issue_jsub(const double4 *jrec, long long nj, int s,
-                                           double4 *dst, uint64_t *bar)
+// Bulk-copy the raw j records of sub-tile s (32 bytes each: FP64 (x, m), or
+// the double-float pairs) into a buffer slot.
+__device__ __forceinline__ void issue_jsub(const void *jrec, long long nj, int s, double4 *dst,
+                                           uint64_t *bar)
 {
     long long j0 = (long long)s * kTJ;
     long long nv = nj - j0;
     if (nv > kTJ) nv = kTJ;
-    unsigned bytes = (unsigned)(nv * sizeof(double4));
+    unsigned bytes = (unsigned)(nv * 32);
     mbar_arrive_tx(bar, bytes);
-    bulk_g2s(dst, jrec + j0, bytes, bar);
+    bulk_g2s(dst, reinterpret_cast<const unsigned char *>(jrec) + j0 * 32, bytes, bar);
 }
 
 // which CTA owns unit u under the equal split of W units over `grid` CTAs
@@ -143,6 +144,18 @@ struct MinBlocks {
 // with DF also {e_x, e_y, e_z, 0}
 template <bool DF> struct CvtWords { static constexpr int value = DF ? 8 : 4; };
 
+// (hi + lo) - (chi + clo) rounded once to FP32, from a double-float value
+// and a double-float centre: TwoSum gives hi - chi = s + t exactly, and the
+// small remainder (lo - clo) + t is added to s with one rounding (its own
+// rounding is far below s's last place), as exact a rounding as forming the
+// difference in FP64
+__device__ __forceinline__ float df_offset(float hi, float lo, float chi, float clo)
+{
+    float s, t;
+    two_sum(hi, -chi, s, t);
+    return __fadd_rn(s, __fadd_rn(__fsub_rn(lo, clo), t));
+}
+
 template <int NP, bool TABLE, bool EXT, bool PK, bool DF>
 __global__ void __launch_bounds__(kNT, MinBlocks<NP, TABLE, DF>::value) k_allpairs(AllPairsArgs a)
 {
@@ -160,6 +173,13 @@ __global__ void __launch_bounds__(kNT, MinBlocks<NP, TABLE, DF>::value) k_allpai
     uint64_t *bar = reinterpret_cast<uint64_t *>(run + 2 * kComp * NP * kNT);
     int *flag = reinterpret_cast<int *>(bar + 2);
     float2 *tab = reinterpret_cast<float2 *>(bar + 4);
+
+    // Newton with single offsets stages double-float records and forms each
+    // offset in FP32 (df_offset, rounded once): no FP64 instruction in the
+    // steady state (GB300 issues FP64 at about two operations per SM-clock,
+    // and the conversion runs between the barriers around the pair loop)
+    constexpr bool HLJ = !TABLE && !DF;
+    const void *jsrc = HLJ ? (const void *)a.jhl : (const void *)a.jrec;
 
     const int tid = threadIdx.x;
     const long long G = gridDim.x;
@@ -181,10 +201,10 @@ __global__ void __launch_bounds__(kNT, MinBlocks<NP, TABLE, DF>::value) k_allpai
     // prefetch the first two sub-tiles
     unsigned pending = 0; // bit k: a copy into buffer k is in flight (thread 0)
     if (tid == 0) {
-        issue_jsub(a.jrec, a.nj, (int)(u0 % a.njsub), raw, &bar[0]);
+        issue_jsub(jsrc, a.nj, (int)(u0 % a.njsub), raw, &bar[0]);
         pending = 1u;
         if (u0 + 1 < u1) {
-            issue_jsub(a.jrec, a.nj, (int)((u0 + 1) % a.njsub), raw + kTJ, &bar[1]);
+            issue_jsub(jsrc, a.nj, (int)((u0 + 1) % a.njsub), raw + kTJ, &bar[1]);
             pending |= 2u;
         }
     }
@@ -199,6 +219,7 @@ __global__ void __launch_bounds__(kNT, MinBlocks<NP, TABLE, DF>::value) k_allpai
     auto RH = [&](int p, int k) -> u64 & { return run[(2 * kComp * p + k) * kNT + tid]; };
     auto RL = [&](int p, int k) -> u64 & { return run[(2 * kComp * p + kComp + k) * kNT + tid]; };
     double cx = 0, cy = 0, cz = 0;
+    float chx = 0, chy = 0, chz = 0, clx = 0, cly = 0, clz = 0;   // HLJ: the centre as hi + lo
     long long cur = -1;
 
     const u64 zero2 = 0ull;
@@ -242,6 +263,9 @@ __global__ void __launch_bounds__(kNT, MinBlocks<NP, TABLE, DF>::value) k_allpai
             cur = t;
             double4 c = a.ctr[t];
             cx = c.x; cy = c.y; cz = c.z;
+            chx = (float)cx; clx = (float)(cx - (double)chx);
+            chy = (float)cy; cly = (float)(cy - (double)chy);
+            chz = (float)cz; clz = (float)(cz - (double)chz);
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
                 float fx[2], fy[2], fz[2], fe[2], rx[2], ry[2], rz[2];
@@ -254,6 +278,12 @@ __global__ void __launch_bounds__(kNT, MinBlocks<NP, TABLE, DF>::value) k_allpai
                         fx[q] = (float)ox;
                         fy[q] = (float)oy;
                         fz[q] = (float)oz;
+                        if (HLJ) {   // the j records' formula, so the own pair differences to 0
+                            const float hx = (float)v.x, hy = (float)v.y, hz = (float)v.z;
+                            fx[q] = df_offset(hx, (float)(v.x - (double)hx), chx, clx);
+                            fy[q] = df_offset(hy, (float)(v.y - (double)hy), chy, cly);
+                            fz[q] = df_offset(hz, (float)(v.z - (double)hz), chz, clz);
+                        }
                         rx[q] = (float)(ox - (double)fx[q]);
                         ry[q] = (float)(oy - (double)fy[q]);
                         rz[q] = (float)(oz - (double)fz[q]);
@@ -287,16 +317,24 @@ __global__ void __launch_bounds__(kNT, MinBlocks<NP, TABLE, DF>::value) k_allpai
         phase ^= 1u << buf;
 
         // convert: FP64 record minus FP64 tile centre, rounded once to FP32
-        // (DF: and the residual of that rounding); each value is stored
-        // twice so one 16-byte load yields f32x2 pairs
+        // (DF: and the residual of that rounding; HLJ: the same rounding
+        // formed in FP32 from the double-float record); each value is stored twice so one
+        // 16-byte load yields f32x2 pairs
         {
             const long long j0 = (long long)s * kTJ;
             long long nv = a.nj - j0;
             if (nv > kTJ) nv = kTJ;
             const double4 *r = raw + buf * kTJ;
+            const float4 *r4 = reinterpret_cast<const float4 *>(r);
             for (int e = tid; e < kTJ; e += kNT) {
                 float x, y, z, m, rx = 0.0f, ry = 0.0f, rz = 0.0f;
-                if (e < nv) {
+                if (HLJ && e < nv) {
+                    const float4 h = r4[2 * e], l = r4[2 * e + 1];
+                    x = df_offset(h.x, l.x, chx, clx);
+                    y = df_offset(h.y, l.y, chy, cly);
+                    z = df_offset(h.z, l.z, chz, clz);
+                    m = h.w;
+                } else if (e < nv) {
                     double4 v = r[e];
                     const double ox = (v.x - cx) * sc, oy = (v.y - cy) * sc, oz = (v.z - cz) * sc;
                     x = (float)ox;
@@ -328,7 +366,7 @@ __global__ void __launch_bounds__(kNT, MinBlocks<NP, TABLE, DF>::value) k_allpai
         // refill the raw buffer just consumed with unit u + 2
         if (tid == 0 && u + 2 < u1) {
             fence_proxy_async();
-            issue_jsub(a.jrec, a.nj, (int)((u + 2) % a.njsub), raw + buf * kTJ, &bar[buf]);
+            issue_jsub(jsrc, a.nj, (int)((u + 2) % a.njsub), raw + buf * kTJ, &bar[buf]);
             pending |= 1u << buf;
         }
 

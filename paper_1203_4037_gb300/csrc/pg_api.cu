@@ -1305,6 +1305,12 @@ int enqueue_allpairs(pg_ctx *c, const Plan &p, double *acc, double *pot)
     a.xi = (const double4 *)c->xt.p;
     a.ctr = (const double4 *)c->ctr.p;
     a.jrec = (const double4 *)c->jrec.p;
+    if (!table && !p.df) {   // the single-form Newton kernel stages double-float j records
+        if ((rc = ensure(c, c->g_jhl, (size_t)std::max<long long>(p.nj, 1) * 32)) ||
+            (rc = pack_j_hilo(c, p.nj)))
+            return rc;
+        a.jhl = (const float4 *)c->g_jhl.p;
+    }
     a.ni = p.ni;
     a.nj = p.nj;
     a.ntiles = p.ntiles;

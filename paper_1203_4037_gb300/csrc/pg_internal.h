@@ -39,6 +39,8 @@ struct AllPairsArgs {
     const double4 *xi;     // i positions (x, y, z, -) in tile order
     const double4 *ctr;    // FP64 centre of each i-tile
     const double4 *jrec;   // j records (x, y, z, m), FP64
+    const float4 *jhl;     // Newton, single form: the j records as double-float pairs
+                           // (hi, m), (lo, m), staged instead of jrec
     long long ni, nj;
     int ntiles;            // ceil(ni / Bi)
     int njsub;             // ceil(nj / kTJ)
