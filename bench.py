@@ -40,6 +40,7 @@ NEWTON_OPS = 13          # FP32-pipe lane-ops per Newton interaction (f32x2 coun
 FP32_LANES_PER_SM = 128
 PAPER_FLOPS_PER_INT = 38
 TREE_NCRIT = 256         # group size bound of the tree rows
+HEADLINE_TRAFFIC = 96.95e6   # DRAM bytes of one 2^20 headline force launch (ncu, read 75.95 + write 21.00 MB)
 
 
 def tree_model(model, n):
@@ -65,7 +66,8 @@ def parse():
     ap.add_argument("--shape", default=None,
                     help="np,packed launch shape of the force kernel (default: the library's)")
     ap.add_argument("--workload", default="newton",
-                    choices=["newton", "table", "cells", "groups", "backward", "narrow", "tree", "pm"],
+                    choices=["newton", "table", "cells", "groups", "backward", "narrow", "tree", "pm",
+                             "small"],
                     help="newton: the headline; the others time one row of the path alone "
                          "(for profiling) and print its measurements")
     ap.add_argument("--model", default="plummer", choices=["plummer", "king"],
@@ -311,8 +313,11 @@ def extra_rows(pg, torch, dev, peak_newton, headline_rate):
         c.set_j_dev(xd, md)
         c.set_i_dev(xd)
         ms = _time_call(torch, lambda: c.run_dev(a, p), 200, warm=20)
-        rows["newton_plummer_4096"] = {"interactions_per_s": 4096 * 4096 / (ms * 1e-3),
-                                       "us_per_call": ms * 1e3, "graph": True}
+        rate4 = 4096 * 4096 / (ms * 1e-3)
+        # double-float differences: 19 FP32-pipe operations per interaction
+        rows["newton_plummer_4096"] = {"interactions_per_s": rate4, "us_per_call": ms * 1e3,
+                                       "graph": True, "launches": c.info()["launches"],
+                                       "frac_fp32_peak_19_ops": rate4 / (peak_newton * 13 / 19)}
         a4, p4 = a.cpu().numpy(), p.cpu().numpy()
         CHECKS.append(("newton_plummer_4096",
                        lambda orc, x=x, m=m, a4=a4, p4=p4: err_ref(
@@ -484,6 +489,9 @@ def extra_rows(pg, torch, dev, peak_newton, headline_rate):
         rows["backward_65536"] = {
             "newton_forward_kernel_ms": fwd, "newton_backward_kernel_ms": bwd,
             "newton_backward_interactions_per_s": n * n / (bwd * 1e-3),
+            # 26 FP32-pipe lane operations per pair (the packed backward)
+            "newton_backward_frac_fp32_peak_26_ops": n * n / (bwd * 1e-3) / (peak_newton * 13 / 26),
+            "newton_backward_over_forward": bwd / fwd,
             "table_backward_kernel_ms": bwd_t,
             "table_backward_interactions_per_s": n * n / (bwd_t * 1e-3)}
     del xd, md, a, w, dx, dm
@@ -685,6 +693,23 @@ def run_row(args):
             info = c.info()
         out.update(ni=ni, nj=N_PART, kernel_ms=kms, interactions_per_s=ni * N_PART / (kms * 1e-3),
                    j_chunks=info["slots"])
+    elif args.workload == "small":
+        # the 4096-body Plummer call (eps = 1/64) in one launch, graph-replayed
+        n = args.n if args.n != N_PART else 4096
+        x, m = gen.plummer(n, gen.CONFIG_SEEDS[1])
+        xd, md = torch.tensor(x, device=dev), torch.tensor(m, device=dev)
+        a, p = torch.empty_like(xd), torch.empty_like(md)
+        with pg.Context(0) as c:
+            c.set_stream(st.cuda_stream)
+            c.set_eps(1 / 64)
+            c.set_self(True)
+            c.set_graph(True)
+            c.set_j_dev(xd, md)
+            c.set_i_dev(xd)
+            ms = _time_call(torch, lambda: c.run_dev(a, p), max(args.steps, 1), warm=args.warmup)
+            info = c.info()
+        out.update(n=n, us_per_call=ms * 1e3, interactions_per_s=n * n / (ms * 1e-3),
+                   launches=info["launches"], grid=info["grid"])
     elif args.workload == "pm":
         # the particle-mesh long range alone on the 2^21 clustered box (or
         # --n particles), Gaussian split r_s = 1/256 on a 256^3 mesh
@@ -901,9 +926,9 @@ def main():
     pairs_rank = ni * npart
     achieved = pairs_rank / (kms * 1e-3)
     # DRAM bytes of one headline launch of this kernel build, from one ncu
-    # pass (dram__bytes_read.sum + dram__bytes_write.sum = 78.96 MB + 21.90
-    # MB); null for other sizes or shapes
-    traffic = 100.86e6 if (npart == N_PART and world == 1 and info["i_per_thread"] == 8) else None
+    # pass (dram__bytes_read.sum + dram__bytes_write.sum); null for other
+    # sizes or shapes, and until measured for this build
+    traffic = HEADLINE_TRAFFIC if (npart == N_PART and world == 1 and info["i_per_thread"] == 8) else None
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_int / 1e9,
             "unit": "Ginteractions/s", "frac": achieved / peak_int, "traffic": traffic,
             "kernel": f"k_allpairs<np={info['i_per_thread'] // 2}, packed={info['packed']}>",
