@@ -670,10 +670,12 @@ def run_row(args):
             c.set_j_dev(xd, md)
             c.set_i_dev(xd)
             kms = _time_kernel(c, lambda: c.run_dev(a), reps=args.steps, warm=args.warmup)
+            ms = _time_call(torch, lambda: c.run_dev(a), args.steps, warm=args.warmup)
             info = c.info()
+            stats = c.tree_stats()
         out.update(n=n, model=args.model, quadrupole=args.quadrupole, ncrit=args.ncrit,
-                   pairs=info["pairs"], kernel_ms=kms,
-                   interactions_per_s=info["pairs"] / (kms * 1e-3))
+                   pairs=info["pairs"], kernel_ms=kms, ms_per_call=ms,
+                   interactions_per_s=info["pairs"] / (kms * 1e-3), walk=stats)
     elif args.workload == "narrow":
         # individual time steps: --n core particles of the 2^20 mixed set
         # against all 2^20 (default 16), path chosen automatically

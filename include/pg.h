@@ -155,8 +155,12 @@ int pg_get_table(pg_ctx *ctx, float *G0, float *G1, long long n);
  *     particles and other nodes are opened.
  * theta = 0 reproduces the direct sum. Needs PG_NEWTON, the self mode with
  * ni == nj, no groups, no periodic box and the global eps (PG_ESTATE
- * otherwise). A tree run reads counts back between its stages, so it
- * synchronises and is not captured in a graph. theta < 0 turns it off.
+ * otherwise). A tree run synchronises once, at its end, to read its
+ * counts back: the call sizes every buffer from the previous call's counts
+ * (with an eighth and 256 more room); when a count outgrows its room, or on
+ * the first call for a particle count, it reads each count back before the
+ * stage that needs it instead (pg_get_tree_stats tells which ran). It is
+ * not captured in a graph. theta < 0 turns it off.
  * A run returns PG_EINVAL when the particles plus pseudo-particles reach
  * 2^27 (the list index width) or the lists reach 2^32 entries.
  * PG_EINVAL for a theta that is not finite, ncrit outside 1 .. 2^20 or
@@ -185,6 +189,28 @@ int pg_set_tree_quadrupole(pg_ctx *ctx, int on);
  * breadth first, level by level and in key order within a level). Syncs. */
 int pg_get_tree(pg_ctx *ctx, long long *sizes, long long *perm, long long *g_i0,
                 long long *g_ni, long long *j_off, long long *jlist);
+
+/* How the tree walk runs (both make the same lists).
+ * PG_TREE_WALK_AUTO (the default): one warp walks one group breadth first,
+ * holding the nodes the group opened at the previous level (at most 512,
+ * PG_TREE_WALK_QUEUE) in shared memory; a group that opens more on one
+ * level (a small theta) makes the call use the level walk.
+ * PG_TREE_WALK_LEVEL: the level walk always: all groups level by level,
+ * one thread per (group, node) visit, with the next level's size read back
+ * between levels. PG_EINVAL for another mode. */
+#define PG_TREE_WALK_AUTO 0
+#define PG_TREE_WALK_LEVEL 1
+#define PG_TREE_WALK_QUEUE 512
+int pg_set_tree_walk(pg_ctx *ctx, int mode);
+
+/* The last tree run's execution: out[0] the walk that made the lists
+ * (1 group walk, 2 level walk), out[1] 1 if the run read each count back
+ * before the stage that needs it, 0 if it ran from the previous call's
+ * room, out[2] the most nodes one group opened on one level (group walk;
+ * above PG_TREE_WALK_QUEUE when it gave up), out[3] the host read-backs of
+ * the call (counting the run from room that came out too small, if any).
+ * Writes min(nout, 4) values. */
+int pg_get_tree_stats(pg_ctx *ctx, long long *out, int nout);
 
 /* The particle-mesh (PM) long-range force of the PPPM and TreePM methods
  * whose short-range part the arbitrary-shape force loop evaluates (Section

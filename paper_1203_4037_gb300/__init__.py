@@ -25,6 +25,7 @@ PG_NEWTON, PG_TABLE = 0, 1
 PG_PATH_AUTO, PG_PATH_TILED, PG_PATH_NARROW = 0, 1, 2
 PG_SPLIT_GAUSS, PG_SPLIT_S2 = 0, 1
 PG_DIFF_AUTO, PG_DIFF_SINGLE, PG_DIFF_DOUBLE = 0, 1, 2
+PG_TREE_WALK_AUTO, PG_TREE_WALK_LEVEL, PG_TREE_WALK_QUEUE = 0, 1, 512
 
 STATUS_NAMES = {0: "PG_OK", -1: "PG_EINVAL", -2: "PG_ESTATE", -3: "PG_ENOMEM", -4: "PG_ECUDA",
                 -5: "PG_ETIMEOUT"}
@@ -79,6 +80,8 @@ SIGNATURES = {
     "pg_set_table_pot_values": (_I, [_P, _P, _LL]),
     "pg_set_tree": (_I, [_P, _D, _I, _I]),
     "pg_set_tree_quadrupole": (_I, [_P, _I]),
+    "pg_set_tree_walk": (_I, [_P, _I]),
+    "pg_get_tree_stats": (_I, [_P, _P, _I]),
     "pg_get_tree_pseudo": (_I, [_P, _P]),
     "pg_set_pm": (_I, [_P, _I, _I, _D]),
     "pg_pm_forces": (_I, [_P, _P, _P, _LL, _P, _P]),
@@ -205,6 +208,18 @@ def pg_set_tree(ctx, theta, ncrit=64, nleaf=8):
 
 def pg_set_tree_quadrupole(ctx, on):
     return _check(ctx, lib().pg_set_tree_quadrupole(ctx, int(bool(on))))
+
+
+def pg_set_tree_walk(ctx, mode):
+    return _check(ctx, lib().pg_set_tree_walk(ctx, int(mode)))
+
+
+def pg_get_tree_stats(ctx):
+    """The last tree run's execution: walk (1 group, 2 level), exact (1 if
+    counts were read back between stages), queue_peak, reads."""
+    out = np.zeros(4, dtype=np.int64)
+    _check(ctx, lib().pg_get_tree_stats(ctx, _ptr(out), 4))
+    return dict(walk=int(out[0]), exact=int(out[1]), queue_peak=int(out[2]), reads=int(out[3]))
 
 
 def pg_get_tree(ctx):
@@ -495,6 +510,12 @@ class Context:
     def set_tree(self, theta, ncrit=64, nleaf=8, quadrupole=False):
         pg_set_tree(self.h, theta, ncrit, nleaf)
         pg_set_tree_quadrupole(self.h, quadrupole)
+
+    def set_tree_walk(self, mode):
+        pg_set_tree_walk(self.h, mode)
+
+    def tree_stats(self):
+        return pg_get_tree_stats(self.h)
 
     def get_tree(self):
         t = pg_get_tree(self.h)

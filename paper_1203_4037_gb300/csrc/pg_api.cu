@@ -11,6 +11,8 @@
 #include "pg.h"
 #include "pg_internal.h"
 
+static_assert(pg::kGroupWalkQ == PG_TREE_WALK_QUEUE, "the group walk's queue is the documented one");
+
 using namespace pg;
 
 namespace {
@@ -101,13 +103,24 @@ struct pg_ctx {
     bool tree_quad = false;
     double tree_theta = 0.75;
     int tree_ncrit = 64, tree_nleaf = 8;
-    enum { TB_BBOX, TB_GEO, TB_KEY, TB_PERM, TB_XS, TB_XI0, TB_SCAN, TB_RUNS, TB_FIRST, TB_COUNT,
+    int tree_walk_mode = PG_TREE_WALK_AUTO;
+    enum { TB_BBOX, TB_GEO, TB_KEY, TB_PERM, TB_XS, TB_XI0, TB_SCAN, TB_META, TB_FIRST, TB_COUNT,
            TB_CHILD0, TB_CHILDN, TB_LEV, TB_M, TB_S, TB_GAT, TB_GSCAN, TB_GI0, TB_GNI, TB_GBOX,
-           TB_IOFF, TB_JCOUNT, TB_JOFF, TB_JLIST, TB_JREC2, TB_ITEMOFF, TB_ITEMS, TB_PAIRS,
-           TB_VG, TB_VK, TB_VE, TB_VC, TB_VSUMS, TB_SEG, TB_BASE, TB_ETOT, TB_GBOXF, TB_NODEW,
+           TB_IOFF, TB_JCOUNT, TB_JOFF, TB_JLIST, TB_JREC2, TB_ITEMOFF, TB_ITEMS,
+           TB_VG, TB_VK, TB_VE, TB_VC, TB_VSUMS, TB_SEG, TB_BASE, TB_GBOXF, TB_NODEW,
            TB_FILT, TB_COM, TB_T, TB_BIG, TB_NBIG, TB_TSUMS, TB_HL, TB_N };
     DevBuf tb[TB_N];
     long long tree_sizes[6] = {0, 0, 0, 0, 0, 0};
+    // the room the last exact tree call left (nodes, groups, list entries),
+    // for the n and pseudo-particle count it ran with, and its nodes per
+    // level; a later call with the same n and P runs from these without
+    // reading counts back (tree_fast)
+    long long tree_cap[3] = {0, 0, 0};
+    long long tree_cap_n = -1;
+    int tree_cap_p = 0;
+    long long tree_hint[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    bool tree_fast = false;
+    long long tree_stats[4] = {0, 0, 0, 0};   // walk (1 group, 2 level), exact, queue peak, read-backs
     long long ngroups = 0;
     std::vector<long long> h_ioff, h_joff;
     DevBuf g_ioff, g_joff, g_jlist, g_items, g_ctr, g_queue, g_jhl, g_ihl;
@@ -592,6 +605,22 @@ int pg_set_tree_quadrupole(pg_ctx *c, int on)
 {
     if (!c) return PG_EINVAL;
     c->tree_quad = on != 0;
+    return PG_OK;
+}
+
+int pg_set_tree_walk(pg_ctx *c, int mode)
+{
+    if (!c) return PG_EINVAL;
+    if (mode != PG_TREE_WALK_AUTO && mode != PG_TREE_WALK_LEVEL)
+        return fail(c, PG_EINVAL, "tree walk mode must be PG_TREE_WALK_AUTO or PG_TREE_WALK_LEVEL");
+    c->tree_walk_mode = mode;
+    return PG_OK;
+}
+
+int pg_get_tree_stats(pg_ctx *c, long long *out, int nout)
+{
+    if (!c || (!out && nout > 0)) return PG_EINVAL;
+    for (int k = 0; k < nout && k < 4; ++k) out[k] = c->tree_stats[k];
     return PG_OK;
 }
 
@@ -1729,70 +1758,55 @@ int prep_sort(pg_ctx *c, long long n)
     return PG_OK;
 }
 
-// The tree front end (Section 5.1's tree usage): build the tree over the
-// particles, walk it per group, and evaluate the lists in the batched-group
-// kernel. The stages size their buffers from counts read back in between,
-// so a tree run synchronises and is never captured in a graph.
-int enqueue_tree(pg_ctx *c, double *acc, double *pot)
+// room for a count that was x: an eighth and 256 more, at most bound
+long long tree_room(long long x, long long bound) { return std::min(bound, x + x / 8 + 256); }
+
+// buffers whose size follows the room for nodes, groups and list entries
+int tree_node_bufs(pg_ctx *c, TreeScratch &t, long long n)
+{
+    const long long k = std::max(t.cap_nodes, 1LL), P = t.npseudo;
+    int rc;
+    if ((rc = tbuf(c, pg_ctx::TB_FIRST, k * 4, t.first)) || (rc = tbuf(c, pg_ctx::TB_COUNT, k * 4, t.count)) ||
+        (rc = tbuf(c, pg_ctx::TB_CHILD0, k * 4, t.child0)) || (rc = tbuf(c, pg_ctx::TB_CHILDN, k * 4, t.childn)) ||
+        (rc = tbuf(c, pg_ctx::TB_LEV, k, t.lev)) || (rc = tbuf(c, pg_ctx::TB_M, k * 8, t.M)) ||
+        (rc = tbuf(c, pg_ctx::TB_S, k * 24, t.S)) ||
+        (rc = tbuf(c, pg_ctx::TB_JREC2, (n + P * k) * 32, t.jrec2)) ||
+        (rc = tbuf(c, pg_ctx::TB_COM, k * 32, t.com)) ||
+        (rc = tbuf(c, pg_ctx::TB_T, (P == 3 ? k : 1) * 48, t.T)) ||
+        (rc = tbuf(c, pg_ctx::TB_BIG, (P == 3 ? k : 1) * 4, t.big_list)) ||
+        (rc = tbuf(c, pg_ctx::TB_NBIG, 4, t.nbig)) ||
+        (rc = tbuf(c, pg_ctx::TB_NODEW, k * sizeof(TreeNodeW), t.nodew)) ||
+        (rc = ensure(c, c->g_jhl, (size_t)(n + P * k) * 32)))
+        return rc;
+    return PG_OK;
+}
+
+int tree_group_bufs(pg_ctx *c, TreeScratch &t, long long n, int Bi)
+{
+    const long long g = std::max(t.cap_groups, 1LL);
+    int rc;
+    if ((rc = tbuf(c, pg_ctx::TB_GBOX, g * 48, t.gbox)) || (rc = tbuf(c, pg_ctx::TB_GBOXF, g * 32, t.gboxf)) ||
+        (rc = tbuf(c, pg_ctx::TB_JCOUNT, (g + 1) * 4, t.jcount)) ||
+        (rc = tbuf(c, pg_ctx::TB_JOFF, (g + 1) * 8, t.j_off)) ||
+        (rc = tbuf(c, pg_ctx::TB_ITEMOFF, (g + 1) * 4, t.item_off)) ||
+        (rc = tbuf(c, pg_ctx::TB_ITEMS, (g + n / Bi + 1) * sizeof(GroupItem), t.items)) ||
+        (rc = ensure(c, c->g_ctr, (size_t)g * 32)))
+        return rc;
+    t.gctr = (double4 *)c->g_ctr.p;
+    return PG_OK;
+}
+
+// the level walk, with a read-back per level to size the next frontier
+int tree_level_walk(pg_ctx *c, TreeScratch &t, long long n, long long ng, int &reads)
 {
     int rc;
-    const long long n = c->ni;
-    c->last_pairs = 0;
-    if (n == 0) return PG_OK;
-    TreeScratch t{};
-    if ((rc = prep_sort(c, n)) ||
-        (rc = tbuf(c, pg_ctx::TB_BBOX, 48, t.bbox)) || (rc = tbuf(c, pg_ctx::TB_GEO, 32, t.geo)) ||
-        (rc = tbuf(c, pg_ctx::TB_KEY, n * 4, t.key)) || (rc = tbuf(c, pg_ctx::TB_PERM, n * 4, t.perm)) ||
-        (rc = tbuf(c, pg_ctx::TB_XS, n * 32, t.xs)) || (rc = tbuf(c, pg_ctx::TB_XI0, n * 32, t.xi0)) ||
-        (rc = tbuf(c, pg_ctx::TB_SCAN, (11 * (n + 1) + 1) * 4, t.scan)) ||
-        (rc = tbuf(c, pg_ctx::TB_TSUMS, ((11 * (n + 1) + 1) / 4096 + 2) * 4, t.tsums)) ||
-        (rc = tbuf(c, pg_ctx::TB_RUNS, 64, t.runs_dev)))
-        return rc;
-    PG_CUDA(c, tree_stage_keys((const double4 *)c->jrec.p, n, t, c->sort, c->stream));
-    unsigned runs[16] = {0};
-    if ((rc = read_dev(c, runs, t.runs_dev, 11 * sizeof(unsigned)))) return rc;
-    long long lev_off[12] = {0};
-    for (int L = 0; L < 11; ++L) lev_off[L + 1] = lev_off[L] + runs[L];
-    const long long nnodes = lev_off[11];
-    t.npseudo = c->tree_quad ? 3 : 1;
-    // list entries index the j records in 27 bits (the batched kernel's limit)
-    if (n + t.npseudo * nnodes >= (1LL << 27))
-        return fail(c, PG_EINVAL, "tree too large: particles + pseudo-particles must stay below 2^27");
-    if ((rc = tbuf(c, pg_ctx::TB_FIRST, nnodes * 4, t.first)) ||
-        (rc = tbuf(c, pg_ctx::TB_COUNT, nnodes * 4, t.count)) ||
-        (rc = tbuf(c, pg_ctx::TB_CHILD0, nnodes * 4, t.child0)) ||
-        (rc = tbuf(c, pg_ctx::TB_CHILDN, nnodes * 4, t.childn)) ||
-        (rc = tbuf(c, pg_ctx::TB_LEV, nnodes, t.lev)) || (rc = tbuf(c, pg_ctx::TB_M, nnodes * 8, t.M)) ||
-        (rc = tbuf(c, pg_ctx::TB_S, nnodes * 24, t.S)) || (rc = tbuf(c, pg_ctx::TB_GAT, n * 4, t.gat)) ||
-        (rc = tbuf(c, pg_ctx::TB_GSCAN, (n + 1) * 4, t.gscan)) ||
-        (rc = tbuf(c, pg_ctx::TB_GI0, n * 4, t.g_i0)) || (rc = tbuf(c, pg_ctx::TB_GNI, n * 4, t.g_ni)) ||
-        (rc = tbuf(c, pg_ctx::TB_GBOX, n * 48, t.gbox)) ||
-        (rc = tbuf(c, pg_ctx::TB_IOFF, (n + 1) * 8, t.i_off)) ||
-        (rc = tbuf(c, pg_ctx::TB_JREC2, (n + t.npseudo * nnodes) * 32, t.jrec2)) ||
-        (rc = tbuf(c, pg_ctx::TB_COM, nnodes * 32, t.com)) ||
-        (rc = tbuf(c, pg_ctx::TB_T, (t.npseudo == 3 ? nnodes : 1) * 48, t.T)) ||
-        (rc = tbuf(c, pg_ctx::TB_NODEW, nnodes * sizeof(TreeNodeW), t.nodew)))
-        return rc;
-    PG_CUDA(c, tree_stage_nodes(n, lev_off, c->tree_ncrit, t, c->sort, c->stream));
-    if ((rc = read_dev(c, runs + 11, t.runs_dev + 11, sizeof(unsigned)))) return rc;
-    const long long ng = runs[11];
-    if ((rc = tbuf(c, pg_ctx::TB_JCOUNT, (ng + 1) * 4, t.jcount)) ||
-        (rc = tbuf(c, pg_ctx::TB_JOFF, (ng + 1) * 8, t.j_off)) ||
-        (rc = tbuf(c, pg_ctx::TB_BIG, (t.npseudo == 3 ? nnodes : 1) * 4, t.big_list)) ||
-        (rc = tbuf(c, pg_ctx::TB_NBIG, 4, t.nbig)) ||
-        (rc = tbuf(c, pg_ctx::TB_SEG, 2 * 11 * ng * 4, t.seg)) ||
+    if ((rc = tbuf(c, pg_ctx::TB_SEG, 2 * 11 * ng * 4, t.seg)) ||
         (rc = tbuf(c, pg_ctx::TB_BASE, 11 * ng * 8, t.base)) ||
-        (rc = tbuf(c, pg_ctx::TB_ETOT, 16, t.etot)) ||
-        (rc = tbuf(c, pg_ctx::TB_GBOXF, ng * 32, t.gboxf)) ||
-        (rc = tbuf(c, pg_ctx::TB_FILT, sizeof(WalkFilter), t.filt)) ||
         (rc = walk_room(c, t, std::max(8 * n, 2 * ng), 0, 0)))
         return rc;
-    PG_CUDA(c, tree_stage_jrec(n, nnodes, lev_off, c->sms, t, c->stream));
-    // the walk, one level at a time; the next frontier's size comes back
-    // to size its room
     long long lev_v[12] = {0, ng};
     int nlev = 1;
-    PG_CUDA(c, tree_walk_init(ng, c->tree_theta, t, c->stream));
+    PG_CUDA(c, tree_walk_init(ng, t, c->stream));
     for (int L = 0; L < 11; ++L) {
         const long long o = lev_v[L], nf = lev_v[L + 1] - o;
         if (nf > (1LL << 28))
@@ -1800,6 +1814,7 @@ int enqueue_tree(pg_ctx *c, double *acc, double *pot)
         PG_CUDA(c, tree_walk_level(n, ng, L, o, nf, c->tree_theta, c->tree_nleaf, t, c->stream));
         if (L == 10) break;       // the finest level opens nothing
         unsigned nnext = 0;
+        ++reads;
         if ((rc = read_dev(c, &nnext, t.vc + nf, sizeof(unsigned)))) return rc;
         if (nnext == 0) break;
         if ((rc = walk_room(c, t, lev_v[L + 1] + nnext, lev_v[L + 1], nf + 1))) return rc;
@@ -1808,33 +1823,130 @@ int enqueue_tree(pg_ctx *c, double *acc, double *pot)
         nlev = L + 2;
     }
     PG_CUDA(c, tree_walk_lists(ng, lev_v, nlev, t, c->sort, c->stream));
-    unsigned long long ent[2] = {0, 0};      // 64-bit entry sum, list length
-    if ((rc = read_dev(c, ent, t.etot, sizeof ent))) return rc;
-    const long long nlist = (long long)ent[1];
-    if (ent[0] >= (1ull << 32) || ent[1] != ent[0])
+    TreeMeta h;
+    ++reads;
+    if ((rc = read_dev(c, &h, t.meta, sizeof h))) return rc;
+    if (h.ent >= (1ull << 32) || (unsigned long long)h.nlist != h.ent)
         return fail(c, PG_EINVAL, "tree interaction lists too long: raise theta or lower ncrit");
-    if ((rc = tbuf(c, pg_ctx::TB_JLIST, nlist * 4, t.jlist))) return rc;
+    t.cap_list = tree_room(h.nlist, 1LL << 32);
+    if ((rc = tbuf(c, pg_ctx::TB_JLIST, std::max(t.cap_list, 1LL) * 4, t.jlist))) return rc;
     PG_CUDA(c, tree_walk_fill(n, ng, lev_v, nlev, t, (int *)c->status.p, c->stream));
+    return PG_OK;
+}
+
+// The tree front end (Section 5.1's tree usage): build the tree over the
+// particles, walk it per group, and evaluate the lists in the batched-group
+// kernel. Every stage reads the counts it needs (level offsets, groups,
+// list length, items) from the device record t.meta. With exact = false
+// the buffers have the room the last exact call left, nothing is read back
+// before the end, and one read there says whether every count fitted
+// (*redo = true when one did not: the results are void and the caller runs
+// the call again exact). With exact = true each count is read back before
+// the stage that sizes a buffer by it, and the level walk takes over when a
+// group's queue overflows (or when asked for).
+int tree_call(pg_ctx *c, double *acc, double *pot, bool exact, bool *redo, int &reads)
+{
+    int rc;
+    const long long n = c->ni;
+    *redo = false;
+    TreeScratch t{};
+    t.npseudo = c->tree_quad ? 3 : 1;
+    const long long P = t.npseudo;
+    const long long kNoRoomCheck = 1LL << 60;
+    if (exact) {
+        t.cap_nodes = kNoRoomCheck;
+        t.cap_groups = n;            // groups never outnumber particles
+        t.cap_list = kNoRoomCheck;
+    } else {
+        t.cap_nodes = c->tree_cap[0];
+        t.cap_groups = c->tree_cap[1];
+        t.cap_list = c->tree_cap[2];
+    }
+    for (int L = 0; L < 11; ++L) t.hint_runs[L] = c->tree_hint[L];
     const int Bi = groups_bi(groups_np(c));
-    if ((rc = tbuf(c, pg_ctx::TB_ITEMOFF, (ng + 1) * 4, t.item_off)) ||
-        (rc = tbuf(c, pg_ctx::TB_ITEMS, (ng + n / Bi + 1) * sizeof(GroupItem), t.items)) ||
-        (rc = tbuf(c, pg_ctx::TB_PAIRS, 16, t.pairs)))
+    float4 *hl = nullptr;
+    if ((rc = prep_sort(c, n)) ||
+        (rc = tbuf(c, pg_ctx::TB_BBOX, 48, t.bbox)) || (rc = tbuf(c, pg_ctx::TB_GEO, 48, t.geo)) ||
+        (rc = tbuf(c, pg_ctx::TB_KEY, n * 4, t.key)) || (rc = tbuf(c, pg_ctx::TB_PERM, n * 4, t.perm)) ||
+        (rc = tbuf(c, pg_ctx::TB_XS, n * 32, t.xs)) || (rc = tbuf(c, pg_ctx::TB_XI0, n * 32, t.xi0)) ||
+        (rc = tbuf(c, pg_ctx::TB_SCAN, (11 * (n + 1) + 1) * 4, t.scan)) ||
+        (rc = tbuf(c, pg_ctx::TB_TSUMS, ((11 * (n + 1) + 1) / 4096 + 2) * 4, t.tsums)) ||
+        (rc = tbuf(c, pg_ctx::TB_META, sizeof(TreeMeta), t.meta)) ||
+        (rc = tbuf(c, pg_ctx::TB_GAT, n * 4, t.gat)) || (rc = tbuf(c, pg_ctx::TB_GSCAN, (n + 1) * 4, t.gscan)) ||
+        (rc = tbuf(c, pg_ctx::TB_GI0, n * 4, t.g_i0)) || (rc = tbuf(c, pg_ctx::TB_GNI, n * 4, t.g_ni)) ||
+        (rc = tbuf(c, pg_ctx::TB_IOFF, (n + 1) * 8, t.i_off)) ||
+        (rc = tbuf(c, pg_ctx::TB_FILT, sizeof(WalkFilter), t.filt)) ||
+        (rc = tbuf(c, pg_ctx::TB_HL, n * 32, hl)) ||
+        (rc = ensure(c, c->g_ihl, (size_t)n * 32)) || (rc = ensure(c, c->g_queue, 16)))
         return rc;
-    PG_CUDA(c, tree_stage_records(n, nnodes, ng, Bi, t, c->sort, c->stream));
-    unsigned long long pi[2] = {0, 0};       // pairs, work items
-    if ((rc = read_dev(c, pi, t.pairs, sizeof pi))) return rc;
-    const unsigned long long pairs = pi[0];
-    const long long nitems = (long long)pi[1];
-    const long long nj = n + t.npseudo * nnodes;
-    if ((rc = ensure(c, c->g_jhl, (size_t)nj * 32)) || (rc = ensure(c, c->g_ihl, (size_t)n * 32)) ||
-        (rc = ensure(c, c->g_ctr, (size_t)std::max<long long>(ng, 1) * 32)) ||
-        (rc = ensure(c, c->g_queue, 16)))
+    if (!exact && ((rc = tree_node_bufs(c, t, n)) || (rc = tree_group_bufs(c, t, n, Bi)) ||
+                   (rc = tbuf(c, pg_ctx::TB_JLIST, std::max(t.cap_list, 1LL) * 4, t.jlist))))
         return rc;
-    PG_CUDA(c, launch_pack_hilo(t.jrec2, nj, (float4 *)c->g_jhl.p, c->stream));
+    PG_CUDA(c, cudaMemsetAsync(t.meta, 0, sizeof(TreeMeta), c->stream));
+    TreeMeta h{};
+
+    // keys, sort, level offsets
+    PG_CUDA(c, tree_stage_keys((const double4 *)c->jrec.p, n, t, c->sort, c->stream));
+    if (exact) {
+        ++reads;
+        if ((rc = read_dev(c, &h, t.meta, sizeof h))) return rc;
+        if (h.flags & kTreeTooLarge)
+            return fail(c, PG_EINVAL, "tree too large: particles + pseudo-particles must stay below 2^27");
+        t.cap_nodes = tree_room(h.nnodes, 11 * n + 1);
+        for (int L = 0; L < 11; ++L) t.hint_runs[L] = h.lev_off[L + 1] - h.lev_off[L];
+        if ((rc = tree_node_bufs(c, t, n))) return rc;
+    }
+    // nodes, moments, groups
+    PG_CUDA(c, tree_stage_nodes(n, c->tree_ncrit, t, c->sort, c->stream));
+    if (exact) {
+        ++reads;
+        if ((rc = read_dev(c, &h, t.meta, sizeof h))) return rc;
+        t.cap_groups = tree_room(h.ngroups, n);
+        if ((rc = tree_group_bufs(c, t, n, Bi))) return rc;
+    }
+    PG_CUDA(c, tree_stage_jrec(n, c->sms, t, c->stream));
+    PG_CUDA(c, tree_walk_prep(c->tree_theta, t, c->stream));
+    // the walk
+    int walk = 1;
+    if (!exact || c->tree_walk_mode == PG_TREE_WALK_AUTO)
+        PG_CUDA(c, tree_group_walk(false, n, c->tree_theta, c->tree_nleaf, c->sms, t, c->sort, nullptr,
+                                   c->stream));
+    if (exact) {
+        if (c->tree_walk_mode == PG_TREE_WALK_AUTO) {
+            ++reads;
+            if ((rc = read_dev(c, &h, t.meta, sizeof h))) return rc;
+            if (h.flags & kTreeWalkQueue) walk = 2;
+            else if (h.flags & kTreeListLong)
+                return fail(c, PG_EINVAL, "tree interaction lists too long: raise theta or lower ncrit");
+        } else {
+            walk = 2;
+        }
+        c->tree_stats[2] = h.qmax;
+        if (walk == 2) {
+            if ((rc = tree_level_walk(c, t, n, h.ngroups, reads))) return rc;
+        } else {
+            t.cap_list = tree_room(h.nlist, 1LL << 32);
+            if ((rc = tbuf(c, pg_ctx::TB_JLIST, std::max(t.cap_list, 1LL) * 4, t.jlist))) return rc;
+        }
+    }
+    if (walk == 1)
+        PG_CUDA(c, tree_group_walk(true, n, c->tree_theta, c->tree_nleaf, c->sms, t, c->sort,
+                                   (int *)c->status.p, c->stream));
+    // work items, the double-float records, the groups' centres, the forces
+    PG_CUDA(c, tree_stage_records(Bi, t, c->sort, c->stream));
+    const long long nj_room = n + P * (exact ? h.nnodes : t.cap_nodes);
+    PG_CUDA(c, launch_pack_hilo(t.jrec2, nj_room, (float4 *)c->g_jhl.p, c->stream));
     c->jhl_n = -1;      // the buffer now holds the tree's records
-    PG_CUDA(c, launch_pack_hilo(t.xi0, n, (float4 *)c->g_ihl.p, c->stream));
-    c->ihl_n = -1;      // and the i buffer the particles in key order
-    PG_CUDA(c, launch_group_ctr(t.xi0, t.i_off, ng, 0, 0, (double4 *)c->g_ctr.p, c->stream));
+    // the i records' double-float pairs: the j records' own (the first n are
+    // the particles in key order), unless the kernel reads each i's eps^2
+    // from the i pair's w (eps = 0), which the j pair holds its mass in
+    const float4 *ihl = (const float4 *)c->g_jhl.p;
+    if (use_ext(c)) {
+        PG_CUDA(c, launch_pack_hilo(t.xi0, n, (float4 *)c->g_ihl.p, c->stream));
+        ihl = (const float4 *)c->g_ihl.p;
+        t.launches += 1;
+    }
+    c->ihl_n = -1;      // the i buffer no longer holds the last set_i's records
     GroupArgs g = group_args(c);
     g.xi = t.xi0;
     g.jrec = t.jrec2;
@@ -1843,10 +1955,12 @@ int enqueue_tree(pg_ctx *c, double *acc, double *pot)
     g.items = t.items;
     g.gctr = (const double4 *)c->g_ctr.p;
     g.jhl = (const float4 *)c->g_jhl.p;
-    g.ihl = (const float4 *)c->g_ihl.p;
-    g.nitems = (int)nitems;
-    g.warp_from = (int)nitems;       // lists are long: every item in CTA mode
-    g.nj = nj;
+    g.ihl = ihl;
+    g.nitems = -1;                   // the item count is read on the device
+    g.nitems_dev = &t.meta->nitems;
+    g.warp_from = -1;                // lists are long: every item in CTA mode
+    g.warp_from_dev = &t.meta->nitems;
+    g.nj = nj_room;
     g.perm = t.perm;
     g.list_self = 1;
     g.acc = acc;
@@ -1855,20 +1969,65 @@ int enqueue_tree(pg_ctx *c, double *acc, double *pot)
     // the kernel writes FP32 (hi, lo) sums; the finish kernel converts them
     // on full warps (the FP64 output from each set's first lane was a fifth
     // of the kernel's pipe time on tree lists)
-    if ((rc = tbuf(c, pg_ctx::TB_HL, n * 32, g.hl))) return rc;
+    g.hl = hl;
     if ((rc = launch_group_kernel(c, g, false))) return rc;
     PG_CUDA(c, launch_groups_finish(g, c->stream));
-    c->last_launches += 1;
-    c->last_pairs = (long long)pairs;
-    c->last_slots = ng;
-    c->last_launches += t.launches + 3;     // the stages, then two packs and the centres
+    c->last_launches += t.launches + 2;     // the stages; finish, the j pack
+    // the one read-back of a run from room: did every count fit?
+    ++reads;
+    if ((rc = read_dev(c, &h, t.meta, sizeof h))) return rc;
+    if (h.flags) {
+        if (!exact) {
+            *redo = true;
+            return PG_OK;
+        }
+        if (h.flags & kTreeTooLarge)
+            return fail(c, PG_EINVAL, "tree too large: particles + pseudo-particles must stay below 2^27");
+        return fail(c, PG_EINVAL, "tree interaction lists too long: raise theta or lower ncrit");
+    }
+    c->last_pairs = (long long)h.pairs;
+    c->last_slots = h.ngroups;
     c->tree_sizes[0] = n;
-    c->tree_sizes[1] = nnodes;
-    c->tree_sizes[2] = ng;
-    c->tree_sizes[3] = nlist;
-    c->tree_sizes[4] = nitems;
-    c->tree_sizes[5] = t.npseudo;
+    c->tree_sizes[1] = h.nnodes;
+    c->tree_sizes[2] = h.ngroups;
+    c->tree_sizes[3] = h.nlist;
+    c->tree_sizes[4] = h.nitems;
+    c->tree_sizes[5] = P;
+    if (exact) {
+        // the room this call left serves the next ones, with the group walk
+        c->tree_cap[0] = t.cap_nodes;
+        c->tree_cap[1] = t.cap_groups;
+        c->tree_cap[2] = t.cap_list;
+        c->tree_cap_n = n;
+        c->tree_cap_p = (int)P;
+        c->tree_fast = walk == 1;
+    } else {
+        c->tree_stats[2] = h.qmax;
+    }
+    for (int L = 0; L < 11; ++L) c->tree_hint[L] = h.lev_off[L + 1] - h.lev_off[L];
+    c->tree_stats[0] = walk;
+    c->tree_stats[1] = exact ? 1 : 0;
     return PG_OK;
+}
+
+int enqueue_tree(pg_ctx *c, double *acc, double *pot)
+{
+    c->last_pairs = 0;
+    const long long n = c->ni;
+    if (n == 0) return PG_OK;
+    int reads = 0, rc;
+    bool redo = false;
+    const long long P = c->tree_quad ? 3 : 1;
+    if (c->tree_fast && c->tree_walk_mode == PG_TREE_WALK_AUTO && c->tree_cap_n == n && c->tree_cap_p == P) {
+        if ((rc = tree_call(c, acc, pot, false, &redo, reads))) return rc;
+        if (!redo) {
+            c->tree_stats[3] = reads;
+            return PG_OK;
+        }
+    }
+    rc = tree_call(c, acc, pot, true, &redo, reads);
+    c->tree_stats[3] = reads;
+    return rc;
 }
 
 int enqueue_groups(pg_ctx *c, double *acc, double *pot)

@@ -1323,11 +1323,11 @@ __device__ __forceinline__ void group_ctr_warp(const double4 *__restrict__ xi,
 }
 
 __global__ void k_group_ctr(const double4 *__restrict__ xi, const long long *__restrict__ i_off,
-                            long long ngroups, long long chunk, long long ni,
-                            double4 *__restrict__ ctr)
+                            long long ngroups, const long long *__restrict__ ngroups_dev, long long chunk,
+                            long long ni, double4 *__restrict__ ctr)
 {
     long long g = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (g >= ngroups) return;
+    if (g >= ngroups || (ngroups_dev && g >= *ngroups_dev)) return;
     group_ctr_warp(xi, i_off, g, chunk, ni, threadIdx.x & 31, ctr);
 }
 
@@ -1360,10 +1360,11 @@ cudaError_t launch_narrow_prep(const double4 *xi, long long ni, long long chunk,
 }
 
 cudaError_t launch_group_ctr(const double4 *xi, const long long *i_off, long long ngroups,
-                             long long chunk, long long ni, double4 *ctr, cudaStream_t st)
+                             long long chunk, long long ni, double4 *ctr, cudaStream_t st,
+                             const long long *ngroups_dev)
 {
     if (ngroups <= 0) return cudaSuccess;
-    k_group_ctr<<<(unsigned)((ngroups + 3) / 4), 128, 0, st>>>(xi, i_off, ngroups, chunk, ni, ctr);
+    k_group_ctr<<<(unsigned)((ngroups + 3) / 4), 128, 0, st>>>(xi, i_off, ngroups, ngroups_dev, chunk, ni, ctr);
     return cudaGetLastError();
 }
 

@@ -295,8 +295,10 @@ cudaError_t launch_groups_warp(const GroupArgs &g, int grid, bool table, bool ce
 cudaError_t launch_table_merge(const float2 *AG1, const float *P0, const float *P1, float4 *AGP,
                                int E, int F, cudaStream_t st);
 cudaError_t launch_set_w(double4 *x, const double *eps, long long n, cudaStream_t st);
+// ngroups_dev set: the group count is read on the device (ngroups bounds it)
 cudaError_t launch_group_ctr(const double4 *xi, const long long *i_off, long long ngroups,
-                             long long chunk, long long ni, double4 *ctr, cudaStream_t st);
+                             long long chunk, long long ni, double4 *ctr, cudaStream_t st,
+                             const long long *ngroups_dev = nullptr);
 
 // periodic cell list: particles binned and sorted by cell, one group per
 // cell whose j-list is the 27 neighbour cells with image shift codes
@@ -333,14 +335,42 @@ struct WalkFilter {
     int on;                     // magnitudes in the range the bounds assume
 };
 
+// The tree call's counts, kept on the device: every stage after the one
+// that produces a count reads it here, so a call needs no read-back before
+// its end. flags records a count that exceeded the room the host gave it
+// (the call's results are then void and it runs again with exact sizes) or
+// a limit of the method.
+struct TreeMeta {
+    long long lev_off[12];      // nodes of level L: [lev_off[L], lev_off[L + 1])
+    long long nnodes, ngroups, nlist;
+    unsigned long long ent;     // list entries, 64-bit sum over the groups
+    unsigned long long pairs;   // pairs the force kernel evaluates
+    unsigned nitems;            // its work items
+    unsigned next[2];           // group walk: claim counters (count, fill pass)
+    unsigned qmax;              // group walk: most opened nodes one level held
+    int flags;                  // kTree* bits
+};
+constexpr int kTreeRoomNodes = 1;    // nodes beyond the room
+constexpr int kTreeRoomGroups = 2;   // groups beyond the room
+constexpr int kTreeRoomList = 4;     // list entries beyond the room
+constexpr int kTreeWalkQueue = 8;    // a group's walk opened more nodes than its queue holds
+constexpr int kTreeTooLarge = 16;    // particles + pseudo-particles reach 2^27
+constexpr int kTreeListLong = 32;    // list entries reach 2^32
+constexpr int kTreeRoomMask = kTreeRoomNodes | kTreeRoomGroups | kTreeRoomList;
+// opened nodes one warp's walk holds per level (the 2^20-particle Plummer
+// and King W0 = 9 trees at theta = 0.75 open at most 66)
+constexpr int kGroupWalkQ = 512;
+
 struct TreeScratch {
     unsigned long long *bbox;   // 6: ordered-int min and max per axis
-    double *geo;                // 4: root corner and span
+    double *geo;                // 5: root corner, span, 1024 / span
     unsigned *key, *perm;       // n: keys in key order, key order -> input index
     double4 *xs, *xi0;          // n: particles in key order (x, m), (x, 0)
     unsigned *scan;             // 11 (n + 1) + 1: run flags of every level, scanned into node indices
     unsigned *tsums;            // scan sums for it
-    unsigned *runs_dev;         // 16: runs per level, then groups, items
+    TreeMeta *meta;             // the call's counts
+    long long cap_nodes, cap_groups, cap_list;   // the room given to nodes, groups, list entries
+    long long hint_runs[11];    // nodes per level of the last call: grid sizes only
     int *first, *count, *child0, *childn;   // nnodes
     unsigned char *lev;         // nnodes
     double *M, *S;              // nnodes, 3 nnodes
@@ -348,6 +378,7 @@ struct TreeScratch {
     unsigned *gscan;            // n + 1
     int *g_i0, *g_ni;           // groups
     double *gbox;               // 6 per group
+    double4 *gctr;              // per group: its box's midpoint (the force kernel's origin)
     float4 *gboxf;              // 2 per group: the box rounded to FP32
     TreeNodeW *nodew;           // nnodes
     double4 *com;               // nnodes: centre of mass (S / M, M)
@@ -374,18 +405,28 @@ struct TreeScratch {
     unsigned long long *etot;   // 2: 64-bit total of the entries, list length
     int launches;               // kernels the stages launched
 };
+// The tree call's stages. Every stage reads the counts of the stages
+// before it from t.meta and checks the room it writes into against t.cap_*;
+// a count beyond its room sets a flag and the kernels after it do nothing.
+// keys: sort, every level's runs, level offsets and node count
 cudaError_t tree_stage_keys(const double4 *jrec, long long n, TreeScratch &t, SortScratch &sort,
                             cudaStream_t st);
-cudaError_t tree_stage_nodes(long long n, const long long *lev_off, int ncrit, TreeScratch &t,
-                             SortScratch &sort, cudaStream_t st);
-cudaError_t tree_stage_jrec(long long n, long long nnodes, const long long *lev_off, int sms,
-                            TreeScratch &t, cudaStream_t st);
-// the walk, level by level: init takes the groups' boxes and puts every
-// group at the root; level L
-// decides its frontier (visits [o, o + nf)) and scans the opened children,
-// whose count is vc[nf]; expand writes them after the frontier; lists
-// places every entry (offsets j_off), fill writes jlist
-cudaError_t tree_walk_init(long long ngroups, double theta, TreeScratch &t, cudaStream_t st);
+// nodes, moments (monopole records; second moments), groups
+cudaError_t tree_stage_nodes(long long n, int ncrit, TreeScratch &t, SortScratch &sort, cudaStream_t st);
+// the j records: particles in key order, pseudo-particles
+cudaError_t tree_stage_jrec(long long n, int sms, TreeScratch &t, cudaStream_t st);
+// the groups' boxes and the walk's FP32 pre-test bounds (both walks)
+cudaError_t tree_walk_prep(double theta, TreeScratch &t, cudaStream_t st);
+// the group walk (one warp per group): the count pass with the list offsets
+// (fill = false), then the fill pass writing jlist
+cudaError_t tree_group_walk(bool fill, long long n, double theta, int nleaf, int sms, TreeScratch &t,
+                            SortScratch &sort, int *status, cudaStream_t st);
+// the level walk (all groups level by level; sizes from the host): init
+// puts every group at the root; level L decides its frontier (visits
+// [o, o + nf)) and scans the opened children, whose count is vc[nf]; expand
+// writes them after the frontier; lists places every entry (offsets j_off),
+// fill writes jlist
+cudaError_t tree_walk_init(long long ngroups, TreeScratch &t, cudaStream_t st);
 cudaError_t tree_walk_level(long long n, long long ngroups, int L, long long o, long long nf,
                             double theta, int nleaf, TreeScratch &t, cudaStream_t st);
 cudaError_t tree_walk_expand(long long o, long long nf, TreeScratch &t, cudaStream_t st);
@@ -393,8 +434,9 @@ cudaError_t tree_walk_lists(long long ngroups, const long long *lev_v, int nlev,
                             SortScratch &sort, cudaStream_t st);
 cudaError_t tree_walk_fill(long long n, long long ngroups, const long long *lev_v, int nlev,
                            TreeScratch &t, int *status, cudaStream_t st);
-cudaError_t tree_stage_records(long long n, long long nnodes, long long ngroups, int Bi,
-                               TreeScratch &t, SortScratch &sort, cudaStream_t st);
+// the force kernel's work items (groups cut into chunks of Bi), their count
+// and the pairs
+cudaError_t tree_stage_records(int Bi, TreeScratch &t, SortScratch &sort, cudaStream_t st);
 
 // narrow all-pairs: part[k ni + i] for j chunks k = 0 .. nchunks - 1 (the
 // tile fields of c are unused)

@@ -83,7 +83,7 @@ __global__ void k_tree_bbox(const double4 *__restrict__ x, long long n, unsigned
         }
 }
 
-// geo = {lo_x, lo_y, lo_z, span}
+// geo = {lo_x, lo_y, lo_z, span, 1024 / span rounded}
 __global__ void k_tree_span(const unsigned long long *bb, double *geo)
 {
     if (threadIdx.x != 0) return;
@@ -96,6 +96,7 @@ __global__ void k_tree_span(const unsigned long long *bb, double *geo)
     }
     if (!(span > 0.0)) span = 1.0;
     geo[3] = span;
+    geo[4] = __ddiv_rn(1024.0, span);
 }
 
 __device__ __forceinline__ unsigned spread10(unsigned v)
@@ -106,6 +107,27 @@ __device__ __forceinline__ unsigned spread10(unsigned v)
     return r;
 }
 
+// The cell index q = floor(RN(d / span) 1024) of d = RN(x - lo) >= 0 per
+// axis. RN(d / span) 1024 is z = 1024 d / span rounded to nearest (the
+// scaling is exact), so q = floor(z) except where z lies within half an
+// ulp (at most 2^-43, z <= 1024) below an integer, which it rounds up to.
+// t = RN(d RN(1024 / span)) is within 2^-41 of z (two roundings of
+// relative 2^-53, z <= 1024); where t is more than 2^-40 from every
+// integer, no integer lies between z and t and none within half an ulp
+// above z, so q = floor(t). Nearer an integer (or t not finite, a span so
+// small that 1024 / span overflows) the quotient is formed exactly. The
+// keys are those of the correctly rounded division, bit for bit, with one
+// FP64 multiply per axis instead of a division.
+__device__ __forceinline__ unsigned cell_of(double x, double lo, double span, double c1024)
+{
+    const double d = __dsub_rn(x, lo);
+    const double t = __dmul_rn(d, c1024);
+    double f = floor(t);
+    if (!(t < 2048.0) || __dsub_rn(t, f) <= 0x1p-40 || __dsub_rn(__dadd_rn(f, 1.0), t) <= 0x1p-40)
+        f = floor(__dmul_rn(__ddiv_rn(d, span), 1024.0));
+    return f >= 1023.0 ? 1023u : (unsigned)f;
+}
+
 __global__ void k_tree_keys(const double4 *__restrict__ x, long long n, const double *geo,
                             unsigned *__restrict__ key, unsigned *__restrict__ idx)
 {
@@ -113,15 +135,10 @@ __global__ void k_tree_keys(const double4 *__restrict__ x, long long n, const do
     if (i >= n) return;
     const double4 v = x[i];
     const double c[3] = {v.x, v.y, v.z};
-    const double span = geo[3];
+    const double span = geo[3], c1024 = geo[4];
     unsigned k = 0;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const double u = __ddiv_rn(__dsub_rn(c[a], geo[a]), span);
-        const double f = floor(__dmul_rn(u, 1024.0));
-        const unsigned q = f >= 1023.0 ? 1023u : (unsigned)f;
-        k |= spread10(q) << (2 - a);
-    }
+    for (int a = 0; a < 3; ++a) k |= spread10(cell_of(c[a], geo[a], span, c1024)) << (2 - a);
     key[i] = k;
     idx[i] = (unsigned)i;
 }
@@ -143,10 +160,6 @@ __global__ void k_tree_gather(const double4 *__restrict__ x, const unsigned *__r
 // One exclusive scan over the whole array numbers every node: the entry at a
 // run's first particle is the runs of all lower levels plus the runs of its
 // own level before it, its node index.
-struct LevelOffsets {
-    long long o[kLevels + 1];  // nodes of level L: [o[L], o[L + 1])
-};
-
 __global__ void k_tree_flags(const unsigned *__restrict__ key, long long n, unsigned *__restrict__ scan)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -158,48 +171,63 @@ __global__ void k_tree_flags(const unsigned *__restrict__ key, long long n, unsi
     if (L == kLevels - 1 && i == n) scan[(long long)kLevels * (n + 1)] = 0u;
 }
 
-// runs per level, for the host
-__global__ void k_tree_level_runs(const unsigned *__restrict__ scan, long long n, unsigned *__restrict__ runs)
+// the level offsets and the node count, checked against the room the host
+// gave the nodes and against the records' 27-bit index limit
+__global__ void k_tree_level_meta(const unsigned *__restrict__ scan, long long n, int npseudo,
+                                  long long cap_nodes, TreeMeta *m)
 {
-    const int L = threadIdx.x;
-    if (L < kLevels) runs[L] = scan[(long long)(L + 1) * (n + 1)] - scan[(long long)L * (n + 1)];
+    if (threadIdx.x != 0) return;
+    long long o = 0;
+    for (int L = 0; L < kLevels; ++L) {
+        m->lev_off[L] = o;
+        o += scan[(long long)(L + 1) * (n + 1)] - scan[(long long)L * (n + 1)];
+    }
+    m->lev_off[kLevels] = o;
+    m->nnodes = o;
+    int f = 0;
+    if (o > cap_nodes) f |= kTreeRoomNodes;
+    if (n + npseudo * o >= (1LL << 27)) f |= kTreeTooLarge;
+    m->flags |= f;
 }
 
 // each run's first particle, every level
-__global__ void k_tree_starts(const unsigned *__restrict__ key, const unsigned *__restrict__ scan,
-                              long long n, int *__restrict__ first)
+__global__ void k_tree_starts(const TreeMeta *__restrict__ m, const unsigned *__restrict__ key,
+                              const unsigned *__restrict__ scan, long long n, int *__restrict__ first)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int L = blockIdx.y;
-    if (i >= n) return;
+    if (i >= n || m->flags) return;
     const int sh = 3 * (kBits - L);
     if (i == 0 || (key[i] >> sh) != (key[i - 1] >> sh)) first[scan[(long long)L * (n + 1) + i]] = (int)i;
 }
 
-// counts, levels and children, every level: the children of a node with
-// particles [f, e) are the next level's runs from the one at f to the one
-// at e
-__global__ void k_tree_nodes(LevelOffsets lo, long long n, const unsigned *__restrict__ scan,
-                             int *__restrict__ first, int *__restrict__ count,
+// counts, levels and children, every level (blockIdx.y; level offsets read
+// on the device, the grid strides over the level): the children of a node
+// with particles [f, e) are the next level's runs from the one at f to the
+// one at e
+__global__ void k_tree_nodes(const TreeMeta *__restrict__ m, long long n, const unsigned *__restrict__ scan,
+                             const int *__restrict__ first, int *__restrict__ count,
                              int *__restrict__ child0, int *__restrict__ childn,
                              unsigned char *__restrict__ lev)
 {
-    const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int L = blockIdx.y;
-    const long long runs = lo.o[L + 1] - lo.o[L];
-    if (r >= runs) return;
-    const long long k = lo.o[L] + r;
-    const int f = first[k];
-    const int e = r + 1 < runs ? first[k + 1] : (int)n;
-    count[k] = e - f;
-    lev[k] = (unsigned char)L;
-    if (L + 1 < kLevels) {
-        const unsigned *next = scan + (long long)(L + 1) * (n + 1);
-        child0[k] = (int)next[f];
-        childn[k] = (int)(next[e] - next[f]);
-    } else {
-        child0[k] = 0;
-        childn[k] = 0;
+    if (m->flags) return;
+    const long long o = m->lev_off[L], runs = m->lev_off[L + 1] - o;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < runs;
+         r += (long long)gridDim.x * blockDim.x) {
+        const long long k = o + r;
+        const int f = first[k];
+        const int e = r + 1 < runs ? first[k + 1] : (int)n;
+        count[k] = e - f;
+        lev[k] = (unsigned char)L;
+        if (L + 1 < kLevels) {
+            const unsigned *next = scan + (long long)(L + 1) * (n + 1);
+            child0[k] = (int)next[f];
+            childn[k] = (int)(next[e] - next[f]);
+        } else {
+            child0[k] = 0;
+            childn[k] = 0;
+        }
     }
 }
 
@@ -233,15 +261,12 @@ __device__ __forceinline__ double4 node_finish(long long k, double m, double s0,
     return c;
 }
 
-// the finest level from its particles, in key order; T = sum m (x - c)(x - c)^T
-__global__ void k_tree_moments_leaf(long long off, long long runs, const int *__restrict__ first,
-                                    const int *__restrict__ count, const int *__restrict__ child0,
-                                    const int *__restrict__ childn, const double4 *__restrict__ xs,
-                                    double *__restrict__ M, double *__restrict__ S, NodeOut o)
+// one node of the finest level
+__device__ __forceinline__ void moments_leaf_one(long long k, const int *__restrict__ first,
+                                                 const int *__restrict__ count, const int *__restrict__ child0,
+                                                 const int *__restrict__ childn, const double4 *__restrict__ xs,
+                                                 double *__restrict__ M, double *__restrict__ S, const NodeOut &o)
 {
-    const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (r >= runs) return;
-    const long long k = off + r;
     double m = 0.0, s0 = 0.0, s1 = 0.0, s2 = 0.0;
     const int f = first[k], e = f + count[k];
     for (int i = f; i < e; ++i) {
@@ -271,16 +296,25 @@ __global__ void k_tree_moments_leaf(long long off, long long runs, const int *__
     for (int q = 0; q < 6; ++q) o.T[6 * k + q] = t[q];
 }
 
-// the levels above from their children in order; T moved to the parent's
-// centre by the parallel-axis rule, T = sum T_ch + M_ch (c_ch - c)(c_ch - c)^T
-__global__ void k_tree_moments_up(long long off, long long runs, const int *__restrict__ first,
-                                  const int *__restrict__ count, const int *__restrict__ child0,
-                                  const int *__restrict__ childn, double *__restrict__ M,
-                                  double *__restrict__ S, NodeOut o)
+// the finest level from its particles, in key order; T = sum m (x - c)(x - c)^T
+__global__ void k_tree_moments_leaf(const TreeMeta *__restrict__ tm, const int *__restrict__ first,
+                                    const int *__restrict__ count, const int *__restrict__ child0,
+                                    const int *__restrict__ childn, const double4 *__restrict__ xs,
+                                    double *__restrict__ M, double *__restrict__ S, NodeOut o)
 {
-    const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (r >= runs) return;
-    const long long k = off + r;
+    if (tm->flags) return;
+    const long long off = tm->lev_off[kLevels - 1], runs = tm->lev_off[kLevels] - off;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < runs;
+         r += (long long)gridDim.x * blockDim.x)
+        moments_leaf_one(off + r, first, count, child0, childn, xs, M, S, o);
+}
+
+// one node above the finest level
+__device__ __forceinline__ void moments_up_one(long long k, const int *__restrict__ first,
+                                               const int *__restrict__ count, const int *__restrict__ child0,
+                                               const int *__restrict__ childn, double *__restrict__ M,
+                                               double *__restrict__ S, const NodeOut &o)
+{
     double m = 0.0, s0 = 0.0, s1 = 0.0, s2 = 0.0;
     const int c0 = child0[k], c1 = c0 + childn[k];
     for (int ch = c0; ch < c1; ++ch) {
@@ -310,26 +344,43 @@ __global__ void k_tree_moments_up(long long off, long long runs, const int *__re
     for (int q = 0; q < 6; ++q) o.T[6 * k + q] = t[q];
 }
 
+// the levels above from their children in order; T moved to the parent's
+// centre by the parallel-axis rule, T = sum T_ch + M_ch (c_ch - c)(c_ch - c)^T
+__global__ void k_tree_moments_up(const TreeMeta *__restrict__ tm, int L, const int *__restrict__ first,
+                                  const int *__restrict__ count, const int *__restrict__ child0,
+                                  const int *__restrict__ childn, double *__restrict__ M,
+                                  double *__restrict__ S, NodeOut o)
+{
+    if (tm->flags) return;
+    const long long off = tm->lev_off[L], runs = tm->lev_off[L + 1] - off;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < runs;
+         r += (long long)gridDim.x * blockDim.x)
+        moments_up_one(off + r, first, count, child0, childn, M, S, o);
+}
+
 // group marks at their first particle: gat[i] = node, else -1 (set before)
 // groups: nodes with at most ncrit particles whose parent (the previous
 // level's node holding the first particle) has more, and finest-level nodes
 // whose parent has more; marked at their first particle, every level
-__global__ void k_tree_group_marks(LevelOffsets lo, long long n, const unsigned *__restrict__ scan,
-                                   const int *__restrict__ first, const int *__restrict__ count,
-                                   int ncrit, int *__restrict__ gat)
+__global__ void k_tree_group_marks(const TreeMeta *__restrict__ m, long long n,
+                                   const unsigned *__restrict__ scan, const int *__restrict__ first,
+                                   const int *__restrict__ count, int ncrit, int *__restrict__ gat)
 {
-    const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int L = blockIdx.y;
-    if (r >= lo.o[L + 1] - lo.o[L]) return;
-    const long long k = lo.o[L] + r;
-    long long pc = -1;
-    if (L > 0) {
-        const long long p = (long long)scan[(long long)(L - 1) * (n + 1) + first[k] + 1] - 1;
-        pc = count[p];
+    if (m->flags) return;
+    const long long o = m->lev_off[L], runs = m->lev_off[L + 1] - o;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < runs;
+         r += (long long)gridDim.x * blockDim.x) {
+        const long long k = o + r;
+        long long pc = -1;
+        if (L > 0) {
+            const long long p = (long long)scan[(long long)(L - 1) * (n + 1) + first[k] + 1] - 1;
+            pc = count[p];
+        }
+        const bool grp = (count[k] <= ncrit && (L == 0 || pc > ncrit)) ||
+                         (L == kLevels - 1 && pc > ncrit);
+        if (grp) gat[first[k]] = (int)k;
     }
-    const bool grp = (count[k] <= ncrit && (L == 0 || pc > ncrit)) ||
-                     (L == kLevels - 1 && pc > ncrit);
-    if (grp) gat[first[k]] = (int)k;
 }
 
 __global__ void k_tree_group_flags(const int *__restrict__ gat, long long n, unsigned *__restrict__ f)
@@ -339,13 +390,22 @@ __global__ void k_tree_group_flags(const int *__restrict__ gat, long long n, uns
     f[i] = i < n && gat[i] >= 0 ? 1u : 0u;
 }
 
-// groups in particle order with their boxes; i_off[g] (ngroups + 1 entries)
-__global__ void k_tree_groups(const int *__restrict__ gat, const unsigned *__restrict__ gscan,
-                              long long n, const int *__restrict__ count, int *__restrict__ g_i0,
-                              int *__restrict__ g_ni, long long *__restrict__ i_off)
+// groups in particle order; i_off[g] (ngroups + 1 entries); the group count
+// (checked against the room the host gave the groups)
+__global__ void k_tree_groups(TreeMeta *m, long long cap_groups, const int *__restrict__ gat,
+                              const unsigned *__restrict__ gscan, long long n, const int *__restrict__ count,
+                              int *__restrict__ g_i0, int *__restrict__ g_ni, long long *__restrict__ i_off)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i == n) i_off[gscan[n]] = n;
+    const long long ng = gscan[n];
+    if (ng > cap_groups) {
+        if (i == 0) atomicOr(&m->flags, kTreeRoomGroups);
+        return;
+    }
+    if (i == n) {
+        i_off[ng] = n;
+        m->ngroups = ng;
+    }
     if (i >= n || gat[i] < 0) return;
     const unsigned g = gscan[i];
     g_i0[g] = (int)i;
@@ -358,12 +418,12 @@ __global__ void k_tree_groups(const int *__restrict__ gat, const unsigned *__res
 // order-preserving integer images of the coordinates (integer compares run
 // at full rate; FP64 compares do not)
 __global__ void k_tree_gbox(const int *__restrict__ g_i0, const int *__restrict__ g_ni,
-                            long long ngroups, const double4 *__restrict__ xs,
-                            double *__restrict__ gbox, float4 *__restrict__ gboxf)
+                            const TreeMeta *__restrict__ m, const double4 *__restrict__ xs,
+                            double *__restrict__ gbox, float4 *__restrict__ gboxf, double4 *__restrict__ ctr)
 {
     const long long g = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (g >= ngroups) return;
+    if (m->flags || g >= m->ngroups) return;
     const int i0 = g_i0[g], ni = g_ni[g];
     unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
     for (int k = i0 + lane; k < i0 + ni; k += 32) {
@@ -393,6 +453,9 @@ __global__ void k_tree_gbox(const int *__restrict__ g_i0, const int *__restrict_
                                    __double2float_rn(dl[2]), 0.f);
         gboxf[2 * g + 1] = make_float4(__double2float_rn(dh[0]), __double2float_rn(dh[1]),
                                        __double2float_rn(dh[2]), 0.f);
+        // the centre the force kernel takes its FP32 offsets from: the box's
+        // midpoint
+        ctr[g] = make_double4(0.5 * (dl[0] + dh[0]), 0.5 * (dl[1] + dh[1]), 0.5 * (dl[2] + dh[2]), 0.0);
     }
 }
 
@@ -431,7 +494,7 @@ struct LevelArgs {
     unsigned *ve;              // visits: entries the decision emits
     unsigned *vc;              // this level: children the decision opens (nf + 1)
     unsigned *seg;             // per level and group: visits [first, end)
-    unsigned long long *etot;  // 64-bit sum of the entries
+    unsigned long long *ent;   // 64-bit sum of the entries
     double theta2;
 };
 
@@ -456,14 +519,19 @@ __global__ void k_walk_filter(const double *geo, double theta2, WalkFilter *f)
             (theta2 == 0.0 || (theta2 >= 0x1p-40 && theta2 <= 0x1p40));
 }
 
-__global__ void k_walk_init(long long ngroups, int *vg, int *vk, unsigned long long *etot)
+// the level walk's start: every group at the root, the entry sum at zero
+// (a group walk that ran out of queue before it counted some entries)
+__global__ void k_walk_init(long long ngroups, int *vg, int *vk, TreeMeta *m)
 {
     const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (g < ngroups) {
         vg[g] = (int)g;
         vk[g] = 0;          // the root
     }
-    if (g == 0) *etot = 0ull;
+    if (g == 0) {
+        m->ent = 0ull;
+        m->flags &= ~kTreeWalkQueue;
+    }
 }
 
 // the FP32 bounds of one axis' squared distance, added into [lo2, hi2]
@@ -476,6 +544,44 @@ __device__ __forceinline__ void axis_bounds(float c, float lo, float hi, float e
     hi2 = __fadd_ru(hi2, __fmul_ru(dh, dh));
 }
 
+// The opening decision for node k of level L (record nd) and a group whose
+// first particle is i0, with its box in FP32 (gbf: low, high corner) and
+// FP64 (bx: low x, y, z, high x, y, z): true where the node is taken as
+// its pseudo-particles. Both walks decide with this one function.
+__device__ __forceinline__ bool walk_accepts(const WalkFilter &F, int L, const TreeNodeW &nd, int k, int i0,
+                                             const float4 *gbf, const double *bx, const double4 *com,
+                                             double theta2)
+{
+    if (nd.first <= i0 && i0 < nd.first + nd.count) return false;     // it holds the group
+    int verdict = 0;                   // 1 accept, -1 not, 0 undecided
+    if (F.on) {
+        const float4 bl = gbf[0], bh = gbf[1];
+        float lo2 = 0.f, hi2 = 0.f;
+        axis_bounds(nd.cx, bl.x, bh.x, F.e, lo2, hi2);
+        axis_bounds(nd.cy, bl.y, bh.y, F.e, lo2, hi2);
+        axis_bounds(nd.cz, bl.z, bh.z, F.e, lo2, hi2);
+        const float limlo = __fmul_rd(__fmul_rd(F.t2lo, lo2), 0x1.fffffcp-1f);
+        const float limhi = __fmul_ru(__fmul_ru(F.t2hi, hi2), 0x1.000002p+0f);
+        if (F.s2hi[L] < limlo) verdict = 1;
+        else if (F.s2lo[L] >= limhi) verdict = -1;
+    }
+    if (verdict == 0) {
+        // the FP64 test, rounded operation by operation
+        const double4 cm = com[k];
+        double d2 = 0.0;
+        for (int x = 0; x < 3; ++x) {
+            const double c = x == 0 ? cm.x : x == 1 ? cm.y : cm.z;
+            const double lo = bx[x], hi = bx[3 + x];
+            double d = 0.0;
+            if (c < lo) d = __dsub_rn(lo, c);
+            else if (c > hi) d = __dsub_rn(c, hi);
+            d2 = __dadd_rn(d2, __dmul_rn(d, d));
+        }
+        verdict = F.s2[L] < __dmul_rn(theta2, d2) ? 1 : -1;
+    }
+    return verdict > 0;
+}
+
 __global__ void k_walk_test(LevelArgs a)
 {
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -484,40 +590,8 @@ __global__ void k_walk_test(LevelArgs a)
         const long long v = a.o + q;
         const int g = a.vg[v], k = a.vk[v];
         const TreeNodeW nd = a.nodew[k];
-        const int i0 = a.g_i0[g];
-        const bool holds = nd.first <= i0 && i0 < nd.first + nd.count;
-        bool accept = false;
-        if (!holds) {
-            const WalkFilter &F = *a.filt;
-            int verdict = 0;                   // 1 accept, -1 not, 0 undecided
-            if (F.on) {
-                const float4 bl = a.gboxf[2 * (long long)g], bh = a.gboxf[2 * (long long)g + 1];
-                float lo2 = 0.f, hi2 = 0.f;
-                axis_bounds(nd.cx, bl.x, bh.x, F.e, lo2, hi2);
-                axis_bounds(nd.cy, bl.y, bh.y, F.e, lo2, hi2);
-                axis_bounds(nd.cz, bl.z, bh.z, F.e, lo2, hi2);
-                const float limlo = __fmul_rd(__fmul_rd(F.t2lo, lo2), 0x1.fffffcp-1f);
-                const float limhi = __fmul_ru(__fmul_ru(F.t2hi, hi2), 0x1.000002p+0f);
-                if (F.s2hi[a.L] < limlo) verdict = 1;
-                else if (F.s2lo[a.L] >= limhi) verdict = -1;
-            }
-            if (verdict == 0) {
-                // the FP64 test, rounded operation by operation
-                const double *bx = a.gbox + 6 * (long long)g;
-                const double4 cm = a.com[k];
-                double d2 = 0.0;
-                for (int x = 0; x < 3; ++x) {
-                    const double c = x == 0 ? cm.x : x == 1 ? cm.y : cm.z;
-                    const double lo = bx[x], hi = bx[3 + x];
-                    double d = 0.0;
-                    if (c < lo) d = __dsub_rn(lo, c);
-                    else if (c > hi) d = __dsub_rn(c, hi);
-                    d2 = __dadd_rn(d2, __dmul_rn(d, d));
-                }
-                verdict = F.s2[a.L] < __dmul_rn(a.theta2, d2) ? 1 : -1;
-            }
-            accept = verdict > 0;
-        }
+        const bool accept = walk_accepts(*a.filt, a.L, nd, k, a.g_i0[g], a.gboxf + 2 * (long long)g,
+                                         a.gbox + 6 * (long long)g, a.com, a.theta2);
         unsigned e = 0, c = 0;
         if (accept) {
             e = (unsigned)a.npseudo;
@@ -538,7 +612,7 @@ __global__ void k_walk_test(LevelArgs a)
         a.vc[q] = 0u;
     }
     for (int s = 16; s; s >>= 1) e64 += __shfl_xor_sync(0xffffffffu, e64, s);
-    if ((threadIdx.x & 31) == 0 && e64) atomicAdd(a.etot, e64);
+    if ((threadIdx.x & 31) == 0 && e64) atomicAdd(a.ent, e64);
 }
 
 // the opened nodes' children, in order, after this level's frontier
@@ -575,14 +649,14 @@ __global__ void k_walk_count(long long ngroups, int nlev, const unsigned *__rest
 __global__ void k_walk_base(long long ngroups, int nlev, const unsigned *__restrict__ jscan,
                             const unsigned *__restrict__ seg, const unsigned *__restrict__ ve,
                             long long *__restrict__ j_off, long long *__restrict__ base,
-                            unsigned long long *__restrict__ etot)
+                            TreeMeta *m)
 {
     const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (g > ngroups) return;
     long long off = jscan[g];
     j_off[g] = off;
     if (g == ngroups) {
-        etot[1] = (unsigned long long)off;    // the list length, beside the entry sum
+        m->nlist = off;    // the list length, beside the entry sum
         return;
     }
     for (int L = 0; L < nlev; ++L) {
@@ -617,6 +691,191 @@ __global__ void k_walk_fill(int L, long long o, long long nf, long long n, long 
     } else {
         const int f = nodew[k].first;
         for (unsigned t = 0; t < e; ++t) jlist[dst + t] = f + (int)t;
+    }
+}
+
+// The group walk: one warp walks one group's tree at a time, breadth first,
+// and needs neither the visit arrays nor a launch per level. The warp keeps
+// the nodes its group opened at the level before, as (first child, number
+// of children) packed in one word (child0 << 3 | childn - 1: child0 < 2^27,
+// 1 <= childn <= 8), in a shared-memory queue. Per level it lays their
+// children out in order (at most 256 per 32 opened nodes), decides 32 at a
+// time with walk_accepts, appends the nodes it opens to the next queue in
+// order (ballot), and gives the decisions' entries consecutive list
+// positions (a warp scan). Children of nodes in key order come in key
+// order, so the list is the level walk's: each level's entries in key
+// order, level after level. A level that opens more than kGroupWalkQ nodes
+// stops the pass (flag kTreeWalkQueue) and the call takes the level walk.
+// The count pass gives each group's entries; the fill pass writes them.
+constexpr int kGwWarps = 8;                       // warps per block
+constexpr int kGwKids = 256;                      // children of 32 opened nodes
+constexpr int kGwU = 2;                           // chunks of 32 children a step decides
+constexpr int kGwWords = 2 * kGroupWalkQ + kGwKids;   // shared words per warp
+
+struct GroupWalkArgs {
+    long long n;
+    TreeMeta *meta;
+    const int *g_i0;
+    const double *gbox;
+    const float4 *gboxf;
+    const TreeNodeW *nodew;
+    const double4 *com;
+    const WalkFilter *filt;
+    int nleaf, npseudo;
+    double theta2;
+    unsigned *jcount;          // count pass: entries per group, 0 at ngroups
+    const long long *j_off;    // fill pass: the list offsets
+    int *jlist;                // fill pass: the lists
+    int *status;               // fill pass: an entry outside its group's list
+};
+
+__device__ __forceinline__ unsigned warp_incl_scan(unsigned v, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
+}
+
+template <bool FILL>
+__global__ void __launch_bounds__(32 * kGwWarps) k_walk_groups(GroupWalkArgs a)
+{
+    __shared__ unsigned sq[kGwWarps * kGwWords];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    TreeMeta *m = a.meta;
+    if (m->flags) return;
+    const long long ng = m->ngroups;
+    if (!FILL && blockIdx.x == 0 && threadIdx.x == 0) a.jcount[ng] = 0u;
+    unsigned *qa = sq + w * kGwWords, *qb = qa + kGroupWalkQ, *kids = qb + kGroupWalkQ;
+    const unsigned below = (1u << lane) - 1u;
+    const WalkFilter &F = *a.filt;
+    unsigned long long ent = 0;
+    unsigned qmax = 0;
+    bool over = false;
+    for (;;) {
+        unsigned gq = 0;
+        if (lane == 0) gq = *(volatile int *)&m->flags ? 0xffffffffu : atomicAdd(&m->next[FILL ? 1 : 0], 1u);
+        const long long g = __shfl_sync(0xffffffffu, gq, 0);
+        if (g >= ng) break;
+        const int i0 = a.g_i0[g];
+        const float4 *gbf = a.gboxf + 2 * g;
+        const double *bx = a.gbox + 6 * g;
+        const long long lo = FILL ? a.j_off[g] : 0, hi = FILL ? a.j_off[g + 1] : 0;
+        long long pos = lo;
+        unsigned *cur = qa, *nxt = qb;
+        unsigned ncur = 1;
+        if (lane == 0) cur[0] = 0u;          // the root: one child, node 0
+        __syncwarp();
+        for (int L = 0; L < kLevels && ncur; ++L) {
+            unsigned nnext = 0;
+            for (unsigned pb = 0; pb < ncur; pb += 32) {
+                unsigned c0 = 0, cn = 0;
+                if (pb + lane < ncur) {
+                    const unsigned e = cur[pb + lane];
+                    c0 = e >> 3;
+                    cn = (e & 7u) + 1u;
+                }
+                const unsigned incl = warp_incl_scan(cn, lane);
+                const unsigned nk = __shfl_sync(0xffffffffu, incl, 31);
+                for (unsigned t = 0, d = incl - cn; t < cn; ++t) kids[d + t] = c0 + t;
+                __syncwarp();
+                // kGwU chunks of 32 children per step: their records load
+                // together, then each chunk's decisions go out in order
+                for (unsigned kb = 0; kb < nk; kb += 32 * kGwU) {
+                    unsigned e[kGwU];
+                    bool acc[kGwU], open[kGwU];
+                    int k[kGwU];
+                    TreeNodeW nd[kGwU];
+#pragma unroll
+                    for (int u = 0; u < kGwU; ++u) {
+                        k[u] = -1;
+                        if (kb + 32 * u + lane < nk) {
+                            k[u] = (int)kids[kb + 32 * u + lane];
+                            nd[u] = a.nodew[k[u]];
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kGwU; ++u) {
+                        e[u] = 0;
+                        acc[u] = open[u] = false;
+                        if (k[u] >= 0) {
+                            acc[u] = walk_accepts(F, L, nd[u], k[u], i0, gbf, bx, a.com, a.theta2);
+                            if (acc[u]) e[u] = (unsigned)a.npseudo;
+                            else if (L == kLevels - 1 || nd[u].count <= a.nleaf) e[u] = (unsigned)nd[u].count;
+                            else open[u] = true;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kGwU; ++u) {
+                        const unsigned om = __ballot_sync(0xffffffffu, open[u]);
+                        if (open[u]) {
+                            const unsigned slot = nnext + __popc(om & below);
+                            if (slot < (unsigned)kGroupWalkQ)
+                                nxt[slot] = ((unsigned)nd[u].child0 << 3) | (unsigned)(nd[u].childn - 1);
+                        }
+                        nnext += __popc(om);
+                        const unsigned ei = warp_incl_scan(e[u], lane);
+                        if (FILL && e[u]) {
+                            const long long d = pos + (ei - e[u]);
+                            if (d + e[u] > hi) {
+                                report(a.status, kStatusBadIndex, 11);
+                            } else if (acc[u]) {
+                                const int p0 = (int)(a.n + (long long)a.npseudo * k[u]);
+                                for (int q = 0; q < a.npseudo; ++q) a.jlist[d + q] = p0 + q;
+                            } else {
+                                for (unsigned t = 0; t < e[u]; ++t) a.jlist[d + t] = nd[u].first + (int)t;
+                            }
+                        }
+                        pos += __shfl_sync(0xffffffffu, ei, 31);
+                    }
+                }
+                __syncwarp();
+            }
+            qmax = nnext > qmax ? nnext : qmax;
+            if (nnext > (unsigned)kGroupWalkQ) {
+                over = true;
+                break;
+            }
+            unsigned *tq = cur;
+            cur = nxt;
+            nxt = tq;
+            ncur = nnext;
+            __syncwarp();
+        }
+        if (over) break;
+        if (FILL) {
+            if (pos != hi && lane == 0) report(a.status, kStatusBadIndex, 12);
+        } else {
+            if (lane == 0) a.jcount[g] = (unsigned)pos;
+            ent += (unsigned long long)pos;
+        }
+    }
+    if (lane == 0) {
+        if (over) atomicOr(&m->flags, kTreeWalkQueue);
+        if (!FILL) {
+            if (ent) atomicAdd(&m->ent, ent);
+            atomicMax(&m->qmax, qmax);
+        }
+    }
+}
+
+// the list offsets from the scanned entry counts, the list length, and its
+// checks (2^32 entries; the room the host gave the list)
+__global__ void k_walk_offsets(TreeMeta *m, const unsigned *__restrict__ jscan, long long *__restrict__ j_off,
+                               long long cap_list)
+{
+    if (m->flags) return;
+    const long long ng = m->ngroups;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g <= ng;
+         g += (long long)gridDim.x * blockDim.x)
+        j_off[g] = jscan[g];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const unsigned long long len = jscan[ng];
+        m->nlist = (long long)len;
+        if (m->ent >= (1ull << 32) || m->ent != len) atomicOr(&m->flags, kTreeListLong);
+        else if ((long long)len > cap_list) atomicOr(&m->flags, kTreeRoomList);
     }
 }
 
@@ -675,12 +934,11 @@ __device__ __forceinline__ void write_quad(double4 *out, long long k, double4 c,
 // closed form (one: T = 0, all three at c; two: T = (m1 m2 / M) d d^T with
 // d = x2 - x1, so e1 = d / |d|, a = |d| sqrt(2 m1 m2) / M, b = 0); the others
 // go to a list for the eigen-solver.
-__global__ void k_tree_quad_small(long long nnodes, const double4 *__restrict__ com,
-                                  const int *__restrict__ first, const int *__restrict__ count,
-                                  const double4 *__restrict__ xs, double4 *__restrict__ out,
-                                  int *__restrict__ big_list, unsigned *__restrict__ nbig)
+__device__ __forceinline__ void quad_small_one(long long k, long long nnodes, const double4 *__restrict__ com,
+                                               const int *__restrict__ first, const int *__restrict__ count,
+                                               const double4 *__restrict__ xs, double4 *__restrict__ out,
+                                               int *__restrict__ big_list, unsigned *__restrict__ nbig)
 {
-    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     bool big = false;
     if (k < nnodes) {
         const double4 c = com[k];
@@ -709,6 +967,18 @@ __global__ void k_tree_quad_small(long long nnodes, const double4 *__restrict__ 
     if (lane == leader) base = atomicAdd(nbig, (unsigned)__popc(mask));
     base = __shfl_sync(0xffffffffu, base, leader);
     if (big) big_list[base + __popc(mask & ((1u << lane) - 1u))] = (int)k;
+}
+
+__global__ void k_tree_quad_small(const TreeMeta *__restrict__ m, const double4 *__restrict__ com,
+                                  const int *__restrict__ first, const int *__restrict__ count,
+                                  const double4 *__restrict__ xs, double4 *__restrict__ out,
+                                  int *__restrict__ big_list, unsigned *__restrict__ nbig)
+{
+    if (m->flags) return;
+    const long long nnodes = m->nnodes;
+    // the loop is uniform over each warp (its ballot takes every lane)
+    for (long long k0 = blockIdx.x * (long long)blockDim.x; k0 < nnodes; k0 += (long long)gridDim.x * blockDim.x)
+        quad_small_one(k0 + threadIdx.x, nnodes, com, first, count, xs, out, big_list, nbig);
 }
 
 // the listed nodes: T's eigen-decomposition by cyclic Jacobi rotations
@@ -753,12 +1023,11 @@ __global__ void k_tree_quad_big(const int *__restrict__ big_list, const unsigned
 }
 
 // items: the groups cut into chunks of at most Bi particles; pairs = sum ni nj
-__global__ void k_tree_items(const int *__restrict__ g_i0, const int *__restrict__ g_ni,
-                             const unsigned *__restrict__ item_off, const long long *__restrict__ j_off,
-                             long long ngroups, int Bi, GroupItem *__restrict__ items,
-                             unsigned long long *__restrict__ pairs)
+__device__ __forceinline__ void items_one(long long g, long long ngroups, const int *__restrict__ g_i0,
+                                          const int *__restrict__ g_ni, const unsigned *__restrict__ item_off,
+                                          const long long *__restrict__ j_off, int Bi,
+                                          GroupItem *__restrict__ items, unsigned long long *pairs)
 {
-    const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     unsigned long long p = 0;
     if (g < ngroups) {
         const int ni = g_ni[g];
@@ -777,12 +1046,27 @@ __global__ void k_tree_items(const int *__restrict__ g_i0, const int *__restrict
     if ((threadIdx.x & 31) == 0 && p) atomicAdd(pairs, p);
 }
 
-__global__ void k_tree_item_counts(const int *__restrict__ g_ni, long long ngroups, int Bi,
-                                   unsigned *__restrict__ c)
+__global__ void k_tree_items(TreeMeta *m, const int *__restrict__ g_i0, const int *__restrict__ g_ni,
+                             const unsigned *__restrict__ item_off, const long long *__restrict__ j_off,
+                             int Bi, GroupItem *__restrict__ items)
 {
-    const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (g > ngroups) return;
-    c[g] = g < ngroups ? (unsigned)((g_ni[g] + Bi - 1) / Bi) : 0u;
+    if (m->flags) return;           // the item count stays zero: the force kernel does nothing
+    const long long ngroups = m->ngroups;
+    if (blockIdx.x == 0 && threadIdx.x == 0) m->nitems = item_off[ngroups];
+    // the loop is uniform over each warp (its reduction takes every lane)
+    for (long long g0 = blockIdx.x * (long long)blockDim.x; g0 < ngroups; g0 += (long long)gridDim.x * blockDim.x)
+        items_one(g0 + threadIdx.x, ngroups, g_i0, g_ni, item_off, j_off, Bi, items, &m->pairs);
+}
+
+// items per group, and zero from the group count up to the room (cap + 1
+// entries, the length the host scans)
+__global__ void k_tree_item_counts(const TreeMeta *__restrict__ m, const int *__restrict__ g_ni, long long cap,
+                                   int Bi, unsigned *__restrict__ c)
+{
+    const long long ngroups = m->flags ? 0 : m->ngroups;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g <= cap;
+         g += (long long)gridDim.x * blockDim.x)
+        c[g] = g < ngroups ? (unsigned)((g_ni[g] + Bi - 1) / Bi) : 0u;
 }
 
 unsigned blocks_of(long long n) { return (unsigned)((std::max(n, 1LL) + 255) / 256); }
@@ -792,6 +1076,35 @@ cudaError_t scan(TreeScratch &t, unsigned *a, long long n, unsigned *sums, cudaS
 {
     if (n > 0) t.launches += 3;
     return launch_excl_scan(a, n, sums, st);
+}
+
+// the widest level of the last call's tree: the grid of the per-level
+// kernels (they stride over the level, so any grid is correct)
+long long widest_hint(const TreeScratch &t)
+{
+    long long w = 1;
+    for (int L = 0; L < kLevels; ++L) w = std::max(w, t.hint_runs[L]);
+    return w;
+}
+
+// blocks of the group walk per SM, once per device
+int gw_blocks_per_sm()
+{
+    static int per[kMaxDevices];
+    static bool done[kMaxDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        (void)cudaGetLastError();
+        return 1;
+    }
+    once_per_device(done, [&]() {
+        int b = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_walk_groups<false>, 32 * kGwWarps, 0);
+        per[dev] = e == cudaSuccess && b > 0 ? b : 1;
+        return e;
+    });
+    (void)cudaGetLastError();
+    return per[dev] > 0 ? per[dev] : 1;
 }
 
 }  // namespace
@@ -806,61 +1119,90 @@ cudaError_t tree_stage_keys(const double4 *jrec, long long n, TreeScratch &t, So
     unsigned *ko = nullptr, *perm = nullptr;
     cudaError_t e = launch_radix_sort(sort.keys[0], sort.vals[0], n, 3 * kBits, sort, &ko, &perm, st);
     if (e != cudaSuccess) return e;
-    t.launches += 4 + (n > 0 ? (3 * kBits + 7) / 8 * 5 : 0) + 3;   // with the gather, flags, runs
+    t.launches += 4 + (n > 0 ? (3 * kBits + 7) / 8 * 5 : 0) + 3;   // with the gather, flags, offsets
     cudaMemcpyAsync(t.key, ko, n * sizeof(unsigned), cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(t.perm, perm, n * sizeof(unsigned), cudaMemcpyDeviceToDevice, st);
     k_tree_gather<<<blocks_of(n), 256, 0, st>>>(jrec, t.perm, n, t.xs, t.xi0);
     // every level's run flags, one scan numbering all nodes
     k_tree_flags<<<dim3(blocks_of(n + 1), kLevels), 256, 0, st>>>(t.key, n, t.scan);
     if ((e = scan(t, t.scan, (long long)kLevels * (n + 1) + 1, t.tsums, st)) != cudaSuccess) return e;
-    k_tree_level_runs<<<1, 32, 0, st>>>(t.scan, n, t.runs_dev);
+    k_tree_level_meta<<<1, 32, 0, st>>>(t.scan, n, t.npseudo, t.cap_nodes, t.meta);
     return cudaGetLastError();
 }
 
-cudaError_t tree_stage_nodes(long long n, const long long *lev_off, int ncrit, TreeScratch &t,
-                             SortScratch &sort, cudaStream_t st)
+cudaError_t tree_stage_nodes(long long n, int ncrit, TreeScratch &t, SortScratch &sort, cudaStream_t st)
 {
-    LevelOffsets lo;
-    long long widest = 1;
-    for (int L = 0; L <= kLevels; ++L) lo.o[L] = lev_off[L];
-    for (int L = 0; L < kLevels; ++L) widest = std::max(widest, lev_off[L + 1] - lev_off[L]);
-    k_tree_starts<<<dim3(blocks_of(n), kLevels), 256, 0, st>>>(t.key, t.scan, n, t.first);
-    k_tree_nodes<<<dim3(blocks_of(widest), kLevels), 256, 0, st>>>(lo, n, t.scan, t.first, t.count,
-                                                                    t.child0, t.childn, t.lev);
+    const unsigned wide = blocks_of(widest_hint(t));
+    k_tree_starts<<<dim3(blocks_of(n), kLevels), 256, 0, st>>>(t.meta, t.key, t.scan, n, t.first);
+    k_tree_nodes<<<dim3(wide, kLevels), 256, 0, st>>>(t.meta, n, t.scan, t.first, t.count, t.child0, t.childn,
+                                                      t.lev);
     // moments bottom-up, with each node's centre, walk record and (quadrupole)
     // second moment
     NodeOut no{t.com, t.npseudo == 1 ? t.jrec2 + n : nullptr, t.nodew, t.npseudo == 3 ? t.T : nullptr};
-    {
-        const long long L = kLevels - 1, runs = lev_off[L + 1] - lev_off[L];
-        k_tree_moments_leaf<<<blocks_of(runs), 256, 0, st>>>(lev_off[L], runs, t.first, t.count, t.child0,
-                                                             t.childn, t.xs, t.M, t.S, no);
-    }
-    for (int L = kLevels - 2; L >= 0; --L) {
-        const long long runs = lev_off[L + 1] - lev_off[L];
-        k_tree_moments_up<<<blocks_of(runs), 256, 0, st>>>(lev_off[L], runs, t.first, t.count, t.child0,
-                                                           t.childn, t.M, t.S, no);
-    }
+    k_tree_moments_leaf<<<blocks_of(t.hint_runs[kLevels - 1]), 256, 0, st>>>(t.meta, t.first, t.count, t.child0,
+                                                                             t.childn, t.xs, t.M, t.S, no);
+    for (int L = kLevels - 2; L >= 0; --L)
+        k_tree_moments_up<<<blocks_of(t.hint_runs[L]), 256, 0, st>>>(t.meta, L, t.first, t.count, t.child0,
+                                                                     t.childn, t.M, t.S, no);
     cudaMemsetAsync(t.gat, 0xff, n * sizeof(int), st);
-    k_tree_group_marks<<<dim3(blocks_of(widest), kLevels), 256, 0, st>>>(lo, n, t.scan, t.first, t.count,
-                                                                          ncrit, t.gat);
+    k_tree_group_marks<<<dim3(wide, kLevels), 256, 0, st>>>(t.meta, n, t.scan, t.first, t.count, ncrit, t.gat);
     k_tree_group_flags<<<blocks_of(n + 1), 256, 0, st>>>(t.gat, n, t.gscan);
     t.launches += kLevels + 5;         // starts, nodes, moments, marks, flags, groups
     cudaError_t e = scan(t, t.gscan, n + 1, sort.sums, st);
     if (e != cudaSuccess) return e;
-    k_tree_groups<<<blocks_of(n + 1), 256, 0, st>>>(t.gat, t.gscan, n, t.count, t.g_i0, t.g_ni,
-                                                    t.i_off);
-    cudaMemcpyAsync(t.runs_dev + kLevels, t.gscan + n, sizeof(unsigned), cudaMemcpyDeviceToDevice, st);
+    k_tree_groups<<<blocks_of(n + 1), 256, 0, st>>>(t.meta, t.cap_groups, t.gat, t.gscan, n, t.count, t.g_i0,
+                                                    t.g_ni, t.i_off);
     return cudaGetLastError();
 }
 
-cudaError_t tree_walk_init(long long ngroups, double theta, TreeScratch &t, cudaStream_t st)
+cudaError_t tree_walk_prep(double theta, TreeScratch &t, cudaStream_t st)
 {
-    k_tree_gbox<<<(unsigned)((ngroups + 7) / 8), 256, 0, st>>>(t.g_i0, t.g_ni, ngroups, t.xs, t.gbox,
-                                                               t.gboxf);
+    k_tree_gbox<<<(unsigned)((t.cap_groups + 7) / 8), 256, 0, st>>>(t.g_i0, t.g_ni, t.meta, t.xs, t.gbox,
+                                                                    t.gboxf, t.gctr);
     k_walk_filter<<<1, 32, 0, st>>>(t.geo, theta * theta, t.filt);
+    t.launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t tree_group_walk(bool fill, long long n, double theta, int nleaf, int sms, TreeScratch &t,
+                            SortScratch &sort, int *status, cudaStream_t st)
+{
+    GroupWalkArgs a{};
+    a.n = n;
+    a.meta = t.meta;
+    a.g_i0 = t.g_i0;
+    a.gbox = t.gbox;
+    a.gboxf = t.gboxf;
+    a.nodew = t.nodew;
+    a.com = t.com;
+    a.filt = t.filt;
+    a.nleaf = nleaf;
+    a.npseudo = t.npseudo;
+    a.theta2 = theta * theta;
+    a.jcount = t.jcount;
+    a.j_off = t.j_off;
+    a.jlist = t.jlist;
+    a.status = status;
+    const unsigned grid = (unsigned)std::max(1, sms * gw_blocks_per_sm());
+    if (fill) {
+        k_walk_groups<true><<<grid, 32 * kGwWarps, 0, st>>>(a);
+        ++t.launches;
+        return cudaGetLastError();
+    }
+    k_walk_groups<false><<<grid, 32 * kGwWarps, 0, st>>>(a);
+    cudaError_t e = scan(t, t.jcount, t.cap_groups + 1, sort.sums, st);
+    if (e != cudaSuccess) return e;
+    k_walk_offsets<<<std::min(blocks_of(t.cap_groups + 1), 4096u), 256, 0, st>>>(t.meta, t.jcount, t.j_off,
+                                                                                  t.cap_list);
+    t.launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t tree_walk_init(long long ngroups, TreeScratch &t, cudaStream_t st)
+{
     cudaMemsetAsync(t.seg, 0, 2 * (size_t)kLevels * ngroups * sizeof(unsigned), st);
-    k_walk_init<<<blocks_of(ngroups), 256, 0, st>>>(ngroups, t.vg, t.vk, t.etot);
-    t.launches += 3;
+    k_walk_init<<<blocks_of(ngroups), 256, 0, st>>>(ngroups, t.vg, t.vk, t.meta);
+    ++t.launches;
     return cudaGetLastError();
 }
 
@@ -886,7 +1228,7 @@ cudaError_t tree_walk_level(long long n, long long ngroups, int L, long long o, 
     a.ve = t.ve;
     a.vc = t.vc;
     a.seg = t.seg;
-    a.etot = t.etot;
+    a.ent = &t.meta->ent;
     a.theta2 = theta * theta;
     k_walk_test<<<blocks_of(nf + 1), 256, 0, st>>>(a);
     ++t.launches;
@@ -910,7 +1252,7 @@ cudaError_t tree_walk_lists(long long ngroups, const long long *lev_v, int nlev,
     k_walk_count<<<blocks_of(ngroups + 1), 256, 0, st>>>(ngroups, nlev, t.seg, t.ve, t.jcount);
     if ((e = scan(t, t.jcount, ngroups + 1, sort.sums, st)) != cudaSuccess) return e;
     k_walk_base<<<blocks_of(ngroups + 1), 256, 0, st>>>(ngroups, nlev, t.jcount, t.seg, t.ve, t.j_off,
-                                                        t.base, t.etot);
+                                                        t.base, t.meta);
     t.launches += 2;
     return cudaGetLastError();
 }
@@ -930,15 +1272,15 @@ cudaError_t tree_walk_fill(long long n, long long ngroups, const long long *lev_
 // the j records: particles in key order, then P pseudo-particles per node
 // (monopoles: written with the moments; quadrupoles: three from the second
 // moments)
-cudaError_t tree_stage_jrec(long long n, long long nnodes, const long long *lev_off, int sms,
-                            TreeScratch &t, cudaStream_t st)
+cudaError_t tree_stage_jrec(long long n, int sms, TreeScratch &t, cudaStream_t st)
 {
-    (void)lev_off;
     cudaMemcpyAsync(t.jrec2, t.xs, n * sizeof(double4), cudaMemcpyDeviceToDevice, st);
     if (t.npseudo == 3) {
         cudaMemsetAsync(t.nbig, 0, sizeof(unsigned), st);
-        k_tree_quad_small<<<blocks_of(nnodes), 256, 0, st>>>(nnodes, t.com, t.first, t.count, t.xs,
-                                                             t.jrec2 + n, t.big_list, t.nbig);
+        long long hint = 0;
+        for (int L = 0; L < kLevels; ++L) hint += t.hint_runs[L];
+        k_tree_quad_small<<<blocks_of(hint), 256, 0, st>>>(t.meta, t.com, t.first, t.count, t.xs, t.jrec2 + n,
+                                                           t.big_list, t.nbig);
         k_tree_quad_big<<<(unsigned)std::max(1, 4 * sms), 128, 0, st>>>(t.big_list, t.nbig, t.com, t.T,
                                                                        t.jrec2 + n);
         t.launches += 2;
@@ -946,17 +1288,15 @@ cudaError_t tree_stage_jrec(long long n, long long nnodes, const long long *lev_
     return cudaGetLastError();
 }
 
-cudaError_t tree_stage_records(long long n, long long nnodes, long long ngroups, int Bi,
-                               TreeScratch &t, SortScratch &sort, cudaStream_t st)
+cudaError_t tree_stage_records(int Bi, TreeScratch &t, SortScratch &sort, cudaStream_t st)
 {
-    k_tree_item_counts<<<blocks_of(ngroups + 1), 256, 0, st>>>(t.g_ni, ngroups, Bi, t.item_off);
+    k_tree_item_counts<<<std::min(blocks_of(t.cap_groups + 1), 4096u), 256, 0, st>>>(t.meta, t.g_ni, t.cap_groups,
+                                                                                      Bi, t.item_off);
     t.launches += 2;      // with the items below
-    cudaError_t e = scan(t, t.item_off, ngroups + 1, sort.sums, st);
+    cudaError_t e = scan(t, t.item_off, t.cap_groups + 1, sort.sums, st);
     if (e != cudaSuccess) return e;
-    cudaMemsetAsync(t.pairs, 0, 2 * sizeof(unsigned long long), st);
-    k_tree_items<<<blocks_of(ngroups), 256, 0, st>>>(t.g_i0, t.g_ni, t.item_off, t.j_off, ngroups, Bi,
-                                                    t.items, t.pairs);
-    cudaMemcpyAsync(t.pairs + 1, t.item_off + ngroups, sizeof(unsigned), cudaMemcpyDeviceToDevice, st);
+    k_tree_items<<<blocks_of(t.cap_groups), 256, 0, st>>>(t.meta, t.g_i0, t.g_ni, t.item_off, t.j_off, Bi,
+                                                          t.items);
     return cudaGetLastError();
 }
 
