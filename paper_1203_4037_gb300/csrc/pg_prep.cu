@@ -138,10 +138,15 @@ __global__ void k_morton(const double4 *__restrict__ x, long long n,
 // Each warp owns a chunk of kChunk consecutive elements; a pass histograms
 // the chunk's 8-bit digits, a scan turns the digit-major histogram into
 // global offsets, and the scatter re-reads the chunk in order and ranks
-// equal digits by lane order, which keeps the sort stable.
+// equal digits by lane order, which keeps the sort stable. A lane loads
+// kBatch rounds' elements before it uses them, so a warp has kBatch loads
+// in flight instead of one (about seven warps per SM hold the 2^20-key
+// sorts' chunks; one load at a time left each pass latency-bound).
 constexpr int kRounds = 32;
 constexpr int kChunk = 32 * kRounds;
 constexpr int kWarpsPerBlock = 4;
+constexpr int kBatch = 8;
+static_assert(kRounds % kBatch == 0, "rounds come in whole batches");
 
 size_t sort_hist_entries(long long n)
 {
@@ -158,10 +163,18 @@ __global__ void k_rs_hist(const unsigned *__restrict__ keys, long long n, int sh
     for (int d = lane; d < 256; d += 32) cnt[w][d] = 0;
     __syncwarp();
     if (chunk < nchunks) {
-        long long base = chunk * kChunk;
-        for (int r = 0; r < kRounds; ++r) {
-            long long e = base + r * 32 + lane;
-            if (e < n) atomicAdd(&cnt[w][(keys[e] >> shift) & 255u], 1u);
+        const long long base = chunk * kChunk;
+#pragma unroll 1
+        for (int r0 = 0; r0 < kRounds; r0 += kBatch) {
+            unsigned k[kBatch];
+#pragma unroll
+            for (int b = 0; b < kBatch; ++b) {
+                const long long e = base + (r0 + b) * 32 + lane;
+                k[b] = e < n ? keys[e] : 0u;
+            }
+#pragma unroll
+            for (int b = 0; b < kBatch; ++b)
+                if (base + (r0 + b) * 32 + lane < n) atomicAdd(&cnt[w][(k[b] >> shift) & 255u], 1u);
         }
     }
     __syncwarp();
@@ -169,37 +182,101 @@ __global__ void k_rs_hist(const unsigned *__restrict__ keys, long long n, int sh
         for (int d = lane; d < 256; d += 32) hist[(long long)d * nchunks + chunk] = cnt[w][d];
 }
 
-__global__ void k_rs_scatter(const unsigned *__restrict__ kin, const unsigned *__restrict__ vin,
-                             unsigned *__restrict__ kout, unsigned *__restrict__ vout, long long n,
-                             int shift, long long nchunks, const unsigned *__restrict__ offs)
+// The scatter ranks each key as before (its destination: the chunk's
+// offset for its digit plus the lane-ordered rank of equal digits before
+// it), but places it in shared memory first, at its destination's position
+// within the block's range for its digit (a block's chunks are adjacent in
+// the digit-major offsets, so each digit's keys of a block go to one
+// contiguous range). The block then writes its keys out in that order:
+// runs of consecutive addresses instead of up to 32 scattered words per
+// warp round.
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) k_rs_scatter(const unsigned *__restrict__ kin,
+                                                                    const unsigned *__restrict__ vin,
+                                                                    unsigned *__restrict__ kout,
+                                                                    unsigned *__restrict__ vout, long long n,
+                                                                    int shift, long long nchunks,
+                                                                    const unsigned *__restrict__ offs)
 {
     __shared__ unsigned cnt[kWarpsPerBlock][256];
-    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    long long chunk = blockIdx.x * (long long)kWarpsPerBlock + w;
-    if (chunk >= nchunks) return;          // whole warp leaves together
-    for (int d = lane; d < 256; d += 32) cnt[w][d] = offs[(long long)d * nchunks + chunk];
-    __syncwarp();
-    long long base = chunk * kChunk;
-    unsigned lt = (1u << lane) - 1u;
-    for (int r = 0; r < kRounds; ++r) {
-        long long e = base + r * 32 + lane;
-        bool valid = e < n;
-        unsigned key = valid ? kin[e] : 0u;
-        unsigned val = valid ? vin[e] : 0u;
-        unsigned d = valid ? ((key >> shift) & 255u) : 256u + lane;   // invalid lanes never match
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        int leader = __ffs(peers) - 1;
-        unsigned rank = __popc(peers & lt);
-        unsigned start = 0;
-        if (valid && lane == leader) start = cnt[w][d];
-        start = __shfl_sync(0xffffffffu, start, leader);
-        __syncwarp();
-        if (valid) {
-            kout[start + rank] = key;
-            vout[start + rank] = val;
-            if (lane == leader) cnt[w][d] = start + __popc(peers);
+    __shared__ unsigned sk[kWarpsPerBlock * kChunk], sv[kWarpsPerBlock * kChunk];
+    __shared__ unsigned gstart[256], lstart[256];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long chunk0 = blockIdx.x * (long long)kWarpsPerBlock, chunk = chunk0 + w;
+    const long long last = min(chunk0 + kWarpsPerBlock, nchunks);       // the block's chunks [chunk0, last)
+    // per digit: the block's first destination and its key count; the
+    // offsets are an exclusive scan, so the entry after the block's last
+    // chunk of digit d ends the block's run of d (n after the array)
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) {
+        const long long e = (long long)d * nchunks + last;
+        gstart[d] = offs[(long long)d * nchunks + chunk0];
+        lstart[d] = (e < 256 * nchunks ? offs[e] : (unsigned)n) - gstart[d];
+    }
+    __syncthreads();
+    if (w == 0) {        // lstart: exclusive scan of the counts over the digits
+        unsigned v[8], tot = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            v[q] = lstart[8 * lane + q];
+            tot += v[q];
         }
-        __syncwarp();
+        unsigned incl = tot;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        unsigned run = incl - tot;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            lstart[8 * lane + q] = run;
+            run += v[q];
+        }
+    }
+    if (chunk < nchunks)
+        for (int d = lane; d < 256; d += 32) cnt[w][d] = offs[(long long)d * nchunks + chunk];
+    __syncthreads();
+    const long long base = chunk * kChunk;
+    const unsigned lt = (1u << lane) - 1u;
+    if (chunk < nchunks) {
+#pragma unroll 1
+        for (int r0 = 0; r0 < kRounds; r0 += kBatch) {
+            unsigned kk[kBatch], vv[kBatch];
+#pragma unroll
+            for (int b = 0; b < kBatch; ++b) {
+                const long long e = base + (r0 + b) * 32 + lane;
+                kk[b] = e < n ? kin[e] : 0u;
+                vv[b] = e < n ? vin[e] : 0u;
+            }
+#pragma unroll
+            for (int b = 0; b < kBatch; ++b) {
+                const bool valid = base + (r0 + b) * 32 + lane < n;
+                const unsigned key = kk[b], val = vv[b];
+                const unsigned d = valid ? ((key >> shift) & 255u) : 256u + lane;   // invalid lanes never match
+                const unsigned peers = __match_any_sync(0xffffffffu, d);
+                const int leader = __ffs(peers) - 1;
+                const unsigned rank = __popc(peers & lt);
+                unsigned start = 0;
+                if (valid && lane == leader) start = cnt[w][d];
+                start = __shfl_sync(0xffffffffu, start, leader);
+                __syncwarp();
+                if (valid) {
+                    const unsigned p = lstart[d] + (start + rank - gstart[d]);
+                    sk[p] = key;
+                    sv[p] = val;
+                    if (lane == leader) cnt[w][d] = start + __popc(peers);
+                }
+                __syncwarp();
+            }
+        }
+    }
+    __syncthreads();
+    // the block's keys in destination order
+    const long long b0 = chunk0 * kChunk;
+    const int nb = (int)(min(n, last * (long long)kChunk) - b0);
+    for (int p = threadIdx.x; p < nb; p += blockDim.x) {
+        const unsigned key = sk[p], d = (key >> shift) & 255u;
+        const unsigned g = gstart[d] + ((unsigned)p - lstart[d]);
+        kout[g] = key;
+        vout[g] = sv[p];
     }
 }
 

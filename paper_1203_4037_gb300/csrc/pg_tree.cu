@@ -76,11 +76,23 @@ __global__ void k_tree_bbox(const double4 *__restrict__ x, long long n, unsigned
             lo[a] = min(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], s));
             hi[a] = max(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], s));
         }
+    // the block's extremes, then one atomic per value and block (a warp's
+    // own atomics on the same six words serialised in L2)
+    __shared__ unsigned long long part[32][6];
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if ((threadIdx.x & 31) == 0)
         for (int a = 0; a < 3; ++a) {
-            atomicMin(&bb[a], lo[a]);
-            atomicMax(&bb[3 + a], hi[a]);
+            part[w][a] = lo[a];
+            part[w][3 + a] = hi[a];
         }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int v = threadIdx.x;
+        unsigned long long r = part[0][v];
+        for (int k = 1; k < nw; ++k) r = v < 3 ? min(r, part[k][v]) : max(r, part[k][v]);
+        if (v < 3) atomicMin(&bb[v], r);
+        else atomicMax(&bb[v], r);
+    }
 }
 
 // geo = {lo_x, lo_y, lo_z, span, 1024 / span rounded}
@@ -117,15 +129,38 @@ __device__ __forceinline__ unsigned spread10(unsigned v)
 // above z, so q = floor(t). Nearer an integer (or t not finite, a span so
 // small that 1024 / span overflows) the quotient is formed exactly. The
 // keys are those of the correctly rounded division, bit for bit, with one
-// FP64 multiply per axis instead of a division.
+// FP64 multiply per axis instead of a division. The integer part of t and
+// its distance to the integers on either side come from t's bits (FP64
+// instructions issue at about two per SM-clock on this GPU, integer ones
+// at 64): t = mant 2^(e - 52), and for 0 <= e <= 10 the low sh = 52 - e
+// bits of mant are t's fraction in units of 2^-sh.
 __device__ __forceinline__ unsigned cell_of(double x, double lo, double span, double c1024)
 {
     const double d = __dsub_rn(x, lo);
     const double t = __dmul_rn(d, c1024);
-    double f = floor(t);
-    if (!(t < 2048.0) || __dsub_rn(t, f) <= 0x1p-40 || __dsub_rn(__dadd_rn(f, 1.0), t) <= 0x1p-40)
-        f = floor(__dmul_rn(__ddiv_rn(d, span), 1024.0));
-    return f >= 1023.0 ? 1023u : (unsigned)f;
+    const unsigned long long u = (unsigned long long)__double_as_longlong(t);
+    const int e = (int)((u >> 52) & 0x7ffu) - 1023;
+    const unsigned long long f52 = u & ((1ull << 52) - 1);
+    bool near;          // within 2^-40 of an integer, or outside [0, 2048)
+    unsigned q = 0;
+    if ((u >> 63) || e > 10) {
+        near = true;                                    // negative, >= 2048, inf or NaN
+    } else if (e < 0) {
+        // q = 0; near 0: t <= 2^-40; near 1: t >= 1 - 2^-40 (e = -1 and
+        // 1 + f52 2^-52 >= 2 - 2^-39)
+        near = e < -40 || (e == -40 && f52 == 0) || (e == -1 && f52 >= (1ull << 52) - (1ull << 13));
+    } else {
+        const int sh = 52 - e;                          // 42 .. 52
+        const unsigned long long mant = f52 | (1ull << 52);
+        const unsigned long long fr = mant & ((1ull << sh) - 1), tol = 1ull << (sh - 40);
+        q = (unsigned)(mant >> sh);
+        near = fr <= tol || fr >= (1ull << sh) - tol;
+    }
+    if (near) {
+        const double f = floor(__dmul_rn(__ddiv_rn(d, span), 1024.0));
+        return f >= 1023.0 ? 1023u : (unsigned)f;
+    }
+    return q >= 1023u ? 1023u : q;
 }
 
 __global__ void k_tree_keys(const double4 *__restrict__ x, long long n, const double *geo,
@@ -356,6 +391,25 @@ __global__ void k_tree_moments_up(const TreeMeta *__restrict__ tm, int L, const 
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < runs;
          r += (long long)gridDim.x * blockDim.x)
         moments_up_one(off + r, first, count, child0, childn, M, S, o);
+}
+
+// The coarse levels L0, L0 - 1, ..., 0 in one block, level after level
+// (the barrier makes a level's moments visible to the next): they hold few
+// nodes, and a launch each was mostly launch and latency.
+__global__ void __launch_bounds__(1024) k_tree_moments_top(const TreeMeta *__restrict__ tm, int L0,
+                                                          const int *__restrict__ first,
+                                                          const int *__restrict__ count,
+                                                          const int *__restrict__ child0,
+                                                          const int *__restrict__ childn, double *__restrict__ M,
+                                                          double *__restrict__ S, NodeOut o)
+{
+    if (tm->flags) return;
+    for (int L = L0; L >= 0; --L) {
+        const long long off = tm->lev_off[L], runs = tm->lev_off[L + 1] - off;
+        for (long long r = threadIdx.x; r < runs; r += blockDim.x)
+            moments_up_one(off + r, first, count, child0, childn, M, S, o);
+        __syncthreads();
+    }
 }
 
 // group marks at their first particle: gat[i] = node, else -1 (set before)
@@ -1141,13 +1195,21 @@ cudaError_t tree_stage_nodes(long long n, int ncrit, TreeScratch &t, SortScratch
     NodeOut no{t.com, t.npseudo == 1 ? t.jrec2 + n : nullptr, t.nodew, t.npseudo == 3 ? t.T : nullptr};
     k_tree_moments_leaf<<<blocks_of(t.hint_runs[kLevels - 1]), 256, 0, st>>>(t.meta, t.first, t.count, t.child0,
                                                                              t.childn, t.xs, t.M, t.S, no);
-    for (int L = kLevels - 2; L >= 0; --L)
+    // levels of at most kTopNodes nodes in the last call (their counts grow
+    // with the level) go to the one-block kernel
+    constexpr long long kTopNodes = 2048;
+    int L0 = -1;
+    while (L0 + 1 < kLevels - 1 && t.hint_runs[L0 + 1] <= kTopNodes) ++L0;
+    for (int L = kLevels - 2; L > L0; --L)
         k_tree_moments_up<<<blocks_of(t.hint_runs[L]), 256, 0, st>>>(t.meta, L, t.first, t.count, t.child0,
                                                                      t.childn, t.M, t.S, no);
+    if (L0 >= 0)
+        k_tree_moments_top<<<1, 1024, 0, st>>>(t.meta, L0, t.first, t.count, t.child0, t.childn, t.M, t.S, no);
     cudaMemsetAsync(t.gat, 0xff, n * sizeof(int), st);
     k_tree_group_marks<<<dim3(wide, kLevels), 256, 0, st>>>(t.meta, n, t.scan, t.first, t.count, ncrit, t.gat);
     k_tree_group_flags<<<blocks_of(n + 1), 256, 0, st>>>(t.gat, n, t.gscan);
-    t.launches += kLevels + 5;         // starts, nodes, moments, marks, flags, groups
+    // starts, nodes, leaf moments, the levels above, marks, flags, groups
+    t.launches += 3 + (kLevels - 2 - L0) + (L0 >= 0 ? 1 : 0) + 3;
     cudaError_t e = scan(t, t.gscan, n + 1, sort.sums, st);
     if (e != cudaSuccess) return e;
     k_tree_groups<<<blocks_of(n + 1), 256, 0, st>>>(t.meta, t.cap_groups, t.gat, t.gscan, n, t.count, t.g_i0,
