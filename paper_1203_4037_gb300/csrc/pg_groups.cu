@@ -301,10 +301,26 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
         for (int k = 0; k < 4; ++k) RH(p, k) = RL(p, k) = 0ull;
     }
 
-    // register prefetch of one tile of records
+    // register prefetch of one tile of records. With a j-list (single-form
+    // variants: the tree and group lists) the list indices run one tile
+    // further ahead (jidx holds the next tile's), so a record gather never
+    // waits on the index load issued just before it; the double-float
+    // variants serve the list-free narrow path and keep one stage (their
+    // registers are at the three-CTA limit)
+    constexpr bool kIdxAhead = !CELL && !DF;
     float4 rc32[kPT];
     float4 rlo[CELL ? 1 : kPT];
     int code[CELL ? kPT : 1];
+    int jidx[kIdxAhead ? kPT : 1];
+    auto fetch_idx = [&](long long t0) {
+        if constexpr (kIdxAhead) {
+#pragma unroll
+            for (int r = 0; r < kPT; ++r) {
+                const long long e = t0 + r * NT + tid;
+                jidx[r] = a.jlist ? (e < je ? a.jlist[e] : 0) & 0x07ffffff : 0;
+            }
+        }
+    };
     auto fetch = [&](long long t0) {
 #pragma unroll
         for (int r = 0; r < kPT; ++r) {
@@ -314,6 +330,8 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
             if (CELL) {
                 code[r] = cell_find(cr, (int)e);
                 j = (long long)cr[32 + code[r]] + e;
+            } else if constexpr (kIdxAhead) {
+                j = a.jlist ? (long long)jidx[r] : e;
             } else {
                 j = a.jlist ? (ok ? a.jlist[e] : 0) & 0x07ffffff : e;
             }
@@ -329,7 +347,9 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
             }
         }
     };
+    fetch_idx(jb);
     fetch(jb);
+    fetch_idx(jb + TJ);
     for (long long t0 = jb; t0 < je; t0 += TJ) {
         // publish the prefetched tile as FP32 offsets in the i frame
 #pragma unroll
@@ -370,7 +390,10 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
             }
         }
         __syncthreads();
-        if (t0 + TJ < je) fetch(t0 + TJ);   // loads in flight during the compute
+        if (t0 + TJ < je) {                  // loads in flight during the compute
+            fetch(t0 + TJ);
+            fetch_idx(t0 + 2 * TJ);
+        }
         long long nv = je - t0;
         if (nv > TJ) nv = TJ;
         if (active) {
