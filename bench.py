@@ -547,6 +547,12 @@ def extra_rows(pg, torch, dev, peak_newton, headline_rate):
         call_pp_pm = _time_call(torch, lambda: c.run_dev(a), 5, warm=2)
         app = a[csel].cpu().numpy()
         pm_ms = _time_call(torch, lambda: c.pm_forces_dev(xd, md, a, p), 5, warm=2)
+        pm_fft = c.pm_fft()
+        # the same call with cuFFT's transforms instead of the hand-written ones
+        c.set_pm_fft(pg.PG_FFT_LIBRARY)
+        pm_lib_ms = _time_call(torch, lambda: c.pm_forces_dev(xd, md, a, p), 5, warm=2)
+        c.set_pm_fft(pg.PG_FFT_AUTO)
+        c.pm_forces_dev(xd, md, a, p)
         apm, ppm = a[csel].cpu().numpy(), p[csel].cpu().numpy()
 
         def pm_err(orc, x=x, m=m, cidx=cidx, apm=apm, ppm=ppm, app=app):
@@ -571,7 +577,9 @@ def extra_rows(pg, torch, dev, peak_newton, headline_rate):
         CHECKS.append(("pm_2e21_mesh256_gauss", pm_err))
         CHECKS.append(("pp_plus_pm_2e21_E4F8_mesh256", pppm_err))
         rows["pm_2e21_mesh256_gauss"] = {"ms_per_call": pm_ms, "particles_per_s": n / (pm_ms * 1e-3),
-                                         "mesh": 256, "r_s_over_h": 1.0}
+                                         "mesh": 256, "r_s_over_h": 1.0,
+                                         "fft": {1: "hand-written", 2: "cuFFT"}.get(pm_fft, "none"),
+                                         "ms_per_call_with_cufft": pm_lib_ms}
         rows["pp_plus_pm_2e21_E4F8_mesh256"] = {"ms_per_call": call_pp_pm,
                                                 "particles_per_s": n / (call_pp_pm * 1e-3)}
     del xd, md, a
@@ -724,7 +732,11 @@ def run_row(args):
             c.set_periodic(1.0)
             c.set_pm(256, pg.PG_SPLIT_GAUSS, 1 / 256)
             ms = _time_call(torch, lambda: c.pm_forces_dev(xd, md, a, p), args.steps, warm=args.warmup)
-        out.update(n=n, mesh=256, ms_per_call=ms, particles_per_s=n / (ms * 1e-3))
+            fft = c.pm_fft()
+            c.set_pm_fft(pg.PG_FFT_LIBRARY)
+            ms_lib = _time_call(torch, lambda: c.pm_forces_dev(xd, md, a, p), args.steps, warm=args.warmup)
+        out.update(n=n, mesh=256, ms_per_call=ms, particles_per_s=n / (ms * 1e-3),
+                   fft={1: "hand-written", 2: "cuFFT"}.get(fft, "none"), ms_per_call_with_cufft=ms_lib)
     elif args.workload == "cells":
         n = args.n if args.n != N_PART else 1 << 21
         x, m = gen.clustered_box(n, gen.CONFIG_SEEDS[3])

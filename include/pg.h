@@ -220,7 +220,8 @@ int pg_get_tree_stats(pg_ctx *ctx, long long *out, int nout);
  * -4 pi D(k) / k^2 with the split factor D (split = PG_SPLIT_GAUSS, scale
  * = r_s; or PG_SPLIT_S2, scale = the S2 diameter a) divided twice by the
  * TSC window, the k = 0 mode and the Nyquist planes dropped, spectral
- * gradient, TSC interpolation. FP32 mesh and FFTs (cuFFT), FP64 in and out.
+ * gradient, TSC interpolation. FP32 mesh and FFTs (see pg_set_pm_fft),
+ * FP64 in and out.
  * Once set, a pg_run in the periodic (cell-list) mode returns PP + PM:
  * the mesh forces at the i-particles from the j-particles are added to the
  * PP forces (and the mesh potential, which includes each particle's own
@@ -228,6 +229,20 @@ int pg_get_tree_stats(pg_ctx *ctx, long long *out, int nout);
  * PG_EINVAL for an odd ngrid or one outside 8 .. 1024, another split, or a
  * scale that is not finite and positive. */
 int pg_set_pm(pg_ctx *ctx, int ngrid, int split, double scale);
+
+/* The FFTs of the PM solve. PG_FFT_AUTO (the default): hand-written FFTs
+ * for a power-of-two mesh from 8 to 512 (a radix-4 Stockham FFT per line in
+ * shared memory; five passes over the mesh with the Green's function and
+ * the spectral gradient applied inside them), cuFFT for other sizes.
+ * PG_FFT_LIBRARY: cuFFT for every size (one real-to-complex transform, the
+ * Green's function, a batch of four complex-to-real transforms). Both
+ * compute the same fields up to FP32 rounding. pg_get_pm_fft writes to
+ * *kind which the last PM solve used: 1 hand-written, 2 cuFFT, 0 none yet.
+ * PG_EINVAL for another mode or a NULL kind. */
+#define PG_FFT_AUTO 0
+#define PG_FFT_LIBRARY 1
+int pg_set_pm_fft(pg_ctx *ctx, int mode);
+int pg_get_pm_fft(pg_ctx *ctx, int *kind);
 
 /* The PM long-range acceleration a[3 n] and potential phi[n] (may be NULL)
  * of n particles x[3 n], m[n] on each other, alone (positions are wrapped

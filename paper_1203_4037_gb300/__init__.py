@@ -26,6 +26,7 @@ PG_PATH_AUTO, PG_PATH_TILED, PG_PATH_NARROW = 0, 1, 2
 PG_SPLIT_GAUSS, PG_SPLIT_S2 = 0, 1
 PG_DIFF_AUTO, PG_DIFF_SINGLE, PG_DIFF_DOUBLE = 0, 1, 2
 PG_TREE_WALK_AUTO, PG_TREE_WALK_LEVEL, PG_TREE_WALK_QUEUE = 0, 1, 512
+PG_FFT_AUTO, PG_FFT_LIBRARY = 0, 1
 
 STATUS_NAMES = {0: "PG_OK", -1: "PG_EINVAL", -2: "PG_ESTATE", -3: "PG_ENOMEM", -4: "PG_ECUDA",
                 -5: "PG_ETIMEOUT"}
@@ -81,6 +82,8 @@ SIGNATURES = {
     "pg_set_tree": (_I, [_P, _D, _I, _I]),
     "pg_set_tree_quadrupole": (_I, [_P, _I]),
     "pg_set_tree_walk": (_I, [_P, _I]),
+    "pg_set_pm_fft": (_I, [_P, _I]),
+    "pg_get_pm_fft": (_I, [_P, _P]),
     "pg_get_tree_stats": (_I, [_P, _P, _I]),
     "pg_get_tree_pseudo": (_I, [_P, _P]),
     "pg_set_pm": (_I, [_P, _I, _I, _D]),
@@ -246,6 +249,17 @@ def pg_get_tree_pseudo(ctx, nnodes, npseudo):
 
 def pg_set_pm(ctx, ngrid, split=PG_SPLIT_GAUSS, scale=0.0):
     return _check(ctx, lib().pg_set_pm(ctx, int(ngrid), int(split), float(scale)))
+
+
+def pg_set_pm_fft(ctx, mode):
+    return _check(ctx, lib().pg_set_pm_fft(ctx, int(mode)))
+
+
+def pg_get_pm_fft(ctx):
+    """Which FFT the last PM solve used: 1 hand-written, 2 cuFFT, 0 none."""
+    k = C.c_int(0)
+    _check(ctx, lib().pg_get_pm_fft(ctx, C.byref(k)))
+    return int(k.value)
 
 
 def pg_pm_forces(ctx, x, m):
@@ -576,6 +590,12 @@ class Context:
 
     def set_pm(self, ngrid, split=PG_SPLIT_GAUSS, scale=0.0):
         pg_set_pm(self.h, ngrid, split, scale)
+
+    def set_pm_fft(self, mode):
+        pg_set_pm_fft(self.h, mode)
+
+    def pm_fft(self):
+        return pg_get_pm_fft(self.h)
 
     def pm_forces(self, x, m):
         return pg_pm_forces(self.h, x, m)

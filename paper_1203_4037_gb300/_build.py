@@ -16,7 +16,7 @@ LIB = os.path.join(HERE, "libpg.so")
 OBJDIR = os.path.join(HERE, "_build")
 
 SOURCES = ["pg_api.cu", "pg_allpairs.cu", "pg_prep.cu", "pg_table.cu", "pg_groups.cu", "pg_tree.cu",
-           "pg_pm.cu", "pg_backward.cu", "pg_noalloc.cu", "pg_micro.cu", "pg_small.cu"]
+           "pg_pm.cu", "pg_fft.cu", "pg_backward.cu", "pg_noalloc.cu", "pg_micro.cu", "pg_small.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
                 "-I", INCLUDE, "-I", CSRC]

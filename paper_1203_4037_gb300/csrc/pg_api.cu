@@ -95,6 +95,7 @@ struct pg_ctx {
     // (0 Gaussian, 1 S2) and its scale; records and buffers of the
     // stand-alone entry points
     PmState *pm = nullptr;
+    int pm_fft = PG_FFT_AUTO;
     int pm_n = 0, pm_split = 0;
     double pm_scale = 0.0;
     DevBuf pm_rec, pm_x, pm_m, pm_acc, pm_pot;
@@ -638,10 +639,29 @@ int pg_set_pm(pg_ctx *c, int ngrid, int split, double scale)
         return fail(c, PG_EINVAL, "split must be PG_SPLIT_GAUSS or PG_SPLIT_S2");
     if (!(scale > 0.0) || !std::isfinite(scale)) return fail(c, PG_EINVAL, "scale must be finite and > 0");
     if (!c->pm) c->pm = pm_create();
+    pm_set_fft(c->pm, c->pm_fft);
     c->pm_n = ngrid;
     c->pm_split = split;
     c->pm_scale = scale;
     drop_graph(c);
+    return PG_OK;
+}
+
+int pg_set_pm_fft(pg_ctx *c, int mode)
+{
+    if (!c) return PG_EINVAL;
+    if (mode != PG_FFT_AUTO && mode != PG_FFT_LIBRARY)
+        return fail(c, PG_EINVAL, "the PM FFT mode must be PG_FFT_AUTO or PG_FFT_LIBRARY");
+    if (mode != c->pm_fft) drop_graph(c);
+    c->pm_fft = mode;
+    if (c->pm) pm_set_fft(c->pm, mode);
+    return PG_OK;
+}
+
+int pg_get_pm_fft(pg_ctx *c, int *kind)
+{
+    if (!c || !kind) return PG_EINVAL;
+    *kind = c->pm ? pm_last_fft(c->pm) : 0;
     return PG_OK;
 }
 

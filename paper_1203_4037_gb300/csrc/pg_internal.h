@@ -222,6 +222,19 @@ cudaError_t launch_radix_sort(unsigned *keys, unsigned *vals, long long n, int k
 struct PmState;
 PmState *pm_create();
 void pm_destroy(PmState *s);
+// 0: the hand-written FFTs for a power-of-two mesh from 8 to 512 (cuFFT
+// for other sizes), 1: cuFFT always; the last solve's FFT (1 hand-written,
+// 2 cuFFT, 0 none yet)
+void pm_set_fft(PmState *s, int mode);
+int pm_last_fft(const PmState *s);
+// the hand-written mesh solve (pg_fft.cu): rho (N^3) to the four fields
+// (4 N^3: -dphi/dx, -dphi/dy, -dphi/dz, phi) with the Green's table gtab
+// (by n^2) and the window table wtab (by index), kf = 2 pi / L; scratch S
+// (N^2 N/2 complex) and W (3 N^2 N/2 complex); tw from fft_twiddles
+bool fft_mesh_ok(int N);
+void fft_twiddles(int N, float2 *host);
+cudaError_t fft_solve(const float *rho, float *field, float2 *S, float2 *W, const float2 *tw, const float *gtab,
+                      const float *wtab, float kf, int N, cudaStream_t st);
 // tgt_order: an interpolation order of the targets to use instead of sorting
 // them into mesh order (a permutation of 0 .. nt-1 that keeps neighbours
 // together; the cell list's cell order), or nullptr

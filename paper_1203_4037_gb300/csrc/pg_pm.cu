@@ -9,7 +9,9 @@
 //  1. TSC assignment: around the nearest mesh point j0 = floor(u + 1/2) of
 //     u = x / h, offset d = u - j0, weights 1/2 (1/2 - d)^2, 3/4 - d^2,
 //     1/2 (1/2 + d)^2 per axis; density m w / h^3, FP32 atomics;
-//  2. real-to-complex FFT (cuFFT, a plain library FFT);
+//  2. real-to-complex FFT: the hand-written FFTs of pg_fft.cu for a
+//     power-of-two mesh from 8 to 512 (steps 2-4 fused there), cuFFT for
+//     the other sizes or on request (pm_set_fft);
 //  3. per mode k = 2 pi n / L: phi_k = rho_k G(n^2) / (W(n_x) W(n_y) W(n_z)),
 //     G = -4 pi D(k) / (k^2 N^3) with the split factor D (Gaussian
 //     exp(-k^2 r_s^2), or the S2 clouds' S(k a)^2), W = sinc^6(pi n / N)
@@ -37,6 +39,9 @@ struct PmState {
     double L = 0.0, scale = 0.0;
     cufftHandle r2c = 0, c2r = 0;
     bool have_r2c = false, have_c2r = false;
+    int fft_mode = 0;            // 0: hand-written where the mesh allows, 1: cuFFT
+    int last_fft = 0;            // the last solve: 1 hand-written, 2 cuFFT
+    float2 *twid = nullptr;      // N: e^{-2 pi i m / N} (hand-written FFTs)
     float *rho = nullptr;        // N^3
     float2 *rk = nullptr;        // N^2 (N/2 + 1)
     float2 *spec = nullptr;      // 4 N^2 (N/2 + 1)
@@ -201,8 +206,9 @@ void release(PmState &s)
     s.have_r2c = s.have_c2r = false;
     for (void *p : {(void *)s.rho, (void *)s.rk, (void *)s.spec, (void *)s.field, (void *)s.gtab,
                     (void *)s.wtab, (void *)s.mj_raw, (void *)s.mj_tgt, (void *)s.md_raw, (void *)s.md_tgt,
-                    (void *)s.perm_tgt})
+                    (void *)s.perm_tgt, (void *)s.twid})
         if (p) cudaFree(p);
+    s.twid = nullptr;
     s.rho = nullptr;
     s.rk = s.spec = nullptr;
     s.field = s.gtab = s.wtab = nullptr;
@@ -233,6 +239,9 @@ void pm_destroy(PmState *s)
     delete s;
 }
 
+void pm_set_fft(PmState *s, int mode) { s->fft_mode = mode; }
+int pm_last_fft(const PmState *s) { return s->last_fft; }
+
 namespace {
 
 // mesh, plans and tables for (N, split, scale, L); room for n records
@@ -253,20 +262,18 @@ int ensure(PmState *s, double L, int N, int split, double scale, long long n, st
             err = "PM mesh allocation failed";
             return PG_ENOMEM;
         }
-        if (cufftPlan3d(&s->r2c, N, N, N, CUFFT_R2C) != CUFFT_SUCCESS) {
-            release(*s);
-            err = "cufftPlan3d failed";
-            return PG_ECUDA;
+        if (fft_mesh_ok(N)) {
+            std::vector<float2> tw((size_t)N);
+            fft_twiddles(N, tw.data());
+            if (cudaMalloc(&s->twid, (size_t)N * sizeof(float2)) != cudaSuccess ||
+                cudaMemcpy(s->twid, tw.data(), (size_t)N * sizeof(float2), cudaMemcpyHostToDevice) !=
+                    cudaSuccess) {
+                (void)cudaGetLastError();
+                release(*s);
+                err = "PM twiddle table allocation failed";
+                return PG_ENOMEM;
+            }
         }
-        s->have_r2c = true;
-        int dims[3] = {N, N, N};
-        if (cufftPlanMany(&s->c2r, 3, dims, nullptr, 1, (int)M, nullptr, 1, (int)N3, CUFFT_C2R, 4) !=
-            CUFFT_SUCCESS) {
-            release(*s);
-            err = "cufftPlanMany failed";
-            return PG_ECUDA;
-        }
-        s->have_c2r = true;
         s->N = N;
         s->split = -1;
     }
@@ -379,11 +386,47 @@ void deposit(PmState *s, const int4 *mj, const float4 *md, long long n, float *r
     if (launches) *launches += 1;
 }
 
+// the cuFFT plans of the mesh (made on first use)
+int lib_plans(PmState *s, std::string &err)
+{
+    if (s->have_r2c && s->have_c2r) return PG_OK;
+    const int N = s->N;
+    const long long N3 = (long long)N * N * N, M = (long long)N * N * (N / 2 + 1);
+    if (!s->have_r2c) {
+        if (cufftPlan3d(&s->r2c, N, N, N, CUFFT_R2C) != CUFFT_SUCCESS) {
+            err = "cufftPlan3d failed";
+            return PG_ECUDA;
+        }
+        s->have_r2c = true;
+    }
+    int dims[3] = {N, N, N};
+    if (cufftPlanMany(&s->c2r, 3, dims, nullptr, 1, (int)M, nullptr, 1, (int)N3, CUFFT_C2R, 4) != CUFFT_SUCCESS) {
+        err = "cufftPlanMany failed";
+        return PG_ECUDA;
+    }
+    s->have_c2r = true;
+    return PG_OK;
+}
+
 // rho -> the four fields (FFT, Green's function, batched inverse FFT)
 int solve_fields(PmState *s, float *rho, cudaStream_t st, int *launches, std::string &err)
 {
     const int N = s->N;
     const long long M = (long long)N * N * (N / 2 + 1);
+    if (s->fft_mode == 0 && fft_mesh_ok(N)) {
+        const cudaError_t e = fft_solve(rho, s->field, s->rk, s->spec, s->twid, s->gtab, s->wtab,
+                                        (float)(2.0 * M_PI / s->L), N, st);
+        if (e != cudaSuccess) {
+            err = cudaGetErrorString(e);
+            return PG_ECUDA;
+        }
+        if (launches) *launches += 5;
+        s->last_fft = 1;
+        return PG_OK;
+    }
+    int rc = lib_plans(s, err);
+    if (rc) return rc;
+    s->last_fft = 2;
     if (cufftSetStream(s->r2c, st) != CUFFT_SUCCESS || cufftSetStream(s->c2r, st) != CUFFT_SUCCESS) {
         err = "cufftSetStream failed";
         return PG_ECUDA;
