@@ -61,16 +61,27 @@ namespace {
 __device__ __forceinline__ int wrap_index(int j, int N) { return j < 0 ? j + N : j >= N ? j - N : j; }
 
 // one coordinate in mesh units: the nearest mesh point j0 in [0, N) and the
-// offset d = u - j0 in [-1/2, 1/2] of u = x / h (FP64; the wrap into the
-// box costs a division only for a coordinate outside it)
-__device__ __forceinline__ int mesh_axis(double x, double inv_h, int N, float &d)
+// offset d = u - j0 in [-1/2, 1/2] of u = x / h. u is formed in 32.32 fixed
+// point, t = u 2^32 rounded to an integer (one FP64 multiply by 2^32 / h and
+// one conversion: GB300 issues FP64 at about two operations per SM-clock),
+// wrapped into [0, N 2^32) with integer arithmetic; j0 = floor(u + 1/2)
+// and d come from t's integer and fraction bits. d is within 2^-33 of the
+// FP64 offset, far below its own FP32 rounding. Coordinates up to 2^29
+// boxes from the origin are wrapped exactly; farther ones are reduced in
+// FP64 first.
+__device__ __forceinline__ int mesh_axis(double x, double scale32, int N, float &d)
 {
-    double u = x * inv_h;
-    if (u < 0.0 || u >= (double)N) u -= N * floor(u / N);
-    const double j0 = floor(u + 0.5);
-    d = (float)(u - j0);
-    const int j = (int)j0;
-    return j >= N ? j - N : j;
+    const long long P = (long long)N << 32;             // the box in fixed point
+    double u = x * scale32;
+    if (!(fabs(u) < 0x1p61)) u -= (double)P * floor(u / (double)P);
+    long long t = __double2ll_rn(u);
+    if (t < 0 || t >= P) {
+        t %= P;
+        if (t < 0) t += P;
+    }
+    const long long j = (t + (1LL << 31)) >> 32;
+    d = (float)(int)(t - (j << 32)) * 0x1p-32f;
+    return (int)(j >= N ? j - N : j);
 }
 
 __device__ __forceinline__ void tsc_weights(float d, float w[3])
@@ -108,7 +119,7 @@ __global__ void k_pm_assign(const int4 *__restrict__ mj, const float4 *__restric
 // mesh order: a record's key is the row-major index of its nearest mesh
 // point, so that neighbouring threads share stencil points; the mesh record
 // (point; offsets and mass) is written here once, in input order
-__global__ void k_pm_keys(const double4 *__restrict__ rec, long long n, double inv_h, int N,
+__global__ void k_pm_keys(const double4 *__restrict__ rec, long long n, double scale32, int N,
                           unsigned *__restrict__ keys, unsigned *__restrict__ vals, int4 *__restrict__ mj,
                           float4 *__restrict__ md)
 {
@@ -116,8 +127,8 @@ __global__ void k_pm_keys(const double4 *__restrict__ rec, long long n, double i
     if (i >= n) return;
     const double4 v = rec[i];
     float dx, dy, dz;
-    const int jx = mesh_axis(v.x, inv_h, N, dx), jy = mesh_axis(v.y, inv_h, N, dy),
-              jz = mesh_axis(v.z, inv_h, N, dz);
+    const int jx = mesh_axis(v.x, scale32, N, dx), jy = mesh_axis(v.y, scale32, N, dy),
+              jz = mesh_axis(v.z, scale32, N, dz);
     keys[i] = ((unsigned)jx * (unsigned)N + (unsigned)jy) * (unsigned)N + (unsigned)jz;
     vals[i] = (unsigned)i;
     mj[i] = make_int4(jx, jy, jz, 0);
@@ -353,8 +364,8 @@ cudaError_t records(PmState *s, const double4 *rec, long long n, bool sorted, in
                     const unsigned *order = nullptr)
 {
     const int N = s->N;
-    k_pm_keys<<<blocks256(n), 256, 0, st>>>(rec, n, N / s->L, N, sort.keys[0], sort.vals[0], s->mj_raw,
-                                            s->md_raw);
+    k_pm_keys<<<blocks256(n), 256, 0, st>>>(rec, n, std::ldexp(N / s->L, 32), N, sort.keys[0], sort.vals[0],
+                                            s->mj_raw, s->md_raw);
     if (launches) *launches += 1;
     if (!sorted) return cudaGetLastError();
     const unsigned *perm = order;
