@@ -233,26 +233,26 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_y(float2 *__restrict__ spec
             for (int r = 0; r < R1; ++r) base[(long long)r * H + t] = v[r];
         }
     } else {
-    for (int t = tid; t < R2 * C; t += T) {
-        const int c = t & (C - 1), j = t >> lgC;
-        float2 v[R1];
+        for (int t = tid; t < R2 * C; t += T) {
+            const int c = t & (C - 1), j = t >> lgC;
+            float2 v[R1];
 #pragma unroll
-        for (int r = 0; r < R1; ++r) v[r] = base[(long long)(j + r * R2) * H + c];
-        dft<R1, false>(v);
+            for (int r = 0; r < R1; ++r) v[r] = base[(long long)(j + r * R2) * H + c];
+            dft<R1, false>(v);
 #pragma unroll
-        for (int r = 0; r < R1; ++r) b0[(j * R1 + r) * S + c] = v[r];
-    }
-    __syncthreads();
-    for (int t = tid; t < R1 * C; t += T) {
-        const int c = t & (C - 1), j = t >> lgC;
-        float2 v[R2];
+            for (int r = 0; r < R1; ++r) b0[(j * R1 + r) * S + c] = v[r];
+        }
+        __syncthreads();
+        for (int t = tid; t < R1 * C; t += T) {
+            const int c = t & (C - 1), j = t >> lgC;
+            float2 v[R2];
 #pragma unroll
-        for (int r = 0; r < R2; ++r) v[r] = b0[(j + r * R1) * S + c];
-        twiddle<R2, false>(v, j, tw, N / len);
-        dft<R2, false>(v);
+            for (int r = 0; r < R2; ++r) v[r] = b0[(j + r * R1) * S + c];
+            twiddle<R2, false>(v, j, tw, N / len);
+            dft<R2, false>(v);
 #pragma unroll
-        for (int r = 0; r < R2; ++r) base[(long long)(j + r * R1) * H + c] = v[r];
-    }
+            for (int r = 0; r < R2; ++r) base[(long long)(j + r * R1) * H + c] = v[r];
+        }
     }
 }
 
