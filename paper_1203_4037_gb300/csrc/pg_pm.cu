@@ -26,6 +26,7 @@
 #include <cufft.h>
 
 #include <cmath>
+#include <cstdint>
 #include <string>
 #include <vector>
 
@@ -91,8 +92,38 @@ __device__ __forceinline__ void tsc_weights(float d, float w[3])
     w[2] = 0.5f * (0.5f + d) * (0.5f + d);
 }
 
+// the three cells z0 - 1 .. z0 + 1 of one stencil row with weights w0, w1,
+// w2: vector atomics on the aligned groups of four cells that hold them
+// (one or two; the other lanes add +0, which leaves a cell unchanged), or
+// three scalar atomics when the row wraps around the box or vec is off (the
+// host sets it when N is a multiple of four and the mesh 16-byte aligned,
+// so that every row is)
+__device__ __forceinline__ void deposit_row(float *__restrict__ row, int zc, int N, bool vec, float w0, float w1,
+                                            float w2)
+{
+    if (!vec || zc < 0 || zc + 2 >= N) {
+        atomicAdd(row + wrap_index(zc, N), w0);
+        atomicAdd(row + wrap_index(zc + 1, N), w1);
+        atomicAdd(row + wrap_index(zc + 2, N), w2);
+        return;
+    }
+    const int a4 = zc & ~3, o = zc - a4;
+    float4 *g = reinterpret_cast<float4 *>(row + a4);
+    if (o == 0) {
+        atomicAdd(g, make_float4(w0, w1, w2, 0.0f));
+    } else if (o == 1) {
+        atomicAdd(g, make_float4(0.0f, w0, w1, w2));
+    } else if (o == 2) {
+        atomicAdd(g, make_float4(0.0f, 0.0f, w0, w1));
+        atomicAdd(g + 1, make_float4(w2, 0.0f, 0.0f, 0.0f));
+    } else {
+        atomicAdd(g, make_float4(0.0f, 0.0f, 0.0f, w0));
+        atomicAdd(g + 1, make_float4(w1, w2, 0.0f, 0.0f));
+    }
+}
+
 __global__ void k_pm_assign(const int4 *__restrict__ mj, const float4 *__restrict__ md, long long n, int N,
-                            float vinv, float *__restrict__ rho)
+                            float vinv, float *__restrict__ rho, int vec)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -110,8 +141,7 @@ __global__ void k_pm_assign(const int4 *__restrict__ mj, const float4 *__restric
         for (int b = 0; b < 3; ++b) {
             const long long row = (ix * N + wrap_index(j.y + b - 1, N)) * N;
             const float wab = mv * wx[a] * wy[b];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) atomicAdd(rho + row + wrap_index(j.z + c - 1, N), wab * wz[c]);
+            deposit_row(rho + row, j.z - 1, N, vec != 0, wab * wz[0], wab * wz[1], wab * wz[2]);
         }
     }
 }
@@ -393,7 +423,8 @@ void deposit(PmState *s, const int4 *mj, const float4 *md, long long n, float *r
     const long long N3 = (long long)N * N * N;
     const float vinv = (float)((double)N3 / (s->L * s->L * s->L));     // 1 / h^3
     cudaMemsetAsync(rho, 0, N3 * sizeof(float), st);
-    k_pm_assign<<<blocks256(n), 256, 0, st>>>(mj, md, n, N, vinv, rho);
+    const int vec = (N % 4 == 0 && ((uintptr_t)rho & 15) == 0) ? 1 : 0;
+    k_pm_assign<<<blocks256(n), 256, 0, st>>>(mj, md, n, N, vinv, rho, vec);
     if (launches) *launches += 1;
 }
 

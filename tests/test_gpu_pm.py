@@ -242,3 +242,35 @@ def test_pp_plus_pm_under_a_graph(pg, orc):
                 c.run()
             out.append(c.get_force(len(x))[0])
     assert_mesh_parity(out[1], out[0], "graph")
+
+
+def test_deposit_scalar_paths(pg):
+    # the deposit adds a stencil row with vector atomics only when the mesh
+    # side is a multiple of four and the mesh 16-byte aligned: a side of 18,
+    # and a mesh that starts 4 bytes into its buffer, take the scalar atomics
+    torch = pytest.importorskip("torch")
+    x, m = gen.clustered_box(6000, 68, nclump=10, sigma=0.03)
+    with pg.Context(0) as c:
+        c.set_periodic(1.0)
+        c.set_pm(18, pg.PG_SPLIT_GAUSS, 1.5 / 18)
+        a, p = c.pm_forces(x, m)
+    ao, po = opm.mesh_forces(x, m, 1.0, 18, "gauss", 1.5 / 18)
+    assert_mesh_parity(a, ao, "N = 18")
+    assert_mesh_parity(p[:, None], po[:, None], "N = 18 phi")
+    N = 32
+    dev = torch.device("cuda:0")
+    xd, md = torch.tensor(x, device=dev), torch.tensor(m, device=dev)
+    with pg.Context(0) as c:
+        c.set_periodic(1.0)
+        c.set_pm(N, pg.PG_SPLIT_GAUSS, 1.25 / N)
+        r_al = torch.empty(N ** 3, dtype=torch.float32, device=dev)
+        r_mis = torch.empty(N ** 3 + 1, dtype=torch.float32, device=dev)[1:]
+        assert r_mis.data_ptr() % 16 == 4
+        c.pm_deposit_dev(xd, md, r_al)
+        c.pm_deposit_dev(xd, md, r_mis)
+        torch.cuda.synchronize()
+    ra, rm = r_al.cpu().numpy(), r_mis.cpu().numpy()
+    ro = opm.deposit(x, m, 1.0, N).ravel()
+    # FP32 atomics in any order: each cell within a few roundings of its sum
+    scale = np.abs(ro).max()
+    assert np.abs(ra - ro).max() <= 1e-5 * scale and np.abs(rm - ro).max() <= 1e-5 * scale
