@@ -74,6 +74,8 @@ def parse():
                     help="tree workload: the particle set")
     ap.add_argument("--quadrupole", action="store_true",
                     help="tree workload: quadrupole pseudo-particles")
+    ap.add_argument("--level-walk", action="store_true",
+                    help="tree workload: the level walk instead of the group walk")
     ap.add_argument("--ncrit", type=int, default=TREE_NCRIT, help="tree workload: group size bound")
     return ap.parse_args()
 
@@ -675,6 +677,8 @@ def run_row(args):
             c.set_self(True)
             c.set_timing(True)
             c.set_tree(0.75, args.ncrit, 8, quadrupole=args.quadrupole)
+            if args.level_walk:
+                c.set_tree_walk(pg.PG_TREE_WALK_LEVEL)
             c.set_j_dev(xd, md)
             c.set_i_dev(xd)
             kms = _time_kernel(c, lambda: c.run_dev(a), reps=args.steps, warm=args.warmup)
