@@ -109,7 +109,7 @@ struct pg_ctx {
            TB_CHILD0, TB_CHILDN, TB_LEV, TB_M, TB_S, TB_GAT, TB_GSCAN, TB_GI0, TB_GNI, TB_GBOX,
            TB_IOFF, TB_JCOUNT, TB_JOFF, TB_JLIST, TB_JREC2, TB_ITEMOFF, TB_ITEMS,
            TB_VG, TB_VK, TB_VE, TB_VC, TB_VSUMS, TB_SEG, TB_BASE, TB_GBOXF, TB_NODEW,
-           TB_FILT, TB_COM, TB_T, TB_BIG, TB_NBIG, TB_TSUMS, TB_HL, TB_N };
+           TB_FILT, TB_COM, TB_T, TB_BIG, TB_NBIG, TB_TSUMS, TB_HL, TB_WSCR, TB_EMIT, TB_GEMIT, TB_N };
     DevBuf tb[TB_N];
     long long tree_sizes[6] = {0, 0, 0, 0, 0, 0};
     // the room the last exact tree call left (nodes, groups, list entries),
@@ -1902,6 +1902,15 @@ int tree_call(pg_ctx *c, double *acc, double *pot, bool exact, bool *redo, int &
     if (!exact && ((rc = tree_node_bufs(c, t, n)) || (rc = tree_group_bufs(c, t, n, Bi)) ||
                    (rc = tbuf(c, pg_ctx::TB_JLIST, std::max(t.cap_list, 1LL) * 4, t.jlist))))
         return rc;
+    if (!exact) {
+        // the count pass records each group's decisions for the fill pass:
+        // its emitters never outnumber its list entries
+        t.emit_cap = std::max(t.cap_list, 1LL);
+        if ((rc = tbuf(c, pg_ctx::TB_EMIT, t.emit_cap * 4, t.emit)) ||
+            (rc = tbuf(c, pg_ctx::TB_WSCR, group_walk_warps(c->sms) * kGroupWalkScratch * 4, t.wscratch)) ||
+            (rc = tbuf(c, pg_ctx::TB_GEMIT, std::max(t.cap_groups, 1LL) * 8, t.gemit)))
+            return rc;
+    }
     PG_CUDA(c, cudaMemsetAsync(t.meta, 0, sizeof(TreeMeta), c->stream));
     TreeMeta h{};
 

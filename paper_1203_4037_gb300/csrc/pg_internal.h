@@ -361,6 +361,7 @@ struct TreeMeta {
     unsigned nitems;            // its work items
     unsigned next[2];           // group walk: claim counters (count, fill pass)
     unsigned qmax;              // group walk: most opened nodes one level held
+    unsigned emit_next;         // group walk: emitters placed so far
     int flags;                  // kTree* bits
 };
 constexpr int kTreeRoomNodes = 1;    // nodes beyond the room
@@ -373,6 +374,8 @@ constexpr int kTreeRoomMask = kTreeRoomNodes | kTreeRoomGroups | kTreeRoomList;
 // opened nodes one warp's walk holds per level (the 2^20-particle Plummer
 // and King W0 = 9 trees at theta = 0.75 open at most 66)
 constexpr int kGroupWalkQ = 512;
+// emitters (accepted nodes, leaves) one warp records for its group
+constexpr int kGroupWalkScratch = 4096;
 
 struct TreeScratch {
     unsigned long long *bbox;   // 6: ordered-int min and max per axis
@@ -384,6 +387,13 @@ struct TreeScratch {
     TreeMeta *meta;             // the call's counts
     long long cap_nodes, cap_groups, cap_list;   // the room given to nodes, groups, list entries
     long long hint_runs[11];    // nodes per level of the last call: grid sizes only
+    // the group walk's recorded decisions (nullptr: not recorded): per warp a
+    // scratch of kGroupWalkScratch emitters, the emitters of every group
+    // (emit_cap room), and per group its (first emitter, count), first = -1
+    // where the fill pass walks again
+    unsigned *wscratch, *emit;
+    long long emit_cap;
+    int2 *gemit;
     int *first, *count, *child0, *childn;   // nnodes
     unsigned char *lev;         // nnodes
     double *M, *S;              // nnodes, 3 nnodes
@@ -434,6 +444,8 @@ cudaError_t tree_walk_prep(double theta, TreeScratch &t, cudaStream_t st);
 // (fill = false), then the fill pass writing jlist
 cudaError_t tree_group_walk(bool fill, long long n, double theta, int nleaf, int sms, TreeScratch &t,
                             SortScratch &sort, int *status, cudaStream_t st);
+// warps of the group walk's grid (the emitter scratch holds one slice each)
+long long group_walk_warps(int sms);
 // the level walk (all groups level by level; sizes from the host): init
 // puts every group at the root; level L decides its frontier (visits
 // [o, o + nf)) and scans the opened children, whose count is vc[nf]; expand

@@ -781,6 +781,14 @@ struct GroupWalkArgs {
     const long long *j_off;    // fill pass: the list offsets
     int *jlist;                // fill pass: the lists
     int *status;               // fill pass: an entry outside its group's list
+    // the count pass's record of each group's emitting nodes, in list order
+    // (bit 31 set: accepted, its pseudo-particles; clear: a leaf, its
+    // particles), which the fill pass expands instead of walking again;
+    // emit == nullptr: not recorded
+    unsigned *wscratch;        // kGroupWalkScratch per warp of the grid
+    unsigned *emit;            // emit_cap: every group's emitters
+    long long emit_cap;
+    int2 *gemit;               // per group: first emitter and count (first -1: walk again)
 };
 
 __device__ __forceinline__ unsigned warp_incl_scan(unsigned v, int lane)
@@ -791,6 +799,60 @@ __device__ __forceinline__ unsigned warp_incl_scan(unsigned v, int lane)
         if (lane >= o) v += y;
     }
     return v;
+}
+
+// the end of a group's count pass: its nemit emitters (in the warp's
+// scratch) get a slice of the emitter array, or first = -1 when they
+// overflowed the scratch or the array's room (the fill pass then walks the
+// group again)
+__device__ __forceinline__ void place_emitters(const GroupWalkArgs &a, TreeMeta *m, const unsigned *scr,
+                                               unsigned nemit, long long g, int lane)
+{
+    __syncwarp();                           // every lane's scratch writes visible
+    long long first = -1;
+    if (nemit <= (unsigned)kGroupWalkScratch) {
+        unsigned long long f = 0;
+        if (lane == 0) f = atomicAdd(&m->emit_next, nemit);
+        f = __shfl_sync(0xffffffffu, f, 0);
+        // the first emitter is kept as an int
+        if (f + nemit <= (unsigned long long)min(a.emit_cap, 0x7fffffffLL)) first = (long long)f;
+    }
+    if (first >= 0)
+        for (unsigned t = lane; t < nemit; t += 32) a.emit[first + t] = scr[t];
+    if (lane == 0) a.gemit[g] = make_int2(first >= 0 ? (int)first : -1, (int)nemit);
+    __syncwarp();
+}
+
+// the fill pass of a recorded group: its cnt emitters from emit[first]
+// expanded into list entries from pos, in order
+__device__ __forceinline__ void expand_emitters(const GroupWalkArgs &a, int first, int cnt, long long pos,
+                                                long long hi, int lane)
+{
+    for (int b = 0; b < cnt; b += 32) {
+        unsigned e = 0;
+        int p0 = 0;
+        if (b + lane < cnt) {
+            const unsigned code = a.emit[first + b + lane];
+            const int k = (int)(code & 0x7fffffffu);
+            if (code >> 31) {
+                e = (unsigned)a.npseudo;
+                p0 = (int)(a.n + (long long)a.npseudo * k);
+            } else {
+                const TreeNodeW nd = a.nodew[k];
+                e = (unsigned)nd.count;
+                p0 = nd.first;
+            }
+        }
+        const unsigned ei = warp_incl_scan(e, lane);
+        if (e) {
+            const long long d = pos + (ei - e);
+            if (d + e > hi) report(a.status, kStatusBadIndex, 13);
+            else
+                for (unsigned t = 0; t < e; ++t) a.jlist[d + t] = p0 + (int)t;
+        }
+        pos += __shfl_sync(0xffffffffu, ei, 31);
+    }
+    if (pos != hi && lane == 0) report(a.status, kStatusBadIndex, 12);
 }
 
 template <bool FILL>
@@ -808,6 +870,9 @@ __global__ void __launch_bounds__(32 * kGwWarps) k_walk_groups(GroupWalkArgs a)
     unsigned long long ent = 0;
     unsigned qmax = 0;
     bool over = false;
+    unsigned *scr = !FILL && a.emit
+                        ? a.wscratch + ((long long)blockIdx.x * kGwWarps + w) * kGroupWalkScratch
+                        : nullptr;
     for (;;) {
         unsigned gq = 0;
         if (lane == 0) gq = *(volatile int *)&m->flags ? 0xffffffffu : atomicAdd(&m->next[FILL ? 1 : 0], 1u);
@@ -818,6 +883,15 @@ __global__ void __launch_bounds__(32 * kGwWarps) k_walk_groups(GroupWalkArgs a)
         const double *bx = a.gbox + 6 * g;
         const long long lo = FILL ? a.j_off[g] : 0, hi = FILL ? a.j_off[g + 1] : 0;
         long long pos = lo;
+        if (FILL && a.emit) {
+            // the count pass recorded this group's emitters: expand them
+            const int2 ge = a.gemit[g];
+            if (ge.x >= 0) {
+                expand_emitters(a, ge.x, ge.y, pos, hi, lane);
+                continue;
+            }
+        }
+        unsigned nemit = 0;
         unsigned *cur = qa, *nxt = qb;
         unsigned ncur = 1;
         if (lane == 0) cur[0] = 0u;          // the root: one child, node 0
@@ -870,6 +944,13 @@ __global__ void __launch_bounds__(32 * kGwWarps) k_walk_groups(GroupWalkArgs a)
                                 nxt[slot] = ((unsigned)nd[u].child0 << 3) | (unsigned)(nd[u].childn - 1);
                         }
                         nnext += __popc(om);
+                        if (!FILL && scr) {      // record the chunk's emitters in order
+                            const unsigned em = __ballot_sync(0xffffffffu, e[u] != 0u);
+                            const unsigned slot = nemit + __popc(em & below);
+                            if (e[u] && slot < (unsigned)kGroupWalkScratch)
+                                scr[slot] = acc[u] ? (0x80000000u | (unsigned)k[u]) : (unsigned)k[u];
+                            nemit += __popc(em);
+                        }
                         const unsigned ei = warp_incl_scan(e[u], lane);
                         if (FILL && e[u]) {
                             const long long d = pos + (ei - e[u]);
@@ -904,6 +985,7 @@ __global__ void __launch_bounds__(32 * kGwWarps) k_walk_groups(GroupWalkArgs a)
         } else {
             if (lane == 0) a.jcount[g] = (unsigned)pos;
             ent += (unsigned long long)pos;
+            if (scr) place_emitters(a, m, scr, nemit, g, lane);
         }
     }
     if (lane == 0) {
@@ -1245,6 +1327,10 @@ cudaError_t tree_group_walk(bool fill, long long n, double theta, int nleaf, int
     a.j_off = t.j_off;
     a.jlist = t.jlist;
     a.status = status;
+    a.wscratch = t.wscratch;
+    a.emit = t.emit;
+    a.emit_cap = t.emit_cap;
+    a.gemit = t.gemit;
     const unsigned grid = (unsigned)std::max(1, sms * gw_blocks_per_sm());
     if (fill) {
         k_walk_groups<true><<<grid, 32 * kGwWarps, 0, st>>>(a);
@@ -1259,6 +1345,8 @@ cudaError_t tree_group_walk(bool fill, long long n, double theta, int nleaf, int
     t.launches += 2;
     return cudaGetLastError();
 }
+
+long long group_walk_warps(int sms) { return (long long)std::max(1, sms * gw_blocks_per_sm()) * kGwWarps; }
 
 cudaError_t tree_walk_init(long long ngroups, TreeScratch &t, cudaStream_t st)
 {

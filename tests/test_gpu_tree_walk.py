@@ -183,3 +183,23 @@ def test_keys_on_and_beside_cell_edges(pg, orc):
         ao, po = orc.tree_forces(x, m, 1e-3, theta, 32, 4)
         assert_parity(rel_vec(a, ao), what="a")
         assert_parity(rel_scalar(p, po), what="phi")
+
+
+def test_recorded_and_rewalked_groups(pg, orc):
+    # a call from room replays the count pass's recorded emitters (accepted
+    # nodes and leaves) in the fill pass; a group with more than 4096 of them
+    # (186 of the 1149 groups here, theta = 0.3) is walked again instead. The
+    # lists of both kinds equal the oracle's
+    x, m = gen.plummer(20000, 7108)
+    o = orc.tree_build(x, m, 0.3, 64, 8)
+    assert np.max(np.diff(o["j_off"])) > 4096
+    with pg.Context(0) as c:
+        c.set_eps(1e-3)
+        c.set_self(True)
+        c.set_tree(0.3, 64, 8)
+        a1, p1, t1, s1 = run_once(pg, c, x, m)
+        a2, p2, t2, s2 = run_once(pg, c, x, m)
+    assert s1["exact"] == 1 and s2["exact"] == 0 and s2["walk"] == 1
+    same_lists(t1, o)
+    same_lists(t2, o)
+    assert np.array_equal(a1, a2) and np.array_equal(p1, p2)
