@@ -33,6 +33,11 @@ struct PinBuf {
 struct pg_ctx {
     int device = 0;
     cudaStream_t own_stream = nullptr;
+    // the tree call's second stream (the moments chain and the record
+    // packing beside the groups and the walk) and its events: links built,
+    // moments done, j records packed
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t tree_ev[3] = {nullptr, nullptr, nullptr};
     cudaStream_t stream = nullptr;
     int sms = 0;
 
@@ -486,6 +491,9 @@ void pg_destroy(pg_ctx *c)
     if (c->tk0) cudaEventDestroy(c->tk0);
     if (c->tk1) cudaEventDestroy(c->tk1);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    if (c->side_stream) cudaStreamDestroy(c->side_stream);
+    for (cudaEvent_t e : c->tree_ev)
+        if (e) cudaEventDestroy(e);
     delete c;
 }
 
@@ -1911,6 +1919,14 @@ int tree_call(pg_ctx *c, double *acc, double *pot, bool exact, bool *redo, int &
             (rc = tbuf(c, pg_ctx::TB_GEMIT, std::max(t.cap_groups, 1LL) * 8, t.gemit)))
             return rc;
     }
+    if (!c->side_stream) {
+        PG_CUDA(c, cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking));
+        for (cudaEvent_t &e : c->tree_ev) PG_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        PG_CUDA(c, cudaEventRecord(c->tree_ev[2], c->side_stream));
+    }
+    // nothing of an earlier call (one that returned between its fork and
+    // join) still runs on the side stream
+    PG_CUDA(c, cudaStreamWaitEvent(c->stream, c->tree_ev[2], 0));
     PG_CUDA(c, cudaMemsetAsync(t.meta, 0, sizeof(TreeMeta), c->stream));
     TreeMeta h{};
 
@@ -1925,16 +1941,28 @@ int tree_call(pg_ctx *c, double *acc, double *pot, bool exact, bool *redo, int &
         for (int L = 0; L < 11; ++L) t.hint_runs[L] = h.lev_off[L + 1] - h.lev_off[L];
         if ((rc = tree_node_bufs(c, t, n))) return rc;
     }
-    // nodes, moments, groups
-    PG_CUDA(c, tree_stage_nodes(n, c->tree_ncrit, t, c->sort, c->stream));
+    // node links; then the moments, the pseudo-particles and the records'
+    // double-float packing on the side stream, beside the groups and the walk
+    // (which waits for the moments only; the force kernel for the packing)
+    PG_CUDA(c, tree_stage_links(n, t, c->stream));
+    PG_CUDA(c, cudaEventRecord(c->tree_ev[0], c->stream));
+    PG_CUDA(c, cudaStreamWaitEvent(c->side_stream, c->tree_ev[0], 0));
+    PG_CUDA(c, tree_stage_moments(n, t, c->side_stream));
+    PG_CUDA(c, cudaEventRecord(c->tree_ev[1], c->side_stream));
+    PG_CUDA(c, tree_stage_jrec(n, c->sms, t, c->side_stream));
+    const long long nj_room = n + P * (exact ? h.nnodes : t.cap_nodes);
+    PG_CUDA(c, launch_pack_hilo(t.jrec2, nj_room, (float4 *)c->g_jhl.p, c->side_stream));
+    PG_CUDA(c, cudaEventRecord(c->tree_ev[2], c->side_stream));
+    c->jhl_n = -1;      // the buffer now holds the tree's records
+    PG_CUDA(c, tree_stage_groups(n, c->tree_ncrit, t, c->sort, c->stream));
     if (exact) {
         ++reads;
         if ((rc = read_dev(c, &h, t.meta, sizeof h))) return rc;
         t.cap_groups = tree_room(h.ngroups, n);
         if ((rc = tree_group_bufs(c, t, n, Bi))) return rc;
     }
-    PG_CUDA(c, tree_stage_jrec(n, c->sms, t, c->stream));
     PG_CUDA(c, tree_walk_prep(c->tree_theta, t, c->stream));
+    PG_CUDA(c, cudaStreamWaitEvent(c->stream, c->tree_ev[1], 0));
     // the walk
     int walk = 1;
     if (!exact || c->tree_walk_mode == PG_TREE_WALK_AUTO)
@@ -1961,11 +1989,9 @@ int tree_call(pg_ctx *c, double *acc, double *pot, bool exact, bool *redo, int &
     if (walk == 1)
         PG_CUDA(c, tree_group_walk(true, n, c->tree_theta, c->tree_nleaf, c->sms, t, c->sort,
                                    (int *)c->status.p, c->stream));
-    // work items, the double-float records, the groups' centres, the forces
+    // work items, then (with the packed records) the forces
     PG_CUDA(c, tree_stage_records(Bi, t, c->sort, c->stream));
-    const long long nj_room = n + P * (exact ? h.nnodes : t.cap_nodes);
-    PG_CUDA(c, launch_pack_hilo(t.jrec2, nj_room, (float4 *)c->g_jhl.p, c->stream));
-    c->jhl_n = -1;      // the buffer now holds the tree's records
+    PG_CUDA(c, cudaStreamWaitEvent(c->stream, c->tree_ev[2], 0));
     // the i records' double-float pairs: the j records' own (the first n are
     // the particles in key order), unless the kernel reads each i's eps^2
     // from the i pair's w (eps = 0), which the j pair holds its mass in

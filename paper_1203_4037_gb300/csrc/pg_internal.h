@@ -434,8 +434,11 @@ struct TreeScratch {
 // keys: sort, every level's runs, level offsets and node count
 cudaError_t tree_stage_keys(const double4 *jrec, long long n, TreeScratch &t, SortScratch &sort,
                             cudaStream_t st);
-// nodes, moments (monopole records; second moments), groups
-cudaError_t tree_stage_nodes(long long n, int ncrit, TreeScratch &t, SortScratch &sort, cudaStream_t st);
+// node starts, counts and children; then, independent of each other, the
+// moments (with the monopole records and second moments) and the groups
+cudaError_t tree_stage_links(long long n, TreeScratch &t, cudaStream_t st);
+cudaError_t tree_stage_moments(long long n, TreeScratch &t, cudaStream_t st);
+cudaError_t tree_stage_groups(long long n, int ncrit, TreeScratch &t, SortScratch &sort, cudaStream_t st);
 // the j records: particles in key order, pseudo-particles
 cudaError_t tree_stage_jrec(long long n, int sms, TreeScratch &t, cudaStream_t st);
 // the groups' boxes and the walk's FP32 pre-test bounds (both walks)

@@ -1266,14 +1266,21 @@ cudaError_t tree_stage_keys(const double4 *jrec, long long n, TreeScratch &t, So
     return cudaGetLastError();
 }
 
-cudaError_t tree_stage_nodes(long long n, int ncrit, TreeScratch &t, SortScratch &sort, cudaStream_t st)
+// node starts, counts and children (every level)
+cudaError_t tree_stage_links(long long n, TreeScratch &t, cudaStream_t st)
 {
     const unsigned wide = blocks_of(widest_hint(t));
     k_tree_starts<<<dim3(blocks_of(n), kLevels), 256, 0, st>>>(t.meta, t.key, t.scan, n, t.first);
     k_tree_nodes<<<dim3(wide, kLevels), 256, 0, st>>>(t.meta, n, t.scan, t.first, t.count, t.child0, t.childn,
                                                       t.lev);
-    // moments bottom-up, with each node's centre, walk record and (quadrupole)
-    // second moment
+    t.launches += 2;
+    return cudaGetLastError();
+}
+
+// moments bottom-up, with each node's centre, walk record and (quadrupole)
+// second moment
+cudaError_t tree_stage_moments(long long n, TreeScratch &t, cudaStream_t st)
+{
     NodeOut no{t.com, t.npseudo == 1 ? t.jrec2 + n : nullptr, t.nodew, t.npseudo == 3 ? t.T : nullptr};
     k_tree_moments_leaf<<<blocks_of(t.hint_runs[kLevels - 1]), 256, 0, st>>>(t.meta, t.first, t.count, t.child0,
                                                                              t.childn, t.xs, t.M, t.S, no);
@@ -1287,11 +1294,18 @@ cudaError_t tree_stage_nodes(long long n, int ncrit, TreeScratch &t, SortScratch
                                                                      t.childn, t.M, t.S, no);
     if (L0 >= 0)
         k_tree_moments_top<<<1, 1024, 0, st>>>(t.meta, L0, t.first, t.count, t.child0, t.childn, t.M, t.S, no);
+    t.launches += 1 + (kLevels - 2 - L0) + (L0 >= 0 ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// the groups: marks at their first particle, numbered by a scan
+cudaError_t tree_stage_groups(long long n, int ncrit, TreeScratch &t, SortScratch &sort, cudaStream_t st)
+{
+    const unsigned wide = blocks_of(widest_hint(t));
     cudaMemsetAsync(t.gat, 0xff, n * sizeof(int), st);
     k_tree_group_marks<<<dim3(wide, kLevels), 256, 0, st>>>(t.meta, n, t.scan, t.first, t.count, ncrit, t.gat);
     k_tree_group_flags<<<blocks_of(n + 1), 256, 0, st>>>(t.gat, n, t.gscan);
-    // starts, nodes, leaf moments, the levels above, marks, flags, groups
-    t.launches += 3 + (kLevels - 2 - L0) + (L0 >= 0 ? 1 : 0) + 3;
+    t.launches += 3;         // marks, flags, groups
     cudaError_t e = scan(t, t.gscan, n + 1, sort.sums, st);
     if (e != cudaSuccess) return e;
     k_tree_groups<<<blocks_of(n + 1), 256, 0, st>>>(t.meta, t.cap_groups, t.gat, t.gscan, n, t.count, t.g_i0,
