@@ -293,7 +293,11 @@ int pg_set_table_pot_values(pg_ctx *ctx, const float *v, long long n);
 int pg_set_n(pg_ctx *ctx, long long nj);
 
 /* Store j-particles adr .. adr+nj-1 (g5_set_xmj, Section 3.6): positions
- * x (host double[nj][3]) and masses m (host double[nj]). Copies. */
+ * x (host double[nj][3]) and masses m (host double[nj]). Copies: the
+ * caller may reuse x and m when the call returns. Pageable memory is
+ * copied into the context's page-locked staging buffer and sent from there
+ * in stream order; page-locked (pinned) x and m are sent by DMA directly,
+ * and the call then waits for that copy (and the stream's earlier work). */
 int pg_set_j(pg_ctx *ctx, long long adr, long long nj, const double *x, const double *m);
 
 /* Device twin of pg_set_j: x (device double[nj][3]), m (device double[nj]). */
@@ -306,7 +310,8 @@ int pg_set_j_dev(pg_ctx *ctx, long long adr, long long nj, const double *x, cons
  * extension (the paper's API takes positions and masses apart). */
 int pg_set_j_rec_dev(pg_ctx *ctx, long long adr, long long nj, const double *rec);
 
-/* The i-particles of the next pg_run: x (host double[ni][3]). Copies. */
+/* The i-particles of the next pg_run: x (host double[ni][3]). Copies, as
+ * pg_set_j does (pinned x: by DMA, waited for). */
 int pg_set_i(pg_ctx *ctx, long long ni, const double *x);
 
 /* Device twin of pg_set_i. */
@@ -356,7 +361,9 @@ int pg_run(pg_ctx *ctx);
 
 /* Copy the last results to the host: a (double[ni][3]) and phi (double[ni],
  * may be NULL; zeros in PG_TABLE mode). Synchronises; returns PG_ETIMEOUT
- * if a device wait gave up. ni must equal the count given to pg_set_i. */
+ * if a device wait gave up. ni must equal the count given to pg_set_i.
+ * Page-locked (pinned) a and phi are written by DMA directly; others
+ * through the context's page-locked staging buffer. */
 int pg_get_force(pg_ctx *ctx, double *a, double *phi, long long ni);
 
 /* Enqueue one force evaluation writing device outputs: a (device

@@ -368,9 +368,21 @@ def pg_run(ctx):
     return _check(ctx, lib().pg_run(ctx))
 
 
-def pg_get_force(ctx, ni, want_phi=True):
-    a = np.empty((ni, 3), dtype=np.float64)
-    phi = np.empty(ni, dtype=np.float64) if want_phi else None
+def pg_get_force(ctx, ni, want_phi=True, out=None):
+    """The last results as (a, phi) numpy arrays; out = (a, phi) writes into
+    the caller's arrays (contiguous float64; phi may be None), which may be
+    page-locked, as from torch's pin_memory(), for a direct copy."""
+    if out is not None:
+        a, phi = out
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
+                and a.shape == (ni, 3)):
+            raise ValueError("out[0] must be a contiguous float64 array of shape (ni, 3)")
+        if phi is not None and not (isinstance(phi, np.ndarray) and phi.dtype == np.float64
+                                    and phi.flags.c_contiguous and phi.shape == (ni,)):
+            raise ValueError("out[1] must be a contiguous float64 array of shape (ni,) or None")
+    else:
+        a = np.empty((ni, 3), dtype=np.float64)
+        phi = np.empty(ni, dtype=np.float64) if want_phi else None
     _check(ctx, lib().pg_get_force(ctx, _ptr(a), _ptr(phi), int(ni)))
     return a, phi
 
@@ -675,8 +687,8 @@ class Context:
     def run(self):
         pg_run(self.h)
 
-    def get_force(self, ni, want_phi=True):
-        return pg_get_force(self.h, ni, want_phi)
+    def get_force(self, ni, want_phi=True, out=None):
+        return pg_get_force(self.h, ni, want_phi, out)
 
     def run_dev(self, a, phi=None):
         _require_dev(a, *([phi] if phi is not None else []))

@@ -238,6 +238,31 @@ int ensure(pg_ctx *c, DevBuf &b, size_t bytes)
     return PG_OK;
 }
 
+int ensure_pin(pg_ctx *c, PinBuf &b, size_t bytes);
+
+// host memory the device can reach by DMA (page-locked or registered)
+bool host_pinned(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost;
+}
+
+// a copy from the caller's page-locked memory, in stream order, finished
+// before the call returns (the caller may then reuse the memory)
+int copy_pinned_in(pg_ctx *c, void *dst, const void *src, size_t bytes, PinBuf &b)
+{
+    int rc;
+    if ((rc = ensure_pin(c, b, 0))) return rc;      // the event; earlier copies through b done
+    PG_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream));
+    PG_CUDA(c, cudaEventRecord(b.done, c->stream));
+    PG_CUDA(c, cudaEventSynchronize(b.done));
+    return PG_OK;
+}
+
 int ensure_pin(pg_ctx *c, PinBuf &b, size_t bytes)
 {
     if (!b.done) {
@@ -906,11 +931,19 @@ int pg_set_j(pg_ctx *c, long long adr, long long nj, const double *x, const doub
     int rc;
     if ((rc = grow_j(c, adr + nj))) return rc;
     size_t bx = (size_t)nj * 24, bm = (size_t)nj * 8;
-    if ((rc = ensure_pin(c, c->pin_j, bx + bm)) || (rc = ensure(c, c->stage, bx + bm))) return rc;
-    std::memcpy(c->pin_j.p, x, bx);
-    std::memcpy((char *)c->pin_j.p + bx, m, bm);
-    PG_CUDA(c, cudaMemcpyAsync(c->stage.p, c->pin_j.p, bx + bm, cudaMemcpyHostToDevice, c->stream));
-    PG_CUDA(c, cudaEventRecord(c->pin_j.done, c->stream));
+    if ((rc = ensure(c, c->stage, bx + bm))) return rc;
+    if (host_pinned(x) && host_pinned(m)) {
+        // page-locked input: DMA straight from it
+        if ((rc = copy_pinned_in(c, c->stage.p, x, bx, c->pin_j)) ||
+            (rc = copy_pinned_in(c, (char *)c->stage.p + bx, m, bm, c->pin_j)))
+            return rc;
+    } else {
+        if ((rc = ensure_pin(c, c->pin_j, bx + bm))) return rc;
+        std::memcpy(c->pin_j.p, x, bx);
+        std::memcpy((char *)c->pin_j.p + bx, m, bm);
+        PG_CUDA(c, cudaMemcpyAsync(c->stage.p, c->pin_j.p, bx + bm, cudaMemcpyHostToDevice, c->stream));
+        PG_CUDA(c, cudaEventRecord(c->pin_j.done, c->stream));
+    }
     const double *dx = (const double *)c->stage.p;
     PG_CUDA(c, launch_pack_j(dx, dx + 3 * nj, (double4 *)c->jrec.p + adr, nj, c->stream));
     c->nj_hw = std::max(c->nj_hw, adr + nj);
@@ -969,13 +1002,17 @@ int pg_set_i(pg_ctx *c, long long ni, const double *x)
     c->epsi_applied = false;   // new i records: eps^2 not yet in them
     if (ni == 0) return PG_OK;
     size_t bx = (size_t)ni * 24;
-    if ((rc = ensure_pin(c, c->pin_i, bx))) return rc;
     // the device staging area is only touched in stream order, so j and i
     // copies can share it
     if ((rc = ensure(c, c->stage, bx))) return rc;
-    std::memcpy(c->pin_i.p, x, bx);
-    PG_CUDA(c, cudaMemcpyAsync(c->stage.p, c->pin_i.p, bx, cudaMemcpyHostToDevice, c->stream));
-    PG_CUDA(c, cudaEventRecord(c->pin_i.done, c->stream));
+    if (host_pinned(x)) {
+        if ((rc = copy_pinned_in(c, c->stage.p, x, bx, c->pin_i))) return rc;
+    } else {
+        if ((rc = ensure_pin(c, c->pin_i, bx))) return rc;
+        std::memcpy(c->pin_i.p, x, bx);
+        PG_CUDA(c, cudaMemcpyAsync(c->stage.p, c->pin_i.p, bx, cudaMemcpyHostToDevice, c->stream));
+        PG_CUDA(c, cudaEventRecord(c->pin_i.done, c->stream));
+    }
     PG_CUDA(c, launch_pack_i((const double *)c->stage.p, (double4 *)c->xi.p, ni, c->stream,
                              (float4 *)c->g_ihl.p));
     c->ihl_n = ni;
@@ -2344,6 +2381,12 @@ int pg_get_force(pg_ctx *c, double *a, double *phi, long long ni)
     if (ni == 0) return pg_sync(c);
     int rc;
     size_t ba = (size_t)ni * 24, bp = phi ? (size_t)ni * 8 : 0;
+    if (host_pinned(a) && (!phi || host_pinned(phi))) {
+        // page-locked output: DMA straight into it
+        PG_CUDA(c, cudaMemcpyAsync(a, c->acc.p, ba, cudaMemcpyDeviceToHost, c->stream));
+        if (phi) PG_CUDA(c, cudaMemcpyAsync(phi, c->pot.p, bp, cudaMemcpyDeviceToHost, c->stream));
+        return pg_sync(c);
+    }
     if ((rc = ensure_pin(c, c->pin_o, ba + bp))) return rc;
     PG_CUDA(c, cudaMemcpyAsync(c->pin_o.p, c->acc.p, ba, cudaMemcpyDeviceToHost, c->stream));
     if (phi)

@@ -195,3 +195,32 @@ def test_mixed_2e20_sampled(pg, orc):
     ao, po = orc.newton_subset(x, m, eps, idx)
     assert_parity(rel_vec(a[idx], ao), what="a")
     assert_parity(rel_scalar(p[idx], po), what="phi")
+
+
+def test_pinned_host_buffers():
+    # page-locked inputs and outputs go by DMA straight to and from the
+    # caller's memory; the results are those of the pageable path, bit for bit
+    torch = pytest.importorskip("torch")
+    pg = need_cuda()
+    x, m = gen.plummer(3000, 7401)
+    xi = x[:1700]
+
+    def pinned(arr):
+        return torch.from_numpy(np.ascontiguousarray(arr)).pin_memory().numpy()
+
+    with pg.Context(0) as c:
+        c.set_eps(1 / 64)
+        c.set_j(x, m)
+        c.set_i(xi)
+        c.run()
+        a0, p0 = c.get_force(len(xi))
+        xh, mh, xih = pinned(x), pinned(m), pinned(xi)
+        ah, ph = pinned(np.zeros((len(xi), 3))), pinned(np.zeros(len(xi)))
+        c.set_j(xh, mh)
+        c.set_i(xih)
+        xh[:] = 0.0                      # the calls copied before returning
+        xih[:] = 0.0
+        c.run()
+        a1, p1 = c.get_force(len(xi), out=(ah, ph))
+        assert a1 is ah and p1 is ph
+    assert np.array_equal(a0, a1) and np.array_equal(p0, p1)
