@@ -532,6 +532,18 @@ def extra_rows(pg, torch, dev, peak_newton, headline_rate):
                                            useful_fraction=useful / pairs)
         except Exception as exc:  # report, do not hide
             rows["cells_2e21_E4F8"]["pairs_useful_error"] = repr(exc)
+        try:
+            # the table lookup's own ceiling: random 8-byte gathers per SM per
+            # clock from one shared table (the kernels' placement), four
+            # interleaved shared copies, and the read-only global path
+            sm_clk = peak_newton * 13 / 128          # SMs x basis clock
+            g = {k: pg.pg_microbench(kind)[0] for k, kind in
+                 (("shared", 4), ("shared_4_copies", 5), ("global_readonly", 6))}
+            rows["cells_2e21_E4F8"].update(
+                pairs_per_sm_clk=rate / sm_clk, gather_lane_per_sm_clk=g,
+                frac_of_gather_ceiling=rate / sm_clk / g["shared"])
+        except Exception as exc:  # report, do not hide
+            rows["cells_2e21_E4F8"]["gather_ceiling_error"] = repr(exc)
         cidx = gen.sample_indices(n, 1024, 64)
         csel = torch.tensor(cidx, device=dev)
         ac = a[csel].cpu().numpy()

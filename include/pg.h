@@ -454,7 +454,9 @@ int pg_set_allpairs_path(pg_ctx *ctx, int path);
 
 /* Launch shape override: i per thread = 2*np (np in {1, 2, 4}; 0 = chosen
  * by problem size, the default),
- * CTAs per SM (0 = occupancy limit), packed = 1: pair arithmetic in packed
+ * CTAs per SM (0 = occupancy limit; for a periodic cell list whose small
+ * cells go to the warp-mode kernel, one fewer, so that a block of that kernel
+ * fits beside the CTA-mode kernel on every SM), packed = 1: pair arithmetic in packed
  * FP32x2 instructions, 0: scalar FP32 (same roundings), -1 = keep. */
 int pg_set_shape(pg_ctx *ctx, int np, int ctas_per_sm, int packed);
 
@@ -483,7 +485,11 @@ int pg_info(pg_ctx *ctx, long long *out, int n);
  * 1 packed FP32x2 FMA (lane operations), 2 MUFU rsqrt, 3 the Newton pair
  * term with every operand in registers (interactions), 4 random 8-byte
  * gathers from a 4096-entry table in shared memory (lane gathers: the
- * tabulated force's lookup when a warp's pairs hit random bins). Writes the rate per
+ * tabulated force's lookup when a warp's pairs hit random bins), 5 the same
+ * gathers from four interleaved copies of the table in shared memory (each
+ * lane reads the copy of its lane index mod 4, which sits on its own quarter
+ * of the banks; 1024-thread blocks, one per SM), 6 the same gathers through
+ * the read-only global path from a table in device memory. Writes the rate per
  * SM per clock (at the device's maximum clock) and per second. Synchronises
  * the legacy default stream. */
 int pg_microbench(int kind, double *per_sm_clock, double *per_second);

@@ -452,7 +452,9 @@ def pg_info(ctx):
 def pg_microbench(kind):
     """(rate per SM per clock, rate per second) of: 0 FFMA, 1 FFMA2 lane ops,
     2 MUFU rsqrt, 3 Newton pair-term interactions with register operands,
-    4 random 8-byte gathers from a 4096-entry shared-memory table."""
+    4 random 8-byte gathers from a 4096-entry shared-memory table, 5 the
+    same from four interleaved shared copies, 6 the same through the
+    read-only global path."""
     a, b = C.c_double(), C.c_double()
     rc = lib().pg_microbench(int(kind), C.byref(a), C.byref(b))
     if rc != PG_OK:

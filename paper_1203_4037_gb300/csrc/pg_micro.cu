@@ -3,8 +3,9 @@
 // pair term's exact instruction mix with every operand in registers (no
 // shared or global memory), and random 8-byte gathers from a 4096-entry
 // table in shared memory (the tabulated force's lookup, Section 3.4, with
-// indices spread like those of pairs inside the cutoff), each timed with
-// CUDA events.
+// indices spread like those of pairs inside the cutoff), the same gathers
+// from four interleaved copies and through the read-only global path (the
+// placements that could raise that ceiling), each timed with CUDA events.
 #include <cuda_runtime.h>
 
 #include "pg.h"
@@ -123,6 +124,79 @@ __global__ void __launch_bounds__(kMicroThreads) k_micro(int kind, int iters, fl
     if (acc == 12345.678f && blockIdx.x < kSinkSize) g_micro_sink[blockIdx.x] = acc;
 }
 
+// The same random 8-byte gathers from other placements of the table:
+// C > 0: C interleaved copies in shared memory, entry e of copy c in 8-byte
+// slot C e + c (copy c on bank pairs c, c + C, ...), lane l reading copy
+// l mod C, so that the lanes of a warp spread over C disjoint bank sets;
+// C = 0: the read-only global path (L1) on a table in device memory.
+template <int C, int NTH>
+__global__ void __launch_bounds__(NTH) k_micro_gather(int iters, const float2 *__restrict__ gtab_dev)
+{
+    extern __shared__ float2 gtab[];
+    if (C > 0) {
+        for (int k = threadIdx.x; k < kGatherTable * C; k += NTH) gtab[k] = make_float2(1e-30f * (k / C), 0.0f);
+        __syncthreads();
+    }
+    const int copy = C > 0 ? (threadIdx.x & 31) % C : 0;
+    unsigned h[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) h[c] = (threadIdx.x + 1) * 2654435761u + c * 40503u + blockIdx.x;
+    float sum = 0.0f;
+    for (int it = 0; it < iters; ++it)
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) {
+            const unsigned e = (h[c] >> 12) & (kGatherTable - 1);
+            const float2 v = C > 0 ? gtab[e * C + copy] : __ldg(gtab_dev + e);
+            h[c] = h[c] * 1664525u + 1013904223u + __float_as_uint(v.y);
+            sum += v.x;
+        }
+    if (sum == 12345.678f && blockIdx.x < kSinkSize) g_micro_sink[blockIdx.x] = sum;
+}
+
+// kind 5: four interleaved shared copies (1024-thread blocks, one per SM:
+// 128 KB of table); kind 6: the read-only global path
+int micro_gather(int kind, int sms, float *ms, double *gathers)
+{
+    constexpr int kCopies = 4, kThreadsC = 1024;
+    const int iters = kind == 5 ? 4096 : 512;
+    float2 *dtab = nullptr;
+    int nth = kMicroThreads, blocks = 0;
+    size_t smem = 0;
+    cudaError_t e = cudaSuccess;
+    if (kind == 5) {
+        smem = (size_t)kGatherTable * kCopies * sizeof(float2);
+        e = cudaFuncSetAttribute(k_micro_gather<kCopies, kThreadsC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        nth = kThreadsC;
+        blocks = sms;
+    } else {
+        e = cudaMalloc(&dtab, kGatherTable * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMemset(dtab, 0, kGatherTable * sizeof(float2));
+        blocks = sms * 8;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {   // warm-up, then the timed launch
+        const int n = pass ? iters : 16;
+        if (pass) cudaEventRecord(e0);
+        if (kind == 5)
+            k_micro_gather<kCopies, kThreadsC><<<blocks, nth, smem>>>(n, nullptr);
+        else
+            k_micro_gather<0, kMicroThreads><<<blocks, nth>>>(n, dtab);
+        if (pass) cudaEventRecord(e1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (dtab) cudaFree(dtab);
+    *gathers = (double)blocks * nth * iters * kChains;
+    if (e != cudaSuccess) { (void)cudaGetLastError(); return PG_ECUDA; }
+    return PG_OK;
+}
+
 }  // namespace
 }  // namespace pg
 
@@ -130,11 +204,21 @@ using namespace pg;
 
 extern "C" int pg_microbench(int kind, double *per_sm_clock, double *per_second)
 {
-    if (kind < 0 || kind > 4 || !per_sm_clock || !per_second) return PG_EINVAL;
+    if (kind < 0 || kind > 6 || !per_sm_clock || !per_second) return PG_EINVAL;
     int dev = 0, sms = 0, clk_khz = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { (void)cudaGetLastError(); return PG_ECUDA; }
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
+    if (kind >= 5) {
+        float ms = 0;
+        double g = 0;
+        const int rc = micro_gather(kind, sms, &ms, &g);
+        if (rc) return rc;
+        if (ms <= 0) return PG_ECUDA;
+        *per_second = g / (ms * 1e-3);
+        *per_sm_clock = *per_second / ((double)sms * clk_khz * 1e3);
+        return PG_OK;
+    }
     const int blocks = sms * 8;
     const int iters = kind == 2 || kind == 4 ? 4096 : 16384;
     // lane operations per thread per iteration: FFMA 8, FFMA2 16, rsqrt 8,

@@ -1,7 +1,9 @@
 """The roofline microbenchmark returns plausible ceilings on the device:
 FP32 FMA lane rates near 128 per SM per clock, MUFU rsqrt near 16, the
-Newton pair term in registers between the MUFU and FP32 bounds, and random
-8-byte shared-memory gathers below the conflict-free 16 per SM per clock."""
+Newton pair term in registers between the MUFU and FP32 bounds, random
+8-byte shared-memory gathers below the conflict-free 16 per SM per clock
+(from one table or four interleaved copies), and the same gathers through
+the read-only global path below the shared ones."""
 
 import pytest
 
@@ -22,3 +24,9 @@ def test_microbench_ceilings():
     assert 2 < mix < 11 and mix_s > 1e11
     gather, _ = pg.pg_microbench(4)
     assert 1 < gather <= 16.5
+    copies, _ = pg.pg_microbench(5)
+    assert 1 < copies <= 16.5
+    glob, _ = pg.pg_microbench(6)
+    assert 0 < glob < gather
+    with pytest.raises(pg.PGError):
+        pg.pg_microbench(7)
