@@ -50,6 +50,7 @@ class PairForceFn(torch.autograd.Function):
         x = x.contiguous()
         m = m.contiguous()
         c.set_j_dev(x, m)
+        c.set_n(x.shape[0])      # the whole set: a smaller one than the last ends here
         c.set_i_dev(x)
         a = torch.empty_like(x)
         c.run_dev(a)
@@ -68,6 +69,7 @@ class PairForceFn(torch.autograd.Function):
         else:
             c.set_eps(eps)
         c.set_j_dev(x, m)
+        c.set_n(x.shape[0])
         c.set_i_dev(x)
         w = grad_a.contiguous().to(torch.float64)
         dx = torch.empty_like(x)

@@ -2528,8 +2528,11 @@ int pg_backward_dev(pg_ctx *c, const double *w, double *dx, double *dm, float *d
     a.xi = (const double4 *)c->xt.p;
     a.wv = (const double4 *)c->bw_wt.p;
     a.ctr = (const double4 *)c->ctr.p;
-    a.jx = (const double4 *)c->jrec.p;
-    a.jwv = (const double4 *)c->bw_wj.p;
+    // Newton: the j records in the i-particles' tile order, so that the own
+    // pair falls in the sub-tiles beside the diagonal (the kernel tests for
+    // it only there); the table kernel keeps the records' order
+    a.jx = (const double4 *)(table ? c->jrec.p : c->xt.p);
+    a.jwv = (const double4 *)(table ? c->bw_wj.p : c->bw_wt.p);
     a.n = n;
     a.ntiles = ntiles;
     a.njsub = njsub;

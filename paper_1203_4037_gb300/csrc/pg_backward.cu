@@ -25,6 +25,7 @@
 namespace pg {
 
 constexpr int kKI = 4;                      // i per thread
+constexpr float kFltMinNormal = 1.17549435e-38f;   // smallest normal FP32
 constexpr int kBiB = kNT * kKI;
 
 int backward_bi() { return kBiB; }
@@ -254,6 +255,60 @@ __global__ void __launch_bounds__(kNT) k_backward(BackwardArgs a)
 constexpr int kNPB = 2;                       // i-pairs per thread
 static_assert(2 * kNPB == kKI, "the packed kernel keeps the tile of the scalar one");
 
+// The pair loop over one staged sub-tile of kTJ j (jb its first index). The
+// j records are in the i-particles' (tile) order, so the own pair can only
+// sit in the sub-tiles that overlap the thread's i-tile: CHECK (those, and
+// every sub-tile at eps = 0, where a coincident pair has r^2 = 0) zeroes q
+// for j = the i's own index and for r^2 = 0; elsewhere r^2 >= eps^2 > 0 and
+// no pair is the own one, so the tests are left out.
+template <bool CHECK>
+__device__ __forceinline__ void bw_newton_tile(const ulonglong2 *__restrict__ cv, int jb, u64 c0v,
+                                               const u64 (&xi)[kNPB], const u64 (&yi)[kNPB],
+                                               const u64 (&zi)[kNPB], const u64 (&mk)[kNPB],
+                                               const u64 (&wkx)[kNPB], const u64 (&wky)[kNPB],
+                                               const u64 (&wkz)[kNPB], const int (&self0)[kNPB],
+                                               const int (&self1)[kNPB], u64 (&acc)[kNPB][8])
+{
+#pragma unroll 4
+    for (int e = 0; e < kTJ; ++e) {
+        const ulonglong2 xy = cv[4 * e], zm = cv[4 * e + 1], wxy = cv[4 * e + 2], wz0 = cv[4 * e + 3];
+        const int j = jb + e;
+#pragma unroll
+        for (int p = 0; p < kNPB; ++p) {
+            const u64 dx = f2sub(xy.x, xi[p]), dy = f2sub(xy.y, yi[p]), dz = f2sub(zm.x, zi[p]);
+            u64 r2 = f2fma(dx, dx, c0v);
+            r2 = f2fma(dy, dy, r2);
+            r2 = f2fma(dz, dz, r2);
+            u64 wd = f2mul(dx, wxy.x);
+            wd = f2fma(dy, wxy.y, wd);
+            wd = f2fma(dz, wz0.x, wd);
+            u64 dk = f2mul(dx, wkx[p]);
+            dk = f2fma(dy, wky[p], dk);
+            dk = f2fma(dz, wkz[p], dk);
+            const u64 du = f2fma(mk[p], wd, f2mul(zm.y, dk));   // m_k d.w_j - m_j d.w_k
+            float ra, rb;
+            up2(r2, ra, rb);
+            float qa = rsq(ra), qb = rsq(rb);
+            if (CHECK) {
+                qa = (ra > 0.0f && j != self0[p]) ? qa : 0.0f;
+                qb = (rb > 0.0f && j != self1[p]) ? qb : 0.0f;
+            }
+            const u64 q = pk2(qa, qb);
+            const u64 q2 = f2mul(q, q);
+            const u64 K = f2mul(q, q2);
+            const u64 tt = f2mul(f2mul(K, q2), du);
+            acc[p][0] = f2fma(K, wxy.x, acc[p][0]);
+            acc[p][1] = f2fma(K, wxy.y, acc[p][1]);
+            acc[p][2] = f2fma(K, wz0.x, acc[p][2]);
+            acc[p][3] = f2fma(zm.y, K, acc[p][3]);    // -sum m_j K
+            acc[p][4] = f2fma(tt, dx, acc[p][4]);
+            acc[p][5] = f2fma(tt, dy, acc[p][5]);
+            acc[p][6] = f2fma(tt, dz, acc[p][6]);
+            acc[p][7] = f2fma(K, wd, acc[p][7]);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kNT, 2) k_backward_newton(BackwardArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -344,7 +399,7 @@ __global__ void __launch_bounds__(kNT, 2) k_backward_newton(BackwardArgs a)
                         fz[q] = (float)(v.z - cz);
                         fm[q] = (float)v.w;
                         gx[q] = (float)w.x; gy[q] = (float)w.y; gz[q] = (float)w.z;
-                        sf[q] = a.perm ? (int)a.perm[i] : (int)i;
+                        sf[q] = (int)i;        // j records in the same order
                     } else {
                         fx[q] = fy[q] = fz[q] = fm[q] = gx[q] = gy[q] = gz[q] = 0.0f;
                         sf[q] = -1;
@@ -408,43 +463,11 @@ __global__ void __launch_bounds__(kNT, 2) k_backward_newton(BackwardArgs a)
 #pragma unroll
             for (int k = 0; k < 8; ++k) acc[p][k] = 0ull;
         const ulonglong2 *cv = reinterpret_cast<const ulonglong2 *>(cvt);
-        const int jb = (int)j0;
-#pragma unroll 4
-        for (int e = 0; e < kTJ; ++e) {
-            const ulonglong2 xy = cv[4 * e], zm = cv[4 * e + 1], wxy = cv[4 * e + 2], wz0 = cv[4 * e + 3];
-            const int j = jb + e;
-#pragma unroll
-            for (int p = 0; p < kNPB; ++p) {
-                const u64 dx = f2sub(xy.x, xi[p]), dy = f2sub(xy.y, yi[p]), dz = f2sub(zm.x, zi[p]);
-                u64 r2 = f2fma(dx, dx, c0v);
-                r2 = f2fma(dy, dy, r2);
-                r2 = f2fma(dz, dz, r2);
-                u64 wd = f2mul(dx, wxy.x);
-                wd = f2fma(dy, wxy.y, wd);
-                wd = f2fma(dz, wz0.x, wd);
-                u64 dk = f2mul(dx, wkx[p]);
-                dk = f2fma(dy, wky[p], dk);
-                dk = f2fma(dz, wkz[p], dk);
-                const u64 du = f2fma(mk[p], wd, f2mul(zm.y, dk));   // m_k d.w_j - m_j d.w_k
-                float ra, rb;
-                up2(r2, ra, rb);
-                float qa = rsq(ra), qb = rsq(rb);
-                qa = (ra > 0.0f && j != self0[p]) ? qa : 0.0f;
-                qb = (rb > 0.0f && j != self1[p]) ? qb : 0.0f;
-                const u64 q = pk2(qa, qb);
-                const u64 q2 = f2mul(q, q);
-                const u64 K = f2mul(q, q2);
-                const u64 tt = f2mul(f2mul(K, q2), du);
-                acc[p][0] = f2fma(K, wxy.x, acc[p][0]);
-                acc[p][1] = f2fma(K, wxy.y, acc[p][1]);
-                acc[p][2] = f2fma(K, wz0.x, acc[p][2]);
-                acc[p][3] = f2fma(zm.y, K, acc[p][3]);    // -sum m_j K
-                acc[p][4] = f2fma(tt, dx, acc[p][4]);
-                acc[p][5] = f2fma(tt, dy, acc[p][5]);
-                acc[p][6] = f2fma(tt, dz, acc[p][6]);
-                acc[p][7] = f2fma(K, wd, acc[p][7]);
-            }
-        }
+        const bool diag = j0 < (t + 1) * kBiB && j0 + kTJ > t * kBiB;
+        if (diag || !(a.eps2 >= kFltMinNormal))
+            bw_newton_tile<true>(cv, (int)j0, c0v, xi, yi, zi, mk, wkx, wky, wkz, self0, self1, acc);
+        else
+            bw_newton_tile<false>(cv, (int)j0, c0v, xi, yi, zi, mk, wkx, wky, wkz, self0, self1, acc);
 #pragma unroll
         for (int p = 0; p < kNPB; ++p)
 #pragma unroll

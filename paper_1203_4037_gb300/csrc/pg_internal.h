@@ -156,8 +156,8 @@ struct BackwardArgs {
     const double4 *xi;     // i positions + mass (x, y, z, m) in tile order
     const double4 *wv;     // i loss weights (wx, wy, wz, -) in tile order
     const double4 *ctr;    // tile centres
-    const double4 *jx;     // j positions + mass in record order
-    const double4 *jwv;    // j loss weights in record order
+    const double4 *jx;     // j positions + mass (record order; tile order for the Newton kernel)
+    const double4 *jwv;    // j loss weights, in the order of jx
     long long n;
     int ntiles, njsub;
     long long W;

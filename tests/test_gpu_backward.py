@@ -57,6 +57,36 @@ def test_newton_small_full(pg, torch, orc):
     assert np.abs(dx.sum(axis=0)).max() <= 1e-5 * np.abs(dx).sum()
 
 
+def test_newton_diagonal_subtiles(pg, torch, orc):
+    # The Newton kernel takes the j records in the i-particles' tile order
+    # and tests for the own pair only in the j sub-tiles that overlap the
+    # thread's i-tile. A Morton-ordered set (20011 particles: a ragged last
+    # tile) at eps = 1/64, sampled against the oracle's analytic gradient
+    n = 20011
+    x, m = gen.plummer(n, 7411)
+    m = m * np.exp(np.random.default_rng(7412).uniform(-1, 1, n))
+    w = gen.unit_vectors(n, 7413)
+    dx, dm, _, _ = grads(pg, torch, x, m, w, eps=1 / 64)
+    idx = gen.sample_indices(n, 256, 7414)
+    ox, om = orc.grad_newton_at(x, m, w, 1 / 64, idx)
+    assert normrel(dx[idx], ox) <= 1e-5 and normrel(dm[idx], om) <= 1e-5
+
+
+def test_newton_eps0_full(pg, torch, orc):
+    # eps = 0 tests every sub-tile (a coincident pair would have r^2 = 0): a
+    # jittered 14^3 lattice (no two particles closer than a fifth of the
+    # spacing; 2744 = 5 tiles of 512 and a ragged one) in full
+    rng = np.random.default_rng(7415)
+    g = np.stack(np.meshgrid(*[np.arange(14)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    x = (g + rng.uniform(-0.4, 0.4, g.shape)) / 14.0
+    m = rng.uniform(0.5, 1.5, len(x)) / len(x)
+    w = gen.unit_vectors(len(x), 7416)
+    dx, dm, L, _ = grads(pg, torch, x, m, w, eps=0.0)
+    ox, om, oL = orc.grad_newton(x, m, w, 0.0)
+    assert L == pytest.approx(oL, rel=1e-5)
+    assert normrel(dx, ox) <= 1e-5 and normrel(dm, om) <= 1e-5
+
+
 def test_table_small_full(pg, torch, orc):
     # a compact set: with fewer i-particles than a few tiles the FP32 offsets
     # are taken from centres of tiles that span the whole set
