@@ -320,6 +320,27 @@ def extra_rows(pg, torch, dev, peak_newton, headline_rate):
         rows["newton_plummer_4096"] = {"interactions_per_s": rate4, "us_per_call": ms * 1e3,
                                        "graph": True, "launches": c.info()["launches"],
                                        "frac_fp32_peak_19_ops": rate4 / (peak_newton * 13 / 19)}
+        # single-call latency: one call at a time, the stream idle before it;
+        # CUDA events around the call, and the host's clock from the call to
+        # the end of a synchronize
+        for graph in (True, False):
+            c.set_graph(graph)
+            ev, host = [], []
+            for k in range(25):
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                t0 = time.perf_counter()
+                e0.record(st)
+                c.run_dev(a, p)
+                e1.record(st)
+                e1.synchronize()
+                t1 = time.perf_counter()
+                if k >= 5:
+                    ev.append(e0.elapsed_time(e1) * 1e3)
+                    host.append((t1 - t0) * 1e6)
+            key = "single_call_graph" if graph else "single_call"
+            rows["newton_plummer_4096"][key] = {"us_events": statistics.median(ev),
+                                                "us_host": statistics.median(host)}
         a4, p4 = a.cpu().numpy(), p.cpu().numpy()
         CHECKS.append(("newton_plummer_4096",
                        lambda orc, x=x, m=m, a4=a4, p4=p4: err_ref(
