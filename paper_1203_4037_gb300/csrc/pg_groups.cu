@@ -376,12 +376,20 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
                 x = y = z = 1.0e4f;
                 m = 0.0f;
             }
-            // separate {x, y} and {z, m} arrays: lanes of a set that read
-            // consecutive j then read consecutive 16-byte words
-            cvt[2 * e + 0] = pk2(x, x);
-            cvt[2 * e + 1] = pk2(y, y);
-            cvt[2 * TJ + 2 * e + 0] = pk2(z, z);
-            cvt[2 * TJ + 2 * e + 1] = pk2(m, m);
+            if (CELL && !EXT) {
+                // one 16-byte word per j (the cell list's kernel is bound by
+                // the shared-memory pipe: one wavefront per j step instead
+                // of two; the pairs are formed in registers; with the
+                // potential's table the registers would spill)
+                reinterpret_cast<float4 *>(cvt)[e] = make_float4(x, y, z, m);
+            } else {
+                // separate {x, y} and {z, m} arrays: lanes of a set that read
+                // consecutive j then read consecutive 16-byte words
+                cvt[2 * e + 0] = pk2(x, x);
+                cvt[2 * e + 1] = pk2(y, y);
+                cvt[2 * TJ + 2 * e + 0] = pk2(z, z);
+                cvt[2 * TJ + 2 * e + 1] = pk2(m, m);
+            }
             if (DF) {
                 cvt[4 * TJ + 2 * e + 0] = pk2(lx, lx);
                 cvt[4 * TJ + 2 * e + 1] = pk2(ly, ly);
@@ -402,8 +410,15 @@ __device__ __forceinline__ void group_item(const GroupArgs &a, const GroupItem &
             const int nv_lane = (int)nv;
 #pragma unroll(GroupsUnrollJ<TABLE>::value)
             for (int e = lane; e < nv_lane; e += L) {
-                const ulonglong2 xy = reinterpret_cast<const ulonglong2 *>(cvt)[e];
-                const ulonglong2 zm = reinterpret_cast<const ulonglong2 *>(cvt)[TJ + e];
+                ulonglong2 xy, zm;
+                if (CELL && !EXT) {
+                    const float4 v = reinterpret_cast<const float4 *>(cvt)[e];
+                    xy = make_ulonglong2(pk2(v.x, v.x), pk2(v.y, v.y));
+                    zm = make_ulonglong2(pk2(v.z, v.z), pk2(v.w, v.w));
+                } else {
+                    xy = reinterpret_cast<const ulonglong2 *>(cvt)[e];
+                    zm = reinterpret_cast<const ulonglong2 *>(cvt)[TJ + e];
+                }
                 ulonglong2 lxy = make_ulonglong2(0ull, 0ull), lz0 = lxy;
                 if (DF) {
                     lxy = reinterpret_cast<const ulonglong2 *>(cvt)[2 * TJ + e];
