@@ -146,6 +146,79 @@ __global__ void k_pm_assign(const int4 *__restrict__ mj, const float4 *__restric
     }
 }
 
+// The same deposit from records in an order that keeps particles of one
+// mesh point together (mesh or cell-list order). The lanes of a warp that
+// hold the same nearest mesh point (a run of consecutive lanes) would add to
+// the same 27 cells in the same instructions, and those atomics serialise:
+// the run's weights are summed in the warp first (a segmented scan over the
+// lanes), and the run's last lane adds the 27 sums. A warp whose lanes all
+// hold different points takes the plain path.
+__global__ void __launch_bounds__(256) k_pm_assign_runs(const int4 *__restrict__ mj, const float4 *__restrict__ md,
+                                                        long long n, int N, float vinv, float *__restrict__ rho,
+                                                        int vec)
+{
+    constexpr unsigned kFull = 0xffffffffu;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool valid = i < n;
+    const int4 j = valid ? mj[i] : make_int4(0, 0, 0, 0);
+    const float4 d = valid ? md[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    // a lane past the end gets a key no record has
+    const long long key = valid ? ((long long)j.x * N + j.y) * N + j.z : -1 - (long long)lane;
+    const long long prev = __shfl_up_sync(kFull, key, 1);
+    const unsigned heads = __ballot_sync(kFull, lane == 0 || prev != key);
+    if (!valid && heads == kFull) return;          // past the end, and no lane waits for a shuffle
+    float wx[3], wy[3], wz[3];
+    tsc_weights(d.x, wx);
+    tsc_weights(d.y, wy);
+    tsc_weights(d.z, wz);
+    const float mv = valid ? d.w * vinv : 0.0f;
+    if (heads == kFull) {                          // no two lanes share a point
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const long long ix = wrap_index(j.x + a - 1, N);
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const long long row = (ix * N + wrap_index(j.y + b - 1, N)) * N;
+                const float wab = mv * wx[a] * wy[b];
+                deposit_row(rho + row, j.z - 1, N, vec != 0, wab * wz[0], wab * wz[1], wab * wz[2]);
+            }
+        }
+        return;
+    }
+    // first lane of this lane's run, and whether this lane ends it
+    const unsigned upto = lane == 31 ? heads : heads & ((2u << lane) - 1u);   // heads at lanes <= this one
+    const int start = 31 - __clz(upto);
+    const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+    float w[27];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) w[9 * a + 3 * b + c] = mv * wx[a] * wy[b] * wz[c];
+#pragma unroll
+    for (int sft = 1; sft < 32; sft <<= 1) {
+        const bool take = lane - sft >= start;
+#pragma unroll
+        for (int q = 0; q < 27; ++q) {
+            const float t = __shfl_up_sync(kFull, w[q], sft);
+            if (take) w[q] += t;
+        }
+    }
+    if (!valid || !tail) return;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const long long ix = wrap_index(j.x + a - 1, N);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const long long row = (ix * N + wrap_index(j.y + b - 1, N)) * N;
+            deposit_row(rho + row, j.z - 1, N, vec != 0, w[9 * a + 3 * b], w[9 * a + 3 * b + 1],
+                        w[9 * a + 3 * b + 2]);
+        }
+    }
+}
+
 // mesh order: a record's key is the row-major index of its nearest mesh
 // point, so that neighbouring threads share stencil points; the mesh record
 // (point; offsets and mass) is written here once, in input order
@@ -413,10 +486,11 @@ cudaError_t records(PmState *s, const double4 *rec, long long n, bool sorted, in
     return cudaGetLastError();
 }
 
-// the TSC deposit of n records into rho (cleared first). Records in input
-// order: in mesh order neighbouring threads add to the same cells and the
-// atomics serialise
-void deposit(PmState *s, const int4 *mj, const float4 *md, long long n, float *rho, cudaStream_t st,
+// the TSC deposit of n records into rho (cleared first): records in input
+// order (runs = false), or in an order that keeps the particles of a mesh
+// point together, whose runs of one point the warp sums first (runs = true;
+// in input order neighbouring threads rarely share a point)
+void deposit(PmState *s, const int4 *mj, const float4 *md, long long n, float *rho, bool runs, cudaStream_t st,
              int *launches)
 {
     const int N = s->N;
@@ -424,7 +498,10 @@ void deposit(PmState *s, const int4 *mj, const float4 *md, long long n, float *r
     const float vinv = (float)((double)N3 / (s->L * s->L * s->L));     // 1 / h^3
     cudaMemsetAsync(rho, 0, N3 * sizeof(float), st);
     const int vec = (N % 4 == 0 && ((uintptr_t)rho & 15) == 0) ? 1 : 0;
-    k_pm_assign<<<blocks256(n), 256, 0, st>>>(mj, md, n, N, vinv, rho, vec);
+    if (runs)
+        k_pm_assign_runs<<<blocks256(n), 256, 0, st>>>(mj, md, n, N, vinv, rho, vec);
+    else
+        k_pm_assign<<<blocks256(n), 256, 0, st>>>(mj, md, n, N, vinv, rho, vec);
     if (launches) *launches += 1;
 }
 
@@ -504,13 +581,17 @@ int pm_run(PmState *s, const double4 *src, long long ns, const double4 *tgt, lon
 {
     int rc = ensure(s, L, N, split, scale, std::max(ns, nt), err);
     if (rc) return rc;
-    // the sources deposited in input order; the targets interpolated in mesh
-    // order (one set of records when they are the same particles)
+    // the targets interpolated in mesh order; the sources deposited in that
+    // order when they are the same particles (one set of records), else in
+    // input order
     const bool same = src == tgt && ns == nt;
     cudaError_t e = records(s, src, ns, same, s->mj_tgt, s->md_tgt, s->perm_tgt, sort, st, launches,
                             same ? tgt_order : nullptr);
     if (e == cudaSuccess) {
-        deposit(s, s->mj_raw, s->md_raw, ns, s->rho, st, launches);
+        if (same)
+            deposit(s, s->mj_tgt, s->md_tgt, ns, s->rho, true, st, launches);
+        else
+            deposit(s, s->mj_raw, s->md_raw, ns, s->rho, false, st, launches);
         if (!same)
             e = records(s, tgt, nt, true, s->mj_tgt, s->md_tgt, s->perm_tgt, sort, st, launches, tgt_order);
     }
@@ -535,7 +616,7 @@ int pm_deposit(PmState *s, const double4 *src, long long ns, double L, int N, in
         err = cudaGetErrorString(e);
         return PG_ECUDA;
     }
-    deposit(s, s->mj_raw, s->md_raw, ns, rho, st, launches);
+    deposit(s, s->mj_raw, s->md_raw, ns, rho, false, st, launches);
     return finish(err);
 }
 
