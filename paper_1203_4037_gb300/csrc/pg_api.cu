@@ -2221,11 +2221,11 @@ int enqueue_cells(pg_ctx *c, double *acc, double *pot)
     PG_CUDA(c, launch_cell_build((const double4 *)c->jrec.p, n, c->box, nc, Bi, c->scale, s,
                                  c->sort, c->stream));
     // kernels of the build: key, count, gather, sizes, pairs, iota, items,
-    // permute (8), two scans (6), the 24-bit item sort (15) and the cell
-    // sort (5 per 8 key bits)
+    // permute (8), two scans (6), the 8-bit item sort (5) and the cell sort
+    // (5 per 8 key bits)
     int cell_bits = 0;
     while ((1LL << cell_bits) < ncell) ++cell_bits;
-    c->last_launches += 29 + 5 * ((cell_bits + 7) / 8);
+    c->last_launches += 19 + 5 * ((cell_bits + 7) / 8);
     GroupArgs g = group_args(c);
     g.xi = s.xs;
     g.jrec = s.xs;

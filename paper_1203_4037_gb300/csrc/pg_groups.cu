@@ -1521,11 +1521,17 @@ __global__ void k_cell_items(const unsigned *__restrict__ start, long long ncell
         it.ni = (int)min((unsigned)Bi, ni - k * Bi);
         it.pad = 0;
         items[o + k] = it;
-        // CTA-sized items first, longest first; then the warp-sized ones
-        unsigned long long cost = ((unsigned long long)it.ni * jcount[g]) >> 2;
-        unsigned cq = cost > 0x7fffffull ? 0x7fffffu : (unsigned)cost;
+        // CTA-sized items first, longest first (by cost classes a quarter
+        // of a binade wide: q = 4 floor(log2 c) + the next two bits of c);
+        // then the warp-sized ones. One 8-bit radix pass; 255 is left for the
+        // unused slots, which sort last. The order only balances the queue:
+        // each item's sums do not depend on it.
+        const unsigned long long cost = (unsigned long long)it.ni * jcount[g];
+        const int e = 63 - __clzll(cost | 1ull);
+        const unsigned q = 4u * (unsigned)e + (unsigned)(e >= 2 ? (cost >> (e - 2)) & 3ull : (cost << (2 - e)) & 3ull);
+        const unsigned cq = q > 126u ? 126u : q;
         const bool small = it.ni <= kWarpItemNi && (long long)it.ni * jcount[g] <= kWarpItemPairs;
-        keys[o + k] = ((small ? 1u : 0u) << 23) | (0x7fffffu - cq);
+        keys[o + k] = ((small ? 1u : 0u) << 7) | (126u - cq);
         vals[o + k] = o + k;
         if (!small) atomicAdd(ncta, 1u);
     }
@@ -1573,7 +1579,7 @@ cudaError_t launch_cell_build(const double4 *jrec, long long n, double box, int 
     k_cell_items<<<gc, 256, 0, st>>>(s.start, ncell, Bi, s.ioff, s.jcount, s.items_raw,
                                      sort.keys[0], sort.vals[0], s.ncta);
     unsigned *order;
-    if ((e = launch_radix_sort(sort.keys[0], sort.vals[0], s.item_cap, 24, sort, &ko, &order, st)) !=
+    if ((e = launch_radix_sort(sort.keys[0], sort.vals[0], s.item_cap, 8, sort, &ko, &order, st)) !=
         cudaSuccess)
         return e;
     k_items_permute<<<(unsigned)((s.item_cap + 255) / 256), 256, 0, st>>>(s.items_raw, order,
