@@ -737,9 +737,10 @@ def run_row(args):
             c.set_j_dev(xd, md)
             c.set_i_dev(xid)
             kms = _time_kernel(c, lambda: c.run_dev(a), reps=args.steps, warm=args.warmup)
+            call = _time_call(torch, lambda: c.run_dev(a), args.steps, warm=args.warmup)
             info = c.info()
-        out.update(ni=ni, nj=N_PART, kernel_ms=kms, interactions_per_s=ni * N_PART / (kms * 1e-3),
-                   j_chunks=info["slots"])
+        out.update(ni=ni, nj=N_PART, kernel_ms=kms, us_per_call=call * 1e3,
+                   interactions_per_s=ni * N_PART / (kms * 1e-3), j_chunks=info["slots"])
     elif args.workload == "small":
         # the 4096-body Plummer call (eps = 1/64) in one launch, graph-replayed
         n = args.n if args.n != N_PART else 4096
