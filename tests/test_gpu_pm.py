@@ -51,6 +51,45 @@ def test_pm_matches_the_oracle(pg, split, N, scale_cells, L):
     assert_mesh_parity(p[:, None], po[:, None], "phi")
 
 
+def test_deposit_runs_of_one_mesh_point(pg):
+    # The one-call deposit reads the particles in mesh order, where those of
+    # one mesh point are consecutive lanes whose weights a warp sums before
+    # its atomics. Runs of 1 to 70 particles around 300 points (runs that
+    # cross warps and end at lane 31), each particle a little off its point
+    # (distinct weights), plus a uniform background: the one-call forces
+    # against the oracle, and against the two-step form, which deposits in
+    # input order without the runs
+    rng = np.random.default_rng(7501)
+    N = 32
+    pts = rng.integers(0, N, size=(300, 3))
+    sizes = rng.integers(1, 71, size=300)
+    cl = np.repeat(pts, sizes, axis=0) / N + rng.uniform(-0.3, 0.3, (sizes.sum(), 3)) / N
+    x = np.mod(np.concatenate([cl, rng.random((3000, 3))]), 1.0)
+    x = x[rng.permutation(len(x))]
+    m = rng.uniform(0.5, 1.5, len(x)) / len(x)
+    scale = 1.25 / N
+    with pg.Context(0) as c:
+        c.set_periodic(1.0)
+        c.set_pm(N, pg.PG_SPLIT_GAUSS, scale)
+        a, p = c.pm_forces(x, m)
+    ao, po = opm.mesh_forces(x, m, 1.0, N, "gauss", scale)
+    assert_mesh_parity(a, ao, "a")
+    assert_mesh_parity(p[:, None], po[:, None], "phi")
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda:0")
+    xd, md = torch.tensor(x, device=dev), torch.tensor(m, device=dev)
+    with pg.Context(0) as c:
+        c.set_periodic(1.0)
+        c.set_pm(N, pg.PG_SPLIT_GAUSS, scale)
+        r = torch.empty(N ** 3, dtype=torch.float32, device=dev)
+        c.pm_deposit_dev(xd, md, r)
+        a2 = torch.empty_like(xd)
+        p2 = torch.empty_like(md)
+        c.pm_solve_dev(r, xd, a2, p2)
+        torch.cuda.synchronize()
+    assert_mesh_parity(a2.cpu().numpy(), a, "two steps against one call")
+
+
 def test_positions_outside_the_box_wrap(pg):
     x, m = gen.clustered_box(5000, 62, nclump=10, sigma=0.02)
     shift = np.random.default_rng(4).integers(-3, 4, size=x.shape).astype(np.float64)
