@@ -47,8 +47,8 @@ __host__ __device__ __forceinline__ long long sk_owner(long long u, long long gr
     return ((u + 1) * grid - 1) / W;
 }
 
-template <bool TABLE>
-__global__ void __launch_bounds__(kNT) k_backward(BackwardArgs a)
+// The table's backward (scalar FP32, kKI i per thread)
+__global__ void __launch_bounds__(kNT) k_backward_table(BackwardArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     double4 *rawx = reinterpret_cast<double4 *>(smem);                 // [2][kTJ]
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(kNT) k_backward(BackwardArgs a)
     uint64_t *bar = reinterpret_cast<uint64_t *>(cv + 2 * kTJ);
     int *flag = reinterpret_cast<int *>(bar + 2);
     float2 *tab = reinterpret_cast<float2 *>(bar + 4);
-    float *hist = reinterpret_cast<float *>(tab + (TABLE ? a.tab.n : 0));
+    float *hist = reinterpret_cast<float *>(tab + a.tab.n);
 
     const int tid = threadIdx.x;
     const long long G = gridDim.x, b = blockIdx.x;
@@ -69,11 +69,9 @@ __global__ void __launch_bounds__(kNT) k_backward(BackwardArgs a)
         mbar_init(&bar[1], 1);
         mbar_fence_init();
     }
-    if (TABLE) {
-        for (int k = tid; k < a.tab.n; k += kNT) {
-            tab[k] = a.tab.AG1[k];
-            hist[k] = 0.0f;
-        }
+    for (int k = tid; k < a.tab.n; k += kNT) {
+        tab[k] = a.tab.AG1[k];
+        hist[k] = 0.0f;
     }
     __syncthreads();
 
@@ -87,8 +85,8 @@ __global__ void __launch_bounds__(kNT) k_backward(BackwardArgs a)
         }
     }
 
-    const float c0 = TABLE ? 2.0f : a.eps2;
-    const double sc = TABLE ? a.tab.scale : 1.0;
+    const float c0 = 2.0f;
+    const double sc = a.tab.scale;
     float xk[kKI], yk[kKI], zk[kKI], mk[kKI], wkx[kKI], wky[kKI], wkz[kKI];
     float gx[kKI], gy[kKI], gz[kKI], gm[kKI];
     float hx[kKI], hy[kKI], hz[kKI], hm[kKI], lx[kKI], ly[kKI], lz[kKI], lm[kKI];
@@ -182,32 +180,23 @@ __global__ void __launch_bounds__(kNT) k_backward(BackwardArgs a)
                 const float uz = __fsub_rn(__fmul_rn(mk[q], w.z), __fmul_rn(p.w, wkz[q]));
                 const float du = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
                 const float wd = fmaf(dx, w.x, fmaf(dy, w.y, dz * w.z));
-                float K, c2;
-                if (!TABLE) {
-                    float q1 = rsq(r2);
-                    q1 = r2 > 0.0f ? q1 : 0.0f;
-                    const float qq = q1 * q1;
-                    K = q1 * qq;
-                    c2 = -3.0f * K * qq * du;
-                } else {
-                    const float sv = fminf(r2, a.tab.s_max);
-                    const unsigned bits = __float_as_uint(sv);
-                    const unsigned idx = (bits >> a.tab.shift) - a.tab.base;
-                    const float2 ag = tab[idx];
-                    K = fmaf(sv, ag.y, ag.x);
-                    c2 = 2.0f * ag.y * du;
-                    if (sv < a.tab.s_max) {
-                        // hat weights of the bin's two knots; the knot spacing
-                        // is 2^(exponent of s_k - F)
-                        const unsigned kb = bits & ~((1u << a.tab.shift) - 1u);
-                        const float sk = __uint_as_float(kb);
-                        const float ds = __uint_as_float((kb & 0x7f800000u) -
-                                                         ((unsigned)(23 - a.tab.shift) << 23));
-                        const float tt = (sv - sk) / ds;
-                        const float pw = p.w * fmaf(dx, wkx[q], fmaf(dy, wky[q], dz * wkz[q]));
-                        atomicAdd(&hist[idx], pw * (1.0f - tt));
-                        atomicAdd(&hist[idx + 1], pw * tt);
-                    }
+                const float sv = fminf(r2, a.tab.s_max);
+                const unsigned bits = __float_as_uint(sv);
+                const unsigned idx = (bits >> a.tab.shift) - a.tab.base;
+                const float2 ag = tab[idx];
+                const float K = fmaf(sv, ag.y, ag.x);
+                const float c2 = 2.0f * ag.y * du;
+                if (sv < a.tab.s_max) {
+                    // hat weights of the bin's two knots; the knot spacing
+                    // is 2^(exponent of s_k - F)
+                    const unsigned kb = bits & ~((1u << a.tab.shift) - 1u);
+                    const float sk = __uint_as_float(kb);
+                    const float ds = __uint_as_float((kb & 0x7f800000u) -
+                                                     ((unsigned)(23 - a.tab.shift) << 23));
+                    const float tt = (sv - sk) / ds;
+                    const float pw = p.w * fmaf(dx, wkx[q], fmaf(dy, wky[q], dz * wkz[q]));
+                    atomicAdd(&hist[idx], pw * (1.0f - tt));
+                    atomicAdd(&hist[idx + 1], pw * tt);
                 }
                 gx[q] = fmaf(K, ux, fmaf(c2, dx, gx[q]));
                 gy[q] = fmaf(K, uy, fmaf(c2, dy, gy[q]));
@@ -233,7 +222,7 @@ __global__ void __launch_bounds__(kNT) k_backward(BackwardArgs a)
         return;
     }
     if (cur >= 0) flush(cur);
-    if (TABLE && a.dv) {
+    if (a.dv) {
         __syncthreads();
         for (int k = tid; k < a.tab.n; k += kNT)
             if (hist[k] != 0.0f) atomicAdd(&a.dv[k], (double)hist[k]);
@@ -493,13 +482,12 @@ size_t backward_smem(bool table, int ntab)
     return s;
 }
 
-template <bool TABLE>
 static cudaError_t configure_b()
 {
     static bool done[kMaxDevices] = {};
     return once_per_device(done, [] {
-        return cudaFuncSetAttribute(k_backward<TABLE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)backward_smem(TABLE, 1 << 13));
+        return cudaFuncSetAttribute(k_backward_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)backward_smem(true, 1 << 13));
     });
 }
 
@@ -515,10 +503,10 @@ static cudaError_t configure_bn()
 // Newton: the packed kernel; table: the scalar one with the knot histogram
 int backward_max_blocks_per_sm(bool table, int ntab)
 {
-    cudaError_t e = table ? configure_b<true>() : configure_bn();
+    cudaError_t e = table ? configure_b() : configure_bn();
     if (e != cudaSuccess) return 1;
     int nb = 0;
-    e = table ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_backward<true>, kNT,
+    e = table ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_backward_table, kNT,
                                                              backward_smem(true, ntab))
               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_backward_newton, kNT,
                                                              backward_newton_smem());
@@ -529,9 +517,9 @@ cudaError_t launch_backward(const BackwardArgs &a, int grid, bool table, size_t 
                             cudaStream_t st)
 {
     if (grid <= 0) return cudaSuccess;
-    cudaError_t e = table ? configure_b<true>() : configure_bn();
+    cudaError_t e = table ? configure_b() : configure_bn();
     if (e != cudaSuccess) return e;
-    if (table) k_backward<true><<<grid, kNT, smem, st>>>(a);
+    if (table) k_backward_table<<<grid, kNT, smem, st>>>(a);
     else k_backward_newton<<<grid, kNT, backward_newton_smem(), st>>>(a);
     return cudaGetLastError();
 }
